@@ -1,0 +1,479 @@
+"""FP64 CPU oracle of the IBDL operator hot path (Leathers 2022, arXiv 2210.07403).
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this module. The CUDA product path never calls it, and this
+module shares no code with it (no kernels, headers, tables or helpers): the only common
+dependency is the seeded input generator ``ibdl_inputs``, which holds no method arithmetic.
+
+Everything here is a plain, slow, literal transcription of the discrete operators, written
+for a reader to check against the paper by eye:
+
+  δ_h         regularised delta, Sec. 2.2.2 (√-Peskin 4-point) and its cosine variant
+  S, S*       spread / interpolation, Sec. 2.2.2
+  S̃Q          dipole spread ∇·(S(Q n)), Sec. 5.1.1 and Sec. 5.3.1
+  -L⁻¹        periodic Fourier solve, Sec. 2.2.1, Sec. 2.2.4 (Δ₀⁻¹: mean-zero inverse)
+  A Q         −S* L⁻¹ S̃ Q + ½Q, Sec. 5.3.2 (Eq. "ibdl schur again")
+  A Q Stokes  −S*Δ₀⁻¹∇Δ₀⁻¹Δ S(Q·n) − S*Δ₀⁻¹ P ∇·(S A) + ½Q, Sec. 6.3.3 (interior, η = 0)
+  GMRES       unrestarted, zero initial guess, Sec. 5.3.2
+
+Readings of points the paper leaves open are listed with each function; all are the same
+readings the CUDA path takes.
+
+Array conventions: a grid field of dimension d has shape (N,)*d indexed [..., y, x]
+(x fastest); boundary arrays are SoA, X and n of shape (d, M), densities (c, M).
+
+Parity status: every function below is pinned by ``tests/test_oracle_pins.py`` against
+closed forms, invariants, brute force on tiny inputs or the paper's printed iteration counts.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+# ----------------------------------------------------------------------------------------
+# δ_h: one-dimensional kernels φ and their derivatives (Sec. 2.2.2)
+# ----------------------------------------------------------------------------------------
+
+
+def phi_sqrt(r):
+    """Peskin 4-point kernel (Sec. 2.2.2):
+    φ(r) = (3 − 2|r| + √(1 + 4|r| − 4r²))/8 for |r| ≤ 1,
+           (5 − 2|r| − √(−7 + 12|r| − 4r²))/8 for 1 ≤ |r| ≤ 2, 0 beyond."""
+    a = np.abs(np.asarray(r, dtype=np.float64))
+    out = np.zeros_like(a)
+    m1 = a <= 1
+    m2 = (a > 1) & (a < 2)
+    out[m1] = (3 - 2 * a[m1] + np.sqrt(1 + 4 * a[m1] - 4 * a[m1] ** 2)) / 8
+    out[m2] = (5 - 2 * a[m2] - np.sqrt(-7 + 12 * a[m2] - 4 * a[m2] ** 2)) / 8
+    return out
+
+
+def dphi_sqrt(r):
+    """dφ/dr of the √-Peskin kernel, differentiated piece by piece (C¹ at |r| = 0, 1, 2)."""
+    r = np.asarray(r, dtype=np.float64)
+    a = np.abs(r)
+    out = np.zeros_like(a)
+    m1 = a <= 1
+    m2 = (a > 1) & (a < 2)
+    out[m1] = (-2 + (2 - 4 * a[m1]) / np.sqrt(1 + 4 * a[m1] - 4 * a[m1] ** 2)) / 8
+    out[m2] = (-2 - (6 - 4 * a[m2]) / np.sqrt(-7 + 12 * a[m2] - 4 * a[m2] ** 2)) / 8
+    return np.sign(r) * out
+
+
+def phi_cos(r):
+    """Cosine 4-point kernel φ(r) = (1 + cos(πr/2))/4 for |r| < 2 (the workloads' delta)."""
+    r = np.asarray(r, dtype=np.float64)
+    return np.where(np.abs(r) < 2, 0.25 * (1 + np.cos(0.5 * np.pi * r)), 0.0)
+
+
+def dphi_cos(r):
+    r = np.asarray(r, dtype=np.float64)
+    return np.where(np.abs(r) < 2, -0.125 * np.pi * np.sin(0.5 * np.pi * r), 0.0)
+
+
+KERNELS = {"sqrt": (phi_sqrt, dphi_sqrt), "cos": (phi_cos, dphi_cos)}
+
+# ----------------------------------------------------------------------------------------
+# grid and boundary
+# ----------------------------------------------------------------------------------------
+
+
+@dataclass
+class Grid:
+    """Periodic box [origin, origin + box)^d with N nodes per axis, x_i = origin + i h
+    (Sec. 2.2.1, which uses origin −L/2)."""
+
+    dim: int
+    N: int
+    box: float = 1.0
+    origin: tuple = None
+
+    def __post_init__(self):
+        if self.origin is None:
+            self.origin = (0.0,) * self.dim
+        self.origin = tuple(float(o) for o in self.origin)
+
+    @property
+    def h(self) -> float:
+        return self.box / self.N
+
+    @property
+    def shape(self):
+        return (self.N,) * self.dim
+
+    def coords(self):
+        """Node coordinates as a list [x, y(, z)] of arrays of the grid's shape."""
+        ax = [self.origin[j] + self.h * np.arange(self.N) for j in range(self.dim)]
+        mesh = np.meshgrid(*ax[::-1], indexing="ij")  # [.., y, x] ordering
+        return mesh[::-1]
+
+
+@dataclass
+class Geometry:
+    """The discrete immersed boundary and the operator options."""
+
+    grid: Grid
+    X: np.ndarray  # (d, M)
+    n: np.ndarray  # (d, M) outward unit normals
+    w: np.ndarray  # (M,) quadrature weights Δs_i
+    delta: str = "cos"
+    dipole: str = "analytic"  # "analytic" | "spectral_div"
+    symbol: str = "spectral"  # "spectral" | "fd2"
+    pde: str = "scalar"  # "scalar" (L = Δ − λ) | "stokes" (μΔ, η = 0)
+    lam: float = 0.0
+    mu: float = 1.0
+
+    @property
+    def M(self) -> int:
+        return self.X.shape[1]
+
+    @property
+    def ncomp(self) -> int:
+        return self.grid.dim if self.pde == "stokes" else 1
+
+
+def geometry_from_problem(p) -> Geometry:
+    """Build a Geometry from an ``ibdl_inputs.Problem``."""
+    return Geometry(Grid(p.dim, p.N, p.box, p.origin), p.bd.X, p.bd.n, p.bd.w, p.delta,
+                    p.dipole, p.symbol, p.pde, p.lam, p.mu)
+
+
+def _stencil(geom: Geometry):
+    """For each point and axis, the four node indices touched by the 4-point kernel and the
+    scaled offsets r = (x_node − X)/h. The first node is floor((X − origin)/h) − 1, so the
+    four nodes straddle X; indices wrap periodically."""
+    g = geom.grid
+    xi = (geom.X - np.asarray(g.origin)[:, None]) / g.h  # (d, M)
+    base = np.floor(xi).astype(np.int64) - 1
+    a = np.arange(4)
+    idx = (base[:, :, None] + a) % g.N  # (d, M, 4)
+    r = (base[:, :, None] + a) - xi[:, :, None]  # (d, M, 4)
+    return idx, r
+
+
+def _offsets(dim):
+    return itertools.product(range(4), repeat=dim)
+
+
+def _node_index(idx, off):
+    """Tuple of index arrays in [..., y, x] order for stencil offset ``off``."""
+    d = len(off)
+    return tuple(idx[j, :, off[j]] for j in reversed(range(d)))
+
+
+# ----------------------------------------------------------------------------------------
+# S, S*, S̃ (Sec. 2.2.2, Sec. 5.3.1)
+# ----------------------------------------------------------------------------------------
+
+
+def spread(geom: Geometry, F: np.ndarray) -> np.ndarray:
+    """(S F)(x_g) = Σ_i F_i δ_h(x_g − X_i) Δs_i, δ_h = h^{−d} Π_j φ(x_j/h) (Sec. 2.2.2)."""
+    g = geom.grid
+    phi, _ = KERNELS[geom.delta]
+    idx, r = _stencil(geom)
+    out = np.zeros(g.shape)
+    for off in _offsets(g.dim):
+        wt = np.ones(geom.M)
+        for j in range(g.dim):
+            wt = wt * phi(r[j, :, off[j]])
+        np.add.at(out, _node_index(idx, off), F * geom.w * wt / g.h ** g.dim)
+    return out
+
+
+def interp(geom: Geometry, u: np.ndarray) -> np.ndarray:
+    """(S* u)(X_i) = Σ_g u_g δ_h(x_g − X_i) h^d (Sec. 2.2.2); at most 4^d terms per point."""
+    g = geom.grid
+    phi, _ = KERNELS[geom.delta]
+    idx, r = _stencil(geom)
+    out = np.zeros(geom.M)
+    for off in _offsets(g.dim):
+        wt = np.ones(geom.M)
+        for j in range(g.dim):
+            wt = wt * phi(r[j, :, off[j]])
+        out += u[_node_index(idx, off)] * wt
+    return out
+
+
+def spread_grad(geom: Geometry, V: np.ndarray) -> np.ndarray:
+    """Σ_i Δs_i Σ_m V_{m,i} ∂_m δ_h(x_g − X_i): the analytic divergence of S(V) for a
+    boundary vector field V of shape (d, M). With V = Q n this is S̃Q = ∇·(S(Q n))
+    (Sec. 5.1.1), the dipole spread with the exact gradient of δ_h."""
+    g = geom.grid
+    phi, dphi = KERNELS[geom.delta]
+    idx, r = _stencil(geom)
+    out = np.zeros(g.shape)
+    for off in _offsets(g.dim):
+        ph = [phi(r[j, :, off[j]]) for j in range(g.dim)]
+        dph = [dphi(r[j, :, off[j]]) / g.h for j in range(g.dim)]
+        val = np.zeros(geom.M)
+        for m in range(g.dim):
+            term = V[m].copy()
+            for j in range(g.dim):
+                term = term * (dph[j] if j == m else ph[j])
+            val += term
+        np.add.at(out, _node_index(idx, off), geom.w * val / g.h ** g.dim)
+    return out
+
+
+def interp_grad(geom: Geometry, u: np.ndarray) -> np.ndarray:
+    """(S*∇u)-like gather with the analytic kernel gradient: G_{m,i} = Σ_g u_g ∂_m δ_h(x_g − X_i) h^d.
+    This is the transpose partner of ``spread_grad`` (used by the adjoint operator)."""
+    g = geom.grid
+    phi, dphi = KERNELS[geom.delta]
+    idx, r = _stencil(geom)
+    out = np.zeros((g.dim, geom.M))
+    for off in _offsets(g.dim):
+        ph = [phi(r[j, :, off[j]]) for j in range(g.dim)]
+        dph = [dphi(r[j, :, off[j]]) / g.h for j in range(g.dim)]
+        ug = u[_node_index(idx, off)]
+        for m in range(g.dim):
+            term = ug.copy()
+            for j in range(g.dim):
+                term = term * (dph[j] if j == m else ph[j])
+            out[m] += term
+    return out
+
+
+# ----------------------------------------------------------------------------------------
+# Fourier symbols and the periodic solve (Sec. 2.2.1, Sec. 2.3.1, Sec. 2.2.4)
+# ----------------------------------------------------------------------------------------
+
+
+def wavenumbers(grid: Grid):
+    """k = 2π m / box with m = 0, 1, …, N/2 − 1, −N/2, …, −1 (np.fft ordering)."""
+    return 2 * np.pi * np.fft.fftfreq(grid.N, d=1.0 / grid.N) / grid.box
+
+
+def symbols(grid: Grid, kind: str):
+    """Per-axis symbols of the Laplacian and of the first derivative, broadcast to the grid.
+
+    spectral: −Δ ↦ Σ k_j², ∂_j ↦ i k_j, with the first-derivative symbol set to 0 at the
+              Nyquist index m = −N/2 (reading: that mode has no real counterpart; zeroing it
+              makes the discrete ∇· exactly minus the adjoint of ∇).
+    fd2:      5-point Laplacian −Δ ↦ Σ (4/h²) sin²(k_j h/2) (Sec. 2.2.1) and the centred
+              difference ∂_j ↦ i sin(k_j h)/h (Sec. 5.3.1), zero at Nyquist by itself.
+    Returns (lap, [deriv_j]) with lap real (the symbol of −Δ) and deriv_j imaginary."""
+    k = wavenumbers(grid)
+    h = grid.h
+    d = grid.dim
+    if kind == "spectral":
+        lap1 = k * k
+        kd = k.copy()
+        kd[grid.N // 2] = 0.0
+        der1 = 1j * kd
+    elif kind == "fd2":
+        lap1 = 4.0 / h ** 2 * np.sin(k * h / 2) ** 2
+        der1 = 1j * np.sin(k * h) / h
+    else:
+        raise ValueError(kind)
+    shape = grid.shape
+    lap = np.zeros(shape)
+    der = []
+    for j in range(d):
+        bshape = [1] * d
+        bshape[d - 1 - j] = grid.N  # axis j lives at array position d−1−j
+        lap = lap + lap1.reshape(bshape)
+        der.append(np.broadcast_to(der1.reshape(bshape), shape))
+    return lap, der
+
+
+def minus_Linv(geom: Geometry, f: np.ndarray) -> np.ndarray:
+    """u = −L⁻¹ f for L = Δ − λ on the periodic box: û = f̂ / (|k|²_sym + λ). When λ = 0 the
+    k = 0 mode is set to zero, i.e. Δ₀⁻¹ returns the mean-zero solution (Sec. 2.2.4)."""
+    lap, _ = symbols(geom.grid, geom.symbol)
+    F = np.fft.fftn(f)
+    den = lap + geom.lam
+    U = np.zeros_like(F)
+    nz = den != 0
+    U[nz] = F[nz] / den[nz]
+    return np.real(np.fft.ifftn(U))
+
+
+def dipole_field(geom: Geometry, Q: np.ndarray) -> np.ndarray:
+    """S̃Q = ∇·(S(Q n)) on the grid (Sec. 5.3.1). ``analytic``: the exact gradient of δ_h;
+    ``spectral_div``: spread the vector Q n, then take the divergence with the same Fourier
+    symbol family as the Laplacian (the paper's choice: match the PDE discretisation)."""
+    if geom.dipole == "analytic":
+        return spread_grad(geom, Q[None, :] * geom.n)
+    _, der = symbols(geom.grid, geom.symbol)
+    acc = np.zeros(geom.grid.shape, dtype=complex)
+    for j in range(geom.grid.dim):
+        acc += der[j] * np.fft.fftn(spread(geom, Q * geom.n[j]))
+    return np.real(np.fft.ifftn(acc))
+
+
+# ----------------------------------------------------------------------------------------
+# the IBDL Schur operator (scalar: Sec. 5.3.2; Stokes: Sec. 6.3.3)
+# ----------------------------------------------------------------------------------------
+
+
+def field_scalar(geom: Geometry, Q: np.ndarray) -> np.ndarray:
+    """u = −L⁻¹ S̃ Q on the grid (step 2 of the method in Sec. 5.1.2 with g̃ = 0)."""
+    return minus_Linv(geom, dipole_field(geom, Q))
+
+
+def stokes_velocity(geom: Geometry, Q: np.ndarray) -> np.ndarray:
+    """Velocity of the interior Stokes IBDL system (Sec. 6.1.1, Eq. "ibdl stokes"; Sec. 6.3.3
+    with η = 0, g̃ = 0) on the grid, shape (d, N, …):
+
+        u = −Δ₀⁻¹∇Δ₀⁻¹Δ S(Q·n) − Δ₀⁻¹ P ∇·(S A),   A_lm = Q_l n_m + Q_m n_l,
+        P = I − ∇Δ₀⁻¹∇·.
+
+    In Fourier space with k̃ the first-derivative symbol's wave vector and |k|² the
+    Laplacian's: û = (i k̃ ŝ + P̂ ĝ)/|k|², P̂ = I − k̃k̃ᵀ/|k|², û(0) = 0, where s = S(Q·n) and
+    g = ∇·(S A) (μ cancels because η = 0). Reading: Δ₀⁻¹Δ only removes the mean, which ∇
+    annihilates, so the source term is −∇Δ₀⁻¹ s, the same as the Brinkman form of Sec. 6.3.2.
+    ``analytic`` takes g_l = Σ_m ∂_m S(A_lm) with the exact gradient of δ_h;
+    ``spectral_div`` spreads A_lm and applies the derivative symbols."""
+    g = geom.grid
+    d = g.dim
+    Q = Q.reshape(d, geom.M)
+    n = geom.n
+    s_hat = np.fft.fftn(spread(geom, np.sum(Q * n, axis=0)))
+    lap, der = symbols(g, geom.symbol)
+    A = np.array([[Q[l] * n[m] + Q[m] * n[l] for m in range(d)] for l in range(d)])
+    g_hat = []
+    for l in range(d):
+        if geom.dipole == "analytic":
+            g_hat.append(np.fft.fftn(spread_grad(geom, A[l])))
+        else:
+            acc = np.zeros(g.shape, dtype=complex)
+            for m in range(d):
+                acc += der[m] * np.fft.fftn(spread(geom, A[l, m]))
+            g_hat.append(acc)
+    nz = lap != 0
+    inv = np.zeros(g.shape)
+    inv[nz] = 1.0 / lap[nz]
+    # k̃ k̃ᵀ with i k̃_l = der[l]  ⇒  k̃_l k̃_m = −der[l] der[m]
+    kdotg = sum(-1j * der[m] * g_hat[m] for m in range(d))  # k̃·ĝ
+    u = np.zeros((d,) + g.shape)
+    for l in range(d):
+        Pg = g_hat[l] - (-1j * der[l]) * kdotg * inv
+        U = (der[l] * s_hat + Pg) * inv
+        U[~nz] = 0.0
+        u[l] = np.real(np.fft.ifftn(U))
+    return u
+
+
+def grid_field(geom: Geometry, Q: np.ndarray) -> np.ndarray:
+    """The grid solution from a density: scalar u (shape grid) or Stokes velocity (d, grid)."""
+    if geom.pde == "stokes":
+        return stokes_velocity(geom, Q)
+    return field_scalar(geom, Q.reshape(-1))
+
+
+def apply(geom: Geometry, Q: np.ndarray) -> np.ndarray:
+    """A Q = S* u + ½ Q with u the grid field of Q: scalar A Q = −S*L⁻¹S̃Q + ½Q (Sec. 5.3.2),
+    Stokes A Q = S* u(Q) + ½Q (Sec. 6.3.3). Q and the result are flat SoA arrays (c·M,)."""
+    Q = np.asarray(Q, dtype=np.float64).reshape(-1)
+    if geom.pde == "stokes":
+        d = geom.grid.dim
+        u = stokes_velocity(geom, Q)
+        return np.concatenate([interp(geom, u[l]) for l in range(d)]) + 0.5 * Q
+    return interp(geom, field_scalar(geom, Q)) + 0.5 * Q
+
+
+def dipole_adjoint(geom: Geometry, u: np.ndarray) -> np.ndarray:
+    """(S̃)* u: the adjoint of the dipole spread under ⟨f, u⟩_h = h^d Σ_g f_g u_g and
+    ⟨a, b⟩_w = Σ_i Δs_i a_i b_i. analytic: Σ_m n_m Σ_g u_g ∂_m δ_h(x_g − X_i) h^d (the
+    kernel-gradient gather); spectral_div: −Σ_m n_m S*(∂_m u), because the derivative symbol
+    is imaginary and odd, i.e. anti-self-adjoint."""
+    if geom.dipole == "analytic":
+        return np.sum(geom.n * interp_grad(geom, u), axis=0)
+    _, der = symbols(geom.grid, geom.symbol)
+    U = np.fft.fftn(u)
+    return -sum(geom.n[m] * interp(geom, np.real(np.fft.ifftn(der[m] * U)))
+                for m in range(geom.grid.dim))
+
+
+def adjoint_apply(geom: Geometry, W: np.ndarray) -> np.ndarray:
+    """A* W for the scalar operator, adjoint with respect to the Δs-weighted boundary inner
+    product. S is adjoint to S* under the weighted products (Sec. 2.1, Sec. 2.2.4), and −L⁻¹
+    has a real even symbol, so it is self-adjoint; hence A* W = ½W + (S̃)*(−L⁻¹)(S W)."""
+    if geom.pde != "scalar":
+        raise NotImplementedError("adjoint implemented for the scalar operator")
+    W = np.asarray(W, dtype=np.float64).reshape(-1)
+    return 0.5 * W + dipole_adjoint(geom, minus_Linv(geom, spread(geom, W)))
+
+
+def dense_operator(geom: Geometry, fn=apply) -> np.ndarray:
+    """Assemble the operator column by column (c·M applications)."""
+    nd = geom.ncomp * geom.M
+    A = np.zeros((nd, nd))
+    e = np.zeros(nd)
+    for j in range(nd):
+        e[:] = 0
+        e[j] = 1
+        A[:, j] = fn(geom, e)
+    return A
+
+
+# ----------------------------------------------------------------------------------------
+# GMRES (Sec. 5.3.2: the Schur operator is not symmetric, so "gmres" is used)
+# ----------------------------------------------------------------------------------------
+
+
+@dataclass
+class GmresResult:
+    x: np.ndarray
+    iterations: int
+    history: list  # relative residual after each iteration (least-squares value)
+    true_rel_residual: float
+
+
+def gmres(op, b: np.ndarray, rtol: float, maxit: int = 50, x0=None) -> GmresResult:
+    """Unrestarted GMRES from the definition: after k steps, x_k = x0 + V_k y_k where V_k is an
+    orthonormal basis of the Krylov space K_k(A, r0) built by Arnoldi (modified Gram–Schmidt)
+    and y_k = argmin ‖β e₁ − H̄_k y‖₂ (solved by a library least-squares routine). Stops at the
+    first k with ‖β e₁ − H̄_k y_k‖₂ ≤ rtol·‖b‖₂ (relative Euclidean residual; reading of the
+    paper's "gmres, tolerance 1e-8")."""
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    x0 = np.zeros_like(b) if x0 is None else np.asarray(x0, dtype=np.float64).reshape(-1)
+    r0 = b - (op(x0) if np.any(x0) else 0.0)
+    beta = float(np.linalg.norm(r0))
+    bnorm = float(np.linalg.norm(b))
+    if beta == 0.0:
+        return GmresResult(x0, 0, [], 0.0)
+    V = [r0 / beta]
+    H = np.zeros((maxit + 1, maxit))
+    hist = []
+    y = np.zeros(0)
+    k = 0
+    for k in range(maxit):
+        w = op(V[k])
+        for j in range(k + 1):
+            H[j, k] = float(np.dot(V[j], w))
+            w = w - H[j, k] * V[j]
+        H[k + 1, k] = float(np.linalg.norm(w))
+        e1 = np.zeros(k + 2)
+        e1[0] = beta
+        y = np.linalg.lstsq(H[:k + 2, :k + 1], e1, rcond=None)[0]
+        res = float(np.linalg.norm(e1 - H[:k + 2, :k + 1] @ y))
+        hist.append(res / bnorm)
+        if res <= rtol * bnorm or H[k + 1, k] == 0.0:
+            break
+        V.append(w / H[k + 1, k])
+    x = x0 + np.stack(V[:k + 1], axis=1) @ y
+    true = float(np.linalg.norm(b - op(x))) / bnorm
+    return GmresResult(x, k + 1, hist, true)
+
+
+def solve(geom: Geometry, Ub: np.ndarray, rtol: float, maxit: int = 50) -> GmresResult:
+    """Q solving A Q = U_b (g̃ = 0, so the right-hand side is U_b; Sec. 5.1.2 step 1)."""
+    return gmres(lambda q: apply(geom, q), np.asarray(Ub, dtype=np.float64).reshape(-1),
+                 rtol, maxit)
+
+
+def fitted_order(hs, errs) -> float:
+    """Least-squares slope of log(err) against log(h)."""
+    return float(np.polyfit(np.log(hs), np.log(errs), 1)[0])
+
+
+def domain_norms(u_err: np.ndarray, mask: np.ndarray, h: float, dim: int, omega: float):
+    """L1, L2 and max norms scaled by the area of Ω (Sec. 2.2.1)."""
+    e = np.abs(u_err[mask])
+    return (h ** dim / omega * e.sum(), math.sqrt(h ** dim / omega * (e * e).sum()),
+            float(e.max()) if e.size else 0.0)

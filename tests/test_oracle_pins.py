@@ -1,0 +1,512 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics (CPU only).
+
+Each test checks the oracle against something other than itself: closed forms of the delta
+kernels, discrete identities the paper states, brute-force evaluation on tiny inputs, an
+independently assembled saddle-point system, manufactured solutions, and the GMRES iteration
+counts the paper prints. A plausible slip anywhere in the oracle (a dropped term, a sign, an
+index or transposition error) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import ibdl_inputs as I
+from oracle import ibdl_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                a, b, c = line.split()
+                rows.append((int(a), float(b), int(c)))
+    return rows
+
+
+# ----------------------------------------------------------------------------------------
+# δ_h kernels (Sec. 2.2.2)
+# ----------------------------------------------------------------------------------------
+
+FRAC = np.linspace(0, 1, 97)[:-1]
+
+
+@pytest.mark.parametrize("kind", ["sqrt", "cos"])
+def test_phi_partition_moments(kind):
+    phi, _ = O.KERNELS[kind]
+    j = np.arange(-4, 5)[:, None]
+    r = FRAC[None, :] - j
+    v = phi(r)
+    assert np.allclose(v.sum(0), 1.0, atol=1e-15)  # partition of unity
+    even = v[(j[:, 0] % 2) == 0].sum(0)
+    odd = v[(j[:, 0] % 2) == 1].sum(0)
+    assert np.allclose(even, 0.5, atol=1e-15) and np.allclose(odd, 0.5, atol=1e-15)
+    assert np.allclose((v * v).sum(0), 3.0 / 8.0, atol=1e-15)  # Σφ² = 3/8
+    m1 = (r * v).sum(0)
+    if kind == "sqrt":
+        assert np.allclose(m1, 0.0, atol=1e-15)  # first moment vanishes
+    else:
+        # cosine kernel: Σ (r−j) φ(r−j) = f − ½ + ½(cos(πf/2) − sin(πf/2)), f = frac(r)
+        ref = FRAC - 0.5 + 0.5 * (np.cos(np.pi * FRAC / 2) - np.sin(np.pi * FRAC / 2))
+        assert np.allclose(m1, ref, atol=1e-15)
+        assert 0.02 < np.abs(m1).max() < 0.022
+    assert np.all(v >= 0)
+    assert np.all(phi(np.array([2.0, -2.0, 2.5, 7.0])) == 0)
+
+
+def test_phi_sqrt_values():
+    # Closed-form values of the √-Peskin kernel.
+    assert O.phi_sqrt(np.array([0.0]))[0] == pytest.approx(0.5, abs=1e-16)
+    assert O.phi_sqrt(np.array([1.0]))[0] == pytest.approx(0.25, abs=1e-16)
+    assert O.phi_sqrt(np.array([0.5]))[0] == pytest.approx((2 + math.sqrt(2)) / 8, abs=1e-16)
+    assert O.phi_sqrt(np.array([1.5]))[0] == pytest.approx((2 - math.sqrt(2)) / 8, abs=1e-16)
+
+
+@pytest.mark.parametrize("kind", ["sqrt", "cos"])
+def test_dphi_is_derivative_and_c1(kind):
+    phi, dphi = O.KERNELS[kind]
+    r = np.linspace(-2.2, 2.2, 881)
+    r = r[np.min(np.abs(r[:, None] - np.array([-2, -1, 0, 1, 2])[None, :]), 1) > 1e-3]
+    e = 1e-6
+    fd = (phi(r + e) - phi(r - e)) / (2 * e)
+    assert np.allclose(dphi(r), fd, atol=1e-8)
+    for k in (0.0, 1.0, 2.0):  # continuity of φ' at the piece boundaries
+        for s in (1, -1):
+            x = s * k
+            assert dphi(np.array([x - 1e-9]))[0] == pytest.approx(dphi(np.array([x + 1e-9]))[0], abs=1e-6)
+    assert dphi(np.array([0.0]))[0] == 0.0
+
+
+# ----------------------------------------------------------------------------------------
+# S, S*, S̃ (Sec. 2.2.2, Sec. 5.3.1)
+# ----------------------------------------------------------------------------------------
+
+
+def _tiny_geom(dim=2, N=12, M=17, delta="cos", seed=0, box=1.3, origin=None, **kw):
+    rng = np.random.default_rng(seed)
+    origin = origin if origin is not None else tuple(rng.uniform(-0.5, 0.5, dim))
+    X = np.asarray(origin)[:, None] + rng.uniform(-0.5, 1.5, (dim, M)) * box  # some wrap around
+    n = rng.standard_normal((dim, M))
+    n /= np.linalg.norm(n, axis=0)
+    w = rng.uniform(0.5, 1.5, M) * box / N
+    return O.Geometry(O.Grid(dim, N, box, origin), X, n, w, delta, **kw)
+
+
+def _brute_delta(geom, which="phi"):
+    """Dense matrix D[g, i] = δ_h(x_g − X_i) (or ∂_m δ_h) evaluated over every node with the
+    periodic minimum image: independent of the oracle's stencil bookkeeping."""
+    g = geom.grid
+    phi, dphi = O.KERNELS[geom.delta]
+    coords = [c.reshape(-1) for c in g.coords()]
+    L = g.box
+    diffs = []
+    for j in range(g.dim):
+        dj = coords[j][:, None] - geom.X[j][None, :]
+        dj = dj - L * np.round(dj / L)
+        diffs.append(dj / g.h)
+    if which == "phi":
+        out = np.ones_like(diffs[0])
+        for j in range(g.dim):
+            out = out * phi(diffs[j])
+        return out / g.h ** g.dim
+    grads = []
+    for m in range(g.dim):
+        out = np.ones_like(diffs[0])
+        for j in range(g.dim):
+            out = out * (dphi(diffs[j]) / g.h if j == m else phi(diffs[j]))
+        grads.append(out / g.h ** g.dim)
+    return grads
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("delta", ["sqrt", "cos"])
+def test_spread_interp_bruteforce(dim, delta):
+    geom = _tiny_geom(dim=dim, N=10 if dim == 2 else 7, M=13, delta=delta, seed=dim)
+    D = _brute_delta(geom)
+    rng = np.random.default_rng(7)
+    F = rng.standard_normal(geom.M)
+    u = rng.standard_normal(geom.grid.shape)
+    assert np.allclose(O.spread(geom, F).reshape(-1), D @ (F * geom.w), rtol=1e-13, atol=1e-12)
+    assert np.allclose(O.interp(geom, u), geom.grid.h ** dim * (D.T @ u.reshape(-1)), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_spread_grad_bruteforce(dim):
+    geom = _tiny_geom(dim=dim, N=9 if dim == 2 else 7, M=11, delta="sqrt", seed=5)
+    G = _brute_delta(geom, "grad")
+    rng = np.random.default_rng(8)
+    V = rng.standard_normal((dim, geom.M))
+    ref = sum(G[m] @ (V[m] * geom.w) for m in range(dim))
+    assert np.allclose(O.spread_grad(geom, V).reshape(-1), ref, rtol=1e-12, atol=1e-10)
+    u = rng.standard_normal(geom.grid.shape)
+    ref2 = np.stack([geom.grid.h ** dim * (G[m].T @ u.reshape(-1)) for m in range(dim)])
+    assert np.allclose(O.interp_grad(geom, u), ref2, rtol=1e-12, atol=1e-10)
+
+
+@pytest.mark.parametrize("delta", ["sqrt", "cos"])
+def test_dipole_is_derivative_in_point_position(delta):
+    """∇_x δ_h(x − X) = −∇_X δ_h(x − X): S̃Q = ∇·S(Qn) equals minus the derivative of the
+    ordinary spread of Q when every point moves along its normal (central difference)."""
+    geom = _tiny_geom(N=16, M=21, delta=delta, seed=3)
+    rng = np.random.default_rng(4)
+    Q = rng.standard_normal(geom.M)
+    eps = 1e-5 * geom.grid.h
+
+    def moved(s):
+        gg = O.Geometry(geom.grid, geom.X + s * eps * geom.n, geom.n, geom.w, delta)
+        return O.spread(gg, Q)
+
+    fd = -(moved(1) - moved(-1)) / (2 * eps)
+    an = O.dipole_field(geom, Q)
+    assert np.allclose(an, fd, rtol=1e-6, atol=1e-6 * np.abs(an).max())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("delta", ["sqrt", "cos"])
+def test_adjointness_and_conservation(dim, delta):
+    """⟨SF, u⟩_h = ⟨F, S*u⟩_w (Sec. 2.1; discrete form Sec. 2.2.4), S*1 = 1, ∫SF = Σ Δs F."""
+    geom = _tiny_geom(dim=dim, N=16 if dim == 2 else 8, M=40, delta=delta, seed=11)
+    rng = np.random.default_rng(12)
+    F = rng.standard_normal(geom.M)
+    u = rng.standard_normal(geom.grid.shape)
+    h = geom.grid.h
+    lhs = h ** dim * np.sum(O.spread(geom, F) * u)
+    rhs = np.sum(geom.w * F * O.interp(geom, u))
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+    assert np.allclose(O.interp(geom, np.ones(geom.grid.shape)), 1.0, atol=1e-14)
+    assert h ** dim * O.spread(geom, F).sum() == pytest.approx(np.sum(geom.w * F), rel=1e-13)
+    V = rng.standard_normal((dim, geom.M))
+    lhs = h ** dim * np.sum(O.spread_grad(geom, V) * u)
+    rhs = np.sum(geom.w * V * O.interp_grad(geom, u))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+# ----------------------------------------------------------------------------------------
+# Fourier symbols and the periodic solve (Sec. 2.2.1, Sec. 2.2.4, Sec. 2.3.1)
+# ----------------------------------------------------------------------------------------
+
+
+def _lap5(u, h):
+    """5-point Laplacian (Sec. 2.2.1) by periodic shifts, any dimension."""
+    out = -2 * u.ndim * u
+    for ax in range(u.ndim):
+        out = out + np.roll(u, 1, ax) + np.roll(u, -1, ax)
+    return out / h ** 2
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("lam", [0.0, 7.5])
+def test_fd2_solve_inverts_five_point_stencil(dim, lam):
+    g = O.Grid(dim, 16 if dim == 2 else 8, 1.7, (0.1,) * dim)
+    geom = O.Geometry(g, np.zeros((dim, 1)), np.ones((dim, 1)), np.ones(1), symbol="fd2", lam=lam)
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal(g.shape)
+    if lam == 0.0:
+        f -= f.mean()  # solvability for the periodic Laplacian
+    v = O.minus_Linv(geom, f)
+    # −(Δ − λ) v = f  ⇔  v = −L⁻¹ f
+    assert np.allclose(-(_lap5(v, g.h) - lam * v), f, atol=1e-10 * np.abs(f).max())
+    if lam == 0.0:
+        assert abs(v.mean()) < 1e-13  # Δ₀⁻¹ returns the mean-zero solution
+
+
+@pytest.mark.parametrize("lam", [0.0, 3.0])
+def test_spectral_solve_single_modes(lam):
+    """On a Fourier mode cos(k·x + c) the spectral solve divides by |k|² + λ exactly."""
+    g = O.Grid(2, 16, 2.0, (-1.0, -1.0))
+    geom = O.Geometry(g, np.zeros((2, 1)), np.ones((2, 1)), np.ones(1), lam=lam)
+    x, y = g.coords()
+    for mx, my in [(1, 0), (0, 3), (2, -5), (7, 7), (3, 1)]:
+        kx, ky = 2 * np.pi * mx / g.box, 2 * np.pi * my / g.box
+        f = np.cos(kx * x + ky * y + 0.3)
+        assert np.allclose(O.minus_Linv(geom, f), f / (kx * kx + ky * ky + lam), atol=1e-14)
+    assert np.allclose(O.minus_Linv(geom, np.ones(g.shape)), 0.0 if lam == 0 else 1.0 / max(lam, 1))
+
+
+def test_derivative_symbols():
+    """Spectral ∂_x of sin(kx) is k cos(kx) except at the Nyquist mode (set to zero);
+    the fd2 symbol reproduces the centred difference."""
+    g = O.Grid(2, 16, 1.0)
+    x, y = g.coords()
+    _, der = O.symbols(g, "spectral")
+    for m in (1, 3, 7):
+        k = 2 * np.pi * m
+        got = np.real(np.fft.ifftn(der[0] * np.fft.fftn(np.sin(k * x + 0.2))))
+        assert np.allclose(got, k * np.cos(k * x + 0.2), atol=1e-11)
+        got = np.real(np.fft.ifftn(der[1] * np.fft.fftn(np.sin(k * y))))
+        assert np.allclose(got, k * np.cos(k * y), atol=1e-11)
+    nyq = np.cos(np.pi * 16 * x)  # the m = N/2 mode
+    assert np.allclose(np.real(np.fft.ifftn(der[0] * np.fft.fftn(nyq))), 0.0, atol=1e-12)
+    _, derf = O.symbols(g, "fd2")
+    u = np.random.default_rng(0).standard_normal(g.shape)
+    cd = (np.roll(u, -1, 1) - np.roll(u, 1, 1)) / (2 * g.h)
+    assert np.allclose(np.real(np.fft.ifftn(derf[0] * np.fft.fftn(u))), cd, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------------------
+# operator-level pins (Sec. 3, Sec. 5.3)
+# ----------------------------------------------------------------------------------------
+
+
+def _circle_geom(N, delta="sqrt", lam=0.0, dipole="analytic", symbol="spectral", alpha=1.0):
+    M = I.points_for_spacing(2 * np.pi * 0.25, 1.0 / N, alpha)
+    bd = I.circle(M)
+    return O.Geometry(O.Grid(2, N), bd.X, bd.n, bd.w, delta, dipole, symbol, "scalar", lam), bd
+
+
+@pytest.mark.parametrize("delta", ["sqrt", "cos"])
+def test_constant_density_jump(delta):
+    """Q ≡ 1: u = −Δ₀⁻¹S̃1 approximates χ_Ω − |Ω|/|C| (the indicator construction of
+    Sec. 5.3.5 via the Green's-derivative identity of Sec. 3), so S*u → ½ − |Ω|/|C| and
+    A·1 → 1 − |Ω|/|C| (= 1 − π/16 for the circle), at first order in h."""
+    target = 1 - math.pi / 16
+    errs = []
+    for N in (32, 64, 128):
+        geom, bd = _circle_geom(N, delta)
+        errs.append(abs(O.apply(geom, np.ones(bd.M)).mean() - target))
+        if N == 128:
+            u = O.field_scalar(geom, np.ones(bd.M))
+            x, y = geom.grid.coords()
+            r = np.hypot(x - 0.5, y - 0.5)
+            # the cosine kernel's non-zero first moment shifts the plateaus by O(h)
+            tol = 1e-3 if delta == "sqrt" else 2e-2
+            assert np.allclose(u[r < 0.15], 1 - math.pi / 16, atol=tol)
+            assert np.allclose(u[r > 0.4], -math.pi / 16, atol=tol)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.015
+    assert O.fitted_order([1 / 32, 1 / 64, 1 / 128], errs) > 0.7
+
+
+def test_circle_mode_one_periodic_correction():
+    """For Q = cos θ on the circle, the free-space double layer gives A Q = ½Q (the PV
+    integral of ∇G·n is constant on a circle, Sec. 3). The mean-zero periodic Green's function
+    adds |x|²/(4|C|), whose double-layer potential on the circle is (|Ω|/(2|C|)) cos θ, so the
+    cos θ coefficient of A Q tends to ½ + π/32; the m = 3 diagonal tends to ½."""
+    e1, e3 = [], []
+    for N in (64, 128, 256):
+        geom, bd = _circle_geom(N)
+        th = bd.t
+        c1 = 2 * np.mean(O.apply(geom, np.cos(th)) * np.cos(th))
+        c3 = 2 * np.mean(O.apply(geom, np.cos(3 * th)) * np.cos(3 * th))
+        e1.append(abs(c1 - (0.5 + math.pi / 32)))
+        e3.append(abs(c3 - 0.5))
+    assert e1[0] > e1[1] > e1[2] and e1[2] < 6e-3
+    assert e3[0] > e3[1] > e3[2] and e3[2] < 6e-3
+
+
+@pytest.mark.parametrize("delta,lam,dipole", [("sqrt", 0.0, "analytic"), ("cos", 3.0, "analytic"),
+                                              ("cos", 0.0, "spectral_div")])
+def test_gmres_matches_dense_lu(delta, lam, dipole):
+    geom, bd = _circle_geom(32, delta, lam, dipole)
+    Ub = I.harmonic_cubic(bd.X[0], bd.X[1])
+    A = O.dense_operator(geom)
+    q_lu = np.linalg.solve(A, Ub)
+    res = O.solve(geom, Ub, 1e-14, maxit=bd.M)
+    assert np.linalg.norm(res.x - q_lu) <= 1e-11 * np.linalg.norm(q_lu)
+    assert res.true_rel_residual < 1e-12
+
+
+@pytest.mark.parametrize("dipole", ["analytic", "spectral_div"])
+def test_saddle_system_dense(dipole):
+    """Assemble the un-reduced IBDL system [[L, S̃], [S*, ½I]] (Sec. 5.3.2) densely on a 16²
+    grid from stencils and brute-force kernel evaluations (5-point Laplacian, centred
+    differences; no FFT), solve it by LU, and compare Q and u with the oracle's GMRES on the
+    Schur operator and its grid field."""
+    N, lam = 16, 2.0
+    geom, bd = _circle_geom(N, "sqrt", lam, dipole, "fd2", alpha=1.5)
+    g = geom.grid
+    n2 = N * N
+    eye = np.eye(n2).reshape((n2,) + g.shape)
+    Lmat = np.stack([(_lap5(e, g.h) - lam * e).reshape(-1) for e in eye], axis=1)
+    D = _brute_delta(geom)  # (n2, M)
+    if dipole == "analytic":
+        G = _brute_delta(geom, "grad")
+        St = sum(G[m] * (geom.w * geom.n[m])[None, :] for m in range(2))
+    else:
+        def cdiff(u, ax):
+            return (np.roll(u, -1, ax) - np.roll(u, 1, ax)) / (2 * g.h)
+        St = np.zeros((n2, bd.M))
+        for m, ax in ((0, 1), (1, 0)):
+            cols = (D * (geom.w * geom.n[m])[None, :]).T.reshape((bd.M,) + g.shape)
+            St += np.stack([cdiff(c, ax).reshape(-1) for c in cols], axis=1)
+    Sstar = g.h ** 2 * D.T
+    K = np.block([[Lmat, St], [Sstar, 0.5 * np.eye(bd.M)]])
+    Ub = np.sin(2 * bd.t)
+    sol = np.linalg.solve(K, np.concatenate([np.zeros(n2), Ub]))
+    u_lu, q_lu = sol[:n2], sol[n2:]
+    res = O.solve(geom, Ub, 1e-14, maxit=bd.M)
+    assert np.allclose(res.x, q_lu, rtol=0, atol=1e-10 * np.abs(q_lu).max())
+    assert np.allclose(O.field_scalar(geom, res.x).reshape(-1), u_lu, atol=1e-10 * np.abs(u_lu).max())
+
+
+def test_null_vector_of_unreduced_system():
+    """(u, Q) = (χ_{C∖Ω}, −1) is in the null space of [[Δ, S̃], [S*, ½I]] (Sec. 5.3.3): with the
+    mean-zero inverse, u = −Δ₀⁻¹S̃(−1) equals χ_{C∖Ω} up to a constant and the regularisation
+    error, and S*(χ_{C∖Ω}) + ½(−1) ≈ 0 on Γ."""
+    geom, bd = _circle_geom(128)
+    u = O.field_scalar(geom, -np.ones(bd.M))
+    x, y = geom.grid.coords()
+    r = np.hypot(x - 0.5, y - 0.5)
+    outside = u[r > 0.4].mean()
+    inside = u[r < 0.15].mean()
+    assert outside - inside == pytest.approx(1.0, abs=5e-3)
+    chi = u - inside  # ≈ χ_{C∖Ω}
+    assert np.allclose(O.interp(geom, chi) - 0.5, 0.0, atol=2e-2)
+
+
+@pytest.mark.parametrize("dipole", ["analytic", "spectral_div"])
+def test_adjoint_identity(dipole):
+    geom, bd = _circle_geom(32, "cos", 2.0, dipole)
+    rng = np.random.default_rng(3)
+    Q, W = rng.standard_normal(bd.M), rng.standard_normal(bd.M)
+    lhs = np.sum(bd.w * O.apply(geom, Q) * W)
+    rhs = np.sum(bd.w * Q * O.adjoint_apply(geom, W))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+# ----------------------------------------------------------------------------------------
+# the paper's printed numbers and manufactured solutions
+# ----------------------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("row", _golden("ibdl_iterations_circle_helmholtz.txt"))
+def test_paper_iteration_table(row):
+    N, alpha, its = row
+    p = I.paper_circle_helmholtz(N, alpha)
+    res = O.solve(O.geometry_from_problem(p), p.Ub, 1e-8)
+    assert res.iterations == its
+
+
+@pytest.mark.parametrize("row", _golden("ibdl_iterations_tol1e-10.txt"))
+def test_paper_iterations_tight_tolerance(row):
+    N, alpha, its = row
+    p = I.paper_circle_helmholtz(N, alpha)
+    res = O.solve(O.geometry_from_problem(p), p.Ub, 1e-10)
+    assert abs(res.iterations - its) <= 1
+
+
+def test_first_order_convergence_paper_helmholtz():
+    """u = I₂(r) sin 2θ / I₂(0.25) solves the paper's circle Helmholtz problem (Sec. 5.4.1);
+    away from Γ the IBDL grid solution converges at first order."""
+    special = pytest.importorskip("scipy.special")
+    errs, hs = [], []
+    for N in (64, 128, 256):
+        p = I.paper_circle_helmholtz(N, 1.0)
+        geom = O.geometry_from_problem(p)
+        q = O.solve(geom, p.Ub, 1e-10).x
+        u = O.field_scalar(geom, q)
+        x, y = geom.grid.coords()
+        r = np.hypot(x, y)
+        ex = special.iv(2, r) * np.sin(2 * np.arctan2(y, x)) / special.iv(2, 0.25)
+        errs.append(np.abs(u - ex)[r < 0.15].max())
+        hs.append(1.0 / N)
+    assert O.fitted_order(hs, errs) > 0.85
+
+
+@pytest.mark.parametrize("delta", ["cos", "sqrt"])
+def test_harmonic_cubic_converges(delta):
+    """The workload's Laplace problem, u = Re((z − z0)^3): interior error decreases with h."""
+    errs = []
+    for N in (32, 64, 128):
+        p = I.circle_laplace(N, I.points_for_spacing(2 * np.pi * 0.25, 1.0 / N), delta=delta)
+        geom = O.geometry_from_problem(p)
+        res = O.solve(geom, p.Ub, 1e-10)
+        assert res.iterations <= 8
+        u = O.field_scalar(geom, res.x)
+        x, y = geom.grid.coords()
+        r = np.hypot(x - 0.5, y - 0.5)
+        errs.append(np.abs(u - I.harmonic_cubic(x, y))[r < 0.15].max())
+    assert errs[0] > errs[1] > errs[2]
+    assert O.fitted_order([1 / 32, 1 / 64, 1 / 128], errs) > 0.4
+
+
+# ----------------------------------------------------------------------------------------
+# Stokes (Sec. 6.1, Sec. 6.3.3)
+# ----------------------------------------------------------------------------------------
+
+
+def _stokes_geom(N, delta="sqrt", dipole="analytic", symbol="spectral"):
+    M = I.points_for_spacing(2 * np.pi * 0.25, 1.0 / N)
+    bd = I.circle(M)
+    return O.Geometry(O.Grid(2, N), bd.X, bd.n, bd.w, delta, dipole, symbol, "stokes"), bd
+
+
+@pytest.mark.parametrize("dipole", ["analytic", "spectral_div"])
+def test_stokes_velocity_satisfies_pde(dipole):
+    """The velocity returned for a density satisfies, mode by mode away from Nyquist, the
+    discrete equations of Sec. 6.1.1: ∇·u + S(Q·n) = 0 and Δu + ∇·(S A) = ∇p for some p
+    (a gradient ⇔ zero discrete curl), with mean-zero u."""
+    geom, bd = _stokes_geom(32, dipole=dipole)
+    g = geom.grid
+    rng = np.random.default_rng(9)
+    Q = rng.standard_normal((2, bd.M))
+    u = O.stokes_velocity(geom, Q.reshape(-1))
+    lap, der = O.symbols(g, "spectral")
+    Uh = [np.fft.fftn(u[0]), np.fft.fftn(u[1])]
+    sh = np.fft.fftn(O.spread(geom, np.sum(Q * bd.n, 0)))
+    A = [[Q[l] * bd.n[m] + Q[m] * bd.n[l] for m in range(2)] for l in range(2)]
+    if dipole == "analytic":
+        gh = [np.fft.fftn(O.spread_grad(geom, np.array(A[l]))) for l in range(2)]
+    else:
+        gh = [sum(der[m] * np.fft.fftn(O.spread(geom, A[l][m])) for m in range(2)) for l in range(2)]
+    kx = np.broadcast_to(np.fft.fftfreq(32, 1 / 32)[None, :], g.shape)
+    ky = np.broadcast_to(np.fft.fftfreq(32, 1 / 32)[:, None], g.shape)
+    ok = (np.abs(kx) != 16) & (np.abs(ky) != 16) & (lap != 0)
+    div = der[0] * Uh[0] + der[1] * Uh[1] + sh
+    assert np.abs(div[ok]).max() < 1e-9 * np.abs(sh).max()
+    mom = [-lap * Uh[l] + gh[l] for l in range(2)]
+    curl = der[0] * mom[1] - der[1] * mom[0]
+    assert np.abs(curl[ok]).max() < 1e-9 * np.abs(gh[0]).max() * 2 * np.pi * 16
+    assert abs(u[0].mean()) < 1e-14 and abs(u[1].mean()) < 1e-14
+
+
+@pytest.mark.parametrize("flow", ["poly", "rotation"])
+def test_stokes_first_order(flow):
+    fn = I.stokes_poly if flow == "poly" else I.rigid_rotation
+    errs = []
+    for N in (64, 128, 256):
+        geom, bd = _stokes_geom(N)
+        Ub = fn(bd.X[0], bd.X[1])
+        res = O.solve(geom, Ub, 1e-10, maxit=60)
+        assert res.iterations <= 14  # Sec. 6.4.1 reports 9-10 for the Brinkman analogue
+        u = O.stokes_velocity(geom, res.x)
+        x, y = geom.grid.coords()
+        r = np.hypot(x - 0.5, y - 0.5)
+        errs.append(np.abs(u - fn(x, y)).max(0)[r < 0.15].max())
+    assert O.fitted_order([1 / 64, 1 / 128, 1 / 256], errs) > 0.85
+
+
+def test_stokes_gmres_matches_dense_lu():
+    geom, bd = _stokes_geom(32)
+    Ub = I.stokes_poly(bd.X[0], bd.X[1]).reshape(-1)
+    A = O.dense_operator(geom)
+    q_lu = np.linalg.solve(A, Ub)
+    res = O.solve(geom, Ub, 1e-13, maxit=2 * bd.M)
+    assert np.linalg.norm(res.x - q_lu) <= 1e-9 * np.linalg.norm(q_lu)
+
+
+# ----------------------------------------------------------------------------------------
+# 3-D
+# ----------------------------------------------------------------------------------------
+
+
+def test_sphere_harmonic_converges():
+    """The 3-D workload's problem on coarse grids: x² − y² + z(x − 0.5) is harmonic, and the
+    interior error of the IBDL solution decreases as the grid is refined."""
+    errs = []
+    for N in (16, 24, 32):
+        M = int(round(4 * np.pi * 0.25 ** 2 * N * N))
+        p = I.sphere_poisson(N, M)
+        geom = O.geometry_from_problem(p)
+        res = O.solve(geom, p.Ub, 1e-8)
+        assert res.iterations <= 10
+        u = O.field_scalar(geom, res.x)
+        x, y, z = geom.grid.coords()
+        r = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)
+        errs.append(np.abs(u - I.harmonic_3d(x, y, z))[r < 0.12].max())
+    assert errs[0] > errs[1] > errs[2]
