@@ -1,0 +1,179 @@
+/*
+ * ibdl.h — C ABI of the GB300 (sm_103a) implementation of the Immersed Boundary Double Layer
+ * (IBDL) operator and its GMRES solve (Leathers 2022, arXiv 2210.07403).
+ *
+ * The problem (Sec. 5.1, Sec. 6.1): find the boundary density Q of the second-kind system
+ *
+ *     L u + S̃ Q = 0 in the periodic box C,      S* u + ½ Q = U_b on Γ,
+ *
+ * with L = Δ − λ (screened Poisson, λ ≥ 0, Sec. 5.1.1) or the Stokes system
+ * μΔu − ∇p + μ∇·(S A) = 0, ∇·u + S(Q·n) = 0 (Sec. 6.1.1, interior domain, η = 0). Eliminating
+ * u gives the Schur operator applied at every GMRES iteration (Sec. 5.3.2, Eq. "ibdl schur
+ * again"; Sec. 6.3.3):
+ *
+ *     A Q = −S* L⁻¹ S̃ Q + ½ Q.
+ *
+ * Data layout (all entry points):
+ *   - boundary arrays are structure-of-arrays, FP64: X and normals are [dim][n_points]
+ *     (x coordinates first), weights [n_points]; densities and data are [c][n_points] with
+ *     c = 1 (scalar) or c = dim (Stokes: Q_x[M] then Q_y[M]).
+ *   - grid fields are row-major with x fastest: u[z][y][x].
+ *   - the grid is cubic: n nodes per axis on [origin, origin + box)^dim, h = box / n,
+ *     node i at origin + i·h (Sec. 2.2.1).
+ *
+ * Ownership: the caller owns every pointer it passes. ibdl_create_geometry copies X, normals
+ * and weights and owns all workspace (grid spectra, sorted point tables, twiddles, Krylov
+ * basis); nothing the caller passes is retained after a call returns.
+ *
+ * Streams: every call enqueues its work on the CUDA stream given (a cudaStream_t passed as
+ * void*; NULL = the legacy default stream). ibdl_apply, ibdl_adjoint and ibdl_evaluate_field
+ * are asynchronous. ibdl_solve synchronises the stream before returning its status.
+ *
+ * Errors: every call returns an ibdl_status and never aborts the process. On failure,
+ * ibdl_last_error() returns a message describing the last error on the calling thread.
+ *
+ * Threads: a geometry may be used by one thread at a time; distinct geometries are independent.
+ */
+#ifndef IBDL_H
+#define IBDL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IBDL_OK = 0,
+  IBDL_ERR_INVALID_ARG = 1,   /* a null pointer, an out-of-range size or option          */
+  IBDL_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has the CUDA error) */
+  IBDL_ERR_NO_MEMORY = 3,     /* device or pinned host allocation failed                 */
+  IBDL_ERR_NOT_CONVERGED = 4, /* GMRES hit maxit; Q holds the best iterate               */
+  IBDL_ERR_NONFINITE = 5,     /* NaN/Inf in the inputs or in a residual                  */
+  IBDL_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up                      */
+  IBDL_ERR_UNSUPPORTED = 7    /* a valid combination this build does not implement       */
+} ibdl_status;
+
+/* PDE on the periodic box */
+enum { IBDL_PDE_SCALAR = 0, /* L = Δ − λ (Sec. 5.1.1); λ = 0 uses the mean-zero Δ₀⁻¹ (Sec. 2.2.4) */
+       IBDL_PDE_STOKES = 1  /* μΔu − ∇p, interior, η = 0 (Sec. 6.3.3); dim = 2 only           */ };
+
+/* one-dimensional 4-point kernel φ of δ_h = h^-d Π φ(x_j/h) (Sec. 2.2.2) */
+enum { IBDL_DELTA_COS = 0,  /* φ(r) = (1 + cos(πr/2))/4, |r| < 2                            */
+       IBDL_DELTA_SQRT = 1  /* Peskin's 4-point kernel with square roots (Sec. 2.2.2)         */ };
+
+/* discretisation of the dipole spread S̃Q = ∇·(S(Q n)) (Sec. 5.1.1, Sec. 5.3.1) */
+enum { IBDL_DIPOLE_ANALYTIC = 0,     /* exact gradient of δ_h: one scalar field (Stokes: 3)   */
+       IBDL_DIPOLE_SPECTRAL_DIV = 1  /* spread Q n, divergence by the derivative symbol       */ };
+
+/* Fourier symbols of the differential operators (Sec. 2.2.1, Sec. 2.3.1, Sec. 5.3.1) */
+enum { IBDL_SYMBOL_SPECTRAL = 0, /* −Δ ↦ |k|², ∂ ↦ ik (0 at the Nyquist index)             */
+       IBDL_SYMBOL_FD2 = 1       /* 5-point Laplacian and centred first differences         */ };
+
+/* arithmetic of the grid work inside one operator application */
+enum { IBDL_FP64 = 0, IBDL_FP32 = 1,
+       IBDL_MIXED = 2 /* solve only: FP32 applies, FP64 Arnoldi and FP64 refinement residual */ };
+
+typedef struct ibdl_geometry ibdl_geometry; /* opaque, library-owned */
+
+typedef struct {
+  int dim;              /* 2 or 3                                                          */
+  int n;                /* grid nodes per axis: a power of two, 16..8192 (2-D), 16..256 (3-D) */
+  double box;           /* side length of the periodic box, > 0                             */
+  double origin[3];     /* lower corner of the box (unused entries ignored)                 */
+  int64_t n_points;     /* M ≥ 1                                                           */
+  const double* X;      /* [dim][M] boundary points                                         */
+  const double* normals;/* [dim][M] unit normals pointing out of Ω                          */
+  const double* weights;/* [M] quadrature weights Δs_i (arclength, Sec. 2.2.2)               */
+  int pde;              /* IBDL_PDE_*                                                       */
+  double lambda;        /* screening λ ≥ 0 for IBDL_PDE_SCALAR                               */
+  double mu;            /* viscosity μ > 0 for IBDL_PDE_STOKES (cancels from A when η = 0)   */
+  int delta;            /* IBDL_DELTA_*                                                     */
+  int dipole;           /* IBDL_DIPOLE_*                                                    */
+  int symbol;           /* IBDL_SYMBOL_*                                                    */
+  int inputs_on_device; /* nonzero: X, normals, weights are device pointers                 */
+} ibdl_geometry_desc;
+
+typedef struct {
+  double rtol;          /* stop when ‖U_b − A Q‖₂ ≤ rtol·‖U_b‖₂ (relative Euclidean residual)  */
+  int restart;          /* Krylov subspace size m before a restart, 1..64                    */
+  int maxit;            /* maximum total Krylov iterations (all restarts and sweeps)         */
+  int precision;        /* IBDL_FP64 (plain), IBDL_FP32 or IBDL_MIXED (FP32 inner, FP64 outer) */
+  double inner_rtol;    /* IBDL_MIXED: relative tolerance of each inner FP32-apply GMRES      */
+  int max_refine;       /* IBDL_MIXED: maximum refinement sweeps                             */
+  int io_on_host;       /* nonzero: U_b and Q are host pointers (copied inside the call)     */
+} ibdl_solve_opts;
+
+typedef struct {
+  int iterations;       /* Krylov iterations, all cycles and sweeps                          */
+  int fp64_applies;     /* operator applications with FP64 grid arithmetic                   */
+  int fp32_applies;     /* operator applications with FP32 grid arithmetic                   */
+  int sweeps;           /* refinement sweeps (IBDL_MIXED), restart cycles otherwise          */
+  double rel_residual;  /* final ‖U_b − A₆₄Q‖₂/‖U_b‖₂ with an FP64 application (plain: the    */
+                        /* GMRES estimate of the last cycle)                                 */
+  double seconds;       /* wall time of the call                                             */
+  int64_t kernel_launches; /* CUDA kernels this call launched (including ones that found the  */
+                        /* solve already converged and returned at once)                     */
+} ibdl_solve_info;
+
+/* Stage timing (off by default). When enabled, every operator application records CUDA events
+ * on the caller's stream around each of its kernels, and every Arnoldi step around its kernel.
+ * ibdl_get_stage_times synchronises the device, adds up the device milliseconds and the
+ * launches of every stage recorded since the previous call, writes them to ms[] and launches[]
+ * (IBDL_STAGE_COUNT entries each), and resets the record. At most 16384 events are kept; later
+ * launches are not timed. */
+enum { IBDL_STAGE_SPREAD_ROWFFT_FP64 = 0, IBDL_STAGE_COLUMN_FP64 = 1, IBDL_STAGE_ROWIFFT_GATHER_FP64 = 2,
+       IBDL_STAGE_SPREAD_ROWFFT_FP32 = 3, IBDL_STAGE_COLUMN_FP32 = 4, IBDL_STAGE_ROWIFFT_GATHER_FP32 = 5,
+       IBDL_STAGE_ARNOLDI = 6, IBDL_STAGE_OTHER = 7, IBDL_STAGE_COUNT = 8 };
+ibdl_status ibdl_set_stage_timing(ibdl_geometry* geom, int enable);
+ibdl_status ibdl_get_stage_times(ibdl_geometry* geom, double* ms, int64_t* launches);
+
+/* Build the geometry: copy the boundary, bucket points by stencil cell, precompute the kernel
+ * weights (FP64 and FP32) and FFT twiddles, allocate all workspace. Points may lie outside
+ * the box; they wrap periodically. Errors: IBDL_ERR_INVALID_ARG (sizes, non-unit normals,
+ * non-positive weights, non-finite coordinates), IBDL_ERR_UNSUPPORTED (Stokes in 3-D),
+ * IBDL_ERR_NO_MEMORY, IBDL_ERR_CUDA. Synchronises `stream`. */
+ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* desc, void* stream, ibdl_geometry** out);
+
+/* Release all device and host memory of the geometry. Safe on NULL. Synchronises the device. */
+ibdl_status ibdl_destroy_geometry(ibdl_geometry* geom);
+
+/* Y = A Q = S*u + ½Q with u = −L⁻¹S̃Q (scalar, Sec. 5.3.2 Eq. "ibdl schur again") or the
+ * Stokes velocity of Sec. 6.3.3. Q and Y are device FP64 arrays [c][M] (they may not alias);
+ * `precision` (IBDL_FP64 or IBDL_FP32) selects the grid arithmetic. Asynchronous on `stream`. */
+ibdl_status ibdl_apply(ibdl_geometry* geom, int precision, const double* Q, double* Y, void* stream);
+
+/* Z = A* W, the adjoint of A with respect to the Δs-weighted boundary inner product
+ * Σ_i Δs_i a_i b_i: A* W = ½W + (S̃)* (−L⁻¹) S W, where S* is the adjoint of S under the weighted
+ * products (Sec. 2.1, Sec. 2.2.4). Scalar PDE only (IBDL_ERR_UNSUPPORTED for Stokes). Device
+ * FP64 arrays [M]; asynchronous. */
+ibdl_status ibdl_adjoint(ibdl_geometry* geom, int precision, const double* W, double* Z, void* stream);
+
+/* Solve A Q = U_b by GMRES from a zero initial guess (Sec. 5.1.2 step 1 and Sec. 5.3.2 with
+ * g̃ = 0). IBDL_FP64: restarted GMRES(m), FP64 everything. IBDL_MIXED: iterative refinement,
+ * each sweep an inner GMRES with FP32 applications and FP64 Arnoldi/Hessenberg, then the FP64
+ * residual U_b − A₆₄Q. U_b and Q are [c][M] FP64, device pointers unless opts->io_on_host.
+ * Returns IBDL_ERR_NOT_CONVERGED (Q = best iterate) when maxit is reached. `info` may be NULL. */
+ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const ibdl_solve_opts* opts,
+                       ibdl_solve_info* info, void* stream);
+
+/* The grid solution of a density (Sec. 5.1.2 step 2 with g̃ = 0): scalar u = −L⁻¹S̃Q written
+ * to u_grid[n^dim]; Stokes velocity written to u_grid[dim][n^dim]. FP64 device arrays;
+ * asynchronous. */
+ibdl_status ibdl_evaluate_field(ibdl_geometry* geom, const double* Q, double* u_grid, void* stream);
+
+/* Default solve options: rtol 1e-8, restart 50, maxit 200, IBDL_FP64, inner_rtol 1e-4,
+ * max_refine 6, device I/O. */
+void ibdl_default_solve_opts(ibdl_solve_opts* opts);
+
+/* Geometry facts: number of density components c and points M. */
+ibdl_status ibdl_geometry_sizes(const ibdl_geometry* geom, int* ncomp, int64_t* n_points);
+
+/* Message for the last failed call on this thread ("" if none). Valid until the next call. */
+const char* ibdl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBDL_H */

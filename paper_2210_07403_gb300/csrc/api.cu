@@ -1,0 +1,173 @@
+// extern "C" entry points of include/ibdl.h: argument checks, then the launchers.
+#include <cstring>
+#include <string>
+
+#include "ibdl_internal.cuh"
+
+struct ibdl_geometry {
+  ibdl::Geometry* g;
+};
+
+namespace ibdl {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+ibdl_status fail(ibdl_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+ibdl_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? IBDL_ERR_NO_MEMORY : IBDL_ERR_CUDA;
+}
+
+ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometry** out);
+ibdl_status destroy_geometry(Geometry* g);
+
+// Device (or managed) memory check for caller buffers handed to kernels: a host pointer
+// passed to a kernel would fault, so it is rejected here instead.
+static ibdl_status check_device_ptr(const void* p, const char* name) {
+  if (!p) return fail(IBDL_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IBDL_ERR_INVALID_ARG, std::string(name) + " is not a CUDA device pointer");
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(IBDL_ERR_INVALID_ARG, std::string(name) + " is not a CUDA device pointer");
+  return IBDL_OK;
+}
+
+static bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + bytes && pb < pa + bytes;
+}
+
+}  // namespace ibdl
+
+using namespace ibdl;
+
+extern "C" {
+
+ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* desc, void* stream, ibdl_geometry** out) {
+  set_error("");
+  if (!out) return fail(IBDL_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  Geometry* g = nullptr;
+  ibdl_status st = create_geometry(desc, static_cast<cudaStream_t>(stream), &g);
+  if (st != IBDL_OK) return st;
+  *out = new ibdl_geometry{g};
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_destroy_geometry(ibdl_geometry* geom) {
+  set_error("");
+  if (!geom) return IBDL_OK;
+  ibdl_status st = destroy_geometry(geom->g);
+  delete geom;
+  return st;
+}
+
+ibdl_status ibdl_apply(ibdl_geometry* geom, int precision, const double* Q, double* Y, void* stream) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
+  Geometry* g = geom->g;
+  IBDL_TRY(check_device_ptr(Q, "Q"));
+  IBDL_TRY(check_device_ptr(Y, "Y"));
+  if (ranges_overlap(Q, Y, sizeof(double) * g->ncomp * g->M)) return fail(IBDL_ERR_INVALID_ARG, "Q and Y overlap");
+  return apply_any(g, precision, Q, Y, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+ibdl_status ibdl_adjoint(ibdl_geometry* geom, int precision, const double* W, double* Z, void* stream) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
+  Geometry* g = geom->g;
+  if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_adjoint: scalar PDE only");
+  IBDL_TRY(check_device_ptr(W, "W"));
+  IBDL_TRY(check_device_ptr(Z, "Z"));
+  if (ranges_overlap(W, Z, sizeof(double) * g->M)) return fail(IBDL_ERR_INVALID_ARG, "W and Z overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return g->dim == 2 ? adjoint_2d(g, precision, W, Z, s) : adjoint_3d(g, precision, W, Z, s);
+}
+
+void ibdl_default_solve_opts(ibdl_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->rtol = 1e-8;
+  o->restart = 50;
+  o->maxit = 200;
+  o->precision = IBDL_FP64;
+  o->inner_rtol = 1e-4;
+  o->max_refine = 6;
+  o->io_on_host = 0;
+}
+
+ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const ibdl_solve_opts* opts,
+                       ibdl_solve_info* info, void* stream) {
+  set_error("");
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  ibdl_solve_opts o;
+  if (opts)
+    o = *opts;
+  else
+    ibdl_default_solve_opts(&o);
+  if (!(o.rtol > 0) || !(o.rtol < 1)) return fail(IBDL_ERR_INVALID_ARG, "rtol must be in (0, 1)");
+  if (o.restart < 1 || o.restart > 64) return fail(IBDL_ERR_INVALID_ARG, "restart must be in [1, 64]");
+  if (o.maxit < 1) return fail(IBDL_ERR_INVALID_ARG, "maxit must be >= 1");
+  if (o.precision != IBDL_FP64 && o.precision != IBDL_FP32 && o.precision != IBDL_MIXED)
+    return fail(IBDL_ERR_INVALID_ARG, "unknown precision");
+  if (o.precision == IBDL_MIXED && (!(o.inner_rtol > 0) || !(o.inner_rtol < 1) || o.max_refine < 1))
+    return fail(IBDL_ERR_INVALID_ARG, "mixed precision needs inner_rtol in (0, 1) and max_refine >= 1");
+  if (!Ub || !Q) return fail(IBDL_ERR_INVALID_ARG, "U_b and Q are required");
+  if (!o.io_on_host) {
+    IBDL_TRY(check_device_ptr(Ub, "U_b"));
+    IBDL_TRY(check_device_ptr(Q, "Q"));
+  }
+  const int64_t before = geom->g->launches;
+  ibdl_status st = solve_impl(geom->g, Ub, Q, &o, info, static_cast<cudaStream_t>(stream));
+  if (info) info->kernel_launches = geom->g->launches - before;
+  return st;
+}
+
+ibdl_status ibdl_evaluate_field(ibdl_geometry* geom, const double* Q, double* u_grid, void* stream) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  IBDL_TRY(check_device_ptr(Q, "Q"));
+  IBDL_TRY(check_device_ptr(u_grid, "u_grid"));
+  Geometry* g = geom->g;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return g->dim == 2 ? field_2d(g, Q, u_grid, s) : field_3d(g, Q, u_grid, s);
+}
+
+ibdl_status ibdl_geometry_sizes(const ibdl_geometry* geom, int* ncomp, int64_t* n_points) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (ncomp) *ncomp = geom->g->ncomp;
+  if (n_points) *n_points = geom->g->M;
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_set_stage_timing(ibdl_geometry* geom, int enable) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  return set_stage_timing(geom->g, enable);
+}
+
+ibdl_status ibdl_get_stage_times(ibdl_geometry* geom, double* ms, int64_t* launches) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (!ms || !launches) return fail(IBDL_ERR_INVALID_ARG, "ms and launches are required");
+  return get_stage_times(geom->g, ms, launches);
+}
+
+const char* ibdl_last_error(void) { return ibdl::g_last_error.c_str(); }
+
+}  // extern "C"

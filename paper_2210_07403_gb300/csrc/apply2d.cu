@@ -1,0 +1,570 @@
+// Two-dimensional IBDL operator: spread → FFT → Fourier symbol → inverse FFT → interpolate.
+//
+// One application A Q = S* u + ½Q, u = −L⁻¹ S̃ Q (Sec. 5.3.2) or the Stokes velocity (Sec. 6.3.3),
+// runs as three kernels, each owning a disjoint piece of the grid (no global atomics on the grid
+// and no grid memset):
+//
+//   k_spread_rowfft   band of R rows: accumulate the dipole sources of every point whose 4×4
+//                     stencil meets the band (shared-memory atomics), FFT along x with two real
+//                     rows packed as one complex row, unpack to the packed half spectrum.
+//   k_colpass         group of C kx columns: FFT along y, Fourier symbol, inverse FFT along y.
+//   k_rowifft_gather  band of R rows: inverse FFT along x, then interpolate (S*) the band's part
+//                     of every point's stencil and add it to Y (which the first kernel set to ½Q).
+//
+// Packed half spectrum: for a real row a, A_k (k = 0..n/2) is stored at [0, n/2) with slot 0
+// holding (A_0, A_{n/2}), both real. Along y, the kx = 0 and kx = n/2 columns are therefore one
+// complex column a + i b with a, b real columns; the column pass separates them by Hermitian
+// symmetry before the symbol and repacks after it.
+#include <type_traits>
+
+#include "fft.cuh"
+
+namespace ibdl {
+
+enum { OP_SCALAR_AN = 0, OP_SCALAR_SD = 1, OP_STOKES_AN = 2, OP_STOKES_SD = 3, OP_ADJ_AN = 4,
+       OP_ADJ_SD = 5 };
+
+// grid fields entering / leaving the Fourier stage, and boundary components in / out
+template <int OP>
+struct Traits;
+template <>
+struct Traits<OP_SCALAR_AN> { static constexpr int NIN = 1, NOUT = 1, C = 1; };  // f = S̃Q
+// (NMAX = max(NIN, NOUT) sizes the shared buffers of the column pass)
+template <>
+struct Traits<OP_SCALAR_SD> { static constexpr int NIN = 2, NOUT = 1, C = 1; };  // S(Qn_x), S(Qn_y)
+template <>
+struct Traits<OP_STOKES_AN> { static constexpr int NIN = 3, NOUT = 2, C = 2; };  // s, g_x, g_y
+template <>
+struct Traits<OP_STOKES_SD> { static constexpr int NIN = 4, NOUT = 2, C = 2; };  // s, A11, A22, A12
+template <>
+struct Traits<OP_ADJ_AN> { static constexpr int NIN = 1, NOUT = 1, C = 1; };     // S W
+template <>
+struct Traits<OP_ADJ_SD> { static constexpr int NIN = 1, NOUT = 2, C = 1; };     // S W → ∂_x v, ∂_y v
+
+enum { G_INTERP = 0, G_GRID = 1 };
+
+constexpr int kThreads = 256;
+
+template <typename T>
+struct RowParams {
+  int n, log2n, R;
+  int M;
+  const int* cell_start;
+  const int* base;
+  const int* perm;
+  const T* phi;
+  const T* dphi;
+  const T* wscale;
+  const T* nrm;
+  const double* in;   // [c][M] density
+  double* out;        // [c][M] result (first kernel stores ½·in, last kernel adds S*u)
+  cplx<T>* spec;      // [nf][n][n/2]
+  const cplx<T>* tw;  // [n]
+  const int* stop;    // optional: skip all work when *stop != 0
+  double* grid;       // G_GRID: [nf][n][n]
+};
+
+template <typename T>
+struct ColParams {
+  int n, log2n, C;
+  T lam, scale;
+  const T* lap1;
+  const T* der1;
+  cplx<T>* spec;
+  const cplx<T>* tw;
+  const int* stop;
+};
+
+// Sorted points whose base row lies in the cell rows [r0 − 3, r0 + R) (mod n): at most two
+// contiguous ranges of the cell-sorted order.
+struct PointRanges {
+  int s0, cnt1, s2, cnt;
+  __device__ int at(int t) const { return t < cnt1 ? s0 + t : s2 + (t - cnt1); }
+};
+__device__ __forceinline__ PointRanges band_points(const int* cell_start, int n, int r0, int R) {
+  PointRanges pr;
+  const int lo = r0 - 3, hi = r0 + R;
+  if (lo >= 0) {
+    pr.s0 = cell_start[lo];
+    pr.cnt1 = cell_start[hi] - pr.s0;
+    pr.s2 = 0;
+    pr.cnt = pr.cnt1;
+  } else {
+    pr.s0 = cell_start[lo + n];
+    pr.cnt1 = cell_start[n] - pr.s0;
+    pr.s2 = cell_start[0];
+    pr.cnt = pr.cnt1 + (cell_start[hi] - pr.s2);
+  }
+  return pr;
+}
+
+// ------------------------------------------------------------------------------------------
+// kernel 1: spread + forward FFT along x
+// ------------------------------------------------------------------------------------------
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
+  if (p.stop && *p.stop) return;
+  constexpr int NIN = Traits<OP>::NIN;
+  constexpr int NC = Traits<OP>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, R = p.R, half = R >> 1, M = p.M;
+  const int seqs = NIN * half;
+  cplx<T>* bufA = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufB = bufA + (size_t)seqs * n;
+  T* acc = reinterpret_cast<T*>(bufA);  // field f, local row lr, column x at ((f·half + lr/2)·n + x)·2 + (lr & 1)
+  const int r0 = blockIdx.x * R;
+
+  // jump term: out = ½·in (the gather kernel adds S*u afterwards)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NC * M; i += gridDim.x * blockDim.x)
+    p.out[i] = 0.5 * p.in[i];
+  for (int i = threadIdx.x; i < seqs * n * 2; i += blockDim.x) acc[i] = T(0);
+  __syncthreads();
+
+  const PointRanges pr = band_points(p.cell_start, n, r0, R);
+  for (int t = threadIdx.x; t < pr.cnt; t += blockDim.x) {
+    const int s = pr.at(t);
+    const int i = p.perm[s];
+    const int bx = p.base[s], by = p.base[M + s];
+    T px[4], py[4], dx[4], dy[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      px[a] = p.phi[(0 * 4 + a) * M + s];
+      py[a] = p.phi[(1 * 4 + a) * M + s];
+      dx[a] = p.dphi[(0 * 4 + a) * M + s];
+      dy[a] = p.dphi[(1 * 4 + a) * M + s];
+    }
+    const T ws = p.wscale[s];
+    const T nx = p.nrm[s], ny = p.nrm[M + s];
+    // per-point source strengths
+    T c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    if (OP == OP_SCALAR_AN || OP == OP_SCALAR_SD) {
+      const T q = T(p.in[i]) * ws;
+      c0 = q * nx;
+      c1 = q * ny;
+    } else if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
+      const T qx = T(p.in[i]), qy = T(p.in[M + i]);
+      c0 = ws * (qx * nx + qy * ny);      // Q·n
+      c1 = ws * (T(2) * qx * nx);         // A_xx
+      c2 = ws * (T(2) * qy * ny);         // A_yy
+      c3 = ws * (qx * ny + qy * nx);      // A_xy
+    } else {
+      c0 = T(p.in[i]) * ws;               // plain spread of W
+    }
+#pragma unroll
+    for (int ay = 0; ay < 4; ++ay) {
+      const int row = (by + ay) & (n - 1);
+      const int lr = (row - r0) & (n - 1);
+      if (lr >= R) continue;
+      T* rowp = acc + (size_t)(lr >> 1) * n * 2 + (lr & 1);
+      const size_t fstride = (size_t)half * n * 2;
+#pragma unroll
+      for (int ax = 0; ax < 4; ++ax) {
+        const int col = (bx + ax) & (n - 1);
+        T* cell = rowp + (size_t)col * 2;
+        const T pp = px[ax] * py[ay];
+        if (OP == OP_SCALAR_AN) {
+          atomicAdd(cell, c0 * dx[ax] * py[ay] + c1 * px[ax] * dy[ay]);
+        } else if (OP == OP_SCALAR_SD) {
+          atomicAdd(cell, c0 * pp);
+          atomicAdd(cell + fstride, c1 * pp);
+        } else if (OP == OP_STOKES_AN) {
+          const T ddx = dx[ax] * py[ay], ddy = px[ax] * dy[ay];
+          atomicAdd(cell, c0 * pp);
+          atomicAdd(cell + fstride, c1 * ddx + c3 * ddy);      // g_x = ∂_x S(A_xx) + ∂_y S(A_xy)
+          atomicAdd(cell + 2 * fstride, c3 * ddx + c2 * ddy);  // g_y = ∂_x S(A_xy) + ∂_y S(A_yy)
+        } else if (OP == OP_STOKES_SD) {
+          atomicAdd(cell, c0 * pp);
+          atomicAdd(cell + fstride, c1 * pp);
+          atomicAdd(cell + 2 * fstride, c2 * pp);
+          atomicAdd(cell + 3 * fstride, c3 * pp);
+        } else {
+          atomicAdd(cell, c0 * pp);
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  const cplx<T>* res = fft_stockham<T, false>(bufA, bufB, p.log2n, seqs, n, p.tw);
+
+  // unpack Z = FFT(a + i b) into A = FFT(a), B = FFT(b), k = 0..n/2, packed format
+  const int nh = n >> 1, lnh = p.log2n - 1;
+  for (int t = threadIdx.x; t < seqs * nh; t += blockDim.x) {
+    const int sq = t >> lnh, k = t & (nh - 1);
+    const int f = sq / half, j = sq - f * half;
+    const cplx<T>* Z = res + (size_t)sq * n;
+    cplx<T> A, B;
+    if (k == 0) {
+      const cplx<T> z0 = Z[0], zh = Z[nh];
+      A = mk(z0.x, zh.x);
+      B = mk(z0.y, zh.y);
+    } else {
+      const cplx<T> zk = Z[k], zc = Z[n - k];
+      A = mk(T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y));
+      B = mk(T(0.5) * (zk.y + zc.y), T(0.5) * (zc.x - zk.x));
+    }
+    const int row = r0 + 2 * j;
+    p.spec[((size_t)f * n + row) * nh + k] = A;
+    p.spec[((size_t)f * n + row + 1) * nh + k] = B;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Fourier symbols: NIN transformed fields in → NOUT out at wavenumber indices (kx, ky)
+// ------------------------------------------------------------------------------------------
+template <typename T, int OP>
+__device__ __forceinline__ void apply_symbol(const ColParams<T>& p, int kx, int ky, const cplx<T>* in,
+                                             cplx<T>* out) {
+  const T lap = p.lap1[kx] + p.lap1[ky];
+  const T dkx = p.der1[kx], dky = p.der1[ky];
+  if (OP == OP_SCALAR_AN || OP == OP_SCALAR_SD || OP == OP_ADJ_AN || OP == OP_ADJ_SD) {
+    // −L⁻¹ ↦ 1/(|k|² + λ), zero mode dropped when λ = 0 (Δ₀⁻¹)
+    const T den = lap + p.lam;
+    const T sig = den != T(0) ? p.scale / den : T(0);
+    if (OP == OP_SCALAR_AN || OP == OP_ADJ_AN) {
+      out[0] = cscale(in[0], sig);
+    } else if (OP == OP_SCALAR_SD) {
+      // ∇·F ↦ i(k̃_x F̂_x + k̃_y F̂_y)
+      const cplx<T> d = cadd(cscale(in[0], dkx), cscale(in[1], dky));
+      out[0] = cscale(cmuli(d), sig);
+    } else {
+      const cplx<T> v = cscale(in[0], sig);
+      out[0] = cscale(cmuli(v), dkx);
+      out[1] = cscale(cmuli(v), dky);
+    }
+  } else {
+    // Stokes, interior, η = 0: û = (i k̃ ŝ + P̂ ĝ)/|k|², P̂ = I − k̃k̃ᵀ/|k|²
+    const T inv = lap != T(0) ? T(1) / lap : T(0);
+    cplx<T> gx, gy;
+    if (OP == OP_STOKES_AN) {
+      gx = in[1];
+      gy = in[2];
+    } else {  // ĝ_l = i k̃_m Â_lm with fields A11, A22, A12 in slots 1, 2, 3
+      gx = cmuli(cadd(cscale(in[1], dkx), cscale(in[3], dky)));
+      gy = cmuli(cadd(cscale(in[3], dkx), cscale(in[2], dky)));
+    }
+    const cplx<T> kg = cadd(cscale(gx, dkx), cscale(gy, dky));
+    const cplx<T> is = cmuli(in[0]);
+    const T sc = inv * p.scale;
+    out[0] = cscale(cadd(cscale(is, dkx), csub(gx, cscale(kg, dkx * inv))), sc);
+    out[1] = cscale(cadd(cscale(is, dky), csub(gy, cscale(kg, dky * inv))), sc);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// kernel 2: FFT along y, symbol, inverse FFT along y, for C kx columns per CTA
+// ------------------------------------------------------------------------------------------
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
+  if (p.stop && *p.stop) return;
+  constexpr int NIN = Traits<OP>::NIN;
+  constexpr int NOUT = Traits<OP>::NOUT;
+  constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, C = p.C, nh = n >> 1;
+  cplx<T>* bufA = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufB = bufA + (size_t)NMAX * C * n;
+  const int k0 = blockIdx.x * C;
+
+  for (int t = threadIdx.x; t < NIN * n * C; t += blockDim.x) {
+    const int f = t / (n * C);
+    const int rem = t - f * n * C;
+    const int row = rem / C, c = rem - row * C;
+    bufA[(size_t)(f * C + c) * n + row] = p.spec[((size_t)f * n + row) * nh + k0 + c];
+  }
+  __syncthreads();
+  cplx<T>* res = fft_stockham<T, false>(bufA, bufB, p.log2n, NIN * C, n, p.tw);
+  cplx<T>* other = res == bufA ? bufB : bufA;
+
+  for (int t = threadIdx.x; t < C * n; t += blockDim.x) {
+    const int c = t / n, ky = t - c * n;
+    const int kx = k0 + c;
+    cplx<T> in[NIN], out[NOUT];
+    if (kx != 0) {
+#pragma unroll
+      for (int f = 0; f < NIN; ++f) in[f] = res[(size_t)(f * C + c) * n + ky];
+      apply_symbol<T, OP>(p, kx, ky, in, out);
+#pragma unroll
+      for (int f = 0; f < NOUT; ++f) res[(size_t)(f * C + c) * n + ky] = out[f];
+    } else if (ky <= nh) {
+      // packed kx = 0 | kx = n/2 column: P = Â + i B̂ with Â, B̂ Hermitian in ky
+      const int j = ky, jp = (n - ky) & (n - 1);
+      cplx<T> Aj[NIN], Ajp[NIN], Bj[NIN], Bjp[NIN];
+#pragma unroll
+      for (int f = 0; f < NIN; ++f) {
+        const cplx<T> P = res[(size_t)(f * C + c) * n + j];
+        const cplx<T> Pp = res[(size_t)(f * C + c) * n + jp];
+        // Â(j) = (P(j) + conj P(−j))/2, B̂(j) = −i (P(j) − conj P(−j))/2
+        Aj[f] = mk(T(0.5) * (P.x + Pp.x), T(0.5) * (P.y - Pp.y));
+        Bj[f] = mk(T(0.5) * (P.y + Pp.y), T(0.5) * (Pp.x - P.x));
+        Ajp[f] = mk(T(0.5) * (Pp.x + P.x), T(0.5) * (Pp.y - P.y));
+        Bjp[f] = mk(T(0.5) * (Pp.y + P.y), T(0.5) * (P.x - Pp.x));
+      }
+      cplx<T> oA[NOUT], oB[NOUT], oAp[NOUT], oBp[NOUT];
+      apply_symbol<T, OP>(p, 0, j, Aj, oA);
+      apply_symbol<T, OP>(p, nh, j, Bj, oB);
+      apply_symbol<T, OP>(p, 0, jp, Ajp, oAp);
+      apply_symbol<T, OP>(p, nh, jp, Bjp, oBp);
+#pragma unroll
+      for (int f = 0; f < NOUT; ++f) {
+        res[(size_t)(f * C + c) * n + j] = cadd(oA[f], cmuli(oB[f]));
+        if (jp != j) res[(size_t)(f * C + c) * n + jp] = cadd(oAp[f], cmuli(oBp[f]));
+      }
+    }
+  }
+  __syncthreads();
+  const cplx<T>* out = fft_stockham<T, true>(res, other, p.log2n, NOUT * C, n, p.tw);
+  for (int t = threadIdx.x; t < NOUT * n * C; t += blockDim.x) {
+    const int f = t / (n * C);
+    const int rem = t - f * n * C;
+    const int row = rem / C, c = rem - row * C;
+    p.spec[((size_t)f * n + row) * nh + k0 + c] = out[(size_t)(f * C + c) * n + row];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// kernel 3: inverse FFT along x, then interpolation (or write the grid)
+// ------------------------------------------------------------------------------------------
+template <typename T, int OP, int GMODE>
+__global__ void __launch_bounds__(kThreads) k_rowifft_gather(RowParams<T> p) {
+  if (p.stop && *p.stop) return;
+  constexpr int NOUT = Traits<OP>::NOUT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, R = p.R, half = R >> 1, M = p.M, nh = n >> 1, lnh = p.log2n - 1;
+  const int seqs = NOUT * half;
+  cplx<T>* bufA = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufB = bufA + (size_t)seqs * n;
+  const int r0 = blockIdx.x * R;
+
+  // rebuild Z = A + i B over all k from the packed half spectra of rows (r0+2j, r0+2j+1)
+  for (int t = threadIdx.x; t < seqs * nh; t += blockDim.x) {
+    const int sq = t >> lnh, k = t & (nh - 1);
+    const int f = sq / half, j = sq - f * half;
+    const int row = r0 + 2 * j;
+    const cplx<T> A = p.spec[((size_t)f * n + row) * nh + k];
+    const cplx<T> B = p.spec[((size_t)f * n + row + 1) * nh + k];
+    cplx<T>* Z = bufA + (size_t)sq * n;
+    if (k == 0) {
+      Z[0] = mk(A.x, B.x);
+      Z[nh] = mk(A.y, B.y);
+    } else {
+      Z[k] = mk(A.x - B.y, A.y + B.x);
+      Z[n - k] = mk(A.x + B.y, B.x - A.y);
+    }
+  }
+  __syncthreads();
+  const cplx<T>* res = fft_stockham<T, true>(bufA, bufB, p.log2n, seqs, n, p.tw);
+  const T* u = reinterpret_cast<const T*>(res);  // field f, row lr, col x at ((f·half + lr/2)·n + x)·2 + (lr&1)
+  const size_t fstride = (size_t)half * n * 2;
+
+  if (GMODE == G_GRID) {
+    for (int t = threadIdx.x; t < NOUT * R * n; t += blockDim.x) {
+      const int f = t / (R * n);
+      const int rem = t - f * R * n;
+      const int lr = rem / n, x = rem - lr * n;
+      p.grid[((size_t)f * n + r0 + lr) * n + x] = double(u[f * fstride + ((size_t)(lr >> 1) * n + x) * 2 + (lr & 1)]);
+    }
+    return;
+  }
+
+  const PointRanges pr = band_points(p.cell_start, n, r0, R);
+  for (int t = threadIdx.x; t < pr.cnt; t += blockDim.x) {
+    const int s = pr.at(t);
+    const int i = p.perm[s];
+    const int bx = p.base[s], by = p.base[M + s];
+    T px[4], py[4], dx[4], dy[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      px[a] = p.phi[(0 * 4 + a) * M + s];
+      py[a] = p.phi[(1 * 4 + a) * M + s];
+      if (OP == OP_ADJ_AN) {
+        dx[a] = p.dphi[(0 * 4 + a) * M + s];
+        dy[a] = p.dphi[(1 * 4 + a) * M + s];
+      }
+    }
+    T acc0 = 0, acc1 = 0;
+    bool touched = false;
+#pragma unroll
+    for (int ay = 0; ay < 4; ++ay) {
+      const int row = (by + ay) & (n - 1);
+      const int lr = (row - r0) & (n - 1);
+      if (lr >= R) continue;
+      touched = true;
+      const T* rowp = u + (size_t)(lr >> 1) * n * 2 + (lr & 1);
+#pragma unroll
+      for (int ax = 0; ax < 4; ++ax) {
+        const int col = (bx + ax) & (n - 1);
+        const T v0 = rowp[(size_t)col * 2];
+        if (OP == OP_ADJ_AN) {
+          acc0 += v0 * dx[ax] * py[ay];
+          acc1 += v0 * px[ax] * dy[ay];
+        } else {
+          const T pp = px[ax] * py[ay];
+          acc0 += v0 * pp;
+          if (NOUT == 2) acc1 += rowp[fstride + (size_t)col * 2] * pp;
+        }
+      }
+    }
+    if (!touched) continue;
+    if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
+      atomicAdd(p.out + i, double(acc0));
+      atomicAdd(p.out + M + i, double(acc1));
+    } else if (OP == OP_ADJ_AN) {
+      // (S̃)* v = n · (kernel-gradient gather of v)
+      atomicAdd(p.out + i, double(p.nrm[s]) * double(acc0) + double(p.nrm[M + s]) * double(acc1));
+    } else if (OP == OP_ADJ_SD) {
+      // (S̃)* v = −Σ_m n_m S*(∂_m v)
+      atomicAdd(p.out + i, -(double(p.nrm[s]) * double(acc0) + double(p.nrm[M + s]) * double(acc1)));
+    } else {
+      atomicAdd(p.out + i, double(acc0));
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+template <typename T>
+static RowParams<T> row_params(Geometry* g, const double* in, double* out, const int* stop, double* grid) {
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  RowParams<T> rp;
+  rp.n = g->n;
+  rp.log2n = __builtin_ctz(g->n);
+  rp.R = g->rows_per_cta[pi];
+  rp.M = (int)g->M;
+  rp.cell_start = g->cell_start;
+  rp.base = g->base;
+  rp.perm = g->perm;
+  const PointTable<T>& tb = *reinterpret_cast<const PointTable<T>*>(pi ? (const void*)&g->t32 : (const void*)&g->t64);
+  rp.phi = tb.phi;
+  rp.dphi = tb.dphi;
+  rp.wscale = tb.wscale;
+  rp.nrm = tb.nrm;
+  rp.in = in;
+  rp.out = out;
+  rp.spec = reinterpret_cast<cplx<T>*>(g->spec);
+  rp.tw = reinterpret_cast<const cplx<T>*>(pi ? (const void*)g->tw32 : (const void*)g->tw64);
+  rp.stop = stop;
+  rp.grid = grid;
+  return rp;
+}
+
+template <typename T>
+static ColParams<T> col_params(Geometry* g, const int* stop) {
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  ColParams<T> cp;
+  cp.n = g->n;
+  cp.log2n = __builtin_ctz(g->n);
+  cp.C = g->cols_per_cta[pi];
+  cp.lam = T(g->pde == IBDL_PDE_SCALAR ? g->lambda : 0.0);
+  cp.scale = T(1.0 / ((double)g->n * (double)g->n));
+  cp.lap1 = reinterpret_cast<const T*>(pi ? (const void*)g->lap32 : (const void*)g->lap64);
+  cp.der1 = reinterpret_cast<const T*>(pi ? (const void*)g->der32 : (const void*)g->der64);
+  cp.spec = reinterpret_cast<cplx<T>*>(g->spec);
+  cp.tw = reinterpret_cast<const cplx<T>*>(pi ? (const void*)g->tw32 : (const void*)g->tw64);
+  cp.stop = stop;
+  return cp;
+}
+
+template <typename T, int OP>
+static size_t smem_spread(const Geometry* g, int R) {
+  return 2 * (size_t)Traits<OP>::NIN * (R / 2) * g->n * sizeof(cplx<T>);
+}
+template <typename T, int OP>
+static size_t smem_gather(const Geometry* g, int R) {
+  return 2 * (size_t)Traits<OP>::NOUT * (R / 2) * g->n * sizeof(cplx<T>);
+}
+template <typename T, int OP>
+static size_t smem_col(const Geometry* g, int C) {
+  const int nmax = Traits<OP>::NIN > Traits<OP>::NOUT ? Traits<OP>::NIN : Traits<OP>::NOUT;
+  return 2 * (size_t)nmax * C * g->n * sizeof(cplx<T>);
+}
+
+static const size_t kSmemLimit = 227 * 1024;
+
+template <typename T, int OP>
+static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream_t s, const int* stop,
+                          double* grid) {
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi];
+  if (R == 0 || C == 0)
+    return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
+  const size_t s1 = smem_spread<T, OP>(g, R), s2 = smem_col<T, OP>(g, C), s3 = smem_gather<T, OP>(g, R);
+  if (s1 > kSmemLimit || s2 > kSmemLimit || s3 > kSmemLimit)
+    return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
+  // Opt in to large dynamic shared memory once per kernel instance.
+  static bool attr_done = false;
+  if (!attr_done) {
+    IBDL_CUDA(cudaFuncSetAttribute(k_spread_rowfft<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    IBDL_CUDA(cudaFuncSetAttribute(k_colpass<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    IBDL_CUDA(cudaFuncSetAttribute(k_rowifft_gather<T, OP, G_INTERP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    IBDL_CUDA(cudaFuncSetAttribute(k_rowifft_gather<T, OP, G_GRID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    attr_done = true;
+  }
+  RowParams<T> rp = row_params<T>(g, in, out, stop, grid);
+  ColParams<T> cp = col_params<T>(g, stop);
+  const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
+  if (g->timing) timing_mark(g, s, -1);
+  k_spread_rowfft<T, OP><<<g->n / R, kThreads, s1, s>>>(rp);
+  if (g->timing) timing_mark(g, s, st0);
+  k_colpass<T, OP><<<(g->n / 2) / C, kThreads, s2, s>>>(cp);
+  if (g->timing) timing_mark(g, s, st0 + 1);
+  if (grid)
+    k_rowifft_gather<T, OP, G_GRID><<<g->n / R, kThreads, s3, s>>>(rp);
+  else
+    k_rowifft_gather<T, OP, G_INTERP><<<g->n / R, kThreads, s3, s>>>(rp);
+  if (g->timing) timing_mark(g, s, st0 + 2);
+  g->launches += 3;
+  IBDL_CUDA(cudaGetLastError());
+  return IBDL_OK;
+}
+
+template <typename T>
+static ibdl_status apply_t(Geometry* g, const double* Q, double* Y, cudaStream_t s, const int* stop, double* grid) {
+  if (g->pde == IBDL_PDE_STOKES)
+    return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<T, OP_STOKES_AN>(g, Q, Y, s, stop, grid)
+                                             : run_op<T, OP_STOKES_SD>(g, Q, Y, s, stop, grid);
+  return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<T, OP_SCALAR_AN>(g, Q, Y, s, stop, grid)
+                                           : run_op<T, OP_SCALAR_SD>(g, Q, Y, s, stop, grid);
+}
+
+ibdl_status apply_2d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s, const int* stop) {
+  return precision == IBDL_FP32 ? apply_t<float>(g, Q, Y, s, stop, nullptr)
+                                : apply_t<double>(g, Q, Y, s, stop, nullptr);
+}
+
+ibdl_status field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s) {
+  return apply_t<double>(g, Q, g->tmp_m, s, nullptr, u);
+}
+
+ibdl_status adjoint_2d(Geometry* g, int precision, const double* W, double* Z, cudaStream_t s) {
+  if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "adjoint: scalar PDE only");
+  if (precision == IBDL_FP32)
+    return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<float, OP_ADJ_AN>(g, W, Z, s, nullptr, nullptr)
+                                             : run_op<float, OP_ADJ_SD>(g, W, Z, s, nullptr, nullptr);
+  return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<double, OP_ADJ_AN>(g, W, Z, s, nullptr, nullptr)
+                                           : run_op<double, OP_ADJ_SD>(g, W, Z, s, nullptr, nullptr);
+}
+
+// Band height R (rows per CTA, even) and kx columns per CTA C, per precision, within the
+// shared-memory limit for the widest field count this geometry uses.
+ibdl_status plan_2d(Geometry* g) {
+  const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
+  for (int pi = 0; pi < 2; ++pi) {
+    const size_t cs = pi ? sizeof(float2) : sizeof(double2);
+    int R = g->n >= 256 ? 2 : 2;
+    while (R > 2 && 2 * (size_t)nf * (R / 2) * g->n * cs > kSmemLimit) R /= 2;
+    if (2 * (size_t)nf * (R / 2) * g->n * cs > kSmemLimit) R = 0;
+    int C = 2;
+    while (C > 1 && 2 * (size_t)nf * C * g->n * cs > kSmemLimit) C /= 2;
+    if (2 * (size_t)nf * C * g->n * cs > kSmemLimit) C = 0;
+    if ((g->n / 2) % (C ? C : 1)) C = 1;
+    g->rows_per_cta[pi] = R;
+    g->cols_per_cta[pi] = C;
+  }
+  if (g->rows_per_cta[0] == 0 && g->rows_per_cta[1] == 0)
+    return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT");
+  return IBDL_OK;
+}
+
+}  // namespace ibdl

@@ -1,0 +1,412 @@
+// GMRES for A Q = U_b (Sec. 5.3.2: the Schur operator is not symmetric) on the device.
+//
+// Arnoldi runs in one CTA per iteration: classical Gram–Schmidt applied twice (CGS2) against
+// the basis in FP64, the new Hessenberg column is reduced by the stored Givens rotations, and
+// the residual estimate |g_{k}| is compared with the target on the device. When the target is
+// met (or the cycle is full, or a non-finite value appears) the CTA raises a stop flag that
+// every kernel of the following iterations reads first, so the host can queue iteration j+1
+// before it has looked at iteration j's status: one host wait per iteration, overlapped with
+// the next iteration's GPU work.
+//
+// Mixed precision: iterative refinement. Each sweep solves A₃₂ d = r with FP32 grid arithmetic
+// and the same FP64 Arnoldi/Hessenberg, then forms the FP64 residual r = U_b − A₆₄ Q.
+#include <chrono>
+#include <cmath>
+
+#include "ibdl_internal.cuh"
+
+namespace ibdl {
+
+enum { KMAX = 64 };
+enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_NONFINITE = 3 };
+
+struct GmresState {
+  int stop;    // nonzero: every queued kernel returns at once
+  int status;  // ST_*
+  int k;       // Arnoldi steps completed in this cycle
+  int pad;
+  double res;      // |g_k|, the GMRES residual estimate
+  double beta;     // ‖r0‖ of the cycle
+  double target;   // absolute tolerance on the residual
+  double rnorm;    // ‖r‖ from k_residual
+  double cs[KMAX], sn[KMAX], g[KMAX + 1];
+  double H[(KMAX + 1) * KMAX];  // column j at H[j·(m+1) + i]
+};
+
+struct HostStatus {
+  int stop, status, k, pad;
+  double res, beta, target, rnorm;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum; every thread gets the result
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = threadIdx.x < (unsigned)nw ? red[threadIdx.x] : 0.0;
+  if (warp == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// start a cycle: V_0 = r/‖r‖, g = ‖r‖ e_1
+__global__ void __launch_bounds__(1024) k_gmres_start(GmresState* st, const double* __restrict__ r, double* V, int nd,
+                                                      double target) {
+  __shared__ double red[32];
+  double s = 0;
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) s += r[i] * r[i];
+  const double beta = sqrt(block_sum(s, red));
+  const bool bad = !isfinite(beta);
+  const double inv = (beta > 0 && !bad) ? 1.0 / beta : 0.0;
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) V[i] = r[i] * inv;
+  if (threadIdx.x == 0) {
+    st->beta = beta;
+    st->target = target;
+    st->res = beta;
+    st->k = 0;
+    st->g[0] = beta;
+    if (bad) {
+      st->status = ST_NONFINITE;
+      st->stop = 1;
+    } else if (beta <= target) {
+      st->status = ST_CONVERGED;
+      st->stop = 1;
+    } else {
+      st->status = ST_RUNNING;
+      st->stop = 0;
+    }
+  }
+}
+
+// one Arnoldi step j: w = V_{j+1} (already A V_j) is orthogonalised against V_0..V_j by CGS2
+__global__ void __launch_bounds__(1024) k_arnoldi(GmresState* st, double* V, int j, int nd, int m) {
+  if (st->stop) return;
+  __shared__ double hp[KMAX + 1], hsum[KMAX + 1], red[32];
+  double* w = V + (size_t)(j + 1) * nd;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x <= (unsigned)j) hsum[threadIdx.x] = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = warp; i <= j; i += nw) {
+      const double* v = V + (size_t)i * nd;
+      double s = 0;
+      for (int k = lane; k < nd; k += 32) s += v[k] * w[k];
+      s = warp_sum(s);
+      if (lane == 0) hp[i] = s;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nd; k += blockDim.x) {
+      double acc = w[k];
+      for (int i = 0; i <= j; ++i) acc -= hp[i] * V[(size_t)i * nd + k];
+      w[k] = acc;
+    }
+    if (threadIdx.x <= (unsigned)j) hsum[threadIdx.x] += hp[threadIdx.x];
+    __syncthreads();
+  }
+  double s = 0;
+  for (int k = threadIdx.x; k < nd; k += blockDim.x) s += w[k] * w[k];
+  const double hn = sqrt(block_sum(s, red));
+  const double inv = hn > 0 ? 1.0 / hn : 0.0;
+  for (int k = threadIdx.x; k < nd; k += blockDim.x) w[k] *= inv;
+  if (threadIdx.x == 0) {
+    double* h = st->H + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) h[i] = hsum[i];
+    h[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double t = st->cs[i] * h[i] + st->sn[i] * h[i + 1];
+      h[i + 1] = -st->sn[i] * h[i] + st->cs[i] * h[i + 1];
+      h[i] = t;
+    }
+    const double a = h[j], b = h[j + 1];
+    const double r = hypot(a, b);
+    const double c = r > 0 ? a / r : 1.0, sn = r > 0 ? b / r : 0.0;
+    h[j] = r;
+    h[j + 1] = 0.0;
+    st->cs[j] = c;
+    st->sn[j] = sn;
+    st->g[j + 1] = -sn * st->g[j];
+    st->g[j] = c * st->g[j];
+    const double res = fabs(st->g[j + 1]);
+    st->res = res;
+    st->k = j + 1;
+    if (!isfinite(res) || !isfinite(hn)) {
+      st->status = ST_NONFINITE;
+      st->stop = 1;
+    } else if (res <= st->target) {
+      st->status = ST_CONVERGED;
+      st->stop = 1;
+    } else if (hn == 0.0) {
+      st->status = ST_BREAKDOWN;  // invariant Krylov space: the least-squares solution is exact
+      st->stop = 1;
+    } else if (j + 1 >= m) {
+      st->stop = 1;  // cycle full
+    }
+  }
+}
+
+// x += V_{0..k-1} y with R y = g (back substitution on the Givens-reduced Hessenberg)
+__global__ void __launch_bounds__(1024) k_gmres_update(GmresState* st, const double* __restrict__ V, double* x, int nd,
+                                                       int m) {
+  __shared__ double y[KMAX];
+  const int k = st->k;
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double t = st->g[i];
+      for (int l = i + 1; l < k; ++l) t -= st->H[(size_t)l * (m + 1) + i] * y[l];
+      const double d = st->H[(size_t)i * (m + 1) + i];
+      y[i] = d != 0.0 ? t / d : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nd; idx += blockDim.x) {
+    double acc = x[idx];
+    for (int i = 0; i < k; ++i) acc += y[i] * V[(size_t)i * nd + idx];
+    x[idx] = acc;
+  }
+}
+
+// r = b − Ax, st->rnorm = ‖r‖
+__global__ void __launch_bounds__(1024) k_residual(GmresState* st, const double* __restrict__ b,
+                                                   const double* __restrict__ Ax, double* r, int nd) {
+  __shared__ double red[32];
+  double s = 0;
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+    const double v = b[i] - Ax[i];
+    r[i] = v;
+    s += v * v;
+  }
+  const double nrm = sqrt(block_sum(s, red));
+  if (threadIdx.x == 0) st->rnorm = nrm;
+}
+
+__global__ void k_axpy(double* x, const double* __restrict__ d, int nd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nd) x[i] += d[i];
+}
+
+// ------------------------------------------------------------------------------------------
+// host driver
+// ------------------------------------------------------------------------------------------
+static ibdl_status ensure_workspace(Geometry* g, int m) {
+  if (g->V && g->krylov_m >= m) return IBDL_OK;
+  if (g->V) cudaFree(g->V);
+  g->V = nullptr;
+  const size_t nd = (size_t)g->ncomp * g->M;
+  IBDL_CUDA(cudaMalloc((void**)&g->V, sizeof(double) * nd * (m + 1)));
+  if (!g->gm) IBDL_CUDA(cudaMalloc((void**)&g->gm, sizeof(GmresState)));
+  if (!g->vec) IBDL_CUDA(cudaMalloc((void**)&g->vec, sizeof(double) * nd * 5));
+  if (!g->host_status) IBDL_CUDA(cudaMallocHost(&g->host_status, 2 * sizeof(HostStatus)));
+  g->krylov_m = m;
+  return IBDL_OK;
+}
+
+struct CycleResult {
+  int its;
+  int status;
+  double res;
+};
+
+// One GMRES(m) cycle on right-hand side r0 from a zero correction, accumulating into x.
+static ibdl_status gmres_cycle(Geometry* g, int prec, const double* r0, double* x, double target, int m, int budget,
+                               cudaStream_t s, CycleResult* cr) {
+  GmresState* st = reinterpret_cast<GmresState*>(g->gm);
+  HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
+  const int nd = (int)(g->ncomp * g->M);
+  double* V = g->V;
+  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, V, nd, target);
+  g->launches += 1;
+  IBDL_CUDA(cudaGetLastError());
+  const int steps = m < budget ? m : budget;
+  cudaEvent_t evs[2] = {g->ev, g->ev};
+  // the geometry owns one event; a second one is created per call for the double buffer
+  cudaEvent_t ev2;
+  IBDL_CUDA(cudaEventCreateWithFlags(&ev2, cudaEventDisableTiming));
+  evs[1] = ev2;
+  IBDL_CUDA(cudaMemcpyAsync(&hs[1], st, sizeof(HostStatus), cudaMemcpyDeviceToHost, s));
+  IBDL_CUDA(cudaEventRecord(evs[1], s));
+  ibdl_status err = IBDL_OK;
+  for (int j = 0; j < steps; ++j) {
+    err = apply_any(g, prec, V + (size_t)j * nd, V + (size_t)(j + 1) * nd, s, &st->stop);
+    if (err != IBDL_OK) break;
+    if (g->timing) timing_mark(g, s, -1);
+    k_arnoldi<<<1, 1024, 0, s>>>(st, V, j, nd, m);
+    if (g->timing) timing_mark(g, s, IBDL_STAGE_ARNOLDI);
+    g->launches += 1;
+    if (cudaGetLastError() != cudaSuccess) {
+      err = fail(IBDL_ERR_CUDA, "k_arnoldi launch failed");
+      break;
+    }
+    // wait for the previous step's status while this step runs
+    const int prev = (j + 1) & 1;
+    if (cudaEventSynchronize(evs[prev]) != cudaSuccess) {
+      err = fail(IBDL_ERR_CUDA, "event synchronize failed");
+      break;
+    }
+    const bool stopped = hs[prev].stop != 0;
+    if (cudaMemcpyAsync(&hs[j & 1], st, sizeof(HostStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaEventRecord(evs[j & 1], s) != cudaSuccess) {
+      err = fail(IBDL_ERR_CUDA, "status copy failed");
+      break;
+    }
+    if (stopped) break;
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(ev2);
+  if (err != IBDL_OK) return err;
+  HostStatus fin;
+  IBDL_CUDA(cudaMemcpy(&fin, st, sizeof(HostStatus), cudaMemcpyDeviceToHost));
+  k_gmres_update<<<1, 1024, 0, s>>>(st, V, x, nd, m);
+  g->launches += 1;
+  IBDL_CUDA(cudaGetLastError());
+  cr->its = fin.k;
+  cr->status = fin.status;
+  cr->res = fin.res;
+  return IBDL_OK;
+}
+
+// r = b − A₆₄ x, returns ‖r‖ (synchronous)
+static ibdl_status true_residual(Geometry* g, const double* b, const double* x, double* r, double* Ax, cudaStream_t s,
+                                 double* rnorm) {
+  GmresState* st = reinterpret_cast<GmresState*>(g->gm);
+  const int nd = (int)(g->ncomp * g->M);
+  IBDL_TRY(apply_any(g, IBDL_FP64, x, Ax, s, nullptr));
+  k_residual<<<1, 1024, 0, s>>>(st, b, Ax, r, nd);
+  g->launches += 1;
+  IBDL_CUDA(cudaGetLastError());
+  HostStatus fin;
+  IBDL_CUDA(cudaMemcpyAsync(&fin, st, sizeof(HostStatus), cudaMemcpyDeviceToHost, s));
+  IBDL_CUDA(cudaStreamSynchronize(s));
+  *rnorm = fin.rnorm;
+  return IBDL_OK;
+}
+
+static double host_norm(Geometry* g, const double* v_dev, cudaStream_t s) {
+  GmresState* st = reinterpret_cast<GmresState*>(g->gm);
+  const int nd = (int)(g->ncomp * g->M);
+  // ‖v‖ via k_residual with Ax = 0 would need a zero vector; use b − 0 trick with the x slot cleared
+  double* zero = g->vec + 4 * (size_t)nd;
+  cudaMemsetAsync(zero, 0, sizeof(double) * nd, s);
+  double* scratch = g->tmp_m;
+  k_residual<<<1, 1024, 0, s>>>(st, v_dev, zero, scratch, nd);
+  g->launches += 1;
+  HostStatus fin;
+  cudaMemcpyAsync(&fin, st, sizeof(HostStatus), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  return fin.rnorm;
+}
+
+ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solve_opts* o, ibdl_solve_info* info,
+                       cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int m = o->restart;
+  IBDL_TRY(ensure_workspace(g, m));
+  const int nd = (int)(g->ncomp * g->M);
+  double* b = g->vec;
+  double* x = g->vec + (size_t)nd;
+  double* r = g->vec + 2 * (size_t)nd;
+  double* d = g->vec + 3 * (size_t)nd;
+  IBDL_CUDA(cudaMemcpyAsync(b, Ub, sizeof(double) * nd, o->io_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  IBDL_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nd, s));
+  const double bnorm = host_norm(g, b, s);
+  if (!std::isfinite(bnorm)) return fail(IBDL_ERR_NONFINITE, "U_b contains NaN or Inf");
+  ibdl_solve_info inf = {};
+  ibdl_status ret = IBDL_OK;
+  const double target = o->rtol * bnorm;
+  if (bnorm == 0.0) {
+    inf.rel_residual = 0.0;
+  } else if (o->precision != IBDL_MIXED) {
+    // plain restarted GMRES(m) with FP64 (or FP32) applies
+    int used = 0;
+    bool done = false;
+    const double* rhs = b;
+    while (!done) {
+      CycleResult cr;
+      IBDL_TRY(gmres_cycle(g, o->precision, rhs, x, target, m, o->maxit - used, s, &cr));
+      used += cr.its;
+      inf.sweeps += 1;
+      if (o->precision == IBDL_FP32)
+        inf.fp32_applies += cr.its;
+      else
+        inf.fp64_applies += cr.its;
+      inf.rel_residual = cr.res / bnorm;
+      if (cr.status == ST_NONFINITE) {
+        ret = fail(IBDL_ERR_NONFINITE, "non-finite value in the GMRES iteration");
+        break;
+      }
+      if (cr.status == ST_CONVERGED || cr.status == ST_BREAKDOWN) break;
+      if (used >= o->maxit) {
+        ret = fail(IBDL_ERR_NOT_CONVERGED, "GMRES reached maxit");
+        break;
+      }
+      // restart from the true residual
+      double rn = 0;
+      IBDL_TRY(true_residual(g, b, x, r, d, s, &rn));
+      inf.fp64_applies += 1;
+      inf.rel_residual = rn / bnorm;
+      if (rn <= target) break;
+      rhs = r;
+    }
+    inf.iterations = used;
+  } else {
+    // iterative refinement: inner FP32-apply GMRES on the FP64 residual, FP64 update
+    int used = 0;
+    const double* rhs = b;
+    double rn = bnorm;
+    for (int sweep = 0; sweep < o->max_refine; ++sweep) {
+      IBDL_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * nd, s));
+      const double inner_target = o->inner_rtol * rn > target ? o->inner_rtol * rn : 0.5 * target;
+      // inner solve, with restarts, until the inner target or the budget
+      const double* irhs = rhs;
+      while (true) {
+        CycleResult cr;
+        IBDL_TRY(gmres_cycle(g, IBDL_FP32, irhs, d, inner_target, m, o->maxit - used, s, &cr));
+        used += cr.its;
+        inf.fp32_applies += cr.its;
+        if (cr.status == ST_NONFINITE) return fail(IBDL_ERR_NONFINITE, "non-finite value in the GMRES iteration");
+        if (cr.status != ST_RUNNING || used >= o->maxit) break;
+        // inner restart on the FP32 residual of the correction: r_in = rhs − A₃₂ d
+        GmresState* st = reinterpret_cast<GmresState*>(g->gm);
+        double* Ad = g->vec + 4 * (size_t)nd;
+        IBDL_TRY(apply_any(g, IBDL_FP32, d, Ad, s, nullptr));
+        inf.fp32_applies += 1;
+        k_residual<<<1, 1024, 0, s>>>(st, rhs, Ad, g->tmp_m, nd);
+        g->launches += 1;
+        IBDL_CUDA(cudaGetLastError());
+        irhs = g->tmp_m;
+        // a cycle correction accumulates into d through the same update kernel
+        (void)st;
+      }
+      k_axpy<<<(nd + 255) / 256, 256, 0, s>>>(x, d, nd);
+      g->launches += 1;
+      IBDL_CUDA(cudaGetLastError());
+      inf.sweeps += 1;
+      IBDL_TRY(true_residual(g, b, x, r, d, s, &rn));
+      inf.fp64_applies += 1;
+      inf.rel_residual = rn / bnorm;
+      if (!std::isfinite(rn)) return fail(IBDL_ERR_NONFINITE, "non-finite residual");
+      if (rn <= target) break;
+      if (used >= o->maxit) break;
+      rhs = r;
+    }
+    inf.iterations = used;
+    if (inf.rel_residual > o->rtol && ret == IBDL_OK)
+      ret = fail(IBDL_ERR_NOT_CONVERGED, "mixed-precision refinement did not reach rtol");
+  }
+  IBDL_CUDA(cudaMemcpyAsync(Q, x, sizeof(double) * nd, o->io_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  IBDL_CUDA(cudaStreamSynchronize(s));
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  return ret;
+}
+
+}  // namespace ibdl

@@ -1,0 +1,158 @@
+// Internal declarations of the IBDL CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ibdl.h"
+
+namespace ibdl {
+
+// ------------------------------------------------------------------------------------------
+// error handling: every failure becomes an ibdl_status plus a thread-local message
+// ------------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+ibdl_status fail(ibdl_status st, const std::string& msg);
+ibdl_status cuda_fail(cudaError_t e, const char* what);
+
+#define IBDL_CUDA(call)                                         \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return ::ibdl::cuda_fail(e_, #call); \
+  } while (0)
+
+#define IBDL_TRY(call)                    \
+  do {                                    \
+    ibdl_status s_ = (call);              \
+    if (s_ != IBDL_OK) return s_;         \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------
+// complex arithmetic
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct cplx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> mk(T a, T b) {
+  cplx<T> c;
+  c.x = a;
+  c.y = b;
+  return c;
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cconj(cplx<T> a) { return mk(a.x, -a.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return mk(a.x * s, a.y * s); }
+// multiply by i
+template <typename T>
+__device__ __forceinline__ cplx<T> cmuli(cplx<T> a) { return mk(-a.y, a.x); }
+
+// ------------------------------------------------------------------------------------------
+// geometry: everything an operator application needs, resident on the device
+// ------------------------------------------------------------------------------------------
+enum { MAX_FIELDS_IN = 4, MAX_FIELDS_OUT = 3 };
+
+// Per-point stencil table in sorted (cell) order, one copy per precision. For axis j the
+// four nodes are base[j] + a (mod n), a = 0..3, with kernel weights phi[j][a] = φ(r) and
+// dphi[j][a] = φ'(r)/h where r = (x_node − X)/h.
+template <typename T>
+struct PointTable {
+  T* phi;      // [dim][4][M]
+  T* dphi;     // [dim][4][M]
+  T* wscale;   // [M] Δs_i / h^dim
+  T* nrm;      // [dim][M] unit normals
+};
+
+struct Geometry {
+  // description
+  int dim, n, pde, delta, dipole, symbol;
+  double box, h, lambda, mu;
+  double origin[3];
+  int64_t M;
+  int ncomp;       // c: 1 scalar, dim Stokes
+  int nf_in;       // grid fields spread per application
+  int nf_out;      // grid fields interpolated per application
+
+  // sorted points
+  int* perm;       // [M] sorted position -> original index
+  int* base;       // [dim][M] base node per axis (sorted order), already wrapped to [0, n)
+  int* cell_start; // [ncell + 1], cells = n^(dim-1) rows of constant (y, z) base
+  int ncell;
+  PointTable<double> t64;
+  PointTable<float> t32;
+
+  // workspace: half spectra, packed format (see apply kernels): [nf][rows][n/2] complex
+  void* spec;      // sized for nf_in fields in FP64
+  size_t spec_bytes;
+  double2* tw64;   // [n] e^{-2πi j/n}
+  float2* tw32;
+  // per-axis Fourier symbols indexed by FFT index j (wavenumber 2π m/box, m = j or j − n):
+  // lap = symbol of −∂² along one axis, der = k̃ with ∂ ↦ i k̃ (0 at Nyquist)
+  double *lap64, *der64;
+  float *lap32, *der32;
+  double* ubuf;    // evaluate_field / adjoint helpers: [c][n^dim] FP64
+  double* tmp_m;   // [c*M] scratch boundary vector
+
+  // launch plan (2-D and 3-D)
+  int rows_per_cta[2];   // band height R for the row kernels, per precision (0 = fp64, 1 = fp32)
+  int cols_per_cta[2];   // kx columns per CTA in the column kernels
+  size_t smem_row[2], smem_col[2], smem_row_inv[2];
+
+  // GMRES workspace (allocated lazily, sized for `krylov_m`)
+  int krylov_m;
+  double* V;       // [(m+1)][c*M]
+  double* gm;      // small device state (Hessenberg, Givens, g, status)
+  double* vec;     // [4][c*M] work vectors (b, x, r, d)
+  void* host_status;   // pinned
+  cudaEvent_t ev;
+
+  // counters and optional stage timing (events around every kernel)
+  int64_t launches;
+  int timing;
+  cudaEvent_t* ev_pool;
+  int* ev_stage;   // stage id of the interval that ends at event i (−1: a start marker)
+  int ev_cap, ev_used;
+};
+
+// record an event on `s` closing an interval of `stage` (−1 opens a new interval)
+void timing_mark(Geometry* g, cudaStream_t s, int stage);
+ibdl_status set_stage_timing(Geometry* g, int enable);
+ibdl_status get_stage_times(Geometry* g, double* ms, int64_t* launches);
+
+// ------------------------------------------------------------------------------------------
+// launchers implemented in the .cu files
+// ------------------------------------------------------------------------------------------
+ibdl_status apply_2d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s,
+                     const int* stop_flag);
+ibdl_status apply_3d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s,
+                     const int* stop_flag);
+ibdl_status field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s);
+ibdl_status field_3d(Geometry* g, const double* Q, double* u, cudaStream_t s);
+ibdl_status adjoint_2d(Geometry* g, int precision, const double* W, double* Z, cudaStream_t s);
+ibdl_status adjoint_3d(Geometry* g, int precision, const double* W, double* Z, cudaStream_t s);
+ibdl_status plan_2d(Geometry* g);
+ibdl_status plan_3d(Geometry* g);
+ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solve_opts* o,
+                       ibdl_solve_info* info, cudaStream_t s);
+
+inline ibdl_status apply_any(Geometry* g, int precision, const double* Q, double* Y,
+                             cudaStream_t s, const int* stop_flag) {
+  return g->dim == 2 ? apply_2d(g, precision, Q, Y, s, stop_flag)
+                     : apply_3d(g, precision, Q, Y, s, stop_flag);
+}
+
+}  // namespace ibdl

@@ -1,0 +1,305 @@
+"""Python binding of the IBDL C ABI (``include/ibdl.h``).
+
+The functions ``ibdl_*`` below have the names, arguments and return values of the C entry
+points and only marshal arguments through ctypes; every step of the operator and the solve runs
+in the CUDA library ``libibdl.so``. ``Geometry`` is a small convenience wrapper that takes
+numpy arrays or CUDA ``torch`` tensors (PyTorch supplies device memory and streams).
+
+Loading fails loudly: if ``libibdl.so`` is missing (not built) or cannot be loaded, every call
+raises ``RuntimeError``; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int64, c_void_p
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libibdl.so")
+
+# status codes (ibdl_status)
+IBDL_OK = 0
+IBDL_ERR_INVALID_ARG = 1
+IBDL_ERR_CUDA = 2
+IBDL_ERR_NO_MEMORY = 3
+IBDL_ERR_NOT_CONVERGED = 4
+IBDL_ERR_NONFINITE = 5
+IBDL_ERR_TIMEOUT = 6
+IBDL_ERR_UNSUPPORTED = 7
+STATUS_NAMES = {0: "IBDL_OK", 1: "IBDL_ERR_INVALID_ARG", 2: "IBDL_ERR_CUDA", 3: "IBDL_ERR_NO_MEMORY",
+                4: "IBDL_ERR_NOT_CONVERGED", 5: "IBDL_ERR_NONFINITE", 6: "IBDL_ERR_TIMEOUT",
+                7: "IBDL_ERR_UNSUPPORTED"}
+
+IBDL_PDE_SCALAR, IBDL_PDE_STOKES = 0, 1
+IBDL_DELTA_COS, IBDL_DELTA_SQRT = 0, 1
+IBDL_DIPOLE_ANALYTIC, IBDL_DIPOLE_SPECTRAL_DIV = 0, 1
+IBDL_SYMBOL_SPECTRAL, IBDL_SYMBOL_FD2 = 0, 1
+IBDL_FP64, IBDL_FP32, IBDL_MIXED = 0, 1, 2
+
+_PDE = {"scalar": IBDL_PDE_SCALAR, "stokes": IBDL_PDE_STOKES}
+_DELTA = {"cos": IBDL_DELTA_COS, "sqrt": IBDL_DELTA_SQRT}
+_DIPOLE = {"analytic": IBDL_DIPOLE_ANALYTIC, "spectral_div": IBDL_DIPOLE_SPECTRAL_DIV}
+_SYMBOL = {"spectral": IBDL_SYMBOL_SPECTRAL, "fd2": IBDL_SYMBOL_FD2}
+_PREC = {"fp64": IBDL_FP64, "fp32": IBDL_FP32, "mixed": IBDL_MIXED}
+
+
+class ibdl_geometry_desc(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("n", c_int), ("box", c_double), ("origin", c_double * 3),
+                ("n_points", c_int64), ("X", c_void_p), ("normals", c_void_p), ("weights", c_void_p),
+                ("pde", c_int), ("lambda_", c_double), ("mu", c_double), ("delta", c_int),
+                ("dipole", c_int), ("symbol", c_int), ("inputs_on_device", c_int)]
+
+
+class ibdl_solve_opts(ctypes.Structure):
+    _fields_ = [("rtol", c_double), ("restart", c_int), ("maxit", c_int), ("precision", c_int),
+                ("inner_rtol", c_double), ("max_refine", c_int), ("io_on_host", c_int)]
+
+
+class ibdl_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", c_int), ("fp64_applies", c_int), ("fp32_applies", c_int),
+                ("sweeps", c_int), ("rel_residual", c_double), ("seconds", c_double),
+                ("kernel_launches", c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# exported symbols and their ctypes signatures
+SIGNATURES = {
+    "ibdl_create_geometry": (c_int, [POINTER(ibdl_geometry_desc), c_void_p, POINTER(c_void_p)]),
+    "ibdl_destroy_geometry": (c_int, [c_void_p]),
+    "ibdl_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "ibdl_adjoint": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "ibdl_solve": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(ibdl_solve_opts),
+                           POINTER(ibdl_solve_info), c_void_p]),
+    "ibdl_evaluate_field": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ibdl_default_solve_opts": (None, [POINTER(ibdl_solve_opts)]),
+    "ibdl_geometry_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int64)]),
+    "ibdl_set_stage_timing": (c_int, [c_void_p, c_int]),
+    "ibdl_get_stage_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
+    "ibdl_last_error": (c_char_p, []),
+}
+
+IBDL_STAGE_COUNT = 8
+STAGE_NAMES = ["spread_rowfft_fp64", "column_fp64", "rowifft_gather_fp64", "spread_rowfft_fp32",
+               "column_fp32", "rowifft_gather_fp32", "arnoldi", "other"]
+
+_lib = None
+_load_error = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libibdl.so (once) and attach the ctypes signatures. Raises RuntimeError on failure."""
+    global _lib, _load_error
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        _load_error = f"{path} not found: build it with `python -c 'import __graft_entry__ as g; g.build()'`"
+        raise RuntimeError(_load_error)
+    try:
+        lib = ctypes.CDLL(path)
+    except OSError as e:  # pragma: no cover - depends on the machine
+        _load_error = f"cannot load {path}: {e}"
+        raise RuntimeError(_load_error) from e
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class IbdlError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(status: int):
+    if status != IBDL_OK:
+        raise IbdlError(status, ibdl_last_error())
+    return status
+
+
+# ---- the C entry points, one to one --------------------------------------------------------
+
+
+def ibdl_create_geometry(desc: ibdl_geometry_desc, stream: int = 0) -> c_void_p:
+    out = c_void_p()
+    _check(load().ibdl_create_geometry(byref(desc), c_void_p(stream), byref(out)))
+    return out
+
+
+def ibdl_destroy_geometry(geom) -> int:
+    return _check(load().ibdl_destroy_geometry(geom))
+
+
+def ibdl_apply(geom, precision: int, Q: int, Y: int, stream: int = 0) -> int:
+    return _check(load().ibdl_apply(geom, precision, c_void_p(Q), c_void_p(Y), c_void_p(stream)))
+
+
+def ibdl_adjoint(geom, precision: int, W: int, Z: int, stream: int = 0) -> int:
+    return _check(load().ibdl_adjoint(geom, precision, c_void_p(W), c_void_p(Z), c_void_p(stream)))
+
+
+def ibdl_solve(geom, Ub: int, Q: int, opts: ibdl_solve_opts, info: ibdl_solve_info, stream: int = 0,
+               check: bool = True) -> int:
+    st = load().ibdl_solve(geom, c_void_p(Ub), c_void_p(Q), byref(opts), byref(info), c_void_p(stream))
+    return _check(st) if check else st
+
+
+def ibdl_evaluate_field(geom, Q: int, u_grid: int, stream: int = 0) -> int:
+    return _check(load().ibdl_evaluate_field(geom, c_void_p(Q), c_void_p(u_grid), c_void_p(stream)))
+
+
+def ibdl_default_solve_opts() -> ibdl_solve_opts:
+    o = ibdl_solve_opts()
+    load().ibdl_default_solve_opts(byref(o))
+    return o
+
+
+def ibdl_geometry_sizes(geom):
+    c, m = c_int(), c_int64()
+    _check(load().ibdl_geometry_sizes(geom, byref(c), byref(m)))
+    return c.value, m.value
+
+
+def ibdl_set_stage_timing(geom, enable: int) -> int:
+    return _check(load().ibdl_set_stage_timing(geom, int(enable)))
+
+
+def ibdl_get_stage_times(geom):
+    ms = (c_double * IBDL_STAGE_COUNT)()
+    n = (c_int64 * IBDL_STAGE_COUNT)()
+    _check(load().ibdl_get_stage_times(geom, ms, n))
+    return list(ms), list(n)
+
+
+def ibdl_last_error() -> str:
+    return load().ibdl_last_error().decode()
+
+
+# ---- convenience wrapper ------------------------------------------------------------------
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Geometry:
+    """An IBDL geometry on the current CUDA device (arguments mirror ``ibdl_geometry_desc``)."""
+
+    def __init__(self, X, normals, weights, n: int, box: float = 1.0, origin=(0.0, 0.0, 0.0),
+                 pde: str = "scalar", lam: float = 0.0, mu: float = 1.0, delta: str = "cos",
+                 dipole: str = "analytic", symbol: str = "spectral", stream=None):
+        import torch
+
+        self._torch = torch
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+        nrm = np.ascontiguousarray(np.asarray(normals, dtype=np.float64))
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+        dim, M = X.shape
+        d = ibdl_geometry_desc()
+        d.dim, d.n, d.box = dim, int(n), float(box)
+        for j in range(3):
+            d.origin[j] = float(origin[j]) if j < len(origin) else 0.0
+        d.n_points = M
+        d.X, d.normals, d.weights = X.ctypes.data, nrm.ctypes.data, w.ctypes.data
+        d.pde, d.lambda_, d.mu = _PDE[pde], float(lam), float(mu)
+        d.delta, d.dipole, d.symbol = _DELTA[delta], _DIPOLE[dipole], _SYMBOL[symbol]
+        d.inputs_on_device = 0
+        self.dim, self.n, self.M, self.pde = dim, int(n), M, pde
+        self.ncomp = dim if pde == "stokes" else 1
+        self._h = ibdl_create_geometry(d, _stream_handle(stream))
+
+    @classmethod
+    def from_problem(cls, p, **overrides):
+        kw = dict(n=p.N, box=p.box, origin=p.origin, pde=p.pde, lam=p.lam, mu=p.mu, delta=p.delta,
+                  dipole=p.dipole, symbol=p.symbol)
+        kw.update(overrides)
+        return cls(p.bd.X, p.bd.n, p.bd.w, **kw)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _vec(self, v):
+        t = self._torch
+        if isinstance(v, np.ndarray):
+            v = t.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).cuda()
+        assert v.is_cuda and v.dtype == t.float64 and v.is_contiguous()
+        assert v.numel() == self.ncomp * self.M
+        return v
+
+    def apply(self, Q, Y=None, precision: str = "fp64", stream=None):
+        Q = self._vec(Q)
+        if Y is None:
+            Y = self._torch.empty_like(Q)
+        ibdl_apply(self._h, _PREC[precision], Q.data_ptr(), Y.data_ptr(), _stream_handle(stream))
+        return Y
+
+    def adjoint(self, W, Z=None, precision: str = "fp64", stream=None):
+        W = self._vec(W)
+        if Z is None:
+            Z = self._torch.empty_like(W)
+        ibdl_adjoint(self._h, _PREC[precision], W.data_ptr(), Z.data_ptr(), _stream_handle(stream))
+        return Z
+
+    def evaluate_field(self, Q, stream=None):
+        Q = self._vec(Q)
+        shape = (self.n,) * self.dim
+        if self.pde == "stokes":
+            shape = (self.dim,) + shape
+        u = self._torch.empty(shape, dtype=self._torch.float64, device=Q.device)
+        ibdl_evaluate_field(self._h, Q.data_ptr(), u.data_ptr(), _stream_handle(stream))
+        return u
+
+    def solve(self, Ub, rtol: float = 1e-8, precision: str = "fp64", restart: int = 50, maxit: int = 200,
+              inner_rtol: float = 1e-4, max_refine: int = 6, Q=None, stream=None, check: bool = True):
+        """Solve A Q = U_b. U_b on the device (torch float64) or a host numpy array / CPU tensor
+        (then the copies happen inside the call, io_on_host). Returns (Q, info dict, status)."""
+        t = self._torch
+        o = ibdl_default_solve_opts()
+        o.rtol, o.restart, o.maxit, o.precision = rtol, restart, maxit, _PREC[precision]
+        o.inner_rtol, o.max_refine = inner_rtol, max_refine
+        host = isinstance(Ub, np.ndarray) or (hasattr(Ub, "is_cuda") and not Ub.is_cuda)
+        if host:
+            Ub = t.as_tensor(np.ascontiguousarray(np.asarray(Ub, dtype=np.float64)).reshape(-1)) \
+                if isinstance(Ub, np.ndarray) else Ub.contiguous()
+            o.io_on_host = 1
+            if Q is None:
+                Q = t.empty_like(Ub)
+        else:
+            Ub = self._vec(Ub)
+            if Q is None:
+                Q = t.empty_like(Ub)
+        info = ibdl_solve_info()
+        st = ibdl_solve(self._h, Ub.data_ptr(), Q.data_ptr(), o, info, _stream_handle(stream), check=check)
+        return Q, info.as_dict(), st
+
+    def set_stage_timing(self, enable: bool = True):
+        ibdl_set_stage_timing(self._h, int(enable))
+
+    def stage_times(self):
+        """{stage name: (total device ms, launches)} since the previous call."""
+        ms, n = ibdl_get_stage_times(self._h)
+        return {STAGE_NAMES[i]: (ms[i], n[i]) for i in range(IBDL_STAGE_COUNT) if n[i]}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            ibdl_destroy_geometry(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Tolerances (relative, ‖gpu − oracle‖₂/‖oracle‖₂ unless stated):
+  FP64 grid arithmetic  1e-12 for one application (FFT rounding is O(log N · 1e-16) and the
+                        operator norm is O(1)); 1e-10 for solves (the FP64 bound the method's
+                        accuracy target states).
+  FP32 grid arithmetic  2e-5 for one application (single-precision FFT rounding O(log N · 6e-8)
+                        amplified by the O(10) ratio of ‖S̃‖‖L⁻¹‖‖S*‖ to ‖A‖).
+  Mixed-precision solve 1e-8 against the oracle solution (refinement drives the FP64 residual
+                        below rtol·‖U_b‖ with rtol chosen so that the error bound holds).
+"""
+import numpy as np
+import pytest
+
+import ibdl_inputs as I
+from oracle import ibdl_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_07403_gb300 import build as b
+    from paper_2210_07403_gb300 import ibdl
+
+    b.build()
+    ibdl.load()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def _geom(p):
+    from paper_2210_07403_gb300 import Geometry
+
+    return Geometry.from_problem(p)
+
+
+def _scalar_problem(N, M, delta="cos", dipole="analytic", symbol="spectral", lam=0.0, center=(0.5, 0.5),
+                    R=0.25, box=1.0, origin=(0.0, 0.0)):
+    bd = I.circle(M, R, center)
+    Ub = I.harmonic_cubic(bd.X[0], bd.X[1], z0=center)[None, :]
+    return I.Problem("t", 2, N, box, origin, bd, Ub, "scalar", lam=lam, delta=delta, dipole=dipole, symbol=symbol)
+
+
+def _stokes_problem(N, M, delta="cos", dipole="analytic", symbol="spectral"):
+    p = I.star_stokes(N, M, delta=delta, dipole=dipole, symbol=symbol)
+    return p
+
+
+SCALAR_CASES = [
+    # N, M, delta, dipole, symbol, lam
+    (16, 25, "cos", "analytic", "spectral", 0.0),
+    (64, 100, "cos", "analytic", "spectral", 0.0),
+    (64, 100, "sqrt", "analytic", "fd2", 3.0),
+    (64, 137, "sqrt", "spectral_div", "spectral", 0.0),
+    (128, 201, "cos", "spectral_div", "fd2", 50.0),
+    (256, 403, "sqrt", "analytic", "spectral", 7.0),
+]
+
+
+@pytest.mark.parametrize("case", SCALAR_CASES)
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_scalar_apply(case, precision, tol):
+    N, M, delta, dipole, symbol, lam = case
+    p = _scalar_problem(N, M, delta, dipole, symbol, lam)
+    g = _geom(p)
+    og = O.geometry_from_problem(p)
+    rng = np.random.default_rng(N + M)
+    for _ in range(2):
+        q = rng.standard_normal(M)
+        y = g.apply(torch.from_numpy(q).cuda(), precision=precision).cpu().numpy()
+        assert _rel(y, O.apply(og, q)) < tol
+
+
+@pytest.mark.parametrize("dipole", ["analytic", "spectral_div"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_stokes_apply(dipole, precision, tol):
+    p = _stokes_problem(128, 200, dipole=dipole)
+    g = _geom(p)
+    og = O.geometry_from_problem(p)
+    q = np.random.default_rng(1).standard_normal(2 * p.bd.M)
+    y = g.apply(torch.from_numpy(q).cuda(), precision=precision).cpu().numpy()
+    assert _rel(y, O.apply(og, q)) < tol
+
+
+def test_apply_wraps_periodically_and_ragged_point_counts():
+    """Boundaries that cross the periodic box edge, a single point, and many points per cell."""
+    for center, M in [((0.02, 0.97), 90), ((0.5, 0.5), 1), ((0.3, 0.6), 1000)]:
+        p = _scalar_problem(32, M, "sqrt", "analytic", "spectral", 1.0, center=center, R=0.2)
+        g = _geom(p)
+        og = O.geometry_from_problem(p)
+        q = np.random.default_rng(M).standard_normal(M)
+        y = g.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+        assert _rel(y, O.apply(og, q)) < 1e-12
+
+
+def test_apply_box_and_origin():
+    """A non-unit box with the paper's centred origin (Sec. 2.2.1: [−L/2, L/2]²)."""
+    bd = I.circle(150, 0.6, (0.0, 0.0))
+    p = I.Problem("t", 2, 64, 2.0, (-1.0, -1.0), bd, np.sin(2 * bd.t)[None, :], "scalar", lam=1.0,
+                  delta="sqrt", dipole="spectral_div", symbol="fd2")
+    g = _geom(p)
+    q = np.random.default_rng(3).standard_normal(150)
+    y = g.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+    assert _rel(y, O.apply(O.geometry_from_problem(p), q)) < 1e-12
+
+
+@pytest.mark.parametrize("pde", ["scalar", "stokes"])
+def test_evaluate_field(pde):
+    p = _scalar_problem(64, 100) if pde == "scalar" else _stokes_problem(64, 120)
+    g = _geom(p)
+    og = O.geometry_from_problem(p)
+    q = np.random.default_rng(2).standard_normal(p.ncomp * p.bd.M)
+    u = g.evaluate_field(torch.from_numpy(q).cuda()).cpu().numpy()
+    ref = O.grid_field(og, q)
+    assert u.shape == ref.shape
+    assert _rel(u, ref) < 1e-12
+
+
+@pytest.mark.parametrize("dipole", ["analytic", "spectral_div"])
+def test_adjoint(dipole):
+    p = _scalar_problem(64, 100, "sqrt", dipole, "spectral", 2.0)
+    g = _geom(p)
+    og = O.geometry_from_problem(p)
+    w = np.random.default_rng(4).standard_normal(100)
+    z = g.adjoint(torch.from_numpy(w).cuda()).cpu().numpy()
+    assert _rel(z, O.adjoint_apply(og, w)) < 1e-12
+    z32 = g.adjoint(torch.from_numpy(w).cuda(), precision="fp32").cpu().numpy()
+    assert _rel(z32, O.adjoint_apply(og, w)) < 2e-5
+
+
+def test_solve_circle_laplace_fp64():
+    """The 64² circle workload: GMRES to 1e-10, same iteration count and Q as the oracle."""
+    p = I.circle_laplace(64, 100)
+    g = _geom(p)
+    ref = O.solve(O.geometry_from_problem(p), p.Ub, 1e-10)
+    Q, info, _ = g.solve(torch.from_numpy(p.Ub.reshape(-1)).cuda(), rtol=1e-10)
+    assert info["iterations"] == ref.iterations
+    assert _rel(Q.cpu().numpy(), ref.x) < 1e-10
+    assert info["rel_residual"] <= 1e-10
+
+
+def test_solve_paper_iteration_count():
+    """The paper's circle Helmholtz problem (Sec. 5.4.1) needs 4 GMRES iterations at N = 256."""
+    p = I.paper_circle_helmholtz(256, 1.0)
+    g = _geom(p)
+    Q, info, _ = g.solve(torch.from_numpy(p.Ub.reshape(-1)).cuda(), rtol=1e-8)
+    assert info["iterations"] == 4
+    ref = O.solve(O.geometry_from_problem(p), p.Ub, 1e-8)
+    assert _rel(Q.cpu().numpy(), ref.x) < 1e-10
+
+
+def test_solve_stokes_full_size_fp64_and_mixed():
+    """The 512² Stokes star workload at full size: FP64 plain GMRES and mixed precision
+    (FP32 applies, FP64 Arnoldi and refinement) against the oracle's solution."""
+    p = I.star_stokes()
+    g = _geom(p)
+    og = O.geometry_from_problem(p)
+    ref = O.solve(og, p.Ub, 1e-12, maxit=80)
+    ub = torch.from_numpy(p.Ub.reshape(-1)).cuda()
+    Q64, info64, _ = g.solve(ub, rtol=1e-12, maxit=80)
+    assert _rel(Q64.cpu().numpy(), ref.x) < 1e-10
+    Qm, infom, _ = g.solve(ub, rtol=1e-10, precision="mixed", maxit=200)
+    assert infom["rel_residual"] <= 1e-10
+    assert _rel(Qm.cpu().numpy(), ref.x) < 1e-8
+    assert infom["fp32_applies"] > infom["fp64_applies"]
+    # sampled operator outputs at full size
+    q = np.random.default_rng(5).standard_normal(2 * p.bd.M)
+    y = g.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+    assert _rel(y, O.apply(og, q)) < 1e-12
+
+
+def test_solve_host_buffers():
+    p = I.circle_laplace(64, 100)
+    g = _geom(p)
+    Q, info, _ = g.solve(p.Ub.reshape(-1), rtol=1e-10)
+    ref = O.solve(O.geometry_from_problem(p), p.Ub, 1e-10)
+    assert not Q.is_cuda
+    assert _rel(Q.numpy(), ref.x) < 1e-10
+
+
+def test_error_paths():
+    from paper_2210_07403_gb300 import ibdl
+
+    p = I.circle_laplace(32, 50)
+    g = _geom(p)
+    q_host = torch.zeros(50, dtype=torch.float64)
+    with pytest.raises(ibdl.IbdlError) as e:
+        ibdl.ibdl_apply(g.handle, ibdl.IBDL_FP64, q_host.data_ptr(), q_host.data_ptr())
+    assert e.value.status == ibdl.IBDL_ERR_INVALID_ARG
+    ub = torch.from_numpy(p.Ub.reshape(-1)).cuda()
+    bad = ub.clone()
+    bad[3] = float("nan")
+    _, _, st = g.solve(bad, check=False)
+    assert st == ibdl.IBDL_ERR_NONFINITE
+    Q, info, st = g.solve(ub, rtol=1e-12, maxit=1, check=False)
+    assert st == ibdl.IBDL_ERR_NOT_CONVERGED and info["iterations"] == 1
+    # the geometry is still usable afterwards
+    Q, info, st = g.solve(ub, rtol=1e-8)
+    assert st == ibdl.IBDL_OK
+    with pytest.raises(ibdl.IbdlError):
+        ibdl.ibdl_apply(g.handle, 7, ub.data_ptr(), Q.data_ptr())
