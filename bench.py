@@ -1,0 +1,376 @@
+"""Benchmark of the IBDL operator hot path on GB300 (one JSON line on rank 0).
+
+Workload: 2-D steady Stokes IBDL solve on the unit periodic box, 512² grid, star
+r(θ) = 0.25(1 + 0.2 cos 5θ) with 800 points equispaced in arclength, cosine 4-point delta,
+analytic dipole spread, spectral symbols; boundary data = rigid rotation + seeded random modes
+|m| ≤ 8, amplitude 0.1, made flux free (synthetic, seed 2).
+
+A step is one mixed-precision solve (FP32 operator applications inside GMRES, FP64 Arnoldi,
+FP64 refinement residual) to the relative residual that keeps the solution within 1e-8 of the
+FP64 plain GPU solve. `value` is solves/s over all ranks (each rank solves its own replica:
+weak scaling, no collective). L2 is flushed (a 256 MiB write) before every timed step and the
+flush is outside the per-step CUDA-event timing.
+
+Also reported: FP32/FP64 operator applications per second, the FP64 plain GPU solve rate, the
+per-kernel device times (stage timing events), the roofline of the dominant kernel, SM clocks
+sampled during the timed region, the end-to-end rate through the C ABI with host buffers, and
+the FP64 CPU oracle timed on this host (`cpu_baseline`).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IBDL operator applies/s & solves/s at 1e-8 vs FP64 plain GPU; % HBM roofline"
+WORKLOAD = "stokes_star_512"
+N_GRID, N_POINTS = 512, 800
+SOLVE_RTOL = 1e-9          # residual tolerance of the timed solves (error ≤ 1e-8 checked below)
+REF_RTOL = 1e-13           # the FP64 plain GPU reference solution
+ACCURACY = 1e-8
+
+
+def _config():
+    return {"workload": WORKLOAD, "grid": f"{N_GRID}x{N_GRID}", "n_points": N_POINTS, "pde": "stokes",
+            "delta": "cos", "dipole": "analytic", "symbol": "spectral", "solve_rtol": SOLVE_RTOL,
+            "precision": "mixed: fp32 applies, fp64 arnoldi + refinement",
+            "l2": "flushed before each timed step (256 MiB write, untimed)", "seed": 2}
+
+
+def _problem():
+    import ibdl_inputs as I
+
+    return I.star_stokes(N_GRID, N_POINTS)
+
+
+# ------------------------------------------------------------------------------------------
+# the FP64 CPU oracle (cpu_baseline and --impl reference)
+# ------------------------------------------------------------------------------------------
+
+_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import ibdl_inputs as I
+from oracle import ibdl_oracle as O
+p = I.star_stokes({n}, {m})
+g = O.geometry_from_problem(p)
+times = []
+t_end = time.perf_counter() + {budget}
+while len(times) < {max_solves} and (not times or time.perf_counter() < t_end):
+    t0 = time.perf_counter()
+    r = O.solve(g, p.Ub, {rtol}, maxit=100)
+    times.append(time.perf_counter() - t0)
+print(json.dumps({{"times": times, "iterations": r.iterations}}))
+"""
+
+
+def run_oracle(budget_s: float, max_solves: int, rtol: float = SOLVE_RTOL):
+    """Time the oracle's FP64 solve of the workload in a fresh single-threaded process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _ORACLE_SNIPPET.format(root=ROOT, n=N_GRID, m=N_POINTS, budget=budget_s, max_solves=max_solves,
+                                  rtol=rtol)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+
+_SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={_SMI_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# algorithmic HBM bytes per launch of each kernel of the 2-D Stokes application (analytic
+# dipole: 3 fields spread, 2 interpolated), w bytes per real, grid N²: the packed half
+# spectrum of one real field is N²·w bytes.
+def _kernel_bytes(stage: str, n: int, m: int) -> float:
+    w = 8 if stage.endswith("fp64") else 4
+    grid = n * n * w
+    pts = m * (2 * 4 * 4 + 4) * w / 2  # point tables read per pass (small)
+    if stage.startswith("spread_rowfft"):
+        return 3 * grid + pts
+    if stage.startswith("column"):
+        return 5 * grid
+    if stage.startswith("rowifft_gather"):
+        return 2 * grid + pts
+    return 0.0
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2210_07403_gb300 import Geometry, build as b
+    from paper_2210_07403_gb300 import ibdl
+
+    b.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p = _problem()
+    geom = Geometry.from_problem(p)
+    nd = 2 * p.bd.M
+    ub = torch.from_numpy(p.Ub.reshape(-1).copy()).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def l2_flush():
+        flush.fill_(1.0)
+
+    # FP64 plain GPU reference solution (tight tolerance)
+    q_ref, info_ref, _ = geom.solve(ub, rtol=REF_RTOL, maxit=100)
+
+    def solve(precision, host=False):
+        if host:
+            return geom.solve(ub_host, rtol=SOLVE_RTOL, precision=precision, maxit=200)
+        return geom.solve(ub, rtol=SOLVE_RTOL, precision=precision, maxit=200)
+
+    ub_host = torch.from_numpy(p.Ub.reshape(-1).copy()).pin_memory()
+
+    for _ in range(args.warmup):
+        solve("mixed")
+        solve("fp64")
+        geom.apply(ub, precision="fp32")
+        geom.apply(ub, precision="fp64")
+    torch.cuda.synchronize()
+
+    def timed(fn, K):
+        """K device-timed calls of fn with an untimed L2 flush before each; returns ms list."""
+        ms = []
+        outs = []
+        for _ in range(K):
+            l2_flush()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs.append(fn())
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, outs
+
+    K = args.steps
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    geom.set_stage_timing(True)
+    geom.stage_times()
+    with ClockSampler(local_rank) as clocks:
+        t_wall0 = time.perf_counter()
+        ms_mixed, outs = timed(lambda: solve("mixed"), K)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    stages_mixed = geom.stage_times()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    err_mixed = max(float(torch.linalg.norm(q - q_ref) / torch.linalg.norm(q_ref)) for q, _, _ in outs)
+    info_m = outs[-1][1]
+    launches = int(sum(o[1]["kernel_launches"] for o in outs))
+
+    # FP64 plain GPU solves (the comparison path)
+    ms_fp64, outs64 = timed(lambda: solve("fp64"), K)
+    err_fp64 = max(float(torch.linalg.norm(q - q_ref) / torch.linalg.norm(q_ref)) for q, _, _ in outs64)
+
+    # operator applications, per-kernel device times for the roofline
+    Y = torch.empty_like(ub)
+    geom.stage_times()
+    ms_a32, _ = timed(lambda: geom.apply(ub, Y, precision="fp32"), max(K, 20))
+    st32 = geom.stage_times()
+    ms_a64, _ = timed(lambda: geom.apply(ub, Y, precision="fp64"), max(K, 20))
+    st64 = geom.stage_times()
+    geom.set_stage_timing(False)
+
+    # end to end through the C ABI with host buffers (copies inside the call)
+    ms_e2e, outs_e2e = timed(lambda: solve("mixed", host=True), K)
+    err_e2e = max(float(torch.linalg.norm(q.to(dev) - q_ref) / torch.linalg.norm(q_ref)) for q, _, _ in outs_e2e)
+
+    # max over ranks
+    t_mixed = sum(ms_mixed) / 1e3
+    t_e2e = sum(ms_e2e) / 1e3
+    tt = torch.tensor([t_mixed, t_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t_mixed, t_e2e = float(tt[0]), float(tt[1])
+    if rank != 0:
+        return None
+
+    value = world * K / t_mixed
+    e2e_value = world * K / t_e2e
+
+    # dominant kernel of the timed mixed solves, and its average launch from the apply loop
+    per_stage = {k: v for k, v in stages_mixed.items()}
+    dom = max((k for k in per_stage if k != "arnoldi" and k != "other"), key=lambda k: per_stage[k][0])
+    loop = st32 if dom.endswith("fp32") else st64
+    dom_ms = loop[dom][0] / loop[dom][1]
+    bytes_dom = _kernel_bytes(dom, N_GRID, N_POINTS)
+    peak, peak_src = _peaks()
+    achieved = bytes_dom / (dom_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
+            "avg_launch_us": round(dom_ms * 1e3, 2), "algorithmic_bytes": int(bytes_dom),
+            "note": "grid fields are L2-resident between kernels of one application (6 MB FP32)"}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        o = run_oracle(budget_s=12.0, max_solves=8)
+        tm = float(np.mean(o["times"]))
+        cpu = {"value": round(1.0 / tm, 4), "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(o['times'])} FP64 numpy oracle solves of the 512² Stokes star to rtol "
+                         f"{SOLVE_RTOL:g} ({o['iterations']} GMRES iterations each), single thread"}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(t_mixed / K * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 applies + f64 arnoldi/refinement",
+        "data": "synthetic (seeded star boundary and Fourier-mode boundary data)", "config": _config(),
+        "applies_per_s": {"fp32": round(1e3 / float(np.mean(ms_a32)), 1),
+                          "fp64": round(1e3 / float(np.mean(ms_a64)), 1)},
+        "fp64_plain": {"solves_per_s": round(K / (sum(ms_fp64) / 1e3), 3), "error_vs_ref": err_fp64,
+                       "iterations": outs64[-1][1]["iterations"]},
+        "mixed": {"error_vs_fp64_plain": err_mixed, "iterations": info_m["iterations"],
+                  "fp32_applies": info_m["fp32_applies"], "fp64_applies": info_m["fp64_applies"],
+                  "sweeps": info_m["sweeps"], "rel_residual": info_m["rel_residual"],
+                  "accuracy_ok": err_mixed <= ACCURACY},
+        "speedup_mixed_vs_fp64_plain": round(sum(ms_fp64) / sum(ms_mixed), 3),
+        "stage_ms_per_step": {k: round(v[0] / K, 4) for k, v in stages_mixed.items()},
+        "stage_launches_per_step": {k: round(v[1] / K, 2) for k, v in stages_mixed.items()},
+        "apply_kernel_us": {**{k: round(v[0] / v[1] * 1e3, 2) for k, v in st32.items()},
+                            **{k: round(v[0] / v[1] * 1e3, 2) for k, v in st64.items()}},
+        "roofline": roof,
+        "clocks": clocks.summary(),
+        "e2e": {"value": round(e2e_value, 3), "unit": "solves/s", "h2d_bytes_per_step": nd * 8,
+                "d2h_bytes_per_step": nd * 8, "error_vs_fp64_plain": err_e2e},
+        "gpu_launches": launches,
+        "wall_s_timed_region": round(t_wall, 3),
+        "cpu_baseline": cpu,
+    }
+    geom.close()
+    return out
+
+
+# ------------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ------------------------------------------------------------------------------------------
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return None
+    o = run_oracle(budget_s=1e9, max_solves=args.warmup + args.steps)
+    times = o["times"][args.warmup:]
+    K = len(times)
+    value = K / sum(times)
+    return {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": args.gpus, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(sum(times) / K * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(),
+        "impl": "reference",
+        "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "kind": "oracle", "cores": 1,
+                         "sample": f"{K} FP64 numpy oracle solves of the 512² Stokes star, single thread"},
+        "e2e": {"value": round(value, 4), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
