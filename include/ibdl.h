@@ -169,6 +169,23 @@ void ibdl_default_solve_opts(ibdl_solve_opts* opts);
 /* Geometry facts: number of density components c and points M. */
 ibdl_status ibdl_geometry_sizes(const ibdl_geometry* geom, int* ncomp, int64_t* n_points);
 
+/* Y = A Q for a 2-D problem without allocating any memory (the paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, e.g. code inside a region being
+ * captured into a CUDA graph, or a real-time loop that must not take the allocator's locks; such
+ * callers cannot create an ibdl_geometry, which allocates). `desc` describes the geometry as for
+ * ibdl_create_geometry, with X, normals and weights in device memory (inputs_on_device = 1); their
+ * values are not checked (finite coordinates, unit normals and positive weights are the caller's
+ * responsibility). Q and Y are device FP64 arrays [c][M]; `precision` is IBDL_FP64 or IBDL_FP32.
+ * All work space comes from one fixed 8 MiB array inside the library, per GPU, held from library
+ * load to process exit: problems needing more (about nf·n²·8 bytes of spectra with nf = 1 to 4
+ * fields, plus about 250 bytes per point) are rejected with IBDL_ERR_INVALID_ARG and a message
+ * giving the size. The first call on each GPU looks up that array's device address (a one-time
+ * set-up that makes no stream call); make that first call before any stream capture begins. Every
+ * call rebuilds the point tables in the shared array, so calls whose GPU work overlaps (other
+ * streams or threads) race and give wrong results. Asynchronous on `stream`. */
+ibdl_status ibdl_apply_noalloc(const ibdl_geometry_desc* desc, int precision, const double* Q, double* Y,
+                               void* stream);
+
 /* Message for the last failed call on this thread ("" if none). Valid until the next call. */
 const char* ibdl_last_error(void);
 

@@ -141,6 +141,25 @@ __global__ void k_symbols(int n, double box, int symbol, double* lap64, double* 
   der32[j] = (float)der;
 }
 
+// Runs the set-up kernels of a geometry into buffers the caller already holds (g's table,
+// spectrum and symbol pointers, plus key/count/cursor work arrays); allocates nothing.
+ibdl_status fill_geometry_tables(Geometry* g, const double* dX, const double* dN, const double* dW, int* key,
+                                 int* count, int* cursor, cudaStream_t s) {
+  const int M = (int)g->M, n = g->n, dim = g->dim, tb = 256;
+  IBDL_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * g->ncell, s));
+  k_point_keys<<<(M + tb - 1) / tb, tb, 0, s>>>(dim, n, M, dX, g->origin[0], g->origin[1], g->origin[2], g->h, key, count);
+  k_scan<<<1, 1024, 0, s>>>(g->ncell, count, g->cell_start);
+  IBDL_CUDA(cudaMemcpyAsync(cursor, g->cell_start, sizeof(int) * (g->ncell + 1), cudaMemcpyDeviceToDevice, s));
+  k_scatter<<<(M + tb - 1) / tb, tb, 0, s>>>(M, key, cursor, g->perm);
+  k_sort_cells<<<(g->ncell + tb - 1) / tb, tb, 0, s>>>(g->ncell, g->cell_start, g->perm);
+  k_tables<<<(M + tb - 1) / tb, tb, 0, s>>>(dim, n, M, g->delta, dX, dN, dW, g->origin[0], g->origin[1], g->origin[2],
+                                             g->h, g->perm, g->base, g->t64, g->t32);
+  k_twiddles<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->tw64, g->tw32);
+  k_symbols<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->box, g->symbol, g->lap64, g->der64, g->lap32, g->der32);
+  IBDL_CUDA(cudaGetLastError());
+  return IBDL_OK;
+}
+
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 template <typename P>

@@ -77,6 +77,7 @@ SIGNATURES = {
     "ibdl_evaluate_field": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ibdl_default_solve_opts": (None, [POINTER(ibdl_solve_opts)]),
     "ibdl_geometry_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int64)]),
+    "ibdl_apply_noalloc": (c_int, [POINTER(ibdl_geometry_desc), c_int, c_void_p, c_void_p, c_void_p]),
     "ibdl_set_stage_timing": (c_int, [c_void_p, c_int]),
     "ibdl_get_stage_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
     "ibdl_last_error": (c_char_p, []),
