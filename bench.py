@@ -36,6 +36,7 @@ METRIC = "IBDL operator applies/s & solves/s at 1e-8 vs FP64 plain GPU; % HBM ro
 WORKLOAD = "stokes_star_512"
 N_GRID, N_POINTS = 512, 800
 SOLVE_RTOL = 1e-9          # residual tolerance of the timed solves (error ≤ 1e-8 checked below)
+INNER_RTOL = 1e-5          # relative tolerance of each inner FP32-apply GMRES (two refinement sweeps)
 REF_RTOL = 1e-13           # the FP64 plain GPU reference solution
 ACCURACY = 1e-8
 
@@ -43,7 +44,8 @@ ACCURACY = 1e-8
 def _config():
     return {"workload": WORKLOAD, "grid": f"{N_GRID}x{N_GRID}", "n_points": N_POINTS, "pde": "stokes",
             "delta": "cos", "dipole": "analytic", "symbol": "spectral", "solve_rtol": SOLVE_RTOL,
-            "precision": "mixed: fp32 applies, fp64 arnoldi + refinement",
+            "precision": "mixed: fp32 applies, fp64 arnoldi + refinement", "inner_rtol": INNER_RTOL,
+            "gmres": "restart 50, each cycle one CUDA graph with a device-side while loop",
             "l2": "flushed before each timed step (256 MiB write, untimed)", "seed": 2}
 
 
@@ -191,9 +193,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     q_ref, info_ref, _ = geom.solve(ub, rtol=REF_RTOL, maxit=100)
 
     def solve(precision, host=False):
-        if host:
-            return geom.solve(ub_host, rtol=SOLVE_RTOL, precision=precision, maxit=200)
-        return geom.solve(ub, rtol=SOLVE_RTOL, precision=precision, maxit=200)
+        src = ub_host if host else ub
+        return geom.solve(src, rtol=SOLVE_RTOL, precision=precision, maxit=200, inner_rtol=INNER_RTOL)
 
     ub_host = torch.from_numpy(p.Ub.reshape(-1).copy()).pin_memory()
 
@@ -223,14 +224,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    geom.set_stage_timing(True)
-    geom.stage_times()
     with ClockSampler(local_rank) as clocks:
         t_wall0 = time.perf_counter()
         ms_mixed, outs = timed(lambda: solve("mixed"), K)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
-    stages_mixed = geom.stage_times()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -242,6 +240,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # FP64 plain GPU solves (the comparison path)
     ms_fp64, outs64 = timed(lambda: solve("fp64"), K)
     err_fp64 = max(float(torch.linalg.norm(q - q_ref) / torch.linalg.norm(q_ref)) for q, _, _ in outs64)
+
+    # per-stage device time of a mixed solve (a separate pass: stage timing records an event
+    # around every kernel and drives GMRES from the host, so it is kept out of the timed steps)
+    geom.set_stage_timing(True)
+    geom.stage_times()
+    for _ in range(K):
+        solve("mixed")
+    stages_mixed = geom.stage_times()
 
     # operator applications, per-kernel device times for the roofline
     Y = torch.empty_like(ub)
@@ -304,8 +310,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                   "sweeps": info_m["sweeps"], "rel_residual": info_m["rel_residual"],
                   "accuracy_ok": err_mixed <= ACCURACY},
         "speedup_mixed_vs_fp64_plain": round(sum(ms_fp64) / sum(ms_mixed), 3),
-        "stage_ms_per_step": {k: round(v[0] / K, 4) for k, v in stages_mixed.items()},
-        "stage_launches_per_step": {k: round(v[1] / K, 2) for k, v in stages_mixed.items()},
+        "stage_ms_per_solve_host_driven": {k: round(v[0] / K, 4) for k, v in stages_mixed.items()},
+        "stage_launches_per_solve": {k: round(v[1] / K, 2) for k, v in stages_mixed.items()},
         "apply_kernel_us": {**{k: round(v[0] / v[1] * 1e3, 2) for k, v in st32.items()},
                             **{k: round(v[0] / v[1] * 1e3, 2) for k, v in st64.items()}},
         "roofline": roof,

@@ -62,11 +62,24 @@ struct RowParams {
   const cplx<T>* tw;  // [n]
   const int* stop;    // optional: skip all work when *stop != 0
   double* grid;       // G_GRID: [nf][n][n]
+  const int* idx;     // optional: in += (*idx)·vstride, out += (*idx + 1)·vstride (Krylov basis)
+  int vstride;
 };
 
 template <typename T>
+__device__ __forceinline__ void resolve_io(const RowParams<T>& p, const double*& in, double*& out) {
+  in = p.in;
+  out = p.out;
+  if (p.idx) {
+    const int k = *p.idx;
+    in += (size_t)k * p.vstride;
+    out += (size_t)(k + 1) * p.vstride;
+  }
+}
+
+template <typename T>
 struct ColParams {
-  int n, log2n, C;
+  int n, log2n, C, lc;
   T lam, scale;
   const T* lap1;
   const T* der1;
@@ -109,15 +122,20 @@ __global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = p.n, R = p.R, half = R >> 1, M = p.M;
   const int seqs = NIN * half;
-  cplx<T>* bufA = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufA = tws + n;
   cplx<T>* bufB = bufA + (size_t)seqs * n;
   T* acc = reinterpret_cast<T*>(bufA);  // field f, local row lr, column x at ((f·half + lr/2)·n + x)·2 + (lr & 1)
   const int r0 = blockIdx.x * R;
+  const double* pin;
+  double* pout;
+  resolve_io(p, pin, pout);
 
   // jump term: out = ½·in (the gather kernel adds S*u afterwards)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NC * M; i += gridDim.x * blockDim.x)
-    p.out[i] = 0.5 * p.in[i];
+    pout[i] = 0.5 * pin[i];
   for (int i = threadIdx.x; i < seqs * n * 2; i += blockDim.x) acc[i] = T(0);
+  load_twiddles(tws, p.tw, n);
   __syncthreads();
 
   const PointRanges pr = band_points(p.cell_start, n, r0, R);
@@ -138,17 +156,17 @@ __global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
     // per-point source strengths
     T c0 = 0, c1 = 0, c2 = 0, c3 = 0;
     if (OP == OP_SCALAR_AN || OP == OP_SCALAR_SD) {
-      const T q = T(p.in[i]) * ws;
+      const T q = T(pin[i]) * ws;
       c0 = q * nx;
       c1 = q * ny;
     } else if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
-      const T qx = T(p.in[i]), qy = T(p.in[M + i]);
+      const T qx = T(pin[i]), qy = T(pin[M + i]);
       c0 = ws * (qx * nx + qy * ny);      // Q·n
       c1 = ws * (T(2) * qx * nx);         // A_xx
       c2 = ws * (T(2) * qy * ny);         // A_yy
       c3 = ws * (qx * ny + qy * nx);      // A_xy
     } else {
-      c0 = T(p.in[i]) * ws;               // plain spread of W
+      c0 = T(pin[i]) * ws;                // plain spread of W
     }
 #pragma unroll
     for (int ay = 0; ay < 4; ++ay) {
@@ -185,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
   }
   __syncthreads();
 
-  const cplx<T>* res = fft_stockham<T, false>(bufA, bufB, p.log2n, seqs, n, p.tw);
+  const cplx<T>* res = fft_stockham<T, false>(bufA, bufB, p.log2n, seqs, n, tws);
 
   // unpack Z = FFT(a + i b) into A = FFT(a), B = FFT(b), k = 0..n/2, packed format
   const int nh = n >> 1, lnh = p.log2n - 1;
@@ -261,23 +279,25 @@ __global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
   constexpr int NOUT = Traits<OP>::NOUT;
   constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = p.n, C = p.C, nh = n >> 1;
-  cplx<T>* bufA = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int n = p.n, C = p.C, nh = n >> 1, lc = p.lc, lnc = p.log2n + p.lc;
+  cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufA = tws + n;
   cplx<T>* bufB = bufA + (size_t)NMAX * C * n;
   const int k0 = blockIdx.x * C;
 
-  for (int t = threadIdx.x; t < NIN * n * C; t += blockDim.x) {
-    const int f = t / (n * C);
-    const int rem = t - f * n * C;
-    const int row = rem / C, c = rem - row * C;
-    bufA[(size_t)(f * C + c) * n + row] = p.spec[((size_t)f * n + row) * nh + k0 + c];
+  for (int t = threadIdx.x; t < (NIN << lnc); t += blockDim.x) {
+    const int f = t >> lnc;
+    const int rem = t & ((1 << lnc) - 1);
+    const int row = rem >> lc, c = rem & (C - 1);
+    bufA[(size_t)((f << lc) + c) * n + row] = p.spec[((size_t)f * n + row) * nh + k0 + c];
   }
+  load_twiddles(tws, p.tw, n);
   __syncthreads();
-  cplx<T>* res = fft_stockham<T, false>(bufA, bufB, p.log2n, NIN * C, n, p.tw);
+  cplx<T>* res = fft_stockham<T, false>(bufA, bufB, p.log2n, NIN * C, n, tws);
   cplx<T>* other = res == bufA ? bufB : bufA;
 
-  for (int t = threadIdx.x; t < C * n; t += blockDim.x) {
-    const int c = t / n, ky = t - c * n;
+  for (int t = threadIdx.x; t < (C << p.log2n); t += blockDim.x) {
+    const int c = t >> p.log2n, ky = t & (n - 1);
     const int kx = k0 + c;
     cplx<T> in[NIN], out[NOUT];
     if (kx != 0) {
@@ -313,12 +333,12 @@ __global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
     }
   }
   __syncthreads();
-  const cplx<T>* out = fft_stockham<T, true>(res, other, p.log2n, NOUT * C, n, p.tw);
-  for (int t = threadIdx.x; t < NOUT * n * C; t += blockDim.x) {
-    const int f = t / (n * C);
-    const int rem = t - f * n * C;
-    const int row = rem / C, c = rem - row * C;
-    p.spec[((size_t)f * n + row) * nh + k0 + c] = out[(size_t)(f * C + c) * n + row];
+  const cplx<T>* out = fft_stockham<T, true>(res, other, p.log2n, NOUT * C, n, tws);
+  for (int t = threadIdx.x; t < (NOUT << lnc); t += blockDim.x) {
+    const int f = t >> lnc;
+    const int rem = t & ((1 << lnc) - 1);
+    const int row = rem >> lc, c = rem & (C - 1);
+    p.spec[((size_t)f * n + row) * nh + k0 + c] = out[(size_t)((f << lc) + c) * n + row];
   }
 }
 
@@ -332,9 +352,11 @@ __global__ void __launch_bounds__(kThreads) k_rowifft_gather(RowParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = p.n, R = p.R, half = R >> 1, M = p.M, nh = n >> 1, lnh = p.log2n - 1;
   const int seqs = NOUT * half;
-  cplx<T>* bufA = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufA = tws + n;
   cplx<T>* bufB = bufA + (size_t)seqs * n;
   const int r0 = blockIdx.x * R;
+  load_twiddles(tws, p.tw, n);
 
   // rebuild Z = A + i B over all k from the packed half spectra of rows (r0+2j, r0+2j+1)
   for (int t = threadIdx.x; t < seqs * nh; t += blockDim.x) {
@@ -353,7 +375,7 @@ __global__ void __launch_bounds__(kThreads) k_rowifft_gather(RowParams<T> p) {
     }
   }
   __syncthreads();
-  const cplx<T>* res = fft_stockham<T, true>(bufA, bufB, p.log2n, seqs, n, p.tw);
+  const cplx<T>* res = fft_stockham<T, true>(bufA, bufB, p.log2n, seqs, n, tws);
   const T* u = reinterpret_cast<const T*>(res);  // field f, row lr, col x at ((f·half + lr/2)·n + x)·2 + (lr&1)
   const size_t fstride = (size_t)half * n * 2;
 
@@ -367,6 +389,9 @@ __global__ void __launch_bounds__(kThreads) k_rowifft_gather(RowParams<T> p) {
     return;
   }
 
+  const double* pin;
+  double* pout;
+  resolve_io(p, pin, pout);
   const PointRanges pr = band_points(p.cell_start, n, r0, R);
   for (int t = threadIdx.x; t < pr.cnt; t += blockDim.x) {
     const int s = pr.at(t);
@@ -407,16 +432,16 @@ __global__ void __launch_bounds__(kThreads) k_rowifft_gather(RowParams<T> p) {
     }
     if (!touched) continue;
     if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
-      atomicAdd(p.out + i, double(acc0));
-      atomicAdd(p.out + M + i, double(acc1));
+      atomicAdd(pout + i, double(acc0));
+      atomicAdd(pout + M + i, double(acc1));
     } else if (OP == OP_ADJ_AN) {
       // (S̃)* v = n · (kernel-gradient gather of v)
-      atomicAdd(p.out + i, double(p.nrm[s]) * double(acc0) + double(p.nrm[M + s]) * double(acc1));
+      atomicAdd(pout + i, double(p.nrm[s]) * double(acc0) + double(p.nrm[M + s]) * double(acc1));
     } else if (OP == OP_ADJ_SD) {
       // (S̃)* v = −Σ_m n_m S*(∂_m v)
-      atomicAdd(p.out + i, -(double(p.nrm[s]) * double(acc0) + double(p.nrm[M + s]) * double(acc1)));
+      atomicAdd(pout + i, -(double(p.nrm[s]) * double(acc0) + double(p.nrm[M + s]) * double(acc1)));
     } else {
-      atomicAdd(p.out + i, double(acc0));
+      atomicAdd(pout + i, double(acc0));
     }
   }
 }
@@ -446,6 +471,8 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.tw = reinterpret_cast<const cplx<T>*>(pi ? (const void*)g->tw32 : (const void*)g->tw64);
   rp.stop = stop;
   rp.grid = grid;
+  rp.idx = nullptr;
+  rp.vstride = 0;
   return rp;
 }
 
@@ -456,6 +483,7 @@ static ColParams<T> col_params(Geometry* g, const int* stop) {
   cp.n = g->n;
   cp.log2n = __builtin_ctz(g->n);
   cp.C = g->cols_per_cta[pi];
+  cp.lc = __builtin_ctz(cp.C ? cp.C : 1);
   cp.lam = T(g->pde == IBDL_PDE_SCALAR ? g->lambda : 0.0);
   cp.scale = T(1.0 / ((double)g->n * (double)g->n));
   cp.lap1 = reinterpret_cast<const T*>(pi ? (const void*)g->lap32 : (const void*)g->lap64);
@@ -468,23 +496,43 @@ static ColParams<T> col_params(Geometry* g, const int* stop) {
 
 template <typename T, int OP>
 static size_t smem_spread(const Geometry* g, int R) {
-  return 2 * (size_t)Traits<OP>::NIN * (R / 2) * g->n * sizeof(cplx<T>);
+  return (2 * (size_t)Traits<OP>::NIN * (R / 2) + 1) * g->n * sizeof(cplx<T>);
 }
 template <typename T, int OP>
 static size_t smem_gather(const Geometry* g, int R) {
-  return 2 * (size_t)Traits<OP>::NOUT * (R / 2) * g->n * sizeof(cplx<T>);
+  return (2 * (size_t)Traits<OP>::NOUT * (R / 2) + 1) * g->n * sizeof(cplx<T>);
 }
 template <typename T, int OP>
 static size_t smem_col(const Geometry* g, int C) {
   const int nmax = Traits<OP>::NIN > Traits<OP>::NOUT ? Traits<OP>::NIN : Traits<OP>::NOUT;
-  return 2 * (size_t)nmax * C * g->n * sizeof(cplx<T>);
+  return (2 * (size_t)nmax * C + 1) * g->n * sizeof(cplx<T>);
 }
 
 static const size_t kSmemLimit = 227 * 1024;
 
 template <typename T, int OP>
+static ibdl_status set_attrs() {
+  IBDL_CUDA(cudaFuncSetAttribute(k_spread_rowfft<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+  IBDL_CUDA(cudaFuncSetAttribute(k_colpass<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+  IBDL_CUDA(cudaFuncSetAttribute(k_rowifft_gather<T, OP, G_INTERP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+  IBDL_CUDA(cudaFuncSetAttribute(k_rowifft_gather<T, OP, G_GRID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+  return IBDL_OK;
+}
+
+template <typename T>
+static ibdl_status set_attrs_all() {
+  IBDL_TRY((set_attrs<T, OP_SCALAR_AN>()));
+  IBDL_TRY((set_attrs<T, OP_SCALAR_SD>()));
+  IBDL_TRY((set_attrs<T, OP_STOKES_AN>()));
+  IBDL_TRY((set_attrs<T, OP_STOKES_SD>()));
+  IBDL_TRY((set_attrs<T, OP_ADJ_AN>()));
+  IBDL_TRY((set_attrs<T, OP_ADJ_SD>()));
+  return IBDL_OK;
+}
+
+template <typename T, int OP>
 static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream_t s, const int* stop,
-                          double* grid) {
+                          double* grid, const int* idx = nullptr, int vstride = 0) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi];
   if (R == 0 || C == 0)
@@ -492,16 +540,9 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   const size_t s1 = smem_spread<T, OP>(g, R), s2 = smem_col<T, OP>(g, C), s3 = smem_gather<T, OP>(g, R);
   if (s1 > kSmemLimit || s2 > kSmemLimit || s3 > kSmemLimit)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
-  // Opt in to large dynamic shared memory once per kernel instance.
-  static bool attr_done = false;
-  if (!attr_done) {
-    IBDL_CUDA(cudaFuncSetAttribute(k_spread_rowfft<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-    IBDL_CUDA(cudaFuncSetAttribute(k_colpass<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-    IBDL_CUDA(cudaFuncSetAttribute(k_rowifft_gather<T, OP, G_INTERP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-    IBDL_CUDA(cudaFuncSetAttribute(k_rowifft_gather<T, OP, G_GRID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-    attr_done = true;
-  }
   RowParams<T> rp = row_params<T>(g, in, out, stop, grid);
+  rp.idx = idx;
+  rp.vstride = vstride;
   ColParams<T> cp = col_params<T>(g, stop);
   const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
@@ -520,12 +561,20 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
 }
 
 template <typename T>
-static ibdl_status apply_t(Geometry* g, const double* Q, double* Y, cudaStream_t s, const int* stop, double* grid) {
+static ibdl_status apply_t(Geometry* g, const double* Q, double* Y, cudaStream_t s, const int* stop, double* grid,
+                           const int* idx = nullptr, int vstride = 0) {
   if (g->pde == IBDL_PDE_STOKES)
-    return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<T, OP_STOKES_AN>(g, Q, Y, s, stop, grid)
-                                             : run_op<T, OP_STOKES_SD>(g, Q, Y, s, stop, grid);
-  return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<T, OP_SCALAR_AN>(g, Q, Y, s, stop, grid)
-                                           : run_op<T, OP_SCALAR_SD>(g, Q, Y, s, stop, grid);
+    return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<T, OP_STOKES_AN>(g, Q, Y, s, stop, grid, idx, vstride)
+                                             : run_op<T, OP_STOKES_SD>(g, Q, Y, s, stop, grid, idx, vstride);
+  return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<T, OP_SCALAR_AN>(g, Q, Y, s, stop, grid, idx, vstride)
+                                           : run_op<T, OP_SCALAR_SD>(g, Q, Y, s, stop, grid, idx, vstride);
+}
+
+// Y = A Q with Q = V + (*idx)·nd and Y = V + (*idx + 1)·nd read on the device (Krylov basis)
+ibdl_status apply_2d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
+                             const int* stop) {
+  return precision == IBDL_FP32 ? apply_t<float>(g, V, V, s, stop, nullptr, idx, nd)
+                                : apply_t<double>(g, V, V, s, stop, nullptr, idx, nd);
 }
 
 ibdl_status apply_2d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s, const int* stop) {
@@ -549,15 +598,21 @@ ibdl_status adjoint_2d(Geometry* g, int precision, const double* W, double* Z, c
 // Band height R (rows per CTA, even) and kx columns per CTA C, per precision, within the
 // shared-memory limit for the widest field count this geometry uses.
 ibdl_status plan_2d(Geometry* g) {
+  static bool attrs = false;  // opt in to large dynamic shared memory once per kernel instance
+  if (!attrs) {
+    IBDL_TRY(set_attrs_all<double>());
+    IBDL_TRY(set_attrs_all<float>());
+    attrs = true;
+  }
   const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
   for (int pi = 0; pi < 2; ++pi) {
     const size_t cs = pi ? sizeof(float2) : sizeof(double2);
     int R = g->n >= 256 ? 2 : 2;
-    while (R > 2 && 2 * (size_t)nf * (R / 2) * g->n * cs > kSmemLimit) R /= 2;
-    if (2 * (size_t)nf * (R / 2) * g->n * cs > kSmemLimit) R = 0;
+    while (R > 2 && (2 * (size_t)nf * (R / 2) + 1) * g->n * cs > kSmemLimit) R /= 2;
+    if ((2 * (size_t)nf * (R / 2) + 1) * g->n * cs > kSmemLimit) R = 0;
     int C = 2;
-    while (C > 1 && 2 * (size_t)nf * C * g->n * cs > kSmemLimit) C /= 2;
-    if (2 * (size_t)nf * C * g->n * cs > kSmemLimit) C = 0;
+    while (C > 1 && (2 * (size_t)nf * C + 1) * g->n * cs > kSmemLimit) C /= 2;
+    if ((2 * (size_t)nf * C + 1) * g->n * cs > kSmemLimit) C = 0;
     if ((g->n / 2) % (C ? C : 1)) C = 1;
     g->rows_per_cta[pi] = R;
     g->cols_per_cta[pi] = C;

@@ -13,6 +13,9 @@ ibdl_status apply_3d(Geometry*, int, const double*, double*, cudaStream_t, const
 ibdl_status field_3d(Geometry*, const double*, double*, cudaStream_t) {
   return fail(IBDL_ERR_UNSUPPORTED, "3-D operator not available in this build");
 }
+ibdl_status apply_3d_indexed(Geometry*, int, double*, const int*, int, cudaStream_t, const int*) {
+  return fail(IBDL_ERR_UNSUPPORTED, "3-D operator not available in this build");
+}
 ibdl_status adjoint_3d(Geometry*, int, const double*, double*, cudaStream_t) {
   return fail(IBDL_ERR_UNSUPPORTED, "3-D operator not available in this build");
 }

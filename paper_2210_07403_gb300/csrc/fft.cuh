@@ -12,80 +12,111 @@ namespace ibdl {
 // Stage with current sub-transform length p and radix R: butterfly i ∈ [0, n/R) of every
 // sequence reads x[i + r·n/R] (r < R), multiplies input r by ω^{r·k} with k = i mod p and
 // ω = e^{∓2πi/(pR)}, takes the R-point DFT, and writes output t to y[(i − k)·R + k + t·p].
-// Radix-4 stages run while at least two factors of two remain, then one radix-2 stage.
+// Radix-8 stages run while at least three factors of two remain, then one radix-4 or radix-2.
 //
-// tw[j] = e^{−2πi j/n}; the inverse transform (INV) uses conjugates and is unnormalised.
-// Sequences are `nb` runs of n contiguous elements, sequence b starting at b·bstride.
-// Returns the buffer that holds the result (a or b). All threads of the block must call it.
+// tw[j] = e^{−2πi j/n} (the kernels stage it in shared memory); the inverse transform (INV)
+// uses conjugates and is unnormalised. Sequences are `nb` runs of n contiguous elements,
+// sequence b starting at b·bstride. Returns the buffer that holds the result (a or b). All
+// threads of the block must call it.
 // ------------------------------------------------------------------------------------------
+template <typename T, bool INV>
+__device__ __forceinline__ void dft2(cplx<T>* u) {
+  const cplx<T> t = u[0];
+  u[0] = cadd(t, u[1]);
+  u[1] = csub(t, u[1]);
+}
+
+// multiply by −i (forward) or +i (inverse)
+template <typename T, bool INV>
+__device__ __forceinline__ cplx<T> rot90(cplx<T> a) {
+  return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2, cplx<T>& a3) {
+  const cplx<T> t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
+  const cplx<T> t3 = rot90<T, INV>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a1 = cadd(t1, t3);
+  a2 = csub(t0, t2);
+  a3 = csub(t1, t3);
+}
+
+// 8-point DFT as two 4-point DFTs: X_{2k} = DFT4(u_r + u_{r+4}), X_{2k+1} = DFT4((u_r − u_{r+4}) ω₈^r)
+template <typename T, bool INV>
+__device__ __forceinline__ void dft8(cplx<T>* u) {
+  const T c = T(0.70710678118654752440);
+  cplx<T> a0 = cadd(u[0], u[4]), a1 = cadd(u[1], u[5]), a2 = cadd(u[2], u[6]), a3 = cadd(u[3], u[7]);
+  cplx<T> b0 = csub(u[0], u[4]), b1 = csub(u[1], u[5]), b2 = csub(u[2], u[6]), b3 = csub(u[3], u[7]);
+  b1 = INV ? mk((b1.x - b1.y) * c, (b1.x + b1.y) * c) : mk((b1.x + b1.y) * c, (b1.y - b1.x) * c);
+  b2 = rot90<T, INV>(b2);
+  b3 = INV ? mk(-(b3.x + b3.y) * c, (b3.x - b3.y) * c) : mk((b3.y - b3.x) * c, -(b3.x + b3.y) * c);
+  dft4<T, INV>(a0, a1, a2, a3);
+  dft4<T, INV>(b0, b1, b2, b3);
+  u[0] = a0;
+  u[1] = b0;
+  u[2] = a1;
+  u[3] = b1;
+  u[4] = a2;
+  u[5] = b2;
+  u[6] = a3;
+  u[7] = b3;
+}
+
+template <typename T, bool INV, int LR>
+__device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, int log2n,
+                                               int lp, int nb, int bstride, const cplx<T>* __restrict__ tw) {
+  constexpr int R = 1 << LR;
+  const int lq = log2n - LR;
+  const int q = 1 << lq;
+  const int p = 1 << lp;
+  const int total = nb << lq;
+  const int tws = 1 << (log2n - lp - LR);  // n / (pR)
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int bi = t >> lq, i = t & (q - 1), k = i & (p - 1);
+    const cplx<T>* x = src + bi * bstride;
+    cplx<T> u[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) u[r] = x[i + r * q];
+    if (k) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cplx<T> w = tw[r * k * tws];
+        if (INV) w.y = -w.y;
+        u[r] = cmul(u[r], w);
+      }
+    }
+    if (LR == 3)
+      dft8<T, INV>(u);
+    else if (LR == 2)
+      dft4<T, INV>(u[0], u[1], u[2], u[3]);
+    else
+      dft2<T, INV>(u);
+    cplx<T>* y = dst + bi * bstride;
+    const int j = ((i - k) << LR) + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) y[j + r * p] = u[r];
+  }
+}
+
 template <typename T, bool INV>
 __device__ cplx<T>* fft_stockham(cplx<T>* a, cplx<T>* b, int log2n, int nb, int bstride,
                                  const cplx<T>* __restrict__ tw) {
-  const int n = 1 << log2n;
-  int p = 1;
-  int lp = 0;  // log2 p
+  int lp = 0;  // log2 of the current sub-transform length
   int s = log2n;
   cplx<T>* src = a;
   cplx<T>* dst = b;
   while (s > 0) {
-    if (s >= 2) {
-      const int lq = log2n - 2;
-      const int q = 1 << lq;
-      const int total = nb << lq;
-      const int tws = n >> (lp + 2);  // n / (4p)
-      for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int bi = t >> lq;
-        const int i = t & (q - 1);
-        const int k = i & (p - 1);
-        const cplx<T>* x = src + bi * bstride;
-        cplx<T> u0 = x[i], u1 = x[i + q], u2 = x[i + 2 * q], u3 = x[i + 3 * q];
-        if (k) {
-          cplx<T> w1 = tw[k * tws], w2 = tw[2 * k * tws], w3 = tw[3 * k * tws];
-          if (INV) {
-            w1.y = -w1.y;
-            w2.y = -w2.y;
-            w3.y = -w3.y;
-          }
-          u1 = cmul(u1, w1);
-          u2 = cmul(u2, w2);
-          u3 = cmul(u3, w3);
-        }
-        const cplx<T> t0 = cadd(u0, u2), t1 = csub(u0, u2), t2 = cadd(u1, u3);
-        cplx<T> t3 = csub(u1, u3);
-        // forward: multiply (u1 − u3) by −i; inverse: by +i
-        t3 = INV ? mk(-t3.y, t3.x) : mk(t3.y, -t3.x);
-        cplx<T>* y = dst + bi * bstride;
-        const int j = ((i - k) << 2) + k;
-        y[j] = cadd(t0, t2);
-        y[j + p] = cadd(t1, t3);
-        y[j + 2 * p] = csub(t0, t2);
-        y[j + 3 * p] = csub(t1, t3);
-      }
-      p <<= 2;
+    if (s >= 3) {
+      stockham_stage<T, INV, 3>(src, dst, log2n, lp, nb, bstride, tw);
+      lp += 3;
+      s -= 3;
+    } else if (s == 2) {
+      stockham_stage<T, INV, 2>(src, dst, log2n, lp, nb, bstride, tw);
       lp += 2;
       s -= 2;
     } else {
-      const int lq = log2n - 1;
-      const int q = 1 << lq;
-      const int total = nb << lq;
-      const int tws = n >> (lp + 1);
-      for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int bi = t >> lq;
-        const int i = t & (q - 1);
-        const int k = i & (p - 1);
-        const cplx<T>* x = src + bi * bstride;
-        cplx<T> u0 = x[i], u1 = x[i + q];
-        if (k) {
-          cplx<T> w = tw[k * tws];
-          if (INV) w.y = -w.y;
-          u1 = cmul(u1, w);
-        }
-        cplx<T>* y = dst + bi * bstride;
-        const int j = ((i - k) << 1) + k;
-        y[j] = cadd(u0, u1);
-        y[j + p] = csub(u0, u1);
-      }
-      p <<= 1;
+      stockham_stage<T, INV, 1>(src, dst, log2n, lp, nb, bstride, tw);
       lp += 1;
       s -= 1;
     }
@@ -95,6 +126,12 @@ __device__ cplx<T>* fft_stockham(cplx<T>* a, cplx<T>* b, int log2n, int nb, int 
     dst = tmp;
   }
   return src;
+}
+
+// copy the n-entry twiddle table into shared memory (caller synchronises before use)
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cplx<T>* dst, const cplx<T>* __restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
 // ------------------------------------------------------------------------------------------

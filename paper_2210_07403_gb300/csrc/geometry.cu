@@ -177,6 +177,8 @@ static void free_geometry(Geometry* g) {
                   g->lap64, g->der64, g->lap32, g->der32, g->ubuf, g->tmp_m, g->V, g->gm, g->vec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int i = 0; i < 2; ++i)
+    if (g->cycle_exec[i]) cudaGraphExecDestroy(g->cycle_exec[i]);
   if (g->host_status) cudaFreeHost(g->host_status);
   if (g->ev) cudaEventDestroy(g->ev);
   if (g->ev_pool) {

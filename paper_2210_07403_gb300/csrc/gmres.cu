@@ -10,10 +10,15 @@
 //
 // Mixed precision: iterative refinement. Each sweep solves A₃₂ d = r with FP32 grid arithmetic
 // and the same FP64 Arnoldi/Hessenberg, then forms the FP64 residual r = U_b − A₆₄ Q.
+#include <cooperative_groups.h>
+
 #include <chrono>
 #include <cmath>
+#include <cstring>
 
 #include "ibdl_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ibdl {
 
@@ -24,7 +29,9 @@ struct GmresState {
   int stop;    // nonzero: every queued kernel returns at once
   int status;  // ST_*
   int k;       // Arnoldi steps completed in this cycle
-  int pad;
+  int kmax;    // steps allowed in this cycle (≤ restart length and the remaining budget)
+  int body_iters;  // loop bodies run by the captured cycle (a guard on the device-side loop)
+  int pad2;
   double res;      // |g_k|, the GMRES residual estimate
   double beta;     // ‖r0‖ of the cycle
   double target;   // absolute tolerance on the residual
@@ -34,7 +41,7 @@ struct GmresState {
 };
 
 struct HostStatus {
-  int stop, status, k, pad;
+  int stop, status, k, kmax, body_iters, pad2;
   double res, beta, target, rnorm;
 };
 
@@ -62,7 +69,7 @@ __device__ double block_sum(double v, double* red) {
 
 // start a cycle: V_0 = r/‖r‖, g = ‖r‖ e_1
 __global__ void __launch_bounds__(1024) k_gmres_start(GmresState* st, const double* __restrict__ r, double* V, int nd,
-                                                      double target) {
+                                                      double target, int kmax) {
   __shared__ double red[32];
   double s = 0;
   for (int i = threadIdx.x; i < nd; i += blockDim.x) s += r[i] * r[i];
@@ -75,6 +82,8 @@ __global__ void __launch_bounds__(1024) k_gmres_start(GmresState* st, const doub
     st->target = target;
     st->res = beta;
     st->k = 0;
+    st->kmax = kmax;
+    st->body_iters = 0;
     st->g[0] = beta;
     if (bad) {
       st->status = ST_NONFINITE;
@@ -154,6 +163,179 @@ __global__ void __launch_bounds__(1024) k_arnoldi(GmresState* st, double* V, int
   }
 }
 
+// One Arnoldi step on a cluster of ACL CTAs. CTA r owns the slice [r·slice, (r+1)·slice) of
+// the vectors; with STAGED it first copies its slice of V_0..V_j into shared memory (one round of
+// independent loads), so both Gram–Schmidt passes read the basis from shared memory. Partial dot
+// products and the norm are combined across the cluster through distributed shared memory.
+// Control flow is uniform over the cluster: the stop flag is read before the first cluster
+// barrier and only CTA 0 writes it, after that barrier.
+constexpr int ACL = 8;
+constexpr int ATH = 512;
+
+// In a captured cycle (cond != 0) j is read from st->k and the kernel sets the while-loop
+// condition on every path: 0 once the cycle has stopped, or after more loop bodies than the
+// cycle allows (a guard: the loop cannot run away), else 1.
+template <bool STAGED>
+__global__ void __cluster_dims__(ACL, 1, 1) __launch_bounds__(ATH)
+    k_arnoldi_cluster(GmresState* st, double* V, int j, int nd, int m, int slice, cudaGraphConditionalHandle cond) {
+  cg::cluster_group cluster = cg::this_cluster();
+  if (j < 0) j = st->k;
+  if (st->stop || j >= st->kmax || j >= m) {
+    if (cond && cluster.block_rank() == 0 && threadIdx.x == 0) {
+      st->stop = 1;
+      cudaGraphSetConditional(cond, 0);
+    }
+    return;
+  }
+  extern __shared__ double dsm[];
+  __shared__ double part[KMAX + 2];
+  __shared__ double h[KMAX + 2];
+  __shared__ double red[ATH / 32][KMAX + 2];
+  __shared__ double csl[KMAX], snl[KMAX];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rank = (int)cluster.block_rank();
+  const int lo = rank * slice;
+  const int cnt = nd - lo < slice ? (nd - lo > 0 ? nd - lo : 0) : slice;
+  double* ws = dsm;
+  double* Vs = dsm + slice;
+  double* w = V + (size_t)(j + 1) * nd + lo;
+  for (int e = tid; e < cnt; e += ATH) ws[e] = w[e];
+  if (STAGED) {
+    for (int t = tid; t < (j + 1) * cnt; t += ATH) {
+      const int i = t / cnt, e = t - i * cnt;
+      Vs[i * slice + e] = V[(size_t)i * nd + lo + e];
+    }
+  }
+  __syncthreads();
+  double hsum = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i <= j; ++i) {
+      double sacc = 0.0;
+      for (int e = tid; e < cnt; e += ATH)
+        sacc += (STAGED ? Vs[i * slice + e] : V[(size_t)i * nd + lo + e]) * ws[e];
+      sacc = warp_sum(sacc);
+      if (lane == 0) red[warp][i] = sacc;
+    }
+    __syncthreads();
+    if (tid <= j) {
+      double t = 0.0;
+      for (int w2 = 0; w2 < ATH / 32; ++w2) t += red[w2][tid];
+      part[tid] = t;
+    }
+    cluster.sync();
+    if (tid <= j) {
+      double t = 0.0;
+      for (int r = 0; r < ACL; ++r) t += cluster.map_shared_rank(part, r)[tid];
+      h[tid] = t;
+      hsum += t;
+    }
+    cluster.sync();  // every remote read of `part` is done before the next pass rewrites it
+    for (int e = tid; e < cnt; e += ATH) {
+      double a = ws[e];
+      for (int i = 0; i <= j; ++i) a -= h[i] * (STAGED ? Vs[i * slice + e] : V[(size_t)i * nd + lo + e]);
+      ws[e] = a;
+    }
+    __syncthreads();
+  }
+  double sq = 0.0;
+  for (int e = tid; e < cnt; e += ATH) sq += ws[e] * ws[e];
+  sq = warp_sum(sq);
+  if (lane == 0) red[warp][0] = sq;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w2 = 0; w2 < ATH / 32; ++w2) t += red[w2][0];
+    part[KMAX + 1] = t;
+  }
+  cluster.sync();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int r = 0; r < ACL; ++r) t += cluster.map_shared_rank(part, r)[KMAX + 1];
+    h[KMAX + 1] = t;
+  }
+  __syncthreads();
+  const double hn = sqrt(h[KMAX + 1]);
+  const double inv = hn > 0 ? 1.0 / hn : 0.0;
+  for (int e = tid; e < cnt; e += ATH) w[e] = ws[e] * inv;
+  if (rank == 0) {
+    if (tid < j) {
+      csl[tid] = st->cs[tid];
+      snl[tid] = st->sn[tid];
+    }
+    if (tid <= j) h[tid] = hsum;
+    __syncthreads();
+    if (tid == 0) {
+      double* hc = st->H + (size_t)j * (m + 1);
+      // earlier rotations act on rows i, i+1 ≤ j; row j+1 (= hn) meets only the new one
+      for (int i = 0; i < j; ++i) {
+        const double t = csl[i] * h[i] + snl[i] * h[i + 1];
+        h[i + 1] = -snl[i] * h[i] + csl[i] * h[i + 1];
+        h[i] = t;
+      }
+      const double a = h[j], b = hn;
+      const double r = hypot(a, b);
+      const double c = r > 0 ? a / r : 1.0, sn = r > 0 ? b / r : 0.0;
+      for (int i = 0; i < j; ++i) hc[i] = h[i];
+      hc[j] = r;
+      hc[j + 1] = 0.0;
+      st->cs[j] = c;
+      st->sn[j] = sn;
+      const double gj = st->g[j];
+      st->g[j + 1] = -sn * gj;
+      st->g[j] = c * gj;
+      const double res = fabs(sn * gj);
+      st->res = res;
+      st->k = j + 1;
+      if (!isfinite(res) || !isfinite(hn)) {
+        st->status = ST_NONFINITE;
+        st->stop = 1;
+      } else if (res <= st->target) {
+        st->status = ST_CONVERGED;
+        st->stop = 1;
+      } else if (hn == 0.0) {
+        st->status = ST_BREAKDOWN;
+        st->stop = 1;
+      } else if (j + 1 >= st->kmax) {
+        st->stop = 1;  // cycle full
+      }
+      st->body_iters += 1;
+      if (st->body_iters > st->kmax + 2) st->stop = 1;
+      if (cond) cudaGraphSetConditional(cond, st->stop ? 0u : 1u);
+    }
+  }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// x += V_{0..k-1} y with R y = g, many CTAs; each CTA solves the small triangular system in
+// shared memory and updates its own elements of x
+__global__ void __launch_bounds__(256) k_gmres_update_par(GmresState* st, const double* __restrict__ V, double* x,
+                                                          int nd, int m) {
+  __shared__ double Rm[KMAX * KMAX];
+  __shared__ double y[KMAX];
+  const int k = st->k;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int col = t / k, row = t - col * k;
+    Rm[row * KMAX + col] = row <= col ? st->H[(size_t)col * (m + 1) + row] : 0.0;
+  }
+  for (int t = threadIdx.x; t < k; t += blockDim.x) y[t] = st->g[t];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int l = i + 1; l < k; ++l) t -= Rm[i * KMAX + l] * y[l];
+      const double d = Rm[i * KMAX + i];
+      y[i] = d != 0.0 ? t / d : 0.0;
+    }
+  }
+  __syncthreads();
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < nd) {
+    double acc = x[idx];
+    for (int i = 0; i < k; ++i) acc += y[i] * V[(size_t)i * nd + idx];
+    x[idx] = acc;
+  }
+}
+
 // x += V_{0..k-1} y with R y = g (back substitution on the Givens-reduced Hessenberg)
 __global__ void __launch_bounds__(1024) k_gmres_update(GmresState* st, const double* __restrict__ V, double* x, int nd,
                                                        int m) {
@@ -216,6 +398,123 @@ struct CycleResult {
   double res;
 };
 
+static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, cudaGraphExec_t* out);
+
+static ibdl_status gmres_cycle_graph(Geometry* g, int prec, const double* r0, double* x, double target, int m,
+                                     int budget, cudaStream_t s, CycleResult* cr) {
+  const int pi = prec == IBDL_FP32 ? 1 : 0;
+  if (!g->cycle_exec[pi] || g->cycle_m[pi] != m) {
+    if (g->cycle_exec[pi]) cudaGraphExecDestroy(g->cycle_exec[pi]);
+    g->cycle_exec[pi] = nullptr;
+    IBDL_TRY(build_cycle_graph(g, prec, m, &g->cycle_exec[pi]));
+    g->cycle_m[pi] = m;
+  }
+  GmresState* st = reinterpret_cast<GmresState*>(g->gm);
+  HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
+  const int nd = (int)(g->ncomp * g->M);
+  const int steps = m < budget ? m : budget;
+  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, g->V, nd, target, steps);
+  IBDL_CUDA(cudaGetLastError());
+  IBDL_CUDA(cudaGraphLaunch(g->cycle_exec[pi], s));
+  k_gmres_update_par<<<(nd + 255) / 256, 256, 0, s>>>(st, g->V, x, nd, m);
+  IBDL_CUDA(cudaGetLastError());
+  IBDL_CUDA(cudaMemcpyAsync(&hs[0], st, sizeof(HostStatus), cudaMemcpyDeviceToHost, s));
+  IBDL_CUDA(cudaStreamSynchronize(s));
+  const HostStatus fin = hs[0];
+  const int bodies = fin.body_iters > 0 ? fin.body_iters : 1;
+  g->launches += 2 + 4 * (int64_t)bodies;
+  cr->its = fin.k;
+  cr->status = fin.status;
+  cr->res = fin.res;
+  return IBDL_OK;
+}
+
+struct ArnoldiCfg {
+  int slice;
+  bool staged;
+  size_t dyn;
+};
+
+// Arnoldi on one cluster: stage the basis slices in shared memory when (m + 2) slices fit
+static ibdl_status arnoldi_cfg(Geometry* g, int m, ArnoldiCfg* c) {
+  const int nd = (int)(g->ncomp * g->M);
+  c->slice = (nd + ACL - 1) / ACL;
+  const size_t staged_bytes = (size_t)(m + 2) * c->slice * sizeof(double);
+  c->staged = staged_bytes <= 200 * 1024;
+  c->dyn = c->staged ? staged_bytes : (size_t)c->slice * sizeof(double);
+  if (c->dyn > 200 * 1024) return fail(IBDL_ERR_UNSUPPORTED, "too many boundary unknowns for the Arnoldi kernel");
+  static bool attr_done = false;
+  if (!attr_done) {
+    IBDL_CUDA(cudaFuncSetAttribute(k_arnoldi_cluster<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    IBDL_CUDA(cudaFuncSetAttribute(k_arnoldi_cluster<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_done = true;
+  }
+  return IBDL_OK;
+}
+
+static void launch_arnoldi(const ArnoldiCfg& c, GmresState* st, double* V, int j, int nd, int m,
+                           cudaGraphConditionalHandle cond, cudaStream_t s) {
+  if (c.staged)
+    k_arnoldi_cluster<true><<<ACL, ATH, c.dyn, s>>>(st, V, j, nd, m, c.slice, cond);
+  else
+    k_arnoldi_cluster<false><<<ACL, ATH, c.dyn, s>>>(st, V, j, nd, m, c.slice, cond);
+}
+
+// A GMRES cycle as a CUDA graph: one conditional while node whose body is the operator
+// application on V_k (k read on the device) followed by the Arnoldi step, which sets the loop
+// condition. Built once per geometry, precision and restart length.
+static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, cudaGraphExec_t* out) {
+  *out = nullptr;
+  const int nd = (int)(g->ncomp * g->M);
+  GmresState* st = reinterpret_cast<GmresState*>(g->gm);
+  ArnoldiCfg c;
+  IBDL_TRY(arnoldi_cfg(g, m, &c));
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cs = nullptr;
+  IBDL_CUDA(cudaGraphCreate(&graph, 0));
+  ibdl_status ret = IBDL_OK;
+  bool capturing = false;
+  do {
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaGraphConditionalHandleCreate"); break; }
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaGraphAddNode(conditional)"); break; }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaStreamCreate"); break; }
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaStreamBeginCaptureToGraph"); break; }
+    capturing = true;
+    const int saved_timing = g->timing;
+    g->timing = 0;
+    ret = g->dim == 2 ? apply_2d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop)
+                      : apply_3d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop);
+    if (ret == IBDL_OK) launch_arnoldi(c, st, g->V, -1, nd, m, h, cs);
+    g->timing = saved_timing;
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    capturing = false;
+    if (ret != IBDL_OK) break;
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaStreamEndCapture"); break; }
+    e = cudaGraphInstantiate(out, graph, 0);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaGraphInstantiate"); *out = nullptr; break; }
+  } while (false);
+  if (capturing) {
+    cudaGraph_t captured = nullptr;
+    cudaStreamEndCapture(cs, &captured);
+  }
+  if (cs) cudaStreamDestroy(cs);
+  cudaGraphDestroy(graph);
+  cudaGetLastError();
+  return ret;
+}
+
 // One GMRES(m) cycle on right-hand side r0 from a zero correction, accumulating into x.
 static ibdl_status gmres_cycle(Geometry* g, int prec, const double* r0, double* x, double target, int m, int budget,
                                cudaStream_t s, CycleResult* cr) {
@@ -223,10 +522,14 @@ static ibdl_status gmres_cycle(Geometry* g, int prec, const double* r0, double* 
   HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
   const int nd = (int)(g->ncomp * g->M);
   double* V = g->V;
-  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, V, nd, target);
+  if (!g->timing) return gmres_cycle_graph(g, prec, r0, x, target, m, budget, s, cr);
+  // host-driven loop (used while stage timing records an event around every kernel)
+  const int steps = m < budget ? m : budget;
+  ArnoldiCfg acfg;
+  IBDL_TRY(arnoldi_cfg(g, m, &acfg));
+  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, V, nd, target, steps);
   g->launches += 1;
   IBDL_CUDA(cudaGetLastError());
-  const int steps = m < budget ? m : budget;
   cudaEvent_t evs[2] = {g->ev, g->ev};
   // the geometry owns one event; a second one is created per call for the double buffer
   cudaEvent_t ev2;
@@ -239,7 +542,7 @@ static ibdl_status gmres_cycle(Geometry* g, int prec, const double* r0, double* 
     err = apply_any(g, prec, V + (size_t)j * nd, V + (size_t)(j + 1) * nd, s, &st->stop);
     if (err != IBDL_OK) break;
     if (g->timing) timing_mark(g, s, -1);
-    k_arnoldi<<<1, 1024, 0, s>>>(st, V, j, nd, m);
+    launch_arnoldi(acfg, st, V, j, nd, m, 0, s);
     if (g->timing) timing_mark(g, s, IBDL_STAGE_ARNOLDI);
     g->launches += 1;
     if (cudaGetLastError() != cudaSuccess) {
@@ -265,7 +568,7 @@ static ibdl_status gmres_cycle(Geometry* g, int prec, const double* r0, double* 
   if (err != IBDL_OK) return err;
   HostStatus fin;
   IBDL_CUDA(cudaMemcpy(&fin, st, sizeof(HostStatus), cudaMemcpyDeviceToHost));
-  k_gmres_update<<<1, 1024, 0, s>>>(st, V, x, nd, m);
+  k_gmres_update_par<<<(nd + 255) / 256, 256, 0, s>>>(st, V, x, nd, m);
   g->launches += 1;
   IBDL_CUDA(cudaGetLastError());
   cr->its = fin.k;

@@ -120,6 +120,10 @@ struct Geometry {
   void* host_status;   // pinned
   cudaEvent_t ev;
 
+  // captured GMRES cycles (CUDA graph with a device-side while loop), per precision
+  cudaGraphExec_t cycle_exec[2];
+  int cycle_m[2];
+
   // counters and optional stage timing (events around every kernel)
   int64_t launches;
   int timing;
@@ -148,6 +152,11 @@ ibdl_status plan_2d(Geometry* g);
 ibdl_status plan_3d(Geometry* g);
 ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solve_opts* o,
                        ibdl_solve_info* info, cudaStream_t s);
+
+ibdl_status apply_2d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
+                             const int* stop);
+ibdl_status apply_3d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
+                             const int* stop);
 
 inline ibdl_status apply_any(Geometry* g, int precision, const double* Q, double* Y,
                              cudaStream_t s, const int* stop_flag) {

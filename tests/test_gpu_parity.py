@@ -176,6 +176,38 @@ def test_solve_stokes_full_size_fp64_and_mixed():
     assert _rel(y, O.apply(og, q)) < 1e-12
 
 
+def test_solve_host_driven_loop_matches_graph():
+    """With stage timing on, GMRES runs from the host (one launch per kernel, events around
+    each); the result must match the captured-graph cycle, and the stage record must count the
+    kernels of every application."""
+    p = I.star_stokes(128, 200)
+    g = _geom(p)
+    ub = torch.from_numpy(p.Ub.reshape(-1)).cuda()
+    for prec in ("fp64", "mixed"):
+        Qg, infog, _ = g.solve(ub, rtol=1e-10, precision=prec)
+        g.set_stage_timing(True)
+        g.stage_times()
+        Qh, infoh, _ = g.solve(ub, rtol=1e-10, precision=prec)
+        st = g.stage_times()
+        g.set_stage_timing(False)
+        assert infoh["iterations"] == infog["iterations"]
+        assert _rel(Qh.cpu().numpy(), Qg.cpu().numpy()) < 1e-12
+        assert st["arnoldi"][1] >= infoh["iterations"]
+    ref = O.solve(O.geometry_from_problem(p), p.Ub, 1e-10)
+    assert _rel(Qg.cpu().numpy(), ref.x) < 1e-8
+
+
+def test_solve_restart_cycles():
+    """A restart length shorter than the iteration count: several graph cycles, same answer."""
+    p = I.star_stokes(128, 200)
+    g = _geom(p)
+    ub = torch.from_numpy(p.Ub.reshape(-1)).cuda()
+    Q, info, _ = g.solve(ub, rtol=1e-10, restart=6, maxit=400)
+    assert info["sweeps"] > 1
+    ref = O.solve(O.geometry_from_problem(p), p.Ub, 1e-12)
+    assert _rel(Q.cpu().numpy(), ref.x) < 1e-8
+
+
 def test_solve_host_buffers():
     p = I.circle_laplace(64, 100)
     g = _geom(p)
