@@ -124,8 +124,10 @@ __global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
   const int seqs = NIN * half;
   cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufA = tws + n;
-  cplx<T>* bufB = bufA + (size_t)seqs * n;
-  T* acc = reinterpret_cast<T*>(bufA);  // field f, local row lr, column x at ((f·half + lr/2)·n + x)·2 + (lr & 1)
+  cplx<T>* bufB = bufA + padded((size_t)seqs * n);
+  // accumulation view: field f, local row lr, column x → complex element e = (f·half + lr/2)·n + x
+  // of the padded buffer, real part for even lr and imaginary part for odd lr
+  T* acc = reinterpret_cast<T*>(bufA);
   const int r0 = blockIdx.x * R;
   const double* pin;
   double* pout;
@@ -134,90 +136,72 @@ __global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
   // jump term: out = ½·in (the gather kernel adds S*u afterwards)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NC * M; i += gridDim.x * blockDim.x)
     pout[i] = 0.5 * pin[i];
-  for (int i = threadIdx.x; i < seqs * n * 2; i += blockDim.x) acc[i] = T(0);
+  for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
   load_twiddles(tws, p.tw, n);
   __syncthreads();
 
+  // one thread per (point, stencil node): 16 work items per point whose stencil meets the band
   const PointRanges pr = band_points(p.cell_start, n, r0, R);
-  for (int t = threadIdx.x; t < pr.cnt; t += blockDim.x) {
-    const int s = pr.at(t);
+  for (int t = threadIdx.x; t < pr.cnt * 16; t += blockDim.x) {
+    const int s = pr.at(t >> 4);
+    const int ay = (t >> 2) & 3, ax = t & 3;
+    const int by = p.base[M + s];
+    const int row = (by + ay) & (n - 1);
+    const int lr = (row - r0) & (n - 1);
+    if (lr >= R) continue;
     const int i = p.perm[s];
-    const int bx = p.base[s], by = p.base[M + s];
-    T px[4], py[4], dx[4], dy[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      px[a] = p.phi[(0 * 4 + a) * M + s];
-      py[a] = p.phi[(1 * 4 + a) * M + s];
-      dx[a] = p.dphi[(0 * 4 + a) * M + s];
-      dy[a] = p.dphi[(1 * 4 + a) * M + s];
-    }
+    const int col = (p.base[s] + ax) & (n - 1);
+    const T px = p.phi[(0 * 4 + ax) * M + s], py = p.phi[(1 * 4 + ay) * M + s];
     const T ws = p.wscale[s];
     const T nx = p.nrm[s], ny = p.nrm[M + s];
-    // per-point source strengths
-    T c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-    if (OP == OP_SCALAR_AN || OP == OP_SCALAR_SD) {
+    const int e = (lr >> 1) * n + col;  // field 0; field f adds f·half·n
+    const int odd = lr & 1;
+    const T pp = px * py;
+    if (OP == OP_SCALAR_AN) {
       const T q = T(pin[i]) * ws;
-      c0 = q * nx;
-      c1 = q * ny;
+      const T ddx = p.dphi[(0 * 4 + ax) * M + s] * py, ddy = px * p.dphi[(1 * 4 + ay) * M + s];
+      atomicAdd(acc + 2 * pidx(e) + odd, q * (nx * ddx + ny * ddy));
+    } else if (OP == OP_SCALAR_SD) {
+      const T q = T(pin[i]) * ws * pp;
+      atomicAdd(acc + 2 * pidx(e) + odd, q * nx);
+      atomicAdd(acc + 2 * pidx(e + half * n) + odd, q * ny);
     } else if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
       const T qx = T(pin[i]), qy = T(pin[M + i]);
-      c0 = ws * (qx * nx + qy * ny);      // Q·n
-      c1 = ws * (T(2) * qx * nx);         // A_xx
-      c2 = ws * (T(2) * qy * ny);         // A_yy
-      c3 = ws * (qx * ny + qy * nx);      // A_xy
-    } else {
-      c0 = T(pin[i]) * ws;                // plain spread of W
-    }
-#pragma unroll
-    for (int ay = 0; ay < 4; ++ay) {
-      const int row = (by + ay) & (n - 1);
-      const int lr = (row - r0) & (n - 1);
-      if (lr >= R) continue;
-      T* rowp = acc + (size_t)(lr >> 1) * n * 2 + (lr & 1);
-      const size_t fstride = (size_t)half * n * 2;
-#pragma unroll
-      for (int ax = 0; ax < 4; ++ax) {
-        const int col = (bx + ax) & (n - 1);
-        T* cell = rowp + (size_t)col * 2;
-        const T pp = px[ax] * py[ay];
-        if (OP == OP_SCALAR_AN) {
-          atomicAdd(cell, c0 * dx[ax] * py[ay] + c1 * px[ax] * dy[ay]);
-        } else if (OP == OP_SCALAR_SD) {
-          atomicAdd(cell, c0 * pp);
-          atomicAdd(cell + fstride, c1 * pp);
-        } else if (OP == OP_STOKES_AN) {
-          const T ddx = dx[ax] * py[ay], ddy = px[ax] * dy[ay];
-          atomicAdd(cell, c0 * pp);
-          atomicAdd(cell + fstride, c1 * ddx + c3 * ddy);      // g_x = ∂_x S(A_xx) + ∂_y S(A_xy)
-          atomicAdd(cell + 2 * fstride, c3 * ddx + c2 * ddy);  // g_y = ∂_x S(A_xy) + ∂_y S(A_yy)
-        } else if (OP == OP_STOKES_SD) {
-          atomicAdd(cell, c0 * pp);
-          atomicAdd(cell + fstride, c1 * pp);
-          atomicAdd(cell + 2 * fstride, c2 * pp);
-          atomicAdd(cell + 3 * fstride, c3 * pp);
-        } else {
-          atomicAdd(cell, c0 * pp);
-        }
+      const T c0 = ws * (qx * nx + qy * ny);  // Q·n
+      const T c1 = ws * (T(2) * qx * nx);     // A_xx
+      const T c2 = ws * (T(2) * qy * ny);     // A_yy
+      const T c3 = ws * (qx * ny + qy * nx);  // A_xy
+      atomicAdd(acc + 2 * pidx(e) + odd, c0 * pp);
+      if (OP == OP_STOKES_AN) {
+        const T ddx = p.dphi[(0 * 4 + ax) * M + s] * py, ddy = px * p.dphi[(1 * 4 + ay) * M + s];
+        atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * ddx + c3 * ddy);      // g_x = ∂_x S(A_xx) + ∂_y S(A_xy)
+        atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c3 * ddx + c2 * ddy);  // g_y = ∂_x S(A_xy) + ∂_y S(A_yy)
+      } else {
+        atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * pp);
+        atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c2 * pp);
+        atomicAdd(acc + 2 * pidx(e + 3 * half * n) + odd, c3 * pp);
       }
+    } else {
+      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * ws * pp);  // plain spread of W
     }
   }
   __syncthreads();
 
-  const cplx<T>* res = fft_stockham<T, false>(bufA, bufB, p.log2n, seqs, n, tws);
+  const cplx<T>* res = fft_run<T, false>(bufA, bufB, p.log2n, seqs, tws);
 
   // unpack Z = FFT(a + i b) into A = FFT(a), B = FFT(b), k = 0..n/2, packed format
   const int nh = n >> 1, lnh = p.log2n - 1;
   for (int t = threadIdx.x; t < seqs * nh; t += blockDim.x) {
     const int sq = t >> lnh, k = t & (nh - 1);
     const int f = sq / half, j = sq - f * half;
-    const cplx<T>* Z = res + (size_t)sq * n;
+    const int zb = sq * n;
     cplx<T> A, B;
     if (k == 0) {
-      const cplx<T> z0 = Z[0], zh = Z[nh];
+      const cplx<T> z0 = res[pidx(zb)], zh = res[pidx(zb + nh)];
       A = mk(z0.x, zh.x);
       B = mk(z0.y, zh.y);
     } else {
-      const cplx<T> zk = Z[k], zc = Z[n - k];
+      const cplx<T> zk = res[pidx(zb + k)], zc = res[pidx(zb + n - k)];
       A = mk(T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y));
       B = mk(T(0.5) * (zk.y + zc.y), T(0.5) * (zc.x - zk.x));
     }
@@ -231,10 +215,10 @@ __global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
 // Fourier symbols: NIN transformed fields in → NOUT out at wavenumber indices (kx, ky)
 // ------------------------------------------------------------------------------------------
 template <typename T, int OP>
-__device__ __forceinline__ void apply_symbol(const ColParams<T>& p, int kx, int ky, const cplx<T>* in,
-                                             cplx<T>* out) {
-  const T lap = p.lap1[kx] + p.lap1[ky];
-  const T dkx = p.der1[kx], dky = p.der1[ky];
+__device__ __forceinline__ void apply_symbol(const ColParams<T>& p, const T* lap1, const T* der1, int kx, int ky,
+                                             const cplx<T>* in, cplx<T>* out) {
+  const T lap = lap1[kx] + lap1[ky];
+  const T dkx = der1[kx], dky = der1[ky];
   if (OP == OP_SCALAR_AN || OP == OP_SCALAR_SD || OP == OP_ADJ_AN || OP == OP_ADJ_SD) {
     // −L⁻¹ ↦ 1/(|k|² + λ), zero mode dropped when λ = 0 (Δ₀⁻¹)
     const T den = lap + p.lam;
@@ -272,6 +256,18 @@ __device__ __forceinline__ void apply_symbol(const ColParams<T>& p, int kx, int 
 // ------------------------------------------------------------------------------------------
 // kernel 2: FFT along y, symbol, inverse FFT along y, for C kx columns per CTA
 // ------------------------------------------------------------------------------------------
+// element m of column sequence bi = f·C + c, straight from / to the packed half spectra
+template <typename T>
+struct ColumnIO {
+  cplx<T>* spec;
+  int n, nh, k0, lc, C;
+  __device__ __forceinline__ size_t at(int bi, int m) const {
+    return ((size_t)(bi >> lc) * n + m) * nh + k0 + (bi & (C - 1));
+  }
+  __device__ __forceinline__ cplx<T> load(int bi, int m) const { return spec[at(bi, m)]; }
+  __device__ __forceinline__ void store(int bi, int m, cplx<T> v) const { spec[at(bi, m)] = v; }
+};
+
 template <typename T, int OP>
 __global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
   if (p.stop && *p.stop) return;
@@ -279,21 +275,22 @@ __global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
   constexpr int NOUT = Traits<OP>::NOUT;
   constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = p.n, C = p.C, nh = n >> 1, lc = p.lc, lnc = p.log2n + p.lc;
+  const int n = p.n, C = p.C, nh = n >> 1;
   cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufA = tws + n;
-  cplx<T>* bufB = bufA + (size_t)NMAX * C * n;
+  cplx<T>* bufB = bufA + padded((size_t)NMAX * C * n);
+  T* lap1 = reinterpret_cast<T*>(bufB + padded((size_t)NMAX * C * n));
+  T* der1 = lap1 + n;
   const int k0 = blockIdx.x * C;
-
-  for (int t = threadIdx.x; t < (NIN << lnc); t += blockDim.x) {
-    const int f = t >> lnc;
-    const int rem = t & ((1 << lnc) - 1);
-    const int row = rem >> lc, c = rem & (C - 1);
-    bufA[(size_t)((f << lc) + c) * n + row] = p.spec[((size_t)f * n + row) * nh + k0 + c];
-  }
   load_twiddles(tws, p.tw, n);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    lap1[i] = p.lap1[i];
+    der1[i] = p.der1[i];
+  }
   __syncthreads();
-  cplx<T>* res = fft_stockham<T, false>(bufA, bufB, p.log2n, NIN * C, n, tws);
+  const ColumnIO<T> cio{p.spec, n, nh, k0, p.lc, C};
+  // forward transform along y: the first stage reads the half spectra directly
+  cplx<T>* res = fft_run<T, false>(bufA, bufB, p.log2n, NIN * C, tws, cio, NoIO());
   cplx<T>* other = res == bufA ? bufB : bufA;
 
   for (int t = threadIdx.x; t < (C << p.log2n); t += blockDim.x) {
@@ -302,18 +299,18 @@ __global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
     cplx<T> in[NIN], out[NOUT];
     if (kx != 0) {
 #pragma unroll
-      for (int f = 0; f < NIN; ++f) in[f] = res[(size_t)(f * C + c) * n + ky];
-      apply_symbol<T, OP>(p, kx, ky, in, out);
+      for (int f = 0; f < NIN; ++f) in[f] = res[pidx((f * C + c) * n + ky)];
+      apply_symbol<T, OP>(p, lap1, der1, kx, ky, in, out);
 #pragma unroll
-      for (int f = 0; f < NOUT; ++f) res[(size_t)(f * C + c) * n + ky] = out[f];
+      for (int f = 0; f < NOUT; ++f) res[pidx((f * C + c) * n + ky)] = out[f];
     } else if (ky <= nh) {
       // packed kx = 0 | kx = n/2 column: P = Â + i B̂ with Â, B̂ Hermitian in ky
       const int j = ky, jp = (n - ky) & (n - 1);
       cplx<T> Aj[NIN], Ajp[NIN], Bj[NIN], Bjp[NIN];
 #pragma unroll
       for (int f = 0; f < NIN; ++f) {
-        const cplx<T> P = res[(size_t)(f * C + c) * n + j];
-        const cplx<T> Pp = res[(size_t)(f * C + c) * n + jp];
+        const cplx<T> P = res[pidx((f * C + c) * n + j)];
+        const cplx<T> Pp = res[pidx((f * C + c) * n + jp)];
         // Â(j) = (P(j) + conj P(−j))/2, B̂(j) = −i (P(j) − conj P(−j))/2
         Aj[f] = mk(T(0.5) * (P.x + Pp.x), T(0.5) * (P.y - Pp.y));
         Bj[f] = mk(T(0.5) * (P.y + Pp.y), T(0.5) * (Pp.x - P.x));
@@ -321,70 +318,72 @@ __global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
         Bjp[f] = mk(T(0.5) * (Pp.y + P.y), T(0.5) * (P.x - Pp.x));
       }
       cplx<T> oA[NOUT], oB[NOUT], oAp[NOUT], oBp[NOUT];
-      apply_symbol<T, OP>(p, 0, j, Aj, oA);
-      apply_symbol<T, OP>(p, nh, j, Bj, oB);
-      apply_symbol<T, OP>(p, 0, jp, Ajp, oAp);
-      apply_symbol<T, OP>(p, nh, jp, Bjp, oBp);
+      apply_symbol<T, OP>(p, lap1, der1, 0, j, Aj, oA);
+      apply_symbol<T, OP>(p, lap1, der1, nh, j, Bj, oB);
+      apply_symbol<T, OP>(p, lap1, der1, 0, jp, Ajp, oAp);
+      apply_symbol<T, OP>(p, lap1, der1, nh, jp, Bjp, oBp);
 #pragma unroll
       for (int f = 0; f < NOUT; ++f) {
-        res[(size_t)(f * C + c) * n + j] = cadd(oA[f], cmuli(oB[f]));
-        if (jp != j) res[(size_t)(f * C + c) * n + jp] = cadd(oAp[f], cmuli(oBp[f]));
+        res[pidx((f * C + c) * n + j)] = cadd(oA[f], cmuli(oB[f]));
+        if (jp != j) res[pidx((f * C + c) * n + jp)] = cadd(oAp[f], cmuli(oBp[f]));
       }
     }
   }
   __syncthreads();
-  const cplx<T>* out = fft_stockham<T, true>(res, other, p.log2n, NOUT * C, n, tws);
-  for (int t = threadIdx.x; t < (NOUT << lnc); t += blockDim.x) {
-    const int f = t >> lnc;
-    const int rem = t & ((1 << lnc) - 1);
-    const int row = rem >> lc, c = rem & (C - 1);
-    p.spec[((size_t)f * n + row) * nh + k0 + c] = out[(size_t)((f << lc) + c) * n + row];
-  }
+  // inverse transform along y: the last stage writes the half spectra directly
+  fft_run<T, true>(res, other, p.log2n, NOUT * C, tws, NoIO(), cio);
 }
 
 // ------------------------------------------------------------------------------------------
 // kernel 3: inverse FFT along x, then interpolation (or write the grid)
 // ------------------------------------------------------------------------------------------
+// Z_m = A_m + i B_m (m = 0..n−1) for the row pair (r0 + 2j, r0 + 2j + 1) of field f, sequence
+// sq = f·half + j, rebuilt on the fly from the packed half spectra (A_{n−k} = conj A_k).
+template <typename T>
+struct RowZLoad {
+  const cplx<T>* spec;
+  int n, nh, r0, half;
+  __device__ __forceinline__ cplx<T> load(int sq, int m) const {
+    const int f = sq / half, j = sq - f * half;
+    const size_t ra = ((size_t)f * n + r0 + 2 * j) * nh;
+    const size_t rb = ra + nh;
+    if (m == 0 || m == nh) {
+      const cplx<T> A = spec[ra], B = spec[rb];
+      return m == 0 ? mk(A.x, B.x) : mk(A.y, B.y);
+    }
+    if (m < nh) {
+      const cplx<T> A = spec[ra + m], B = spec[rb + m];
+      return mk(A.x - B.y, A.y + B.x);
+    }
+    const cplx<T> A = spec[ra + (n - m)], B = spec[rb + (n - m)];
+    return mk(A.x + B.y, B.x - A.y);
+  }
+};
+
 template <typename T, int OP, int GMODE>
 __global__ void __launch_bounds__(kThreads) k_rowifft_gather(RowParams<T> p) {
   if (p.stop && *p.stop) return;
   constexpr int NOUT = Traits<OP>::NOUT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = p.n, R = p.R, half = R >> 1, M = p.M, nh = n >> 1, lnh = p.log2n - 1;
+  const int n = p.n, R = p.R, half = R >> 1, M = p.M, nh = n >> 1;
   const int seqs = NOUT * half;
   cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufA = tws + n;
-  cplx<T>* bufB = bufA + (size_t)seqs * n;
+  cplx<T>* bufB = bufA + padded((size_t)seqs * n);
   const int r0 = blockIdx.x * R;
   load_twiddles(tws, p.tw, n);
-
-  // rebuild Z = A + i B over all k from the packed half spectra of rows (r0+2j, r0+2j+1)
-  for (int t = threadIdx.x; t < seqs * nh; t += blockDim.x) {
-    const int sq = t >> lnh, k = t & (nh - 1);
-    const int f = sq / half, j = sq - f * half;
-    const int row = r0 + 2 * j;
-    const cplx<T> A = p.spec[((size_t)f * n + row) * nh + k];
-    const cplx<T> B = p.spec[((size_t)f * n + row + 1) * nh + k];
-    cplx<T>* Z = bufA + (size_t)sq * n;
-    if (k == 0) {
-      Z[0] = mk(A.x, B.x);
-      Z[nh] = mk(A.y, B.y);
-    } else {
-      Z[k] = mk(A.x - B.y, A.y + B.x);
-      Z[n - k] = mk(A.x + B.y, B.x - A.y);
-    }
-  }
   __syncthreads();
-  const cplx<T>* res = fft_stockham<T, true>(bufA, bufB, p.log2n, seqs, n, tws);
-  const T* u = reinterpret_cast<const T*>(res);  // field f, row lr, col x at ((f·half + lr/2)·n + x)·2 + (lr&1)
-  const size_t fstride = (size_t)half * n * 2;
+  const RowZLoad<T> zl{p.spec, n, nh, r0, half};
+  const cplx<T>* res = fft_run<T, true>(bufA, bufB, p.log2n, seqs, tws, zl, NoIO());
+  // real values: field f, local row lr, column x at element e = (f·half + lr/2)·n + x, part lr & 1
+  const T* u = reinterpret_cast<const T*>(res);
 
   if (GMODE == G_GRID) {
     for (int t = threadIdx.x; t < NOUT * R * n; t += blockDim.x) {
       const int f = t / (R * n);
       const int rem = t - f * R * n;
       const int lr = rem / n, x = rem - lr * n;
-      p.grid[((size_t)f * n + r0 + lr) * n + x] = double(u[f * fstride + ((size_t)(lr >> 1) * n + x) * 2 + (lr & 1)]);
+      p.grid[((size_t)f * n + r0 + lr) * n + x] = double(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)]);
     }
     return;
   }
@@ -392,45 +391,34 @@ __global__ void __launch_bounds__(kThreads) k_rowifft_gather(RowParams<T> p) {
   const double* pin;
   double* pout;
   resolve_io(p, pin, pout);
+  // one thread per (point, stencil row in the band): the row's partial sum is added to Y
   const PointRanges pr = band_points(p.cell_start, n, r0, R);
-  for (int t = threadIdx.x; t < pr.cnt; t += blockDim.x) {
-    const int s = pr.at(t);
+  for (int t = threadIdx.x; t < pr.cnt * 4; t += blockDim.x) {
+    const int s = pr.at(t >> 2);
+    const int ay = t & 3;
+    const int row = (p.base[M + s] + ay) & (n - 1);
+    const int lr = (row - r0) & (n - 1);
+    if (lr >= R) continue;
     const int i = p.perm[s];
-    const int bx = p.base[s], by = p.base[M + s];
-    T px[4], py[4], dx[4], dy[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      px[a] = p.phi[(0 * 4 + a) * M + s];
-      py[a] = p.phi[(1 * 4 + a) * M + s];
-      if (OP == OP_ADJ_AN) {
-        dx[a] = p.dphi[(0 * 4 + a) * M + s];
-        dy[a] = p.dphi[(1 * 4 + a) * M + s];
-      }
-    }
+    const int bx = p.base[s];
+    const T py = p.phi[(1 * 4 + ay) * M + s];
+    const T dy = OP == OP_ADJ_AN ? p.dphi[(1 * 4 + ay) * M + s] : T(0);
+    const int eb = (lr >> 1) * n, odd = lr & 1;
     T acc0 = 0, acc1 = 0;
-    bool touched = false;
 #pragma unroll
-    for (int ay = 0; ay < 4; ++ay) {
-      const int row = (by + ay) & (n - 1);
-      const int lr = (row - r0) & (n - 1);
-      if (lr >= R) continue;
-      touched = true;
-      const T* rowp = u + (size_t)(lr >> 1) * n * 2 + (lr & 1);
-#pragma unroll
-      for (int ax = 0; ax < 4; ++ax) {
-        const int col = (bx + ax) & (n - 1);
-        const T v0 = rowp[(size_t)col * 2];
-        if (OP == OP_ADJ_AN) {
-          acc0 += v0 * dx[ax] * py[ay];
-          acc1 += v0 * px[ax] * dy[ay];
-        } else {
-          const T pp = px[ax] * py[ay];
-          acc0 += v0 * pp;
-          if (NOUT == 2) acc1 += rowp[fstride + (size_t)col * 2] * pp;
-        }
+    for (int ax = 0; ax < 4; ++ax) {
+      const int col = (bx + ax) & (n - 1);
+      const T px = p.phi[(0 * 4 + ax) * M + s];
+      const T v0 = u[2 * pidx(eb + col) + odd];
+      if (OP == OP_ADJ_AN) {
+        acc0 += v0 * p.dphi[(0 * 4 + ax) * M + s] * py;
+        acc1 += v0 * px * dy;
+      } else {
+        const T pp = px * py;
+        acc0 += v0 * pp;
+        if (NOUT == 2) acc1 += u[2 * pidx(eb + half * n + col) + odd] * pp;
       }
     }
-    if (!touched) continue;
     if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
       atomicAdd(pout + i, double(acc0));
       atomicAdd(pout + M + i, double(acc1));
@@ -494,18 +482,19 @@ static ColParams<T> col_params(Geometry* g, const int* stop) {
   return cp;
 }
 
+// shared memory: twiddles (n) + two padded FFT buffers (+ the two symbol tables in the column pass)
 template <typename T, int OP>
 static size_t smem_spread(const Geometry* g, int R) {
-  return (2 * (size_t)Traits<OP>::NIN * (R / 2) + 1) * g->n * sizeof(cplx<T>);
+  return (g->n + 2 * padded((size_t)Traits<OP>::NIN * (R / 2) * g->n)) * sizeof(cplx<T>);
 }
 template <typename T, int OP>
 static size_t smem_gather(const Geometry* g, int R) {
-  return (2 * (size_t)Traits<OP>::NOUT * (R / 2) + 1) * g->n * sizeof(cplx<T>);
+  return (g->n + 2 * padded((size_t)Traits<OP>::NOUT * (R / 2) * g->n)) * sizeof(cplx<T>);
 }
 template <typename T, int OP>
 static size_t smem_col(const Geometry* g, int C) {
   const int nmax = Traits<OP>::NIN > Traits<OP>::NOUT ? Traits<OP>::NIN : Traits<OP>::NOUT;
-  return (2 * (size_t)nmax * C + 1) * g->n * sizeof(cplx<T>);
+  return (g->n + 2 * padded((size_t)nmax * C * g->n)) * sizeof(cplx<T>) + 2 * g->n * sizeof(T);
 }
 
 static const size_t kSmemLimit = 227 * 1024;
@@ -608,11 +597,13 @@ ibdl_status plan_2d(Geometry* g) {
   for (int pi = 0; pi < 2; ++pi) {
     const size_t cs = pi ? sizeof(float2) : sizeof(double2);
     int R = g->n >= 256 ? 2 : 2;
-    while (R > 2 && (2 * (size_t)nf * (R / 2) + 1) * g->n * cs > kSmemLimit) R /= 2;
-    if ((2 * (size_t)nf * (R / 2) + 1) * g->n * cs > kSmemLimit) R = 0;
+    auto row_bytes = [&](int r) { return (g->n + 2 * padded((size_t)nf * (r / 2) * g->n)) * cs; };
+    auto col_bytes = [&](int c) { return (g->n + 2 * padded((size_t)nf * c * g->n)) * cs + 2 * g->n * cs / 2; };
+    while (R > 2 && row_bytes(R) > kSmemLimit) R /= 2;
+    if (row_bytes(R) > kSmemLimit) R = 0;
     int C = 2;
-    while (C > 1 && (2 * (size_t)nf * C + 1) * g->n * cs > kSmemLimit) C /= 2;
-    if ((2 * (size_t)nf * C + 1) * g->n * cs > kSmemLimit) C = 0;
+    while (C > 1 && col_bytes(C) > kSmemLimit) C /= 2;
+    if (col_bytes(C) > kSmemLimit) C = 0;
     if ((g->n / 2) % (C ? C : 1)) C = 1;
     g->rows_per_cta[pi] = R;
     g->cols_per_cta[pi] = C;

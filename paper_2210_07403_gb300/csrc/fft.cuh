@@ -1,6 +1,8 @@
 // Shared-memory Stockham FFT and the regularised-delta kernels used by the IBDL kernels.
 #pragma once
 
+#include <type_traits>
+
 #include "ibdl_internal.cuh"
 
 namespace ibdl {
@@ -63,9 +65,26 @@ __device__ __forceinline__ void dft8(cplx<T>* u) {
   u[7] = b3;
 }
 
-template <typename T, bool INV, int LR>
-__device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, int log2n,
-                                               int lp, int nb, int bstride, const cplx<T>* __restrict__ tw) {
+// Shared-memory FFT buffers are padded with one element after every eight, which keeps the
+// radix-8 stride-8 writes of the first stages free of bank conflicts for 8- and 16-byte elements.
+__device__ __forceinline__ int pidx(int x) { return x + (x >> 3); }
+__host__ __device__ constexpr size_t padded(size_t x) { return x + (x >> 3); }
+
+// element m of sequence bi in a padded shared-memory buffer of sequences of length 2^log2n
+template <typename T>
+struct SmemIO {
+  cplx<T>* buf;
+  int log2n;
+  __device__ __forceinline__ cplx<T> load(int bi, int m) const { return buf[pidx((bi << log2n) + m)]; }
+  __device__ __forceinline__ void store(int bi, int m, cplx<T> v) const { buf[pidx((bi << log2n) + m)] = v; }
+};
+
+struct NoIO {};
+
+// One Stockham stage reading through `ld` and writing through `st`.
+template <typename T, bool INV, int LR, class LD, class ST>
+__device__ __forceinline__ void fft_stage(const LD& ld, const ST& st, int log2n, int lp, int nb,
+                                          const cplx<T>* __restrict__ tw) {
   constexpr int R = 1 << LR;
   const int lq = log2n - LR;
   const int q = 1 << lq;
@@ -74,10 +93,9 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ src, 
   const int tws = 1 << (log2n - lp - LR);  // n / (pR)
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int bi = t >> lq, i = t & (q - 1), k = i & (p - 1);
-    const cplx<T>* x = src + bi * bstride;
     cplx<T> u[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) u[r] = x[i + r * q];
+    for (int r = 0; r < R; ++r) u[r] = ld.load(bi, i + r * q);
     if (k) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -92,38 +110,67 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ src, 
       dft4<T, INV>(u[0], u[1], u[2], u[3]);
     else
       dft2<T, INV>(u);
-    cplx<T>* y = dst + bi * bstride;
     const int j = ((i - k) << LR) + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) y[j + r * p] = u[r];
+    for (int r = 0; r < R; ++r) st.store(bi, j + r * p, u[r]);
   }
 }
 
-template <typename T, bool INV>
-__device__ cplx<T>* fft_stockham(cplx<T>* a, cplx<T>* b, int log2n, int nb, int bstride,
-                                 const cplx<T>* __restrict__ tw) {
-  int lp = 0;  // log2 of the current sub-transform length
+template <typename T, bool INV, int LR, class FL, class LS>
+__device__ __forceinline__ void fft_stage_dispatch(bool first, bool last, const SmemIO<T>& in, const SmemIO<T>& out,
+                                                   const FL& fl, const LS& ls, int log2n, int lp, int nb,
+                                                   const cplx<T>* tw) {
+  constexpr bool HF = !std::is_same<FL, NoIO>::value, HL = !std::is_same<LS, NoIO>::value;
+  if constexpr (HF && HL) {
+    if (first && last) {
+      fft_stage<T, INV, LR>(fl, ls, log2n, lp, nb, tw);
+      return;
+    }
+  }
+  if constexpr (HF) {
+    if (first) {
+      fft_stage<T, INV, LR>(fl, out, log2n, lp, nb, tw);
+      return;
+    }
+  }
+  if constexpr (HL) {
+    if (last) {
+      fft_stage<T, INV, LR>(in, ls, log2n, lp, nb, tw);
+      return;
+    }
+  }
+  fft_stage<T, INV, LR>(in, out, log2n, lp, nb, tw);
+}
+
+// All stages of `nb` transforms of length 2^log2n. Stage 0 reads through `fl` (or from the padded
+// buffer a), the last stage writes through `ls` (or to its padded target buffer); in between the
+// stages ping-pong between a and b. Returns the padded buffer the last stage wrote (meaningful
+// when `ls` is NoIO). All threads of the block must call it.
+template <typename T, bool INV, class FL = NoIO, class LS = NoIO>
+__device__ cplx<T>* fft_run(cplx<T>* a, cplx<T>* b, int log2n, int nb, const cplx<T>* __restrict__ tw,
+                            const FL& fl = FL(), const LS& ls = LS()) {
+  int lp = 0;
   int s = log2n;
   cplx<T>* src = a;
   cplx<T>* dst = b;
+  bool first = true;
   while (s > 0) {
-    if (s >= 3) {
-      stockham_stage<T, INV, 3>(src, dst, log2n, lp, nb, bstride, tw);
-      lp += 3;
-      s -= 3;
-    } else if (s == 2) {
-      stockham_stage<T, INV, 2>(src, dst, log2n, lp, nb, bstride, tw);
-      lp += 2;
-      s -= 2;
-    } else {
-      stockham_stage<T, INV, 1>(src, dst, log2n, lp, nb, bstride, tw);
-      lp += 1;
-      s -= 1;
-    }
+    const int lr = s >= 3 ? 3 : s;
+    const bool last = s == lr;
+    const SmemIO<T> in{src, log2n}, out{dst, log2n};
+    if (lr == 3)
+      fft_stage_dispatch<T, INV, 3>(first, last, in, out, fl, ls, log2n, lp, nb, tw);
+    else if (lr == 2)
+      fft_stage_dispatch<T, INV, 2>(first, last, in, out, fl, ls, log2n, lp, nb, tw);
+    else
+      fft_stage_dispatch<T, INV, 1>(first, last, in, out, fl, ls, log2n, lp, nb, tw);
     __syncthreads();
     cplx<T>* tmp = src;
     src = dst;
     dst = tmp;
+    lp += lr;
+    s -= lr;
+    first = false;
   }
   return src;
 }

@@ -1,12 +1,15 @@
 // GMRES for A Q = U_b (Sec. 5.3.2: the Schur operator is not symmetric) on the device.
 //
-// Arnoldi runs in one CTA per iteration: classical Gram–Schmidt applied twice (CGS2) against
-// the basis in FP64, the new Hessenberg column is reduced by the stored Givens rotations, and
-// the residual estimate |g_{k}| is compared with the target on the device. When the target is
-// met (or the cycle is full, or a non-finite value appears) the CTA raises a stop flag that
-// every kernel of the following iterations reads first, so the host can queue iteration j+1
-// before it has looked at iteration j's status: one host wait per iteration, overlapped with
-// the next iteration's GPU work.
+// Arnoldi runs on one 8-CTA cluster per iteration: classical Gram–Schmidt applied twice (CGS2)
+// against the basis in FP64, the new Hessenberg column is reduced by the stored Givens
+// rotations, and the residual estimate |g_{k}| is compared with the target on the device. When
+// the target is met (or the cycle is full, or a non-finite value appears) the step raises a stop
+// flag that every kernel of the following iterations reads first.
+//
+// A restart cycle is one CUDA graph: a conditional while node whose body is one operator
+// application and one Arnoldi step; the Arnoldi step sets the loop condition, so the host waits
+// once per cycle. With stage timing on, the cycle is instead driven from the host (one launch
+// per kernel, the host queuing iteration j+1 before it reads iteration j's status).
 //
 // Mixed precision: iterative refinement. Each sweep solves A₃₂ d = r with FP32 grid arithmetic
 // and the same FP64 Arnoldi/Hessenberg, then forms the FP64 residual r = U_b − A₆₄ Q.
@@ -98,85 +101,23 @@ __global__ void __launch_bounds__(1024) k_gmres_start(GmresState* st, const doub
   }
 }
 
-// one Arnoldi step j: w = V_{j+1} (already A V_j) is orthogonalised against V_0..V_j by CGS2
-__global__ void __launch_bounds__(1024) k_arnoldi(GmresState* st, double* V, int j, int nd, int m) {
-  if (st->stop) return;
-  __shared__ double hp[KMAX + 1], hsum[KMAX + 1], red[32];
-  double* w = V + (size_t)(j + 1) * nd;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x <= (unsigned)j) hsum[threadIdx.x] = 0.0;
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int i = warp; i <= j; i += nw) {
-      const double* v = V + (size_t)i * nd;
-      double s = 0;
-      for (int k = lane; k < nd; k += 32) s += v[k] * w[k];
-      s = warp_sum(s);
-      if (lane == 0) hp[i] = s;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < nd; k += blockDim.x) {
-      double acc = w[k];
-      for (int i = 0; i <= j; ++i) acc -= hp[i] * V[(size_t)i * nd + k];
-      w[k] = acc;
-    }
-    if (threadIdx.x <= (unsigned)j) hsum[threadIdx.x] += hp[threadIdx.x];
-    __syncthreads();
-  }
-  double s = 0;
-  for (int k = threadIdx.x; k < nd; k += blockDim.x) s += w[k] * w[k];
-  const double hn = sqrt(block_sum(s, red));
-  const double inv = hn > 0 ? 1.0 / hn : 0.0;
-  for (int k = threadIdx.x; k < nd; k += blockDim.x) w[k] *= inv;
-  if (threadIdx.x == 0) {
-    double* h = st->H + (size_t)j * (m + 1);
-    for (int i = 0; i <= j; ++i) h[i] = hsum[i];
-    h[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-      const double t = st->cs[i] * h[i] + st->sn[i] * h[i + 1];
-      h[i + 1] = -st->sn[i] * h[i] + st->cs[i] * h[i + 1];
-      h[i] = t;
-    }
-    const double a = h[j], b = h[j + 1];
-    const double r = hypot(a, b);
-    const double c = r > 0 ? a / r : 1.0, sn = r > 0 ? b / r : 0.0;
-    h[j] = r;
-    h[j + 1] = 0.0;
-    st->cs[j] = c;
-    st->sn[j] = sn;
-    st->g[j + 1] = -sn * st->g[j];
-    st->g[j] = c * st->g[j];
-    const double res = fabs(st->g[j + 1]);
-    st->res = res;
-    st->k = j + 1;
-    if (!isfinite(res) || !isfinite(hn)) {
-      st->status = ST_NONFINITE;
-      st->stop = 1;
-    } else if (res <= st->target) {
-      st->status = ST_CONVERGED;
-      st->stop = 1;
-    } else if (hn == 0.0) {
-      st->status = ST_BREAKDOWN;  // invariant Krylov space: the least-squares solution is exact
-      st->stop = 1;
-    } else if (j + 1 >= m) {
-      st->stop = 1;  // cycle full
-    }
-  }
-}
-
-// One Arnoldi step on a cluster of ACL CTAs. CTA r owns the slice [r·slice, (r+1)·slice) of
-// the vectors; with STAGED it first copies its slice of V_0..V_j into shared memory (one round of
-// independent loads), so both Gram–Schmidt passes read the basis from shared memory. Partial dot
-// products and the norm are combined across the cluster through distributed shared memory.
+// One Arnoldi step on a cluster of CL CTAs (16 where the device allows that cluster size, else
+// 8). CTA r owns the slice [r·slice, (r+1)·slice) of the vectors; with STAGED it first copies its
+// slice of V_0..V_j into shared memory (one round of independent loads), so both Gram–Schmidt
+// passes read the basis from shared memory. Warp w forms the partial dot products of basis
+// vectors w, w + 16, …; the partial sums of the cluster are combined through distributed shared
+// memory (two buffers, one per pass, so a pass never overwrites what another CTA still reads).
+// The norm of the new vector comes with the second pass: ‖w₂‖² = ‖w₁‖² − Σ h₂,ᵢ², exact because
+// w₂ = w₁ − V h₂ with V orthonormal and accurate because h₂ only holds rounding-level
+// components after the first pass. Three cluster barriers per step.
 // Control flow is uniform over the cluster: the stop flag is read before the first cluster
-// barrier and only CTA 0 writes it, after that barrier.
-constexpr int ACL = 8;
+// barrier and only CTA 0 writes it, after that barrier. In a captured cycle (cond != 0) j is read
+// from st->k and the kernel sets the while-loop condition on every path: 0 once the cycle has
+// stopped, or after more loop bodies than the cycle allows (a guard), else 1.
 constexpr int ATH = 512;
 
-// In a captured cycle (cond != 0) j is read from st->k and the kernel sets the while-loop
-// condition on every path: 0 once the cycle has stopped, or after more loop bodies than the
-// cycle allows (a guard: the loop cannot run away), else 1.
-template <bool STAGED>
-__global__ void __cluster_dims__(ACL, 1, 1) __launch_bounds__(ATH)
+template <bool STAGED, int CL>
+__global__ void __launch_bounds__(ATH)
     k_arnoldi_cluster(GmresState* st, double* V, int j, int nd, int m, int slice, cudaGraphConditionalHandle cond) {
   cg::cluster_group cluster = cg::this_cluster();
   if (j < 0) j = st->k;
@@ -188,9 +129,9 @@ __global__ void __cluster_dims__(ACL, 1, 1) __launch_bounds__(ATH)
     return;
   }
   extern __shared__ double dsm[];
-  __shared__ double part[KMAX + 2];
+  __shared__ double part1[KMAX + 2], part2[KMAX + 2];
   __shared__ double h[KMAX + 2];
-  __shared__ double red[ATH / 32][KMAX + 2];
+  __shared__ double red[ATH / 32];
   __shared__ double csl[KMAX], snl[KMAX];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rank = (int)cluster.block_rank();
@@ -207,54 +148,64 @@ __global__ void __cluster_dims__(ACL, 1, 1) __launch_bounds__(ATH)
     }
   }
   __syncthreads();
-  double hsum = 0.0;
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int i = 0; i <= j; ++i) {
-      double sacc = 0.0;
-      for (int e = tid; e < cnt; e += ATH)
-        sacc += (STAGED ? Vs[i * slice + e] : V[(size_t)i * nd + lo + e]) * ws[e];
-      sacc = warp_sum(sacc);
-      if (lane == 0) red[warp][i] = sacc;
-    }
-    __syncthreads();
-    if (tid <= j) {
-      double t = 0.0;
-      for (int w2 = 0; w2 < ATH / 32; ++w2) t += red[w2][tid];
-      part[tid] = t;
-    }
-    cluster.sync();
-    if (tid <= j) {
-      double t = 0.0;
-      for (int r = 0; r < ACL; ++r) t += cluster.map_shared_rank(part, r)[tid];
-      h[tid] = t;
-      hsum += t;
-    }
-    cluster.sync();  // every remote read of `part` is done before the next pass rewrites it
-    for (int e = tid; e < cnt; e += ATH) {
-      double a = ws[e];
-      for (int i = 0; i <= j; ++i) a -= h[i] * (STAGED ? Vs[i * slice + e] : V[(size_t)i * nd + lo + e]);
-      ws[e] = a;
-    }
-    __syncthreads();
-  }
-  double sq = 0.0;
-  for (int e = tid; e < cnt; e += ATH) sq += ws[e] * ws[e];
-  sq = warp_sum(sq);
-  if (lane == 0) red[warp][0] = sq;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w2 = 0; w2 < ATH / 32; ++w2) t += red[w2][0];
-    part[KMAX + 1] = t;
+  auto vat = [&](int i, int e) -> double { return STAGED ? Vs[i * slice + e] : V[(size_t)i * nd + lo + e]; };
+
+  // pass 1: h₁ = Vᵀ w, w₁ = w − V h₁
+  for (int i = warp; i <= j; i += ATH / 32) {
+    double sacc = 0.0;
+    for (int e = lane; e < cnt; e += 32) sacc += vat(i, e) * ws[e];
+    sacc = warp_sum(sacc);
+    if (lane == 0) part1[i] = sacc;
   }
   cluster.sync();
-  if (tid == 0) {
+  double hsum = 0.0;
+  if (tid <= j) {
     double t = 0.0;
-    for (int r = 0; r < ACL; ++r) t += cluster.map_shared_rank(part, r)[KMAX + 1];
-    h[KMAX + 1] = t;
+    for (int r = 0; r < CL; ++r) t += cluster.map_shared_rank(part1, r)[tid];
+    h[tid] = t;
+    hsum = t;
   }
   __syncthreads();
-  const double hn = sqrt(h[KMAX + 1]);
+  for (int e = tid; e < cnt; e += ATH) {
+    double a = ws[e];
+    for (int i = 0; i <= j; ++i) a -= h[i] * vat(i, e);
+    ws[e] = a;
+  }
+  __syncthreads();
+
+  // pass 2: h₂ = Vᵀ w₁ and ‖w₁‖² in one reduction (slot j+1), w₂ = w₁ − V h₂
+  for (int i = warp; i <= j + 1; i += ATH / 32) {
+    double sacc = 0.0;
+    if (i <= j) {
+      for (int e = lane; e < cnt; e += 32) sacc += vat(i, e) * ws[e];
+    } else {
+      for (int e = lane; e < cnt; e += 32) sacc += ws[e] * ws[e];
+    }
+    sacc = warp_sum(sacc);
+    if (lane == 0) part2[i] = sacc;
+  }
+  cluster.sync();
+  if (tid <= j + 1) {
+    double t = 0.0;
+    for (int r = 0; r < CL; ++r) t += cluster.map_shared_rank(part2, r)[tid];
+    h[tid] = t;
+    if (tid <= j) hsum += t;
+  }
+  __syncthreads();
+  for (int e = tid; e < cnt; e += ATH) {
+    double a = ws[e];
+    for (int i = 0; i <= j; ++i) a -= h[i] * vat(i, e);
+    ws[e] = a;
+  }
+  if (warp == 0) {
+    double q = 0.0;
+    for (int i = lane; i <= j; i += 32) q += h[i] * h[i];
+    q = warp_sum(q);
+    if (lane == 0) red[0] = q;
+  }
+  __syncthreads();
+  const double hn2 = h[j + 1] - red[0];
+  const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
   const double inv = hn > 0 ? 1.0 / hn : 0.0;
   for (int e = tid; e < cnt; e += ATH) w[e] = ws[e] * inv;
   if (rank == 0) {
@@ -262,6 +213,7 @@ __global__ void __cluster_dims__(ACL, 1, 1) __launch_bounds__(ATH)
       csl[tid] = st->cs[tid];
       snl[tid] = st->sn[tid];
     }
+    __syncthreads();
     if (tid <= j) h[tid] = hsum;
     __syncthreads();
     if (tid == 0) {
@@ -330,27 +282,6 @@ __global__ void __launch_bounds__(256) k_gmres_update_par(GmresState* st, const 
   __syncthreads();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < nd) {
-    double acc = x[idx];
-    for (int i = 0; i < k; ++i) acc += y[i] * V[(size_t)i * nd + idx];
-    x[idx] = acc;
-  }
-}
-
-// x += V_{0..k-1} y with R y = g (back substitution on the Givens-reduced Hessenberg)
-__global__ void __launch_bounds__(1024) k_gmres_update(GmresState* st, const double* __restrict__ V, double* x, int nd,
-                                                       int m) {
-  __shared__ double y[KMAX];
-  const int k = st->k;
-  if (threadIdx.x == 0) {
-    for (int i = k - 1; i >= 0; --i) {
-      double t = st->g[i];
-      for (int l = i + 1; l < k; ++l) t -= st->H[(size_t)l * (m + 1) + i] * y[l];
-      const double d = st->H[(size_t)i * (m + 1) + i];
-      y[i] = d != 0.0 ? t / d : 0.0;
-    }
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < nd; idx += blockDim.x) {
     double acc = x[idx];
     for (int i = 0; i < k; ++i) acc += y[i] * V[(size_t)i * nd + idx];
     x[idx] = acc;
@@ -430,34 +361,82 @@ static ibdl_status gmres_cycle_graph(Geometry* g, int prec, const double* r0, do
 }
 
 struct ArnoldiCfg {
+  int cl;  // CTAs per cluster (16 or 8)
   int slice;
   bool staged;
   size_t dyn;
 };
 
-// Arnoldi on one cluster: stage the basis slices in shared memory when (m + 2) slices fit
+template <bool STAGED, int CL>
+static cudaError_t arnoldi_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(k_arnoldi_cluster<STAGED, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess && CL > 8)
+    e = cudaFuncSetAttribute(k_arnoldi_cluster<STAGED, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+// Cluster size: 16 when a 16-CTA cluster of this kernel fits on the device, else 8. The basis
+// slices are staged in shared memory when (m + 2) slices fit.
 static ibdl_status arnoldi_cfg(Geometry* g, int m, ArnoldiCfg* c) {
+  static int cl_choice = 0;
+  if (!cl_choice) {
+    IBDL_CUDA((arnoldi_attrs<true, 8>()));
+    IBDL_CUDA((arnoldi_attrs<false, 8>()));
+    cl_choice = 8;
+    if (arnoldi_attrs<true, 16>() == cudaSuccess && arnoldi_attrs<false, 16>() == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(ATH);
+      cfg.dynamicSmemBytes = 200 * 1024;
+      cudaLaunchAttribute at;
+      at.id = cudaLaunchAttributeClusterDimension;
+      at.val.clusterDim.x = 16;
+      at.val.clusterDim.y = 1;
+      at.val.clusterDim.z = 1;
+      cfg.attrs = &at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)k_arnoldi_cluster<true, 16>, &cfg) == cudaSuccess &&
+          nclusters >= 1)
+        cl_choice = 16;
+    }
+    cudaGetLastError();
+  }
   const int nd = (int)(g->ncomp * g->M);
-  c->slice = (nd + ACL - 1) / ACL;
+  c->cl = cl_choice;
+  c->slice = (nd + c->cl - 1) / c->cl;
   const size_t staged_bytes = (size_t)(m + 2) * c->slice * sizeof(double);
   c->staged = staged_bytes <= 200 * 1024;
   c->dyn = c->staged ? staged_bytes : (size_t)c->slice * sizeof(double);
   if (c->dyn > 200 * 1024) return fail(IBDL_ERR_UNSUPPORTED, "too many boundary unknowns for the Arnoldi kernel");
-  static bool attr_done = false;
-  if (!attr_done) {
-    IBDL_CUDA(cudaFuncSetAttribute(k_arnoldi_cluster<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    IBDL_CUDA(cudaFuncSetAttribute(k_arnoldi_cluster<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_done = true;
-  }
   return IBDL_OK;
 }
 
-static void launch_arnoldi(const ArnoldiCfg& c, GmresState* st, double* V, int j, int nd, int m,
-                           cudaGraphConditionalHandle cond, cudaStream_t s) {
-  if (c.staged)
-    k_arnoldi_cluster<true><<<ACL, ATH, c.dyn, s>>>(st, V, j, nd, m, c.slice, cond);
-  else
-    k_arnoldi_cluster<false><<<ACL, ATH, c.dyn, s>>>(st, V, j, nd, m, c.slice, cond);
+template <bool STAGED, int CL>
+static cudaError_t launch_arnoldi_t(const ArnoldiCfg& c, GmresState* st, double* V, int j, int nd, int m,
+                                    cudaGraphConditionalHandle cond, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(ATH);
+  cfg.dynamicSmemBytes = c.dyn;
+  cfg.stream = s;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = CL;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_arnoldi_cluster<STAGED, CL>, st, V, j, nd, m, c.slice, cond);
+}
+
+static cudaError_t launch_arnoldi(const ArnoldiCfg& c, GmresState* st, double* V, int j, int nd, int m,
+                                  cudaGraphConditionalHandle cond, cudaStream_t s) {
+  if (c.cl == 16)
+    return c.staged ? launch_arnoldi_t<true, 16>(c, st, V, j, nd, m, cond, s)
+                    : launch_arnoldi_t<false, 16>(c, st, V, j, nd, m, cond, s);
+  return c.staged ? launch_arnoldi_t<true, 8>(c, st, V, j, nd, m, cond, s)
+                  : launch_arnoldi_t<false, 8>(c, st, V, j, nd, m, cond, s);
 }
 
 // A GMRES cycle as a CUDA graph: one conditional while node whose body is the operator
@@ -495,7 +474,10 @@ static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, cudaGraphExec
     g->timing = 0;
     ret = g->dim == 2 ? apply_2d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop)
                       : apply_3d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop);
-    if (ret == IBDL_OK) launch_arnoldi(c, st, g->V, -1, nd, m, h, cs);
+    if (ret == IBDL_OK) {
+      const cudaError_t le = launch_arnoldi(c, st, g->V, -1, nd, m, h, cs);
+      if (le != cudaSuccess) ret = cuda_fail(le, "Arnoldi launch");
+    }
     g->timing = saved_timing;
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(cs, &captured);
@@ -542,7 +524,10 @@ static ibdl_status gmres_cycle(Geometry* g, int prec, const double* r0, double* 
     err = apply_any(g, prec, V + (size_t)j * nd, V + (size_t)(j + 1) * nd, s, &st->stop);
     if (err != IBDL_OK) break;
     if (g->timing) timing_mark(g, s, -1);
-    launch_arnoldi(acfg, st, V, j, nd, m, 0, s);
+    if (launch_arnoldi(acfg, st, V, j, nd, m, 0, s) != cudaSuccess) {
+      err = fail(IBDL_ERR_CUDA, "Arnoldi launch failed");
+      break;
+    }
     if (g->timing) timing_mark(g, s, IBDL_STAGE_ARNOLDI);
     g->launches += 1;
     if (cudaGetLastError() != cudaSuccess) {

@@ -191,7 +191,11 @@ def test_solve_host_driven_loop_matches_graph():
         st = g.stage_times()
         g.set_stage_timing(False)
         assert infoh["iterations"] == infog["iterations"]
-        assert _rel(Qh.cpu().numpy(), Qg.cpu().numpy()) < 1e-12
+        # FP32 applications sum shared-memory atomics in a run-dependent order (~1e-7 relative
+        # per application); two mixed solves each reach a residual ≤ 1e-10, so they agree to
+        # κ(A)·1e-10 with κ(A) = O(10). FP64 applications differ at rounding level only.
+        tol = 1e-12 if prec == "fp64" else 1e-9
+        assert _rel(Qh.cpu().numpy(), Qg.cpu().numpy()) < tol
         assert st["arnoldi"][1] >= infoh["iterations"]
     ref = O.solve(O.geometry_from_problem(p), p.Ub, 1e-10)
     assert _rel(Qg.cpu().numpy(), ref.x) < 1e-8
