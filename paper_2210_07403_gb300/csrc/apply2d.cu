@@ -15,6 +15,7 @@
 // holding (A_0, A_{n/2}), both real. Along y, the kx = 0 and kx = n/2 columns are therefore one
 // complex column a + i b with a, b real columns; the column pass separates them by Hermitian
 // symmetry before the symbol and repacks after it.
+#include <cstdlib>
 #include <type_traits>
 
 #include "fft.cuh"
@@ -43,7 +44,7 @@ struct Traits<OP_ADJ_SD> { static constexpr int NIN = 1, NOUT = 2, C = 1; };    
 
 enum { G_INTERP = 0, G_GRID = 1 };
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 
 template <typename T>
 struct RowParams {
@@ -535,14 +536,15 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   ColParams<T> cp = col_params<T>(g, stop);
   const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
-  k_spread_rowfft<T, OP><<<g->n / R, kThreads, s1, s>>>(rp);
+  const int nt = g->threads ? g->threads : 256;
+  k_spread_rowfft<T, OP><<<g->n / R, nt, s1, s>>>(rp);
   if (g->timing) timing_mark(g, s, st0);
-  k_colpass<T, OP><<<(g->n / 2) / C, kThreads, s2, s>>>(cp);
+  k_colpass<T, OP><<<(g->n / 2) / C, nt, s2, s>>>(cp);
   if (g->timing) timing_mark(g, s, st0 + 1);
   if (grid)
-    k_rowifft_gather<T, OP, G_GRID><<<g->n / R, kThreads, s3, s>>>(rp);
+    k_rowifft_gather<T, OP, G_GRID><<<g->n / R, nt, s3, s>>>(rp);
   else
-    k_rowifft_gather<T, OP, G_INTERP><<<g->n / R, kThreads, s3, s>>>(rp);
+    k_rowifft_gather<T, OP, G_INTERP><<<g->n / R, nt, s3, s>>>(rp);
   if (g->timing) timing_mark(g, s, st0 + 2);
   g->launches += 3;
   IBDL_CUDA(cudaGetLastError());
@@ -605,8 +607,22 @@ ibdl_status plan_2d(Geometry* g) {
     while (C > 1 && col_bytes(C) > kSmemLimit) C /= 2;
     if (col_bytes(C) > kSmemLimit) C = 0;
     if ((g->n / 2) % (C ? C : 1)) C = 1;
+    // launch-shape overrides for tuning experiments (IBDL_PLAN_R, IBDL_PLAN_C, IBDL_THREADS)
+    if (const char* e = getenv("IBDL_PLAN_R")) {
+      const int v = atoi(e);
+      if (v >= 2 && v <= g->n && (v & (v - 1)) == 0 && row_bytes(v) <= kSmemLimit) R = v;
+    }
+    if (const char* e = getenv("IBDL_PLAN_C")) {
+      const int v = atoi(e);
+      if (v >= 1 && v <= g->n / 2 && (v & (v - 1)) == 0 && col_bytes(v) <= kSmemLimit) C = v;
+    }
     g->rows_per_cta[pi] = R;
     g->cols_per_cta[pi] = C;
+  }
+  g->threads = 0;
+  if (const char* e = getenv("IBDL_THREADS")) {
+    const int v = atoi(e);
+    if (v >= 32 && v <= kThreads && v % 32 == 0) g->threads = v;
   }
   if (g->rows_per_cta[0] == 0 && g->rows_per_cta[1] == 0)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT");

@@ -111,6 +111,7 @@ struct Geometry {
   int rows_per_cta[2];   // band height R for the row kernels, per precision (0 = fp64, 1 = fp32)
   int cols_per_cta[2];   // kx columns per CTA in the column kernels
   size_t smem_row[2], smem_col[2], smem_row_inv[2];
+  int threads;           // threads per CTA of the 2-D kernels (0: the default)
 
   // GMRES workspace (allocated lazily, sized for `krylov_m`)
   int krylov_m;
