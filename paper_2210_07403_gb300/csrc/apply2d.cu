@@ -536,7 +536,7 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   ColParams<T> cp = col_params<T>(g, stop);
   const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
-  const int nt = g->threads ? g->threads : 256;
+  const int nt = g->threads ? g->threads : kThreads;
   k_spread_rowfft<T, OP><<<g->n / R, nt, s1, s>>>(rp);
   if (g->timing) timing_mark(g, s, st0);
   k_colpass<T, OP><<<(g->n / 2) / C, nt, s2, s>>>(cp);
@@ -603,14 +603,15 @@ ibdl_status plan_2d(Geometry* g) {
     auto col_bytes = [&](int c) { return (g->n + 2 * padded((size_t)nf * c * g->n)) * cs + 2 * g->n * cs / 2; };
     while (R > 2 && row_bytes(R) > kSmemLimit) R /= 2;
     if (row_bytes(R) > kSmemLimit) R = 0;
-    int C = 2;
+    int C = 1;
     while (C > 1 && col_bytes(C) > kSmemLimit) C /= 2;
     if (col_bytes(C) > kSmemLimit) C = 0;
     if ((g->n / 2) % (C ? C : 1)) C = 1;
     // launch-shape overrides for tuning experiments (IBDL_PLAN_R, IBDL_PLAN_C, IBDL_THREADS)
     if (const char* e = getenv("IBDL_PLAN_R")) {
       const int v = atoi(e);
-      if (v >= 2 && v <= g->n && (v & (v - 1)) == 0 && row_bytes(v) <= kSmemLimit) R = v;
+      // R ≤ n/2 keeps the wrapped band rows [r0 − 3, r0 + R) distinct (no point counted twice)
+      if (v >= 2 && v <= g->n / 2 && (v & (v - 1)) == 0 && row_bytes(v) <= kSmemLimit) R = v;
     }
     if (const char* e = getenv("IBDL_PLAN_C")) {
       const int v = atoi(e);

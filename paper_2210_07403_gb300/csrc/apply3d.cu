@@ -1,23 +1,635 @@
-// Three-dimensional IBDL operator (not yet built in this revision: calls report UNSUPPORTED).
-#include "ibdl_internal.cuh"
+// Three-dimensional IBDL operator (scalar PDE): A Q = S* u + ½Q, u = −L⁻¹ S̃ Q (Sec. 5.3.2; the
+// method's formulation needs no change in 3-D, Sec. 1 and Sec. 7: area weights replace arclength
+// weights and δ_h is the tensor product of three 4-point kernels).
+//
+// Five kernels per application, each owning a disjoint part of the grid:
+//   k3_spread_rowfft   band of R y-rows at one z: spread (shared-memory atomics), FFT along x of
+//                      row pairs packed as a + ib, packed half spectrum (slot 0 = (A_0, A_{n/2}))
+//   k3_colpass<dir>    C kx columns at one z: FFT along y (forward or inverse), no symbol
+//   k3_zpass           C kx columns at the y-frequencies ky and −ky: FFT along z, Fourier symbol,
+//                      inverse FFT along z. The packed kx = 0 | kx = n/2 column holds P = Â + iB̂
+//                      where Â, B̂ are Hermitian in (ky, kz); separating them needs P(−ky, −kz),
+//                      which is why a CTA owns both ky and −ky.
+//   k3_colpass<inv>    inverse FFT along y
+//   k3_rowifft_gather  band of R y-rows: inverse FFT along x, interpolation into Y (set to ½Q by
+//                      the first kernel), or the grid itself.
+// Layout: spec[f][z][y][kx], kx ∈ [0, n/2), rows z·n + y.
+#include <cstdlib>
+#include <type_traits>
+
+#include "fft.cuh"
 
 namespace ibdl {
 
-ibdl_status plan_3d(Geometry* g) {
-  (void)g;
+enum { OP3_SCALAR_AN = 0, OP3_SCALAR_SD = 1, OP3_ADJ_AN = 2, OP3_ADJ_SD = 3 };
+
+template <int OP>
+struct Traits3;
+template <>
+struct Traits3<OP3_SCALAR_AN> { static constexpr int NIN = 1, NOUT = 1; };  // f = S̃Q
+template <>
+struct Traits3<OP3_SCALAR_SD> { static constexpr int NIN = 3, NOUT = 1; };  // S(Q n_m), m = x, y, z
+template <>
+struct Traits3<OP3_ADJ_AN> { static constexpr int NIN = 1, NOUT = 1; };     // S W
+template <>
+struct Traits3<OP3_ADJ_SD> { static constexpr int NIN = 1, NOUT = 3; };     // S W → ∂_m v
+
+enum { G3_INTERP = 0, G3_GRID = 1 };
+constexpr int kThreads3 = 256;
+
+struct Row3Params {
+  int n, log2n, R;
+  int M;
+  const int* cell_start;  // [n·n + 1], cell = base_z·n + base_y
+  const int* base;        // [3][M]
+  const int* perm;
+  const void* phi;        // T [3][4][M]
+  const void* dphi;
+  const void* wscale;
+  const void* nrm;        // T [3][M]
+  const double* in;
+  double* out;
+  void* spec;
+  const void* tw;
+  const int* stop;
+  double* grid;
+  const int* idx;
+  int vstride;
+};
+
+struct Col3Params {
+  int n, log2n, C, lc;
+  int nf;        // fields transformed (y passes)
+  double lam, scale;
+  const void* lap1;
+  const void* der1;
+  void* spec;
+  const void* tw;
+  const int* stop;
+};
+
+__device__ __forceinline__ void resolve_io3(const Row3Params& p, const double*& in, double*& out) {
+  in = p.in;
+  out = p.out;
+  if (p.idx) {
+    const int k = *p.idx;
+    in += (size_t)k * p.vstride;
+    out += (size_t)(k + 1) * p.vstride;
+  }
+}
+
+// Sorted points whose stencil meets the band of y-rows [y0, y0 + R) at plane z: cells (cz, cy)
+// with cz ∈ {z−3, …, z} and cy ∈ [y0 − 3, y0 + R) (mod n): at most 8 contiguous ranges.
+struct Ranges3 {
+  int start[8], count[8];
+  int nr, total;
+  __device__ int at(int t) const {
+    int r = 0;
+    while (t >= count[r]) {
+      t -= count[r];
+      ++r;
+    }
+    return start[r] + t;
+  }
+};
+
+__device__ __forceinline__ Ranges3 band_points3(const int* cell_start, int n, int z, int y0, int R) {
+  Ranges3 rg;
+  rg.nr = 0;
+  rg.total = 0;
+  for (int dz = -3; dz <= 0; ++dz) {
+    const int cz = (z + dz + n) & (n - 1);
+    const int lo = y0 - 3, hi = y0 + R;
+    const int base = cz * n;
+    if (lo >= 0) {
+      const int a = cell_start[base + lo], b = cell_start[base + hi];
+      rg.start[rg.nr] = a;
+      rg.count[rg.nr] = b - a;
+      rg.total += b - a;
+      ++rg.nr;
+    } else {
+      const int a = cell_start[base + lo + n], b = cell_start[base + n];
+      rg.start[rg.nr] = a;
+      rg.count[rg.nr] = b - a;
+      rg.total += b - a;
+      ++rg.nr;
+      const int c = cell_start[base], d = cell_start[base + hi];
+      rg.start[rg.nr] = c;
+      rg.count[rg.nr] = d - c;
+      rg.total += d - c;
+      ++rg.nr;
+    }
+  }
+  for (int r = rg.nr; r < 8; ++r) rg.count[r] = 1 << 30;
+  return rg;
+}
+
+// ------------------------------------------------------------------------------------------
+// kernel 1: spread + FFT along x
+// ------------------------------------------------------------------------------------------
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads3) k3_spread_rowfft(Row3Params p) {
+  if (p.stop && *p.stop) return;
+  constexpr int NIN = Traits3<OP>::NIN;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, R = p.R, half = R >> 1, M = p.M;
+  const int seqs = NIN * half;
+  const T* phi = static_cast<const T*>(p.phi);
+  const T* dphi = static_cast<const T*>(p.dphi);
+  const T* wsc = static_cast<const T*>(p.wscale);
+  const T* nrm = static_cast<const T*>(p.nrm);
+  cplx<T>* spec = static_cast<cplx<T>*>(p.spec);
+  cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufA = tws + n;
+  cplx<T>* bufB = bufA + padded((size_t)seqs * n);
+  T* acc = reinterpret_cast<T*>(bufA);
+  const int bands = n / R;
+  const int z = blockIdx.x / bands, y0 = (blockIdx.x - z * bands) * R;
+  const double* pin;
+  double* pout;
+  resolve_io3(p, pin, pout);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) pout[i] = 0.5 * pin[i];
+  for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
+  load_twiddles(tws, static_cast<const cplx<T>*>(p.tw), n);
+  __syncthreads();
+
+  const Ranges3 rg = band_points3(p.cell_start, n, z, y0, R);
+  for (int t = threadIdx.x; t < rg.total * 16; t += blockDim.x) {
+    const int s = rg.at(t >> 4);
+    const int ay = (t >> 2) & 3, ax = t & 3;
+    const int az = (z - p.base[2 * M + s]) & (n - 1);  // the one stencil plane at z (0..3)
+    const int row = (p.base[M + s] + ay) & (n - 1);
+    const int lr = (row - y0) & (n - 1);
+    if (lr >= R || az > 3) continue;
+    const int i = p.perm[s];
+    const int col = (p.base[s] + ax) & (n - 1);
+    const T px = phi[(0 * 4 + ax) * M + s], py = phi[(1 * 4 + ay) * M + s], pz = phi[(2 * 4 + az) * M + s];
+    const T ws = wsc[s];
+    const int e = (lr >> 1) * n + col;
+    const int odd = lr & 1;
+    const T ppp = px * py * pz;
+    if (OP == OP3_SCALAR_AN) {
+      const T q = T(pin[i]) * ws;
+      const T gx = dphi[(0 * 4 + ax) * M + s] * py * pz;
+      const T gy = px * dphi[(1 * 4 + ay) * M + s] * pz;
+      const T gz = px * py * dphi[(2 * 4 + az) * M + s];
+      atomicAdd(acc + 2 * pidx(e) + odd, q * (nrm[s] * gx + nrm[M + s] * gy + nrm[2 * M + s] * gz));
+    } else if (OP == OP3_SCALAR_SD) {
+      const T q = T(pin[i]) * ws * ppp;
+      atomicAdd(acc + 2 * pidx(e) + odd, q * nrm[s]);
+      atomicAdd(acc + 2 * pidx(e + half * n) + odd, q * nrm[M + s]);
+      atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, q * nrm[2 * M + s]);
+    } else {
+      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * ws * ppp);
+    }
+  }
+  __syncthreads();
+  const cplx<T>* res = fft_run<T, false>(bufA, bufB, p.log2n, seqs, tws);
+  const int nh = n >> 1, lnh = p.log2n - 1;
+  for (int t = threadIdx.x; t < seqs * nh; t += blockDim.x) {
+    const int sq = t >> lnh, k = t & (nh - 1);
+    const int f = sq / half, j = sq - f * half;
+    const int zb = sq * n;
+    cplx<T> A, B;
+    if (k == 0) {
+      const cplx<T> z0 = res[pidx(zb)], zh = res[pidx(zb + nh)];
+      A = mk(z0.x, zh.x);
+      B = mk(z0.y, zh.y);
+    } else {
+      const cplx<T> zk = res[pidx(zb + k)], zc = res[pidx(zb + n - k)];
+      A = mk(T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y));
+      B = mk(T(0.5) * (zk.y + zc.y), T(0.5) * (zc.x - zk.x));
+    }
+    const size_t row = (size_t)z * n + y0 + 2 * j;
+    spec[((size_t)f * n * n + row) * nh + k] = A;
+    spec[((size_t)f * n * n + row + 1) * nh + k] = B;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// kernel 2/4: FFT along y of C kx columns at one z, for nf fields (first and last stages read
+// and write the half spectra directly)
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct YColumnIO {
+  cplx<T>* spec;
+  int n, nh, z, k0, lc, C;
+  __device__ __forceinline__ size_t at(int bi, int m) const {
+    return (((size_t)(bi >> lc) * n + z) * n + m) * nh + k0 + (bi & (C - 1));
+  }
+  __device__ __forceinline__ cplx<T> load(int bi, int m) const { return spec[at(bi, m)]; }
+  __device__ __forceinline__ void store(int bi, int m, cplx<T> v) const { spec[at(bi, m)] = v; }
+};
+
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kThreads3) k3_ypass(Col3Params p) {
+  if (p.stop && *p.stop) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, C = p.C, nh = n >> 1;
+  const int groups = nh / C;
+  const int z = blockIdx.x / groups, k0 = (blockIdx.x - z * groups) * C;
+  cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufA = tws + n;
+  cplx<T>* bufB = bufA + padded((size_t)p.nf * C * n);
+  load_twiddles(tws, static_cast<const cplx<T>*>(p.tw), n);
+  __syncthreads();
+  const YColumnIO<T> io{static_cast<cplx<T>*>(p.spec), n, nh, z, k0, p.lc, C};
+  fft_run<T, INV>(bufA, bufB, p.log2n, p.nf * C, tws, io, io);
+}
+
+// ------------------------------------------------------------------------------------------
+// kernel 3: FFT along z, symbol, inverse FFT along z at (ky, −ky) × C kx columns
+// ------------------------------------------------------------------------------------------
+// sequence bi = (f·2 + q)·C + c: field f, y-frequency slot q (0: ky1, 1: ky2), column c
+template <typename T>
+struct ZColumnIO {
+  cplx<T>* spec;
+  int n, nh, ky1, ky2, k0, lc, C;
+  __device__ __forceinline__ size_t at(int bi, int m) const {
+    const int c = bi & (C - 1), fq = bi >> lc;
+    const int f = fq >> 1, ky = (fq & 1) ? ky2 : ky1;
+    return (((size_t)f * n + m) * n + ky) * nh + k0 + c;
+  }
+  __device__ __forceinline__ cplx<T> load(int bi, int m) const { return spec[at(bi, m)]; }
+  // with ky1 = ky2 the q = 1 slots alias the q = 0 column and carry no symbol: never stored
+  __device__ __forceinline__ void store(int bi, int m, cplx<T> v) const {
+    if (ky1 == ky2 && ((bi >> lc) & 1)) return;
+    spec[at(bi, m)] = v;
+  }
+};
+
+template <typename T, int OP>
+__device__ __forceinline__ void symbol3(const T* lap1, const T* der1, T lam, T scale, int kx, int ky, int kz,
+                                        const cplx<T>* in, cplx<T>* out) {
+  const T lap = lap1[kx] + lap1[ky] + lap1[kz];
+  const T den = lap + lam;
+  const T sig = den != T(0) ? scale / den : T(0);
+  if (OP == OP3_SCALAR_AN || OP == OP3_ADJ_AN) {
+    out[0] = cscale(in[0], sig);
+  } else if (OP == OP3_SCALAR_SD) {
+    const cplx<T> d = cadd(cadd(cscale(in[0], der1[kx]), cscale(in[1], der1[ky])), cscale(in[2], der1[kz]));
+    out[0] = cscale(cmuli(d), sig);
+  } else {
+    const cplx<T> v = cmuli(cscale(in[0], sig));
+    out[0] = cscale(v, der1[kx]);
+    out[1] = cscale(v, der1[ky]);
+    out[2] = cscale(v, der1[kz]);
+  }
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads3) k3_zpass(Col3Params p) {
+  if (p.stop && *p.stop) return;
+  constexpr int NIN = Traits3<OP>::NIN;
+  constexpr int NOUT = Traits3<OP>::NOUT;
+  constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, C = p.C, lc = p.lc, nh = n >> 1;
+  const int groups = nh / C;
+  const int pair = blockIdx.x / groups, k0 = (blockIdx.x - pair * groups) * C;
+  const int ky1 = pair, ky2 = (n - pair) & (n - 1);
+  const int nq = ky1 == ky2 ? 1 : 2;  // y-frequency columns in this CTA
+  cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufA = tws + n;
+  cplx<T>* bufB = bufA + padded((size_t)NMAX * 2 * C * n);
+  T* lap1 = reinterpret_cast<T*>(bufB + padded((size_t)NMAX * 2 * C * n));
+  T* der1 = lap1 + n;
+  load_twiddles(tws, static_cast<const cplx<T>*>(p.tw), n);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    lap1[i] = static_cast<const T*>(p.lap1)[i];
+    der1[i] = static_cast<const T*>(p.der1)[i];
+  }
+  __syncthreads();
+  const ZColumnIO<T> io{static_cast<cplx<T>*>(p.spec), n, nh, ky1, ky2, k0, lc, C};
+  // with one column (ky = −ky) only the q = 0 sequences exist: sequence index bi maps to
+  // (f·2 + 0)·C + c, so transform all 2·C slots per field and ignore q = 1 (it aliases q = 0)
+  cplx<T>* res = fft_run<T, false>(bufA, bufB, p.log2n, NIN * 2 * C, tws, io, NoIO());
+  cplx<T>* other = res == bufA ? bufB : bufA;
+  const T lam = T(p.lam), scale = T(p.scale);
+  auto at = [&](int f, int q, int c, int kz) { return pidx((((f * 2 + q) << lc) + c) * n + kz); };
+  for (int t = threadIdx.x; t < nq * C * n; t += blockDim.x) {
+    const int kz = t & (n - 1);
+    const int qc = t >> p.log2n;
+    const int c = qc & (C - 1), q = qc >> lc;
+    const int kx = k0 + c;
+    const int ky = q ? ky2 : ky1;
+    cplx<T> in[NIN], out[NOUT];
+    if (kx != 0) {
+#pragma unroll
+      for (int f = 0; f < NIN; ++f) in[f] = res[at(f, q, c, kz)];
+      symbol3<T, OP>(lap1, der1, lam, scale, kx, ky, kz, in, out);
+#pragma unroll
+      for (int f = 0; f < NOUT; ++f) res[at(f, q, c, kz)] = out[f];
+      continue;
+    }
+    // packed column: element (ky, kz) pairs with (−ky, −kz); one thread per unordered pair
+    const int kzp = (n - kz) & (n - 1);
+    int qp;
+    if (nq == 2) {
+      if (q == 1) continue;  // the q = 0 thread of the pair handles it
+      qp = 1;
+    } else {
+      if (kz > kzp) continue;
+      qp = 0;
+    }
+    const int kyp = qp ? ky2 : ky1;
+    cplx<T> Aa[NIN], Ba[NIN], Ab[NIN], Bb[NIN];
+#pragma unroll
+    for (int f = 0; f < NIN; ++f) {
+      const cplx<T> P = res[at(f, q, c, kz)];
+      const cplx<T> Pp = res[at(f, qp, c, kzp)];
+      Aa[f] = mk(T(0.5) * (P.x + Pp.x), T(0.5) * (P.y - Pp.y));
+      Ba[f] = mk(T(0.5) * (P.y + Pp.y), T(0.5) * (Pp.x - P.x));
+      Ab[f] = mk(T(0.5) * (Pp.x + P.x), T(0.5) * (Pp.y - P.y));
+      Bb[f] = mk(T(0.5) * (Pp.y + P.y), T(0.5) * (P.x - Pp.x));
+    }
+    cplx<T> oA[NOUT], oB[NOUT], oAp[NOUT], oBp[NOUT];
+    symbol3<T, OP>(lap1, der1, lam, scale, 0, ky, kz, Aa, oA);
+    symbol3<T, OP>(lap1, der1, lam, scale, nh, ky, kz, Ba, oB);
+    symbol3<T, OP>(lap1, der1, lam, scale, 0, kyp, kzp, Ab, oAp);
+    symbol3<T, OP>(lap1, der1, lam, scale, nh, kyp, kzp, Bb, oBp);
+    const bool self = (qp == q) && (kzp == kz);
+#pragma unroll
+    for (int f = 0; f < NOUT; ++f) {
+      res[at(f, q, c, kz)] = cadd(oA[f], cmuli(oB[f]));
+      if (!self) res[at(f, qp, c, kzp)] = cadd(oAp[f], cmuli(oBp[f]));
+    }
+  }
+  __syncthreads();
+  fft_run<T, true>(res, other, p.log2n, NOUT * 2 * C, tws, NoIO(), io);
+}
+
+// ------------------------------------------------------------------------------------------
+// kernel 5: inverse FFT along x, interpolation (or the grid)
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct RowZLoad3 {
+  const cplx<T>* spec;
+  int n, nh, row0, half, nrows;  // row0 = z·n + y0; field stride nrows rows
+  __device__ __forceinline__ cplx<T> load(int sq, int m) const {
+    const int f = sq / half, j = sq - f * half;
+    const size_t ra = ((size_t)f * nrows + row0 + 2 * j) * nh;
+    const size_t rb = ra + nh;
+    if (m == 0 || m == nh) {
+      const cplx<T> A = spec[ra], B = spec[rb];
+      return m == 0 ? mk(A.x, B.x) : mk(A.y, B.y);
+    }
+    if (m < nh) {
+      const cplx<T> A = spec[ra + m], B = spec[rb + m];
+      return mk(A.x - B.y, A.y + B.x);
+    }
+    const cplx<T> A = spec[ra + (n - m)], B = spec[rb + (n - m)];
+    return mk(A.x + B.y, B.x - A.y);
+  }
+};
+
+template <typename T, int OP, int GMODE>
+__global__ void __launch_bounds__(kThreads3) k3_rowifft_gather(Row3Params p) {
+  if (p.stop && *p.stop) return;
+  constexpr int NOUT = Traits3<OP>::NOUT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, R = p.R, half = R >> 1, M = p.M, nh = n >> 1;
+  const int seqs = NOUT * half;
+  const T* phi = static_cast<const T*>(p.phi);
+  const T* dphi = static_cast<const T*>(p.dphi);
+  const T* nrm = static_cast<const T*>(p.nrm);
+  cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufA = tws + n;
+  cplx<T>* bufB = bufA + padded((size_t)seqs * n);
+  const int bands = n / R;
+  const int z = blockIdx.x / bands, y0 = (blockIdx.x - z * bands) * R;
+  load_twiddles(tws, static_cast<const cplx<T>*>(p.tw), n);
+  __syncthreads();
+  const RowZLoad3<T> zl{static_cast<const cplx<T>*>(p.spec), n, nh, z * n + y0, half, n * n};
+  const cplx<T>* res = fft_run<T, true>(bufA, bufB, p.log2n, seqs, tws, zl, NoIO());
+  const T* u = reinterpret_cast<const T*>(res);
+  if (GMODE == G3_GRID) {
+    for (int t = threadIdx.x; t < NOUT * R * n; t += blockDim.x) {
+      const int f = t / (R * n);
+      const int rem = t - f * R * n;
+      const int lr = rem / n, x = rem - lr * n;
+      p.grid[(((size_t)f * n + z) * n + y0 + lr) * n + x] = double(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)]);
+    }
+    return;
+  }
+  const double* pin;
+  double* pout;
+  resolve_io3(p, pin, pout);
+  const Ranges3 rg = band_points3(p.cell_start, n, z, y0, R);
+  for (int t = threadIdx.x; t < rg.total * 4; t += blockDim.x) {
+    const int s = rg.at(t >> 2);
+    const int ay = t & 3;
+    const int az = (z - p.base[2 * M + s]) & (n - 1);
+    const int row = (p.base[M + s] + ay) & (n - 1);
+    const int lr = (row - y0) & (n - 1);
+    if (lr >= R || az > 3) continue;
+    const int i = p.perm[s];
+    const int bx = p.base[s];
+    const T py = phi[(1 * 4 + ay) * M + s], pz = phi[(2 * 4 + az) * M + s];
+    const int eb = (lr >> 1) * n, odd = lr & 1;
+    T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+    for (int ax = 0; ax < 4; ++ax) {
+      const int col = (bx + ax) & (n - 1);
+      const T px = phi[(0 * 4 + ax) * M + s];
+      const T v0 = u[2 * pidx(eb + col) + odd];
+      if (OP == OP3_ADJ_AN) {
+        a0 += v0 * dphi[(0 * 4 + ax) * M + s] * py * pz;
+        a1 += v0 * px * dphi[(1 * 4 + ay) * M + s] * pz;
+        a2 += v0 * px * py * dphi[(2 * 4 + az) * M + s];
+      } else {
+        const T w3 = px * py * pz;
+        a0 += v0 * w3;
+        if (NOUT == 3) {
+          a1 += u[2 * pidx(eb + half * n + col) + odd] * w3;
+          a2 += u[2 * pidx(eb + 2 * half * n + col) + odd] * w3;
+        }
+      }
+    }
+    if (OP == OP3_ADJ_AN) {
+      atomicAdd(pout + i, double(nrm[s]) * double(a0) + double(nrm[M + s]) * double(a1) + double(nrm[2 * M + s]) * double(a2));
+    } else if (OP == OP3_ADJ_SD) {
+      atomicAdd(pout + i, -(double(nrm[s]) * double(a0) + double(nrm[M + s]) * double(a1) + double(nrm[2 * M + s]) * double(a2)));
+    } else {
+      atomicAdd(pout + i, double(a0));
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+static const size_t kSmemLimit3 = 227 * 1024;
+
+template <typename T>
+static size_t smem_rows3(int n, int nf, int R) {
+  return (n + 2 * padded((size_t)nf * (R / 2) * n)) * sizeof(cplx<T>);
+}
+template <typename T>
+static size_t smem_y3(int n, int nf, int C) {
+  return (n + 2 * padded((size_t)nf * C * n)) * sizeof(cplx<T>);
+}
+template <typename T>
+static size_t smem_z3(int n, int nf, int C) {
+  return (n + 2 * padded((size_t)nf * 2 * C * n)) * sizeof(cplx<T>) + 2 * n * sizeof(T);
+}
+
+template <typename T, int OP>
+static ibdl_status set_attrs3() {
+  const int v = (int)kSmemLimit3;
+  IBDL_CUDA(cudaFuncSetAttribute(k3_spread_rowfft<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+  IBDL_CUDA(cudaFuncSetAttribute(k3_zpass<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+  IBDL_CUDA(cudaFuncSetAttribute(k3_rowifft_gather<T, OP, G3_INTERP>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+  IBDL_CUDA(cudaFuncSetAttribute(k3_rowifft_gather<T, OP, G3_GRID>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
   return IBDL_OK;
 }
-ibdl_status apply_3d(Geometry*, int, const double*, double*, cudaStream_t, const int*) {
-  return fail(IBDL_ERR_UNSUPPORTED, "3-D operator not available in this build");
+
+template <typename T>
+static ibdl_status set_attrs3_all() {
+  IBDL_TRY((set_attrs3<T, OP3_SCALAR_AN>()));
+  IBDL_TRY((set_attrs3<T, OP3_SCALAR_SD>()));
+  IBDL_TRY((set_attrs3<T, OP3_ADJ_AN>()));
+  IBDL_TRY((set_attrs3<T, OP3_ADJ_SD>()));
+  IBDL_CUDA(cudaFuncSetAttribute(k3_ypass<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit3));
+  IBDL_CUDA(cudaFuncSetAttribute(k3_ypass<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit3));
+  return IBDL_OK;
 }
-ibdl_status field_3d(Geometry*, const double*, double*, cudaStream_t) {
-  return fail(IBDL_ERR_UNSUPPORTED, "3-D operator not available in this build");
+
+ibdl_status plan_3d(Geometry* g) {
+  static bool attrs = false;
+  if (!attrs) {
+    IBDL_TRY(set_attrs3_all<double>());
+    IBDL_TRY(set_attrs3_all<float>());
+    attrs = true;
+  }
+  // Work units sized by FFT volume per CTA: R y-rows per row band, C kx columns per y-pass CTA,
+  // Cz per z-pass CTA (which holds 2·Cz columns: ky and −ky).
+  const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
+  const int n = g->n;
+  auto clampp2 = [](int v, int lo, int hi) { v = v < lo ? lo : (v > hi ? hi : v); int r = 1; while (r * 2 <= v) r *= 2; return r; };
+  for (int pi = 0; pi < 2; ++pi) {
+    const bool f32 = pi == 1;
+    // FP32 CTAs take about 2048 complex elements, FP64 about 1024 (measured on the 128³ sphere);
+    // R ≤ n/2 keeps the wrapped band rows [y0 − 3, y0 + R) distinct (no point counted twice)
+    const int target = f32 ? 2048 : 1024;
+    int R = clampp2(2 * (target / (n * nf)), 2, n / 2);
+    int C = clampp2(target / (n * nf), 1, n / 2);
+    int Cz = clampp2(target / 2 / (n * nf), 1, n / 2);
+    if (const char* e = getenv("IBDL_PLAN3_R")) R = clampp2(atoi(e), 2, n / 2);
+    if (const char* e = getenv("IBDL_PLAN3_C")) C = clampp2(atoi(e), 1, n / 2);
+    if (const char* e = getenv("IBDL_PLAN3_CZ")) Cz = clampp2(atoi(e), 1, n / 2);
+    auto rb = [&](int r) { return f32 ? smem_rows3<float>(n, nf, r) : smem_rows3<double>(n, nf, r); };
+    auto yb = [&](int c) { return f32 ? smem_y3<float>(n, nf, c) : smem_y3<double>(n, nf, c); };
+    auto zb = [&](int c) { return f32 ? smem_z3<float>(n, nf, c) : smem_z3<double>(n, nf, c); };
+    while (R > 2 && rb(R) > kSmemLimit3) R /= 2;
+    while (C > 1 && yb(C) > kSmemLimit3) C /= 2;
+    while (Cz > 1 && zb(Cz) > kSmemLimit3) Cz /= 2;
+    if (rb(R) > kSmemLimit3 || yb(C) > kSmemLimit3 || zb(Cz) > kSmemLimit3) R = C = Cz = 0;
+    g->rows_per_cta[pi] = R;
+    g->cols_per_cta[pi] = C;
+    g->zcols_per_cta[pi] = Cz;
+  }
+  if (g->rows_per_cta[0] == 0 && g->rows_per_cta[1] == 0)
+    return fail(IBDL_ERR_UNSUPPORTED, "3-D grid too large for the shared-memory FFT");
+  return IBDL_OK;
 }
-ibdl_status apply_3d_indexed(Geometry*, int, double*, const int*, int, cudaStream_t, const int*) {
-  return fail(IBDL_ERR_UNSUPPORTED, "3-D operator not available in this build");
+
+template <typename T, int OP>
+static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStream_t s, const int* stop, double* grid,
+                           const int* idx = nullptr, int vstride = 0) {
+  constexpr int NIN = Traits3<OP>::NIN, NOUT = Traits3<OP>::NOUT;
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi], Cz = g->zcols_per_cta[pi];
+  if (R == 0 || C == 0 || Cz == 0)
+    return fail(IBDL_ERR_UNSUPPORTED, "3-D grid too large for the shared-memory FFT at this precision");
+  const int n = g->n;
+  const PointTable<T>& tb = *reinterpret_cast<const PointTable<T>*>(pi ? (const void*)&g->t32 : (const void*)&g->t64);
+  Row3Params rp;
+  rp.n = n;
+  rp.log2n = __builtin_ctz(n);
+  rp.R = R;
+  rp.M = (int)g->M;
+  rp.cell_start = g->cell_start;
+  rp.base = g->base;
+  rp.perm = g->perm;
+  rp.phi = tb.phi;
+  rp.dphi = tb.dphi;
+  rp.wscale = tb.wscale;
+  rp.nrm = tb.nrm;
+  rp.in = in;
+  rp.out = out;
+  rp.spec = g->spec;
+  rp.tw = pi ? (const void*)g->tw32 : (const void*)g->tw64;
+  rp.stop = stop;
+  rp.grid = grid;
+  rp.idx = idx;
+  rp.vstride = vstride;
+  Col3Params cp;
+  cp.n = n;
+  cp.log2n = rp.log2n;
+  cp.C = C;
+  cp.lc = __builtin_ctz(C);
+  cp.lam = g->lambda;
+  cp.scale = 1.0 / ((double)n * n * n);
+  cp.lap1 = pi ? (const void*)g->lap32 : (const void*)g->lap64;
+  cp.der1 = pi ? (const void*)g->der32 : (const void*)g->der64;
+  cp.spec = g->spec;
+  cp.tw = rp.tw;
+  cp.stop = stop;
+  const int rows_grid = n * (n / R), col_grid = n * ((n / 2) / C), z_grid = (n / 2 + 1) * ((n / 2) / Cz);
+  const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
+  if (g->timing) timing_mark(g, s, -1);
+  k3_spread_rowfft<T, OP><<<rows_grid, kThreads3, smem_rows3<T>(n, NIN, R), s>>>(rp);
+  if (g->timing) timing_mark(g, s, st0);
+  cp.nf = NIN;
+  k3_ypass<T, false><<<col_grid, kThreads3, smem_y3<T>(n, NIN, C), s>>>(cp);
+  Col3Params zp = cp;
+  zp.C = Cz;
+  zp.lc = __builtin_ctz(Cz);
+  k3_zpass<T, OP><<<z_grid, kThreads3, smem_z3<T>(n, NIN > NOUT ? NIN : NOUT, Cz), s>>>(zp);
+  cp.nf = NOUT;
+  k3_ypass<T, true><<<col_grid, kThreads3, smem_y3<T>(n, NOUT, C), s>>>(cp);
+  if (g->timing) timing_mark(g, s, st0 + 1);
+  if (grid)
+    k3_rowifft_gather<T, OP, G3_GRID><<<rows_grid, kThreads3, smem_rows3<T>(n, NOUT, R), s>>>(rp);
+  else
+    k3_rowifft_gather<T, OP, G3_INTERP><<<rows_grid, kThreads3, smem_rows3<T>(n, NOUT, R), s>>>(rp);
+  if (g->timing) timing_mark(g, s, st0 + 2);
+  g->launches += 5;
+  IBDL_CUDA(cudaGetLastError());
+  return IBDL_OK;
 }
-ibdl_status adjoint_3d(Geometry*, int, const double*, double*, cudaStream_t) {
-  return fail(IBDL_ERR_UNSUPPORTED, "3-D operator not available in this build");
+
+template <typename T>
+static ibdl_status apply3_t(Geometry* g, const double* Q, double* Y, cudaStream_t s, const int* stop, double* grid,
+                            const int* idx = nullptr, int vstride = 0) {
+  if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "3-D: scalar PDE only");
+  return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op3<T, OP3_SCALAR_AN>(g, Q, Y, s, stop, grid, idx, vstride)
+                                           : run_op3<T, OP3_SCALAR_SD>(g, Q, Y, s, stop, grid, idx, vstride);
+}
+
+ibdl_status apply_3d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s, const int* stop) {
+  return precision == IBDL_FP32 ? apply3_t<float>(g, Q, Y, s, stop, nullptr)
+                                : apply3_t<double>(g, Q, Y, s, stop, nullptr);
+}
+
+ibdl_status apply_3d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
+                             const int* stop) {
+  return precision == IBDL_FP32 ? apply3_t<float>(g, V, V, s, stop, nullptr, idx, nd)
+                                : apply3_t<double>(g, V, V, s, stop, nullptr, idx, nd);
+}
+
+ibdl_status field_3d(Geometry* g, const double* Q, double* u, cudaStream_t s) {
+  return apply3_t<double>(g, Q, g->tmp_m, s, nullptr, u);
+}
+
+ibdl_status adjoint_3d(Geometry* g, int precision, const double* W, double* Z, cudaStream_t s) {
+  if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "adjoint: scalar PDE only");
+  if (precision == IBDL_FP32)
+    return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op3<float, OP3_ADJ_AN>(g, W, Z, s, nullptr, nullptr)
+                                             : run_op3<float, OP3_ADJ_SD>(g, W, Z, s, nullptr, nullptr);
+  return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op3<double, OP3_ADJ_AN>(g, W, Z, s, nullptr, nullptr)
+                                           : run_op3<double, OP3_ADJ_SD>(g, W, Z, s, nullptr, nullptr);
 }
 
 }  // namespace ibdl

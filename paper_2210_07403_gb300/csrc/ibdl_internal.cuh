@@ -109,7 +109,8 @@ struct Geometry {
 
   // launch plan (2-D and 3-D)
   int rows_per_cta[2];   // band height R for the row kernels, per precision (0 = fp64, 1 = fp32)
-  int cols_per_cta[2];   // kx columns per CTA in the column kernels
+  int cols_per_cta[2];   // kx columns per CTA in the column kernels (3-D: the y passes)
+  int zcols_per_cta[2];  // 3-D: kx columns per CTA in the z pass
   size_t smem_row[2], smem_col[2], smem_row_inv[2];
   int threads;           // threads per CTA of the 2-D kernels (0: the default)
 

@@ -242,3 +242,58 @@ def test_error_paths():
     assert st == ibdl.IBDL_OK
     with pytest.raises(ibdl.IbdlError):
         ibdl.ibdl_apply(g.handle, 7, ub.data_ptr(), Q.data_ptr())
+
+
+# ----------------------------------------------------------------------------------------
+# 3-D (scalar operator)
+# ----------------------------------------------------------------------------------------
+
+
+def _sphere_problem(N, delta="cos", dipole="analytic", lam=0.0, M=None):
+    M = M or int(round(4 * np.pi * 0.25 ** 2 * N * N))
+    return I.sphere_poisson(N, M, delta=delta, dipole=dipole, lam=lam)
+
+
+@pytest.mark.parametrize("N,delta,dipole,lam", [(16, "cos", "analytic", 0.0), (32, "sqrt", "analytic", 5.0),
+                                                (32, "cos", "spectral_div", 0.0), (16, "sqrt", "spectral_div", 2.0)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_3d_apply(N, delta, dipole, lam, precision, tol):
+    p = _sphere_problem(N, delta, dipole, lam)
+    g = _geom(p)
+    og = O.geometry_from_problem(p)
+    q = np.random.default_rng(N).standard_normal(p.bd.M)
+    y = g.apply(torch.from_numpy(q).cuda(), precision=precision).cpu().numpy()
+    assert _rel(y, O.apply(og, q)) < tol
+
+
+def test_3d_field_and_adjoint():
+    for dipole in ("analytic", "spectral_div"):
+        p = _sphere_problem(16, "sqrt", dipole, 1.0)
+        g = _geom(p)
+        og = O.geometry_from_problem(p)
+        q = np.random.default_rng(7).standard_normal(p.bd.M)
+        u = g.evaluate_field(torch.from_numpy(q).cuda()).cpu().numpy()
+        assert _rel(u, O.grid_field(og, q)) < 1e-12
+        z = g.adjoint(torch.from_numpy(q).cuda()).cpu().numpy()
+        assert _rel(z, O.adjoint_apply(og, q)) < 1e-12
+
+
+def test_3d_solve_sphere():
+    p = _sphere_problem(32)
+    g = _geom(p)
+    og = O.geometry_from_problem(p)
+    ref = O.solve(og, p.Ub, 1e-10)
+    Q, info, _ = g.solve(torch.from_numpy(p.Ub.reshape(-1)).cuda(), rtol=1e-10)
+    assert info["iterations"] == ref.iterations
+    assert _rel(Q.cpu().numpy(), ref.x) < 1e-10
+    Qm, infom, _ = g.solve(torch.from_numpy(p.Ub.reshape(-1)).cuda(), rtol=1e-10, precision="mixed")
+    assert _rel(Qm.cpu().numpy(), ref.x) < 1e-8
+
+
+def test_3d_full_size_apply():
+    """The 128³ sphere workload with 12 000 Fibonacci points: one FP64 application."""
+    p = I.sphere_poisson()
+    g = _geom(p)
+    q = np.random.default_rng(11).standard_normal(p.bd.M)
+    y = g.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+    assert _rel(y, O.apply(O.geometry_from_problem(p), q)) < 1e-12
