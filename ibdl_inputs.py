@@ -55,7 +55,8 @@ def _curve_by_arclength(radius_fn, M: int, center, rot: float = 0.0, nq: int = 4
     r, dr = radius_fn(th)
     speed = np.sqrt(r * r + dr * dr)
     c = np.fft.rfft(speed) / nq  # speed ≈ c0 + 2 Re Σ_{k≥1} c_k e^{ikθ}
-    big = np.nonzero(np.abs(c[1:]) > 1e-17 * abs(c[0]))[0]
+    # keep the modes above the FFT's round-off floor (≈ 1e-16 |c0|)
+    big = np.nonzero(np.abs(c[1:]) > 1e-15 * abs(c[0]))[0]
     kmax = min(max(int(big[-1]) + 2 if big.size else 16, 16), len(c) - 1)
     ck = c[1:kmax + 1]
     kk = np.arange(1, kmax + 1)

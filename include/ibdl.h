@@ -169,6 +169,35 @@ void ibdl_default_solve_opts(ibdl_solve_opts* opts);
 /* Geometry facts: number of density components c and points M. */
 ibdl_status ibdl_geometry_sizes(const ibdl_geometry* geom, int* ncomp, int64_t* n_points);
 
+/* ---- batches of independent 2-D problems -------------------------------------------------
+ * A batch holds `count` problems with the same pde and dipole form and any grid size, point
+ * count, λ, delta and symbol. Boundary vectors of all problems are concatenated in problem order
+ * (problem b occupies [offsets[b], offsets[b+1]) of every Q, Y, U_b array; see ibdl_batch_sizes).
+ * Every stage of an application is one launch for the whole batch; a batched solve runs one
+ * GMRES per problem, all advancing together in one captured graph per restart cycle. There is
+ * no counterpart in the paper beyond solving each problem as in Sec. 5.3.2. */
+typedef struct ibdl_batch ibdl_batch; /* opaque, library-owned */
+
+/* Create the geometries of `count` 2-D problems (each as ibdl_create_geometry) and the batched
+ * launch tables. Errors: IBDL_ERR_INVALID_ARG (count outside [1, 65536], mixed pde or dipole
+ * forms, any per-problem error, reported with the problem index), IBDL_ERR_UNSUPPORTED (3-D). */
+ibdl_status ibdl_create_batch(const ibdl_geometry_desc* descs, int count, void* stream, ibdl_batch** out);
+ibdl_status ibdl_destroy_batch(ibdl_batch* batch);
+
+/* Number of problems, the offsets (count + 1 entries, may be NULL) and the total length of the
+ * concatenated boundary vectors. */
+ibdl_status ibdl_batch_sizes(const ibdl_batch* batch, int* count, int64_t* offsets, int64_t* total);
+
+/* Y = A Q for every problem of the batch (concatenated device FP64 arrays; FP64 or FP32 grid
+ * arithmetic). Asynchronous. */
+ibdl_status ibdl_batch_apply(ibdl_batch* batch, int precision, const double* Q, double* Y, void* stream);
+
+/* Solve every problem (options as ibdl_solve; maxit bounds the longest problem's iterations).
+ * `infos` (count entries, may be NULL) receives per-problem results. Returns
+ * IBDL_ERR_NOT_CONVERGED if any problem missed rtol. Synchronises `stream`. */
+ibdl_status ibdl_batch_solve(ibdl_batch* batch, const double* Ub, double* Q, const ibdl_solve_opts* opts,
+                             ibdl_solve_info* infos, void* stream);
+
 /* Y = A Q for a 2-D problem without allocating any memory (the paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc, e.g. code inside a region being
  * captured into a CUDA graph, or a real-time loop that must not take the allocator's locks; such

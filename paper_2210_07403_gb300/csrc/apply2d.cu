@@ -16,6 +16,7 @@
 // complex column a + i b with a, b real columns; the column pass separates them by Hermitian
 // symmetry before the symbol and repacks after it.
 #include <cstdlib>
+#include <vector>
 #include <type_traits>
 
 #include "fft.cuh"
@@ -65,6 +66,7 @@ struct RowParams {
   double* grid;       // G_GRID: [nf][n][n]
   const int* idx;     // optional: in += (*idx)·vstride, out += (*idx + 1)·vstride (Krylov basis)
   int vstride;
+  int64_t io_off;     // batched launches: in = in_base + io_off, out = out_base + io_off
 };
 
 template <typename T>
@@ -115,12 +117,15 @@ __device__ __forceinline__ PointRanges band_points(const int* cell_start, int n,
 // ------------------------------------------------------------------------------------------
 // kernel 1: spread + forward FFT along x
 // ------------------------------------------------------------------------------------------
+// Bodies take the work unit (row band / column group) and the problem's number of units, so
+// the same code serves one problem (unit = blockIdx.x) and a batch of problems (unit from a
+// (problem, unit) table).
 template <typename T, int OP>
-__global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
+__device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int unit, int nunits,
+                                                   unsigned char* smem_raw) {
   if (p.stop && *p.stop) return;
   constexpr int NIN = Traits<OP>::NIN;
   constexpr int NC = Traits<OP>::C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = p.n, R = p.R, half = R >> 1, M = p.M;
   const int seqs = NIN * half;
   cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -129,13 +134,13 @@ __global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
   // accumulation view: field f, local row lr, column x → complex element e = (f·half + lr/2)·n + x
   // of the padded buffer, real part for even lr and imaginary part for odd lr
   T* acc = reinterpret_cast<T*>(bufA);
-  const int r0 = blockIdx.x * R;
+  const int r0 = unit * R;
   const double* pin;
   double* pout;
   resolve_io(p, pin, pout);
 
   // jump term: out = ½·in (the gather kernel adds S*u afterwards)
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NC * M; i += gridDim.x * blockDim.x)
+  for (int i = unit * blockDim.x + threadIdx.x; i < NC * M; i += nunits * blockDim.x)
     pout[i] = 0.5 * pin[i];
   for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
   load_twiddles(tws, p.tw, n);
@@ -212,6 +217,12 @@ __global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
   }
 }
 
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  spread_rowfft_body<T, OP>(p, blockIdx.x, gridDim.x, smem_raw);
+}
+
 // ------------------------------------------------------------------------------------------
 // Fourier symbols: NIN transformed fields in → NOUT out at wavenumber indices (kx, ky)
 // ------------------------------------------------------------------------------------------
@@ -270,19 +281,18 @@ struct ColumnIO {
 };
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
+__device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, unsigned char* smem_raw) {
   if (p.stop && *p.stop) return;
   constexpr int NIN = Traits<OP>::NIN;
   constexpr int NOUT = Traits<OP>::NOUT;
   constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = p.n, C = p.C, nh = n >> 1;
   cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufA = tws + n;
   cplx<T>* bufB = bufA + padded((size_t)NMAX * C * n);
   T* lap1 = reinterpret_cast<T*>(bufB + padded((size_t)NMAX * C * n));
   T* der1 = lap1 + n;
-  const int k0 = blockIdx.x * C;
+  const int k0 = unit * C;
   load_twiddles(tws, p.tw, n);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     lap1[i] = p.lap1[i];
@@ -335,6 +345,12 @@ __global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
   fft_run<T, true>(res, other, p.log2n, NOUT * C, tws, NoIO(), cio);
 }
 
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  colpass_body<T, OP>(p, blockIdx.x, smem_raw);
+}
+
 // ------------------------------------------------------------------------------------------
 // kernel 3: inverse FFT along x, then interpolation (or write the grid)
 // ------------------------------------------------------------------------------------------
@@ -362,16 +378,15 @@ struct RowZLoad {
 };
 
 template <typename T, int OP, int GMODE>
-__global__ void __launch_bounds__(kThreads) k_rowifft_gather(RowParams<T> p) {
+__device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int unit, unsigned char* smem_raw) {
   if (p.stop && *p.stop) return;
   constexpr int NOUT = Traits<OP>::NOUT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = p.n, R = p.R, half = R >> 1, M = p.M, nh = n >> 1;
   const int seqs = NOUT * half;
   cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufA = tws + n;
   cplx<T>* bufB = bufA + padded((size_t)seqs * n);
-  const int r0 = blockIdx.x * R;
+  const int r0 = unit * R;
   load_twiddles(tws, p.tw, n);
   __syncthreads();
   const RowZLoad<T> zl{p.spec, n, nh, r0, half};
@@ -435,6 +450,12 @@ __global__ void __launch_bounds__(kThreads) k_rowifft_gather(RowParams<T> p) {
   }
 }
 
+template <typename T, int OP, int GMODE>
+__global__ void __launch_bounds__(kThreads) k_rowifft_gather(RowParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rowifft_gather_body<T, OP, GMODE>(p, blockIdx.x, smem_raw);
+}
+
 // ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
@@ -462,6 +483,7 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.grid = grid;
   rp.idx = nullptr;
   rp.vstride = 0;
+  rp.io_off = 0;
   return rp;
 }
 
@@ -584,6 +606,148 @@ ibdl_status adjoint_2d(Geometry* g, int precision, const double* W, double* Z, c
                                              : run_op<float, OP_ADJ_SD>(g, W, Z, s, nullptr, nullptr);
   return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<double, OP_ADJ_AN>(g, W, Z, s, nullptr, nullptr)
                                            : run_op<double, OP_ADJ_SD>(g, W, Z, s, nullptr, nullptr);
+}
+
+// ------------------------------------------------------------------------------------------
+// batched launches: one grid per stage covers every problem of a batch; CTA i runs work unit
+// units[i] = (problem, unit) with that problem's parameter block
+// ------------------------------------------------------------------------------------------
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads) kb_spread_rowfft(const RowParams<T>* __restrict__ P, const int2* units,
+                                                             const double* in_base, double* out_base) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 u = units[blockIdx.x];
+  RowParams<T> p = P[u.x];
+  p.in = in_base + p.io_off;
+  p.out = out_base + p.io_off;
+  spread_rowfft_body<T, OP>(p, u.y, p.n / p.R, smem_raw);
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads) kb_colpass(const ColParams<T>* __restrict__ P, const int2* units) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 u = units[blockIdx.x];
+  const ColParams<T> p = P[u.x];
+  colpass_body<T, OP>(p, u.y, smem_raw);
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads) kb_rowifft_gather(const RowParams<T>* __restrict__ P, const int2* units,
+                                                              const double* in_base, double* out_base) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 u = units[blockIdx.x];
+  RowParams<T> p = P[u.x];
+  p.in = in_base + p.io_off;
+  p.out = out_base + p.io_off;
+  rowifft_gather_body<T, OP, G_INTERP>(p, u.y, smem_raw);
+}
+
+template <typename T, int OP>
+static ibdl_status batch_launch(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  static bool attrs = false;
+  if (!attrs) {
+    IBDL_CUDA(cudaFuncSetAttribute(kb_spread_rowfft<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    IBDL_CUDA(cudaFuncSetAttribute(kb_colpass<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    IBDL_CUDA(cudaFuncSetAttribute(kb_rowifft_gather<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    attrs = true;
+  }
+  const RowParams<T>* rp = static_cast<const RowParams<T>*>(B->rowp[pi][mode]);
+  const ColParams<T>* cp = static_cast<const ColParams<T>*>(B->colp[pi]);
+  kb_spread_rowfft<T, OP><<<B->nrow_units[pi], kThreads, B->smem_row[pi], s>>>(rp, B->row_units[pi], in_base, out_base);
+  kb_colpass<T, OP><<<B->ncol_units[pi], kThreads, B->smem_col[pi], s>>>(cp, B->col_units[pi]);
+  kb_rowifft_gather<T, OP><<<B->nrow_units[pi], kThreads, B->smem_gather[pi], s>>>(rp, B->row_units[pi], in_base, out_base);
+  B->launches += 3;
+  IBDL_CUDA(cudaGetLastError());
+  return IBDL_OK;
+}
+
+template <typename T>
+static ibdl_status batch_apply_t(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
+  if (B->pde == IBDL_PDE_STOKES)
+    return B->dipole == IBDL_DIPOLE_ANALYTIC ? batch_launch<T, OP_STOKES_AN>(B, mode, in_base, out_base, s)
+                                             : batch_launch<T, OP_STOKES_SD>(B, mode, in_base, out_base, s);
+  return B->dipole == IBDL_DIPOLE_ANALYTIC ? batch_launch<T, OP_SCALAR_AN>(B, mode, in_base, out_base, s)
+                                           : batch_launch<T, OP_SCALAR_SD>(B, mode, in_base, out_base, s);
+}
+
+ibdl_status batch_apply_2d(Batch* B, int precision, int mode, const double* in_base, double* out_base, cudaStream_t s) {
+  return precision == IBDL_FP32 ? batch_apply_t<float>(B, mode, in_base, out_base, s)
+                                : batch_apply_t<double>(B, mode, in_base, out_base, s);
+}
+
+template <typename T, int OP>
+static void batch_smem(Batch* B, Geometry* g, int pi) {
+  const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi];
+  const size_t a = smem_spread<T, OP>(g, R), b = smem_col<T, OP>(g, C), c = smem_gather<T, OP>(g, R);
+  if (a > B->smem_row[pi]) B->smem_row[pi] = a;
+  if (b > B->smem_col[pi]) B->smem_col[pi] = b;
+  if (c > B->smem_gather[pi]) B->smem_gather[pi] = c;
+}
+
+template <typename T>
+static void batch_smem_any(Batch* B, Geometry* g, int pi) {
+  if (B->pde == IBDL_PDE_STOKES) {
+    if (B->dipole == IBDL_DIPOLE_ANALYTIC) batch_smem<T, OP_STOKES_AN>(B, g, pi); else batch_smem<T, OP_STOKES_SD>(B, g, pi);
+  } else {
+    if (B->dipole == IBDL_DIPOLE_ANALYTIC) batch_smem<T, OP_SCALAR_AN>(B, g, pi); else batch_smem<T, OP_SCALAR_SD>(B, g, pi);
+  }
+}
+
+template <typename T>
+static ibdl_status batch_prepare_t(Batch* B, const int* kptr /* device &st[b].k, stride in bytes */, size_t kstride) {
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  std::vector<RowParams<T>> user(B->count), kry(B->count);
+  std::vector<ColParams<T>> col(B->count);
+  std::vector<int2> ru, cu;
+  for (int b = 0; b < B->count; ++b) {
+    Geometry* g = B->geoms[b];
+    if (g->rows_per_cta[pi] == 0 || g->cols_per_cta[pi] == 0)
+      return fail(IBDL_ERR_UNSUPPORTED, "a batch problem's grid is too large for the shared-memory FFT");
+    user[b] = row_params<T>(g, nullptr, nullptr, nullptr, nullptr);
+    user[b].io_off = B->off[b];
+    kry[b] = user[b];
+    col[b] = col_params<T>(g, nullptr);
+    if (kptr) {
+      const int* kb = reinterpret_cast<const int*>(reinterpret_cast<const char*>(kptr) + kstride * b);
+      kry[b].idx = kb;                               // &st[b].k
+      kry[b].stop = kb - 2;                          // &st[b].stop (two ints before k)
+      kry[b].vstride = (int)(g->ncomp * g->M);
+      kry[b].io_off = B->voff[b];
+    }
+    for (int u = 0; u < g->n / g->rows_per_cta[pi]; ++u) ru.push_back(make_int2(b, u));
+    for (int u = 0; u < (g->n / 2) / g->cols_per_cta[pi]; ++u) cu.push_back(make_int2(b, u));
+    batch_smem_any<T>(B, g, pi);
+  }
+  auto upload = [&](void** dst, const void* src, size_t bytes) -> ibdl_status {
+    if (*dst) cudaFree(*dst);
+    *dst = nullptr;
+    IBDL_CUDA(cudaMalloc(dst, bytes));
+    IBDL_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return IBDL_OK;
+  };
+  IBDL_TRY(upload(&B->rowp[pi][0], user.data(), sizeof(RowParams<T>) * B->count));
+  IBDL_TRY(upload(&B->rowp[pi][1], kry.data(), sizeof(RowParams<T>) * B->count));
+  IBDL_TRY(upload(&B->colp[pi], col.data(), sizeof(ColParams<T>) * B->count));
+  IBDL_TRY(upload(reinterpret_cast<void**>(&B->row_units[pi]), ru.data(), sizeof(int2) * ru.size()));
+  IBDL_TRY(upload(reinterpret_cast<void**>(&B->col_units[pi]), cu.data(), sizeof(int2) * cu.size()));
+  B->nrow_units[pi] = (int)ru.size();
+  B->ncol_units[pi] = (int)cu.size();
+  return IBDL_OK;
+}
+
+// Parameter blocks and unit tables of both precisions; the Krylov-basis mode points at the
+// batched GMRES state when it exists (B->st), else mirrors the user mode.
+ibdl_status batch_prepare_2d(Batch* B) {
+  const int* kptr = nullptr;
+  size_t kstride = 0;
+  if (B->st) {
+    kptr = reinterpret_cast<const int*>(static_cast<const char*>(B->st) + 2 * sizeof(int));
+    kstride = batch_state_bytes();
+  }
+  IBDL_TRY(batch_prepare_t<double>(B, kptr, kstride));
+  IBDL_TRY(batch_prepare_t<float>(B, kptr, kstride));
+  return IBDL_OK;
 }
 
 // Band height R (rows per CTA, even) and kx columns per CTA C, per precision, within the

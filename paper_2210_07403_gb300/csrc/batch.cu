@@ -1,0 +1,162 @@
+// Batches of independent 2-D problems: creation, destruction and the C entry points. Every
+// problem is an ordinary geometry (its own sorted tables, spectra and symbols); the batch adds
+// the per-problem parameter blocks and (problem, unit) tables of the batched launches, and the
+// batched GMRES state.
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ibdl_internal.cuh"
+
+struct ibdl_batch {
+  ibdl::Batch* b;
+};
+
+namespace ibdl {
+ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometry** out);
+ibdl_status destroy_geometry(Geometry* g);
+
+static void free_batch(Batch* B) {
+  if (!B) return;
+  cudaDeviceSynchronize();
+  if (B->geoms) {
+    for (int i = 0; i < B->count; ++i)
+      if (B->geoms[i]) destroy_geometry(B->geoms[i]);
+    delete[] B->geoms;
+  }
+  for (int p = 0; p < 2; ++p) {
+    for (int m = 0; m < 2; ++m)
+      if (B->rowp[p][m]) cudaFree(B->rowp[p][m]);
+    if (B->colp[p]) cudaFree(B->colp[p]);
+    if (B->row_units[p]) cudaFree(B->row_units[p]);
+    if (B->col_units[p]) cudaFree(B->col_units[p]);
+    if (B->exec[p]) cudaGraphExecDestroy(B->exec[p]);
+  }
+  void* dev[] = {B->V, B->st, B->ctl, B->vec, B->target, B->active, B->d_off, B->d_voff, B->d_nd, B->d_slice};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  if (B->host_st) cudaFreeHost(B->host_st);
+  delete[] B->off;
+  delete[] B->voff;
+  delete B;
+}
+
+static ibdl_status check_dev(const void* p, const char* name) {
+  if (!p) return fail(IBDL_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IBDL_ERR_INVALID_ARG, std::string(name) + " is not a CUDA device pointer");
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(IBDL_ERR_INVALID_ARG, std::string(name) + " is not a CUDA device pointer");
+  return IBDL_OK;
+}
+
+}  // namespace ibdl
+
+using namespace ibdl;
+
+extern "C" {
+
+ibdl_status ibdl_create_batch(const ibdl_geometry_desc* descs, int count, void* stream, ibdl_batch** out) {
+  set_error("");
+  if (!out) return fail(IBDL_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!descs) return fail(IBDL_ERR_INVALID_ARG, "descs is NULL");
+  if (count < 1 || count > 65536) return fail(IBDL_ERR_INVALID_ARG, "count must be in [1, 65536]");
+  for (int i = 0; i < count; ++i) {
+    if (descs[i].dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "batches hold 2-D problems only");
+    if (descs[i].pde != descs[0].pde || descs[i].dipole != descs[0].dipole)
+      return fail(IBDL_ERR_INVALID_ARG, "all problems of a batch need the same pde and dipole form");
+  }
+  Batch* B = new Batch();
+  std::memset(B, 0, sizeof(Batch));
+  B->count = count;
+  B->pde = descs[0].pde;
+  B->dipole = descs[0].dipole;
+  B->ncomp = descs[0].pde == IBDL_PDE_STOKES ? 2 : 1;
+  B->geoms = new Geometry*[count]();
+  B->off = new int64_t[count + 1];
+  B->voff = new int64_t[count];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  B->off[0] = 0;
+  for (int i = 0; i < count; ++i) {
+    ibdl_status st = create_geometry(descs + i, s, &B->geoms[i]);
+    if (st != IBDL_OK) {
+      const std::string msg = "problem " + std::to_string(i) + ": " + ibdl_last_error();
+      free_batch(B);
+      return fail(st, msg);
+    }
+    B->off[i + 1] = B->off[i] + B->geoms[i]->ncomp * B->geoms[i]->M;
+  }
+  B->total = B->off[count];
+  ibdl_status st = batch_prepare_2d(B);
+  if (st != IBDL_OK) {
+    free_batch(B);
+    return st;
+  }
+  *out = new ibdl_batch{B};
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_destroy_batch(ibdl_batch* batch) {
+  set_error("");
+  if (!batch) return IBDL_OK;
+  free_batch(batch->b);
+  delete batch;
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_batch_sizes(const ibdl_batch* batch, int* count, int64_t* offsets, int64_t* total) {
+  set_error("");
+  if (!batch || !batch->b) return fail(IBDL_ERR_INVALID_ARG, "batch is NULL");
+  const Batch* B = batch->b;
+  if (count) *count = B->count;
+  if (offsets)
+    for (int i = 0; i <= B->count; ++i) offsets[i] = B->off[i];
+  if (total) *total = B->total;
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_batch_apply(ibdl_batch* batch, int precision, const double* Q, double* Y, void* stream) {
+  set_error("");
+  if (!batch || !batch->b) return fail(IBDL_ERR_INVALID_ARG, "batch is NULL");
+  if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
+  IBDL_TRY(check_dev(Q, "Q"));
+  IBDL_TRY(check_dev(Y, "Y"));
+  const int64_t T = batch->b->total;
+  if (Q + T > Y && Y + T > Q) return fail(IBDL_ERR_INVALID_ARG, "Q and Y overlap");
+  return batch_apply_2d(batch->b, precision, 0, Q, Y, static_cast<cudaStream_t>(stream));
+}
+
+ibdl_status ibdl_batch_solve(ibdl_batch* batch, const double* Ub, double* Q, const ibdl_solve_opts* opts,
+                             ibdl_solve_info* infos, void* stream) {
+  set_error("");
+  if (!batch || !batch->b) return fail(IBDL_ERR_INVALID_ARG, "batch is NULL");
+  ibdl_solve_opts o;
+  if (opts)
+    o = *opts;
+  else
+    ibdl_default_solve_opts(&o);
+  if (!(o.rtol > 0) || !(o.rtol < 1)) return fail(IBDL_ERR_INVALID_ARG, "rtol must be in (0, 1)");
+  if (o.restart < 1 || o.restart > 64) return fail(IBDL_ERR_INVALID_ARG, "restart must be in [1, 64]");
+  if (o.maxit < 1) return fail(IBDL_ERR_INVALID_ARG, "maxit must be >= 1");
+  if (o.precision != IBDL_FP64 && o.precision != IBDL_FP32 && o.precision != IBDL_MIXED)
+    return fail(IBDL_ERR_INVALID_ARG, "unknown precision");
+  if (o.precision == IBDL_MIXED && (!(o.inner_rtol > 0) || !(o.inner_rtol < 1) || o.max_refine < 1))
+    return fail(IBDL_ERR_INVALID_ARG, "mixed precision needs inner_rtol in (0, 1) and max_refine >= 1");
+  if (!Ub || !Q) return fail(IBDL_ERR_INVALID_ARG, "U_b and Q are required");
+  if (!o.io_on_host) {
+    IBDL_TRY(check_dev(Ub, "U_b"));
+    IBDL_TRY(check_dev(Q, "Q"));
+  }
+  Batch* B = batch->b;
+  const int64_t before = B->launches;
+  ibdl_status st = batch_solve_impl(B, Ub, Q, &o, infos, static_cast<cudaStream_t>(stream));
+  if (infos)
+    for (int i = 0; i < B->count; ++i) infos[i].kernel_launches = B->launches - before;
+  return st;
+}
+
+}  // extern "C"

@@ -18,6 +18,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <algorithm>
+#include <vector>
 
 #include "ibdl_internal.cuh"
 
@@ -116,18 +118,13 @@ __global__ void __launch_bounds__(1024) k_gmres_start(GmresState* st, const doub
 // stopped, or after more loop bodies than the cycle allows (a guard), else 1.
 constexpr int ATH = 512;
 
+// Returns −1 (every thread) when the step was skipped because the cycle had already stopped;
+// otherwise, on CTA 0 thread 0, 1 if this step stopped the cycle and 0 if it continues.
 template <bool STAGED, int CL>
-__global__ void __launch_bounds__(ATH)
-    k_arnoldi_cluster(GmresState* st, double* V, int j, int nd, int m, int slice, cudaGraphConditionalHandle cond) {
+__device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, int nd, int m, int slice) {
   cg::cluster_group cluster = cg::this_cluster();
   if (j < 0) j = st->k;
-  if (st->stop || j >= st->kmax || j >= m) {
-    if (cond && cluster.block_rank() == 0 && threadIdx.x == 0) {
-      st->stop = 1;
-      cudaGraphSetConditional(cond, 0);
-    }
-    return;
-  }
+  if (st->stop || j >= st->kmax || j >= m) return -1;
   extern __shared__ double dsm[];
   __shared__ double part1[KMAX + 2], part2[KMAX + 2];
   __shared__ double h[KMAX + 2];
@@ -250,12 +247,164 @@ __global__ void __launch_bounds__(ATH)
       } else if (j + 1 >= st->kmax) {
         st->stop = 1;  // cycle full
       }
-      st->body_iters += 1;
-      if (st->body_iters > st->kmax + 2) st->stop = 1;
-      if (cond) cudaGraphSetConditional(cond, st->stop ? 0u : 1u);
     }
   }
   cluster.sync();  // no CTA leaves while another may still read its shared memory
+  return (rank == 0 && tid == 0) ? (st->stop ? 1 : 0) : 0;
+}
+
+// One problem. In a captured cycle (cond != 0) the step sets the while-loop condition on every
+// path: 0 once the cycle has stopped, or after more loop bodies than the cycle allows (a guard
+// on the device-side loop), else 1.
+template <bool STAGED, int CL>
+__global__ void __launch_bounds__(ATH)
+    k_arnoldi_cluster(GmresState* st, double* V, int j, int nd, int m, int slice, cudaGraphConditionalHandle cond) {
+  const int r = arnoldi_body<STAGED, CL>(st, V, j, nd, m, slice);
+  if (cond && cg::this_cluster().block_rank() == 0 && threadIdx.x == 0) {
+    if (r < 0) {
+      st->stop = 1;
+      cudaGraphSetConditional(cond, 0);
+    } else {
+      st->body_iters += 1;
+      if (st->body_iters > st->kmax + 2) st->stop = 1;
+      cudaGraphSetConditional(cond, st->stop ? 0u : 1u);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// batched GMRES: one Arnoldi cluster per problem in one launch; the while loop of the captured
+// cycle ends when no problem is running. Exactly one thread sets the loop condition (the
+// cond_set flag), either the problem whose step brings the running count to zero, or problem
+// 0's first thread when it sees no problem running or the loop-body guard exceeded.
+// ------------------------------------------------------------------------------------------
+struct BatchCtl {
+  int running;
+  int cond_set;
+  int body_iters;
+  int max_bodies;
+};
+
+size_t batch_state_bytes() { return sizeof(GmresState); }
+
+__device__ __forceinline__ void batch_end_loop(BatchCtl* ctl, cudaGraphConditionalHandle cond) {
+  if (atomicExch(&ctl->cond_set, 1) == 0) cudaGraphSetConditional(cond, 0);
+}
+
+template <bool STAGED, int CL>
+__global__ void __launch_bounds__(ATH)
+    kb_arnoldi(GmresState* st, double* V, const int64_t* __restrict__ voff, const int* __restrict__ nd_arr,
+               const int* __restrict__ slice_arr, int m, BatchCtl* ctl, cudaGraphConditionalHandle cond) {
+  const int b = blockIdx.x / CL;
+  const bool lead = cg::this_cluster().block_rank() == 0 && threadIdx.x == 0;
+  if (b == 0 && lead) {
+    const int it = atomicAdd(&ctl->body_iters, 1) + 1;
+    if (it > ctl->max_bodies || atomicAdd(&ctl->running, 0) <= 0) batch_end_loop(ctl, cond);
+  }
+  const int r = arnoldi_body<STAGED, CL>(st + b, V + voff[b], -1, nd_arr[b], m, slice_arr[b]);
+  if (lead && r == 1) {
+    if (atomicSub(&ctl->running, 1) == 1) batch_end_loop(ctl, cond);
+  }
+}
+
+__global__ void kb_ctl_reset(BatchCtl* ctl, int max_bodies) {
+  ctl->running = 0;
+  ctl->cond_set = 0;
+  ctl->body_iters = 0;
+  ctl->max_bodies = max_bodies;
+}
+
+// start a cycle for every problem: V_b,0 = r_b/‖r_b‖; inactive or already converged problems stop
+__global__ void __launch_bounds__(256)
+    kb_gmres_start(GmresState* st, const double* __restrict__ rhs, const int64_t* __restrict__ off, double* V,
+                   const int64_t* __restrict__ voff, const int* __restrict__ nd_arr, const double* __restrict__ target,
+                   const int* __restrict__ active, int kmax, BatchCtl* ctl) {
+  __shared__ double red[32];
+  const int b = blockIdx.x, nd = nd_arr[b];
+  const double* r = rhs + off[b];
+  double* Vb = V + voff[b];
+  double sacc = 0;
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) sacc += r[i] * r[i];
+  const double beta = sqrt(block_sum(sacc, red));
+  const bool bad = !isfinite(beta);
+  const double inv = (beta > 0 && !bad) ? 1.0 / beta : 0.0;
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) Vb[i] = r[i] * inv;
+  if (threadIdx.x == 0) {
+    GmresState* s = st + b;
+    s->beta = beta;
+    s->target = target[b];
+    s->res = beta;
+    s->k = 0;
+    s->kmax = kmax;
+    s->body_iters = 0;
+    s->g[0] = beta;
+    if (bad) {
+      s->status = ST_NONFINITE;
+      s->stop = 1;
+    } else if (!active[b] || beta <= target[b]) {
+      s->status = ST_CONVERGED;
+      s->stop = 1;
+    } else {
+      s->status = ST_RUNNING;
+      s->stop = 0;
+      atomicAdd(&ctl->running, 1);
+    }
+  }
+}
+
+// x_b += V_b y_b for every problem (one CTA per problem)
+__global__ void __launch_bounds__(256)
+    kb_gmres_update(GmresState* st, const double* __restrict__ V, const int64_t* __restrict__ voff, double* x,
+                    const int64_t* __restrict__ off, const int* __restrict__ nd_arr, int m) {
+  __shared__ double Rm[KMAX * KMAX];
+  __shared__ double y[KMAX];
+  const int b = blockIdx.x, nd = nd_arr[b];
+  const GmresState* s = st + b;
+  const int k = s->k;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int col = t / k, row = t - col * k;
+    Rm[row * KMAX + col] = row <= col ? s->H[(size_t)col * (m + 1) + row] : 0.0;
+  }
+  for (int t = threadIdx.x; t < k; t += blockDim.x) y[t] = s->g[t];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int l = i + 1; l < k; ++l) t -= Rm[i * KMAX + l] * y[l];
+      const double d = Rm[i * KMAX + i];
+      y[i] = d != 0.0 ? t / d : 0.0;
+    }
+  }
+  __syncthreads();
+  const double* Vb = V + voff[b];
+  double* xb = x + off[b];
+  for (int idx = threadIdx.x; idx < nd; idx += blockDim.x) {
+    double acc = xb[idx];
+    for (int i = 0; i < k; ++i) acc += y[i] * Vb[(size_t)i * nd + idx];
+    xb[idx] = acc;
+  }
+}
+
+// r_b = b_b − (Ax)_b and st[b].rnorm = ‖r_b‖ for every problem (Ax = NULL: ‖b_b‖)
+__global__ void __launch_bounds__(256)
+    kb_residual(GmresState* st, const double* __restrict__ bv, const double* __restrict__ Ax, double* r,
+                const int64_t* __restrict__ off, const int* __restrict__ nd_arr) {
+  __shared__ double red[32];
+  const int b = blockIdx.x, nd = nd_arr[b];
+  const size_t o = off[b];
+  double sacc = 0;
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+    const double v = bv[o + i] - (Ax ? Ax[o + i] : 0.0);
+    if (r) r[o + i] = v;
+    sacc += v * v;
+  }
+  const double nrm = sqrt(block_sum(sacc, red));
+  if (threadIdx.x == 0) st[b].rnorm = nrm;
+}
+
+__global__ void kb_axpy(double* x, const double* __restrict__ d, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] += d[i];
 }
 
 // x += V_{0..k-1} y with R y = g, many CTAs; each CTA solves the small triangular system in
@@ -694,6 +843,322 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
   IBDL_CUDA(cudaStreamSynchronize(s));
   inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = inf;
+  return ret;
+}
+
+}  // namespace ibdl
+
+namespace ibdl {
+
+// ------------------------------------------------------------------------------------------
+// batched solve driver
+// ------------------------------------------------------------------------------------------
+// Workspace for restart length m: per-problem Krylov bases (offsets voff), states, control
+// block, work vectors, targets, activity flags, and the parameter blocks of the batched apply
+// in Krylov-basis mode (which point at the states).
+static ibdl_status batch_workspace(Batch* B, int m, const ArnoldiCfg& c) {
+  if (B->m == m && B->V) return IBDL_OK;
+  if (B->V) cudaFree(B->V);
+  B->V = nullptr;
+  std::vector<int64_t> voff(B->count);
+  std::vector<int> nd(B->count), slice(B->count);
+  int64_t vtot = 0;
+  for (int b = 0; b < B->count; ++b) {
+    nd[b] = (int)(B->off[b + 1] - B->off[b]);
+    voff[b] = vtot;
+    vtot += (int64_t)(m + 1) * nd[b];
+    slice[b] = (nd[b] + c.cl - 1) / c.cl;
+  }
+  for (int b = 0; b < B->count; ++b) B->voff[b] = voff[b];
+  IBDL_CUDA(cudaMalloc((void**)&B->V, sizeof(double) * vtot));
+  if (!B->st) IBDL_CUDA(cudaMalloc(&B->st, sizeof(GmresState) * B->count));
+  if (!B->ctl) IBDL_CUDA(cudaMalloc(&B->ctl, sizeof(BatchCtl)));
+  if (!B->host_st) IBDL_CUDA(cudaMallocHost(&B->host_st, sizeof(GmresState) * B->count));
+  if (!B->vec) IBDL_CUDA(cudaMalloc((void**)&B->vec, sizeof(double) * 5 * B->total));
+  if (!B->target) IBDL_CUDA(cudaMalloc((void**)&B->target, sizeof(double) * B->count));
+  if (!B->active) IBDL_CUDA(cudaMalloc((void**)&B->active, sizeof(int) * B->count));
+  auto up = [&](void** dst, const void* src, size_t bytes) -> ibdl_status {
+    if (*dst) cudaFree(*dst);
+    *dst = nullptr;
+    IBDL_CUDA(cudaMalloc(dst, bytes));
+    IBDL_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return IBDL_OK;
+  };
+  std::vector<int64_t> off(B->off, B->off + B->count);
+  IBDL_TRY(up(reinterpret_cast<void**>(&B->d_off), off.data(), sizeof(int64_t) * B->count));
+  IBDL_TRY(up(reinterpret_cast<void**>(&B->d_voff), voff.data(), sizeof(int64_t) * B->count));
+  IBDL_TRY(up(reinterpret_cast<void**>(&B->d_nd), nd.data(), sizeof(int) * B->count));
+  IBDL_TRY(up(reinterpret_cast<void**>(&B->d_slice), slice.data(), sizeof(int) * B->count));
+  B->m = m;
+  B->cl = c.cl;
+  for (int i = 0; i < 2; ++i) {
+    if (B->exec[i]) cudaGraphExecDestroy(B->exec[i]);
+    B->exec[i] = nullptr;
+  }
+  return batch_prepare_2d(B);  // Krylov-basis mode now points at the states
+}
+
+template <bool STAGED, int CL>
+static cudaError_t launch_kb_arnoldi(Batch* B, size_t dyn, cudaGraphConditionalHandle cond, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(B->count * CL);
+  cfg.blockDim = dim3(ATH);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = s;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = CL;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kb_arnoldi<STAGED, CL>, static_cast<GmresState*>(B->st), B->V,
+                            (const int64_t*)B->d_voff, (const int*)B->d_nd, (const int*)B->d_slice, B->m,
+                            static_cast<BatchCtl*>(B->ctl), cond);
+}
+
+template <bool STAGED, int CL>
+static cudaError_t kb_arnoldi_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(kb_arnoldi<STAGED, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess && CL > 8)
+    e = cudaFuncSetAttribute(kb_arnoldi<STAGED, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+// the batched cycle graph: while (any problem running) { batched apply on V_b,k ; batched Arnoldi }
+static ibdl_status build_batch_graph(Batch* B, int prec, cudaGraphExec_t* out) {
+  *out = nullptr;
+  int maxslice = 0;
+  for (int b = 0; b < B->count; ++b) {
+    const int nd = (int)(B->off[b + 1] - B->off[b]);
+    maxslice = std::max(maxslice, (nd + B->cl - 1) / B->cl);
+  }
+  const size_t staged_bytes = (size_t)(B->m + 2) * maxslice * sizeof(double);
+  const bool staged = staged_bytes <= 200 * 1024;
+  const size_t dyn = staged ? staged_bytes : (size_t)maxslice * sizeof(double);
+  if (dyn > 200 * 1024) return fail(IBDL_ERR_UNSUPPORTED, "too many boundary unknowns for the Arnoldi kernel");
+  static bool attrs = false;
+  if (!attrs) {
+    IBDL_CUDA((kb_arnoldi_attrs<true, 8>()));
+    IBDL_CUDA((kb_arnoldi_attrs<false, 8>()));
+    if (B->cl == 16) {
+      IBDL_CUDA((kb_arnoldi_attrs<true, 16>()));
+      IBDL_CUDA((kb_arnoldi_attrs<false, 16>()));
+    }
+    attrs = true;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cs = nullptr;
+  IBDL_CUDA(cudaGraphCreate(&graph, 0));
+  ibdl_status ret = IBDL_OK;
+  bool capturing = false;
+  do {
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaGraphConditionalHandleCreate"); break; }
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaGraphAddNode(conditional)"); break; }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaStreamCreate"); break; }
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaStreamBeginCaptureToGraph"); break; }
+    capturing = true;
+    ret = batch_apply_2d(B, prec, 1, B->V, B->V, cs);
+    if (ret == IBDL_OK) {
+      cudaError_t le;
+      if (B->cl == 16)
+        le = staged ? launch_kb_arnoldi<true, 16>(B, dyn, h, cs) : launch_kb_arnoldi<false, 16>(B, dyn, h, cs);
+      else
+        le = staged ? launch_kb_arnoldi<true, 8>(B, dyn, h, cs) : launch_kb_arnoldi<false, 8>(B, dyn, h, cs);
+      if (le != cudaSuccess) ret = cuda_fail(le, "batched Arnoldi launch");
+    }
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    capturing = false;
+    if (ret != IBDL_OK) break;
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaStreamEndCapture"); break; }
+    e = cudaGraphInstantiate(out, graph, 0);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "cudaGraphInstantiate"); *out = nullptr; break; }
+  } while (false);
+  if (capturing) {
+    cudaGraph_t captured = nullptr;
+    cudaStreamEndCapture(cs, &captured);
+  }
+  if (cs) cudaStreamDestroy(cs);
+  cudaGraphDestroy(graph);
+  cudaGetLastError();
+  return ret;
+}
+
+// one batched GMRES cycle on right-hand sides rhs (concatenated) from zero corrections, added
+// into x; per-problem targets in B->target, activity in B->active; returns the states on the host
+static ibdl_status batch_cycle(Batch* B, int prec, const double* rhs, double* x, int kmax, cudaStream_t s) {
+  const int pi = prec == IBDL_FP32 ? 1 : 0;
+  if (!B->exec[pi]) IBDL_TRY(build_batch_graph(B, prec, &B->exec[pi]));
+  GmresState* st = static_cast<GmresState*>(B->st);
+  BatchCtl* ctl = static_cast<BatchCtl*>(B->ctl);
+  kb_ctl_reset<<<1, 1, 0, s>>>(ctl, kmax + 2);
+  kb_gmres_start<<<B->count, 256, 0, s>>>(st, rhs, B->d_off, B->V, B->d_voff, B->d_nd, B->target, B->active, kmax, ctl);
+  IBDL_CUDA(cudaGetLastError());
+  IBDL_CUDA(cudaGraphLaunch(B->exec[pi], s));
+  kb_gmres_update<<<B->count, 256, 0, s>>>(st, B->V, B->d_voff, x, B->d_off, B->d_nd, B->m);
+  IBDL_CUDA(cudaGetLastError());
+  IBDL_CUDA(cudaMemcpyAsync(B->host_st, st, sizeof(GmresState) * B->count, cudaMemcpyDeviceToHost, s));
+  IBDL_CUDA(cudaStreamSynchronize(s));
+  BatchCtl hc;
+  IBDL_CUDA(cudaMemcpy(&hc, ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost));
+  B->launches += 4 + 4 * (int64_t)(hc.body_iters > 0 ? hc.body_iters : 1);
+  return IBDL_OK;
+}
+
+// r = b − A₆₄x for every problem (r may be NULL), norms into the host states (synchronous)
+static ibdl_status batch_residual(Batch* B, const double* bvec, const double* x, double* r, double* Ax,
+                                  std::vector<double>& rn, cudaStream_t s) {
+  GmresState* st = static_cast<GmresState*>(B->st);
+  if (x) IBDL_TRY(batch_apply_2d(B, IBDL_FP64, 0, x, Ax, s));
+  kb_residual<<<B->count, 256, 0, s>>>(st, bvec, x ? Ax : nullptr, r, B->d_off, B->d_nd);
+  B->launches += 1;
+  IBDL_CUDA(cudaGetLastError());
+  IBDL_CUDA(cudaMemcpyAsync(B->host_st, st, sizeof(GmresState) * B->count, cudaMemcpyDeviceToHost, s));
+  IBDL_CUDA(cudaStreamSynchronize(s));
+  const GmresState* hs = static_cast<const GmresState*>(B->host_st);
+  rn.resize(B->count);
+  for (int b = 0; b < B->count; ++b) rn[b] = hs[b].rnorm;
+  return IBDL_OK;
+}
+
+ibdl_status batch_solve_impl(Batch* B, const double* Ub, double* Q, const ibdl_solve_opts* o, ibdl_solve_info* infos,
+                             cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int m = o->restart;
+  // the Arnoldi cluster choice of the single-problem path (needs a geometry to size against)
+  ArnoldiCfg c;
+  IBDL_TRY(arnoldi_cfg(B->geoms[0], m, &c));
+  IBDL_TRY(batch_workspace(B, m, c));
+  const int64_t T = B->total;
+  double* bvec = B->vec;
+  double* x = B->vec + T;
+  double* r = B->vec + 2 * T;
+  double* d = B->vec + 3 * T;
+  double* tmp = B->vec + 4 * T;
+  IBDL_CUDA(cudaMemcpyAsync(bvec, Ub, sizeof(double) * T, o->io_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  IBDL_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * T, s));
+  std::vector<double> bn, rn;
+  IBDL_TRY(batch_residual(B, bvec, nullptr, nullptr, nullptr, bn, s));
+  const int C = B->count;
+  std::vector<ibdl_solve_info> inf(C);
+  std::memset(inf.data(), 0, sizeof(ibdl_solve_info) * C);
+  std::vector<int> active(C), status(C, ST_RUNNING);
+  std::vector<double> target(C);
+  ibdl_status ret = IBDL_OK;
+  for (int b = 0; b < C; ++b) {
+    if (!std::isfinite(bn[b])) return fail(IBDL_ERR_NONFINITE, "U_b of problem " + std::to_string(b) + " contains NaN or Inf");
+    active[b] = bn[b] > 0.0;
+  }
+  auto upload = [&]() -> ibdl_status {
+    IBDL_CUDA(cudaMemcpyAsync(B->active, active.data(), sizeof(int) * C, cudaMemcpyHostToDevice, s));
+    IBDL_CUDA(cudaMemcpyAsync(B->target, target.data(), sizeof(double) * C, cudaMemcpyHostToDevice, s));
+    return IBDL_OK;
+  };
+  auto any_active = [&]() {
+    for (int b = 0; b < C; ++b)
+      if (active[b]) return true;
+    return false;
+  };
+  const GmresState* hs = static_cast<const GmresState*>(B->host_st);
+  int used = 0;  // loop bodies (the longest problem's iterations), counted against maxit
+  if (o->precision != IBDL_MIXED) {
+    // restarted GMRES(m) on every problem at once
+    const double* rhs = bvec;
+    for (int b = 0; b < C; ++b) target[b] = o->rtol * bn[b];
+    while (any_active() && used < o->maxit) {
+      IBDL_TRY(upload());
+      const int kmax = std::min(m, o->maxit - used);
+      IBDL_TRY(batch_cycle(B, o->precision, rhs, x, kmax, s));
+      int longest = 0;
+      for (int b = 0; b < C; ++b) {
+        if (!active[b]) continue;
+        longest = std::max(longest, hs[b].k);
+        inf[b].iterations += hs[b].k;
+        (o->precision == IBDL_FP32 ? inf[b].fp32_applies : inf[b].fp64_applies) += hs[b].k;
+        inf[b].sweeps += 1;
+        inf[b].rel_residual = hs[b].res / bn[b];
+        status[b] = hs[b].status;
+        if (hs[b].status != ST_RUNNING) active[b] = 0;
+      }
+      used += std::max(longest, 1);
+      if (!any_active()) break;
+      // restart the unconverged problems from their true residuals
+      IBDL_TRY(batch_residual(B, bvec, x, r, tmp, rn, s));
+      for (int b = 0; b < C; ++b)
+        if (active[b]) {
+          inf[b].fp64_applies += 1;
+          inf[b].rel_residual = rn[b] / bn[b];
+          if (rn[b] <= target[b]) {
+            active[b] = 0;
+            status[b] = ST_CONVERGED;
+          }
+        }
+      rhs = r;
+    }
+  } else {
+    // iterative refinement: inner FP32-apply GMRES cycles on the FP64 residuals
+    const double* rhs = bvec;
+    rn = bn;
+    for (int sweep = 0; sweep < o->max_refine && any_active() && used < o->maxit; ++sweep) {
+      for (int b = 0; b < C; ++b) target[b] = std::max(o->inner_rtol * rn[b], 0.5 * o->rtol * bn[b]);
+      IBDL_TRY(upload());
+      IBDL_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * T, s));
+      const int kmax = std::min(m, o->maxit - used);
+      IBDL_TRY(batch_cycle(B, IBDL_FP32, rhs, d, kmax, s));
+      int longest = 0;
+      for (int b = 0; b < C; ++b) {
+        if (!active[b]) continue;
+        longest = std::max(longest, hs[b].k);
+        inf[b].iterations += hs[b].k;
+        inf[b].fp32_applies += hs[b].k;
+        inf[b].sweeps += 1;
+        if (hs[b].status == ST_NONFINITE) {
+          status[b] = ST_NONFINITE;
+          active[b] = 0;
+        }
+      }
+      used += std::max(longest, 1);
+      kb_axpy<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(x, d, T);
+      B->launches += 1;
+      IBDL_CUDA(cudaGetLastError());
+      IBDL_TRY(batch_residual(B, bvec, x, r, tmp, rn, s));
+      for (int b = 0; b < C; ++b) {
+        if (!active[b]) continue;
+        inf[b].fp64_applies += 1;
+        inf[b].rel_residual = rn[b] / bn[b];
+        if (rn[b] <= o->rtol * bn[b]) {
+          active[b] = 0;
+          status[b] = ST_CONVERGED;
+        }
+      }
+      rhs = r;
+    }
+  }
+  for (int b = 0; b < C; ++b) {
+    if (status[b] == ST_NONFINITE && ret == IBDL_OK) ret = fail(IBDL_ERR_NONFINITE, "non-finite value in problem " + std::to_string(b));
+    if (bn[b] > 0 && status[b] != ST_CONVERGED && status[b] != ST_BREAKDOWN && ret == IBDL_OK)
+      ret = fail(IBDL_ERR_NOT_CONVERGED, "problem " + std::to_string(b) + " did not reach rtol");
+  }
+  IBDL_CUDA(cudaMemcpyAsync(Q, x, sizeof(double) * T, o->io_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  IBDL_CUDA(cudaStreamSynchronize(s));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (infos)
+    for (int b = 0; b < C; ++b) {
+      inf[b].seconds = secs;
+      infos[b] = inf[b];
+    }
   return ret;
 }
 

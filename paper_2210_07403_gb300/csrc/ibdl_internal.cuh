@@ -134,6 +134,49 @@ struct Geometry {
   int ev_cap, ev_used;
 };
 
+// A batch of independent 2-D problems (same PDE and dipole form; any grid size, point count,
+// λ, delta and symbol per problem). Boundary vectors of all problems are concatenated: problem b
+// owns [off[b], off[b] + c·M_b).
+struct Batch {
+  int count;
+  int pde, dipole, ncomp;
+  Geometry** geoms;      // host array of per-problem geometries (tables, spectra, symbols)
+  int64_t* off;          // host [count + 1]
+  int64_t total;
+  // batched-launch data per precision p (0 fp64, 1 fp32) and mode (0 user buffers, 1 Krylov basis)
+  void* rowp[2][2];      // device RowParams<T>[count]
+  void* colp[2];         // device ColParams<T>[count]
+  int2* row_units[2];    // device (problem, unit) tables
+  int2* col_units[2];
+  int nrow_units[2], ncol_units[2];
+  size_t smem_row[2], smem_col[2], smem_gather[2];
+  // batched GMRES
+  int m;                 // restart length the workspace was sized for (0: none yet)
+  int64_t* voff;         // host [count]: offset of problem b's basis in V
+  double* V;
+  void* st;              // device GmresState[count]
+  void* ctl;             // device control block of the batched while loop
+  void* host_st;         // pinned copy of the states
+  double* vec;           // [5][total]: b, x, r, d, scratch
+  double* target;        // device [count]
+  int* active;           // device [count]
+  cudaGraphExec_t exec[2];
+  int exec_m[2];
+  int64_t launches;
+  int cl;                // Arnoldi cluster size
+  int64_t* d_off;        // device copies of the per-problem offsets, sizes and slices
+  int64_t* d_voff;
+  int* d_nd;
+  int* d_slice;
+};
+
+ibdl_status batch_prepare_2d(Batch* B);
+size_t batch_state_bytes();  // sizeof the per-problem GMRES state (stop, status, k are its first ints)
+ibdl_status batch_apply_2d(Batch* B, int precision, int mode, const double* in_base, double* out_base,
+                           cudaStream_t s);
+ibdl_status batch_solve_impl(Batch* B, const double* Ub, double* Q, const ibdl_solve_opts* o,
+                             ibdl_solve_info* infos, cudaStream_t s);
+
 // record an event on `s` closing an interval of `stage` (−1 opens a new interval)
 void timing_mark(Geometry* g, cudaStream_t s, int stage);
 ibdl_status set_stage_timing(Geometry* g, int enable);

@@ -78,6 +78,12 @@ SIGNATURES = {
     "ibdl_default_solve_opts": (None, [POINTER(ibdl_solve_opts)]),
     "ibdl_geometry_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int64)]),
     "ibdl_apply_noalloc": (c_int, [POINTER(ibdl_geometry_desc), c_int, c_void_p, c_void_p, c_void_p]),
+    "ibdl_create_batch": (c_int, [POINTER(ibdl_geometry_desc), c_int, c_void_p, POINTER(c_void_p)]),
+    "ibdl_destroy_batch": (c_int, [c_void_p]),
+    "ibdl_batch_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int64), POINTER(c_int64)]),
+    "ibdl_batch_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "ibdl_batch_solve": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(ibdl_solve_opts),
+                                 POINTER(ibdl_solve_info), c_void_p]),
     "ibdl_set_stage_timing": (c_int, [c_void_p, c_int]),
     "ibdl_get_stage_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
     "ibdl_last_error": (c_char_p, []),
@@ -167,6 +173,35 @@ def ibdl_geometry_sizes(geom):
     return c.value, m.value
 
 
+def ibdl_create_batch(descs, stream: int = 0) -> c_void_p:
+    arr = (ibdl_geometry_desc * len(descs))(*descs)
+    out = c_void_p()
+    _check(load().ibdl_create_batch(arr, len(descs), c_void_p(stream), byref(out)))
+    return out
+
+
+def ibdl_destroy_batch(batch) -> int:
+    return _check(load().ibdl_destroy_batch(batch))
+
+
+def ibdl_batch_sizes(batch):
+    cnt, tot = c_int(), c_int64()
+    _check(load().ibdl_batch_sizes(batch, byref(cnt), None, byref(tot)))
+    offs = (c_int64 * (cnt.value + 1))()
+    _check(load().ibdl_batch_sizes(batch, None, offs, None))
+    return cnt.value, list(offs), tot.value
+
+
+def ibdl_batch_apply(batch, precision: int, Q: int, Y: int, stream: int = 0) -> int:
+    return _check(load().ibdl_batch_apply(batch, precision, c_void_p(Q), c_void_p(Y), c_void_p(stream)))
+
+
+def ibdl_batch_solve(batch, Ub: int, Q: int, opts: ibdl_solve_opts, infos, stream: int = 0,
+                     check: bool = True) -> int:
+    st = load().ibdl_batch_solve(batch, c_void_p(Ub), c_void_p(Q), byref(opts), infos, c_void_p(stream))
+    return _check(st) if check else st
+
+
 def ibdl_set_stage_timing(geom, enable: int) -> int:
     return _check(load().ibdl_set_stage_timing(geom, int(enable)))
 
@@ -193,6 +228,75 @@ def _stream_handle(stream) -> int:
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def _desc(X, normals, weights, n, box, origin, pde, lam, mu, delta, dipole, symbol):
+    """Descriptor over host arrays (returned arrays must stay alive while it is used)."""
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+    nrm = np.ascontiguousarray(np.asarray(normals, dtype=np.float64))
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    d = ibdl_geometry_desc()
+    d.dim, d.n, d.box = X.shape[0], int(n), float(box)
+    for j in range(3):
+        d.origin[j] = float(origin[j]) if j < len(origin) else 0.0
+    d.n_points = X.shape[1]
+    d.X, d.normals, d.weights = X.ctypes.data, nrm.ctypes.data, w.ctypes.data
+    d.pde, d.lambda_, d.mu = _PDE[pde], float(lam), float(mu)
+    d.delta, d.dipole, d.symbol = _DELTA[delta], _DIPOLE[dipole], _SYMBOL[symbol]
+    d.inputs_on_device = 0
+    return d, (X, nrm, w)
+
+
+class Batch:
+    """A batch of independent 2-D problems (``ibdl_inputs.Problem`` objects); boundary vectors
+    are concatenated in problem order."""
+
+    def __init__(self, problems, stream=None):
+        import torch
+
+        self._torch = torch
+        descs, keep = [], []
+        for p in problems:
+            d, k = _desc(p.bd.X, p.bd.n, p.bd.w, p.N, p.box, p.origin, p.pde, p.lam, p.mu, p.delta,
+                         p.dipole, p.symbol)
+            descs.append(d)
+            keep.append(k)
+        self._h = ibdl_create_batch(descs, _stream_handle(stream))
+        self.count, self.offsets, self.total = ibdl_batch_sizes(self._h)
+
+    def split(self, v):
+        return [v[self.offsets[b]:self.offsets[b + 1]] for b in range(self.count)]
+
+    def apply(self, Q, Y=None, precision: str = "fp64", stream=None):
+        if Y is None:
+            Y = self._torch.empty_like(Q)
+        ibdl_batch_apply(self._h, _PREC[precision], Q.data_ptr(), Y.data_ptr(), _stream_handle(stream))
+        return Y
+
+    def solve(self, Ub, rtol: float = 1e-8, precision: str = "fp64", restart: int = 50, maxit: int = 200,
+              inner_rtol: float = 1e-4, max_refine: int = 6, Q=None, stream=None, check: bool = True):
+        t = self._torch
+        o = ibdl_default_solve_opts()
+        o.rtol, o.restart, o.maxit, o.precision = rtol, restart, maxit, _PREC[precision]
+        o.inner_rtol, o.max_refine = inner_rtol, max_refine
+        if not Ub.is_cuda:
+            o.io_on_host = 1
+        if Q is None:
+            Q = t.empty_like(Ub)
+        infos = (ibdl_solve_info * self.count)()
+        st = ibdl_batch_solve(self._h, Ub.data_ptr(), Q.data_ptr(), o, infos, _stream_handle(stream), check=check)
+        return Q, [i.as_dict() for i in infos], st
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            ibdl_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Geometry:
