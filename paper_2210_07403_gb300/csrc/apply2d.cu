@@ -759,15 +759,26 @@ ibdl_status plan_2d(Geometry* g) {
     IBDL_TRY(set_attrs_all<float>());
     attrs = true;
   }
+  // Work units sized by FFT volume: about 2048 complex elements per CTA in FP32 and 1024 in FP64
+  // (one radix-8 butterfly per thread per stage or fewer), keeping at least 16 row bands and 16
+  // column groups per problem; R ≤ n/2 keeps the wrapped band rows [r0 − 3, r0 + R) distinct.
   const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
+  const int n = g->n;
+  auto clampp2 = [](int v, int lo, int hi) {
+    v = v < lo ? lo : (v > hi ? hi : v);
+    int r = 1;
+    while (r * 2 <= v) r *= 2;
+    return r;
+  };
   for (int pi = 0; pi < 2; ++pi) {
     const size_t cs = pi ? sizeof(float2) : sizeof(double2);
-    int R = g->n >= 256 ? 2 : 2;
+    const int target = pi ? 2048 : 1024;
+    int R = clampp2(2 * (target / (n * g->nf_in)), 2, n / 16 > 2 ? n / 16 : 2);
     auto row_bytes = [&](int r) { return (g->n + 2 * padded((size_t)nf * (r / 2) * g->n)) * cs; };
     auto col_bytes = [&](int c) { return (g->n + 2 * padded((size_t)nf * c * g->n)) * cs + 2 * g->n * cs / 2; };
     while (R > 2 && row_bytes(R) > kSmemLimit) R /= 2;
     if (row_bytes(R) > kSmemLimit) R = 0;
-    int C = 1;
+    int C = clampp2(target / (n * nf), 1, n / 32 > 1 ? n / 32 : 1);
     while (C > 1 && col_bytes(C) > kSmemLimit) C /= 2;
     if (col_bytes(C) > kSmemLimit) C = 0;
     if ((g->n / 2) % (C ? C : 1)) C = 1;
