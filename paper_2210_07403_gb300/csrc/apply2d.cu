@@ -18,6 +18,7 @@
 #include <cstdlib>
 #include <vector>
 #include <type_traits>
+#include <utility>
 
 #include "fft.cuh"
 
@@ -123,7 +124,6 @@ __device__ __forceinline__ PointRanges band_points(const int* cell_start, int n,
 template <typename T, int OP>
 __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int unit, int nunits,
                                                    unsigned char* smem_raw) {
-  if (p.stop && *p.stop) return;
   constexpr int NIN = Traits<OP>::NIN;
   constexpr int NC = Traits<OP>::C;
   const int n = p.n, R = p.R, half = R >> 1, M = p.M;
@@ -135,6 +135,11 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   // of the padded buffer, real part for even lr and imaginary part for odd lr
   T* acc = reinterpret_cast<T*>(bufA);
   const int r0 = unit * R;
+  // prologue independent of the previous kernel, then wait for it (programmatic launch)
+  for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
+  load_twiddles(tws, p.tw, n);
+  cudaGridDependencySynchronize();
+  if (p.stop && *p.stop) return;
   const double* pin;
   double* pout;
   resolve_io(p, pin, pout);
@@ -142,8 +147,6 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   // jump term: out = ½·in (the gather kernel adds S*u afterwards)
   for (int i = unit * blockDim.x + threadIdx.x; i < NC * M; i += nunits * blockDim.x)
     pout[i] = 0.5 * pin[i];
-  for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
-  load_twiddles(tws, p.tw, n);
   __syncthreads();
 
   // one thread per (point, stencil node): 16 work items per point whose stencil meets the band
@@ -282,7 +285,6 @@ struct ColumnIO {
 
 template <typename T, int OP>
 __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, unsigned char* smem_raw) {
-  if (p.stop && *p.stop) return;
   constexpr int NIN = Traits<OP>::NIN;
   constexpr int NOUT = Traits<OP>::NOUT;
   constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
@@ -298,6 +300,8 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
     lap1[i] = p.lap1[i];
     der1[i] = p.der1[i];
   }
+  cudaGridDependencySynchronize();
+  if (p.stop && *p.stop) return;
   __syncthreads();
   const ColumnIO<T> cio{p.spec, n, nh, k0, p.lc, C};
   // forward transform along y: the first stage reads the half spectra directly
@@ -379,7 +383,6 @@ struct RowZLoad {
 
 template <typename T, int OP, int GMODE>
 __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int unit, unsigned char* smem_raw) {
-  if (p.stop && *p.stop) return;
   constexpr int NOUT = Traits<OP>::NOUT;
   const int n = p.n, R = p.R, half = R >> 1, M = p.M, nh = n >> 1;
   const int seqs = NOUT * half;
@@ -388,6 +391,8 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   cplx<T>* bufB = bufA + padded((size_t)seqs * n);
   const int r0 = unit * R;
   load_twiddles(tws, p.tw, n);
+  cudaGridDependencySynchronize();
+  if (p.stop && *p.stop) return;
   __syncthreads();
   const RowZLoad<T> zl{p.spec, n, nh, r0, half};
   const cplx<T>* res = fft_run<T, true>(bufA, bufB, p.log2n, seqs, tws, zl, NoIO());
@@ -522,6 +527,34 @@ static size_t smem_col(const Geometry* g, int C) {
 
 static const size_t kSmemLimit = 227 * 1024;
 
+// Programmatic dependent launch: the kernel may start while the previous kernel on the stream
+// drains; it runs its prologue and then waits in cudaGridDependencySynchronize(). IBDL_NO_PDL=1
+// turns it off.
+static bool use_pdl() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("IBDL_NO_PDL");
+    v = (e && atoi(e) != 0) ? 0 : 1;
+  }
+  return v == 1;
+}
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, bool pdl,
+                            Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = pdl && use_pdl() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <typename T, int OP>
 static ibdl_status set_attrs() {
   IBDL_CUDA(cudaFuncSetAttribute(k_spread_rowfft<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
@@ -561,12 +594,12 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   const int nt = g->threads ? g->threads : kThreads;
   k_spread_rowfft<T, OP><<<g->n / R, nt, s1, s>>>(rp);
   if (g->timing) timing_mark(g, s, st0);
-  k_colpass<T, OP><<<(g->n / 2) / C, nt, s2, s>>>(cp);
+  IBDL_CUDA(launch_k(k_colpass<T, OP>, (g->n / 2) / C, nt, s2, s, !g->timing, cp));
   if (g->timing) timing_mark(g, s, st0 + 1);
   if (grid)
-    k_rowifft_gather<T, OP, G_GRID><<<g->n / R, nt, s3, s>>>(rp);
+    IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_GRID>, g->n / R, nt, s3, s, !g->timing, rp));
   else
-    k_rowifft_gather<T, OP, G_INTERP><<<g->n / R, nt, s3, s>>>(rp);
+    IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_INTERP>, g->n / R, nt, s3, s, !g->timing, rp));
   if (g->timing) timing_mark(g, s, st0 + 2);
   g->launches += 3;
   IBDL_CUDA(cudaGetLastError());
@@ -655,8 +688,10 @@ static ibdl_status batch_launch(Batch* B, int mode, const double* in_base, doubl
   const RowParams<T>* rp = static_cast<const RowParams<T>*>(B->rowp[pi][mode]);
   const ColParams<T>* cp = static_cast<const ColParams<T>*>(B->colp[pi]);
   kb_spread_rowfft<T, OP><<<B->nrow_units[pi], kThreads, B->smem_row[pi], s>>>(rp, B->row_units[pi], in_base, out_base);
-  kb_colpass<T, OP><<<B->ncol_units[pi], kThreads, B->smem_col[pi], s>>>(cp, B->col_units[pi]);
-  kb_rowifft_gather<T, OP><<<B->nrow_units[pi], kThreads, B->smem_gather[pi], s>>>(rp, B->row_units[pi], in_base, out_base);
+  IBDL_CUDA(launch_k(kb_colpass<T, OP>, B->ncol_units[pi], kThreads, B->smem_col[pi], s, true, cp,
+                     (const int2*)B->col_units[pi]));
+  IBDL_CUDA(launch_k(kb_rowifft_gather<T, OP>, B->nrow_units[pi], kThreads, B->smem_gather[pi], s, true, rp,
+                     (const int2*)B->row_units[pi], in_base, out_base));
   B->launches += 3;
   IBDL_CUDA(cudaGetLastError());
   return IBDL_OK;

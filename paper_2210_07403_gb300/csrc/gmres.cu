@@ -16,6 +16,7 @@
 #include <cooperative_groups.h>
 
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <algorithm>
@@ -123,6 +124,7 @@ constexpr int ATH = 512;
 template <bool STAGED, int CL>
 __device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, int nd, int m, int slice) {
   cg::cluster_group cluster = cg::this_cluster();
+  cudaGridDependencySynchronize();  // programmatic launch: wait for the application that wrote V_{j+1}
   if (j < 0) j = st->k;
   if (st->stop || j >= st->kmax || j >= m) return -1;
   extern __shared__ double dsm[];
@@ -509,6 +511,16 @@ static ibdl_status gmres_cycle_graph(Geometry* g, int prec, const double* r0, do
   return IBDL_OK;
 }
 
+// programmatic dependent launch of the Arnoldi step after the application (IBDL_NO_PDL=1: off)
+static bool pdl_allowed() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("IBDL_NO_PDL");
+    v = (e && atoi(e) != 0) ? 0 : 1;
+  }
+  return v == 1;
+}
+
 struct ArnoldiCfg {
   int cl;  // CTAs per cluster (16 or 8)
   int slice;
@@ -569,13 +581,15 @@ static cudaError_t launch_arnoldi_t(const ArnoldiCfg& c, GmresState* st, double*
   cfg.blockDim = dim3(ATH);
   cfg.dynamicSmemBytes = c.dyn;
   cfg.stream = s;
-  cudaLaunchAttribute at;
-  at.id = cudaLaunchAttributeClusterDimension;
-  at.val.clusterDim.x = CL;
-  at.val.clusterDim.y = 1;
-  at.val.clusterDim.z = 1;
-  cfg.attrs = &at;
-  cfg.numAttrs = 1;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_allowed() ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, k_arnoldi_cluster<STAGED, CL>, st, V, j, nd, m, c.slice, cond);
 }
 
@@ -905,13 +919,15 @@ static cudaError_t launch_kb_arnoldi(Batch* B, size_t dyn, cudaGraphConditionalH
   cfg.blockDim = dim3(ATH);
   cfg.dynamicSmemBytes = dyn;
   cfg.stream = s;
-  cudaLaunchAttribute at;
-  at.id = cudaLaunchAttributeClusterDimension;
-  at.val.clusterDim.x = CL;
-  at.val.clusterDim.y = 1;
-  at.val.clusterDim.z = 1;
-  cfg.attrs = &at;
-  cfg.numAttrs = 1;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_allowed() ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, kb_arnoldi<STAGED, CL>, static_cast<GmresState*>(B->st), B->V,
                             (const int64_t*)B->d_voff, (const int*)B->d_nd, (const int*)B->d_slice, B->m,
                             static_cast<BatchCtl*>(B->ctl), cond);
