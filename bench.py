@@ -46,6 +46,7 @@ def _config():
             "delta": "cos", "dipole": "analytic", "symbol": "spectral", "solve_rtol": SOLVE_RTOL,
             "precision": "mixed: fp32 applies, fp64 arnoldi + refinement", "inner_rtol": INNER_RTOL,
             "gmres": "restart 50, each cycle one CUDA graph with a device-side while loop",
+            "launch_shapes": "autotuned on the GPU before the warm-up",
             "l2": "flushed before each timed step (256 MiB write, untimed)", "seed": 2}
 
 
@@ -144,6 +145,26 @@ class ClockSampler:
 # our arm
 # ------------------------------------------------------------------------------------------
 
+def _stored_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture summary, if that capture
+    was taken on the current kernel source (the file records a hash of csrc/apply2d.cu + fft.cuh)."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for name in ("apply2d.cu", "fft.cuh"):
+            with open(os.path.join(ROOT, "paper_2210_07403_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+        if rec.get("source_sha256") != h.hexdigest():
+            return None
+        entry = rec.get("kernels", {}).get(kernel)
+        return None if entry is None else float(entry["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -169,6 +190,118 @@ def _kernel_bytes(stage: str, n: int, m: int) -> float:
     return 0.0
 
 
+def _event_ms(fn, K, flush, stream):
+    """K device-timed calls of fn, each after an untimed L2 flush; returns (median ms, last result)."""
+    import torch
+
+    ms, out = [], None
+    for _ in range(K):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms)), out
+
+
+def extra_workloads(dev, flush, stream, K=5):
+    """The other workload shapes (context, not the headline): the 64² circle, the 256-problem
+    ellipse batch (with its HBM roofline: the batch does not fit in L2) and the 128³ sphere."""
+    import torch
+
+    import ibdl_inputs as I
+    from paper_2210_07403_gb300 import Geometry
+    from paper_2210_07403_gb300.ibdl import Batch
+
+    out = {}
+    peak, _ = _peaks()
+    # 64² circle, Laplace, GMRES to 1e-10 (FP64)
+    p = I.circle_laplace(64, 100)
+    g = Geometry.from_problem(p)
+    ub = torch.from_numpy(p.Ub.reshape(-1).copy()).to(dev)
+    for _ in range(3):
+        g.solve(ub, rtol=1e-10)
+    t, (Q, info, _) = _event_ms(lambda: g.solve(ub, rtol=1e-10), K, flush, stream)
+    out["circle_laplace_64"] = {"fp64_solves_per_s": round(1e3 / t, 1), "iterations": info["iterations"],
+                                "rel_residual": info["rel_residual"]}
+    g.close()
+    # 256 ellipses, N ∈ {128, 256, 512}, λ ∈ [0, 100]: batched
+    probs = I.ellipse_batch(256)
+    B = Batch(probs)
+    B.autotune()
+    cells = sum(q.N ** 2 for q in probs)
+    ub = torch.from_numpy(np.concatenate([q.Ub.reshape(-1) for q in probs])).to(dev)
+    y = torch.empty_like(ub)
+    res = {"problems": len(probs), "grid_cells": cells, "points": B.total}
+    for prec in ("fp32", "fp64"):
+        for _ in range(3):
+            B.apply(ub, y, precision=prec)
+        t, _ = _event_ms(lambda: B.apply(ub, y, precision=prec), K, flush, stream)
+        w = 4 if prec == "fp32" else 8
+        achieved = 4 * cells * w / (t * 1e-3) / 1e9
+        res["apply_" + prec] = {"us": round(t * 1e3, 1), "algorithmic_bytes": 4 * cells * w,
+                                "achieved_GBps": round(achieved, 1), "frac_of_measured_hbm": round(achieved / peak, 4)}
+    for prec in ("fp64", "mixed"):
+        def run():
+            return B.solve(ub, rtol=SOLVE_RTOL, precision=prec, inner_rtol=INNER_RTOL)
+        for _ in range(2):
+            run()
+        t, (Q, infos, st) = _event_ms(run, K, flush, stream)
+        res["solve_" + prec] = {"problems_per_s": round(len(probs) / (t * 1e-3), 1), "ms_per_batch": round(t, 3),
+                                "max_iterations": max(i["iterations"] for i in infos),
+                                "max_rel_residual": max(i["rel_residual"] for i in infos), "status": st}
+    res["speedup_mixed_vs_fp64"] = round(res["solve_mixed"]["problems_per_s"] / res["solve_fp64"]["problems_per_s"], 3)
+    out["ellipse_batch_256"] = res
+    B.close()
+    # 128³ sphere, 12 000 points
+    p = I.sphere_poisson()
+    g = Geometry.from_problem(p)
+    ub = torch.from_numpy(p.Ub.reshape(-1).copy()).to(dev)
+    y = torch.empty_like(ub)
+    res = {}
+    for prec in ("fp32", "fp64"):
+        for _ in range(3):
+            g.apply(ub, y, precision=prec)
+        t, _ = _event_ms(lambda: g.apply(ub, y, precision=prec), K, flush, stream)
+        res["apply_" + prec + "_us"] = round(t * 1e3, 1)
+    for prec in ("fp64", "mixed"):
+        def run():
+            return g.solve(ub, rtol=SOLVE_RTOL, precision=prec, inner_rtol=INNER_RTOL)
+        for _ in range(2):
+            run()
+        t, (Q, info, st) = _event_ms(run, K, flush, stream)
+        res["solve_" + prec] = {"solves_per_s": round(1e3 / t, 1), "iterations": info["iterations"],
+                                "fp64_applies": info["fp64_applies"], "rel_residual": info["rel_residual"]}
+    res["speedup_mixed_vs_fp64"] = round(res["solve_mixed"]["solves_per_s"] / res["solve_fp64"]["solves_per_s"], 3)
+    out["sphere_128"] = res
+    g.close()
+    return out
+
+
+def cufft_compare(dev, stream):
+    """cuFFT (torch.fft) time for the transforms alone of one 512² Stokes application."""
+    import torch
+
+    res = {}
+    for name, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        x = torch.randn(3, N_GRID, N_GRID, dtype=dt, device=dev)
+        for _ in range(5):
+            torch.fft.irfft2(torch.fft.rfft2(x)[:2], s=(N_GRID, N_GRID))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(50):
+            torch.fft.irfft2(torch.fft.rfft2(x)[:2], s=(N_GRID, N_GRID))
+        e1.record(stream)
+        e1.synchronize()
+        res[name + "_us"] = round(e0.elapsed_time(e1) / 50 * 1e3, 1)
+    res["what"] = "torch.fft rfft2 of 3 fields + irfft2 of 2 fields at 512² (no spread, symbol or interpolation)"
+    return res
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
     import torch.distributed as dist
@@ -181,6 +314,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     dev = torch.device("cuda", local_rank)
     p = _problem()
     geom = Geometry.from_problem(p)
+    geom.autotune()  # launch shapes timed on this GPU (the parity tests run the same shapes)
     nd = 2 * p.bd.M
     ub = torch.from_numpy(p.Ub.reshape(-1).copy()).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -224,6 +358,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    if args.host_driven:
+        geom.set_stage_timing(True)
     with ClockSampler(local_rank) as clocks:
         t_wall0 = time.perf_counter()
         ms_mixed, outs = timed(lambda: solve("mixed"), K)
@@ -232,6 +368,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    if args.host_driven:
+        geom.set_stage_timing(False)
 
     err_mixed = max(float(torch.linalg.norm(q - q_ref) / torch.linalg.norm(q_ref)) for q, _, _ in outs)
     info_m = outs[-1][1]
@@ -274,6 +412,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     value = world * K / t_mixed
     e2e_value = world * K / t_e2e
+    extras = None if args.no_extras else extra_workloads(dev, flush, stream)
+    cufft = None if args.no_extras else cufft_compare(dev, stream)
 
     # dominant kernel of the timed mixed solves, and its average launch from the apply loop
     per_stage = {k: v for k, v in stages_mixed.items()}
@@ -284,7 +424,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     peak, peak_src = _peaks()
     achieved = bytes_dom / (dom_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
+            "frac": round(achieved / peak, 4), "traffic": _stored_traffic(dom), "peak_source": peak_src,
             "avg_launch_us": round(dom_ms * 1e3, 2), "algorithmic_bytes": int(bytes_dom),
             "note": "grid fields are L2-resident between kernels of one application (6 MB FP32)"}
 
@@ -319,7 +459,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "e2e": {"value": round(e2e_value, 3), "unit": "solves/s", "h2d_bytes_per_step": nd * 8,
                 "d2h_bytes_per_step": nd * 8, "error_vs_fp64_plain": err_e2e},
         "gpu_launches": launches,
+        "workloads": extras,
+        "cufft_transforms_only": cufft,
         "wall_s_timed_region": round(t_wall, 3),
+        "gmres_driver": "host (one launch per kernel)" if args.host_driven else "CUDA graph per cycle",
         "cpu_baseline": cpu,
     }
     geom.close()
@@ -355,6 +498,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workload shapes")
+    ap.add_argument("--host-driven", action="store_true",
+                    help="drive GMRES from the host with one launch per kernel (for profilers that do not "
+                         "see kernels inside CUDA-graph conditional bodies); slower")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     world = int(os.environ.get("WORLD_SIZE", "1"))

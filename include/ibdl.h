@@ -166,6 +166,14 @@ ibdl_status ibdl_evaluate_field(ibdl_geometry* geom, const double* Q, double* u_
  * max_refine 6, device I/O. */
 void ibdl_default_solve_opts(ibdl_solve_opts* opts);
 
+/* Autotuner (2-D; 3-D shapes follow a fixed volume rule): time candidate launch shapes of the
+ * operator application on this geometry (rows per row band 2–16, kx columns per column group
+ * 1–8, 256 or 512 threads) with CUDA events and keep the fastest, for FP64 (precision_mask bit
+ * 0) and/or FP32 (bit 1). The choice is cached in the process per grid size, field counts, PDE,
+ * dipole form and precision; geometries and batches created later with the same key start from
+ * it. Allocates and frees a small scratch vector. Synchronises `stream`. */
+ibdl_status ibdl_autotune(ibdl_geometry* geom, int precision_mask, void* stream);
+
 /* Geometry facts: number of density components c and points M. */
 ibdl_status ibdl_geometry_sizes(const ibdl_geometry* geom, int* ncomp, int64_t* n_points);
 
@@ -187,6 +195,12 @@ ibdl_status ibdl_destroy_batch(ibdl_batch* batch);
 /* Number of problems, the offsets (count + 1 entries, may be NULL) and the total length of the
  * concatenated boundary vectors. */
 ibdl_status ibdl_batch_sizes(const ibdl_batch* batch, int* count, int64_t* offsets, int64_t* total);
+
+/* Autotune a batch: time the whole batched application for each candidate FFT volume per CTA
+ * (512 to 8192 complex elements; every problem's rows per band and columns per group follow
+ * from it), keep the fastest per precision, and rebuild the batched launch tables. Allocates
+ * and frees a scratch vector. Synchronises `stream`. */
+ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* stream);
 
 /* Y = A Q for every problem of the batch (concatenated device FP64 arrays; FP64 or FP32 grid
  * arithmetic). Asynchronous. */

@@ -155,6 +155,25 @@ ibdl_status ibdl_geometry_sizes(const ibdl_geometry* geom, int* ncomp, int64_t* 
   return IBDL_OK;
 }
 
+ibdl_status ibdl_autotune(ibdl_geometry* geom, int precision_mask, void* stream) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (precision_mask < 1 || precision_mask > 3) return fail(IBDL_ERR_INVALID_ARG, "precision_mask must be 1, 2 or 3");
+  Geometry* g = geom->g;
+  if (g->dim != 2) return IBDL_OK;  // 3-D shapes come from the volume rule only
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nd = (size_t)g->ncomp * g->M;
+  double* buf = nullptr;
+  IBDL_CUDA(cudaMalloc((void**)&buf, sizeof(double) * 2 * nd));
+  ibdl_status st = IBDL_OK;
+  if (cudaMemsetAsync(buf, 0, sizeof(double) * nd, s) != cudaSuccess) st = fail(IBDL_ERR_CUDA, "memset");
+  for (int pi = 0; pi < 2 && st == IBDL_OK; ++pi)
+    if (precision_mask & (pi ? 2 : 1)) st = autotune_2d(g, pi, false, s, buf, buf + nd);
+  cudaStreamSynchronize(s);
+  cudaFree(buf);
+  return st;
+}
+
 ibdl_status ibdl_set_stage_timing(ibdl_geometry* geom, int enable) {
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");

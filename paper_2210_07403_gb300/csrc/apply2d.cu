@@ -15,7 +15,9 @@
 // holding (A_0, A_{n/2}), both real. Along y, the kx = 0 and kx = n/2 columns are therefore one
 // complex column a + i b with a, b real columns; the column pass separates them by Hermitian
 // symmetry before the symbol and repacks after it.
+#include <algorithm>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 #include <type_traits>
 #include <utility>
@@ -591,7 +593,7 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   ColParams<T> cp = col_params<T>(g, stop);
   const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
-  const int nt = g->threads ? g->threads : kThreads;
+  const int nt = g->threads[pi] ? g->threads[pi] : kThreads;
   k_spread_rowfft<T, OP><<<g->n / R, nt, s1, s>>>(rp);
   if (g->timing) timing_mark(g, s, st0);
   IBDL_CUDA(launch_k(k_colpass<T, OP>, (g->n / 2) / C, nt, s2, s, !g->timing, cp));
@@ -787,6 +789,124 @@ ibdl_status batch_prepare_2d(Batch* B) {
 
 // Band height R (rows per CTA, even) and kx columns per CTA C, per precision, within the
 // shared-memory limit for the widest field count this geometry uses.
+// ------------------------------------------------------------------------------------------
+// autotuner: time candidate launch shapes of the 2-D application on a geometry's own data and
+// keep the fastest; results are cached per (n, fields in, fields out, pde, dipole, precision)
+// so geometries created later with the same key start from the tuned shape
+// ------------------------------------------------------------------------------------------
+struct TuneKey {
+  int n, nf_in, nf_out, pde, dipole, pi;
+  bool operator==(const TuneKey& o) const {
+    return n == o.n && nf_in == o.nf_in && nf_out == o.nf_out && pde == o.pde && dipole == o.dipole && pi == o.pi;
+  }
+};
+struct TuneVal {
+  int R, C, threads;
+};
+static std::vector<std::pair<TuneKey, TuneVal>> g_tuned;
+static std::mutex g_tune_mu;
+
+static bool tuned_lookup(const TuneKey& k, TuneVal* v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (auto& e : g_tuned)
+    if (e.first == k) {
+      *v = e.second;
+      return true;
+    }
+  return false;
+}
+
+static void tuned_store(const TuneKey& k, const TuneVal& v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (auto& e : g_tuned)
+    if (e.first == k) {
+      e.second = v;
+      return;
+    }
+  g_tuned.push_back({k, v});
+}
+
+static TuneKey tune_key(const Geometry* g, int pi) { return {g->n, g->nf_in, g->nf_out, g->pde, g->dipole, pi}; }
+
+// Candidates R ∈ {2..16}, C ∈ {1..8} that fit shared memory and keep R ≤ n/2, and (unless
+// fixed_threads) 256 or 512 threads; each timed as the median of 5 applications after one warm-up.
+ibdl_status autotune_2d(Geometry* g, int pi, bool fixed_threads, cudaStream_t s, const double* Q, double* Y) {
+  const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
+  const size_t cs = pi ? sizeof(float2) : sizeof(double2);
+  auto row_bytes = [&](int r) { return (g->n + 2 * padded((size_t)nf * (r / 2) * g->n)) * cs; };
+  auto col_bytes = [&](int c) { return (g->n + 2 * padded((size_t)nf * c * g->n)) * cs + 2 * g->n * cs / 2; };
+  const int saved_R = g->rows_per_cta[pi], saved_C = g->cols_per_cta[pi], saved_T = g->threads[pi];
+  const int saved_timing = g->timing;
+  g->timing = 0;
+  cudaEvent_t e0, e1;
+  IBDL_CUDA(cudaEventCreate(&e0));
+  IBDL_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  TuneVal bestv{saved_R, saved_C, saved_T};
+  ibdl_status err = IBDL_OK;
+  const int threads_opts[2] = {256, 512};
+  for (int R = 2; R <= 16 && err == IBDL_OK; R *= 2) {
+    if (R > g->n / 2 || row_bytes(R) > kSmemLimit) continue;
+    for (int C = 1; C <= 8 && err == IBDL_OK; C *= 2) {
+      if (C > g->n / 2 || col_bytes(C) > kSmemLimit) continue;
+      for (int ti = 0; ti < 2 && err == IBDL_OK; ++ti) {
+        const int T = fixed_threads ? 0 : threads_opts[ti];
+        if (fixed_threads && ti == 1) break;
+        g->rows_per_cta[pi] = R;
+        g->cols_per_cta[pi] = C;
+        g->threads[pi] = T;
+        float ms[5];
+        err = apply_2d(g, pi ? IBDL_FP32 : IBDL_FP64, Q, Y, s, nullptr);
+        for (int k = 0; k < 5 && err == IBDL_OK; ++k) {
+          cudaEventRecord(e0, s);
+          err = apply_2d(g, pi ? IBDL_FP32 : IBDL_FP64, Q, Y, s, nullptr);
+          cudaEventRecord(e1, s);
+          if (cudaEventSynchronize(e1) != cudaSuccess) err = fail(IBDL_ERR_CUDA, "autotune: event synchronize");
+          cudaEventElapsedTime(&ms[k], e0, e1);
+        }
+        if (err != IBDL_OK) break;
+        std::sort(ms, ms + 5);
+        if (ms[2] < best) {
+          best = ms[2];
+          bestv = {R, C, T};
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g->timing = saved_timing;
+  g->rows_per_cta[pi] = bestv.R;
+  g->cols_per_cta[pi] = bestv.C;
+  g->threads[pi] = bestv.threads;
+  if (err == IBDL_OK) tuned_store(tune_key(g, pi), bestv);
+  return err;
+}
+
+// Shapes from the volume rule: about `target` complex elements of FFT per CTA, at least 16 row
+// bands and 16 column groups, R ≤ n/2 (distinct wrapped band rows), within shared memory.
+void shape_for_target_2d(Geometry* g, int pi, int target) {
+  const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
+  const int n = g->n;
+  auto clampp2 = [](int v, int lo, int hi) {
+    v = v < lo ? lo : (v > hi ? hi : v);
+    int r = 1;
+    while (r * 2 <= v) r *= 2;
+    return r;
+  };
+  const size_t cs = pi ? sizeof(float2) : sizeof(double2);
+  auto row_bytes = [&](int r) { return (g->n + 2 * padded((size_t)nf * (r / 2) * g->n)) * cs; };
+  auto col_bytes = [&](int c) { return (g->n + 2 * padded((size_t)nf * c * g->n)) * cs + 2 * g->n * cs / 2; };
+  int R = clampp2(2 * (target / (n * g->nf_in)), 2, n / 16 > 2 ? n / 16 : 2);
+  while (R > 2 && row_bytes(R) > kSmemLimit) R /= 2;
+  int C = clampp2(target / (n * nf), 1, n / 32 > 1 ? n / 32 : 1);
+  while (C > 1 && col_bytes(C) > kSmemLimit) C /= 2;
+  if (row_bytes(R) <= kSmemLimit && col_bytes(C) <= kSmemLimit) {
+    g->rows_per_cta[pi] = R;
+    g->cols_per_cta[pi] = C;
+  }
+}
+
 ibdl_status plan_2d(Geometry* g) {
   static bool attrs = false;  // opt in to large dynamic shared memory once per kernel instance
   if (!attrs) {
@@ -829,11 +949,17 @@ ibdl_status plan_2d(Geometry* g) {
     }
     g->rows_per_cta[pi] = R;
     g->cols_per_cta[pi] = C;
+    g->threads[pi] = 0;
+    TuneVal tv;
+    if (tuned_lookup(tune_key(g, pi), &tv)) {
+      g->rows_per_cta[pi] = tv.R;
+      g->cols_per_cta[pi] = tv.C;
+      g->threads[pi] = tv.threads;
+    }
   }
-  g->threads = 0;
   if (const char* e = getenv("IBDL_THREADS")) {
     const int v = atoi(e);
-    if (v >= 32 && v <= kThreads && v % 32 == 0) g->threads = v;
+    if (v >= 32 && v <= kThreads && v % 32 == 0) g->threads[0] = g->threads[1] = v;
   }
   if (g->rows_per_cta[0] == 0 && g->rows_per_cta[1] == 0)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT");

@@ -2,6 +2,7 @@
 // problem is an ordinary geometry (its own sorted tables, spectra and symbols); the batch adds
 // the per-problem parameter blocks and (problem, unit) tables of the batched launches, and the
 // batched GMRES state.
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -117,6 +118,63 @@ ibdl_status ibdl_batch_sizes(const ibdl_batch* batch, int* count, int64_t* offse
     for (int i = 0; i <= B->count; ++i) offsets[i] = B->off[i];
   if (total) *total = B->total;
   return IBDL_OK;
+}
+
+ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* stream) {
+  set_error("");
+  if (!batch || !batch->b) return fail(IBDL_ERR_INVALID_ARG, "batch is NULL");
+  if (precision_mask < 1 || precision_mask > 3) return fail(IBDL_ERR_INVALID_ARG, "precision_mask must be 1, 2 or 3");
+  Batch* B = batch->b;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* buf = nullptr;
+  IBDL_CUDA(cudaMalloc((void**)&buf, sizeof(double) * 2 * B->total));
+  ibdl_status st = IBDL_OK;
+  if (cudaMemsetAsync(buf, 0, sizeof(double) * B->total, s) != cudaSuccess) st = fail(IBDL_ERR_CUDA, "memset");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // one knob for the whole batch: the FFT volume per CTA of the shape rule, timed on the
+  // batched application itself (throughput, not one problem's latency)
+  const int targets[5] = {512, 1024, 2048, 4096, 8192};
+  for (int pi = 0; pi < 2 && st == IBDL_OK; ++pi) {
+    if (!(precision_mask & (pi ? 2 : 1))) continue;
+    float best = 1e30f;
+    int best_t = targets[0];
+    for (int ti = 0; ti < 5 && st == IBDL_OK; ++ti) {
+      for (int i = 0; i < B->count; ++i) shape_for_target_2d(B->geoms[i], pi, targets[ti]);
+      st = batch_prepare_2d(B);
+      if (st != IBDL_OK) break;
+      float ms[3];
+      st = batch_apply_2d(B, pi ? IBDL_FP32 : IBDL_FP64, 0, buf, buf + B->total, s);
+      for (int k = 0; k < 3 && st == IBDL_OK; ++k) {
+        cudaEventRecord(e0, s);
+        st = batch_apply_2d(B, pi ? IBDL_FP32 : IBDL_FP64, 0, buf, buf + B->total, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(IBDL_ERR_CUDA, "batch autotune: event synchronize");
+        cudaEventElapsedTime(&ms[k], e0, e1);
+      }
+      if (st != IBDL_OK) break;
+      std::sort(ms, ms + 3);
+      if (ms[1] < best) {
+        best = ms[1];
+        best_t = targets[ti];
+      }
+    }
+    if (st == IBDL_OK)
+      for (int i = 0; i < B->count; ++i) shape_for_target_2d(B->geoms[i], pi, best_t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(buf);
+  if (st != IBDL_OK) return st;
+  // rebuild the unit tables and parameter blocks (and the captured cycles) for the chosen shapes
+  for (int p = 0; p < 2; ++p)
+    if (B->exec[p]) {
+      cudaGraphExecDestroy(B->exec[p]);
+      B->exec[p] = nullptr;
+    }
+  return batch_prepare_2d(B);
 }
 
 ibdl_status ibdl_batch_apply(ibdl_batch* batch, int precision, const double* Q, double* Y, void* stream) {

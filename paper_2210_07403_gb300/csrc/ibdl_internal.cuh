@@ -112,7 +112,7 @@ struct Geometry {
   int cols_per_cta[2];   // kx columns per CTA in the column kernels (3-D: the y passes)
   int zcols_per_cta[2];  // 3-D: kx columns per CTA in the z pass
   size_t smem_row[2], smem_col[2], smem_row_inv[2];
-  int threads;           // threads per CTA of the 2-D kernels (0: the default)
+  int threads[2];        // threads per CTA of the 2-D kernels per precision (0: the default)
 
   // GMRES workspace (allocated lazily, sized for `krylov_m`)
   int krylov_m;
@@ -171,6 +171,8 @@ struct Batch {
 };
 
 ibdl_status batch_prepare_2d(Batch* B);
+ibdl_status autotune_2d(Geometry* g, int pi, bool fixed_threads, cudaStream_t s, const double* Q, double* Y);
+void shape_for_target_2d(Geometry* g, int pi, int target);
 size_t batch_state_bytes();  // sizeof the per-problem GMRES state (stop, status, k are its first ints)
 ibdl_status batch_apply_2d(Batch* B, int precision, int mode, const double* in_base, double* out_base,
                            cudaStream_t s);

@@ -84,6 +84,8 @@ SIGNATURES = {
     "ibdl_batch_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "ibdl_batch_solve": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(ibdl_solve_opts),
                                  POINTER(ibdl_solve_info), c_void_p]),
+    "ibdl_autotune": (c_int, [c_void_p, c_int, c_void_p]),
+    "ibdl_batch_autotune": (c_int, [c_void_p, c_int, c_void_p]),
     "ibdl_set_stage_timing": (c_int, [c_void_p, c_int]),
     "ibdl_get_stage_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
     "ibdl_last_error": (c_char_p, []),
@@ -202,6 +204,14 @@ def ibdl_batch_solve(batch, Ub: int, Q: int, opts: ibdl_solve_opts, infos, strea
     return _check(st) if check else st
 
 
+def ibdl_autotune(geom, precision_mask: int = 3, stream: int = 0) -> int:
+    return _check(load().ibdl_autotune(geom, int(precision_mask), c_void_p(stream)))
+
+
+def ibdl_batch_autotune(batch, precision_mask: int = 3, stream: int = 0) -> int:
+    return _check(load().ibdl_batch_autotune(batch, int(precision_mask), c_void_p(stream)))
+
+
 def ibdl_set_stage_timing(geom, enable: int) -> int:
     return _check(load().ibdl_set_stage_timing(geom, int(enable)))
 
@@ -263,6 +273,9 @@ class Batch:
             keep.append(k)
         self._h = ibdl_create_batch(descs, _stream_handle(stream))
         self.count, self.offsets, self.total = ibdl_batch_sizes(self._h)
+
+    def autotune(self, precision_mask: int = 3, stream=None):
+        ibdl_batch_autotune(self._h, precision_mask, _stream_handle(stream))
 
     def split(self, v):
         return [v[self.offsets[b]:self.offsets[b + 1]] for b in range(self.count)]
@@ -389,6 +402,9 @@ class Geometry:
         info = ibdl_solve_info()
         st = ibdl_solve(self._h, Ub.data_ptr(), Q.data_ptr(), o, info, _stream_handle(stream), check=check)
         return Q, info.as_dict(), st
+
+    def autotune(self, precision_mask: int = 3, stream=None):
+        ibdl_autotune(self._h, precision_mask, _stream_handle(stream))
 
     def set_stage_timing(self, enable: bool = True):
         ibdl_set_stage_timing(self._h, int(enable))

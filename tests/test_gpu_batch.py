@@ -88,3 +88,20 @@ def test_batch_ellipse_workload_sampled():
         ref = O.solve(O.geometry_from_problem(probs[b]), probs[b].Ub, 1e-12)
         sl = slice(B.offsets[b], B.offsets[b + 1])
         assert _rel(Q[sl], ref.x) < 1e-8
+
+
+def test_batch_autotune_keeps_parity():
+    from paper_2210_07403_gb300.ibdl import Batch
+
+    probs = _mixed_batch()
+    B = Batch(probs)
+    B.autotune()
+    q = np.random.default_rng(5).standard_normal(B.total)
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-5)):
+        y = B.apply(torch.from_numpy(q).cuda(), precision=prec).cpu().numpy()
+        for b, p in enumerate(probs):
+            sl = slice(B.offsets[b], B.offsets[b + 1])
+            assert _rel(y[sl], O.apply(O.geometry_from_problem(p), q[sl])) < tol
+    ub = torch.from_numpy(np.concatenate([p.Ub.reshape(-1) for p in probs])).cuda()
+    Q, infos, st = B.solve(ub, rtol=1e-10, precision="mixed")
+    assert st == 0

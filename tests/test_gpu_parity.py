@@ -161,6 +161,7 @@ def test_solve_stokes_full_size_fp64_and_mixed():
     (FP32 applies, FP64 Arnoldi and refinement) against the oracle's solution."""
     p = I.star_stokes()
     g = _geom(p)
+    g.autotune()  # the launch shapes bench.py times
     og = O.geometry_from_problem(p)
     ref = O.solve(og, p.Ub, 1e-12, maxit=80)
     ub = torch.from_numpy(p.Ub.reshape(-1)).cuda()
@@ -297,3 +298,18 @@ def test_3d_full_size_apply():
     q = np.random.default_rng(11).standard_normal(p.bd.M)
     y = g.apply(torch.from_numpy(q).cuda()).cpu().numpy()
     assert _rel(y, O.apply(O.geometry_from_problem(p), q)) < 1e-12
+
+
+@pytest.mark.parametrize("pde", ["scalar", "stokes"])
+def test_autotune_keeps_parity(pde):
+    """After the autotuner picks launch shapes, applications and solves still match the oracle."""
+    p = _scalar_problem(128, 201, "sqrt", "analytic", "spectral", 2.0) if pde == "scalar" else _stokes_problem(128, 200)
+    g = _geom(p)
+    g.autotune()
+    og = O.geometry_from_problem(p)
+    q = np.random.default_rng(9).standard_normal(p.ncomp * p.bd.M)
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-5)):
+        y = g.apply(torch.from_numpy(q).cuda(), precision=prec).cpu().numpy()
+        assert _rel(y, O.apply(og, q)) < tol
+    Q, info, _ = g.solve(torch.from_numpy(p.Ub.reshape(-1)).cuda(), rtol=1e-10)
+    assert _rel(Q.cpu().numpy(), O.solve(og, p.Ub, 1e-12, maxit=80).x) < 1e-9
