@@ -302,6 +302,21 @@ def cufft_compare(dev, stream):
     return res
 
 
+def aggregate_over_ranks(local_seconds, steps: int, world: int, device=None):
+    """Whole-job throughput of weak-scaled replicas: every rank solved `steps` problems; the job
+    took as long as the slowest rank. local_seconds: this rank's timed seconds (a list: timed
+    region, then e2e). Returns (values per entry = world·steps / max seconds, max seconds)."""
+    import torch
+
+    t = torch.tensor(list(local_seconds), dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    mx = [float(v) for v in t.tolist()]
+    return [world * steps / v for v in mx], mx
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
     import torch.distributed as dist
@@ -400,18 +415,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     ms_e2e, outs_e2e = timed(lambda: solve("mixed", host=True), K)
     err_e2e = max(float(torch.linalg.norm(q.to(dev) - q_ref) / torch.linalg.norm(q_ref)) for q, _, _ in outs_e2e)
 
-    # max over ranks
-    t_mixed = sum(ms_mixed) / 1e3
-    t_e2e = sum(ms_e2e) / 1e3
-    tt = torch.tensor([t_mixed, t_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    t_mixed, t_e2e = float(tt[0]), float(tt[1])
+    # max over ranks: every rank solved K replicas of the problem
+    (value, e2e_value), (t_mixed, t_e2e) = aggregate_over_ranks([sum(ms_mixed) / 1e3, sum(ms_e2e) / 1e3], K,
+                                                                 world, dev)
     if rank != 0:
         return None
-
-    value = world * K / t_mixed
-    e2e_value = world * K / t_e2e
     extras = None if args.no_extras else extra_workloads(dev, flush, stream)
     cufft = None if args.no_extras else cufft_compare(dev, stream)
 
