@@ -477,3 +477,117 @@ def domain_norms(u_err: np.ndarray, mask: np.ndarray, h: float, dim: int, omega:
     e = np.abs(u_err[mask])
     return (h ** dim / omega * e.sum(), math.sqrt(h ** dim / omega * (e * e).sum()),
             float(e.max()) if e.size else 0.0)
+
+
+# ----------------------------------------------------------------------------------------
+# gradients of a solve with respect to the data and the boundary (scalar operator, analytic
+# dipole): for Q = A(X, n, w)⁻¹ U_b and an objective J(Q) with g = ∂J/∂Q,
+#   λ = A⁻ᵀ g,  ∂J/∂U_b = λ,  ∂J/∂p = −λᵀ (∂A/∂p) Q  for p = X, n, w.
+# ----------------------------------------------------------------------------------------
+
+
+def ddphi_sqrt(r):
+    """φ'' of the √-Peskin kernel on each piece (even in r; jumps at |r| = 0, 1, 2 are harmless
+    almost everywhere)."""
+    a = np.abs(np.asarray(r, dtype=np.float64))
+    out = np.zeros_like(a)
+    m1 = a <= 1
+    m2 = (a > 1) & (a < 2)
+    s = np.sqrt(1 + 4 * a[m1] - 4 * a[m1] ** 2)
+    out[m1] = (-4 / s - (2 - 4 * a[m1]) * (4 - 8 * a[m1]) / (2 * s ** 3)) / 8
+    t = np.sqrt(-7 + 12 * a[m2] - 4 * a[m2] ** 2)
+    out[m2] = (4 / t + (6 - 4 * a[m2]) * (12 - 8 * a[m2]) / (2 * t ** 3)) / 8
+    return out
+
+
+def ddphi_cos(r):
+    r = np.asarray(r, dtype=np.float64)
+    return np.where(np.abs(r) < 2, -(np.pi ** 2 / 16) * np.cos(0.5 * np.pi * r), 0.0)
+
+
+KERNELS2 = {"sqrt": ddphi_sqrt, "cos": ddphi_cos}
+
+
+def transpose_apply(geom: Geometry, G: np.ndarray) -> np.ndarray:
+    """Aᵀ G (Euclidean transpose) = W A* W⁻¹ G with W = diag(Δs) and A* the Δs-weighted adjoint."""
+    G = np.asarray(G, dtype=np.float64).reshape(-1)
+    return geom.w * adjoint_apply(geom, G / geom.w)
+
+
+def solve_transpose(geom: Geometry, G: np.ndarray, rtol: float, maxit: int = 50) -> GmresResult:
+    """λ with Aᵀ λ = G, by GMRES on the transposed operator."""
+    return gmres(lambda v: transpose_apply(geom, v), np.asarray(G, dtype=np.float64).reshape(-1), rtol, maxit)
+
+
+def _stencil_weights(geom: Geometry):
+    """Per stencil offset: node index tuple, and per axis φ, φ', φ'' at r (φ'/h, φ''/h² in x)."""
+    g = geom.grid
+    phi, dphi = KERNELS[geom.delta]
+    ddphi = KERNELS2[geom.delta]
+    idx, r = _stencil(geom)
+    for off in _offsets(g.dim):
+        rr = [r[j, :, off[j]] for j in range(g.dim)]
+        yield (_node_index(idx, off), [phi(x) for x in rr], [dphi(x) / g.h for x in rr],
+               [ddphi(x) / g.h ** 2 for x in rr])
+
+
+def spread_unweighted(geom: Geometry, c: np.ndarray) -> np.ndarray:
+    """ψ_g = Σ_i c_i Φ(x_g − X_i) with Φ = Π_j φ(x_j/h) (no Δs, no h^−d)."""
+    out = np.zeros(geom.grid.shape)
+    for node, ph, _, _ in _stencil_weights(geom):
+        np.add.at(out, node, c * np.prod(ph, axis=0))
+    return out
+
+
+def gather_derivatives(geom: Geometry, u: np.ndarray):
+    """At every point: G_m = Σ_g u_g ∂_m Φ(x_g − X_i) and H_ml = Σ_g u_g ∂_m ∂_l Φ(x_g − X_i)
+    (derivatives with respect to the argument x_g − X_i). Shapes (d, M) and (d, d, M)."""
+    d, M = geom.grid.dim, geom.M
+    G = np.zeros((d, M))
+    H = np.zeros((d, d, M))
+    for node, ph, dph, ddph in _stencil_weights(geom):
+        ug = u[node]
+        for m in range(d):
+            G[m] += ug * np.prod([dph[j] if j == m else ph[j] for j in range(d)], axis=0)
+            for l in range(d):
+                if l == m:
+                    f = [ddph[j] if j == m else ph[j] for j in range(d)]
+                else:
+                    f = [dph[j] if j in (m, l) else ph[j] for j in range(d)]
+                H[m, l] += ug * np.prod(f, axis=0)
+    return G, H
+
+
+def param_gradient(geom: Geometry, Q: np.ndarray, lam: np.ndarray):
+    """Derivatives of L = λᵀ A(X, n, w) Q (scalar operator, analytic dipole spread):
+        (S*u)_j = Σ_g u_g Φ(x_g − X_j), u = −L⁻¹ f, f_g = Σ_k Δs_k Q_k n_k·∇δ_h(x_g − X_k).
+    With ψ = Σ_j λ_j Φ(x_g − X_j) and v = −L⁻¹ ψ (−L⁻¹ is symmetric), λᵀS*u = vᵀ f, so
+        ∂L/∂X_i = −λ_i Σ_g u_g ∇Φ(x_g − X_i) − Δs_i Q_i Σ_g v_g ∇∇δ_h(x_g − X_i) n_i,
+        ∂L/∂n_i = Δs_i Q_i Σ_g v_g ∇δ_h(x_g − X_i),
+        ∂L/∂Δs_i = Q_i n_i · Σ_g v_g ∇δ_h(x_g − X_i).
+    φ'' jumps where a node sits at a whole-number offset (√-Peskin |r| = 1 and 2, cosine
+    |r| = 2), so A is not differentiable in X_i for a point exactly on a grid line; the gradient
+    there takes the value of the piece that contains the offset (a set of measure zero).
+    Returns (dX (d, M), dn (d, M), dw (M,))."""
+    if geom.pde != "scalar" or geom.dipole != "analytic":
+        raise NotImplementedError("gradients are implemented for the scalar operator with the analytic dipole")
+    Q = np.asarray(Q, dtype=np.float64).reshape(-1)
+    lam = np.asarray(lam, dtype=np.float64).reshape(-1)
+    hd = geom.grid.h ** geom.grid.dim
+    u = field_scalar(geom, Q)
+    v = minus_Linv(geom, spread_unweighted(geom, lam))
+    Gu, _ = gather_derivatives(geom, u)
+    Gv, Hv = gather_derivatives(geom, v)
+    Gv, Hv = Gv / hd, Hv / hd
+    dX = -lam[None, :] * Gu - (geom.w * Q)[None, :] * np.einsum("mli,li->mi", Hv, geom.n)
+    dn = (geom.w * Q)[None, :] * Gv
+    dw = Q * np.sum(geom.n * Gv, axis=0)
+    return dX, dn, dw
+
+
+def solve_gradient(geom: Geometry, Ub: np.ndarray, dJdQ: np.ndarray, rtol: float = 1e-13):
+    """Q = A⁻¹U_b and the gradients of J with ∂J/∂Q = dJdQ: returns (Q, dUb, dX, dn, dw)."""
+    Q = solve(geom, Ub, rtol, maxit=200).x
+    lam = solve_transpose(geom, dJdQ, rtol, maxit=200).x
+    dX, dn, dw = param_gradient(geom, Q, lam)
+    return Q, lam, -dX, -dn, -dw

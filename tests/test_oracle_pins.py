@@ -510,3 +510,64 @@ def test_sphere_harmonic_converges():
         r = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)
         errs.append(np.abs(u - I.harmonic_3d(x, y, z))[r < 0.12].max())
     assert errs[0] > errs[1] > errs[2]
+
+
+# ----------------------------------------------------------------------------------------
+# gradients (adjoint solve and boundary derivatives)
+# ----------------------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("kind", ["sqrt", "cos"])
+def test_ddphi_is_second_derivative(kind):
+    _, dphi = O.KERNELS[kind]
+    d2 = O.KERNELS2[kind]
+    r = np.linspace(-2.2, 2.2, 881)
+    r = r[np.min(np.abs(r[:, None] - np.array([-2, -1, 0, 1, 2])[None, :]), 1) > 1e-3]
+    e = 1e-6
+    assert np.allclose(d2(r), (dphi(r + e) - dphi(r - e)) / (2 * e), atol=1e-7)
+
+
+def test_transpose_is_matrix_transpose():
+    geom, bd = _circle_geom(16, "sqrt", 2.0)
+    geom.w = geom.w * (1 + 0.3 * np.sin(np.arange(bd.M)))  # non-uniform weights
+    A = O.dense_operator(geom)
+    At = O.dense_operator(geom, O.transpose_apply)
+    assert np.allclose(At, A.T, atol=1e-12 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("delta,lam,dim", [("sqrt", 2.0, 2), ("cos", 0.0, 2), ("cos", 1.0, 3)])
+def test_gradient_against_finite_differences(delta, lam, dim):
+    """J = gᵀQ(U_b, X, n, w) with Q the solve: the adjoint gradients against central differences
+    in every argument (step 1e-6), perturbing one input at a time."""
+    if dim == 2:
+        geom, bd = _circle_geom(32, delta, lam)
+        Ub = I.harmonic_cubic(bd.X[0], bd.X[1])
+    else:
+        p = I.sphere_poisson(12, 120, delta=delta, lam=lam)
+        geom = O.geometry_from_problem(p)
+        Ub = p.Ub.reshape(-1)
+    rng = np.random.default_rng(17)
+    gvec = rng.standard_normal(geom.M)
+    # non-uniform weights and tilted normals make every term of the formulas matter; the jitter
+    # keeps points off grid lines, where φ'' jumps and A has a kink in X
+    geom.X = geom.X + 0.1 * geom.grid.h * rng.uniform(-1, 1, geom.X.shape)
+    geom.w = geom.w * (1 + 0.2 * rng.uniform(-1, 1, geom.M))
+    nn = geom.n + 0.2 * rng.standard_normal(geom.n.shape)
+    geom.n = nn / np.linalg.norm(nn, axis=0)
+    Q, dUb, dX, dn, dw = O.solve_gradient(geom, Ub, gvec)
+
+    def J(ub=Ub, X=geom.X, n=geom.n, w=geom.w):
+        g2 = O.Geometry(geom.grid, X, n, w, geom.delta, geom.dipole, geom.symbol, geom.pde, geom.lam)
+        return float(gvec @ O.solve(g2, ub, 1e-13, maxit=200).x)
+
+    e = 1e-6
+    for i in rng.choice(geom.M, 3, replace=False):
+        d = np.zeros(geom.M)
+        d[i] = e
+        assert (J(ub=Ub + d) - J(ub=Ub - d)) / (2 * e) == pytest.approx(dUb[i], rel=1e-6, abs=1e-9)
+        assert (J(w=geom.w + d) - J(w=geom.w - d)) / (2 * e) == pytest.approx(dw[i], rel=1e-5, abs=1e-8)
+        for m in range(dim):
+            D = np.zeros_like(geom.X)
+            D[m, i] = e
+            assert (J(X=geom.X + D) - J(X=geom.X - D)) / (2 * e) == pytest.approx(dX[m, i], rel=1e-5, abs=1e-8)
+            assert (J(n=geom.n + D) - J(n=geom.n - D)) / (2 * e) == pytest.approx(dn[m, i], rel=1e-5, abs=1e-8)
