@@ -48,6 +48,13 @@ static bool ranges_overlap(const void* a, const void* b, size_t bytes) {
   return pa < pb + bytes && pb < pa + bytes;
 }
 
+// [a, a + abytes) and [b, b + bbytes) intersect
+static bool spans_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + bbytes && pb < pa + abytes;
+}
+
 }  // namespace ibdl
 
 using namespace ibdl;
@@ -109,8 +116,13 @@ void ibdl_default_solve_opts(ibdl_solve_opts* o) {
   o->io_on_host = 0;
 }
 
-ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const ibdl_solve_opts* opts,
-                       ibdl_solve_info* info, void* stream) {
+}  // extern "C"
+
+namespace ibdl {
+
+// shared argument checks and dispatch of ibdl_solve (op = A) and ibdl_solve_transpose (op = Aᵀ)
+static ibdl_status solve_entry(ibdl_geometry* geom, const double* b, double* x, const ibdl_solve_opts* opts,
+                               ibdl_solve_info* info, void* stream, int op, const char* bname, const char* xname) {
   set_error("");
   if (info) std::memset(info, 0, sizeof(*info));
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
@@ -126,15 +138,69 @@ ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const i
     return fail(IBDL_ERR_INVALID_ARG, "unknown precision");
   if (o.precision == IBDL_MIXED && (!(o.inner_rtol > 0) || !(o.inner_rtol < 1) || o.max_refine < 1))
     return fail(IBDL_ERR_INVALID_ARG, "mixed precision needs inner_rtol in (0, 1) and max_refine >= 1");
-  if (!Ub || !Q) return fail(IBDL_ERR_INVALID_ARG, "U_b and Q are required");
+  if (!b || !x) return fail(IBDL_ERR_INVALID_ARG, std::string(bname) + " and " + xname + " are required");
+  if (op == OPK_AT && geom->g->pde != IBDL_PDE_SCALAR)
+    return fail(IBDL_ERR_UNSUPPORTED, "ibdl_solve_transpose: scalar PDE only");
   if (!o.io_on_host) {
-    IBDL_TRY(check_device_ptr(Ub, "U_b"));
-    IBDL_TRY(check_device_ptr(Q, "Q"));
+    IBDL_TRY(check_device_ptr(b, bname));
+    IBDL_TRY(check_device_ptr(x, xname));
   }
   const int64_t before = geom->g->launches;
-  ibdl_status st = solve_impl(geom->g, Ub, Q, &o, info, static_cast<cudaStream_t>(stream));
+  ibdl_status st = solve_impl(geom->g, b, x, &o, info, static_cast<cudaStream_t>(stream), op);
   if (info) info->kernel_launches = geom->g->launches - before;
   return st;
+}
+
+}  // namespace ibdl
+
+extern "C" {
+
+ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const ibdl_solve_opts* opts,
+                       ibdl_solve_info* info, void* stream) {
+  return solve_entry(geom, Ub, Q, opts, info, stream, OPK_A, "U_b", "Q");
+}
+
+ibdl_status ibdl_solve_transpose(ibdl_geometry* geom, const double* G, double* lambda, const ibdl_solve_opts* opts,
+                                 ibdl_solve_info* info, void* stream) {
+  return solve_entry(geom, G, lambda, opts, info, stream, OPK_AT, "G", "lambda");
+}
+
+ibdl_status ibdl_apply_transpose(ibdl_geometry* geom, int precision, const double* G, double* Z, void* stream) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
+  Geometry* g = geom->g;
+  if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_apply_transpose: scalar PDE only");
+  IBDL_TRY(check_device_ptr(G, "G"));
+  IBDL_TRY(check_device_ptr(Z, "Z"));
+  if (ranges_overlap(G, Z, sizeof(double) * g->M)) return fail(IBDL_ERR_INVALID_ARG, "G and Z overlap");
+  return apply_any(g, precision, G, Z, static_cast<cudaStream_t>(stream), nullptr, OPK_AT);
+}
+
+ibdl_status ibdl_solve_vjp(ibdl_geometry* geom, const double* Q, const double* lambda, double* dX, double* dn,
+                           double* dw, void* stream) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  Geometry* g = geom->g;
+  if (g->pde != IBDL_PDE_SCALAR || g->dipole != IBDL_DIPOLE_ANALYTIC)
+    return fail(IBDL_ERR_UNSUPPORTED, "ibdl_solve_vjp: scalar PDE with the analytic dipole only");
+  IBDL_TRY(check_device_ptr(Q, "Q"));
+  IBDL_TRY(check_device_ptr(lambda, "lambda"));
+  if (!dX && !dn && !dw) return IBDL_OK;
+  const size_t vb = sizeof(double) * g->M, mb = vb * g->dim;
+  double* outs[3] = {dX, dn, dw};
+  const size_t ob[3] = {mb, mb, vb};
+  const char* names[3] = {"dX", "dn", "dw"};
+  for (int k = 0; k < 3; ++k) {
+    if (!outs[k]) continue;
+    IBDL_TRY(check_device_ptr(outs[k], names[k]));
+    if (spans_overlap(outs[k], ob[k], Q, vb) || spans_overlap(outs[k], ob[k], lambda, vb))
+      return fail(IBDL_ERR_INVALID_ARG, std::string(names[k]) + " overlaps Q or lambda");
+    for (int l = 0; l < k; ++l)
+      if (outs[l] && spans_overlap(outs[k], ob[k], outs[l], ob[l]))
+        return fail(IBDL_ERR_INVALID_ARG, std::string(names[k]) + " overlaps " + names[l]);
+  }
+  return solve_vjp_impl(g, Q, lambda, dX, dn, dw, static_cast<cudaStream_t>(stream));
 }
 
 ibdl_status ibdl_evaluate_field(ibdl_geometry* geom, const double* Q, double* u_grid, void* stream) {

@@ -70,6 +70,10 @@ struct RowParams {
   const int* idx;     // optional: in += (*idx)·vstride, out += (*idx + 1)·vstride (Krylov basis)
   int vstride;
   int64_t io_off;     // batched launches: in = in_base + io_off, out = out_base + io_off
+  // adjoint ops only: 1 = the Euclidean transpose Aᵀ = W A* W⁻¹ (spread weight 1/h^d in place
+  // of Δs/h^d, gathered values multiplied by Δs = wscale·h^d)
+  int trans;
+  double hd;          // h^d
 };
 
 template <typename T>
@@ -193,7 +197,9 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
         atomicAdd(acc + 2 * pidx(e + 3 * half * n) + odd, c3 * pp);
       }
     } else {
-      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * ws * pp);  // plain spread of W
+      // plain spread of W (A*), or of W⁻¹λ, i.e. λ with weight 1/h^d (Aᵀ)
+      const T wsp = p.trans ? T(1.0 / p.hd) : ws;
+      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * wsp * pp);
     }
   }
   __syncthreads();
@@ -445,12 +451,12 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
     if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
       atomicAdd(pout + i, double(acc0));
       atomicAdd(pout + M + i, double(acc1));
-    } else if (OP == OP_ADJ_AN) {
-      // (S̃)* v = n · (kernel-gradient gather of v)
-      atomicAdd(pout + i, double(p.nrm[s]) * double(acc0) + double(p.nrm[M + s]) * double(acc1));
-    } else if (OP == OP_ADJ_SD) {
-      // (S̃)* v = −Σ_m n_m S*(∂_m v)
-      atomicAdd(pout + i, -(double(p.nrm[s]) * double(acc0) + double(p.nrm[M + s]) * double(acc1)));
+    } else if (OP == OP_ADJ_AN || OP == OP_ADJ_SD) {
+      // analytic: (S̃)* v = n · (kernel-gradient gather of v); spectral: −Σ_m n_m S*(∂_m v)
+      double val = double(p.nrm[s]) * double(acc0) + double(p.nrm[M + s]) * double(acc1);
+      if (OP == OP_ADJ_SD) val = -val;
+      if (p.trans) val *= double(p.wscale[s]) * p.hd;  // W (S̃)* … for Aᵀ
+      atomicAdd(pout + i, val);
     } else {
       atomicAdd(pout + i, double(acc0));
     }
@@ -491,6 +497,8 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.idx = nullptr;
   rp.vstride = 0;
   rp.io_off = 0;
+  rp.trans = 0;
+  rp.hd = g->h * g->h;
   return rp;
 }
 
@@ -579,7 +587,7 @@ static ibdl_status set_attrs_all() {
 
 template <typename T, int OP>
 static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream_t s, const int* stop,
-                          double* grid, const int* idx = nullptr, int vstride = 0) {
+                          double* grid, const int* idx = nullptr, int vstride = 0, int trans = 0) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi];
   if (R == 0 || C == 0)
@@ -590,6 +598,7 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   RowParams<T> rp = row_params<T>(g, in, out, stop, grid);
   rp.idx = idx;
   rp.vstride = vstride;
+  rp.trans = trans;
   ColParams<T> cp = col_params<T>(g, stop);
   const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
@@ -610,7 +619,12 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
 
 template <typename T>
 static ibdl_status apply_t(Geometry* g, const double* Q, double* Y, cudaStream_t s, const int* stop, double* grid,
-                           const int* idx = nullptr, int vstride = 0) {
+                           const int* idx = nullptr, int vstride = 0, int op = OPK_A) {
+  if (op == OPK_AT) {
+    if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "transpose: scalar PDE only");
+    return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<T, OP_ADJ_AN>(g, Q, Y, s, stop, grid, idx, vstride, 1)
+                                             : run_op<T, OP_ADJ_SD>(g, Q, Y, s, stop, grid, idx, vstride, 1);
+  }
   if (g->pde == IBDL_PDE_STOKES)
     return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<T, OP_STOKES_AN>(g, Q, Y, s, stop, grid, idx, vstride)
                                              : run_op<T, OP_STOKES_SD>(g, Q, Y, s, stop, grid, idx, vstride);
@@ -620,14 +634,23 @@ static ibdl_status apply_t(Geometry* g, const double* Q, double* Y, cudaStream_t
 
 // Y = A Q with Q = V + (*idx)·nd and Y = V + (*idx + 1)·nd read on the device (Krylov basis)
 ibdl_status apply_2d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
-                             const int* stop) {
-  return precision == IBDL_FP32 ? apply_t<float>(g, V, V, s, stop, nullptr, idx, nd)
-                                : apply_t<double>(g, V, V, s, stop, nullptr, idx, nd);
+                             const int* stop, int op) {
+  return precision == IBDL_FP32 ? apply_t<float>(g, V, V, s, stop, nullptr, idx, nd, op)
+                                : apply_t<double>(g, V, V, s, stop, nullptr, idx, nd, op);
 }
 
-ibdl_status apply_2d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s, const int* stop) {
-  return precision == IBDL_FP32 ? apply_t<float>(g, Q, Y, s, stop, nullptr)
-                                : apply_t<double>(g, Q, Y, s, stop, nullptr);
+ibdl_status apply_2d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s, const int* stop,
+                     int op) {
+  return precision == IBDL_FP32 ? apply_t<float>(g, Q, Y, s, stop, nullptr, nullptr, 0, op)
+                                : apply_t<double>(g, Q, Y, s, stop, nullptr, nullptr, 0, op);
+}
+
+// u = −L⁻¹ S̃Q (the forward op's grid field) and v = −L⁻¹(Σ_j λ_j δ_h(x − X_j)) (the transpose
+// op's grid field: λ spread with weight 1/h^d), both FP64 on [n][n]
+ibdl_status field_pair_2d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s) {
+  if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "boundary derivatives: scalar PDE only");
+  IBDL_TRY(apply_t<double>(g, Q, g->tmp_m, s, nullptr, u));
+  return apply_t<double>(g, lam, g->tmp_m, s, nullptr, v, nullptr, 0, OPK_AT);
 }
 
 ibdl_status field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s) {

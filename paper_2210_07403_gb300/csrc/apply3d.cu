@@ -55,6 +55,10 @@ struct Row3Params {
   double* grid;
   const int* idx;
   int vstride;
+  // adjoint ops only: 1 = the Euclidean transpose Aᵀ = W A* W⁻¹ (spread weight 1/h³ in place of
+  // Δs/h³, gathered values multiplied by Δs = wscale·h³)
+  int trans;
+  double hd;  // h³
 };
 
 struct Col3Params {
@@ -180,7 +184,8 @@ __global__ void __launch_bounds__(kThreads3) k3_spread_rowfft(Row3Params p) {
       atomicAdd(acc + 2 * pidx(e + half * n) + odd, q * nrm[M + s]);
       atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, q * nrm[2 * M + s]);
     } else {
-      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * ws * ppp);
+      const T wsp = p.trans ? T(1.0 / p.hd) : ws;  // A*: W; Aᵀ: W⁻¹λ
+      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * wsp * ppp);
     }
   }
   __syncthreads();
@@ -446,10 +451,11 @@ __global__ void __launch_bounds__(kThreads3) k3_rowifft_gather(Row3Params p) {
         }
       }
     }
-    if (OP == OP3_ADJ_AN) {
-      atomicAdd(pout + i, double(nrm[s]) * double(a0) + double(nrm[M + s]) * double(a1) + double(nrm[2 * M + s]) * double(a2));
-    } else if (OP == OP3_ADJ_SD) {
-      atomicAdd(pout + i, -(double(nrm[s]) * double(a0) + double(nrm[M + s]) * double(a1) + double(nrm[2 * M + s]) * double(a2)));
+    if (OP == OP3_ADJ_AN || OP == OP3_ADJ_SD) {
+      double val = double(nrm[s]) * double(a0) + double(nrm[M + s]) * double(a1) + double(nrm[2 * M + s]) * double(a2);
+      if (OP == OP3_ADJ_SD) val = -val;
+      if (p.trans) val *= double(static_cast<const T*>(p.wscale)[s]) * p.hd;
+      atomicAdd(pout + i, val);
     } else {
       atomicAdd(pout + i, double(a0));
     }
@@ -536,7 +542,7 @@ ibdl_status plan_3d(Geometry* g) {
 
 template <typename T, int OP>
 static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStream_t s, const int* stop, double* grid,
-                           const int* idx = nullptr, int vstride = 0) {
+                           const int* idx = nullptr, int vstride = 0, int trans = 0) {
   constexpr int NIN = Traits3<OP>::NIN, NOUT = Traits3<OP>::NOUT;
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi], Cz = g->zcols_per_cta[pi];
@@ -564,6 +570,8 @@ static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStrea
   rp.grid = grid;
   rp.idx = idx;
   rp.vstride = vstride;
+  rp.trans = trans;
+  rp.hd = g->h * g->h * g->h;
   Col3Params cp;
   cp.n = n;
   cp.log2n = rp.log2n;
@@ -602,21 +610,31 @@ static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStrea
 
 template <typename T>
 static ibdl_status apply3_t(Geometry* g, const double* Q, double* Y, cudaStream_t s, const int* stop, double* grid,
-                            const int* idx = nullptr, int vstride = 0) {
+                            const int* idx = nullptr, int vstride = 0, int op = OPK_A) {
   if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "3-D: scalar PDE only");
+  if (op == OPK_AT)
+    return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op3<T, OP3_ADJ_AN>(g, Q, Y, s, stop, grid, idx, vstride, 1)
+                                             : run_op3<T, OP3_ADJ_SD>(g, Q, Y, s, stop, grid, idx, vstride, 1);
   return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op3<T, OP3_SCALAR_AN>(g, Q, Y, s, stop, grid, idx, vstride)
                                            : run_op3<T, OP3_SCALAR_SD>(g, Q, Y, s, stop, grid, idx, vstride);
 }
 
-ibdl_status apply_3d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s, const int* stop) {
-  return precision == IBDL_FP32 ? apply3_t<float>(g, Q, Y, s, stop, nullptr)
-                                : apply3_t<double>(g, Q, Y, s, stop, nullptr);
+ibdl_status apply_3d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s, const int* stop,
+                     int op) {
+  return precision == IBDL_FP32 ? apply3_t<float>(g, Q, Y, s, stop, nullptr, nullptr, 0, op)
+                                : apply3_t<double>(g, Q, Y, s, stop, nullptr, nullptr, 0, op);
 }
 
 ibdl_status apply_3d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
-                             const int* stop) {
-  return precision == IBDL_FP32 ? apply3_t<float>(g, V, V, s, stop, nullptr, idx, nd)
-                                : apply3_t<double>(g, V, V, s, stop, nullptr, idx, nd);
+                             const int* stop, int op) {
+  return precision == IBDL_FP32 ? apply3_t<float>(g, V, V, s, stop, nullptr, idx, nd, op)
+                                : apply3_t<double>(g, V, V, s, stop, nullptr, idx, nd, op);
+}
+
+// u = −L⁻¹S̃Q and v = −L⁻¹(Σ_j λ_j δ_h(x − X_j)), FP64 on [n][n][n]
+ibdl_status field_pair_3d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s) {
+  IBDL_TRY(apply3_t<double>(g, Q, g->tmp_m, s, nullptr, u));
+  return apply3_t<double>(g, lam, g->tmp_m, s, nullptr, v, nullptr, 0, OPK_AT);
 }
 
 ibdl_status field_3d(Geometry* g, const double* Q, double* u, cudaStream_t s) {

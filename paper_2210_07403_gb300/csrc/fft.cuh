@@ -206,5 +206,22 @@ __device__ __forceinline__ double dphi_sqrt(double r) {
     d = (-2.0 - (6.0 - 4.0 * a) / sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) * 0.125;
   return r < 0.0 ? -d : d;
 }
+// second derivatives (even in r); at the joins |r| = 1 (√ form) and |r| = 2 the inner piece's value
+__device__ __forceinline__ double ddphi_cos(double r) {
+  const double c = 3.14159265358979323846 * 3.14159265358979323846 / 16.0;
+  return fabs(r) < 2.0 ? -c * cospi(0.5 * r) : 0.0;
+}
+__device__ __forceinline__ double ddphi_sqrt(double r) {
+  const double a = fabs(r);
+  if (a <= 1.0) {
+    const double q = 1.0 + 4.0 * a - 4.0 * a * a, sq = sqrt(q);
+    return (-4.0 / sq - (2.0 - 4.0 * a) * (4.0 - 8.0 * a) / (2.0 * q * sq)) * 0.125;
+  }
+  if (a < 2.0) {
+    const double q = -7.0 + 12.0 * a - 4.0 * a * a, sq = sqrt(q);
+    return (4.0 / sq + (6.0 - 4.0 * a) * (12.0 - 8.0 * a) / (2.0 * q * sq)) * 0.125;
+  }
+  return 0.0;
+}
 
 }  // namespace ibdl

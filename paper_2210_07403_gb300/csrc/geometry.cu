@@ -76,11 +76,12 @@ __global__ void k_sort_cells(int ncell, const int* __restrict__ start, int* __re
 }
 
 // kernel weights per sorted point: φ(r) and φ'(r)/h at r = (x_node − X)/h for the four
-// nodes of each axis; Δs/h^d; normals. FP64 values, and FP32 copies rounded from them.
+// nodes of each axis; Δs/h^d; normals. FP64 values, and FP32 copies rounded from them. When
+// dd is not NULL also φ''(r)/h² in FP64 (the boundary derivatives need it).
 __global__ void k_tables(int dim, int n, int M, int delta, const double* __restrict__ X,
                          const double* __restrict__ nrm, const double* __restrict__ w, double ox, double oy,
                          double oz, double h, const int* __restrict__ perm, int* __restrict__ base,
-                         PointTable<double> t64, PointTable<float> t32) {
+                         PointTable<double> t64, PointTable<float> t32, double* __restrict__ dd) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= M) return;
   const int i = perm[s];
@@ -97,6 +98,7 @@ __global__ void k_tables(int dim, int n, int M, int delta, const double* __restr
       t64.dphi[(j * 4 + a) * M + s] = dp;
       t32.phi[(j * 4 + a) * M + s] = (float)ph;
       t32.dphi[(j * 4 + a) * M + s] = (float)dp;
+      if (dd) dd[(j * 4 + a) * M + s] = (delta == IBDL_DELTA_SQRT ? ddphi_sqrt(r) : ddphi_cos(r)) / (h * h);
     }
     t64.nrm[j * M + s] = nrm[j * M + i];
     t32.nrm[j * M + s] = (float)nrm[j * M + i];
@@ -153,7 +155,7 @@ ibdl_status fill_geometry_tables(Geometry* g, const double* dX, const double* dN
   k_scatter<<<(M + tb - 1) / tb, tb, 0, s>>>(M, key, cursor, g->perm);
   k_sort_cells<<<(g->ncell + tb - 1) / tb, tb, 0, s>>>(g->ncell, g->cell_start, g->perm);
   k_tables<<<(M + tb - 1) / tb, tb, 0, s>>>(dim, n, M, g->delta, dX, dN, dW, g->origin[0], g->origin[1], g->origin[2],
-                                             g->h, g->perm, g->base, g->t64, g->t32);
+                                             g->h, g->perm, g->base, g->t64, g->t32, g->ddphi64);
   k_twiddles<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->tw64, g->tw32);
   k_symbols<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->box, g->symbol, g->lap64, g->der64, g->lap32, g->der32);
   IBDL_CUDA(cudaGetLastError());
@@ -174,10 +176,11 @@ static void free_geometry(Geometry* g) {
   if (!g) return;
   void* ptrs[] = {g->perm, g->base, g->cell_start, g->t64.phi, g->t64.dphi, g->t64.wscale, g->t64.nrm,
                   g->t32.phi, g->t32.dphi, g->t32.wscale, g->t32.nrm, g->spec, g->tw64, g->tw32,
-                  g->lap64, g->der64, g->lap32, g->der32, g->ubuf, g->tmp_m, g->V, g->gm, g->vec};
+                  g->lap64, g->der64, g->lap32, g->der32, g->ubuf, g->tmp_m, g->V, g->gm, g->vec,
+                  g->ddphi64, g->vjp_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
     if (g->cycle_exec[i]) cudaGraphExecDestroy(g->cycle_exec[i]);
   if (g->host_status) cudaFreeHost(g->host_status);
   if (g->ev) cudaEventDestroy(g->ev);
@@ -352,6 +355,7 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
     GTRY(dalloc(&g->t64.dphi, sizeof(double) * dim * 4 * M));
     GTRY(dalloc(&g->t64.wscale, sizeof(double) * M));
     GTRY(dalloc(&g->t64.nrm, sizeof(double) * dim * M));
+    GTRY(dalloc(&g->ddphi64, sizeof(double) * dim * 4 * M));
     GTRY(dalloc(&g->t32.phi, sizeof(float) * dim * 4 * M));
     GTRY(dalloc(&g->t32.dphi, sizeof(float) * dim * 4 * M));
     GTRY(dalloc(&g->t32.wscale, sizeof(float) * M));
@@ -375,7 +379,7 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
     k_scatter<<<(M + tb - 1) / tb, tb, 0, s>>>(M, key, cursor, g->perm);
     k_sort_cells<<<(g->ncell + tb - 1) / tb, tb, 0, s>>>(g->ncell, g->cell_start, g->perm);
     k_tables<<<(M + tb - 1) / tb, tb, 0, s>>>(dim, n, M, g->delta, dX, dN, dW, g->origin[0], g->origin[1],
-                                               g->origin[2], h, g->perm, g->base, g->t64, g->t32);
+                                               g->origin[2], h, g->perm, g->base, g->t64, g->t32, g->ddphi64);
     k_twiddles<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->tw64, g->tw32);
     k_symbols<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->box, g->symbol, g->lap64, g->der64, g->lap32, g->der32);
     GCUDA(cudaGetLastError());

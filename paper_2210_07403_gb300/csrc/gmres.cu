@@ -480,15 +480,15 @@ struct CycleResult {
   double res;
 };
 
-static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, cudaGraphExec_t* out);
+static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, int op, cudaGraphExec_t* out);
 
-static ibdl_status gmres_cycle_graph(Geometry* g, int prec, const double* r0, double* x, double target, int m,
-                                     int budget, cudaStream_t s, CycleResult* cr) {
-  const int pi = prec == IBDL_FP32 ? 1 : 0;
+static ibdl_status gmres_cycle_graph(Geometry* g, int prec, int op, const double* r0, double* x, double target,
+                                     int m, int budget, cudaStream_t s, CycleResult* cr) {
+  const int pi = 2 * op + (prec == IBDL_FP32 ? 1 : 0);
   if (!g->cycle_exec[pi] || g->cycle_m[pi] != m) {
     if (g->cycle_exec[pi]) cudaGraphExecDestroy(g->cycle_exec[pi]);
     g->cycle_exec[pi] = nullptr;
-    IBDL_TRY(build_cycle_graph(g, prec, m, &g->cycle_exec[pi]));
+    IBDL_TRY(build_cycle_graph(g, prec, m, op, &g->cycle_exec[pi]));
     g->cycle_m[pi] = m;
   }
   GmresState* st = reinterpret_cast<GmresState*>(g->gm);
@@ -604,8 +604,8 @@ static cudaError_t launch_arnoldi(const ArnoldiCfg& c, GmresState* st, double* V
 
 // A GMRES cycle as a CUDA graph: one conditional while node whose body is the operator
 // application on V_k (k read on the device) followed by the Arnoldi step, which sets the loop
-// condition. Built once per geometry, precision and restart length.
-static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, cudaGraphExec_t* out) {
+// condition. Built once per geometry, operator (A or Aᵀ), precision and restart length.
+static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, int op, cudaGraphExec_t* out) {
   *out = nullptr;
   const int nd = (int)(g->ncomp * g->M);
   GmresState* st = reinterpret_cast<GmresState*>(g->gm);
@@ -635,8 +635,8 @@ static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, cudaGraphExec
     capturing = true;
     const int saved_timing = g->timing;
     g->timing = 0;
-    ret = g->dim == 2 ? apply_2d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop)
-                      : apply_3d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop);
+    ret = g->dim == 2 ? apply_2d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop, op)
+                      : apply_3d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop, op);
     if (ret == IBDL_OK) {
       const cudaError_t le = launch_arnoldi(c, st, g->V, -1, nd, m, h, cs);
       if (le != cudaSuccess) ret = cuda_fail(le, "Arnoldi launch");
@@ -661,13 +661,13 @@ static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, cudaGraphExec
 }
 
 // One GMRES(m) cycle on right-hand side r0 from a zero correction, accumulating into x.
-static ibdl_status gmres_cycle(Geometry* g, int prec, const double* r0, double* x, double target, int m, int budget,
-                               cudaStream_t s, CycleResult* cr) {
+static ibdl_status gmres_cycle(Geometry* g, int prec, int op, const double* r0, double* x, double target, int m,
+                               int budget, cudaStream_t s, CycleResult* cr) {
   GmresState* st = reinterpret_cast<GmresState*>(g->gm);
   HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
   const int nd = (int)(g->ncomp * g->M);
   double* V = g->V;
-  if (!g->timing) return gmres_cycle_graph(g, prec, r0, x, target, m, budget, s, cr);
+  if (!g->timing) return gmres_cycle_graph(g, prec, op, r0, x, target, m, budget, s, cr);
   // host-driven loop (used while stage timing records an event around every kernel)
   const int steps = m < budget ? m : budget;
   ArnoldiCfg acfg;
@@ -684,7 +684,7 @@ static ibdl_status gmres_cycle(Geometry* g, int prec, const double* r0, double* 
   IBDL_CUDA(cudaEventRecord(evs[1], s));
   ibdl_status err = IBDL_OK;
   for (int j = 0; j < steps; ++j) {
-    err = apply_any(g, prec, V + (size_t)j * nd, V + (size_t)(j + 1) * nd, s, &st->stop);
+    err = apply_any(g, prec, V + (size_t)j * nd, V + (size_t)(j + 1) * nd, s, &st->stop, op);
     if (err != IBDL_OK) break;
     if (g->timing) timing_mark(g, s, -1);
     if (launch_arnoldi(acfg, st, V, j, nd, m, 0, s) != cudaSuccess) {
@@ -725,12 +725,12 @@ static ibdl_status gmres_cycle(Geometry* g, int prec, const double* r0, double* 
   return IBDL_OK;
 }
 
-// r = b − A₆₄ x, returns ‖r‖ (synchronous)
-static ibdl_status true_residual(Geometry* g, const double* b, const double* x, double* r, double* Ax, cudaStream_t s,
-                                 double* rnorm) {
+// r = b − A₆₄ x (or b − Aᵀ₆₄ x), returns ‖r‖ (synchronous)
+static ibdl_status true_residual(Geometry* g, int op, const double* b, const double* x, double* r, double* Ax,
+                                 cudaStream_t s, double* rnorm) {
   GmresState* st = reinterpret_cast<GmresState*>(g->gm);
   const int nd = (int)(g->ncomp * g->M);
-  IBDL_TRY(apply_any(g, IBDL_FP64, x, Ax, s, nullptr));
+  IBDL_TRY(apply_any(g, IBDL_FP64, x, Ax, s, nullptr, op));
   k_residual<<<1, 1024, 0, s>>>(st, b, Ax, r, nd);
   g->launches += 1;
   IBDL_CUDA(cudaGetLastError());
@@ -757,7 +757,7 @@ static double host_norm(Geometry* g, const double* v_dev, cudaStream_t s) {
 }
 
 ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solve_opts* o, ibdl_solve_info* info,
-                       cudaStream_t s) {
+                       cudaStream_t s, int op) {
   const auto t0 = std::chrono::steady_clock::now();
   const int m = o->restart;
   IBDL_TRY(ensure_workspace(g, m));
@@ -782,7 +782,7 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
     const double* rhs = b;
     while (!done) {
       CycleResult cr;
-      IBDL_TRY(gmres_cycle(g, o->precision, rhs, x, target, m, o->maxit - used, s, &cr));
+      IBDL_TRY(gmres_cycle(g, o->precision, op, rhs, x, target, m, o->maxit - used, s, &cr));
       used += cr.its;
       inf.sweeps += 1;
       if (o->precision == IBDL_FP32)
@@ -801,7 +801,7 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
       }
       // restart from the true residual
       double rn = 0;
-      IBDL_TRY(true_residual(g, b, x, r, d, s, &rn));
+      IBDL_TRY(true_residual(g, op, b, x, r, d, s, &rn));
       inf.fp64_applies += 1;
       inf.rel_residual = rn / bnorm;
       if (rn <= target) break;
@@ -820,7 +820,7 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
       const double* irhs = rhs;
       while (true) {
         CycleResult cr;
-        IBDL_TRY(gmres_cycle(g, IBDL_FP32, irhs, d, inner_target, m, o->maxit - used, s, &cr));
+        IBDL_TRY(gmres_cycle(g, IBDL_FP32, op, irhs, d, inner_target, m, o->maxit - used, s, &cr));
         used += cr.its;
         inf.fp32_applies += cr.its;
         if (cr.status == ST_NONFINITE) return fail(IBDL_ERR_NONFINITE, "non-finite value in the GMRES iteration");
@@ -828,7 +828,7 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
         // inner restart on the FP32 residual of the correction: r_in = rhs − A₃₂ d
         GmresState* st = reinterpret_cast<GmresState*>(g->gm);
         double* Ad = g->vec + 4 * (size_t)nd;
-        IBDL_TRY(apply_any(g, IBDL_FP32, d, Ad, s, nullptr));
+        IBDL_TRY(apply_any(g, IBDL_FP32, d, Ad, s, nullptr, op));
         inf.fp32_applies += 1;
         k_residual<<<1, 1024, 0, s>>>(st, rhs, Ad, g->tmp_m, nd);
         g->launches += 1;
@@ -841,7 +841,7 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
       g->launches += 1;
       IBDL_CUDA(cudaGetLastError());
       inf.sweeps += 1;
-      IBDL_TRY(true_residual(g, b, x, r, d, s, &rn));
+      IBDL_TRY(true_residual(g, op, b, x, r, d, s, &rn));
       inf.fp64_applies += 1;
       inf.rel_residual = rn / bnorm;
       if (!std::isfinite(rn)) return fail(IBDL_ERR_NONFINITE, "non-finite residual");

@@ -94,6 +94,7 @@ struct Geometry {
   int ncell;
   PointTable<double> t64;
   PointTable<float> t32;
+  double* ddphi64; // [dim][4][M] φ''(r)/h² in sorted order (boundary derivatives); may be NULL
 
   // workspace: half spectra, packed format (see apply kernels): [nf][rows][n/2] complex
   void* spec;      // sized for nf_in fields in FP64
@@ -106,6 +107,7 @@ struct Geometry {
   float *lap32, *der32;
   double* ubuf;    // evaluate_field / adjoint helpers: [c][n^dim] FP64
   double* tmp_m;   // [c*M] scratch boundary vector
+  double* vjp_buf; // boundary derivatives: grid fields u and v, allocated on first use
 
   // launch plan (2-D and 3-D)
   int rows_per_cta[2];   // band height R for the row kernels, per precision (0 = fp64, 1 = fp32)
@@ -122,9 +124,10 @@ struct Geometry {
   void* host_status;   // pinned
   cudaEvent_t ev;
 
-  // captured GMRES cycles (CUDA graph with a device-side while loop), per precision
-  cudaGraphExec_t cycle_exec[2];
-  int cycle_m[2];
+  // captured GMRES cycles (CUDA graph with a device-side while loop), per operator (A, Aᵀ)
+  // and precision: index 2·op + (0 fp64, 1 fp32)
+  cudaGraphExec_t cycle_exec[4];
+  int cycle_m[4];
 
   // counters and optional stage timing (events around every kernel)
   int64_t launches;
@@ -187,10 +190,13 @@ ibdl_status get_stage_times(Geometry* g, double* ms, int64_t* launches);
 // ------------------------------------------------------------------------------------------
 // launchers implemented in the .cu files
 // ------------------------------------------------------------------------------------------
+// operator selector: A, or its Euclidean transpose Aᵀ = W A* W⁻¹ (W = diag Δs; scalar PDE)
+enum { OPK_A = 0, OPK_AT = 1 };
+
 ibdl_status apply_2d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s,
-                     const int* stop_flag);
+                     const int* stop_flag, int op = OPK_A);
 ibdl_status apply_3d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s,
-                     const int* stop_flag);
+                     const int* stop_flag, int op = OPK_A);
 ibdl_status field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s);
 ibdl_status field_3d(Geometry* g, const double* Q, double* u, cudaStream_t s);
 ibdl_status adjoint_2d(Geometry* g, int precision, const double* W, double* Z, cudaStream_t s);
@@ -198,17 +204,22 @@ ibdl_status adjoint_3d(Geometry* g, int precision, const double* W, double* Z, c
 ibdl_status plan_2d(Geometry* g);
 ibdl_status plan_3d(Geometry* g);
 ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solve_opts* o,
-                       ibdl_solve_info* info, cudaStream_t s);
+                       ibdl_solve_info* info, cudaStream_t s, int op = OPK_A);
+// grid fields u = −L⁻¹S̃Q and v = −L⁻¹(Σ_j λ_j δ_h(x − X_j)), then the boundary derivatives
+ibdl_status field_pair_2d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s);
+ibdl_status field_pair_3d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s);
+ibdl_status solve_vjp_impl(Geometry* g, const double* Q, const double* lam, double* dX, double* dn, double* dw,
+                           cudaStream_t s);
 
 ibdl_status apply_2d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
-                             const int* stop);
+                             const int* stop, int op = OPK_A);
 ibdl_status apply_3d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
-                             const int* stop);
+                             const int* stop, int op = OPK_A);
 
 inline ibdl_status apply_any(Geometry* g, int precision, const double* Q, double* Y,
-                             cudaStream_t s, const int* stop_flag) {
-  return g->dim == 2 ? apply_2d(g, precision, Q, Y, s, stop_flag)
-                     : apply_3d(g, precision, Q, Y, s, stop_flag);
+                             cudaStream_t s, const int* stop_flag, int op = OPK_A) {
+  return g->dim == 2 ? apply_2d(g, precision, Q, Y, s, stop_flag, op)
+                     : apply_3d(g, precision, Q, Y, s, stop_flag, op);
 }
 
 }  // namespace ibdl

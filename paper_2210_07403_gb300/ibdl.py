@@ -88,6 +88,10 @@ SIGNATURES = {
     "ibdl_batch_autotune": (c_int, [c_void_p, c_int, c_void_p]),
     "ibdl_set_stage_timing": (c_int, [c_void_p, c_int]),
     "ibdl_get_stage_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
+    "ibdl_apply_transpose": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "ibdl_solve_transpose": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(ibdl_solve_opts),
+                                     POINTER(ibdl_solve_info), c_void_p]),
+    "ibdl_solve_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ibdl_last_error": (c_char_p, []),
 }
 
@@ -159,6 +163,22 @@ def ibdl_solve(geom, Ub: int, Q: int, opts: ibdl_solve_opts, info: ibdl_solve_in
     return _check(st) if check else st
 
 
+def ibdl_apply_transpose(geom, precision: int, G: int, Z: int, stream: int = 0) -> int:
+    return _check(load().ibdl_apply_transpose(geom, precision, c_void_p(G), c_void_p(Z), c_void_p(stream)))
+
+
+def ibdl_solve_transpose(geom, G: int, lam: int, opts: ibdl_solve_opts, info: ibdl_solve_info, stream: int = 0,
+                         check: bool = True) -> int:
+    st = load().ibdl_solve_transpose(geom, c_void_p(G), c_void_p(lam), byref(opts), byref(info), c_void_p(stream))
+    return _check(st) if check else st
+
+
+def ibdl_solve_vjp(geom, Q: int, lam: int, dX: int, dn: int, dw: int, stream: int = 0) -> int:
+    """Pointers may be 0 (NULL) for outputs that are not wanted."""
+    return _check(load().ibdl_solve_vjp(geom, c_void_p(Q), c_void_p(lam), c_void_p(dX or None),
+                                        c_void_p(dn or None), c_void_p(dw or None), c_void_p(stream)))
+
+
 def ibdl_evaluate_field(geom, Q: int, u_grid: int, stream: int = 0) -> int:
     return _check(load().ibdl_evaluate_field(geom, c_void_p(Q), c_void_p(u_grid), c_void_p(stream)))
 
@@ -228,6 +248,13 @@ def ibdl_last_error() -> str:
 
 
 # ---- convenience wrapper ------------------------------------------------------------------
+
+
+def _host(a):
+    """FP64 numpy view of a host array or a torch tensor (copied to the host if on a device)."""
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.asarray(a, dtype=np.float64)
 
 
 def _stream_handle(stream) -> int:
@@ -321,19 +348,23 @@ class Geometry:
         import torch
 
         self._torch = torch
-        X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
-        nrm = np.ascontiguousarray(np.asarray(normals, dtype=np.float64))
-        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+        on_device = all(isinstance(a, torch.Tensor) and a.is_cuda for a in (X, normals, weights))
+        if on_device:  # CUDA tensors: the library reads the boundary from device memory
+            X, nrm, w = (a.detach().to(torch.float64).contiguous() for a in (X, normals, weights))
+            ptrs = (X.data_ptr(), nrm.data_ptr(), w.data_ptr())
+        else:
+            X, nrm, w = (np.ascontiguousarray(_host(a)) for a in (X, normals, weights))
+            ptrs = (X.ctypes.data, nrm.ctypes.data, w.ctypes.data)
         dim, M = X.shape
         d = ibdl_geometry_desc()
         d.dim, d.n, d.box = dim, int(n), float(box)
         for j in range(3):
             d.origin[j] = float(origin[j]) if j < len(origin) else 0.0
         d.n_points = M
-        d.X, d.normals, d.weights = X.ctypes.data, nrm.ctypes.data, w.ctypes.data
+        d.X, d.normals, d.weights = ptrs
         d.pde, d.lambda_, d.mu = _PDE[pde], float(lam), float(mu)
         d.delta, d.dipole, d.symbol = _DELTA[delta], _DIPOLE[dipole], _SYMBOL[symbol]
-        d.inputs_on_device = 0
+        d.inputs_on_device = int(on_device)
         self.dim, self.n, self.M, self.pde = dim, int(n), M, pde
         self.ncomp = dim if pde == "stokes" else 1
         self._h = ibdl_create_geometry(d, _stream_handle(stream))
@@ -384,6 +415,36 @@ class Geometry:
               inner_rtol: float = 1e-4, max_refine: int = 6, Q=None, stream=None, check: bool = True):
         """Solve A Q = U_b. U_b on the device (torch float64) or a host numpy array / CPU tensor
         (then the copies happen inside the call, io_on_host). Returns (Q, info dict, status)."""
+        return self._solve(ibdl_solve, Ub, rtol, precision, restart, maxit, inner_rtol, max_refine, Q, stream,
+                           check)
+
+    def solve_transpose(self, G, rtol: float = 1e-8, precision: str = "fp64", restart: int = 50,
+                        maxit: int = 200, inner_rtol: float = 1e-4, max_refine: int = 6, lam=None, stream=None,
+                        check: bool = True):
+        """Solve Aᵀ λ = G (scalar PDE), same options as ``solve``. Returns (λ, info dict, status)."""
+        return self._solve(ibdl_solve_transpose, G, rtol, precision, restart, maxit, inner_rtol, max_refine, lam,
+                           stream, check)
+
+    def apply_transpose(self, G, Z=None, precision: str = "fp64", stream=None):
+        G = self._vec(G)
+        if Z is None:
+            Z = self._torch.empty_like(G)
+        ibdl_apply_transpose(self._h, _PREC[precision], G.data_ptr(), Z.data_ptr(), _stream_handle(stream))
+        return Z
+
+    def solve_vjp(self, Q, lam, stream=None, want=(True, True, True)):
+        """∂J/∂X, ∂J/∂n ([dim][M]) and ∂J/∂Δs ([M]) from the solution Q and the adjoint state
+        λ = A⁻ᵀ ∂J/∂Q; an entry of ``want`` that is False gives None for that output."""
+        t = self._torch
+        Q, lam = self._vec(Q), self._vec(lam)
+        outs = [t.empty((self.dim, self.M), dtype=t.float64, device=Q.device) if want[0] else None,
+                t.empty((self.dim, self.M), dtype=t.float64, device=Q.device) if want[1] else None,
+                t.empty((self.M,), dtype=t.float64, device=Q.device) if want[2] else None]
+        ptrs = [o.data_ptr() if o is not None else 0 for o in outs]
+        ibdl_solve_vjp(self._h, Q.data_ptr(), lam.data_ptr(), *ptrs, _stream_handle(stream))
+        return tuple(outs)
+
+    def _solve(self, entry, Ub, rtol, precision, restart, maxit, inner_rtol, max_refine, Q, stream, check):
         t = self._torch
         o = ibdl_default_solve_opts()
         o.rtol, o.restart, o.maxit, o.precision = rtol, restart, maxit, _PREC[precision]
@@ -400,7 +461,7 @@ class Geometry:
             if Q is None:
                 Q = t.empty_like(Ub)
         info = ibdl_solve_info()
-        st = ibdl_solve(self._h, Ub.data_ptr(), Q.data_ptr(), o, info, _stream_handle(stream), check=check)
+        st = entry(self._h, Ub.data_ptr(), Q.data_ptr(), o, info, _stream_handle(stream), check=check)
         return Q, info.as_dict(), st
 
     def autotune(self, precision_mask: int = 3, stream=None):
