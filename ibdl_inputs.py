@@ -260,6 +260,37 @@ def star_stokes(N: int = 512, M: int = 800, seed: int = 2, delta: str = "cos",
                    meta={"removed_flux": flux, "seed": seed})
 
 
+def star_probes(n_probes: int = 64, N: int = 1024, min_dist_h: float = 8.0, seed: int = 5,
+                a: float = 0.25, eps: float = 0.2, k: int = 5, center=(0.5, 0.5)) -> np.ndarray:
+    """Probe points inside the star r(θ) = a(1 + eps cos kθ), uniform in area, at distance at
+    least min_dist_h·h (h = 1/N) from the curve (distance to 2¹⁶ samples of the curve).
+    Shape (2, n_probes)."""
+    rng = np.random.default_rng(seed)
+    th = np.linspace(0, 2 * np.pi, 1 << 16, endpoint=False)
+    rc = a * (1 + eps * np.cos(k * th))
+    curve = np.stack([center[0] + rc * np.cos(th), center[1] + rc * np.sin(th)])
+    rmax = a * (1 + eps)
+    out = []
+    while len(out) < n_probes:
+        x = center[0] + rmax * rng.uniform(-1, 1)
+        y = center[1] + rmax * rng.uniform(-1, 1)
+        t = np.arctan2(y - center[1], x - center[0])
+        if np.hypot(x - center[0], y - center[1]) >= a * (1 + eps * np.cos(k * t)):
+            continue
+        if np.min(np.hypot(curve[0] - x, curve[1] - y)) < min_dist_h / N:
+            continue
+        out.append((x, y))
+    return np.array(out).T
+
+
+def star_stokes_probes(N: int = 1024, M: int = 1600, n_probes: int = 64, probe_seed: int = 5,
+                       **kw) -> tuple[Problem, np.ndarray]:
+    """The differentiation workload: the Stokes star problem at N², M points (same data recipe
+    as ``star_stokes``) and n_probes probes inside the star at ≥ 8h from it. The objective is
+    J = Σ_p |u(p)|² with u(p) the δ_h interpolation of the grid velocity."""
+    return star_stokes(N, M, **kw), star_probes(n_probes, N, seed=probe_seed)
+
+
 def sphere_poisson(N: int = 128, M: int = 12000, delta: str = "cos", lam: float = 0.0,
                    dipole: str = "analytic", symbol: str = "spectral") -> Problem:
     """3-D Laplace on the unit periodic box: sphere R = 0.25 about (0.5,0.5,0.5), Fibonacci

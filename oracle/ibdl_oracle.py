@@ -509,7 +509,10 @@ KERNELS2 = {"sqrt": ddphi_sqrt, "cos": ddphi_cos}
 
 
 def transpose_apply(geom: Geometry, G: np.ndarray) -> np.ndarray:
-    """Aᵀ G (Euclidean transpose) = W A* W⁻¹ G with W = diag(Δs) and A* the Δs-weighted adjoint."""
+    """Aᵀ G (Euclidean transpose). Scalar: W A* W⁻¹ G with W = diag(Δs) and A* the Δs-weighted
+    adjoint; Stokes: ``stokes_transpose_apply``."""
+    if geom.pde == "stokes":
+        return stokes_transpose_apply(geom, G)
     G = np.asarray(G, dtype=np.float64).reshape(-1)
     return geom.w * adjoint_apply(geom, G / geom.w)
 
@@ -589,5 +592,126 @@ def solve_gradient(geom: Geometry, Ub: np.ndarray, dJdQ: np.ndarray, rtol: float
     """Q = A⁻¹U_b and the gradients of J with ∂J/∂Q = dJdQ: returns (Q, dUb, dX, dn, dw)."""
     Q = solve(geom, Ub, rtol, maxit=200).x
     lam = solve_transpose(geom, dJdQ, rtol, maxit=200).x
-    dX, dn, dw = param_gradient(geom, Q, lam)
+    grad = param_gradient if geom.pde == "scalar" else stokes_param_gradient
+    dX, dn, dw = grad(geom, Q, lam)
     return Q, lam, -dX, -dn, -dw
+
+
+# ----------------------------------------------------------------------------------------
+# Stokes: transpose and boundary derivatives; values and derivatives at probe points
+# ----------------------------------------------------------------------------------------
+# Both operators are A Q = S*(K[s(Q); g(Q)]) + ½Q with K a Fourier multiplier and the spread
+# sources linear in Q:
+#   scalar  f = Σ_i w_i Q_i n_i·∇δ_h(x − X_i),                         K = −L⁻¹ (Sec. 5.3.2)
+#   Stokes  s = Σ_i w_i (Q_i·n_i) δ_h,  g_m = Σ_i w_i Σ_k A_mk,i ∂_kδ_h,   A = Q nᵀ + n Qᵀ,
+#           K[s; g] = F⁻¹[(i k̃ ŝ + P̂ ĝ)/|k|²],  P̂ = I − k̃k̃ᵀ/|k|²    (Sec. 6.3.3, η = 0)
+# With the plain grid sum as inner product, the transpose of a real multiplier with symbol σ(k)
+# has symbol conj σ(k); the transpose of S* is the unweighted spread ψ = Σ_i μ_i Φ(x − X_i).
+
+
+def _multiplier_T(geom: Geometry, psi):
+    """Kᵀψ for ψ of shape (c, grid): scalar → [v] with v = −L⁻¹ψ (real even symbol);
+    Stokes → [v_s, v_g1, …, v_gd] with v̂_s = −i k̃·ψ̂/|k|², v̂_g = P̂ψ̂/|k|²."""
+    if geom.pde == "scalar":
+        return [minus_Linv(geom, psi[0])]
+    g = geom.grid
+    d = g.dim
+    lap, der = symbols(g, geom.symbol)
+    nz = lap != 0
+    inv = np.zeros(g.shape)
+    inv[nz] = 1.0 / lap[nz]
+    kt = [-1j * der[l] for l in range(d)]  # k̃_l (real values), i k̃_l = der[l]
+    P = [np.fft.fftn(psi[l]) for l in range(d)]
+    kp = sum(kt[l] * P[l] for l in range(d))
+    vs = np.real(np.fft.ifftn(-1j * kp * inv))
+    vg = [np.real(np.fft.ifftn((P[m] - kt[m] * kp * inv) * inv)) for m in range(d)]
+    return [vs] + vg
+
+
+def _spread_terms(geom: Geometry, Q: np.ndarray, v):
+    """For the spread sources of Q (analytic dipole) and adjoint grid fields v = Kᵀψ, the
+    pieces of ⟨v, sources(Q)⟩:
+        dQ = ∂/∂Q (the spread transpose), dX, dn, dw = ∂/∂X, ∂/∂n, ∂/∂Δs at fixed Q.
+    Shapes: dQ (c, M), dX and dn (d, M), dw (M,)."""
+    if geom.dipole != "analytic":
+        raise NotImplementedError("derivatives are implemented for the analytic dipole spread")
+    d, M = geom.grid.dim, geom.M
+    hd = geom.grid.h ** d
+    ws = geom.w / hd
+    n = geom.n
+    if geom.pde == "scalar":
+        q = Q.reshape(M)
+        G, H = gather_derivatives(geom, v[0])
+        dQ = (ws * np.sum(n * G, axis=0))[None, :]
+        dX = -(ws * q)[None, :] * np.einsum("mli,li->mi", H, n)
+        dn = (ws * q)[None, :] * G
+        dw = q * np.sum(n * G, axis=0) / hd
+        return dQ, dX, dn, dw
+    Q = Q.reshape(d, M)
+    c = np.sum(Q * n, axis=0)
+    A = np.array([[Q[m] * n[k] + Q[k] * n[m] for k in range(d)] for m in range(d)])  # (d, d, M)
+    a_s = interp(geom, v[0])
+    Gs, _ = gather_derivatives(geom, v[0])
+    G, H = zip(*[gather_derivatives(geom, v[1 + m]) for m in range(d)])
+    G, H = np.array(G), np.array(H)  # G[m, k] = Σ v_gm ∂_kΦ, H[m, k, j] = Σ v_gm ∂_k∂_jΦ
+    dQ = np.array([ws * (n[l] * a_s + sum(n[k] * (G[l, k] + G[k, l]) for k in range(d))) for l in range(d)])
+    dX = -ws[None, :] * (c[None, :] * Gs + np.einsum("mki,mkji->ji", A, H))
+    dn = ws[None, :] * np.array([Q[j] * a_s + sum(Q[m] * G[m, j] for m in range(d))
+                                 + sum(Q[k] * G[j, k] for k in range(d)) for j in range(d)])
+    dw = (c * a_s + np.einsum("mki,mki->i", A, G)) / hd
+    return dQ, dX, dn, dw
+
+
+def stokes_transpose_apply(geom: Geometry, mu: np.ndarray) -> np.ndarray:
+    """Aᵀμ for the Stokes operator: ½μ + (spread transpose)(Kᵀ Σ_i μ_i Φ(x − X_i))."""
+    d, M = geom.grid.dim, geom.M
+    mu = np.asarray(mu, dtype=np.float64).reshape(d, M)
+    psi = [spread_unweighted(geom, mu[l]) for l in range(d)]
+    dQ, _, _, _ = _spread_terms(geom, np.zeros(d * M), _multiplier_T(geom, psi))
+    return (0.5 * mu + dQ).reshape(-1)
+
+
+def stokes_param_gradient(geom: Geometry, Q: np.ndarray, mu: np.ndarray):
+    """Derivatives of L = μᵀ A(X, n, w) Q for the Stokes operator (analytic dipole):
+    the interpolation term −Σ_l μ_{l,i} Σ_g u_l ∇Φ(x_g − X_i) with u the velocity of Q, plus the
+    spread terms of ⟨Kᵀψ, sources(Q)⟩ with ψ_l = Σ_j μ_{l,j} Φ(x − X_j)."""
+    d, M = geom.grid.dim, geom.M
+    Q = np.asarray(Q, dtype=np.float64).reshape(d, M)
+    mu = np.asarray(mu, dtype=np.float64).reshape(d, M)
+    u = stokes_velocity(geom, Q.reshape(-1))
+    dX = np.zeros((d, M))
+    for l in range(d):
+        Gu, _ = gather_derivatives(geom, u[l])
+        dX -= mu[l][None, :] * Gu
+    psi = [spread_unweighted(geom, mu[l]) for l in range(d)]
+    _, sX, sn, sw = _spread_terms(geom, Q, _multiplier_T(geom, psi))
+    return dX + sX, sn, sw
+
+
+def probe_geometry(geom: Geometry, P: np.ndarray) -> Geometry:
+    """The probe points P (d, n_p) as a point set on the same grid (normals and weights unused)."""
+    P = np.asarray(P, dtype=np.float64)
+    nrm = np.zeros_like(P)
+    nrm[0] = 1.0
+    return Geometry(geom.grid, P, nrm, np.ones(P.shape[1]), geom.delta, geom.dipole, geom.symbol, geom.pde,
+                    geom.lam, geom.mu)
+
+
+def probe_evaluate(geom: Geometry, P: np.ndarray, Q: np.ndarray) -> np.ndarray:
+    """E Q: the grid solution of Q (Sec. 5.1.2 step 2) interpolated at the probes with δ_h,
+    u(p) = Σ_g u_g δ_h(x_g − p) h^d. Shape (c, n_p)."""
+    pg = probe_geometry(geom, P)
+    u = grid_field(geom, np.asarray(Q, dtype=np.float64))
+    if geom.pde == "scalar":
+        return interp(pg, u)[None, :]
+    return np.array([interp(pg, u[l]) for l in range(geom.grid.dim)])
+
+
+def probe_vjp(geom: Geometry, P: np.ndarray, Q: np.ndarray, nu: np.ndarray):
+    """For ν of shape (c, n_p): (Eᵀν, ∂(νᵀ E Q)/∂X, ∂/∂n, ∂/∂Δs) with E = E(X, n, Δs) and the
+    probes fixed. Eᵀν spreads ν at the probes (unweighted), applies Kᵀ and the spread transpose."""
+    pg = probe_geometry(geom, P)
+    c = geom.ncomp
+    nu = np.asarray(nu, dtype=np.float64).reshape(c, -1)
+    psi = [spread_unweighted(pg, nu[l]) for l in range(c)]
+    return _spread_terms(geom, np.asarray(Q, dtype=np.float64), _multiplier_T(geom, psi))

@@ -571,3 +571,105 @@ def test_gradient_against_finite_differences(delta, lam, dim):
             D[m, i] = e
             assert (J(X=geom.X + D) - J(X=geom.X - D)) / (2 * e) == pytest.approx(dX[m, i], rel=1e-5, abs=1e-8)
             assert (J(n=geom.n + D) - J(n=geom.n - D)) / (2 * e) == pytest.approx(dn[m, i], rel=1e-5, abs=1e-8)
+
+
+def _star_geom(N, M, seed, tilt=0.2):
+    """Small Stokes star with points off grid lines, tilted normals and uneven weights."""
+    p = I.star_stokes(N, M)
+    g = O.geometry_from_problem(p)
+    rng = np.random.default_rng(seed)
+    g.X = g.X + 0.1 * g.grid.h * rng.uniform(-1, 1, g.X.shape)
+    nn = g.n + tilt * rng.standard_normal(g.n.shape)
+    g.n = nn / np.linalg.norm(nn, axis=0)
+    g.w = g.w * (1 + 0.2 * rng.uniform(-1, 1, g.M))
+    return g, p.Ub.reshape(-1), rng
+
+
+def test_stokes_transpose_is_matrix_transpose():
+    geom, _, _ = _star_geom(16, 30, 1)
+    A = O.dense_operator(geom)
+    At = O.dense_operator(geom, O.transpose_apply)
+    assert np.allclose(At, A.T, atol=1e-12 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("pde", ["scalar", "stokes"])
+def test_probe_transpose_is_matrix_transpose(pde):
+    """Eᵀν from probe_vjp against the dense matrix of Q ↦ E Q assembled column by column."""
+    if pde == "stokes":
+        geom, _, rng = _star_geom(16, 30, 2)
+    else:
+        geom, bd = _circle_geom(16, "sqrt", 1.0)
+        rng = np.random.default_rng(2)
+    P = 0.5 + 0.1 * rng.uniform(-1, 1, (2, 5))
+    nd = geom.ncomp * geom.M
+    E = np.stack([O.probe_evaluate(geom, P, np.eye(nd)[j]).reshape(-1) for j in range(nd)], axis=1)
+    nu = rng.standard_normal(E.shape[0])
+    dQ, _, _, _ = O.probe_vjp(geom, P, np.zeros(nd), nu)
+    assert np.allclose(dQ.reshape(-1), E.T @ nu, atol=1e-12 * np.abs(E).max() * np.abs(nu).sum())
+
+
+def _fd_check(J, args, grads, idx, rng, e=1e-6, rel=1e-5, abs_=1e-8):
+    """Central differences of J in entries (component m, point i) of each named argument."""
+    for name, a in args.items():
+        g = grads[name]
+        for i in idx:
+            for m in range(a.shape[0] if a.ndim == 2 else 1):
+                D = np.zeros_like(a)
+                if a.ndim == 2:
+                    D[m, i] = e
+                else:
+                    D[i] = e
+                fd = (J(**{name: a + D}) - J(**{name: a - D})) / (2 * e)
+                ref = g[m, i] if a.ndim == 2 else g[i]
+                assert fd == pytest.approx(ref, rel=rel, abs=abs_), (name, m, i)
+
+
+def test_stokes_gradient_against_finite_differences():
+    geom, Ub, rng = _star_geom(32, 60, 3)
+    gvec = rng.standard_normal(2 * geom.M)
+    Q, dUb, dX, dn, dw = O.solve_gradient(geom, Ub, gvec)
+
+    def J(ub=Ub, X=geom.X, n=geom.n, w=geom.w):
+        g2 = O.Geometry(geom.grid, X, n, w, geom.delta, geom.dipole, geom.symbol, geom.pde, geom.lam, geom.mu)
+        return float(gvec @ O.solve(g2, ub, 1e-13, maxit=300).x)
+
+    idx = rng.choice(geom.M, 3, replace=False)
+    for i in idx:
+        for m in range(2):
+            d = np.zeros(2 * geom.M)
+            d[m * geom.M + i] = 1e-6
+            assert (J(ub=Ub + d) - J(ub=Ub - d)) / 2e-6 == pytest.approx(dUb[m * geom.M + i], rel=1e-6, abs=1e-9)
+    _fd_check(J, {"X": geom.X, "n": geom.n, "w": geom.w}, {"X": dX, "n": dn, "w": dw}, idx, rng)
+
+
+@pytest.mark.parametrize("pde", ["scalar", "stokes"])
+def test_probe_objective_gradient_against_finite_differences(pde):
+    """J = Σ_p |u(p)|² with Q = A⁻¹U_b: the gradient assembled from probe_vjp (ν = 2u(p)) and the
+    adjoint solve with ∂J/∂Q = Eᵀν, against central differences in U_b, X, n and Δs."""
+    if pde == "stokes":
+        geom, Ub, rng = _star_geom(32, 60, 4)
+        P = I.star_probes(6, 32, min_dist_h=2.0, seed=5)
+    else:
+        geom, bd = _circle_geom(32, "cos", 2.0)
+        rng = np.random.default_rng(4)
+        geom.X = geom.X + 0.1 * geom.grid.h * rng.uniform(-1, 1, geom.X.shape)
+        Ub = I.harmonic_cubic(geom.X[0], geom.X[1])
+        P = 0.5 + 0.12 * rng.uniform(-1, 1, (2, 6))
+
+    def J(ub=Ub, X=geom.X, n=geom.n, w=geom.w):
+        g2 = O.Geometry(geom.grid, X, n, w, geom.delta, geom.dipole, geom.symbol, geom.pde, geom.lam, geom.mu)
+        Q = O.solve(g2, ub, 1e-13, maxit=300).x
+        return float(np.sum(O.probe_evaluate(g2, P, Q) ** 2))
+
+    Q = O.solve(geom, Ub, 1e-13, maxit=300).x
+    nu = 2 * O.probe_evaluate(geom, P, Q)
+    dQ, pX, pn, pw = O.probe_vjp(geom, P, Q, nu)
+    _, dUb, sX, sn, sw = O.solve_gradient(geom, Ub, dQ.reshape(-1))
+    c = geom.ncomp
+    idx = rng.choice(geom.M, 3, replace=False)
+    for i in idx:
+        for m in range(c):
+            d = np.zeros(c * geom.M)
+            d[m * geom.M + i] = 1e-6
+            assert (J(ub=Ub + d) - J(ub=Ub - d)) / 2e-6 == pytest.approx(dUb[m * geom.M + i], rel=1e-5, abs=1e-9)
+    _fd_check(J, {"X": geom.X, "n": geom.n, "w": geom.w}, {"X": pX + sX, "n": pn + sn, "w": pw + sw}, idx, rng)
