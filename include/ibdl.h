@@ -157,35 +157,49 @@ ibdl_status ibdl_adjoint(ibdl_geometry* geom, int precision, const double* W, do
 ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const ibdl_solve_opts* opts,
                        ibdl_solve_info* info, void* stream);
 
-/* Differentiation of the solve. The paper states no derivative; these follow from the operator
- * of Sec. 5.3.2 by the adjoint method. For Q = A⁻¹U_b and an objective J(Q) with G = ∂J/∂Q:
+/* Differentiation. The paper states no derivative; these follow from the operators of
+ * Sec. 5.3.2 and Sec. 6.3.3 by the adjoint method. Both operators are
+ * A Q = S*(K[sources(Q)]) + ½Q with K a Fourier multiplier (−L⁻¹, or the Stokes multiplier
+ * û = (i k̃ ŝ + P̂ ĝ)/|k|²). For Q = A⁻¹U_b and an objective J(Q) with G = ∂J/∂Q:
  *   λ = A⁻ᵀ G,   ∂J/∂U_b = λ,   ∂J/∂p = −∂(λᵀ A(X, n, Δs) Q)/∂p  for p = X, n, Δs.
+ * The normals and weights are independent inputs; a caller whose n and Δs depend on X adds
+ * their chain rule. Derivatives in X use φ'' of the delta kernel, which jumps where a point
+ * sits at a whole-number offset from a node (√-Peskin |r| = 1, 2; cosine |r| = 2): A is not
+ * differentiable in X there and the value returned is that of the piece containing the offset.
+ * Stokes derivatives and transposes need the analytic dipole (IBDL_ERR_UNSUPPORTED otherwise).
  *
- * ibdl_apply_transpose: Z = Aᵀ G, the Euclidean transpose Aᵀ = W A* W⁻¹ (W = diag Δs, A* as in
- * ibdl_adjoint): ½G + W (S̃)* (−L⁻¹) S W⁻¹ G, i.e. G spread with weight h^{−d} in place of
- * Δs h^{−d} and the gathered values multiplied by Δs. Scalar PDE only. Device FP64 [M] that may
- * not alias; asynchronous.
+ * ibdl_apply_transpose: Z = Aᵀ G (Euclidean transpose; [c][M] FP64 device arrays that may not
+ * alias). Scalar: Aᵀ = W A* W⁻¹ (W = diag Δs, A* as in ibdl_adjoint) = ½G + (Δs/h^d)(S̃)*(−L⁻¹)ψ,
+ * ψ = Σ_j G_j Φ(x − X_j). Stokes: ½G + the spread transpose of Kᵀψ, ψ_l = Σ_j G_{l,j} Φ(x − X_j),
+ * K̂ᵀ the conjugate symbol. Asynchronous.
  *
- * ibdl_solve_transpose: solve Aᵀ λ = G by the same GMRES as ibdl_solve (same options, precision
- * modes, graphs and convergence rule, now on ‖G − Aᵀλ‖ ≤ rtol‖G‖). Scalar PDE only. G and
- * lambda are [M] FP64, device pointers unless opts->io_on_host. Synchronises `stream`.
+ * ibdl_solve_transpose: solve Aᵀ λ = G with the GMRES of ibdl_solve (same options, precision
+ * modes, graphs and convergence rule, on ‖G − Aᵀλ‖ ≤ rtol‖G‖). G and lambda are [c][M] FP64,
+ * device pointers unless opts->io_on_host. Synchronises `stream`.
  *
  * ibdl_solve_vjp: given Q (the solution of A Q = U_b) and λ (of Aᵀλ = G), writes
  *   dX[dim][M] = ∂J/∂X,  dn[dim][M] = ∂J/∂n,  dw[M] = ∂J/∂Δs
- * (any of them may be NULL: not computed), with the boundary layout of ibdl_create_geometry.
- * The normals and weights are treated as independent inputs; a caller whose n and Δs depend
- * on X adds their chain rule. FP64 throughout: u = −L⁻¹S̃Q and v = −L⁻¹ Σ_j λ_j δ_h(x − X_j) on
- * the grid, then per point the gradient and Hessian of δ_h against them. φ'' jumps where a
- * point sits at a whole-number offset from a node (√-Peskin |r| = 1, 2; cosine |r| = 2), so A
- * is not differentiable in X there; the value returned is that of the piece containing the
- * offset. Scalar PDE with the analytic dipole only (IBDL_ERR_UNSUPPORTED otherwise). Device
- * FP64 arrays, outputs may not overlap each other or the inputs; asynchronous. The first call
- * allocates two grid fields held by the geometry. */
+ * (any may be NULL: not computed), in the boundary layout of ibdl_create_geometry. FP64: the
+ * grid fields u = K[sources(Q)] and v = Kᵀψ (ψ = Σ_j λ_j Φ(x − X_j)), then per point the value,
+ * gradient and Hessian gathers of δ_h against them. Outputs may not overlap each other or the
+ * inputs. Asynchronous; the first derivative call allocates grid fields held by the geometry.
+ *
+ * Probes (2-D): values of the grid solution at n_probes points P[2][n_probes] (device FP64,
+ * wrapped periodically), u(p) = Σ_g u_g δ_h(x_g − p) h^d, with the geometry's delta kernel.
+ * ibdl_probe_evaluate: U[c][n_probes] = E Q, u the grid field of Q (scalar u or the Stokes
+ * velocity). ibdl_probe_vjp: for ν[c][n_probes] = ∂J/∂U, writes dQ[c][M] = Eᵀν and
+ * dX, dn, dw = ∂(νᵀ E(X, n, Δs) Q)/∂(X, n, Δs) with P fixed (each may be NULL). A full gradient
+ * of J(U) with U = E Q(U_b) adds these to the solve's: pass G = dQ to ibdl_solve_transpose, then
+ * ibdl_solve_vjp. Outputs may not overlap each other or the inputs. Asynchronous. */
 ibdl_status ibdl_apply_transpose(ibdl_geometry* geom, int precision, const double* G, double* Z, void* stream);
 ibdl_status ibdl_solve_transpose(ibdl_geometry* geom, const double* G, double* lambda, const ibdl_solve_opts* opts,
                                  ibdl_solve_info* info, void* stream);
 ibdl_status ibdl_solve_vjp(ibdl_geometry* geom, const double* Q, const double* lambda, double* dX, double* dn,
                            double* dw, void* stream);
+ibdl_status ibdl_probe_evaluate(ibdl_geometry* geom, const double* P, int n_probes, const double* Q, double* U,
+                                void* stream);
+ibdl_status ibdl_probe_vjp(ibdl_geometry* geom, const double* P, int n_probes, const double* Q, const double* nu,
+                           double* dQ, double* dX, double* dn, double* dw, void* stream);
 
 /* The grid solution of a density (Sec. 5.1.2 step 2 with g̃ = 0): scalar u = −L⁻¹S̃Q written
  * to u_grid[n^dim]; Stokes velocity written to u_grid[dim][n^dim]. FP64 device arrays;

@@ -139,8 +139,8 @@ static ibdl_status solve_entry(ibdl_geometry* geom, const double* b, double* x, 
   if (o.precision == IBDL_MIXED && (!(o.inner_rtol > 0) || !(o.inner_rtol < 1) || o.max_refine < 1))
     return fail(IBDL_ERR_INVALID_ARG, "mixed precision needs inner_rtol in (0, 1) and max_refine >= 1");
   if (!b || !x) return fail(IBDL_ERR_INVALID_ARG, std::string(bname) + " and " + xname + " are required");
-  if (op == OPK_AT && geom->g->pde != IBDL_PDE_SCALAR)
-    return fail(IBDL_ERR_UNSUPPORTED, "ibdl_solve_transpose: scalar PDE only");
+  if (op == OPK_AT && geom->g->pde == IBDL_PDE_STOKES && geom->g->dipole != IBDL_DIPOLE_ANALYTIC)
+    return fail(IBDL_ERR_UNSUPPORTED, "ibdl_solve_transpose: Stokes with the analytic dipole only");
   if (!o.io_on_host) {
     IBDL_TRY(check_device_ptr(b, bname));
     IBDL_TRY(check_device_ptr(x, xname));
@@ -149,6 +149,27 @@ static ibdl_status solve_entry(ibdl_geometry* geom, const double* b, double* x, 
   ibdl_status st = solve_impl(geom->g, b, x, &o, info, static_cast<cudaStream_t>(stream), op);
   if (info) info->kernel_launches = geom->g->launches - before;
   return st;
+}
+
+// Optional derivative outputs dX [d][M], dn [d][M], dw [M], dQ [c][M]: device pointers that
+// overlap neither each other nor the inputs.
+static ibdl_status check_outputs(const Geometry* g, double* dX, double* dn, double* dw, double* dQ,
+                                 const void* const* ins, const size_t* ib, int nin, const char* in_names) {
+  const size_t vb = sizeof(double) * g->M;
+  double* outs[4] = {dX, dn, dw, dQ};
+  const size_t ob[4] = {vb * g->dim, vb * g->dim, vb, vb * g->ncomp};
+  const char* names[4] = {"dX", "dn", "dw", "dQ"};
+  for (int k = 0; k < 4; ++k) {
+    if (!outs[k]) continue;
+    IBDL_TRY(check_device_ptr(outs[k], names[k]));
+    for (int j = 0; j < nin; ++j)
+      if (ins[j] && spans_overlap(outs[k], ob[k], ins[j], ib[j]))
+        return fail(IBDL_ERR_INVALID_ARG, std::string(names[k]) + " overlaps " + in_names);
+    for (int l = 0; l < k; ++l)
+      if (outs[l] && spans_overlap(outs[k], ob[k], outs[l], ob[l]))
+        return fail(IBDL_ERR_INVALID_ARG, std::string(names[k]) + " overlaps " + names[l]);
+  }
+  return IBDL_OK;
 }
 
 }  // namespace ibdl
@@ -170,10 +191,11 @@ ibdl_status ibdl_apply_transpose(ibdl_geometry* geom, int precision, const doubl
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
   if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
   Geometry* g = geom->g;
-  if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_apply_transpose: scalar PDE only");
+  if (g->pde == IBDL_PDE_STOKES && g->dipole != IBDL_DIPOLE_ANALYTIC)
+    return fail(IBDL_ERR_UNSUPPORTED, "ibdl_apply_transpose: Stokes with the analytic dipole only");
   IBDL_TRY(check_device_ptr(G, "G"));
   IBDL_TRY(check_device_ptr(Z, "Z"));
-  if (ranges_overlap(G, Z, sizeof(double) * g->M)) return fail(IBDL_ERR_INVALID_ARG, "G and Z overlap");
+  if (ranges_overlap(G, Z, sizeof(double) * g->ncomp * g->M)) return fail(IBDL_ERR_INVALID_ARG, "G and Z overlap");
   return apply_any(g, precision, G, Z, static_cast<cudaStream_t>(stream), nullptr, OPK_AT);
 }
 
@@ -182,25 +204,55 @@ ibdl_status ibdl_solve_vjp(ibdl_geometry* geom, const double* Q, const double* l
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
   Geometry* g = geom->g;
-  if (g->pde != IBDL_PDE_SCALAR || g->dipole != IBDL_DIPOLE_ANALYTIC)
-    return fail(IBDL_ERR_UNSUPPORTED, "ibdl_solve_vjp: scalar PDE with the analytic dipole only");
+  if (g->dipole != IBDL_DIPOLE_ANALYTIC)
+    return fail(IBDL_ERR_UNSUPPORTED, "ibdl_solve_vjp: analytic dipole only");
   IBDL_TRY(check_device_ptr(Q, "Q"));
   IBDL_TRY(check_device_ptr(lambda, "lambda"));
   if (!dX && !dn && !dw) return IBDL_OK;
-  const size_t vb = sizeof(double) * g->M, mb = vb * g->dim;
-  double* outs[3] = {dX, dn, dw};
-  const size_t ob[3] = {mb, mb, vb};
-  const char* names[3] = {"dX", "dn", "dw"};
-  for (int k = 0; k < 3; ++k) {
-    if (!outs[k]) continue;
-    IBDL_TRY(check_device_ptr(outs[k], names[k]));
-    if (spans_overlap(outs[k], ob[k], Q, vb) || spans_overlap(outs[k], ob[k], lambda, vb))
-      return fail(IBDL_ERR_INVALID_ARG, std::string(names[k]) + " overlaps Q or lambda");
-    for (int l = 0; l < k; ++l)
-      if (outs[l] && spans_overlap(outs[k], ob[k], outs[l], ob[l]))
-        return fail(IBDL_ERR_INVALID_ARG, std::string(names[k]) + " overlaps " + names[l]);
-  }
+  const size_t cb = sizeof(double) * g->ncomp * g->M;
+  const void* ins[2] = {Q, lambda};
+  const size_t ib[2] = {cb, cb};
+  IBDL_TRY(check_outputs(g, dX, dn, dw, nullptr, ins, ib, 2, "Q or lambda"));
   return solve_vjp_impl(g, Q, lambda, dX, dn, dw, static_cast<cudaStream_t>(stream));
+}
+
+ibdl_status ibdl_probe_evaluate(ibdl_geometry* geom, const double* P, int n_probes, const double* Q, double* U,
+                                void* stream) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  Geometry* g = geom->g;
+  if (g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_probe_evaluate: 2-D only");
+  if (n_probes < 0) return fail(IBDL_ERR_INVALID_ARG, "n_probes must be >= 0");
+  IBDL_TRY(check_device_ptr(Q, "Q"));
+  if (n_probes > 0) {
+    IBDL_TRY(check_device_ptr(P, "P"));
+    IBDL_TRY(check_device_ptr(U, "U"));
+    if (spans_overlap(U, sizeof(double) * g->ncomp * n_probes, Q, sizeof(double) * g->ncomp * g->M) ||
+        spans_overlap(U, sizeof(double) * g->ncomp * n_probes, P, sizeof(double) * 2 * n_probes))
+      return fail(IBDL_ERR_INVALID_ARG, "U overlaps Q or P");
+  }
+  return probe_evaluate_impl(g, P, n_probes, Q, U, static_cast<cudaStream_t>(stream));
+}
+
+ibdl_status ibdl_probe_vjp(ibdl_geometry* geom, const double* P, int n_probes, const double* Q, const double* nu,
+                           double* dQ, double* dX, double* dn, double* dw, void* stream) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  Geometry* g = geom->g;
+  if (g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_probe_vjp: 2-D only");
+  if (g->dipole != IBDL_DIPOLE_ANALYTIC) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_probe_vjp: analytic dipole only");
+  if (n_probes < 0) return fail(IBDL_ERR_INVALID_ARG, "n_probes must be >= 0");
+  IBDL_TRY(check_device_ptr(Q, "Q"));
+  if (n_probes > 0) {
+    IBDL_TRY(check_device_ptr(P, "P"));
+    IBDL_TRY(check_device_ptr(nu, "nu"));
+  }
+  if (!dQ && !dX && !dn && !dw) return IBDL_OK;
+  const void* ins[3] = {Q, nu, P};
+  const size_t ib[3] = {sizeof(double) * g->ncomp * g->M, sizeof(double) * g->ncomp * n_probes,
+                        sizeof(double) * 2 * n_probes};
+  IBDL_TRY(check_outputs(g, dX, dn, dw, dQ, ins, ib, n_probes > 0 ? 3 : 1, "Q, nu or P"));
+  return probe_vjp_impl(g, P, n_probes, Q, nu, dQ, dX, dn, dw, static_cast<cudaStream_t>(stream));
 }
 
 ibdl_status ibdl_evaluate_field(ibdl_geometry* geom, const double* Q, double* u_grid, void* stream) {

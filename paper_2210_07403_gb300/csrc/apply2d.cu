@@ -27,7 +27,7 @@
 namespace ibdl {
 
 enum { OP_SCALAR_AN = 0, OP_SCALAR_SD = 1, OP_STOKES_AN = 2, OP_STOKES_SD = 3, OP_ADJ_AN = 4,
-       OP_ADJ_SD = 5 };
+       OP_ADJ_SD = 5, OP_STOKES_T = 6 };
 
 // grid fields entering / leaving the Fourier stage, and boundary components in / out
 template <int OP>
@@ -45,6 +45,9 @@ template <>
 struct Traits<OP_ADJ_AN> { static constexpr int NIN = 1, NOUT = 1, C = 1; };     // S W
 template <>
 struct Traits<OP_ADJ_SD> { static constexpr int NIN = 1, NOUT = 2, C = 1; };     // S W → ∂_x v, ∂_y v
+// Stokes transpose (analytic dipole): ψ_x, ψ_y → v_s, v_gx, v_gy
+template <>
+struct Traits<OP_STOKES_T> { static constexpr int NIN = 2, NOUT = 3, C = 2; };
 
 enum { G_INTERP = 0, G_GRID = 1 };
 
@@ -70,10 +73,11 @@ struct RowParams {
   const int* idx;     // optional: in += (*idx)·vstride, out += (*idx + 1)·vstride (Krylov basis)
   int vstride;
   int64_t io_off;     // batched launches: in = in_base + io_off, out = out_base + io_off
-  // adjoint ops only: 1 = the Euclidean transpose Aᵀ = W A* W⁻¹ (spread weight 1/h^d in place
-  // of Δs/h^d, gathered values multiplied by Δs = wscale·h^d)
+  // scalar adjoint ops only: 1 = the Euclidean transpose Aᵀ = W A* W⁻¹ (W⁻¹λ spread with weight
+  // Δs/h^d is λ spread with weight h^−d = 1 · h^−d: the spread weight is 1 and the gathered values
+  // carry Δs/h^d instead of 1)
   int trans;
-  double hd;          // h^d
+  const double* grid_in;  // optional [NIN][n][n]: the band rows are read from it instead of spread
 };
 
 template <typename T>
@@ -150,14 +154,24 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   double* pout;
   resolve_io(p, pin, pout);
 
-  // jump term: out = ½·in (the gather kernel adds S*u afterwards)
-  for (int i = unit * blockDim.x + threadIdx.x; i < NC * M; i += nunits * blockDim.x)
-    pout[i] = 0.5 * pin[i];
+  // jump term: out = ½·in (the gather kernel adds S*u afterwards); none for grid input
+  if (!p.grid_in)
+    for (int i = unit * blockDim.x + threadIdx.x; i < NC * M; i += nunits * blockDim.x)
+      pout[i] = 0.5 * pin[i];
   __syncthreads();
+
+  if (p.grid_in) {
+    for (int t = threadIdx.x; t < NIN * R * n; t += blockDim.x) {
+      const int f = t / (R * n);
+      const int rem = t - f * R * n;
+      const int lr = rem / n, x = rem - lr * n;
+      acc[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)] = T(p.grid_in[((size_t)f * n + r0 + lr) * n + x]);
+    }
+  }
 
   // one thread per (point, stencil node): 16 work items per point whose stencil meets the band
   const PointRanges pr = band_points(p.cell_start, n, r0, R);
-  for (int t = threadIdx.x; t < pr.cnt * 16; t += blockDim.x) {
+  for (int t = threadIdx.x; t < (p.grid_in ? 0 : pr.cnt * 16); t += blockDim.x) {
     const int s = pr.at(t >> 4);
     const int ay = (t >> 2) & 3, ax = t & 3;
     const int by = p.base[M + s];
@@ -196,10 +210,13 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
         atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c2 * pp);
         atomicAdd(acc + 2 * pidx(e + 3 * half * n) + odd, c3 * pp);
       }
+    } else if (OP == OP_STOKES_T) {
+      // ψ_l = Σ_j μ_{l,j} Φ(x − X_j): the transpose of S*, unweighted
+      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * pp);
+      atomicAdd(acc + 2 * pidx(e + half * n) + odd, T(pin[M + i]) * pp);
     } else {
-      // plain spread of W (A*), or of W⁻¹λ, i.e. λ with weight 1/h^d (Aᵀ)
-      const T wsp = p.trans ? T(1.0 / p.hd) : ws;
-      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * wsp * pp);
+      // plain spread of W (A*: weight Δs/h^d), or of λ (Aᵀ: weight 1, Δs/h^d moves to the gather)
+      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * (p.trans ? T(1) : ws) * pp);
     }
   }
   __syncthreads();
@@ -257,6 +274,14 @@ __device__ __forceinline__ void apply_symbol(const ColParams<T>& p, const T* lap
       out[0] = cscale(cmuli(v), dkx);
       out[1] = cscale(cmuli(v), dky);
     }
+  } else if (OP == OP_STOKES_T) {
+    // transpose of the Stokes multiplier (conjugate symbol): v̂_s = −i k̃·ψ̂/|k|², v̂_g = P̂ψ̂/|k|²
+    const T inv = lap != T(0) ? T(1) / lap : T(0);
+    const cplx<T> kp = cadd(cscale(in[0], dkx), cscale(in[1], dky));
+    const T sc = inv * p.scale;
+    out[0] = cscale(cmuli(kp), -sc);
+    out[1] = cscale(csub(in[0], cscale(kp, dkx * inv)), sc);
+    out[2] = cscale(csub(in[1], cscale(kp, dky * inv)), sc);
   } else {
     // Stokes, interior, η = 0: û = (i k̃ ŝ + P̂ ĝ)/|k|², P̂ = I − k̃k̃ᵀ/|k|²
     const T inv = lap != T(0) ? T(1) / lap : T(0);
@@ -431,8 +456,30 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
     const int i = p.perm[s];
     const int bx = p.base[s];
     const T py = p.phi[(1 * 4 + ay) * M + s];
-    const T dy = OP == OP_ADJ_AN ? p.dphi[(1 * 4 + ay) * M + s] : T(0);
+    const T dy = (OP == OP_ADJ_AN || OP == OP_STOKES_T) ? p.dphi[(1 * 4 + ay) * M + s] : T(0);
     const int eb = (lr >> 1) * n, odd = lr & 1;
+    if (OP == OP_STOKES_T) {
+      // a_s = Σ v_s Φ, G_mk = Σ v_gm ∂_kΦ; out_l += (Δs/h²)[n_l a_s + Σ_k n_k (G_lk + G_kl)]
+      T as = 0, gxx = 0, gxy = 0, gyx = 0, gyy = 0;
+#pragma unroll
+      for (int ax = 0; ax < 4; ++ax) {
+        const int col = (bx + ax) & (n - 1);
+        const T px = p.phi[(0 * 4 + ax) * M + s], dx = p.dphi[(0 * 4 + ax) * M + s];
+        const T vs = u[2 * pidx(eb + col) + odd];
+        const T vx = u[2 * pidx(eb + half * n + col) + odd];
+        const T vy = u[2 * pidx(eb + 2 * half * n + col) + odd];
+        as += vs * px * py;
+        gxx += vx * dx * py;
+        gxy += vx * px * dy;
+        gyx += vy * dx * py;
+        gyy += vy * px * dy;
+      }
+      const double ws = double(p.wscale[s]), nx = double(p.nrm[s]), ny = double(p.nrm[M + s]);
+      const double cross = double(gxy) + double(gyx);
+      atomicAdd(pout + i, ws * (nx * double(as) + 2.0 * nx * double(gxx) + ny * cross));
+      atomicAdd(pout + M + i, ws * (ny * double(as) + nx * cross + 2.0 * ny * double(gyy)));
+      continue;
+    }
     T acc0 = 0, acc1 = 0;
 #pragma unroll
     for (int ax = 0; ax < 4; ++ax) {
@@ -455,7 +502,7 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
       // analytic: (S̃)* v = n · (kernel-gradient gather of v); spectral: −Σ_m n_m S*(∂_m v)
       double val = double(p.nrm[s]) * double(acc0) + double(p.nrm[M + s]) * double(acc1);
       if (OP == OP_ADJ_SD) val = -val;
-      if (p.trans) val *= double(p.wscale[s]) * p.hd;  // W (S̃)* … for Aᵀ
+      if (p.trans) val *= double(p.wscale[s]);  // Δs/h^d · (S̃)* … for Aᵀ
       atomicAdd(pout + i, val);
     } else {
       atomicAdd(pout + i, double(acc0));
@@ -498,7 +545,7 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.vstride = 0;
   rp.io_off = 0;
   rp.trans = 0;
-  rp.hd = g->h * g->h;
+  rp.grid_in = nullptr;
   return rp;
 }
 
@@ -582,12 +629,14 @@ static ibdl_status set_attrs_all() {
   IBDL_TRY((set_attrs<T, OP_STOKES_SD>()));
   IBDL_TRY((set_attrs<T, OP_ADJ_AN>()));
   IBDL_TRY((set_attrs<T, OP_ADJ_SD>()));
+  IBDL_TRY((set_attrs<T, OP_STOKES_T>()));
   return IBDL_OK;
 }
 
 template <typename T, int OP>
 static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream_t s, const int* stop,
-                          double* grid, const int* idx = nullptr, int vstride = 0, int trans = 0) {
+                          double* grid, const int* idx = nullptr, int vstride = 0, int trans = 0,
+                          const double* grid_in = nullptr) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi];
   if (R == 0 || C == 0)
@@ -599,6 +648,7 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   rp.idx = idx;
   rp.vstride = vstride;
   rp.trans = trans;
+  rp.grid_in = grid_in;
   ColParams<T> cp = col_params<T>(g, stop);
   const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
@@ -621,7 +671,11 @@ template <typename T>
 static ibdl_status apply_t(Geometry* g, const double* Q, double* Y, cudaStream_t s, const int* stop, double* grid,
                            const int* idx = nullptr, int vstride = 0, int op = OPK_A) {
   if (op == OPK_AT) {
-    if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "transpose: scalar PDE only");
+    if (g->pde == IBDL_PDE_STOKES) {
+      if (g->dipole != IBDL_DIPOLE_ANALYTIC)
+        return fail(IBDL_ERR_UNSUPPORTED, "Stokes transpose: analytic dipole only");
+      return run_op<T, OP_STOKES_T>(g, Q, Y, s, stop, grid, idx, vstride);
+    }
     return g->dipole == IBDL_DIPOLE_ANALYTIC ? run_op<T, OP_ADJ_AN>(g, Q, Y, s, stop, grid, idx, vstride, 1)
                                              : run_op<T, OP_ADJ_SD>(g, Q, Y, s, stop, grid, idx, vstride, 1);
   }
@@ -645,12 +699,20 @@ ibdl_status apply_2d(Geometry* g, int precision, const double* Q, double* Y, cud
                                 : apply_t<double>(g, Q, Y, s, stop, nullptr, nullptr, 0, op);
 }
 
-// u = −L⁻¹ S̃Q (the forward op's grid field) and v = −L⁻¹(Σ_j λ_j δ_h(x − X_j)) (the transpose
-// op's grid field: λ spread with weight 1/h^d), both FP64 on [n][n]
+// u = K[sources(Q)] (the forward op's grid field: c fields) and v = Kᵀψ, ψ_l = Σ_j λ_{l,j} Φ(x − X_j)
+// (the transpose op's grid field: 1 field scalar, v_s and v_g Stokes), FP64 on [·][n][n]
 ibdl_status field_pair_2d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s) {
-  if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "boundary derivatives: scalar PDE only");
   IBDL_TRY(apply_t<double>(g, Q, g->tmp_m, s, nullptr, u));
   return apply_t<double>(g, lam, g->tmp_m, s, nullptr, v, nullptr, 0, OPK_AT);
+}
+
+// v = Kᵀψ for a grid field ψ ([c][n][n]): the transpose op's Fourier stage with its row bands read
+// from ψ instead of spread from the boundary
+ibdl_status transform_T_2d(Geometry* g, const double* psi, double* v, cudaStream_t s) {
+  if (g->dipole != IBDL_DIPOLE_ANALYTIC) return fail(IBDL_ERR_UNSUPPORTED, "analytic dipole only");
+  if (g->pde == IBDL_PDE_STOKES)
+    return run_op<double, OP_STOKES_T>(g, nullptr, nullptr, s, nullptr, v, nullptr, 0, 0, psi);
+  return run_op<double, OP_ADJ_AN>(g, nullptr, nullptr, s, nullptr, v, nullptr, 0, 1, psi);
 }
 
 ibdl_status field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s) {

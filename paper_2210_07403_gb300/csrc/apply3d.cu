@@ -55,10 +55,9 @@ struct Row3Params {
   double* grid;
   const int* idx;
   int vstride;
-  // adjoint ops only: 1 = the Euclidean transpose Aᵀ = W A* W⁻¹ (spread weight 1/h³ in place of
-  // Δs/h³, gathered values multiplied by Δs = wscale·h³)
+  // adjoint ops only: 1 = the Euclidean transpose Aᵀ = W A* W⁻¹ (λ spread with weight 1, gathered
+  // values multiplied by Δs/h³ in place of the spread's Δs/h³ · W⁻¹)
   int trans;
-  double hd;  // h³
 };
 
 struct Col3Params {
@@ -184,7 +183,7 @@ __global__ void __launch_bounds__(kThreads3) k3_spread_rowfft(Row3Params p) {
       atomicAdd(acc + 2 * pidx(e + half * n) + odd, q * nrm[M + s]);
       atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, q * nrm[2 * M + s]);
     } else {
-      const T wsp = p.trans ? T(1.0 / p.hd) : ws;  // A*: W; Aᵀ: W⁻¹λ
+      const T wsp = p.trans ? T(1) : ws;  // A*: W with weight Δs/h³; Aᵀ: λ with weight 1
       atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * wsp * ppp);
     }
   }
@@ -454,7 +453,7 @@ __global__ void __launch_bounds__(kThreads3) k3_rowifft_gather(Row3Params p) {
     if (OP == OP3_ADJ_AN || OP == OP3_ADJ_SD) {
       double val = double(nrm[s]) * double(a0) + double(nrm[M + s]) * double(a1) + double(nrm[2 * M + s]) * double(a2);
       if (OP == OP3_ADJ_SD) val = -val;
-      if (p.trans) val *= double(static_cast<const T*>(p.wscale)[s]) * p.hd;
+      if (p.trans) val *= double(static_cast<const T*>(p.wscale)[s]);
       atomicAdd(pout + i, val);
     } else {
       atomicAdd(pout + i, double(a0));
@@ -571,7 +570,6 @@ static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStrea
   rp.idx = idx;
   rp.vstride = vstride;
   rp.trans = trans;
-  rp.hd = g->h * g->h * g->h;
   Col3Params cp;
   cp.n = n;
   cp.log2n = rp.log2n;
@@ -631,7 +629,7 @@ ibdl_status apply_3d_indexed(Geometry* g, int precision, double* V, const int* i
                                 : apply3_t<double>(g, V, V, s, stop, nullptr, idx, nd, op);
 }
 
-// u = −L⁻¹S̃Q and v = −L⁻¹(Σ_j λ_j δ_h(x − X_j)), FP64 on [n][n][n]
+// u = −L⁻¹S̃Q and v = −L⁻¹(Σ_j λ_j Φ(x − X_j)), FP64 on [n][n][n]
 ibdl_status field_pair_3d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s) {
   IBDL_TRY(apply3_t<double>(g, Q, g->tmp_m, s, nullptr, u));
   return apply3_t<double>(g, lam, g->tmp_m, s, nullptr, v, nullptr, 0, OPK_AT);

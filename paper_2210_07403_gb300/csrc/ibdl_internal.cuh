@@ -205,11 +205,16 @@ ibdl_status plan_2d(Geometry* g);
 ibdl_status plan_3d(Geometry* g);
 ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solve_opts* o,
                        ibdl_solve_info* info, cudaStream_t s, int op = OPK_A);
-// grid fields u = −L⁻¹S̃Q and v = −L⁻¹(Σ_j λ_j δ_h(x − X_j)), then the boundary derivatives
+// grid fields u = K[sources(Q)] and v = Kᵀ(Σ_j λ_j Φ(x − X_j)) (K = −L⁻¹ scalar, the Stokes
+// multiplier otherwise), then the boundary derivatives; Kᵀ of a given grid field (2-D)
+ibdl_status transform_T_2d(Geometry* g, const double* psi, double* v, cudaStream_t s);
 ibdl_status field_pair_2d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s);
 ibdl_status field_pair_3d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s);
 ibdl_status solve_vjp_impl(Geometry* g, const double* Q, const double* lam, double* dX, double* dn, double* dw,
                            cudaStream_t s);
+ibdl_status probe_evaluate_impl(Geometry* g, const double* P, int np, const double* Q, double* U, cudaStream_t s);
+ibdl_status probe_vjp_impl(Geometry* g, const double* P, int np, const double* Q, const double* nu, double* dQ,
+                           double* dX, double* dn, double* dw, cudaStream_t s);
 
 ibdl_status apply_2d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
                              const int* stop, int op = OPK_A);

@@ -92,6 +92,9 @@ SIGNATURES = {
     "ibdl_solve_transpose": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(ibdl_solve_opts),
                                      POINTER(ibdl_solve_info), c_void_p]),
     "ibdl_solve_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ibdl_probe_evaluate": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "ibdl_probe_vjp": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_void_p, c_void_p]),
     "ibdl_last_error": (c_char_p, []),
 }
 
@@ -177,6 +180,19 @@ def ibdl_solve_vjp(geom, Q: int, lam: int, dX: int, dn: int, dw: int, stream: in
     """Pointers may be 0 (NULL) for outputs that are not wanted."""
     return _check(load().ibdl_solve_vjp(geom, c_void_p(Q), c_void_p(lam), c_void_p(dX or None),
                                         c_void_p(dn or None), c_void_p(dw or None), c_void_p(stream)))
+
+
+def ibdl_probe_evaluate(geom, P: int, n_probes: int, Q: int, U: int, stream: int = 0) -> int:
+    return _check(load().ibdl_probe_evaluate(geom, c_void_p(P), n_probes, c_void_p(Q), c_void_p(U),
+                                             c_void_p(stream)))
+
+
+def ibdl_probe_vjp(geom, P: int, n_probes: int, Q: int, nu: int, dQ: int, dX: int, dn: int, dw: int,
+                   stream: int = 0) -> int:
+    """Pointers may be 0 (NULL) for outputs that are not wanted."""
+    return _check(load().ibdl_probe_vjp(geom, c_void_p(P), n_probes, c_void_p(Q), c_void_p(nu), c_void_p(dQ or None),
+                                        c_void_p(dX or None), c_void_p(dn or None), c_void_p(dw or None),
+                                        c_void_p(stream)))
 
 
 def ibdl_evaluate_field(geom, Q: int, u_grid: int, stream: int = 0) -> int:
@@ -442,6 +458,34 @@ class Geometry:
                 t.empty((self.M,), dtype=t.float64, device=Q.device) if want[2] else None]
         ptrs = [o.data_ptr() if o is not None else 0 for o in outs]
         ibdl_solve_vjp(self._h, Q.data_ptr(), lam.data_ptr(), *ptrs, _stream_handle(stream))
+        return tuple(outs)
+
+    def _probes(self, P):
+        t = self._torch
+        if not isinstance(P, t.Tensor):
+            P = t.from_numpy(np.ascontiguousarray(np.asarray(P, dtype=np.float64)))
+        P = P.detach().to(device="cuda", dtype=t.float64).contiguous()
+        assert P.dim() == 2 and P.shape[0] == 2
+        return P
+
+    def probe_evaluate(self, P, Q, stream=None):
+        """Values of the grid solution of Q at the probes P [2][n_p]: shape [c][n_p]."""
+        t = self._torch
+        P, Q = self._probes(P), self._vec(Q)
+        U = t.empty((self.ncomp, P.shape[1]), dtype=t.float64, device=Q.device)
+        ibdl_probe_evaluate(self._h, P.data_ptr(), P.shape[1], Q.data_ptr(), U.data_ptr(), _stream_handle(stream))
+        return U
+
+    def probe_vjp(self, P, Q, nu, stream=None, want=(True, True, True, True)):
+        """(Eᵀν [c·M], ∂(νᵀEQ)/∂X [dim][M], ∂/∂n [dim][M], ∂/∂Δs [M]); False in ``want`` gives None."""
+        t = self._torch
+        P, Q = self._probes(P), self._vec(Q)
+        nu = nu.detach().to(dtype=t.float64).contiguous()
+        assert nu.numel() == self.ncomp * P.shape[1]
+        shapes = [(self.ncomp * self.M,), (self.dim, self.M), (self.dim, self.M), (self.M,)]
+        outs = [t.empty(sh, dtype=t.float64, device=Q.device) if w else None for sh, w in zip(shapes, want)]
+        ptrs = [o.data_ptr() if o is not None else 0 for o in outs]
+        ibdl_probe_vjp(self._h, P.data_ptr(), P.shape[1], Q.data_ptr(), nu.data_ptr(), *ptrs, _stream_handle(stream))
         return tuple(outs)
 
     def _solve(self, entry, Ub, rtol, precision, restart, maxit, inner_rtol, max_refine, Q, stream, check):
