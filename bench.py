@@ -278,7 +278,58 @@ def extra_workloads(dev, flush, stream, K=5):
     res["speedup_mixed_vs_fp64"] = round(res["solve_mixed"]["solves_per_s"] / res["solve_fp64"]["solves_per_s"], 3)
     out["sphere_128"] = res
     g.close()
+    out["stokes_star_probes_1024"] = differentiation_workload(dev, flush, stream, K)
     return out
+
+
+def differentiation_workload(dev, flush, stream, K=5):
+    """Forward + backward of J = Σ_p |u(p)|² on the 1024² Stokes star (1600 points, 64 probes at
+    ≥ 8h): the solve, the probe values, the transposed solve and the boundary derivatives, with
+    gradients to U_b, X, n and Δs. "step" includes building the geometry from the points (what a
+    shape-optimisation step pays); "fwd_bwd" reuses a built geometry."""
+    import torch
+
+    import ibdl_inputs as I
+    from paper_2210_07403_gb300 import autograd as AG
+
+    p, P = I.star_stokes_probes()
+    base = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+            for a in (p.Ub.reshape(-1), p.bd.X, p.bd.n, p.bd.w)]
+    Pd = torch.from_numpy(np.ascontiguousarray(P)).to(dev)
+    res = {"grid": p.N, "points": int(p.bd.X.shape[1]), "probes": int(P.shape[1]), "objective": "sum |u(p)|^2"}
+    grads = {}
+    for prec, rtol in (("fp64", 1e-10), ("mixed", SOLVE_RTOL)):
+        leaves = [a.clone().requires_grad_(True) for a in base]
+
+        def fwd_bwd(b):
+            for a in leaves:
+                a.grad = None
+            J = (b.probe(b.solve(leaves[0], rtol=rtol, precision=prec, inner_rtol=INNER_RTOL), Pd) ** 2).sum()
+            J.backward()
+            return J
+
+        def step():
+            b = AG.Boundary(*leaves[1:], p.N, pde="stokes", delta=p.delta, symbol=p.symbol)
+            J = fwd_bwd(b)
+            b.close()
+            return J
+
+        for _ in range(2):
+            step()
+        t_step, _ = _event_ms(step, K, flush, stream)
+        b = AG.Boundary(*leaves[1:], p.N, pde="stokes", delta=p.delta, symbol=p.symbol)
+        fwd_bwd(b)
+        t_fb, J = _event_ms(lambda: fwd_bwd(b), K, flush, stream)
+        t_fwd, _ = _event_ms(lambda: (b.probe(b.solve(leaves[0].detach(), rtol=rtol, precision=prec,
+                                                      inner_rtol=INNER_RTOL), Pd) ** 2).sum(), K, flush, stream)
+        b.close()
+        grads[prec] = [a.grad.detach().cpu().numpy().reshape(-1) for a in leaves]
+        res[prec] = {"rtol": rtol, "step_ms": round(t_step, 3), "fwd_bwd_ms": round(t_fb, 3),
+                     "forward_ms": round(t_fwd, 3), "J": float(J.detach())}
+    res["mixed_grad_rel_diff_vs_fp64"] = {
+        k: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        for k, a, b in zip(("Ub", "X", "n", "w"), grads["mixed"], grads["fp64"])}
+    return res
 
 
 def cufft_compare(dev, stream):
