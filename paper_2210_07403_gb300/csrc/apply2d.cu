@@ -149,6 +149,10 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
   load_twiddles(tws, p.tw, n);
   cudaGridDependencySynchronize();
+  // Let the next kernel launch and run its prologue. Triggered only after this kernel's own
+  // wait, so every kernel before the previous one has completed by then: a prologue overlaps
+  // its direct predecessor only (its wait still covers this grid's completion and writes).
+  cudaTriggerProgrammaticLaunchCompletion();
   if (p.stop && *p.stop) return;
   const double* pin;
   double* pout;
@@ -334,6 +338,7 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
     der1[i] = p.der1[i];
   }
   cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
   if (p.stop && *p.stop) return;
   __syncthreads();
   const ColumnIO<T> cio{p.spec, n, nh, k0, p.lc, C};
@@ -425,6 +430,7 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   const int r0 = unit * R;
   load_twiddles(tws, p.tw, n);
   cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
   if (p.stop && *p.stop) return;
   __syncthreads();
   const RowZLoad<T> zl{p.spec, n, nh, r0, half};
@@ -653,7 +659,7 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
   const int nt = g->threads[pi] ? g->threads[pi] : kThreads;
-  k_spread_rowfft<T, OP><<<g->n / R, nt, s1, s>>>(rp);
+  IBDL_CUDA(launch_k(k_spread_rowfft<T, OP>, g->n / R, nt, s1, s, !g->timing, rp));
   if (g->timing) timing_mark(g, s, st0);
   IBDL_CUDA(launch_k(k_colpass<T, OP>, (g->n / 2) / C, nt, s2, s, !g->timing, cp));
   if (g->timing) timing_mark(g, s, st0 + 1);

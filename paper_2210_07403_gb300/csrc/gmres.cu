@@ -1,10 +1,11 @@
 // GMRES for A Q = U_b (Sec. 5.3.2: the Schur operator is not symmetric) on the device.
 //
-// Arnoldi runs on one 8-CTA cluster per iteration: classical Gram–Schmidt applied twice (CGS2)
-// against the basis in FP64, the new Hessenberg column is reduced by the stored Givens
-// rotations, and the residual estimate |g_{k}| is compared with the target on the device. When
-// the target is met (or the cycle is full, or a non-finite value appears) the step raises a stop
-// flag that every kernel of the following iterations reads first.
+// Arnoldi runs on one 16-CTA cluster per iteration (8 where 16 is unavailable; arnoldi.cuh):
+// classical Gram–Schmidt applied twice (CGS2) against the basis in FP64, the new Hessenberg
+// column is reduced by the stored Givens rotations, and the residual estimate |g_{k}| is compared
+// with the target on the device. When the target is met (or the cycle is full, or a non-finite
+// value appears) the step raises a stop flag that every kernel of the following iterations reads
+// first.
 //
 // A restart cycle is one CUDA graph: a conditional while node whose body is one operator
 // application and one Arnoldi step; the Arnoldi step sets the loop condition, so the host waits
@@ -22,40 +23,10 @@
 #include <algorithm>
 #include <vector>
 
+#include "arnoldi.cuh"
 #include "ibdl_internal.cuh"
 
-namespace cg = cooperative_groups;
-
 namespace ibdl {
-
-enum { KMAX = 64 };
-enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_NONFINITE = 3 };
-
-struct GmresState {
-  int stop;    // nonzero: every queued kernel returns at once
-  int status;  // ST_*
-  int k;       // Arnoldi steps completed in this cycle
-  int kmax;    // steps allowed in this cycle (≤ restart length and the remaining budget)
-  int body_iters;  // loop bodies run by the captured cycle (a guard on the device-side loop)
-  int pad2;
-  double res;      // |g_k|, the GMRES residual estimate
-  double beta;     // ‖r0‖ of the cycle
-  double target;   // absolute tolerance on the residual
-  double rnorm;    // ‖r‖ from k_residual
-  double cs[KMAX], sn[KMAX], g[KMAX + 1];
-  double H[(KMAX + 1) * KMAX];  // column j at H[j·(m+1) + i]
-};
-
-struct HostStatus {
-  int stop, status, k, kmax, body_iters, pad2;
-  double res, beta, target, rnorm;
-};
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // block-wide sum; every thread gets the result
 __device__ double block_sum(double v, double* red) {
@@ -71,6 +42,35 @@ __device__ double block_sum(double v, double* red) {
   const double r = red[0];
   __syncthreads();
   return r;
+}
+
+// y = R⁻¹ g for the k × k upper-triangular R of the rotated Hessenberg matrix (k ≤ 64), by one
+// warp: the reciprocals of the diagonal in parallel, then the column sweep y_i = r_i / R_ii,
+// r_l −= R_li y_i (l < i), whose per-row chain is one multiply, one shuffle and one FMA (FP64
+// division and long dependent sums are slow on this GPU). Rc holds R by columns (stride KMAX).
+__device__ void upper_solve_warp(const double* Rc, const double* g, int k, double* y) {
+  const int lane = threadIdx.x & 31;
+  double r0 = lane < k ? g[lane] : 0.0, r1 = lane + 32 < k ? g[lane + 32] : 0.0;
+  const double d0 = lane < k ? Rc[lane * KMAX + lane] : 1.0;
+  const double d1 = lane + 32 < k ? Rc[(lane + 32) * KMAX + lane + 32] : 1.0;
+  const double q0 = d0 != 0.0 ? 1.0 / d0 : 0.0, q1 = d1 != 0.0 ? 1.0 / d1 : 0.0;
+  for (int i = k - 1; i >= 0; --i) {
+    const int src = i & 31;
+    const double mine = i < 32 ? r0 * q0 : r1 * q1;
+    const double yi = __shfl_sync(0xffffffffu, mine, src);
+    if (lane == src) y[i] = yi;
+    if (lane < i) r0 = fma(-Rc[i * KMAX + lane], yi, r0);
+    if (lane + 32 < i) r1 = fma(-Rc[i * KMAX + lane + 32], yi, r1);
+  }
+}
+
+// stage the k × k upper triangle of the rotated Hessenberg matrix by columns, and g
+__device__ void stage_upper(const GmresState* s, int k, int m, double* Rc, double* g) {
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int col = t / k, row = t - col * k;
+    Rc[col * KMAX + row] = row <= col ? s->H[(size_t)col * (m + 1) + row] : 0.0;
+  }
+  for (int t = threadIdx.x; t < k; t += blockDim.x) g[t] = s->g[t];
 }
 
 // start a cycle: V_0 = r/‖r‖, g = ‖r‖ e_1
@@ -102,157 +102,6 @@ __global__ void __launch_bounds__(1024) k_gmres_start(GmresState* st, const doub
       st->stop = 0;
     }
   }
-}
-
-// One Arnoldi step on a cluster of CL CTAs (16 where the device allows that cluster size, else
-// 8). CTA r owns the slice [r·slice, (r+1)·slice) of the vectors; with STAGED it first copies its
-// slice of V_0..V_j into shared memory (one round of independent loads), so both Gram–Schmidt
-// passes read the basis from shared memory. Warp w forms the partial dot products of basis
-// vectors w, w + 16, …; the partial sums of the cluster are combined through distributed shared
-// memory (two buffers, one per pass, so a pass never overwrites what another CTA still reads).
-// The norm of the new vector comes with the second pass: ‖w₂‖² = ‖w₁‖² − Σ h₂,ᵢ², exact because
-// w₂ = w₁ − V h₂ with V orthonormal and accurate because h₂ only holds rounding-level
-// components after the first pass. Three cluster barriers per step.
-// Control flow is uniform over the cluster: the stop flag is read before the first cluster
-// barrier and only CTA 0 writes it, after that barrier. In a captured cycle (cond != 0) j is read
-// from st->k and the kernel sets the while-loop condition on every path: 0 once the cycle has
-// stopped, or after more loop bodies than the cycle allows (a guard), else 1.
-constexpr int ATH = 512;
-
-// Returns −1 (every thread) when the step was skipped because the cycle had already stopped;
-// otherwise, on CTA 0 thread 0, 1 if this step stopped the cycle and 0 if it continues.
-template <bool STAGED, int CL>
-__device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, int nd, int m, int slice) {
-  cg::cluster_group cluster = cg::this_cluster();
-  cudaGridDependencySynchronize();  // programmatic launch: wait for the application that wrote V_{j+1}
-  if (j < 0) j = st->k;
-  if (st->stop || j >= st->kmax || j >= m) return -1;
-  extern __shared__ double dsm[];
-  __shared__ double part1[KMAX + 2], part2[KMAX + 2];
-  __shared__ double h[KMAX + 2];
-  __shared__ double red[ATH / 32];
-  __shared__ double csl[KMAX], snl[KMAX];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int rank = (int)cluster.block_rank();
-  const int lo = rank * slice;
-  const int cnt = nd - lo < slice ? (nd - lo > 0 ? nd - lo : 0) : slice;
-  double* ws = dsm;
-  double* Vs = dsm + slice;
-  double* w = V + (size_t)(j + 1) * nd + lo;
-  for (int e = tid; e < cnt; e += ATH) ws[e] = w[e];
-  if (STAGED) {
-    for (int t = tid; t < (j + 1) * cnt; t += ATH) {
-      const int i = t / cnt, e = t - i * cnt;
-      Vs[i * slice + e] = V[(size_t)i * nd + lo + e];
-    }
-  }
-  __syncthreads();
-  auto vat = [&](int i, int e) -> double { return STAGED ? Vs[i * slice + e] : V[(size_t)i * nd + lo + e]; };
-
-  // pass 1: h₁ = Vᵀ w, w₁ = w − V h₁
-  for (int i = warp; i <= j; i += ATH / 32) {
-    double sacc = 0.0;
-    for (int e = lane; e < cnt; e += 32) sacc += vat(i, e) * ws[e];
-    sacc = warp_sum(sacc);
-    if (lane == 0) part1[i] = sacc;
-  }
-  cluster.sync();
-  double hsum = 0.0;
-  if (tid <= j) {
-    double t = 0.0;
-    for (int r = 0; r < CL; ++r) t += cluster.map_shared_rank(part1, r)[tid];
-    h[tid] = t;
-    hsum = t;
-  }
-  __syncthreads();
-  for (int e = tid; e < cnt; e += ATH) {
-    double a = ws[e];
-    for (int i = 0; i <= j; ++i) a -= h[i] * vat(i, e);
-    ws[e] = a;
-  }
-  __syncthreads();
-
-  // pass 2: h₂ = Vᵀ w₁ and ‖w₁‖² in one reduction (slot j+1), w₂ = w₁ − V h₂
-  for (int i = warp; i <= j + 1; i += ATH / 32) {
-    double sacc = 0.0;
-    if (i <= j) {
-      for (int e = lane; e < cnt; e += 32) sacc += vat(i, e) * ws[e];
-    } else {
-      for (int e = lane; e < cnt; e += 32) sacc += ws[e] * ws[e];
-    }
-    sacc = warp_sum(sacc);
-    if (lane == 0) part2[i] = sacc;
-  }
-  cluster.sync();
-  if (tid <= j + 1) {
-    double t = 0.0;
-    for (int r = 0; r < CL; ++r) t += cluster.map_shared_rank(part2, r)[tid];
-    h[tid] = t;
-    if (tid <= j) hsum += t;
-  }
-  __syncthreads();
-  for (int e = tid; e < cnt; e += ATH) {
-    double a = ws[e];
-    for (int i = 0; i <= j; ++i) a -= h[i] * vat(i, e);
-    ws[e] = a;
-  }
-  if (warp == 0) {
-    double q = 0.0;
-    for (int i = lane; i <= j; i += 32) q += h[i] * h[i];
-    q = warp_sum(q);
-    if (lane == 0) red[0] = q;
-  }
-  __syncthreads();
-  const double hn2 = h[j + 1] - red[0];
-  const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
-  const double inv = hn > 0 ? 1.0 / hn : 0.0;
-  for (int e = tid; e < cnt; e += ATH) w[e] = ws[e] * inv;
-  if (rank == 0) {
-    if (tid < j) {
-      csl[tid] = st->cs[tid];
-      snl[tid] = st->sn[tid];
-    }
-    __syncthreads();
-    if (tid <= j) h[tid] = hsum;
-    __syncthreads();
-    if (tid == 0) {
-      double* hc = st->H + (size_t)j * (m + 1);
-      // earlier rotations act on rows i, i+1 ≤ j; row j+1 (= hn) meets only the new one
-      for (int i = 0; i < j; ++i) {
-        const double t = csl[i] * h[i] + snl[i] * h[i + 1];
-        h[i + 1] = -snl[i] * h[i] + csl[i] * h[i + 1];
-        h[i] = t;
-      }
-      const double a = h[j], b = hn;
-      const double r = hypot(a, b);
-      const double c = r > 0 ? a / r : 1.0, sn = r > 0 ? b / r : 0.0;
-      for (int i = 0; i < j; ++i) hc[i] = h[i];
-      hc[j] = r;
-      hc[j + 1] = 0.0;
-      st->cs[j] = c;
-      st->sn[j] = sn;
-      const double gj = st->g[j];
-      st->g[j + 1] = -sn * gj;
-      st->g[j] = c * gj;
-      const double res = fabs(sn * gj);
-      st->res = res;
-      st->k = j + 1;
-      if (!isfinite(res) || !isfinite(hn)) {
-        st->status = ST_NONFINITE;
-        st->stop = 1;
-      } else if (res <= st->target) {
-        st->status = ST_CONVERGED;
-        st->stop = 1;
-      } else if (hn == 0.0) {
-        st->status = ST_BREAKDOWN;
-        st->stop = 1;
-      } else if (j + 1 >= st->kmax) {
-        st->stop = 1;  // cycle full
-      }
-    }
-  }
-  cluster.sync();  // no CTA leaves while another may still read its shared memory
-  return (rank == 0 && tid == 0) ? (st->stop ? 1 : 0) : 0;
 }
 
 // One problem. In a captured cycle (cond != 0) the step sets the while-loop condition on every
@@ -358,25 +207,14 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     kb_gmres_update(GmresState* st, const double* __restrict__ V, const int64_t* __restrict__ voff, double* x,
                     const int64_t* __restrict__ off, const int* __restrict__ nd_arr, int m) {
-  __shared__ double Rm[KMAX * KMAX];
-  __shared__ double y[KMAX];
+  __shared__ double Rc[KMAX * KMAX];
+  __shared__ double gs[KMAX], y[KMAX];
   const int b = blockIdx.x, nd = nd_arr[b];
   const GmresState* s = st + b;
   const int k = s->k;
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    const int col = t / k, row = t - col * k;
-    Rm[row * KMAX + col] = row <= col ? s->H[(size_t)col * (m + 1) + row] : 0.0;
-  }
-  for (int t = threadIdx.x; t < k; t += blockDim.x) y[t] = s->g[t];
+  stage_upper(s, k, m, Rc, gs);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = k - 1; i >= 0; --i) {
-      double t = y[i];
-      for (int l = i + 1; l < k; ++l) t -= Rm[i * KMAX + l] * y[l];
-      const double d = Rm[i * KMAX + i];
-      y[i] = d != 0.0 ? t / d : 0.0;
-    }
-  }
+  if (threadIdx.x < 32) upper_solve_warp(Rc, gs, k, y);
   __syncthreads();
   const double* Vb = V + voff[b];
   double* xb = x + off[b];
@@ -413,23 +251,12 @@ __global__ void kb_axpy(double* x, const double* __restrict__ d, int64_t n) {
 // shared memory and updates its own elements of x
 __global__ void __launch_bounds__(256) k_gmres_update_par(GmresState* st, const double* __restrict__ V, double* x,
                                                           int nd, int m) {
-  __shared__ double Rm[KMAX * KMAX];
-  __shared__ double y[KMAX];
+  __shared__ double Rc[KMAX * KMAX];
+  __shared__ double gs[KMAX], y[KMAX];
   const int k = st->k;
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    const int col = t / k, row = t - col * k;
-    Rm[row * KMAX + col] = row <= col ? st->H[(size_t)col * (m + 1) + row] : 0.0;
-  }
-  for (int t = threadIdx.x; t < k; t += blockDim.x) y[t] = st->g[t];
+  stage_upper(st, k, m, Rc, gs);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = k - 1; i >= 0; --i) {
-      double t = y[i];
-      for (int l = i + 1; l < k; ++l) t -= Rm[i * KMAX + l] * y[l];
-      const double d = Rm[i * KMAX + i];
-      y[i] = d != 0.0 ? t / d : 0.0;
-    }
-  }
+  if (threadIdx.x < 32) upper_solve_warp(Rc, gs, k, y);
   __syncthreads();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < nd) {
@@ -482,6 +309,19 @@ struct CycleResult {
 
 static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, int op, cudaGraphExec_t* out);
 
+// Iterations (application + Arnoldi step) per body of the captured while loop. Inside a body the
+// kernels follow each other with programmatic launch; between bodies the graph waits for the
+// body to finish and re-evaluates the loop condition. IBDL_UNROLL=u (1..8) overrides.
+static int cycle_unroll() {
+  static int v = 0;
+  if (!v) {
+    const char* e = getenv("IBDL_UNROLL");
+    const int u = e ? atoi(e) : 0;
+    v = (u >= 1 && u <= 8) ? u : 2;
+  }
+  return v;
+}
+
 static ibdl_status gmres_cycle_graph(Geometry* g, int prec, int op, const double* r0, double* x, double target,
                                      int m, int budget, cudaStream_t s, CycleResult* cr) {
   const int pi = 2 * op + (prec == IBDL_FP32 ? 1 : 0);
@@ -503,8 +343,9 @@ static ibdl_status gmres_cycle_graph(Geometry* g, int prec, int op, const double
   IBDL_CUDA(cudaMemcpyAsync(&hs[0], st, sizeof(HostStatus), cudaMemcpyDeviceToHost, s));
   IBDL_CUDA(cudaStreamSynchronize(s));
   const HostStatus fin = hs[0];
-  const int bodies = fin.body_iters > 0 ? fin.body_iters : 1;
-  g->launches += 2 + 4 * (int64_t)bodies;
+  const int U = cycle_unroll();
+  const int bodies = fin.body_iters > 0 ? (fin.body_iters + U - 1) / U : 1;
+  g->launches += 2 + 4 * (int64_t)U * bodies;
   cr->its = fin.k;
   cr->status = fin.status;
   cr->res = fin.res;
@@ -537,7 +378,7 @@ static cudaError_t arnoldi_attrs() {
 }
 
 // Cluster size: 16 when a 16-CTA cluster of this kernel fits on the device, else 8. The basis
-// slices are staged in shared memory when (m + 2) slices fit.
+// slices are staged in shared memory when w's slice and m + 1 basis rows fit.
 static ibdl_status arnoldi_cfg(Geometry* g, int m, ArnoldiCfg* c) {
   static int cl_choice = 0;
   if (!cl_choice) {
@@ -566,7 +407,7 @@ static ibdl_status arnoldi_cfg(Geometry* g, int m, ArnoldiCfg* c) {
   const int nd = (int)(g->ncomp * g->M);
   c->cl = cl_choice;
   c->slice = (nd + c->cl - 1) / c->cl;
-  const size_t staged_bytes = (size_t)(m + 2) * c->slice * sizeof(double);
+  const size_t staged_bytes = arnoldi_staged_doubles(m, c->slice) * sizeof(double);
   c->staged = staged_bytes <= 200 * 1024;
   c->dyn = c->staged ? staged_bytes : (size_t)c->slice * sizeof(double);
   if (c->dyn > 200 * 1024) return fail(IBDL_ERR_UNSUPPORTED, "too many boundary unknowns for the Arnoldi kernel");
@@ -602,9 +443,10 @@ static cudaError_t launch_arnoldi(const ArnoldiCfg& c, GmresState* st, double* V
                   : launch_arnoldi_t<false, 8>(c, st, V, j, nd, m, cond, s);
 }
 
-// A GMRES cycle as a CUDA graph: one conditional while node whose body is the operator
-// application on V_k (k read on the device) followed by the Arnoldi step, which sets the loop
-// condition. Built once per geometry, operator (A or Aᵀ), precision and restart length.
+// A GMRES cycle as a CUDA graph: one conditional while node whose body is cycle_unroll() pairs of
+// the operator application on V_k (k read on the device) and the Arnoldi step; every Arnoldi step
+// sets the loop condition (a step after the stop only returns). Built once per geometry, operator
+// (A or Aᵀ), precision and restart length.
 static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, int op, cudaGraphExec_t* out) {
   *out = nullptr;
   const int nd = (int)(g->ncomp * g->M);
@@ -635,11 +477,13 @@ static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, int op, cudaG
     capturing = true;
     const int saved_timing = g->timing;
     g->timing = 0;
-    ret = g->dim == 2 ? apply_2d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop, op)
-                      : apply_3d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop, op);
-    if (ret == IBDL_OK) {
-      const cudaError_t le = launch_arnoldi(c, st, g->V, -1, nd, m, h, cs);
-      if (le != cudaSuccess) ret = cuda_fail(le, "Arnoldi launch");
+    for (int u = 0; u < cycle_unroll() && ret == IBDL_OK; ++u) {
+      ret = g->dim == 2 ? apply_2d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop, op)
+                        : apply_3d_indexed(g, prec, g->V, &st->k, nd, cs, &st->stop, op);
+      if (ret == IBDL_OK) {
+        const cudaError_t le = launch_arnoldi(c, st, g->V, -1, nd, m, h, cs);
+        if (le != cudaSuccess) ret = cuda_fail(le, "Arnoldi launch");
+      }
     }
     g->timing = saved_timing;
     cudaGraph_t captured = nullptr;
@@ -949,7 +793,7 @@ static ibdl_status build_batch_graph(Batch* B, int prec, cudaGraphExec_t* out) {
     const int nd = (int)(B->off[b + 1] - B->off[b]);
     maxslice = std::max(maxslice, (nd + B->cl - 1) / B->cl);
   }
-  const size_t staged_bytes = (size_t)(B->m + 2) * maxslice * sizeof(double);
+  const size_t staged_bytes = arnoldi_staged_doubles(B->m, maxslice) * sizeof(double);
   const bool staged = staged_bytes <= 200 * 1024;
   const size_t dyn = staged ? staged_bytes : (size_t)maxslice * sizeof(double);
   if (dyn > 200 * 1024) return fail(IBDL_ERR_UNSUPPORTED, "too many boundary unknowns for the Arnoldi kernel");
