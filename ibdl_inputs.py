@@ -225,6 +225,7 @@ class Problem:
     symbol: str = "spectral"  # "spectral" | "fd2"
     rtol: float = 1e-10
     meta: dict = field(default_factory=dict)
+    bc: str = "dirichlet"  # "dirichlet": Ub holds U_b; "neumann": Ub holds V_b = ∂u/∂n (Sec. 5.2)
 
     @property
     def h(self) -> float:
@@ -334,3 +335,42 @@ def paper_circle_helmholtz(N: int, alpha: float, delta: str = "sqrt", symbol: st
     return Problem("paper_circle_helmholtz", 2, N, 1.0, (-0.5, -0.5), bd, Ub, "scalar",
                    lam=1.0, delta=delta, dipole=dipole, symbol=symbol, rtol=1e-8,
                    meta={"alpha": alpha})
+
+
+def paper_circle_neumann(N: int, alpha: float = 0.75, lam: float = 1.0, delta: str = "sqrt",
+                         symbol: str = "fd2", dipole: str = "analytic") -> Problem:
+    """Neumann problem on the paper's circle (Sec. 5.2; geometry of Sec. 5.6): Δu − λu = 0 inside
+    r = 0.25 centred in [−0.5, 0.5]², u = I₂(√λ r) sin 2θ / I₂(√λ R), so the unknown U_b = u|Γ is
+    sin 2θ and the data are V_b = ∂u/∂n = √λ I₂'(√λ R)/I₂(√λ R) sin 2θ. Δs ≈ alpha·Δx."""
+    from scipy.special import iv, ivp
+
+    h = 1.0 / N
+    R = 0.25
+    M = points_for_spacing(2 * np.pi * R, h, alpha)
+    bd = circle(M, R, (0.0, 0.0))
+    th = bd.meta["theta"]
+    k = math.sqrt(lam)
+    Vb = (k * ivp(2, k * R) / iv(2, k * R) * np.sin(2 * th))[None, :]
+    return Problem("paper_circle_neumann", 2, N, 1.0, (-0.5, -0.5), bd, Vb, "scalar", lam=lam,
+                   delta=delta, dipole=dipole, symbol=symbol, rtol=1e-10, bc="neumann",
+                   meta={"alpha": alpha, "exact_Ub": np.sin(2 * th)[None, :]})
+
+
+def brinkman_flow(x, y, lam: float, mu: float = 1.0, angle: float = 0.3):
+    """A Brinkman flow without forcing: stream function ψ = e^{κ(x cos a + y sin a)}, κ = √(λ/μ),
+    u = (∂_y ψ, −∂_x ψ) with constant pressure, so μΔu − λu = 0 and ∇·u = 0 (not a Stokes flow)."""
+    k = math.sqrt(lam / mu)
+    e = np.exp(k * ((x - 0.5) * math.cos(angle) + (y - 0.5) * math.sin(angle)))
+    return np.stack([k * math.sin(angle) * e, -k * math.cos(angle) * e])
+
+
+def circle_brinkman(N: int = 128, M: int = 200, lam: float = 10.0, mu: float = 1.0, delta: str = "cos",
+                    symbol: str = "spectral", dipole: str = "analytic") -> Problem:
+    """Interior Brinkman problem (Sec. 6.3.2, η = 0): circle R = 0.25 about (0.5, 0.5) in the unit
+    box, L = μΔ − λ, boundary data the exact flow ``brinkman_flow`` (flux removed, rounding level)."""
+    bd = circle(M, 0.25, (0.5, 0.5))
+    U = brinkman_flow(bd.X[0], bd.X[1], lam, mu)
+    U, flux = remove_normal_flux(U, bd)
+    return Problem("circle_brinkman", 2, N, 1.0, (0.0, 0.0), bd, U, "stokes", lam=lam, mu=mu,
+                   delta=delta, dipole=dipole, symbol=symbol, rtol=1e-10, meta={"removed_flux": flux})
+

@@ -122,9 +122,14 @@ class Geometry:
     delta: str = "cos"
     dipole: str = "analytic"  # "analytic" | "spectral_div"
     symbol: str = "spectral"  # "spectral" | "fd2"
-    pde: str = "scalar"  # "scalar" (L = Δ − λ) | "stokes" (μΔ, η = 0)
+    pde: str = "scalar"  # "scalar" (L = Δ − λ) | "stokes" (L = μΔ − λ: Stokes λ = 0, Brinkman λ = k² > 0)
     lam: float = 0.0
     mu: float = 1.0
+    bc: str = "dirichlet"  # "dirichlet" (jump +½) | "neumann" (jump −½, Sec. 5.2; scalar)
+
+    @property
+    def jump(self) -> float:
+        return -0.5 if self.bc == "neumann" else 0.5
 
     @property
     def M(self) -> int:
@@ -138,7 +143,7 @@ class Geometry:
 def geometry_from_problem(p) -> Geometry:
     """Build a Geometry from an ``ibdl_inputs.Problem``."""
     return Geometry(Grid(p.dim, p.N, p.box, p.origin), p.bd.X, p.bd.n, p.bd.w, p.delta,
-                    p.dipole, p.symbol, p.pde, p.lam, p.mu)
+                    p.dipole, p.symbol, p.pde, p.lam, p.mu, getattr(p, "bc", "dirichlet"))
 
 
 def _stencil(geom: Geometry):
@@ -352,8 +357,13 @@ def stokes_velocity(geom: Geometry, Q: np.ndarray) -> np.ndarray:
     u = np.zeros((d,) + g.shape)
     for l in range(d):
         Pg = g_hat[l] - (-1j * der[l]) * kdotg * inv
-        U = (der[l] * s_hat + Pg) * inv
-        U[~nz] = 0.0
+        if geom.lam > 0:
+            # Brinkman (Sec. 6.3.2, Eq. "brink ibdl eqn", η = 0): L = μΔ − λ, so the projected
+            # dipole term is μ P̂ĝ/(μ|k|² + λ) (defined at k = 0); the source term is unchanged
+            U = der[l] * s_hat * inv + Pg * (geom.mu / (geom.mu * lap + geom.lam))
+        else:
+            U = (der[l] * s_hat + Pg) * inv
+            U[~nz] = 0.0
         u[l] = np.real(np.fft.ifftn(U))
     return u
 
@@ -367,13 +377,14 @@ def grid_field(geom: Geometry, Q: np.ndarray) -> np.ndarray:
 
 def apply(geom: Geometry, Q: np.ndarray) -> np.ndarray:
     """A Q = S* u + ½ Q with u the grid field of Q: scalar A Q = −S*L⁻¹S̃Q + ½Q (Sec. 5.3.2),
-    Stokes A Q = S* u(Q) + ½Q (Sec. 6.3.3). Q and the result are flat SoA arrays (c·M,)."""
+    Stokes A Q = S* u(Q) + ½Q (Sec. 6.3.3). Q and the result are flat SoA arrays (c·M,).
+    Neumann (Sec. 5.2, Eq. "Neumann saddle point"): the jump term is −½Q and the unknown is U_b."""
     Q = np.asarray(Q, dtype=np.float64).reshape(-1)
     if geom.pde == "stokes":
         d = geom.grid.dim
         u = stokes_velocity(geom, Q)
-        return np.concatenate([interp(geom, u[l]) for l in range(d)]) + 0.5 * Q
-    return interp(geom, field_scalar(geom, Q)) + 0.5 * Q
+        return np.concatenate([interp(geom, u[l]) for l in range(d)]) + geom.jump * Q
+    return interp(geom, field_scalar(geom, Q)) + geom.jump * Q
 
 
 def dipole_adjoint(geom: Geometry, u: np.ndarray) -> np.ndarray:
@@ -396,7 +407,7 @@ def adjoint_apply(geom: Geometry, W: np.ndarray) -> np.ndarray:
     if geom.pde != "scalar":
         raise NotImplementedError("adjoint implemented for the scalar operator")
     W = np.asarray(W, dtype=np.float64).reshape(-1)
-    return 0.5 * W + dipole_adjoint(geom, minus_Linv(geom, spread(geom, W)))
+    return geom.jump * W + dipole_adjoint(geom, minus_Linv(geom, spread(geom, W)))
 
 
 def dense_operator(geom: Geometry, fn=apply) -> np.ndarray:
@@ -624,7 +635,8 @@ def _multiplier_T(geom: Geometry, psi):
     P = [np.fft.fftn(psi[l]) for l in range(d)]
     kp = sum(kt[l] * P[l] for l in range(d))
     vs = np.real(np.fft.ifftn(-1j * kp * inv))
-    vg = [np.real(np.fft.ifftn((P[m] - kt[m] * kp * inv) * inv)) for m in range(d)]
+    ginv = geom.mu / (geom.mu * lap + geom.lam) if geom.lam > 0 else inv  # Brinkman: μ/(μ|k|² + λ)
+    vg = [np.real(np.fft.ifftn((P[m] - kt[m] * kp * inv) * ginv)) for m in range(d)]
     return [vs] + vg
 
 
@@ -668,7 +680,7 @@ def stokes_transpose_apply(geom: Geometry, mu: np.ndarray) -> np.ndarray:
     mu = np.asarray(mu, dtype=np.float64).reshape(d, M)
     psi = [spread_unweighted(geom, mu[l]) for l in range(d)]
     dQ, _, _, _ = _spread_terms(geom, np.zeros(d * M), _multiplier_T(geom, psi))
-    return (0.5 * mu + dQ).reshape(-1)
+    return (geom.jump * mu + dQ).reshape(-1)
 
 
 def stokes_param_gradient(geom: Geometry, Q: np.ndarray, mu: np.ndarray):
@@ -686,6 +698,20 @@ def stokes_param_gradient(geom: Geometry, Q: np.ndarray, mu: np.ndarray):
     psi = [spread_unweighted(geom, mu[l]) for l in range(d)]
     _, sX, sn, sw = _spread_terms(geom, Q, _multiplier_T(geom, psi))
     return dX + sX, sn, sw
+
+
+def single_layer(geom: Geometry, V: np.ndarray) -> np.ndarray:
+    """S*(−L⁻¹)(S V): the single-layer operator of the scalar method (the IBSL Schur complement up
+    to sign, Sec. 2.2.3), which carries the Neumann data into the right-hand side."""
+    if geom.pde != "scalar":
+        raise NotImplementedError("single layer: scalar operator")
+    return interp(geom, minus_Linv(geom, spread(geom, np.asarray(V, dtype=np.float64).reshape(-1))))
+
+
+def neumann_rhs(geom: Geometry, Vb: np.ndarray) -> np.ndarray:
+    """Right-hand side S*L⁻¹SV_b of the Neumann equation (Sec. 5.2, Eq. "Neumann saddle point",
+    g̃ = 0) for the normal derivative V_b: −single_layer(V_b)."""
+    return -single_layer(geom, Vb)
 
 
 def probe_geometry(geom: Geometry, P: np.ndarray) -> Geometry:

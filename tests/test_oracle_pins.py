@@ -673,3 +673,99 @@ def test_probe_objective_gradient_against_finite_differences(pde):
             d[m * geom.M + i] = 1e-6
             assert (J(ub=Ub + d) - J(ub=Ub - d)) / 2e-6 == pytest.approx(dUb[m * geom.M + i], rel=1e-5, abs=1e-9)
     _fd_check(J, {"X": geom.X, "n": geom.n, "w": geom.w}, {"X": pX + sX, "n": pn + sn, "w": pw + sw}, idx, rng)
+
+
+# ----------------------------------------------------------------------------------------
+# Brinkman (Sec. 6.3.2) and Neumann (Sec. 5.2)
+# ----------------------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("lam,mu", [(10.0, 1.0), (40.0, 0.5)])
+def test_brinkman_velocity_satisfies_pde(lam, mu):
+    """Mode by mode away from Nyquist: ∇·u + S(Q·n) = 0 and μΔu − λu + μ∇·(S A) = ∇p for some p
+    (zero discrete curl), the interior Brinkman system of Sec. 6.3.2 with η = 0."""
+    geom, bd = _stokes_geom(32)
+    geom.lam, geom.mu = lam, mu
+    g = geom.grid
+    rng = np.random.default_rng(10)
+    Q = rng.standard_normal((2, bd.M))
+    u = O.stokes_velocity(geom, Q.reshape(-1))
+    lap, der = O.symbols(g, "spectral")
+    Uh = [np.fft.fftn(u[0]), np.fft.fftn(u[1])]
+    sh = np.fft.fftn(O.spread(geom, np.sum(Q * bd.n, 0)))
+    A = [[Q[l] * bd.n[m] + Q[m] * bd.n[l] for m in range(2)] for l in range(2)]
+    gh = [np.fft.fftn(O.spread_grad(geom, np.array(A[l]))) for l in range(2)]
+    kx = np.broadcast_to(np.fft.fftfreq(32, 1 / 32)[None, :], g.shape)
+    ky = np.broadcast_to(np.fft.fftfreq(32, 1 / 32)[:, None], g.shape)
+    ok = (np.abs(kx) != 16) & (np.abs(ky) != 16) & (lap != 0)
+    div = der[0] * Uh[0] + der[1] * Uh[1] + sh
+    assert np.abs(div[ok]).max() < 1e-9 * np.abs(sh).max()
+    mom = [-(mu * lap + lam) * Uh[l] + mu * gh[l] for l in range(2)]
+    curl = der[0] * mom[1] - der[1] * mom[0]
+    assert np.abs(curl[ok]).max() < 1e-9 * np.abs(gh[0]).max() * 2 * np.pi * 16
+    # the same velocity is not a Stokes one: the λ term matters
+    mom0 = [-lap * Uh[l] + gh[l] for l in range(2)]
+    assert np.abs((der[0] * mom0[1] - der[1] * mom0[0])[ok]).max() > 1e-3 * np.abs(gh[0]).max()
+
+
+def test_brinkman_tends_to_stokes():
+    geom, bd = _stokes_geom(32)
+    Q = np.random.default_rng(11).standard_normal(2 * bd.M)
+    ref = O.apply(geom, Q)
+    geom.lam = 1e-6
+    assert np.linalg.norm(O.apply(geom, Q) - ref) < 1e-5 * np.linalg.norm(ref)
+
+
+def test_brinkman_first_order():
+    """Interior velocity against the exact unforced Brinkman flow (λ = 100, μ = 1), r < 0.15,
+    relative to its maximum: first order. The Stokes operator on the same data does not approach
+    it (the flow is not a Stokes flow), so the λ term of the symbol is what converges."""
+    errs = []
+    for N in (64, 128, 256):
+        M = I.points_for_spacing(2 * np.pi * 0.25, 1.0 / N, 1.2)
+        p = I.circle_brinkman(N, M, lam=100.0, delta="sqrt")
+        geom = O.geometry_from_problem(p)
+        res = O.solve(geom, p.Ub.reshape(-1), 1e-10, maxit=80)
+        assert res.iterations <= 16
+        u = O.stokes_velocity(geom, res.x)
+        x, y = geom.grid.coords()
+        r = np.hypot(x - 0.5, y - 0.5)
+        exact = I.brinkman_flow(x, y, 100.0)
+        scale = np.abs(exact).max(0)[r < 0.15].max()
+        errs.append(np.abs(u - exact).max(0)[r < 0.15].max() / scale)
+    assert O.fitted_order([1 / 64, 1 / 128, 1 / 256], errs) > 0.85
+    geom.lam = 0.0
+    u0 = O.stokes_velocity(geom, O.solve(geom, p.Ub.reshape(-1), 1e-10, maxit=80).x)
+    assert np.abs(u0 - exact).max(0)[r < 0.15].max() / scale > 5 * errs[-1]
+
+
+def test_neumann_operator_is_dirichlet_minus_identity():
+    geom, bd = _circle_geom(32, "sqrt", 1.0)
+    Q = np.random.default_rng(12).standard_normal(bd.M)
+    ref = O.apply(geom, Q)
+    geom.bc = "neumann"
+    assert np.allclose(O.apply(geom, Q), ref - Q, atol=1e-14)
+
+
+def test_single_layer_weighted_symmetric():
+    """W·S*(−L⁻¹)S is symmetric (S* is the adjoint of S under the weighted products, −L⁻¹ is
+    symmetric), and positive for λ > 0 (−L⁻¹ has a positive symbol)."""
+    geom, bd = _circle_geom(16, "cos", 2.0)
+    geom.w = geom.w * (1 + 0.3 * np.sin(np.arange(bd.M)))
+    SL = np.stack([O.single_layer(geom, e) for e in np.eye(bd.M)], axis=1)
+    WS = geom.w[:, None] * SL
+    assert np.allclose(WS, WS.T, atol=1e-12 * np.abs(WS).max())
+    assert np.linalg.eigvalsh(0.5 * (WS + WS.T)).min() > -1e-12 * np.abs(WS).max()
+
+
+def test_neumann_first_order():
+    """The Neumann solve (Sec. 5.2) on the paper's circle: U_b → u|Γ = sin 2θ at first order, in a
+    few GMRES iterations (the paper reports 4-6 for its Neumann test, Sec. 5.7)."""
+    errs = []
+    for N in (64, 128, 256):
+        p = I.paper_circle_neumann(N)
+        geom = O.geometry_from_problem(p)
+        res = O.solve(geom, O.neumann_rhs(geom, p.Ub.reshape(-1)), 1e-10, maxit=60)
+        assert res.iterations <= 12
+        errs.append(np.abs(res.x - p.meta["exact_Ub"].reshape(-1)).max())
+    assert O.fitted_order([1 / 64, 1 / 128, 1 / 256], errs) > 0.8
