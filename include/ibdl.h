@@ -56,7 +56,14 @@ typedef enum {
 
 /* PDE on the periodic box */
 enum { IBDL_PDE_SCALAR = 0, /* L = Δ − λ (Sec. 5.1.1); λ = 0 uses the mean-zero Δ₀⁻¹ (Sec. 2.2.4) */
-       IBDL_PDE_STOKES = 1  /* μΔu − ∇p, interior, η = 0 (Sec. 6.3.3); dim = 2 only           */ };
+       IBDL_PDE_STOKES = 1  /* μΔu − λu − ∇p, interior, η = 0: Stokes for λ = 0 (Sec. 6.3.3),
+                               Brinkman for λ = k² > 0 (Sec. 6.3.2); dim = 2 only             */ };
+
+/* boundary condition of the scalar problem */
+enum { IBDL_BC_DIRICHLET = 0, /* S*u + ½Q = U_b (Sec. 5.1.1)                                       */
+       IBDL_BC_NEUMANN = 1    /* S*u = ½U_b with U_b the unknown, ∂u/∂n = V_b (Sec. 5.2): the
+                                 operator is (−S*L⁻¹S̃ − ½) and the right-hand side S*L⁻¹S V_b
+                                 is −ibdl_single_layer(V_b) (scalar PDE only)                    */ };
 
 /* one-dimensional 4-point kernel φ of δ_h = h^-d Π φ(x_j/h) (Sec. 2.2.2) */
 enum { IBDL_DELTA_COS = 0,  /* φ(r) = (1 + cos(πr/2))/4, |r| < 2                            */
@@ -86,12 +93,13 @@ typedef struct {
   const double* normals;/* [dim][M] unit normals pointing out of Ω                          */
   const double* weights;/* [M] quadrature weights Δs_i (arclength, Sec. 2.2.2)               */
   int pde;              /* IBDL_PDE_*                                                       */
-  double lambda;        /* screening λ ≥ 0 for IBDL_PDE_SCALAR                               */
-  double mu;            /* viscosity μ > 0 for IBDL_PDE_STOKES (cancels from A when η = 0)   */
+  double lambda;        /* λ ≥ 0: L = Δ − λ (scalar); L = μΔ − λ (Stokes λ = 0, Brinkman λ > 0) */
+  double mu;            /* viscosity μ > 0 for IBDL_PDE_STOKES (cancels from A when λ = 0)   */
   int delta;            /* IBDL_DELTA_*                                                     */
   int dipole;           /* IBDL_DIPOLE_*                                                    */
   int symbol;           /* IBDL_SYMBOL_*                                                    */
   int inputs_on_device; /* nonzero: X, normals, weights are device pointers                 */
+  int bc;               /* IBDL_BC_* (0, Dirichlet, for a zero-initialised descriptor)      */
 } ibdl_geometry_desc;
 
 typedef struct {
@@ -156,6 +164,13 @@ ibdl_status ibdl_adjoint(ibdl_geometry* geom, int precision, const double* W, do
  * Returns IBDL_ERR_NOT_CONVERGED (Q = best iterate) when maxit is reached. `info` may be NULL. */
 ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const ibdl_solve_opts* opts,
                        ibdl_solve_info* info, void* stream);
+
+/* Z = S*(−L⁻¹)(S V): the single-layer operator of the scalar method (the constraint method's
+ * Schur complement up to sign, Sec. 2.2.3), with S the Δs-weighted spread and S* the
+ * interpolation. It carries Neumann data into the right-hand side of the Neumann equation
+ * (Sec. 5.2, Eq. "Neumann saddle point", g̃ = 0): rhs = −Z(V_b). Scalar PDE, 2-D; V and Z are
+ * device FP64 [M] that may not alias; asynchronous. */
+ibdl_status ibdl_single_layer(ibdl_geometry* geom, int precision, const double* V, double* Z, void* stream);
 
 /* Differentiation. The paper states no derivative; these follow from the operators of
  * Sec. 5.3.2 and Sec. 6.3.3 by the adjoint method. Both operators are
@@ -240,10 +255,11 @@ ibdl_status ibdl_destroy_batch(ibdl_batch* batch);
  * concatenated boundary vectors. */
 ibdl_status ibdl_batch_sizes(const ibdl_batch* batch, int* count, int64_t* offsets, int64_t* total);
 
-/* Autotune a batch: time the whole batched application for each candidate FFT volume per CTA
- * (512 to 8192 complex elements; every problem's rows per band and columns per group follow
- * from it), keep the fastest per precision, and rebuild the batched launch tables. Allocates
- * and frees a scratch vector. Synchronises `stream`. */
+/* Autotune a batch: time the whole batched application for each pair of candidate FFT volumes
+ * per CTA, one for the row kernels and one for the column kernel (512 to 8192 complex elements
+ * each; every problem's rows per band and columns per group follow from them), keep the
+ * fastest pair per precision, and rebuild the batched launch tables. Allocates and frees a
+ * scratch vector. Synchronises `stream`. */
 ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* stream);
 
 /* Y = A Q for every problem of the batch (concatenated device FP64 arrays; FP64 or FP32 grid

@@ -199,6 +199,18 @@ ibdl_status ibdl_apply_transpose(ibdl_geometry* geom, int precision, const doubl
   return apply_any(g, precision, G, Z, static_cast<cudaStream_t>(stream), nullptr, OPK_AT);
 }
 
+ibdl_status ibdl_single_layer(ibdl_geometry* geom, int precision, const double* V, double* Z, void* stream) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
+  Geometry* g = geom->g;
+  if (g->pde != IBDL_PDE_SCALAR || g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_single_layer: scalar PDE in 2-D only");
+  IBDL_TRY(check_device_ptr(V, "V"));
+  IBDL_TRY(check_device_ptr(Z, "Z"));
+  if (ranges_overlap(V, Z, sizeof(double) * g->M)) return fail(IBDL_ERR_INVALID_ARG, "V and Z overlap");
+  return single_layer_2d(g, precision, V, Z, static_cast<cudaStream_t>(stream));
+}
+
 ibdl_status ibdl_solve_vjp(ibdl_geometry* geom, const double* Q, const double* lambda, double* dX, double* dn,
                            double* dw, void* stream) {
   set_error("");

@@ -11,10 +11,15 @@
 //   k_rowifft_gather  band of R rows: inverse FFT along x, then interpolate (S*) the band's part
 //                     of every point's stencil and add it to Y (which the first kernel set to ½Q).
 //
-// Packed half spectrum: for a real row a, A_k (k = 0..n/2) is stored at [0, n/2) with slot 0
+// Packed half spectrum: for a real row a, A_k (k = 0..n/2) is stored in n/2 slots with slot 0
 // holding (A_0, A_{n/2}), both real. Along y, the kx = 0 and kx = n/2 columns are therefore one
 // complex column a + i b with a, b real columns; the column pass separates them by Hermitian
 // symmetry before the symbol and repacks after it.
+//
+// Band-major storage: the n rows of a field form bands of R rows (the row kernels' work unit),
+// and element (row, k) of field f sits at (f·n + band·R)·(n/2) + k·R + (row mod R). A row band is
+// one contiguous block, and a column reads R contiguous values per band (128 bytes at R = 16 in
+// FP32) whatever the number of columns a CTA takes.
 #include <algorithm>
 #include <cstdlib>
 #include <mutex>
@@ -27,7 +32,7 @@
 namespace ibdl {
 
 enum { OP_SCALAR_AN = 0, OP_SCALAR_SD = 1, OP_STOKES_AN = 2, OP_STOKES_SD = 3, OP_ADJ_AN = 4,
-       OP_ADJ_SD = 5, OP_STOKES_T = 6 };
+       OP_ADJ_SD = 5, OP_STOKES_T = 6, OP_SL = 7 };
 
 // grid fields entering / leaving the Fourier stage, and boundary components in / out
 template <int OP>
@@ -48,6 +53,9 @@ struct Traits<OP_ADJ_SD> { static constexpr int NIN = 1, NOUT = 2, C = 1; };    
 // Stokes transpose (analytic dipole): ψ_x, ψ_y → v_s, v_gx, v_gy
 template <>
 struct Traits<OP_STOKES_T> { static constexpr int NIN = 2, NOUT = 3, C = 2; };
+// single layer S*(−L⁻¹)(S V): plain spread, −L⁻¹, plain interpolation, no jump term
+template <>
+struct Traits<OP_SL> { static constexpr int NIN = 1, NOUT = 1, C = 1; };
 
 enum { G_INTERP = 0, G_GRID = 1 };
 
@@ -78,6 +86,7 @@ struct RowParams {
   // carry Δs/h^d instead of 1)
   int trans;
   const double* grid_in;  // optional [NIN][n][n]: the band rows are read from it instead of spread
+  double jump;            // jump term coefficient: ½ (Dirichlet), −½ (Neumann), 0 (single layer)
 };
 
 template <typename T>
@@ -94,7 +103,9 @@ __device__ __forceinline__ void resolve_io(const RowParams<T>& p, const double*&
 template <typename T>
 struct ColParams {
   int n, log2n, C, lc;
+  int R;  // rows per band of the band-major spectrum
   T lam, scale;
+  T mu;   // viscosity (Brinkman: L = μΔ − λ)
   const T* lap1;
   const T* der1;
   cplx<T>* spec;
@@ -158,10 +169,10 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   double* pout;
   resolve_io(p, pin, pout);
 
-  // jump term: out = ½·in (the gather kernel adds S*u afterwards); none for grid input
+  // jump term: out = ±½·in (the gather kernel adds S*u afterwards); none for grid input
   if (!p.grid_in)
     for (int i = unit * blockDim.x + threadIdx.x; i < NC * M; i += nunits * blockDim.x)
-      pout[i] = 0.5 * pin[i];
+      pout[i] = p.jump * pin[i];
   __syncthreads();
 
   if (p.grid_in) {
@@ -227,25 +238,23 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
 
   const cplx<T>* res = fft_run<T, false>(bufA, bufB, p.log2n, seqs, tws);
 
-  // unpack Z = FFT(a + i b) into A = FFT(a), B = FFT(b), k = 0..n/2, packed format
-  const int nh = n >> 1, lnh = p.log2n - 1;
-  for (int t = threadIdx.x; t < seqs * nh; t += blockDim.x) {
-    const int sq = t >> lnh, k = t & (nh - 1);
-    const int f = sq / half, j = sq - f * half;
-    const int zb = sq * n;
-    cplx<T> A, B;
+  // unpack Z = FFT(a + i b) of the row pair (2j, 2j + 1) into A = FFT(a) (even rows) and
+  // B = FFT(b) (odd rows), k = 0..n/2, packed format; thread t writes element t of the field's
+  // band-major block, k·R + rr, so consecutive threads write consecutive addresses
+  const int nh = n >> 1, lnh = p.log2n - 1, lR = __ffs(R) - 1;
+  for (int t = threadIdx.x; t < NIN * nh * R; t += blockDim.x) {
+    const int rr = t & (R - 1), k = (t >> lR) & (nh - 1), f = t >> (lR + lnh);
+    const int zb = (f * half + (rr >> 1)) * n;
+    cplx<T> v;
     if (k == 0) {
       const cplx<T> z0 = res[pidx(zb)], zh = res[pidx(zb + nh)];
-      A = mk(z0.x, zh.x);
-      B = mk(z0.y, zh.y);
+      v = (rr & 1) ? mk(z0.y, zh.y) : mk(z0.x, zh.x);
     } else {
       const cplx<T> zk = res[pidx(zb + k)], zc = res[pidx(zb + n - k)];
-      A = mk(T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y));
-      B = mk(T(0.5) * (zk.y + zc.y), T(0.5) * (zc.x - zk.x));
+      v = (rr & 1) ? mk(T(0.5) * (zk.y + zc.y), T(0.5) * (zc.x - zk.x))
+                   : mk(T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y));
     }
-    const int row = r0 + 2 * j;
-    p.spec[((size_t)f * n + row) * nh + k] = A;
-    p.spec[((size_t)f * n + row + 1) * nh + k] = B;
+    p.spec[((size_t)f * n + r0) * nh + (t - f * (nh << lR))] = v;
   }
 }
 
@@ -263,11 +272,11 @@ __device__ __forceinline__ void apply_symbol(const ColParams<T>& p, const T* lap
                                              const cplx<T>* in, cplx<T>* out) {
   const T lap = lap1[kx] + lap1[ky];
   const T dkx = der1[kx], dky = der1[ky];
-  if (OP == OP_SCALAR_AN || OP == OP_SCALAR_SD || OP == OP_ADJ_AN || OP == OP_ADJ_SD) {
+  if (OP == OP_SCALAR_AN || OP == OP_SCALAR_SD || OP == OP_ADJ_AN || OP == OP_ADJ_SD || OP == OP_SL) {
     // −L⁻¹ ↦ 1/(|k|² + λ), zero mode dropped when λ = 0 (Δ₀⁻¹)
     const T den = lap + p.lam;
     const T sig = den != T(0) ? p.scale / den : T(0);
-    if (OP == OP_SCALAR_AN || OP == OP_ADJ_AN) {
+    if (OP == OP_SCALAR_AN || OP == OP_ADJ_AN || OP == OP_SL) {
       out[0] = cscale(in[0], sig);
     } else if (OP == OP_SCALAR_SD) {
       // ∇·F ↦ i(k̃_x F̂_x + k̃_y F̂_y)
@@ -283,9 +292,11 @@ __device__ __forceinline__ void apply_symbol(const ColParams<T>& p, const T* lap
     const T inv = lap != T(0) ? T(1) / lap : T(0);
     const cplx<T> kp = cadd(cscale(in[0], dkx), cscale(in[1], dky));
     const T sc = inv * p.scale;
+    // Brinkman (λ > 0): the projected part carries μ/(μ|k|² + λ) in place of 1/|k|²
+    const T sg = p.lam > T(0) ? p.mu / (p.mu * lap + p.lam) * p.scale : sc;
     out[0] = cscale(cmuli(kp), -sc);
-    out[1] = cscale(csub(in[0], cscale(kp, dkx * inv)), sc);
-    out[2] = cscale(csub(in[1], cscale(kp, dky * inv)), sc);
+    out[1] = cscale(csub(in[0], cscale(kp, dkx * inv)), sg);
+    out[2] = cscale(csub(in[1], cscale(kp, dky * inv)), sg);
   } else {
     // Stokes, interior, η = 0: û = (i k̃ ŝ + P̂ ĝ)/|k|², P̂ = I − k̃k̃ᵀ/|k|²
     const T inv = lap != T(0) ? T(1) / lap : T(0);
@@ -300,21 +311,28 @@ __device__ __forceinline__ void apply_symbol(const ColParams<T>& p, const T* lap
     const cplx<T> kg = cadd(cscale(gx, dkx), cscale(gy, dky));
     const cplx<T> is = cmuli(in[0]);
     const T sc = inv * p.scale;
-    out[0] = cscale(cadd(cscale(is, dkx), csub(gx, cscale(kg, dkx * inv))), sc);
-    out[1] = cscale(cadd(cscale(is, dky), csub(gy, cscale(kg, dky * inv))), sc);
+    if (p.lam > T(0)) {
+      // Brinkman (Sec. 6.3.2): û = i k̃ ŝ/|k|² + μ P̂ ĝ/(μ|k|² + λ), defined at k = 0 as well
+      const T sg = p.mu / (p.mu * lap + p.lam) * p.scale;
+      out[0] = cadd(cscale(is, dkx * sc), cscale(csub(gx, cscale(kg, dkx * inv)), sg));
+      out[1] = cadd(cscale(is, dky * sc), cscale(csub(gy, cscale(kg, dky * inv)), sg));
+    } else {
+      out[0] = cscale(cadd(cscale(is, dkx), csub(gx, cscale(kg, dkx * inv))), sc);
+      out[1] = cscale(cadd(cscale(is, dky), csub(gy, cscale(kg, dky * inv))), sc);
+    }
   }
 }
 
 // ------------------------------------------------------------------------------------------
 // kernel 2: FFT along y, symbol, inverse FFT along y, for C kx columns per CTA
 // ------------------------------------------------------------------------------------------
-// element m of column sequence bi = f·C + c, straight from / to the packed half spectra
+// element m of column sequence bi = f·C + c, straight from / to the band-major half spectra
 template <typename T>
 struct ColumnIO {
   cplx<T>* spec;
-  int n, nh, k0, lc, C;
+  int n, nh, k0, lc, C, R;
   __device__ __forceinline__ size_t at(int bi, int m) const {
-    return ((size_t)(bi >> lc) * n + m) * nh + k0 + (bi & (C - 1));
+    return ((size_t)(bi >> lc) * n + (m & ~(R - 1))) * nh + (size_t)(k0 + (bi & (C - 1))) * R + (m & (R - 1));
   }
   __device__ __forceinline__ cplx<T> load(int bi, int m) const { return spec[at(bi, m)]; }
   __device__ __forceinline__ void store(int bi, int m, cplx<T> v) const { spec[at(bi, m)] = v; }
@@ -341,7 +359,7 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
   cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
   if (p.stop && *p.stop) return;
   __syncthreads();
-  const ColumnIO<T> cio{p.spec, n, nh, k0, p.lc, C};
+  const ColumnIO<T> cio{p.spec, n, nh, k0, p.lc, C, p.R};
   // forward transform along y: the first stage reads the half spectra directly
   cplx<T>* res = fft_run<T, false>(bufA, bufB, p.log2n, NIN * C, tws, cio, NoIO());
   cplx<T>* other = res == bufA ? bufB : bufA;
@@ -397,24 +415,24 @@ __global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
 // kernel 3: inverse FFT along x, then interpolation (or write the grid)
 // ------------------------------------------------------------------------------------------
 // Z_m = A_m + i B_m (m = 0..n−1) for the row pair (r0 + 2j, r0 + 2j + 1) of field f, sequence
-// sq = f·half + j, rebuilt on the fly from the packed half spectra (A_{n−k} = conj A_k).
+// sq = f·half + j, rebuilt on the fly from the band-major half spectra (A_{n−k} = conj A_k):
+// A_k at band offset k·R + 2j, B_k next to it.
 template <typename T>
 struct RowZLoad {
   const cplx<T>* spec;
-  int n, nh, r0, half;
+  int n, nh, r0, half, R;
   __device__ __forceinline__ cplx<T> load(int sq, int m) const {
     const int f = sq / half, j = sq - f * half;
-    const size_t ra = ((size_t)f * n + r0 + 2 * j) * nh;
-    const size_t rb = ra + nh;
+    const cplx<T>* band = spec + ((size_t)f * n + r0) * nh + 2 * j;
     if (m == 0 || m == nh) {
-      const cplx<T> A = spec[ra], B = spec[rb];
+      const cplx<T> A = band[0], B = band[1];
       return m == 0 ? mk(A.x, B.x) : mk(A.y, B.y);
     }
     if (m < nh) {
-      const cplx<T> A = spec[ra + m], B = spec[rb + m];
+      const cplx<T> A = band[(size_t)m * R], B = band[(size_t)m * R + 1];
       return mk(A.x - B.y, A.y + B.x);
     }
-    const cplx<T> A = spec[ra + (n - m)], B = spec[rb + (n - m)];
+    const cplx<T> A = band[(size_t)(n - m) * R], B = band[(size_t)(n - m) * R + 1];
     return mk(A.x + B.y, B.x - A.y);
   }
 };
@@ -433,7 +451,7 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
   if (p.stop && *p.stop) return;
   __syncthreads();
-  const RowZLoad<T> zl{p.spec, n, nh, r0, half};
+  const RowZLoad<T> zl{p.spec, n, nh, r0, half, R};
   const cplx<T>* res = fft_run<T, true>(bufA, bufB, p.log2n, seqs, tws, zl, NoIO());
   // real values: field f, local row lr, column x at element e = (f·half + lr/2)·n + x, part lr & 1
   const T* u = reinterpret_cast<const T*>(res);
@@ -552,6 +570,7 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.io_off = 0;
   rp.trans = 0;
   rp.grid_in = nullptr;
+  rp.jump = g->bc == IBDL_BC_NEUMANN ? -0.5 : 0.5;
   return rp;
 }
 
@@ -563,7 +582,9 @@ static ColParams<T> col_params(Geometry* g, const int* stop) {
   cp.log2n = __builtin_ctz(g->n);
   cp.C = g->cols_per_cta[pi];
   cp.lc = __builtin_ctz(cp.C ? cp.C : 1);
-  cp.lam = T(g->pde == IBDL_PDE_SCALAR ? g->lambda : 0.0);
+  cp.R = g->rows_per_cta[pi];
+  cp.lam = T(g->lambda);
+  cp.mu = T(g->mu);
   cp.scale = T(1.0 / ((double)g->n * (double)g->n));
   cp.lap1 = reinterpret_cast<const T*>(pi ? (const void*)g->lap32 : (const void*)g->lap64);
   cp.der1 = reinterpret_cast<const T*>(pi ? (const void*)g->der32 : (const void*)g->der64);
@@ -636,6 +657,7 @@ static ibdl_status set_attrs_all() {
   IBDL_TRY((set_attrs<T, OP_ADJ_AN>()));
   IBDL_TRY((set_attrs<T, OP_ADJ_SD>()));
   IBDL_TRY((set_attrs<T, OP_STOKES_T>()));
+  IBDL_TRY((set_attrs<T, OP_SL>()));
   return IBDL_OK;
 }
 
@@ -655,6 +677,7 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   rp.vstride = vstride;
   rp.trans = trans;
   rp.grid_in = grid_in;
+  if (OP == OP_SL) rp.jump = 0.0;
   ColParams<T> cp = col_params<T>(g, stop);
   const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
@@ -710,6 +733,13 @@ ibdl_status apply_2d(Geometry* g, int precision, const double* Q, double* Y, cud
 ibdl_status field_pair_2d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s) {
   IBDL_TRY(apply_t<double>(g, Q, g->tmp_m, s, nullptr, u));
   return apply_t<double>(g, lam, g->tmp_m, s, nullptr, v, nullptr, 0, OPK_AT);
+}
+
+// Z = S*(−L⁻¹)(S V) (scalar PDE)
+ibdl_status single_layer_2d(Geometry* g, int precision, const double* V, double* Z, cudaStream_t s) {
+  if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "single layer: scalar PDE only");
+  return precision == IBDL_FP32 ? run_op<float, OP_SL>(g, V, Z, s, nullptr, nullptr)
+                                : run_op<double, OP_SL>(g, V, Z, s, nullptr, nullptr);
 }
 
 // v = Kᵀψ for a grid field ψ ([c][n][n]): the transpose op's Fourier stage with its row bands read
@@ -976,7 +1006,7 @@ ibdl_status autotune_2d(Geometry* g, int pi, bool fixed_threads, cudaStream_t s,
 
 // Shapes from the volume rule: about `target` complex elements of FFT per CTA, at least 16 row
 // bands and 16 column groups, R ≤ n/2 (distinct wrapped band rows), within shared memory.
-void shape_for_target_2d(Geometry* g, int pi, int target) {
+void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target) {
   const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
   const int n = g->n;
   auto clampp2 = [](int v, int lo, int hi) {
@@ -988,9 +1018,9 @@ void shape_for_target_2d(Geometry* g, int pi, int target) {
   const size_t cs = pi ? sizeof(float2) : sizeof(double2);
   auto row_bytes = [&](int r) { return (g->n + 2 * padded((size_t)nf * (r / 2) * g->n)) * cs; };
   auto col_bytes = [&](int c) { return (g->n + 2 * padded((size_t)nf * c * g->n)) * cs + 2 * g->n * cs / 2; };
-  int R = clampp2(2 * (target / (n * g->nf_in)), 2, n / 16 > 2 ? n / 16 : 2);
+  int R = clampp2(2 * (row_target / (n * g->nf_in)), 2, n / 16 > 2 ? n / 16 : 2);
   while (R > 2 && row_bytes(R) > kSmemLimit) R /= 2;
-  int C = clampp2(target / (n * nf), 1, n / 32 > 1 ? n / 32 : 1);
+  int C = clampp2(col_target / (n * nf), 1, n / 32 > 1 ? n / 32 : 1);
   while (C > 1 && col_bytes(C) > kSmemLimit) C /= 2;
   if (row_bytes(R) <= kSmemLimit && col_bytes(C) <= kSmemLimit) {
     g->rows_per_cta[pi] = R;

@@ -58,6 +58,7 @@ struct Row3Params {
   // adjoint ops only: 1 = the Euclidean transpose Aᵀ = W A* W⁻¹ (λ spread with weight 1, gathered
   // values multiplied by Δs/h³ in place of the spread's Δs/h³ · W⁻¹)
   int trans;
+  double jump;  // jump term coefficient: ½ (Dirichlet) or −½ (Neumann)
 };
 
 struct Col3Params {
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(kThreads3) k3_spread_rowfft(Row3Params p) {
   const double* pin;
   double* pout;
   resolve_io3(p, pin, pout);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) pout[i] = 0.5 * pin[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) pout[i] = p.jump * pin[i];
   for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
   load_twiddles(tws, static_cast<const cplx<T>*>(p.tw), n);
   __syncthreads();
@@ -570,6 +571,7 @@ static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStrea
   rp.idx = idx;
   rp.vstride = vstride;
   rp.trans = trans;
+  rp.jump = g->bc == IBDL_BC_NEUMANN ? -0.5 : 0.5;
   Col3Params cp;
   cp.n = n;
   cp.log2n = rp.log2n;

@@ -133,15 +133,17 @@ ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* str
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // one knob for the whole batch: the FFT volume per CTA of the shape rule, timed on the
-  // batched application itself (throughput, not one problem's latency)
+  // two knobs for the whole batch: the FFT volume per CTA of the row kernels and of the column
+  // kernel (the band-major spectra make tall row bands and narrow column groups a useful pair),
+  // timed on the batched application itself (throughput, not one problem's latency)
   const int targets[5] = {512, 1024, 2048, 4096, 8192};
   for (int pi = 0; pi < 2 && st == IBDL_OK; ++pi) {
     if (!(precision_mask & (pi ? 2 : 1))) continue;
     float best = 1e30f;
-    int best_t = targets[0];
-    for (int ti = 0; ti < 5 && st == IBDL_OK; ++ti) {
-      for (int i = 0; i < B->count; ++i) shape_for_target_2d(B->geoms[i], pi, targets[ti]);
+    int best_t = targets[0], best_c = targets[0];
+    for (int ti = 0; ti < 25 && st == IBDL_OK; ++ti) {
+      const int tr = targets[ti / 5], tc = targets[ti % 5];
+      for (int i = 0; i < B->count; ++i) shape_for_target_2d(B->geoms[i], pi, tr, tc);
       st = batch_prepare_2d(B);
       if (st != IBDL_OK) break;
       float ms[3];
@@ -157,11 +159,12 @@ ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* str
       std::sort(ms, ms + 3);
       if (ms[1] < best) {
         best = ms[1];
-        best_t = targets[ti];
+        best_t = tr;
+        best_c = tc;
       }
     }
     if (st == IBDL_OK)
-      for (int i = 0; i < B->count; ++i) shape_for_target_2d(B->geoms[i], pi, best_t);
+      for (int i = 0; i < B->count; ++i) shape_for_target_2d(B->geoms[i], pi, best_t, best_c);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -264,8 +264,10 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
   if (!d->X || !d->normals || !d->weights) return fail(IBDL_ERR_INVALID_ARG, "X, normals and weights are required");
   if (d->pde != IBDL_PDE_SCALAR && d->pde != IBDL_PDE_STOKES) return fail(IBDL_ERR_INVALID_ARG, "unknown pde");
   if (d->pde == IBDL_PDE_STOKES && d->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "Stokes is implemented in 2-D only");
-  if (d->pde == IBDL_PDE_SCALAR && (!(d->lambda >= 0) || !std::isfinite(d->lambda)))
-    return fail(IBDL_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+  if (!(d->lambda >= 0) || !std::isfinite(d->lambda)) return fail(IBDL_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+  if (d->bc != IBDL_BC_DIRICHLET && d->bc != IBDL_BC_NEUMANN) return fail(IBDL_ERR_INVALID_ARG, "unknown boundary condition");
+  if (d->bc == IBDL_BC_NEUMANN && d->pde != IBDL_PDE_SCALAR)
+    return fail(IBDL_ERR_UNSUPPORTED, "Neumann conditions are implemented for the scalar PDE");
   if (d->pde == IBDL_PDE_STOKES && (!(d->mu > 0) || !std::isfinite(d->mu)))
     return fail(IBDL_ERR_INVALID_ARG, "mu must be finite and > 0");
   if (d->delta != IBDL_DELTA_COS && d->delta != IBDL_DELTA_SQRT) return fail(IBDL_ERR_INVALID_ARG, "unknown delta");
@@ -306,6 +308,7 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
   g->h = h;
   g->lambda = d->lambda;
   g->mu = d->mu;
+  g->bc = d->bc;
   for (int j = 0; j < 3; ++j) g->origin[j] = j < dim ? d->origin[j] : 0.0;
   g->M = M;
   g->ncomp = d->pde == IBDL_PDE_STOKES ? dim : 1;

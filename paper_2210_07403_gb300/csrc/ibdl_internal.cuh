@@ -80,6 +80,7 @@ struct PointTable {
 struct Geometry {
   // description
   int dim, n, pde, delta, dipole, symbol;
+  int bc;          // IBDL_BC_*: the jump term is +½Q (Dirichlet) or −½Q (Neumann)
   double box, h, lambda, mu;
   double origin[3];
   int64_t M;
@@ -175,7 +176,8 @@ struct Batch {
 
 ibdl_status batch_prepare_2d(Batch* B);
 ibdl_status autotune_2d(Geometry* g, int pi, bool fixed_threads, cudaStream_t s, const double* Q, double* Y);
-void shape_for_target_2d(Geometry* g, int pi, int target);
+// launch shape from FFT volumes per CTA: rows per band from row_target, kx columns from col_target
+void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target);
 size_t batch_state_bytes();  // sizeof the per-problem GMRES state (stop, status, k are its first ints)
 ibdl_status batch_apply_2d(Batch* B, int precision, int mode, const double* in_base, double* out_base,
                            cudaStream_t s);
@@ -208,6 +210,7 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
 // grid fields u = K[sources(Q)] and v = Kᵀ(Σ_j λ_j Φ(x − X_j)) (K = −L⁻¹ scalar, the Stokes
 // multiplier otherwise), then the boundary derivatives; Kᵀ of a given grid field (2-D)
 ibdl_status transform_T_2d(Geometry* g, const double* psi, double* v, cudaStream_t s);
+ibdl_status single_layer_2d(Geometry* g, int precision, const double* V, double* Z, cudaStream_t s);
 ibdl_status field_pair_2d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s);
 ibdl_status field_pair_3d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s);
 ibdl_status solve_vjp_impl(Geometry* g, const double* Q, const double* lam, double* dX, double* dn, double* dw,

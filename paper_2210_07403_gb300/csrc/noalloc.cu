@@ -93,7 +93,10 @@ extern "C" ibdl_status ibdl_apply_noalloc(const ibdl_geometry_desc* d, int preci
   if (d->n_points < 1 || d->n_points > (int64_t)1 << 28) return fail(IBDL_ERR_INVALID_ARG, "n_points must be in [1, 2^28]");
   if (!d->inputs_on_device) return fail(IBDL_ERR_INVALID_ARG, "X, normals and weights must be device pointers (inputs_on_device = 1)");
   if (d->pde != IBDL_PDE_SCALAR && d->pde != IBDL_PDE_STOKES) return fail(IBDL_ERR_INVALID_ARG, "unknown pde");
-  if (d->pde == IBDL_PDE_SCALAR && !(d->lambda >= 0)) return fail(IBDL_ERR_INVALID_ARG, "lambda must be >= 0");
+  if (!(d->lambda >= 0)) return fail(IBDL_ERR_INVALID_ARG, "lambda must be >= 0");
+  if (d->bc != IBDL_BC_DIRICHLET && d->bc != IBDL_BC_NEUMANN) return fail(IBDL_ERR_INVALID_ARG, "unknown boundary condition");
+  if (d->bc == IBDL_BC_NEUMANN && d->pde != IBDL_PDE_SCALAR)
+    return fail(IBDL_ERR_UNSUPPORTED, "Neumann conditions are implemented for the scalar PDE");
   if (d->pde == IBDL_PDE_STOKES && !(d->mu > 0)) return fail(IBDL_ERR_INVALID_ARG, "mu must be > 0");
   if (d->delta != IBDL_DELTA_COS && d->delta != IBDL_DELTA_SQRT) return fail(IBDL_ERR_INVALID_ARG, "unknown delta");
   if (d->dipole != IBDL_DIPOLE_ANALYTIC && d->dipole != IBDL_DIPOLE_SPECTRAL_DIV) return fail(IBDL_ERR_INVALID_ARG, "unknown dipole");
@@ -118,6 +121,7 @@ extern "C" ibdl_status ibdl_apply_noalloc(const ibdl_geometry_desc* d, int preci
   g.h = d->box / d->n;
   g.lambda = d->lambda;
   g.mu = d->mu;
+  g.bc = d->bc;
   g.origin[0] = d->origin[0];
   g.origin[1] = d->origin[1];
   g.M = d->n_points;

@@ -43,13 +43,15 @@ _DELTA = {"cos": IBDL_DELTA_COS, "sqrt": IBDL_DELTA_SQRT}
 _DIPOLE = {"analytic": IBDL_DIPOLE_ANALYTIC, "spectral_div": IBDL_DIPOLE_SPECTRAL_DIV}
 _SYMBOL = {"spectral": IBDL_SYMBOL_SPECTRAL, "fd2": IBDL_SYMBOL_FD2}
 _PREC = {"fp64": IBDL_FP64, "fp32": IBDL_FP32, "mixed": IBDL_MIXED}
+IBDL_BC_DIRICHLET, IBDL_BC_NEUMANN = 0, 1
+_BC = {"dirichlet": IBDL_BC_DIRICHLET, "neumann": IBDL_BC_NEUMANN}
 
 
 class ibdl_geometry_desc(ctypes.Structure):
     _fields_ = [("dim", c_int), ("n", c_int), ("box", c_double), ("origin", c_double * 3),
                 ("n_points", c_int64), ("X", c_void_p), ("normals", c_void_p), ("weights", c_void_p),
                 ("pde", c_int), ("lambda_", c_double), ("mu", c_double), ("delta", c_int),
-                ("dipole", c_int), ("symbol", c_int), ("inputs_on_device", c_int)]
+                ("dipole", c_int), ("symbol", c_int), ("inputs_on_device", c_int), ("bc", c_int)]
 
 
 class ibdl_solve_opts(ctypes.Structure):
@@ -92,6 +94,7 @@ SIGNATURES = {
     "ibdl_solve_transpose": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(ibdl_solve_opts),
                                      POINTER(ibdl_solve_info), c_void_p]),
     "ibdl_solve_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ibdl_single_layer": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "ibdl_probe_evaluate": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "ibdl_probe_vjp": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                c_void_p, c_void_p]),
@@ -180,6 +183,10 @@ def ibdl_solve_vjp(geom, Q: int, lam: int, dX: int, dn: int, dw: int, stream: in
     """Pointers may be 0 (NULL) for outputs that are not wanted."""
     return _check(load().ibdl_solve_vjp(geom, c_void_p(Q), c_void_p(lam), c_void_p(dX or None),
                                         c_void_p(dn or None), c_void_p(dw or None), c_void_p(stream)))
+
+
+def ibdl_single_layer(geom, precision: int, V: int, Z: int, stream: int = 0) -> int:
+    return _check(load().ibdl_single_layer(geom, precision, c_void_p(V), c_void_p(Z), c_void_p(stream)))
 
 
 def ibdl_probe_evaluate(geom, P: int, n_probes: int, Q: int, U: int, stream: int = 0) -> int:
@@ -283,7 +290,7 @@ def _stream_handle(stream) -> int:
     return stream.cuda_stream
 
 
-def _desc(X, normals, weights, n, box, origin, pde, lam, mu, delta, dipole, symbol):
+def _desc(X, normals, weights, n, box, origin, pde, lam, mu, delta, dipole, symbol, bc="dirichlet"):
     """Descriptor over host arrays (returned arrays must stay alive while it is used)."""
     X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
     nrm = np.ascontiguousarray(np.asarray(normals, dtype=np.float64))
@@ -297,6 +304,7 @@ def _desc(X, normals, weights, n, box, origin, pde, lam, mu, delta, dipole, symb
     d.pde, d.lambda_, d.mu = _PDE[pde], float(lam), float(mu)
     d.delta, d.dipole, d.symbol = _DELTA[delta], _DIPOLE[dipole], _SYMBOL[symbol]
     d.inputs_on_device = 0
+    d.bc = _BC[bc]
     return d, (X, nrm, w)
 
 
@@ -311,7 +319,7 @@ class Batch:
         descs, keep = [], []
         for p in problems:
             d, k = _desc(p.bd.X, p.bd.n, p.bd.w, p.N, p.box, p.origin, p.pde, p.lam, p.mu, p.delta,
-                         p.dipole, p.symbol)
+                         p.dipole, p.symbol, getattr(p, "bc", "dirichlet"))
             descs.append(d)
             keep.append(k)
         self._h = ibdl_create_batch(descs, _stream_handle(stream))
@@ -360,7 +368,7 @@ class Geometry:
 
     def __init__(self, X, normals, weights, n: int, box: float = 1.0, origin=(0.0, 0.0, 0.0),
                  pde: str = "scalar", lam: float = 0.0, mu: float = 1.0, delta: str = "cos",
-                 dipole: str = "analytic", symbol: str = "spectral", stream=None):
+                 dipole: str = "analytic", symbol: str = "spectral", stream=None, bc: str = "dirichlet"):
         import torch
 
         self._torch = torch
@@ -381,6 +389,7 @@ class Geometry:
         d.pde, d.lambda_, d.mu = _PDE[pde], float(lam), float(mu)
         d.delta, d.dipole, d.symbol = _DELTA[delta], _DIPOLE[dipole], _SYMBOL[symbol]
         d.inputs_on_device = int(on_device)
+        d.bc = _BC[bc]
         self.dim, self.n, self.M, self.pde = dim, int(n), M, pde
         self.ncomp = dim if pde == "stokes" else 1
         self._h = ibdl_create_geometry(d, _stream_handle(stream))
@@ -388,6 +397,7 @@ class Geometry:
     @classmethod
     def from_problem(cls, p, **overrides):
         kw = dict(n=p.N, box=p.box, origin=p.origin, pde=p.pde, lam=p.lam, mu=p.mu, delta=p.delta,
+                  bc=getattr(p, "bc", "dirichlet"),
                   dipole=p.dipole, symbol=p.symbol)
         kw.update(overrides)
         return cls(p.bd.X, p.bd.n, p.bd.w, **kw)
@@ -410,6 +420,14 @@ class Geometry:
             Y = self._torch.empty_like(Q)
         ibdl_apply(self._h, _PREC[precision], Q.data_ptr(), Y.data_ptr(), _stream_handle(stream))
         return Y
+
+    def single_layer(self, V, Z=None, precision: str = "fp64", stream=None):
+        """Z = S*(−L⁻¹)(S V) (scalar); −Z(V_b) is the Neumann right-hand side."""
+        V = self._vec(V)
+        if Z is None:
+            Z = self._torch.empty_like(V)
+        ibdl_single_layer(self._h, _PREC[precision], V.data_ptr(), Z.data_ptr(), _stream_handle(stream))
+        return Z
 
     def adjoint(self, W, Z=None, precision: str = "fp64", stream=None):
         W = self._vec(W)

@@ -1,0 +1,158 @@
+"""GPU parity of the Brinkman operator (Sec. 6.3.2) and of Neumann conditions (Sec. 5.2) against
+the FP64 oracle, through the C ABI. Tolerances as for the operator and solve tests: FP64
+application 1e-12, FP32 application 2e-5 (the Brinkman λ only rescales the projected term),
+FP64 solves 1e-10, mixed solves 1e-8, derivatives from the same inputs 1e-11."""
+import numpy as np
+import pytest
+
+import ibdl_inputs as I
+from oracle import ibdl_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_07403_gb300 import build as b
+    from paper_2210_07403_gb300 import ibdl
+
+    b.build()
+    ibdl.load()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def _cuda(v):
+    return torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).cuda()
+
+
+def _geom(p):
+    from paper_2210_07403_gb300 import Geometry
+
+    return Geometry.from_problem(p)
+
+
+BRINKMAN = [
+    # N, M, lam, mu, delta, dipole, symbol
+    (64, 100, 100.0, 1.0, "cos", "analytic", "spectral"),
+    (128, 230, 10.0, 0.5, "sqrt", "spectral_div", "spectral"),
+    (256, 403, 40.0, 2.0, "cos", "analytic", "fd2"),
+]
+
+
+@pytest.mark.parametrize("case", BRINKMAN)
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_brinkman_apply(case, precision, tol):
+    N, M, lam, mu, delta, dipole, symbol = case
+    p = I.circle_brinkman(N, M, lam=lam, mu=mu, delta=delta, dipole=dipole, symbol=symbol)
+    g, og = _geom(p), O.geometry_from_problem(p)
+    rng = np.random.default_rng(N)
+    for _ in range(2):
+        q = rng.standard_normal(2 * M)
+        assert _rel(g.apply(_cuda(q), precision=precision).cpu().numpy(), O.apply(og, q)) < tol
+
+
+def test_brinkman_field():
+    p = I.circle_brinkman(64, 100, lam=30.0, mu=0.7)
+    g, og = _geom(p), O.geometry_from_problem(p)
+    q = np.random.default_rng(3).standard_normal(200)
+    u = g.evaluate_field(_cuda(q)).cpu().numpy()
+    assert _rel(u, O.stokes_velocity(og, q)) < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_brinkman_solve(precision, tol):
+    p = I.circle_brinkman(128, 200, lam=100.0)
+    g, og = _geom(p), O.geometry_from_problem(p)
+    ref = O.solve(og, p.Ub.reshape(-1), 1e-13, maxit=100).x
+    Q, info, _ = g.solve(_cuda(p.Ub.reshape(-1)), rtol=1e-12 if precision == "fp64" else 1e-10,
+                         precision=precision, inner_rtol=1e-5)
+    assert _rel(Q.cpu().numpy(), ref) < tol
+
+
+def test_brinkman_transpose_and_gradient():
+    p = I.circle_brinkman(64, 100, lam=50.0, mu=1.5)
+    og = O.geometry_from_problem(p)
+    rng = np.random.default_rng(5)
+    og.X = og.X + 0.1 * og.grid.h * rng.uniform(-1, 1, og.X.shape)
+    from paper_2210_07403_gb300 import Geometry
+
+    g = Geometry(og.X, og.n, og.w, 64, pde="stokes", lam=50.0, mu=1.5, delta=og.delta)
+    v = rng.standard_normal(200)
+    assert _rel(g.apply_transpose(_cuda(v)).cpu().numpy(), O.transpose_apply(og, v)) < 1e-12
+    Q, L = rng.standard_normal(200), rng.standard_normal(200)
+    dX, dn, dw = O.stokes_param_gradient(og, Q, L)
+    gX, gn, gw = g.solve_vjp(_cuda(Q), _cuda(L))
+    assert _rel(gX.cpu().numpy(), -dX) < 1e-11
+    assert _rel(gn.cpu().numpy(), -dn) < 1e-11
+    assert _rel(gw.cpu().numpy(), -dw) < 1e-11
+
+
+NEUMANN = [
+    # N, alpha, lam, delta, dipole, symbol
+    (64, 0.75, 1.0, "sqrt", "analytic", "fd2"),
+    (128, 1.0, 5.0, "cos", "spectral_div", "spectral"),
+]
+
+
+@pytest.mark.parametrize("case", NEUMANN)
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_neumann_apply_and_single_layer(case, precision, tol):
+    N, alpha, lam, delta, dipole, symbol = case
+    p = I.paper_circle_neumann(N, alpha, lam, delta, symbol, dipole)
+    g, og = _geom(p), O.geometry_from_problem(p)
+    rng = np.random.default_rng(N + 1)
+    q = rng.standard_normal(og.M)
+    assert _rel(g.apply(_cuda(q), precision=precision).cpu().numpy(), O.apply(og, q)) < tol
+    assert _rel(g.single_layer(_cuda(q), precision=precision).cpu().numpy(), O.single_layer(og, q)) < tol
+    if dipole == "analytic":
+        assert _rel(g.apply_transpose(_cuda(q), precision=precision).cpu().numpy(),
+                    O.transpose_apply(og, q)) < tol
+
+
+def test_neumann_solve():
+    """The whole Neumann path on the GPU (right-hand side from ibdl_single_layer, then the solve)
+    against the oracle, and U_b against the exact boundary values at the oracle's accuracy."""
+    p = I.paper_circle_neumann(128)
+    g, og = _geom(p), O.geometry_from_problem(p)
+    Vb = p.Ub.reshape(-1)
+    rhs = -g.single_layer(_cuda(Vb))
+    ref_rhs = O.neumann_rhs(og, Vb)
+    assert _rel(rhs.cpu().numpy(), ref_rhs) < 1e-12
+    ref = O.solve(og, ref_rhs, 1e-13, maxit=60)
+    Q, info, _ = g.solve(rhs, rtol=1e-12)
+    assert info["iterations"] <= ref.iterations + 1
+    assert _rel(Q.cpu().numpy(), ref.x) < 1e-10
+    err = np.abs(Q.cpu().numpy() - p.meta["exact_Ub"].reshape(-1)).max()
+    assert err < 0.1  # first-order discretisation error at N = 128 (0.066 on the oracle)
+
+
+def test_neumann_3d_apply():
+    p = I.sphere_poisson(32, 700, delta="cos", lam=2.0)
+    p.bc = "neumann"
+    g, og = _geom(p), O.geometry_from_problem(p)
+    q = np.random.default_rng(7).standard_normal(og.M)
+    assert _rel(g.apply(_cuda(q)).cpu().numpy(), O.apply(og, q)) < 1e-12
+
+
+def test_variant_error_paths():
+    from paper_2210_07403_gb300 import IbdlError
+
+    p = I.star_stokes(64, 100)
+    p.bc = "neumann"
+    with pytest.raises(IbdlError, match="UNSUPPORTED"):
+        _geom(p)
+    p = I.sphere_poisson(32, 300)
+    g = _geom(p)
+    with pytest.raises(IbdlError, match="UNSUPPORTED"):
+        g.single_layer(_cuda(np.ones(300)))
+    pb = I.circle_brinkman(64, 100)
+    gb = _geom(pb)
+    with pytest.raises(IbdlError, match="UNSUPPORTED"):
+        gb.single_layer(_cuda(np.ones(200)))
