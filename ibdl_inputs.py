@@ -226,6 +226,7 @@ class Problem:
     rtol: float = 1e-10
     meta: dict = field(default_factory=dict)
     bc: str = "dirichlet"  # "dirichlet": Ub holds U_b; "neumann": Ub holds V_b = ∂u/∂n (Sec. 5.2)
+    eta: float = 0.0  # completed method (η > 0, λ = 0): the unknowns gain one mean per component
 
     @property
     def h(self) -> float:
@@ -373,4 +374,22 @@ def circle_brinkman(N: int = 128, M: int = 200, lam: float = 10.0, mu: float = 1
     U, flux = remove_normal_flux(U, bd)
     return Problem("circle_brinkman", 2, N, 1.0, (0.0, 0.0), bd, U, "stokes", lam=lam, mu=mu,
                    delta=delta, dipole=dipole, symbol=symbol, rtol=1e-10, meta={"removed_flux": flux})
+
+
+def cylinder_array(N: int, c: float, eta: float = 10.0, alpha: float = 1.0, delta: str = "cos",
+                   symbol: str = "spectral") -> Problem:
+    """Stokes flow past a periodic array of cylinders (Sec. 6.5.3): the box [−0.5, 0.5]², a disk
+    of area fraction c (radius √(c/π)) at the origin, u = 0 on its boundary, forcing g = (−1, 0),
+    completed method with η; the fluid is exterior, so the normals point into the disk. The
+    constant forcing has no mean-free part, so it enters only the constraint rows:
+    η Σ Δs Q = h² Σ g̃ = (−1, 0) (box area 1)."""
+    r = math.sqrt(c / math.pi)
+    h = 1.0 / N
+    M = points_for_spacing(2 * np.pi * r, h, alpha)
+    bd = circle(M, r, (0.0, 0.0))
+    bd.n = -bd.n
+    p = Problem("cylinder_array", 2, N, 1.0, (-0.5, -0.5), bd, np.zeros((2, M)), "stokes", mu=1.0,
+                delta=delta, dipole="analytic", symbol=symbol, rtol=1e-10,
+                meta={"c": c, "radius": r, "rhs_aug": np.array([-1.0, 0.0])}, eta=eta)
+    return p
 

@@ -126,10 +126,22 @@ class Geometry:
     lam: float = 0.0
     mu: float = 1.0
     bc: str = "dirichlet"  # "dirichlet" (jump +½) | "neumann" (jump −½, Sec. 5.2; scalar)
+    eta: float = 0.0  # completed method (Sec. 5.3.3, Sec. 6.1.3): ηSQ added to the sources
 
     @property
     def jump(self) -> float:
         return -0.5 if self.bc == "neumann" else 0.5
+
+    @property
+    def naug(self) -> int:
+        """Extra unknowns ū of the completed method (λ = 0): one mean per velocity component."""
+        return self.ncomp if self.eta > 0 else 0
+
+    def split(self, x):
+        """(Q (c, M), ū (c,)) from a flat vector of the (possibly augmented) system."""
+        x = np.asarray(x, dtype=np.float64).reshape(-1)
+        c, M = self.ncomp, self.M
+        return x[: c * M].reshape(c, M), x[c * M:]
 
     @property
     def M(self) -> int:
@@ -143,7 +155,8 @@ class Geometry:
 def geometry_from_problem(p) -> Geometry:
     """Build a Geometry from an ``ibdl_inputs.Problem``."""
     return Geometry(Grid(p.dim, p.N, p.box, p.origin), p.bd.X, p.bd.n, p.bd.w, p.delta,
-                    p.dipole, p.symbol, p.pde, p.lam, p.mu, getattr(p, "bc", "dirichlet"))
+                    p.dipole, p.symbol, p.pde, p.lam, p.mu, getattr(p, "bc", "dirichlet"),
+                    getattr(p, "eta", 0.0))
 
 
 def _stencil(geom: Geometry):
@@ -316,8 +329,12 @@ def dipole_field(geom: Geometry, Q: np.ndarray) -> np.ndarray:
 
 
 def field_scalar(geom: Geometry, Q: np.ndarray) -> np.ndarray:
-    """u = −L⁻¹ S̃ Q on the grid (step 2 of the method in Sec. 5.1.2 with g̃ = 0)."""
-    return minus_Linv(geom, dipole_field(geom, Q))
+    """u = −L⁻¹ S̃ Q on the grid (step 2 of the method in Sec. 5.1.2 with g̃ = 0); completed
+    method (Sec. 5.3.3): u₀ = −Δ₀⁻¹(S̃ + ηS)Q, the mean ū added by the caller."""
+    f = dipole_field(geom, Q)
+    if geom.eta > 0:
+        f = f + geom.eta * spread(geom, Q)
+    return minus_Linv(geom, f)
 
 
 def stokes_velocity(geom: Geometry, Q: np.ndarray) -> np.ndarray:
@@ -343,7 +360,12 @@ def stokes_velocity(geom: Geometry, Q: np.ndarray) -> np.ndarray:
     g_hat = []
     for l in range(d):
         if geom.dipole == "analytic":
-            g_hat.append(np.fft.fftn(spread_grad(geom, A[l])))
+            gl = spread_grad(geom, A[l])
+            if geom.eta > 0:
+                # completed method (Sec. 6.3.3, Eq. "discrete operator for Q"): (η/μ)SQ joins
+                # the projected source, P((η/μ)SQ + ∇·(SA))
+                gl = gl + (geom.eta / geom.mu) * spread(geom, Q[l])
+            g_hat.append(np.fft.fftn(gl))
         else:
             acc = np.zeros(g.shape, dtype=complex)
             for m in range(d):
@@ -369,7 +391,13 @@ def stokes_velocity(geom: Geometry, Q: np.ndarray) -> np.ndarray:
 
 
 def grid_field(geom: Geometry, Q: np.ndarray) -> np.ndarray:
-    """The grid solution from a density: scalar u (shape grid) or Stokes velocity (d, grid)."""
+    """The grid solution from a density: scalar u (shape grid) or Stokes velocity (d, grid);
+    for the completed method Q carries ū after the density and u = u₀ + ū."""
+    if geom.naug:
+        Qd, ub = geom.split(Q)
+        if geom.pde == "stokes":
+            return stokes_velocity(geom, Qd.reshape(-1)) + ub[:, None, None]
+        return field_scalar(geom, Qd.reshape(-1)) + ub[0]
     if geom.pde == "stokes":
         return stokes_velocity(geom, Q)
     return field_scalar(geom, Q.reshape(-1))
@@ -378,8 +406,22 @@ def grid_field(geom: Geometry, Q: np.ndarray) -> np.ndarray:
 def apply(geom: Geometry, Q: np.ndarray) -> np.ndarray:
     """A Q = S* u + ½ Q with u the grid field of Q: scalar A Q = −S*L⁻¹S̃Q + ½Q (Sec. 5.3.2),
     Stokes A Q = S* u(Q) + ½Q (Sec. 6.3.3). Q and the result are flat SoA arrays (c·M,).
-    Neumann (Sec. 5.2, Eq. "Neumann saddle point"): the jump term is −½Q and the unknown is U_b."""
+    Neumann (Sec. 5.2, Eq. "Neumann saddle point"): the jump term is −½Q and the unknown is U_b.
+    Completed method (λ = 0; Sec. 5.3.3 and Sec. 6.3.3, Eq. "discrete operator for Q"): the
+    unknowns are (Q, ū), the boundary rows gain ū·1 and the c constraint rows are η Σ_i Δs_i Q_i."""
     Q = np.asarray(Q, dtype=np.float64).reshape(-1)
+    if geom.naug:
+        if geom.lam > 0 or geom.dipole != "analytic" or geom.bc != "dirichlet":
+            raise NotImplementedError("completed method: λ = 0, analytic dipole, Dirichlet data")
+        Qd, ub = geom.split(Q)
+        flat = Qd.reshape(-1)
+        if geom.pde == "stokes":
+            u = stokes_velocity(geom, flat)
+            rows = np.concatenate([interp(geom, u[l]) for l in range(geom.grid.dim)]) + geom.jump * flat
+        else:
+            rows = interp(geom, field_scalar(geom, flat)) + geom.jump * flat
+        rows = rows + np.repeat(ub, geom.M)
+        return np.concatenate([rows, geom.eta * (Qd @ geom.w)])
     if geom.pde == "stokes":
         d = geom.grid.dim
         u = stokes_velocity(geom, Q)
@@ -698,6 +740,19 @@ def stokes_param_gradient(geom: Geometry, Q: np.ndarray, mu: np.ndarray):
     psi = [spread_unweighted(geom, mu[l]) for l in range(d)]
     _, sX, sn, sw = _spread_terms(geom, Q, _multiplier_T(geom, psi))
     return dX + sX, sn, sw
+
+
+def mean_inflow(geom: Geometry, x: np.ndarray) -> float:
+    """U = ∫ u(x₀, y) dy along the left edge x₀ of the box (Sec. 6.5.3: the average horizontal
+    velocity on the left side), by the grid sum over that column of nodes."""
+    u = grid_field(geom, x)
+    return float(u[0][:, 0].sum() * geom.grid.h)
+
+
+def net_force(geom: Geometry, x: np.ndarray) -> np.ndarray:
+    """B = −η ∫_Γ Q ds of the completed Stokes method (Sec. 6.1.3)."""
+    Qd, _ = geom.split(x)
+    return -geom.eta * (Qd @ geom.w)
 
 
 def single_layer(geom: Geometry, V: np.ndarray) -> np.ndarray:
