@@ -100,7 +100,21 @@ typedef struct {
   int symbol;           /* IBDL_SYMBOL_*                                                    */
   int inputs_on_device; /* nonzero: X, normals, weights are device pointers                 */
   int bc;               /* IBDL_BC_* (0, Dirichlet, for a zero-initialised descriptor)      */
+  double eta;           /* completed method, η > 0 (0: not completed); see below          */
 } ibdl_geometry_desc;
+
+/* Completed method (Sec. 5.3.3 Poisson, Sec. 6.1.3 and Sec. 6.3.3 Stokes): for exterior domains
+ * (and wherever the double layer alone cannot represent the flow) the sources gain the
+ * single layer ηSQ and, because λ = 0 leaves the mean of u free, the unknowns gain ū, one mean
+ * per component: the system is
+ *     S*u₀ + ū·1 + ½Q = U_b − (forcing term),    η Σ_i Δs_i Q_i = h^d Σ_g g̃,
+ * u₀ the mean-zero grid field of (S̃ + ηS)Q (Stokes: the projected source is (η/μ)SQ + ∇·(SA)).
+ * With η > 0 (2-D, λ = 0, analytic dipole, Dirichlet data; IBDL_ERR_UNSUPPORTED otherwise)
+ * every boundary vector of ibdl_apply, ibdl_solve and ibdl_evaluate_field has c·M + c entries:
+ * the density [c][M], then ū[c]; the last c entries of a right-hand side are h^d Σ g̃ per
+ * component, and the grid field written by ibdl_evaluate_field is u₀ + ū. The net force on the
+ * boundary is −η Σ_i Δs_i Q_i (Sec. 6.1.3). Transposes, derivatives, probes, the single layer,
+ * batches and ibdl_apply_noalloc do not take completed geometries. */
 
 typedef struct {
   double rtol;          /* stop when ‖U_b − A Q‖₂ ≤ rtol·‖U_b‖₂ (relative Euclidean residual)  */

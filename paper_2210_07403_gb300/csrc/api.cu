@@ -87,13 +87,14 @@ ibdl_status ibdl_apply(ibdl_geometry* geom, int precision, const double* Q, doub
   Geometry* g = geom->g;
   IBDL_TRY(check_device_ptr(Q, "Q"));
   IBDL_TRY(check_device_ptr(Y, "Y"));
-  if (ranges_overlap(Q, Y, sizeof(double) * g->ncomp * g->M)) return fail(IBDL_ERR_INVALID_ARG, "Q and Y overlap");
+  if (ranges_overlap(Q, Y, sizeof(double) * geom_nd(g))) return fail(IBDL_ERR_INVALID_ARG, "Q and Y overlap");
   return apply_any(g, precision, Q, Y, static_cast<cudaStream_t>(stream), nullptr);
 }
 
 ibdl_status ibdl_adjoint(ibdl_geometry* geom, int precision, const double* W, double* Z, void* stream) {
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (geom->g->naug) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_adjoint: not for the completed method (eta > 0)");
   if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
   Geometry* g = geom->g;
   if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_adjoint: scalar PDE only");
@@ -139,6 +140,8 @@ static ibdl_status solve_entry(ibdl_geometry* geom, const double* b, double* x, 
   if (o.precision == IBDL_MIXED && (!(o.inner_rtol > 0) || !(o.inner_rtol < 1) || o.max_refine < 1))
     return fail(IBDL_ERR_INVALID_ARG, "mixed precision needs inner_rtol in (0, 1) and max_refine >= 1");
   if (!b || !x) return fail(IBDL_ERR_INVALID_ARG, std::string(bname) + " and " + xname + " are required");
+  if (op == OPK_AT && geom->g->naug)
+    return fail(IBDL_ERR_UNSUPPORTED, "ibdl_solve_transpose: not for the completed method (eta > 0)");
   if (op == OPK_AT && geom->g->pde == IBDL_PDE_STOKES && geom->g->dipole != IBDL_DIPOLE_ANALYTIC)
     return fail(IBDL_ERR_UNSUPPORTED, "ibdl_solve_transpose: Stokes with the analytic dipole only");
   if (!o.io_on_host) {
@@ -189,6 +192,7 @@ ibdl_status ibdl_solve_transpose(ibdl_geometry* geom, const double* G, double* l
 ibdl_status ibdl_apply_transpose(ibdl_geometry* geom, int precision, const double* G, double* Z, void* stream) {
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (geom->g->naug) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_apply_transpose: not for the completed method (eta > 0)");
   if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
   Geometry* g = geom->g;
   if (g->pde == IBDL_PDE_STOKES && g->dipole != IBDL_DIPOLE_ANALYTIC)
@@ -202,6 +206,7 @@ ibdl_status ibdl_apply_transpose(ibdl_geometry* geom, int precision, const doubl
 ibdl_status ibdl_single_layer(ibdl_geometry* geom, int precision, const double* V, double* Z, void* stream) {
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (geom->g->naug) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_single_layer: not for the completed method (eta > 0)");
   if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
   Geometry* g = geom->g;
   if (g->pde != IBDL_PDE_SCALAR || g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_single_layer: scalar PDE in 2-D only");
@@ -215,6 +220,7 @@ ibdl_status ibdl_solve_vjp(ibdl_geometry* geom, const double* Q, const double* l
                            double* dw, void* stream) {
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (geom->g->naug) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_solve_vjp: not for the completed method (eta > 0)");
   Geometry* g = geom->g;
   if (g->dipole != IBDL_DIPOLE_ANALYTIC)
     return fail(IBDL_ERR_UNSUPPORTED, "ibdl_solve_vjp: analytic dipole only");
@@ -232,6 +238,7 @@ ibdl_status ibdl_probe_evaluate(ibdl_geometry* geom, const double* P, int n_prob
                                 void* stream) {
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (geom->g->naug) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_probe_evaluate: not for the completed method (eta > 0)");
   Geometry* g = geom->g;
   if (g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_probe_evaluate: 2-D only");
   if (n_probes < 0) return fail(IBDL_ERR_INVALID_ARG, "n_probes must be >= 0");
@@ -250,6 +257,7 @@ ibdl_status ibdl_probe_vjp(ibdl_geometry* geom, const double* P, int n_probes, c
                            double* dQ, double* dX, double* dn, double* dw, void* stream) {
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (geom->g->naug) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_probe_vjp: not for the completed method (eta > 0)");
   Geometry* g = geom->g;
   if (g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_probe_vjp: 2-D only");
   if (g->dipole != IBDL_DIPOLE_ANALYTIC) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_probe_vjp: analytic dipole only");
@@ -292,7 +300,7 @@ ibdl_status ibdl_autotune(ibdl_geometry* geom, int precision_mask, void* stream)
   Geometry* g = geom->g;
   if (g->dim != 2) return IBDL_OK;  // 3-D shapes come from the volume rule only
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t nd = (size_t)g->ncomp * g->M;
+  const size_t nd = (size_t)geom_nd(g);
   double* buf = nullptr;
   IBDL_CUDA(cudaMalloc((void**)&buf, sizeof(double) * 2 * nd));
   ibdl_status st = IBDL_OK;

@@ -87,6 +87,11 @@ struct RowParams {
   int trans;
   const double* grid_in;  // optional [NIN][n][n]: the band rows are read from it instead of spread
   double jump;            // jump term coefficient: ½ (Dirichlet), −½ (Neumann), 0 (single layer)
+  // completed method (Sec. 5.3.3, Sec. 6.3.3): the vectors hold ū after the c·M density values
+  int aug;                // 1: add ū_l to the boundary rows, write the rows η Σ_i Δs_i Q_{l,i}
+  double eta;             // η
+  double hd;              // h^d
+  T eta_src;              // weight of the ηSQ source: η (scalar) or η/μ (Stokes, projected part)
 };
 
 template <typename T>
@@ -172,7 +177,27 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   // jump term: out = ±½·in (the gather kernel adds S*u afterwards); none for grid input
   if (!p.grid_in)
     for (int i = unit * blockDim.x + threadIdx.x; i < NC * M; i += nunits * blockDim.x)
-      pout[i] = p.jump * pin[i];
+      pout[i] = p.jump * pin[i] + (p.aug ? pin[NC * M + i / M] : 0.0);
+  if (p.aug && unit == 0) {
+    // constraint rows of the completed method: η Σ_i Δs_i Q_{l,i} (Δs = wscale·h^d); the
+    // partial sums use the second FFT buffer, which the FFT's first stage writes later
+    double* red = reinterpret_cast<double*>(bufB);
+    for (int l = 0; l < NC; ++l) {
+      double v = 0.0;
+      for (int s = threadIdx.x; s < M; s += blockDim.x) v += double(p.wscale[s]) * pin[(size_t)l * M + p.perm[s]];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) pout[NC * M + l] = p.eta * p.hd * t;
+      }
+      __syncthreads();
+    }
+  }
   __syncthreads();
 
   if (p.grid_in) {
@@ -204,7 +229,8 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
     if (OP == OP_SCALAR_AN) {
       const T q = T(pin[i]) * ws;
       const T ddx = p.dphi[(0 * 4 + ax) * M + s] * py, ddy = px * p.dphi[(1 * 4 + ay) * M + s];
-      atomicAdd(acc + 2 * pidx(e) + odd, q * (nx * ddx + ny * ddy));
+      // dipole source n·∇δ_h, plus ηδ_h for the completed method
+      atomicAdd(acc + 2 * pidx(e) + odd, q * (nx * ddx + ny * ddy + p.eta_src * pp));
     } else if (OP == OP_SCALAR_SD) {
       const T q = T(pin[i]) * ws * pp;
       atomicAdd(acc + 2 * pidx(e) + odd, q * nx);
@@ -218,8 +244,11 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
       atomicAdd(acc + 2 * pidx(e) + odd, c0 * pp);
       if (OP == OP_STOKES_AN) {
         const T ddx = p.dphi[(0 * 4 + ax) * M + s] * py, ddy = px * p.dphi[(1 * 4 + ay) * M + s];
-        atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * ddx + c3 * ddy);      // g_x = ∂_x S(A_xx) + ∂_y S(A_xy)
-        atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c3 * ddx + c2 * ddy);  // g_y = ∂_x S(A_xy) + ∂_y S(A_yy)
+        // g_x = ∂_x S(A_xx) + ∂_y S(A_xy), g_y = ∂_x S(A_xy) + ∂_y S(A_yy); the completed method
+        // adds (η/μ) S(Q) to the projected source
+        const T ce = p.eta_src * ws * pp;
+        atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * ddx + c3 * ddy + ce * qx);
+        atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c3 * ddx + c2 * ddy + ce * qy);
       } else {
         atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * pp);
         atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c2 * pp);
@@ -461,7 +490,9 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
       const int f = t / (R * n);
       const int rem = t - f * R * n;
       const int lr = rem / n, x = rem - lr * n;
-      p.grid[((size_t)f * n + r0 + lr) * n + x] = double(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)]);
+      // the completed method's field is u₀ + ū (ū after the density in the input vector)
+      const double ub = p.aug ? p.in[(size_t)Traits<OP>::C * M + f] : 0.0;
+      p.grid[((size_t)f * n + r0 + lr) * n + x] = double(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)]) + ub;
     }
     return;
   }
@@ -571,6 +602,10 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.trans = 0;
   rp.grid_in = nullptr;
   rp.jump = g->bc == IBDL_BC_NEUMANN ? -0.5 : 0.5;
+  rp.aug = g->naug > 0;
+  rp.eta = g->eta;
+  rp.hd = g->h * g->h;
+  rp.eta_src = T(g->naug ? (g->pde == IBDL_PDE_STOKES ? g->eta / g->mu : g->eta) : 0.0);
   return rp;
 }
 
@@ -678,6 +713,10 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   rp.trans = trans;
   rp.grid_in = grid_in;
   if (OP == OP_SL) rp.jump = 0.0;
+  if (OP != OP_SCALAR_AN && OP != OP_STOKES_AN) {  // the completed method exists for these two only
+    rp.aug = 0;
+    rp.eta_src = T(0);
+  }
   ColParams<T> cp = col_params<T>(g, stop);
   const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);

@@ -68,6 +68,7 @@ ibdl_status ibdl_create_batch(const ibdl_geometry_desc* descs, int count, void* 
   if (count < 1 || count > 65536) return fail(IBDL_ERR_INVALID_ARG, "count must be in [1, 65536]");
   for (int i = 0; i < count; ++i) {
     if (descs[i].dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "batches hold 2-D problems only");
+    if (descs[i].eta != 0) return fail(IBDL_ERR_UNSUPPORTED, "batches do not hold completed problems (eta > 0)");
     if (descs[i].pde != descs[0].pde || descs[i].dipole != descs[0].dipole)
       return fail(IBDL_ERR_INVALID_ARG, "all problems of a batch need the same pde and dipole form");
   }

@@ -268,6 +268,9 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
   if (d->bc != IBDL_BC_DIRICHLET && d->bc != IBDL_BC_NEUMANN) return fail(IBDL_ERR_INVALID_ARG, "unknown boundary condition");
   if (d->bc == IBDL_BC_NEUMANN && d->pde != IBDL_PDE_SCALAR)
     return fail(IBDL_ERR_UNSUPPORTED, "Neumann conditions are implemented for the scalar PDE");
+  if (!(d->eta >= 0) || !std::isfinite(d->eta)) return fail(IBDL_ERR_INVALID_ARG, "eta must be finite and >= 0");
+  if (d->eta > 0 && (d->dim != 2 || d->lambda != 0 || d->dipole != IBDL_DIPOLE_ANALYTIC || d->bc != IBDL_BC_DIRICHLET))
+    return fail(IBDL_ERR_UNSUPPORTED, "the completed method needs dim 2, lambda 0, the analytic dipole and Dirichlet data");
   if (d->pde == IBDL_PDE_STOKES && (!(d->mu > 0) || !std::isfinite(d->mu)))
     return fail(IBDL_ERR_INVALID_ARG, "mu must be finite and > 0");
   if (d->delta != IBDL_DELTA_COS && d->delta != IBDL_DELTA_SQRT) return fail(IBDL_ERR_INVALID_ARG, "unknown delta");
@@ -309,9 +312,11 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
   g->lambda = d->lambda;
   g->mu = d->mu;
   g->bc = d->bc;
+  g->eta = d->eta;
   for (int j = 0; j < 3; ++j) g->origin[j] = j < dim ? d->origin[j] : 0.0;
   g->M = M;
   g->ncomp = d->pde == IBDL_PDE_STOKES ? dim : 1;
+  g->naug = d->eta > 0 ? g->ncomp : 0;
   const bool sd = d->dipole == IBDL_DIPOLE_SPECTRAL_DIV;
   if (d->pde == IBDL_PDE_STOKES) {
     g->nf_in = sd ? 4 : 3;
@@ -372,7 +377,7 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
     GTRY(dalloc(&g->der64, sizeof(double) * n));
     GTRY(dalloc(&g->lap32, sizeof(float) * n));
     GTRY(dalloc(&g->der32, sizeof(float) * n));
-    GTRY(dalloc(&g->tmp_m, sizeof(double) * g->ncomp * M));
+    GTRY(dalloc(&g->tmp_m, sizeof(double) * (g->ncomp * M + g->ncomp)));  // room for ū / constraint rows
 
     const int tb = 256;
     GCUDA(cudaMemsetAsync(count, 0, sizeof(int) * g->ncell, s));

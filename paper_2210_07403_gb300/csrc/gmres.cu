@@ -292,7 +292,7 @@ static ibdl_status ensure_workspace(Geometry* g, int m) {
   if (g->V && g->krylov_m >= m) return IBDL_OK;
   if (g->V) cudaFree(g->V);
   g->V = nullptr;
-  const size_t nd = (size_t)g->ncomp * g->M;
+  const size_t nd = (size_t)geom_nd(g);
   IBDL_CUDA(cudaMalloc((void**)&g->V, sizeof(double) * nd * (m + 1)));
   if (!g->gm) IBDL_CUDA(cudaMalloc((void**)&g->gm, sizeof(GmresState)));
   if (!g->vec) IBDL_CUDA(cudaMalloc((void**)&g->vec, sizeof(double) * nd * 5));
@@ -333,7 +333,7 @@ static ibdl_status gmres_cycle_graph(Geometry* g, int prec, int op, const double
   }
   GmresState* st = reinterpret_cast<GmresState*>(g->gm);
   HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
-  const int nd = (int)(g->ncomp * g->M);
+  const int nd = geom_nd(g);
   const int steps = m < budget ? m : budget;
   k_gmres_start<<<1, 1024, 0, s>>>(st, r0, g->V, nd, target, steps);
   IBDL_CUDA(cudaGetLastError());
@@ -404,7 +404,7 @@ static ibdl_status arnoldi_cfg(Geometry* g, int m, ArnoldiCfg* c) {
     }
     cudaGetLastError();
   }
-  const int nd = (int)(g->ncomp * g->M);
+  const int nd = geom_nd(g);
   c->cl = cl_choice;
   c->slice = (nd + c->cl - 1) / c->cl;
   const size_t staged_bytes = arnoldi_staged_doubles(m, c->slice) * sizeof(double);
@@ -449,7 +449,7 @@ static cudaError_t launch_arnoldi(const ArnoldiCfg& c, GmresState* st, double* V
 // (A or Aᵀ), precision and restart length.
 static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, int op, cudaGraphExec_t* out) {
   *out = nullptr;
-  const int nd = (int)(g->ncomp * g->M);
+  const int nd = geom_nd(g);
   GmresState* st = reinterpret_cast<GmresState*>(g->gm);
   ArnoldiCfg c;
   IBDL_TRY(arnoldi_cfg(g, m, &c));
@@ -509,7 +509,7 @@ static ibdl_status gmres_cycle(Geometry* g, int prec, int op, const double* r0, 
                                int budget, cudaStream_t s, CycleResult* cr) {
   GmresState* st = reinterpret_cast<GmresState*>(g->gm);
   HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
-  const int nd = (int)(g->ncomp * g->M);
+  const int nd = geom_nd(g);
   double* V = g->V;
   if (!g->timing) return gmres_cycle_graph(g, prec, op, r0, x, target, m, budget, s, cr);
   // host-driven loop (used while stage timing records an event around every kernel)
@@ -573,7 +573,7 @@ static ibdl_status gmres_cycle(Geometry* g, int prec, int op, const double* r0, 
 static ibdl_status true_residual(Geometry* g, int op, const double* b, const double* x, double* r, double* Ax,
                                  cudaStream_t s, double* rnorm) {
   GmresState* st = reinterpret_cast<GmresState*>(g->gm);
-  const int nd = (int)(g->ncomp * g->M);
+  const int nd = geom_nd(g);
   IBDL_TRY(apply_any(g, IBDL_FP64, x, Ax, s, nullptr, op));
   k_residual<<<1, 1024, 0, s>>>(st, b, Ax, r, nd);
   g->launches += 1;
@@ -587,7 +587,7 @@ static ibdl_status true_residual(Geometry* g, int op, const double* b, const dou
 
 static double host_norm(Geometry* g, const double* v_dev, cudaStream_t s) {
   GmresState* st = reinterpret_cast<GmresState*>(g->gm);
-  const int nd = (int)(g->ncomp * g->M);
+  const int nd = geom_nd(g);
   // ‖v‖ via k_residual with Ax = 0 would need a zero vector; use b − 0 trick with the x slot cleared
   double* zero = g->vec + 4 * (size_t)nd;
   cudaMemsetAsync(zero, 0, sizeof(double) * nd, s);
@@ -605,7 +605,7 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
   const auto t0 = std::chrono::steady_clock::now();
   const int m = o->restart;
   IBDL_TRY(ensure_workspace(g, m));
-  const int nd = (int)(g->ncomp * g->M);
+  const int nd = geom_nd(g);
   double* b = g->vec;
   double* x = g->vec + (size_t)nd;
   double* r = g->vec + 2 * (size_t)nd;

@@ -82,6 +82,8 @@ struct Geometry {
   int dim, n, pde, delta, dipole, symbol;
   int bc;          // IBDL_BC_*: the jump term is +½Q (Dirichlet) or −½Q (Neumann)
   double box, h, lambda, mu;
+  double eta;      // completed method (> 0): ηSQ joins the sources, and the unknowns gain
+  int naug;        // ... naug = ncomp means ū after the density (0 otherwise)
   double origin[3];
   int64_t M;
   int ncomp;       // c: 1 scalar, dim Stokes
@@ -223,6 +225,9 @@ ibdl_status apply_2d_indexed(Geometry* g, int precision, double* V, const int* i
                              const int* stop, int op = OPK_A);
 ibdl_status apply_3d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
                              const int* stop, int op = OPK_A);
+
+// length of a boundary vector of the (possibly augmented) system: c·M density values, then ū
+inline int geom_nd(const Geometry* g) { return (int)(g->ncomp * g->M) + g->naug; }
 
 inline ibdl_status apply_any(Geometry* g, int precision, const double* Q, double* Y,
                              cudaStream_t s, const int* stop_flag, int op = OPK_A) {

@@ -95,6 +95,7 @@ extern "C" ibdl_status ibdl_apply_noalloc(const ibdl_geometry_desc* d, int preci
   if (d->pde != IBDL_PDE_SCALAR && d->pde != IBDL_PDE_STOKES) return fail(IBDL_ERR_INVALID_ARG, "unknown pde");
   if (!(d->lambda >= 0)) return fail(IBDL_ERR_INVALID_ARG, "lambda must be >= 0");
   if (d->bc != IBDL_BC_DIRICHLET && d->bc != IBDL_BC_NEUMANN) return fail(IBDL_ERR_INVALID_ARG, "unknown boundary condition");
+  if (d->eta != 0) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_apply_noalloc: the completed method (eta > 0) is not supported");
   if (d->bc == IBDL_BC_NEUMANN && d->pde != IBDL_PDE_SCALAR)
     return fail(IBDL_ERR_UNSUPPORTED, "Neumann conditions are implemented for the scalar PDE");
   if (d->pde == IBDL_PDE_STOKES && !(d->mu > 0)) return fail(IBDL_ERR_INVALID_ARG, "mu must be > 0");

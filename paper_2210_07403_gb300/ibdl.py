@@ -51,7 +51,8 @@ class ibdl_geometry_desc(ctypes.Structure):
     _fields_ = [("dim", c_int), ("n", c_int), ("box", c_double), ("origin", c_double * 3),
                 ("n_points", c_int64), ("X", c_void_p), ("normals", c_void_p), ("weights", c_void_p),
                 ("pde", c_int), ("lambda_", c_double), ("mu", c_double), ("delta", c_int),
-                ("dipole", c_int), ("symbol", c_int), ("inputs_on_device", c_int), ("bc", c_int)]
+                ("dipole", c_int), ("symbol", c_int), ("inputs_on_device", c_int), ("bc", c_int),
+                ("eta", c_double)]
 
 
 class ibdl_solve_opts(ctypes.Structure):
@@ -368,7 +369,8 @@ class Geometry:
 
     def __init__(self, X, normals, weights, n: int, box: float = 1.0, origin=(0.0, 0.0, 0.0),
                  pde: str = "scalar", lam: float = 0.0, mu: float = 1.0, delta: str = "cos",
-                 dipole: str = "analytic", symbol: str = "spectral", stream=None, bc: str = "dirichlet"):
+                 dipole: str = "analytic", symbol: str = "spectral", stream=None, bc: str = "dirichlet",
+                 eta: float = 0.0):
         import torch
 
         self._torch = torch
@@ -390,14 +392,18 @@ class Geometry:
         d.delta, d.dipole, d.symbol = _DELTA[delta], _DIPOLE[dipole], _SYMBOL[symbol]
         d.inputs_on_device = int(on_device)
         d.bc = _BC[bc]
+        d.eta = float(eta)
         self.dim, self.n, self.M, self.pde = dim, int(n), M, pde
         self.ncomp = dim if pde == "stokes" else 1
+        # completed method: ū (one mean per component) follows the density in every vector
+        self.naug = self.ncomp if eta > 0 else 0
+        self.nd = self.ncomp * M + self.naug
         self._h = ibdl_create_geometry(d, _stream_handle(stream))
 
     @classmethod
     def from_problem(cls, p, **overrides):
         kw = dict(n=p.N, box=p.box, origin=p.origin, pde=p.pde, lam=p.lam, mu=p.mu, delta=p.delta,
-                  bc=getattr(p, "bc", "dirichlet"),
+                  bc=getattr(p, "bc", "dirichlet"), eta=getattr(p, "eta", 0.0),
                   dipole=p.dipole, symbol=p.symbol)
         kw.update(overrides)
         return cls(p.bd.X, p.bd.n, p.bd.w, **kw)
@@ -411,7 +417,7 @@ class Geometry:
         if isinstance(v, np.ndarray):
             v = t.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).cuda()
         assert v.is_cuda and v.dtype == t.float64 and v.is_contiguous()
-        assert v.numel() == self.ncomp * self.M
+        assert v.numel() == self.nd
         return v
 
     def apply(self, Q, Y=None, precision: str = "fp64", stream=None):

@@ -156,3 +156,86 @@ def test_variant_error_paths():
     gb = _geom(pb)
     with pytest.raises(IbdlError, match="UNSUPPORTED"):
         gb.single_layer(_cuda(np.ones(200)))
+
+
+# ----------------------------------------------------------------------------------------
+# completed method (Sec. 5.3.3, Sec. 6.3.3)
+# ----------------------------------------------------------------------------------------
+
+
+def _completed_scalar(N=64):
+    from paper_2210_07403_gb300 import Geometry
+
+    M = I.points_for_spacing(2 * np.pi * 0.25, 1.0 / N, 1.0)
+    bd = I.circle(M)
+    og = O.Geometry(O.Grid(2, N), bd.X, bd.n, bd.w, "sqrt", "analytic", "spectral", "scalar", 0.0, eta=10.0)
+    g = Geometry(bd.X, bd.n, bd.w, N, delta="sqrt", eta=10.0)
+    return g, og, bd
+
+
+@pytest.mark.parametrize("kind", ["stokes", "scalar"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_completed_apply_and_field(kind, precision, tol):
+    if kind == "stokes":
+        p = I.cylinder_array(128, 0.2)
+        g, og = _geom(p), O.geometry_from_problem(p)
+    else:
+        g, og, _ = _completed_scalar()
+    nd = og.ncomp * og.M + og.naug
+    assert g.nd == nd
+    x = np.random.default_rng(8).standard_normal(nd)
+    assert _rel(g.apply(_cuda(x), precision=precision).cpu().numpy(), O.apply(og, x)) < tol
+    if precision == "fp64":
+        assert _rel(g.evaluate_field(_cuda(x)).cpu().numpy(), O.grid_field(og, x)) < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_completed_solve(precision, tol):
+    p = I.cylinder_array(128, 0.2)
+    g, og = _geom(p), O.geometry_from_problem(p)
+    b = np.concatenate([p.Ub.reshape(-1), p.meta["rhs_aug"]])
+    ref = O.solve(og, b, 1e-13, maxit=200).x
+    x, info, _ = g.solve(_cuda(b), rtol=1e-12 if precision == "fp64" else 1e-10, precision=precision,
+                         inner_rtol=1e-5, maxit=300)
+    assert _rel(x.cpu().numpy(), ref) < tol
+
+
+@pytest.mark.parametrize("c", [0.05, 0.2])
+def test_cylinder_drag_1024(c):
+    """The drag of the periodic cylinder array at 1024² on the GPU: the oracle's value to 1e-8
+    and the published boundary-integral value (Sec. 6.5.3, golden file) to 1 %."""
+    import os
+
+    ref = None
+    with open(os.path.join(os.path.dirname(__file__), "golden", "cylinder_drag.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#") and float(line.split()[0]) == c:
+                ref = float(line.split()[2])
+    p = I.cylinder_array(1024, c)
+    g, og = _geom(p), O.geometry_from_problem(p)
+    b = np.concatenate([p.Ub.reshape(-1), p.meta["rhs_aug"]])
+    x, info, _ = g.solve(_cuda(b), rtol=1e-12, maxit=300)
+    xs = x.cpu().numpy()
+    u = g.evaluate_field(x).cpu().numpy()
+    U = u[0][:, 0].sum() / 1024
+    D = -10.0 * (xs[:og.M] @ og.w) / U
+    oref = O.solve(og, b, 1e-12, maxit=300).x
+    Dref = O.net_force(og, oref)[0] / O.mean_inflow(og, oref)
+    assert abs(D - Dref) < 1e-8 * Dref
+    assert abs(D - ref) < 0.01 * ref
+
+
+def test_completed_error_paths():
+    from paper_2210_07403_gb300 import IbdlError
+
+    p = I.cylinder_array(64, 0.2)
+    p.lam = 1.0
+    with pytest.raises(IbdlError, match="UNSUPPORTED"):
+        _geom(p)
+    p = I.cylinder_array(64, 0.2)
+    g = _geom(p)
+    v = _cuda(np.ones(g.nd))
+    with pytest.raises(IbdlError, match="UNSUPPORTED"):
+        g.apply_transpose(v)
+    with pytest.raises(IbdlError, match="UNSUPPORTED"):
+        g.solve_vjp(v, v)
