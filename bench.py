@@ -279,6 +279,7 @@ def extra_workloads(dev, flush, stream, K=5):
     out["sphere_128"] = res
     g.close()
     out["stokes_star_probes_1024"] = differentiation_workload(dev, flush, stream, K)
+    out["cylinder_array_drag_1024"] = cylinder_drag_workload(dev, flush, stream)
     return out
 
 
@@ -329,6 +330,53 @@ def differentiation_workload(dev, flush, stream, K=5):
     res["mixed_grad_rel_diff_vs_fp64"] = {
         k: float(np.linalg.norm(a - b) / np.linalg.norm(b))
         for k, a, b in zip(("Ub", "X", "n", "w"), grads["mixed"], grads["fp64"])}
+    return res
+
+
+def _published_drag():
+    """The paper's drag table (Sec. 6.5.3), as stored in the golden file: c -> (IBDL at 8192², G&K)."""
+    out = {}
+    with open(os.path.join(ROOT, "tests", "golden", "cylinder_drag.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                c, ibdl, gk = line.split()
+                out[float(c)] = (float(ibdl), float(gk))
+    return out
+
+
+def cylinder_drag_workload(dev, flush, stream, K=3, N=1024, cs=(0.05, 0.1, 0.2, 0.3, 0.4, 0.5)):
+    """The paper's Stokes flow past a periodic array of cylinders (Sec. 6.5.3) at N², completed
+    method (η = 10, Δs ≈ Δx): the dimensionless drag D = B₁/(μU) per area fraction c against the
+    published values, and the solve rate in FP64 (rtol 1e-10) and mixed precision (rtol 1e-9)."""
+    import torch
+
+    import ibdl_inputs as I
+    from paper_2210_07403_gb300 import Geometry
+
+    pub = _published_drag()
+    res = {"grid": N, "eta": 10.0, "spacing": "ds ~ dx"}
+    for c in cs:
+        p = I.cylinder_array(N, c)
+        g = Geometry.from_problem(p)
+        b = torch.from_numpy(np.concatenate([p.Ub.reshape(-1), p.meta["rhs_aug"]])).to(dev)
+        w = torch.from_numpy(p.bd.w).to(dev)
+        row = {"points": int(p.bd.X.shape[1])}
+        for prec, rtol in (("fp64", 1e-10), ("mixed", SOLVE_RTOL)):
+            def run():
+                return g.solve(b, rtol=rtol, precision=prec, inner_rtol=INNER_RTOL, maxit=400)
+            run()
+            t, (x, info, st) = _event_ms(run, K, flush, stream)
+            u = g.evaluate_field(x)
+            U = float(u[0][:, 0].sum()) / N
+            D = float(-p.eta * (x[: g.M] * w).sum()) / U
+            row[prec] = {"D": D, "iterations": info["iterations"], "solves_per_s": round(1e3 / t, 1)}
+        ibdl_ref, gk = pub.get(c, (None, None))
+        row["D_published_ibdl_8192"] = ibdl_ref
+        row["D_greengard_kropinski"] = gk
+        if gk:
+            row["rel_diff_vs_gk"] = (row["fp64"]["D"] - gk) / gk
+        res[f"c={c}"] = row
+        g.close()
     return res
 
 
