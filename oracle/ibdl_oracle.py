@@ -15,6 +15,8 @@ for a reader to check against the paper by eye:
   A Q         −S* L⁻¹ S̃ Q + ½Q, Sec. 5.3.2 (Eq. "ibdl schur again")
   A Q Stokes  −S*Δ₀⁻¹∇Δ₀⁻¹Δ S(Q·n) − S*Δ₀⁻¹ P ∇·(S A) + ½Q, Sec. 6.3.3 (interior, η = 0)
   GMRES       unrestarted, zero initial guess, Sec. 5.3.2
+  χ, flags    indicator of the enclosed region, Sec. 5.3.5
+  interp      near-boundary linear interpolation, Sec. 5.3.4
 
 Readings of points the paper leaves open are listed with each function; all are the same
 readings the CUDA path takes.
@@ -796,3 +798,109 @@ def probe_vjp(geom: Geometry, P: np.ndarray, Q: np.ndarray, nu: np.ndarray):
     nu = np.asarray(nu, dtype=np.float64).reshape(c, -1)
     psi = [spread_unweighted(pg, nu[l]) for l in range(c)]
     return _spread_terms(geom, np.asarray(Q, dtype=np.float64), _multiplier_T(geom, psi))
+
+
+# ----------------------------------------------------------------------------------------
+# solution post-processing: indicator flagging (Sec. 5.3.5) and near-boundary interpolation
+# (Sec. 5.3.4)
+# ----------------------------------------------------------------------------------------
+
+
+def indicator(geom: Geometry):
+    """The regularised indicator of the region enclosed by the discrete curve(s), Sec. 5.3.5:
+    χ solves Δχ = −S̃1 (the IBDL grid field of the unit density for the Laplacian, mean-zero
+    inverse, whatever PDE the geometry carries; its δ_h, dipole spread and symbol are kept),
+    shifted so that χ = 0 at the box corner (grid node 0), and the flags |χ| > ½.
+
+    Reading: the paper thresholds χ itself at ½ for outward normals; |χ| flags the enclosed
+    nodes for either orientation of the normals (χ ≈ −1 inside when the normals point inward,
+    as for an exterior problem). Returns (χ, flags) on the grid."""
+    g0 = Geometry(geom.grid, geom.X, geom.n, geom.w, geom.delta, geom.dipole, geom.symbol, "scalar", 0.0)
+    chi = field_scalar(g0, np.ones(geom.M))
+    chi = chi - chi.flat[0]
+    return chi, np.abs(chi) > 0.5
+
+
+def min_image(d, L):
+    """Minimum-image offset in a periodic box of side L: d − L·round(d/L) (ties to even)."""
+    return d - L * np.round(d / L)
+
+
+def nearest_three(geom: Geometry, p):
+    """The three boundary points nearest to the point p (2-D), ordered by the squared
+    minimum-image distance dx·dx + dy·dy in FP64, equal distances by index. Returns the indices
+    and the offsets X_i − p of all points."""
+    d = min_image(geom.X - np.asarray(p, dtype=np.float64)[:, None], geom.grid.box)
+    d2 = d[0] * d[0] + d[1] * d[1]
+    order = np.lexsort((np.arange(geom.M), d2))
+    return order[:3], d, d2
+
+
+def chord_foot(d, i1, i2):
+    """x_A − x_p on the chord from x_1 to x_2 (offsets d relative to x_p), Sec. 5.3.4: the point of
+    the line through x_1, x_2 closest to x_p, x_A = x_2 + t(x_1 − x_2) with
+    t = (x_p − x_2)·(x_1 − x_2)/|x_1 − x_2|². Reading: the printed projection has the sign of
+    (x_2 − x_p) reversed against the text, which asks for the closest point; the text decides.
+    Returns (x_A − x_p, t)."""
+    x1, x2 = d[:, i1], d[:, i2]
+    seg = x1 - x2
+    t = float(-(x2 @ seg) / (seg @ seg))
+    return x2 + t * seg, t
+
+
+def near_boundary_interp(geom: Geometry, Ub, u, omega, m1: float = 6.0, m2: float = 8.0) -> np.ndarray:
+    """Sec. 5.3.4 (2-D), per component of u ((c, N, N) or (N, N)): every node x_p of the mask
+    ``omega`` whose nearest boundary point lies closer than m1·h gets
+        u(x_p) = u_A |x_B − x_p|/|x_B − x_A| + u_B |x_A − x_p|/|x_B − x_A|,
+    x_A the foot of x_p on the chord of its two nearest boundary points x_1, x_2 (when t falls
+    outside [0, 1]: on the chord of the two outermost of the three nearest points, i.e. the
+    pair farthest apart, t then clamped to [0, 1]), u_A = U_b(x_1)|x_A − x_2|/|x_2 − x_1| +
+    U_b(x_2)|x_A − x_1|/|x_2 − x_1|, x_B = x_A + m2·h (x_p − x_A)/|x_p − x_A| and u_B the bilinear
+    interpolation of the four grid values around x_B. A node on the chord (x_A = x_p) takes u_A.
+    Other nodes keep their values. Distances by minimum image; the node set, the neighbours and
+    the fallback are decided on squared FP64 distances. The paper's settings: m1 = 6, m2 = 8
+    (finite differences); m1 = 2(log₂N − 4), m2 = m1 + 2 (spectral)."""
+    grid = geom.grid
+    if grid.dim != 2:
+        raise NotImplementedError("near-boundary interpolation: 2-D")
+    h, N = grid.h, grid.N
+    c = geom.ncomp
+    U = np.asarray(u, dtype=np.float64).reshape((c, N, N))
+    Ubc = np.asarray(Ub, dtype=np.float64).reshape(-1)[: c * geom.M].reshape(c, geom.M)
+    out = U.copy()
+    xs, ys = grid.coords()
+    r1 = m1 * h
+    for iy, ix in zip(*np.nonzero(np.asarray(omega).reshape(N, N))):
+        p = np.array([xs[iy, ix], ys[iy, ix]])
+        three, d, d2 = nearest_three(geom, p)
+        if not d2[three[0]] < r1 * r1:
+            continue
+        i1, i2 = three[0], three[1]
+        xA, t = chord_foot(d, i1, i2)
+        if t < 0.0 or t > 1.0:
+            pairs = [(three[0], three[1]), (three[0], three[2]), (three[1], three[2])]
+            sep = [np.sum((d[:, a] - d[:, b]) ** 2) for a, b in pairs]
+            i1, i2 = pairs[int(np.argmax(sep))]
+            xA, t = chord_foot(d, i1, i2)
+            t = min(1.0, max(0.0, t))
+            xA = d[:, i2] + t * (d[:, i1] - d[:, i2])
+        lseg = math.hypot(*(d[:, i1] - d[:, i2]))
+        wa1 = math.hypot(*(xA - d[:, i2])) / lseg  # weight of U_b(x_1)
+        wa2 = math.hypot(*(xA - d[:, i1])) / lseg  # weight of U_b(x_2)
+        rA = math.hypot(*xA)  # |x_A − x_p|
+        if rA == 0.0:
+            out[:, iy, ix] = Ubc[:, i1] * wa1 + Ubc[:, i2] * wa2
+            continue
+        xB = xA - xA / rA * (m2 * h)  # x_p is the origin: x_B − x_p
+        gx = (p[0] + xB[0] - grid.origin[0]) / h
+        gy = (p[1] + xB[1] - grid.origin[1]) / h
+        jx, jy = int(math.floor(gx)), int(math.floor(gy))
+        ax, ay = gx - jx, gy - jy
+        rB = math.hypot(*xB)  # |x_B − x_p|
+        for comp in range(c):
+            uA = Ubc[comp, i1] * wa1 + Ubc[comp, i2] * wa2
+            F = U[comp]
+            uB = ((1 - ax) * (1 - ay) * F[jy % N, jx % N] + ax * (1 - ay) * F[jy % N, (jx + 1) % N]
+                  + (1 - ax) * ay * F[(jy + 1) % N, jx % N] + ax * ay * F[(jy + 1) % N, (jx + 1) % N])
+            out[comp, iy, ix] = (uA * rB + uB * rA) / (m2 * h)
+    return out.reshape(np.shape(u))

@@ -829,3 +829,156 @@ def test_completed_rejects_screening():
     geom.eta = 1.0
     with pytest.raises(NotImplementedError):
         O.apply(geom, np.ones(bd.M + 1))
+
+
+# ----------------------------------------------------------------------------------------
+# post-processing: indicator flagging (Sec. 5.3.5), near-boundary interpolation (Sec. 5.3.4)
+# ----------------------------------------------------------------------------------------
+
+
+def _three_shapes(N, alpha=0.75):
+    """A circle, a rotated ellipse and a star in one box, as in the indicator illustration of
+    Sec. 5.3.5, with their exact membership tests."""
+    h = 1.0 / N
+    c = I.circle(I.points_for_spacing(2 * np.pi * 0.12, h, alpha), R=0.12, center=(0.25, 0.27))
+    e = I.ellipse(I.points_for_spacing(2 * np.pi * 0.12, h, alpha), 0.16, 0.08, rot=0.6, center=(0.72, 0.3))
+    s = I.star(I.points_for_spacing(2 * np.pi * 0.17, h, alpha), a=0.17, eps=0.2, k=5, center=(0.5, 0.72))
+
+    def inside(x, y):
+        in_c = np.hypot(x - 0.25, y - 0.27) < 0.12
+        xr, yr = x - 0.72, y - 0.3
+        u, v = np.cos(0.6) * xr + np.sin(0.6) * yr, -np.sin(0.6) * xr + np.cos(0.6) * yr
+        in_e = (u / 0.16) ** 2 + (v / 0.08) ** 2 < 1
+        th = np.arctan2(y - 0.72, x - 0.5)
+        in_s = np.hypot(x - 0.5, y - 0.72) < 0.17 * (1 + 0.2 * np.cos(5 * th))
+        return in_c | in_e | in_s
+
+    X = np.concatenate([c.X, e.X, s.X], axis=1)
+    n = np.concatenate([c.n, e.n, s.n], axis=1)
+    w = np.concatenate([c.w, e.w, s.w])
+    return X, n, w, inside
+
+
+def _dist_to(X_dense, x, y):
+    pts = np.stack([x.ravel(), y.ravel()], 1)
+    d = np.full(pts.shape[0], np.inf)
+    for i in range(0, X_dense.shape[1], 512):
+        blk = X_dense[:, i:i + 512].T
+        d = np.minimum(d, np.sqrt(((pts[:, None, :] - blk[None]) ** 2).sum(-1)).min(1))
+    return d.reshape(x.shape)
+
+
+@pytest.mark.parametrize("delta,symbol", [("sqrt", "fd2"), ("cos", "spectral")])
+def test_indicator_flags_three_shapes(delta, symbol):
+    """χ → 1 inside the curves and 0 outside (the jump of the double layer of a unit density,
+    Sec. 3), so the flags equal exact membership at every node farther than 2h from Γ, for
+    three shapes at once; reversed normals give χ → −1 inside and the same flags."""
+    N = 128
+    X, n, w, inside = _three_shapes(N)
+    geom = O.Geometry(O.Grid(2, N), X, n, w, delta, "analytic", symbol, "scalar", 0.0)
+    chi, flags = O.indicator(geom)
+    x, y = geom.grid.coords()
+    Xd, _, _, _ = _three_shapes(2048, alpha=1.0)
+    far = _dist_to(Xd, x, y) > 2.0 / N
+    exact = inside(x, y)
+    assert np.array_equal(flags[far], exact[far])
+    deep = _dist_to(Xd, x, y) > 8.0 / N
+    assert np.abs(chi[deep & exact] - 1).max() < 0.02
+    assert np.abs(chi[deep & ~exact]).max() < 0.02
+    assert abs(chi.flat[0]) == 0.0
+    geom_in = O.Geometry(O.Grid(2, N), X, -n, w, delta, "analytic", symbol, "scalar", 0.0)
+    chi2, flags2 = O.indicator(geom_in)
+    assert np.array_equal(flags2, flags)
+    assert np.allclose(chi2, -chi, atol=1e-12)
+
+
+def test_indicator_ignores_the_geometry_pde():
+    """The indicator solves the Laplace problem whatever PDE, λ or η the geometry carries."""
+    N = 64
+    bd = I.circle(I.points_for_spacing(2 * np.pi * 0.25, 1 / N, 0.75))
+    g0 = O.Geometry(O.Grid(2, N), bd.X, bd.n, bd.w, "cos", "analytic", "spectral", "scalar", 0.0)
+    g1 = O.Geometry(O.Grid(2, N), bd.X, bd.n, bd.w, "cos", "analytic", "spectral", "stokes", 5.0, 2.0)
+    assert np.array_equal(O.indicator(g0)[0], O.indicator(g1)[0])
+
+
+def test_nearest_three_against_brute_force():
+    """Nearest boundary points under periodic wrap: brute force over the nine periodic images."""
+    rng = np.random.default_rng(11)
+    L = 2.0
+    X = rng.uniform(-1, 1, (2, 40))
+    geom = O.Geometry(O.Grid(2, 32, L, (-1.0, -1.0)), X, np.zeros_like(X), np.ones(40))
+    for _ in range(50):
+        p = rng.uniform(-1, 1, 2)
+        three, d, d2 = O.nearest_three(geom, p)
+        best = [min((X[0, i] + sx * L - p[0]) ** 2 + (X[1, i] + sy * L - p[1]) ** 2
+                    for sx in (-1, 0, 1) for sy in (-1, 0, 1)) for i in range(40)]
+        assert list(three) == list(np.argsort(best, kind="stable")[:3])
+        assert np.allclose(d2, best, rtol=1e-13, atol=1e-15)
+
+
+def test_chord_foot_is_the_closest_point():
+    """x_A is the point of the chord's line closest to x_p (brute force along the line)."""
+    rng = np.random.default_rng(12)
+    for _ in range(30):
+        d = rng.standard_normal((2, 2))
+        xA, t = O.chord_foot(d, 0, 1)
+        s = np.linspace(t - 1, t + 1, 20001)
+        line = d[:, 1:2] + s * (d[:, 0:1] - d[:, 1:2])
+        assert abs(s[np.argmin(np.hypot(*line))] - t) < 2e-4
+        assert abs((xA @ (d[:, 0] - d[:, 1]))) < 1e-12
+
+
+@pytest.mark.parametrize("shape", ["circle", "star"])
+def test_near_boundary_reproduces_linear_fields(shape):
+    """Linear data are reproduced exactly: u_A (linear along the chord), u_B (bilinear) and the
+    blend along x_A–x_B are each exact for linear functions, so every replaced node takes the
+    exact value although the grid values within the band and outside Ω are garbage; a Stokes
+    geometry carries two components with different slopes."""
+    N, m1, m2 = 128, 6.0, 8.0
+    M = I.points_for_spacing(2 * np.pi * 0.25, 1 / N, 0.75)
+    bd = I.circle(M) if shape == "circle" else I.star(M)
+    geom = O.Geometry(O.Grid(2, N), bd.X, bd.n, bd.w, "cos", "analytic", "spectral", "stokes")
+    x, y = geom.grid.coords()
+    if shape == "circle":
+        omega = np.hypot(x - 0.5, y - 0.5) < 0.25
+    else:
+        th = np.arctan2(y - 0.5, x - 0.5)
+        omega = np.hypot(x - 0.5, y - 0.5) < 0.25 * (1 + 0.2 * np.cos(5 * th))
+    lin = [lambda x, y: 0.3 + 1.7 * x - 0.9 * y, lambda x, y: -1.1 + 0.4 * x + 2.3 * y]
+    dist = _dist_to(I.circle(4096).X if shape == "circle" else I.star(4096).X, x, y)
+    rng = np.random.default_rng(3)
+    u = np.stack([np.where(omega & (dist > (m1 + 0.3) / N), f(x, y), rng.standard_normal(x.shape)) for f in lin])
+    Ub = np.stack([f(bd.X[0], bd.X[1]) for f in lin])
+    out = O.near_boundary_interp(geom, Ub, u, omega, m1, m2)
+    band = omega & (dist < (m1 - 0.3) / N)
+    for c, f in enumerate(lin):
+        assert np.abs(out[c][band] - f(x, y)[band]).max() < 1e-12
+    keep = ~omega | (dist > (m1 + 0.3) / N)
+    assert np.array_equal(out[:, keep], u[:, keep])
+
+
+@pytest.mark.parametrize("symbol,delta", [("fd2", "sqrt"), ("spectral", "cos")])
+def test_near_boundary_restores_pointwise_convergence(symbol, delta):
+    """Sec. 5.3.4 and its max-norm study: on the interior circle with harmonic data the raw
+    max-norm error over Ω stalls near 1e-2 (the first-order jump smeared over the stencil), while
+    the interpolated one converges (finite differences: m1 = 6, m2 = 8; spectral:
+    m1 = 2(log₂N − 4), m2 = m1 + 2)."""
+    raw, fixed, hs = [], [], []
+    for N in (64, 128, 256):
+        M = I.points_for_spacing(2 * np.pi * 0.25, 1 / N, 0.75)
+        p = I.circle_laplace(N, M, delta=delta, symbol=symbol)
+        geom = O.geometry_from_problem(p)
+        Q = O.solve(geom, p.Ub.reshape(-1), 1e-12, maxit=200).x
+        u = O.field_scalar(geom, Q)
+        _, flags = O.indicator(geom)
+        x, y = geom.grid.coords()
+        exact = I.harmonic_cubic(x, y)
+        m1 = 6.0 if symbol == "fd2" else 2.0 * (math.log2(N) - 4)
+        m2 = 8.0 if symbol == "fd2" else m1 + 2
+        ui = O.near_boundary_interp(geom, p.Ub.reshape(-1), u, flags, m1, m2)
+        raw.append(np.abs(u - exact)[flags].max())
+        fixed.append(np.abs(ui - exact)[flags].max())
+        hs.append(1 / N)
+    assert raw[-1] > 0.8 * raw[0] and raw[-1] > 5e-3
+    assert fixed[-1] < raw[-1] / 10
+    assert O.fitted_order(hs, fixed) > (1.0 if symbol == "fd2" else 0.6)
