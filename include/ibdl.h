@@ -230,6 +230,41 @@ ibdl_status ibdl_probe_evaluate(ibdl_geometry* geom, const double* P, int n_prob
 ibdl_status ibdl_probe_vjp(ibdl_geometry* geom, const double* P, int n_probes, const double* Q, const double* nu,
                            double* dQ, double* dX, double* dn, double* dw, void* stream);
 
+/* Post-processing of a grid solution.
+ *
+ * ibdl_indicator (Sec. 5.3.5): flags the grid nodes enclosed by the discrete boundary. χ solves
+ * Δχ = −S̃1, the IBDL grid field of the unit density for the Laplace problem (mean-zero inverse),
+ * with the geometry's delta kernel, dipole spread and symbol whatever its PDE, λ or η; in the
+ * continuum χ is the indicator of the enclosed region minus its area fraction. The call writes
+ * chi = χ − χ(box corner, node 0) (≈ 1 enclosed, ≈ 0 outside; ≈ −1 enclosed when the normals
+ * point into the enclosed region) and flags = 1 where |chi| > ½, else 0. Several disjoint curves
+ * are flagged at once. chi: device FP64 [n^dim]; flags: device uint8 [n^dim]; they may not
+ * overlap. 2-D and 3-D. Asynchronous. The geometry keeps a post-processing workspace (one FP64
+ * grid field plus, in 2-D, 5 bytes per node), allocated by the first post-processing call.
+ *
+ * ibdl_near_boundary (Sec. 5.3.4, 2-D): replaces the grid values near Γ by linear interpolation.
+ * Every node x_p with omega[x_p] ≠ 0 whose nearest boundary point lies closer than m1·h gets
+ *     u(x_p) = u_A |x_B − x_p|/|x_B − x_A| + u_B |x_A − x_p|/|x_B − x_A|,
+ * x_A the point of the chord between its two nearest boundary points x_1, x_2 closest to x_p (if
+ * that point falls off the chord: the chord between the two of the three nearest points lying
+ * farthest apart, the point clamped to it), u_A = U_b(x_1)|x_A − x_2|/|x_2 − x_1| +
+ * U_b(x_2)|x_A − x_1|/|x_2 − x_1|, x_B = x_A + m2·h (x_p − x_A)/|x_p − x_A| and u_B the bilinear
+ * interpolation of u at the four nodes around x_B. A node on the chord takes u_A; all other nodes
+ * are copied. Distances are minimum-image; nearness and the nearest points are decided on FP64
+ * squared distances, equal ones ordered by point index. The paper's settings: m1 = 6, m2 = 8 with
+ * IBDL_SYMBOL_FD2; m1 = 2(log₂n − 4), m2 = m1 + 2 with IBDL_SYMBOL_SPECTRAL.
+ *   Ub     device FP64 [c][M] boundary values (Dirichlet data; for a Neumann solve, its Q; for a
+ *          completed geometry the first c·M entries of the right-hand side)
+ *   u      device FP64 [c][n][n] grid solution (ibdl_evaluate_field)
+ *   omega  device uint8 [n][n], nonzero on the PDE domain Ω: the flags of ibdl_indicator for an
+ *          interior problem, their complement for an exterior one
+ *   m1     0 < m1 < n/2; m2 > 0 (meshwidths)
+ *   out    device FP64 [c][n][n], may not overlap the inputs
+ * Needs M ≥ 3 (IBDL_ERR_INVALID_ARG) and dim = 2 (IBDL_ERR_UNSUPPORTED otherwise). Asynchronous. */
+ibdl_status ibdl_indicator(ibdl_geometry* geom, double* chi, uint8_t* flags, void* stream);
+ibdl_status ibdl_near_boundary(ibdl_geometry* geom, const double* Ub, const double* u, const uint8_t* omega, double m1,
+                               double m2, double* out, void* stream);
+
 /* The grid solution of a density (Sec. 5.1.2 step 2 with g̃ = 0): scalar u = −L⁻¹S̃Q written
  * to u_grid[n^dim]; Stokes velocity written to u_grid[dim][n^dim]. FP64 device arrays;
  * asynchronous. */

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libibdl.so")
-SOURCES = ["api.cu", "geometry.cu", "apply2d.cu", "apply3d.cu", "gmres.cu", "noalloc.cu", "batch.cu", "vjp.cu"]
+SOURCES = ["api.cu", "geometry.cu", "apply2d.cu", "apply3d.cu", "gmres.cu", "noalloc.cu", "batch.cu", "vjp.cu", "postproc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

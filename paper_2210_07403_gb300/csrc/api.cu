@@ -328,3 +328,36 @@ ibdl_status ibdl_get_stage_times(ibdl_geometry* geom, double* ms, int64_t* launc
 const char* ibdl_last_error(void) { return ibdl::g_last_error.c_str(); }
 
 }  // extern "C"
+
+ibdl_status ibdl_indicator(ibdl_geometry* geom, double* chi, uint8_t* flags, void* stream) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  Geometry* g = geom->g;
+  IBDL_TRY(check_device_ptr(chi, "chi"));
+  IBDL_TRY(check_device_ptr(flags, "flags"));
+  size_t cells = (size_t)g->n * g->n;
+  if (g->dim == 3) cells *= g->n;
+  if (spans_overlap(chi, sizeof(double) * cells, flags, cells)) return fail(IBDL_ERR_INVALID_ARG, "chi and flags overlap");
+  return indicator_impl(g, chi, flags, static_cast<cudaStream_t>(stream));
+}
+
+ibdl_status ibdl_near_boundary(ibdl_geometry* geom, const double* Ub, const double* u, const uint8_t* omega, double m1,
+                               double m2, double* out, void* stream) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  Geometry* g = geom->g;
+  if (g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_near_boundary: 2-D only");
+  if (g->M < 3) return fail(IBDL_ERR_INVALID_ARG, "ibdl_near_boundary: needs at least three boundary points");
+  if (!(m1 > 0) || !(m1 < 0.5 * g->n)) return fail(IBDL_ERR_INVALID_ARG, "m1 must lie in (0, n/2)");
+  if (!(m2 > 0) || !std::isfinite(m2)) return fail(IBDL_ERR_INVALID_ARG, "m2 must be positive and finite");
+  IBDL_TRY(check_device_ptr(Ub, "Ub"));
+  IBDL_TRY(check_device_ptr(u, "u"));
+  IBDL_TRY(check_device_ptr(omega, "omega"));
+  IBDL_TRY(check_device_ptr(out, "out"));
+  const size_t cells = (size_t)g->n * g->n;
+  const size_t ob = sizeof(double) * g->ncomp * cells;
+  if (spans_overlap(out, ob, u, ob) || spans_overlap(out, ob, Ub, sizeof(double) * g->ncomp * g->M) ||
+      spans_overlap(out, ob, omega, cells))
+    return fail(IBDL_ERR_INVALID_ARG, "out overlaps Ub, u or omega");
+  return near_boundary_impl(g, Ub, u, omega, m1, m2, out, static_cast<cudaStream_t>(stream));
+}

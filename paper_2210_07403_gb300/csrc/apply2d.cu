@@ -699,7 +699,7 @@ static ibdl_status set_attrs_all() {
 template <typename T, int OP>
 static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream_t s, const int* stop,
                           double* grid, const int* idx = nullptr, int vstride = 0, int trans = 0,
-                          const double* grid_in = nullptr) {
+                          const double* grid_in = nullptr, bool laplace = false) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi];
   if (R == 0 || C == 0)
@@ -718,6 +718,11 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
     rp.eta_src = T(0);
   }
   ColParams<T> cp = col_params<T>(g, stop);
+  if (laplace) {  // the plain Laplace problem (indicator): no screening, no completed-method terms
+    cp.lam = T(0);
+    rp.aug = 0;
+    rp.eta_src = T(0);
+  }
   const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
   const int nt = g->threads[pi] ? g->threads[pi] : kThreads;
@@ -788,6 +793,13 @@ ibdl_status transform_T_2d(Geometry* g, const double* psi, double* v, cudaStream
   if (g->pde == IBDL_PDE_STOKES)
     return run_op<double, OP_STOKES_T>(g, nullptr, nullptr, s, nullptr, v, nullptr, 0, 0, psi);
   return run_op<double, OP_ADJ_AN>(g, nullptr, nullptr, s, nullptr, v, nullptr, 0, 1, psi);
+}
+
+// u = −Δ₀⁻¹S̃Q (mean-zero) with the geometry's δ_h, dipole spread and symbol, whatever its PDE
+ibdl_status laplace_field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s) {
+  return g->dipole == IBDL_DIPOLE_ANALYTIC
+             ? run_op<double, OP_SCALAR_AN>(g, Q, g->tmp_m, s, nullptr, u, nullptr, 0, 0, nullptr, true)
+             : run_op<double, OP_SCALAR_SD>(g, Q, g->tmp_m, s, nullptr, u, nullptr, 0, 0, nullptr, true);
 }
 
 ibdl_status field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s) {

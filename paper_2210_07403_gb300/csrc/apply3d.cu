@@ -542,7 +542,7 @@ ibdl_status plan_3d(Geometry* g) {
 
 template <typename T, int OP>
 static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStream_t s, const int* stop, double* grid,
-                           const int* idx = nullptr, int vstride = 0, int trans = 0) {
+                           const int* idx = nullptr, int vstride = 0, int trans = 0, bool laplace = false) {
   constexpr int NIN = Traits3<OP>::NIN, NOUT = Traits3<OP>::NOUT;
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi], Cz = g->zcols_per_cta[pi];
@@ -577,7 +577,7 @@ static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStrea
   cp.log2n = rp.log2n;
   cp.C = C;
   cp.lc = __builtin_ctz(C);
-  cp.lam = g->lambda;
+  cp.lam = laplace ? 0.0 : g->lambda;
   cp.scale = 1.0 / ((double)n * n * n);
   cp.lap1 = pi ? (const void*)g->lap32 : (const void*)g->lap64;
   cp.der1 = pi ? (const void*)g->der32 : (const void*)g->der64;
@@ -635,6 +635,13 @@ ibdl_status apply_3d_indexed(Geometry* g, int precision, double* V, const int* i
 ibdl_status field_pair_3d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s) {
   IBDL_TRY(apply3_t<double>(g, Q, g->tmp_m, s, nullptr, u));
   return apply3_t<double>(g, lam, g->tmp_m, s, nullptr, v, nullptr, 0, OPK_AT);
+}
+
+// u = −Δ₀⁻¹S̃Q (mean-zero), the geometry's λ ignored
+ibdl_status laplace_field_3d(Geometry* g, const double* Q, double* u, cudaStream_t s) {
+  return g->dipole == IBDL_DIPOLE_ANALYTIC
+             ? run_op3<double, OP3_SCALAR_AN>(g, Q, g->tmp_m, s, nullptr, u, nullptr, 0, 0, true)
+             : run_op3<double, OP3_SCALAR_SD>(g, Q, g->tmp_m, s, nullptr, u, nullptr, 0, 0, true);
 }
 
 ibdl_status field_3d(Geometry* g, const double* Q, double* u, cudaStream_t s) {

@@ -177,7 +177,7 @@ static void free_geometry(Geometry* g) {
   void* ptrs[] = {g->perm, g->base, g->cell_start, g->t64.phi, g->t64.dphi, g->t64.wscale, g->t64.nrm,
                   g->t32.phi, g->t32.dphi, g->t32.wscale, g->t32.nrm, g->spec, g->tw64, g->tw32,
                   g->lap64, g->der64, g->lap32, g->der32, g->ubuf, g->tmp_m, g->V, g->gm, g->vec,
-                  g->ddphi64, g->vjp_buf};
+                  g->ddphi64, g->vjp_buf, g->X64, g->pp_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 4; ++i)
@@ -395,7 +395,7 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
     GCUDA(cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming));
     GTRY(dim == 2 ? plan_2d(g) : plan_3d(g));
   }
-  cudaFree(dX);
+  g->X64 = dX;  // kept: the near-boundary interpolation decides on the caller's coordinates
   cudaFree(dN);
   cudaFree(dW);
   cudaFree(key);

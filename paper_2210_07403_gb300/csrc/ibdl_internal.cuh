@@ -98,6 +98,9 @@ struct Geometry {
   PointTable<double> t64;
   PointTable<float> t32;
   double* ddphi64; // [dim][4][M] φ''(r)/h² in sorted order (boundary derivatives); may be NULL
+  double* X64;     // [dim][M] the caller's coordinates, original order (post-processing)
+  void* pp_buf;    // post-processing scratch, allocated on first use
+  size_t pp_bytes;
 
   // workspace: half spectra, packed format (see apply kernels): [nf][rows][n/2] complex
   void* spec;      // sized for nf_in fields in FP64
@@ -214,6 +217,11 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
 ibdl_status transform_T_2d(Geometry* g, const double* psi, double* v, cudaStream_t s);
 ibdl_status single_layer_2d(Geometry* g, int precision, const double* V, double* Z, cudaStream_t s);
 ibdl_status field_pair_2d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s);
+ibdl_status laplace_field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s);
+ibdl_status laplace_field_3d(Geometry* g, const double* Q, double* u, cudaStream_t s);
+ibdl_status indicator_impl(Geometry* g, double* chi, uint8_t* flags, cudaStream_t s);
+ibdl_status near_boundary_impl(Geometry* g, const double* Ub, const double* u, const uint8_t* omega, double m1,
+                               double m2, double* out, cudaStream_t s);
 ibdl_status field_pair_3d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s);
 ibdl_status solve_vjp_impl(Geometry* g, const double* Q, const double* lam, double* dX, double* dn, double* dw,
                            cudaStream_t s);

@@ -99,6 +99,8 @@ SIGNATURES = {
     "ibdl_probe_evaluate": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "ibdl_probe_vjp": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                c_void_p, c_void_p]),
+    "ibdl_indicator": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ibdl_near_boundary": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_void_p, c_void_p]),
     "ibdl_last_error": (c_char_p, []),
 }
 
@@ -201,6 +203,15 @@ def ibdl_probe_vjp(geom, P: int, n_probes: int, Q: int, nu: int, dQ: int, dX: in
     return _check(load().ibdl_probe_vjp(geom, c_void_p(P), n_probes, c_void_p(Q), c_void_p(nu), c_void_p(dQ or None),
                                         c_void_p(dX or None), c_void_p(dn or None), c_void_p(dw or None),
                                         c_void_p(stream)))
+
+
+def ibdl_indicator(geom, chi: int, flags: int, stream: int = 0) -> int:
+    return _check(load().ibdl_indicator(geom, c_void_p(chi), c_void_p(flags), c_void_p(stream)))
+
+
+def ibdl_near_boundary(geom, Ub: int, u: int, omega: int, m1: float, m2: float, out: int, stream: int = 0) -> int:
+    return _check(load().ibdl_near_boundary(geom, c_void_p(Ub), c_void_p(u), c_void_p(omega), c_double(m1),
+                                            c_double(m2), c_void_p(out), c_void_p(stream)))
 
 
 def ibdl_evaluate_field(geom, Q: int, u_grid: int, stream: int = 0) -> int:
@@ -511,6 +522,31 @@ class Geometry:
         ptrs = [o.data_ptr() if o is not None else 0 for o in outs]
         ibdl_probe_vjp(self._h, P.data_ptr(), P.shape[1], Q.data_ptr(), nu.data_ptr(), *ptrs, _stream_handle(stream))
         return tuple(outs)
+
+    def indicator(self, stream=None):
+        """(χ shifted to 0 at the box corner [n]*dim float64, flags |χ| > ½ [n]*dim uint8): the nodes
+        enclosed by the boundary (Sec. 5.3.5)."""
+        t = self._torch
+        shape = (self.n,) * self.dim
+        chi = t.empty(shape, dtype=t.float64, device="cuda")
+        flags = t.empty(shape, dtype=t.uint8, device="cuda")
+        ibdl_indicator(self._h, chi.data_ptr(), flags.data_ptr(), _stream_handle(stream))
+        return chi, flags
+
+    def near_boundary(self, Ub, u, omega, m1: float, m2: float, out=None, stream=None):
+        """Grid solution u with the values of Ω within m1·h of Γ replaced by the linear interpolation
+        of Sec. 5.3.4 between U_b on Γ and u at m2·h (2-D). ``omega`` is a uint8 (or bool) mask of Ω."""
+        t = self._torch
+        Ub = t.as_tensor(Ub, dtype=t.float64).to("cuda").contiguous()
+        u = u.to(dtype=t.float64).contiguous()
+        omega = omega.to(device="cuda", dtype=t.uint8).contiguous()
+        assert Ub.numel() >= self.ncomp * self.M and u.numel() == self.ncomp * self.n ** 2
+        assert omega.numel() == self.n ** 2
+        if out is None:
+            out = t.empty_like(u)
+        ibdl_near_boundary(self._h, Ub.data_ptr(), u.data_ptr(), omega.data_ptr(), m1, m2, out.data_ptr(),
+                           _stream_handle(stream))
+        return out
 
     def _solve(self, entry, Ub, rtol, precision, restart, maxit, inner_rtol, max_refine, Q, stream, check):
         t = self._torch

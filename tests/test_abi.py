@@ -76,6 +76,8 @@ def test_host_side_argument_checks(lib):
     assert lib.ibdl_apply(None, 0, None, None, None) == ibdl.IBDL_ERR_INVALID_ARG
     assert lib.ibdl_adjoint(None, 0, None, None, None) == ibdl.IBDL_ERR_INVALID_ARG
     assert lib.ibdl_evaluate_field(None, None, None, None) == ibdl.IBDL_ERR_INVALID_ARG
+    assert lib.ibdl_indicator(None, None, None, None) == ibdl.IBDL_ERR_INVALID_ARG
+    assert lib.ibdl_near_boundary(None, None, None, None, 6.0, 8.0, None, None) == ibdl.IBDL_ERR_INVALID_ARG
     info = ibdl.ibdl_solve_info()
     assert lib.ibdl_solve(None, None, None, ctypes.byref(o), ctypes.byref(info), None) == ibdl.IBDL_ERR_INVALID_ARG
     assert lib.ibdl_destroy_geometry(None) == ibdl.IBDL_OK
