@@ -280,6 +280,7 @@ def extra_workloads(dev, flush, stream, K=5):
     g.close()
     out["stokes_star_probes_1024"] = differentiation_workload(dev, flush, stream, K)
     out["cylinder_array_drag_1024"] = cylinder_drag_workload(dev, flush, stream)
+    out["postprocess"] = postprocess_workload(dev, flush, stream)
     return out
 
 
@@ -377,6 +378,57 @@ def cylinder_drag_workload(dev, flush, stream, K=3, N=1024, cs=(0.05, 0.1, 0.2, 
             row["rel_diff_vs_gk"] = (row["fp64"]["D"] - gk) / gk
         res[f"c={c}"] = row
         g.close()
+    return res
+
+
+def postprocess_workload(dev, flush, stream, K=5, Ns=(256, 512, 1024, 2048)):
+    """Post-processing (Sec. 5.3.4, Sec. 5.3.5). The paper's max-norm study on its circle problem
+    (Δu − u = 0 inside r = 0.25, U_b = sin 2θ, Δs ≈ 0.75Δx, finite differences, m1 = 6, m2 = 8):
+    GPU solve → field → indicator → near-boundary interpolation, max error over Ω without and with
+    the interpolation against u = I₂(r) sin 2θ / I₂(0.25). Then the device time of each step on the
+    1024² Stokes star (spectral settings m1 = 12, m2 = 14)."""
+    import torch
+    from scipy.special import iv
+
+    import ibdl_inputs as I
+    from paper_2210_07403_gb300 import Geometry
+
+    res = {"problem": "circle r=0.25, Delta u - u = 0, U_b = sin 2theta, fd2, sqrt delta, m1=6, m2=8"}
+    raw, fixed = [], []
+    for N in Ns:
+        p = I.paper_circle_helmholtz(N, 0.75, "sqrt", "fd2")
+        g = Geometry.from_problem(p)
+        ub = torch.from_numpy(p.Ub.reshape(-1).copy()).to(dev)
+        Q, info, _ = g.solve(ub, rtol=1e-10, maxit=200)
+        u = g.evaluate_field(Q)
+        _, flags = g.indicator()
+        ui = g.near_boundary(ub, u, flags, 6.0, 8.0)
+        xs = p.origin[0] + np.arange(N) / N
+        x, y = np.meshgrid(xs, xs)
+        exact = iv(2, np.hypot(x, y)) / iv(2, 0.25) * np.sin(2 * np.arctan2(y, x))
+        m = flags.cpu().numpy().astype(bool)
+        raw.append(float(np.abs(u.cpu().numpy() - exact)[m].max()))
+        fixed.append(float(np.abs(ui.cpu().numpy() - exact)[m].max()))
+        g.close()
+    res["grids"] = list(Ns)
+    res["max_err_raw"] = raw
+    res["max_err_interpolated"] = fixed
+    res["order_interpolated"] = round(float(np.polyfit(np.log([1.0 / N for N in Ns]), np.log(fixed), 1)[0]), 3)
+    p = I.star_stokes(1024, 1600)
+    g = Geometry.from_problem(p)
+    ub = torch.from_numpy(p.Ub.reshape(-1).copy()).to(dev)
+    Q, info, _ = g.solve(ub, rtol=1e-10, maxit=200)
+    u = g.evaluate_field(Q)
+    _, flags = g.indicator()
+    out = torch.empty_like(u)
+    for _ in range(3):
+        g.indicator()
+        g.near_boundary(ub, u, flags, 12.0, 14.0, out=out)
+    t_ind, _ = _event_ms(lambda: g.indicator(), K, flush, stream)
+    t_nb, _ = _event_ms(lambda: g.near_boundary(ub, u, flags, 12.0, 14.0, out=out), K, flush, stream)
+    res["stokes_star_1024"] = {"indicator_us": round(t_ind * 1e3, 1), "near_boundary_us": round(t_nb * 1e3, 1),
+                               "nodes_replaced": int((out != u).any(0).sum()), "m1": 12, "m2": 14}
+    g.close()
     return res
 
 

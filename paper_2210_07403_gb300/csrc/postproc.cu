@@ -22,11 +22,12 @@
 // gives each listed node one warp. The warp scans the points whose cell row lies within K rows
 // of the node (rows of the geometry's cell-sorted order), keeps the three nearest per lane,
 // merges them across the warp, and rescans all M points when the row slab cannot guarantee the
-// result (the third distance not below (K − 1)·h).
-#include <math_constants.h>
-
+// result (the third distance not below W = (K − 1)·h). Within the slab a point whose |dx| is not
+// below W is dropped after one FP64 subtraction and comparison: the kernel is bound by the FP64
+// pipe, so the work per point decides its time.
 #include <climits>
 #include <cmath>
+#include <cstring>
 
 #include "fft.cuh"
 
@@ -89,95 +90,115 @@ __global__ void k_compact(int64_t cells, const uint8_t* __restrict__ marks, cons
 struct NearParams {
   int n, M, c, K;
   double h, L, o0, o1;
-  double r1sq;    // (m1·h)²
-  double slabsq;  // ((K − 1)·h)²: a slab result is exact when its third distance is below this
-  double m2h;     // m2·h
-  const double* X;         // [2][M] original order
-  const int* perm;         // sorted position → original index
-  const int* cell_start;   // [n + 1] rows of constant base y
-  const double* Ub;        // [c][M]
-  const double* u;         // [c][n][n]
-  double* out;             // [c][n][n]
+  unsigned long long r1key;    // bits of (m1·h)²
+  unsigned long long slabkey;  // bits of W², W = (K − 1)·h: a slab result is exact when its third
+                               // distance is below W
+  unsigned long long slabbits, halfbits;  // bits of W and of L/2
+  double halfL;
+  double m2h;                  // m2·h
+  const double* X;             // [2][M] original order
+  const int* perm;             // sorted position → original index
+  const int* cell_start;       // [n + 1] rows of constant base y
+  const double* Ub;            // [c][M]
+  const double* u;             // [c][n][n]
+  double* out;                 // [c][n][n]
   const int* list;
   const int* count;
 };
+
+// Non-negative doubles order as their bit patterns (as unsigned integers), so distances are
+// compared on the integer pipe: the FP64 unit, the bound of this kernel, only forms them.
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ unsigned long long absbits(double v) { return dbits(v) & 0x7fffffffffffffffull; }
 
 // minimum-image offset d − L·rint(d/L), each operation rounded on its own
 __device__ __forceinline__ double mimg(double d, double L) {
   return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
 }
 
-__device__ __forceinline__ bool lex_less(double da, int ia, double db, int ib) {
-  return da < db || (da == db && ia < ib);
-}
-
-struct Top3 {
-  double d[3];
-  int i[3];
-  __device__ void init() {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      d[k] = CUDART_INF;
-      i[k] = INT_MAX;
-    }
-  }
-  __device__ void insert(double dd, int ii) {
-    if (!lex_less(dd, ii, d[2], i[2])) return;
-    if (lex_less(dd, ii, d[1], i[1])) {
-      d[2] = d[1];
-      i[2] = i[1];
-      if (lex_less(dd, ii, d[0], i[0])) {
-        d[1] = d[0];
-        i[1] = i[0];
-        d[0] = dd;
-        i[0] = ii;
-      } else {
-        d[1] = dd;
-        i[1] = ii;
-      }
-    } else {
-      d[2] = dd;
-      i[2] = ii;
-    }
-  }
-};
-
-__device__ __forceinline__ void offset(const NearParams& p, int i, double px, double py, double& dx, double& dy) {
-  dx = mimg(__dsub_rn(p.X[i], px), p.L);
-  dy = mimg(__dsub_rn(p.X[p.M + i], py), p.L);
+// the same for |d| < L/2 without the division: d/L then rounds to a value of magnitude ≤ ½,
+// which rounds to zero (ties to even), and the formula returns d
+__device__ __forceinline__ double mimg_fast(double d, const NearParams& p) {
+  return absbits(d) < p.halfbits ? d : mimg(d, p.L);
 }
 
 __device__ __forceinline__ double sqdist(double dx, double dy) { return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)); }
 
-// lanes scan sorted positions [a, b) into their own three nearest
+__device__ __forceinline__ bool key_less(unsigned long long ka, int ia, unsigned long long kb, int ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+constexpr unsigned long long kInfKey = 0x7ff0000000000000ull;  // +∞
+
+// a lane's three nearest, (squared-distance bits, index) ascending
+struct Top3 {
+  unsigned long long k0, k1, k2;
+  int i0, i1, i2;
+  __device__ void init() {
+    k0 = k1 = k2 = kInfKey;
+    i0 = i1 = i2 = INT_MAX;
+  }
+  __device__ void insert(unsigned long long k, int i) {
+    if (!key_less(k, i, k2, i2)) return;
+    if (key_less(k, i, k1, i1)) {
+      k2 = k1;
+      i2 = i1;
+      if (key_less(k, i, k0, i0)) {
+        k1 = k0;
+        i1 = i0;
+        k0 = k;
+        i0 = i;
+      } else {
+        k1 = k;
+        i1 = i;
+      }
+    } else {
+      k2 = k;
+      i2 = i;
+    }
+  }
+};
+
+// lanes scan sorted positions [a, b) into their own three nearest. With WINDOW a point whose |dx| is
+// not below W is skipped: it is no nearer than W, and a slab result is kept only when its third
+// distance is below W (otherwise every point is rescanned without the window)
+template <bool WINDOW>
 __device__ __forceinline__ void scan_range(const NearParams& p, int a, int b, int lane, double px, double py, Top3& t) {
   for (int s = a + lane; s < b; s += 32) {
     const int i = p.perm[s];
-    double dx, dy;
-    offset(p, i, px, py, dx, dy);
-    t.insert(sqdist(dx, dy), i);
+    const double dx = mimg_fast(__dsub_rn(p.X[i], px), p);
+    if (WINDOW && absbits(dx) >= p.slabbits) continue;
+    const double dy = mimg_fast(__dsub_rn(p.X[p.M + i], py), p);
+    t.insert(dbits(sqdist(dx, dy)), i);
   }
 }
 
-// the warp's three nearest (d², index), in every lane
-__device__ __forceinline__ void warp_top3(const Top3& t, int lane, double* d, int* idx) {
-  int ptr = 0;
+// the warp's three nearest, in every lane: three rounds of a butterfly minimum over the lanes'
+// heads; the lane whose head wins pops it
+__device__ __forceinline__ void warp_top3(Top3 t, unsigned long long* key, int* idx) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    double bd = ptr < 3 ? t.d[ptr] : CUDART_INF;
-    int bi = ptr < 3 ? t.i[ptr] : INT_MAX;
+  for (int r = 0; r < 3; ++r) {
+    unsigned long long bk = t.k0;
+    int bi = t.i0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (lex_less(od, oi, bd, bi)) {
-        bd = od;
+      if (key_less(ok, oi, bk, bi)) {
+        bk = ok;
         bi = oi;
       }
     }
-    d[k] = bd;
-    idx[k] = bi;
-    if (ptr < 3 && t.i[ptr] == bi && bi != INT_MAX) ++ptr;
+    key[r] = bk;
+    idx[r] = bi;
+    if (t.i0 == bi && bi != INT_MAX) {
+      t.k0 = t.k1;
+      t.i0 = t.i1;
+      t.k1 = t.k2;
+      t.i1 = t.i2;
+      t.k2 = kInfKey;
+      t.i2 = INT_MAX;
+    }
   }
 }
 
@@ -185,94 +206,117 @@ __device__ __forceinline__ double dot2(double ax, double ay, double bx, double b
   return __dadd_rn(__dmul_rn(ax, bx), __dmul_rn(ay, by));
 }
 
-__global__ void __launch_bounds__(kPPThreads) k_near(NearParams p) {
+__device__ __forceinline__ double node_x(const NearParams& p, int i) { return __dadd_rn(p.o0, __dmul_rn(p.h, (double)i)); }
+__device__ __forceinline__ double node_y(const NearParams& p, int i) { return __dadd_rn(p.o1, __dmul_rn(p.h, (double)i)); }
+
+// the interpolated value(s) of one node from its three nearest boundary points (original indices)
+__device__ void near_tail(const NearParams& p, int node, const int* i3) {
+  const int n = p.n;
+  const int ix = node % n, iy = node / n;
+  const double px = node_x(p, ix), py = node_y(p, iy);
+  double dx[3], dy[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dx[k] = mimg_fast(__dsub_rn(p.X[i3[k]], px), p);
+    dy[k] = mimg_fast(__dsub_rn(p.X[p.M + i3[k]], py), p);
+  }
+  int a = 0, b = 1;
+  double sx = __dsub_rn(dx[0], dx[1]), sy = __dsub_rn(dy[0], dy[1]);
+  double tt = -__ddiv_rn(dot2(dx[1], dy[1], sx, sy), dot2(sx, sy, sx, sy));
+  if (tt < 0.0 || tt > 1.0) {
+    // the pair of the three nearest that lies farthest apart (the first of equal ones)
+    const double s01 = sqdist(__dsub_rn(dx[0], dx[1]), __dsub_rn(dy[0], dy[1]));
+    const double s02 = sqdist(__dsub_rn(dx[0], dx[2]), __dsub_rn(dy[0], dy[2]));
+    const double s12 = sqdist(__dsub_rn(dx[1], dx[2]), __dsub_rn(dy[1], dy[2]));
+    if (s02 > s01 && s02 >= s12) {
+      b = 2;
+    } else if (s12 > s01 && s12 > s02) {
+      a = 1;
+      b = 2;
+    }
+    sx = __dsub_rn(dx[a], dx[b]);
+    sy = __dsub_rn(dy[a], dy[b]);
+    tt = -__ddiv_rn(dot2(dx[b], dy[b], sx, sy), dot2(sx, sy, sx, sy));
+    tt = fmin(1.0, fmax(0.0, tt));
+  }
+  const double ax_ = dx[b] + tt * sx, ay_ = dy[b] + tt * sy;  // x_A − x_p
+  const double lseg = hypot(sx, sy);
+  const double wa1 = hypot(ax_ - dx[b], ay_ - dy[b]) / lseg;  // weight of U_b(x_1)
+  const double wa2 = hypot(ax_ - dx[a], ay_ - dy[a]) / lseg;  // weight of U_b(x_2)
+  const double rA = hypot(ax_, ay_);
+  const int i1 = i3[a], i2 = i3[b];
+  const size_t cells = (size_t)n * n;
+  if (rA == 0.0) {
+    for (int c = 0; c < p.c; ++c)
+      p.out[c * cells + node] = p.Ub[(size_t)c * p.M + i1] * wa1 + p.Ub[(size_t)c * p.M + i2] * wa2;
+    return;
+  }
+  const double bx = ax_ - ax_ / rA * p.m2h, by = ay_ - ay_ / rA * p.m2h;  // x_B − x_p
+  const double gx = (px + bx - p.o0) / p.h, gy = (py + by - p.o1) / p.h;
+  const double fx = floor(gx), fy = floor(gy);
+  const double wx = gx - fx, wy = gy - fy;
+  const int jx0 = wrapn((long long)fx, n), jy0 = wrapn((long long)fy, n);
+  const int jx1 = jx0 + 1 == n ? 0 : jx0 + 1, jy1 = jy0 + 1 == n ? 0 : jy0 + 1;
+  const double rB = hypot(bx, by);
+  for (int c = 0; c < p.c; ++c) {
+    const double* F = p.u + c * cells;
+    const double uA = p.Ub[(size_t)c * p.M + i1] * wa1 + p.Ub[(size_t)c * p.M + i2] * wa2;
+    const double uB = (1 - wx) * (1 - wy) * F[(size_t)jy0 * n + jx0] + wx * (1 - wy) * F[(size_t)jy0 * n + jx1] +
+                      (1 - wx) * wy * F[(size_t)jy1 * n + jx0] + wx * wy * F[(size_t)jy1 * n + jx1];
+    p.out[c * cells + node] = (uA * rB + uB * rA) / p.m2h;
+  }
+}
+
+// Each warp takes 32 listed nodes at a time: for each in turn all lanes scan its candidate points
+// and merge; lane k keeps node k's three nearest. Then every lane finishes its own node, so the
+// FP64 arithmetic of the interpolation runs on all 32 lanes instead of one.
+__global__ void __launch_bounds__(kPPThreads, 2) k_near(NearParams p) {
   const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int warps = gridDim.x * (blockDim.x >> 5);
   const int count = *p.count;
   const int n = p.n;
-  for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < count; w += warps) {
-    const int node = p.list[w];
-    const int ix = node % n, iy = node / n;
-    const double px = __dadd_rn(p.o0, __dmul_rn(p.h, (double)ix));
-    const double py = __dadd_rn(p.o1, __dmul_rn(p.h, (double)iy));
-    Top3 t;
-    t.init();
-    const bool whole = 2 * p.K + 3 >= n;
-    if (whole) {
-      scan_range(p, 0, p.M, lane, px, py, t);
-    } else {
-      const int lo = iy - p.K - 2, hi = iy + p.K + 1;  // cell rows [lo, hi), wrapped
-      if (lo < 0) {
-        scan_range(p, p.cell_start[lo + n], p.cell_start[n], lane, px, py, t);
-        scan_range(p, p.cell_start[0], p.cell_start[hi], lane, px, py, t);
-      } else if (hi > n) {
-        scan_range(p, p.cell_start[lo], p.cell_start[n], lane, px, py, t);
-        scan_range(p, p.cell_start[0], p.cell_start[hi - n], lane, px, py, t);
-      } else {
-        scan_range(p, p.cell_start[lo], p.cell_start[hi], lane, px, py, t);
-      }
-    }
-    double d3[3];
-    int i3[3];
-    warp_top3(t, lane, d3, i3);
-    if (!(d3[0] < p.r1sq)) continue;  // not within m1·h of Γ (a point beyond the slab is farther still)
-    if (!whole && !(d3[2] < p.slabsq)) {
+  const bool whole = 2 * p.K + 3 >= n;
+  for (int base = gw * 32; base < count; base += warps * 32) {
+    const int nb = min(32, count - base);
+    int mine[3] = {-1, -1, -1};
+    for (int k = 0; k < nb; ++k) {
+      const int node = p.list[base + k];
+      const int ix = node % n, iy = node / n;
+      const double px = node_x(p, ix), py = node_y(p, iy);
+      Top3 t;
       t.init();
-      scan_range(p, 0, p.M, lane, px, py, t);
-      warp_top3(t, lane, d3, i3);
-    }
-    if (lane != 0) continue;
-    // offsets of the three nearest from x_p (x_p at the origin)
-    double dx[3], dy[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) offset(p, i3[k], px, py, dx[k], dy[k]);
-    int a = 0, b = 1;
-    double sx = __dsub_rn(dx[a], dx[b]), sy = __dsub_rn(dy[a], dy[b]);
-    double tt = -__ddiv_rn(dot2(dx[b], dy[b], sx, sy), dot2(sx, sy, sx, sy));
-    if (tt < 0.0 || tt > 1.0) {
-      // the pair of the three nearest that lies farthest apart
-      const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
-      double best = -1.0;
-      for (int q = 0; q < 3; ++q) {
-        const double ex = __dsub_rn(dx[pa[q]], dx[pb[q]]), ey = __dsub_rn(dy[pa[q]], dy[pb[q]]);
-        const double sep = sqdist(ex, ey);
-        if (sep > best) {
-          best = sep;
-          a = pa[q];
-          b = pb[q];
+      if (whole) {
+        scan_range<false>(p, 0, p.M, lane, px, py, t);
+      } else {
+        const int lo = iy - p.K - 2, hi = iy + p.K + 1;  // cell rows [lo, hi), wrapped
+        if (lo < 0) {
+          scan_range<true>(p, p.cell_start[lo + n], p.cell_start[n], lane, px, py, t);
+          scan_range<true>(p, p.cell_start[0], p.cell_start[hi], lane, px, py, t);
+        } else if (hi > n) {
+          scan_range<true>(p, p.cell_start[lo], p.cell_start[n], lane, px, py, t);
+          scan_range<true>(p, p.cell_start[0], p.cell_start[hi - n], lane, px, py, t);
+        } else {
+          scan_range<true>(p, p.cell_start[lo], p.cell_start[hi], lane, px, py, t);
         }
       }
-      sx = __dsub_rn(dx[a], dx[b]);
-      sy = __dsub_rn(dy[a], dy[b]);
-      tt = -__ddiv_rn(dot2(dx[b], dy[b], sx, sy), dot2(sx, sy, sx, sy));
-      tt = fmin(1.0, fmax(0.0, tt));
+      unsigned long long key[3];
+      int idx[3];
+      warp_top3(t, key, idx);
+      // not within m1·h of Γ (a point beyond the slab or the window is farther still)
+      if (!(key[0] < p.r1key)) continue;
+      if (!whole && !(key[2] < p.slabkey)) {
+        t.init();
+        scan_range<false>(p, 0, p.M, lane, px, py, t);
+        warp_top3(t, key, idx);
+      }
+      if (lane == k) {
+        mine[0] = idx[0];
+        mine[1] = idx[1];
+        mine[2] = idx[2];
+      }
     }
-    const double ax_ = dx[b] + tt * sx, ay_ = dy[b] + tt * sy;  // x_A − x_p
-    const double lseg = hypot(sx, sy);
-    const double wa1 = hypot(ax_ - dx[b], ay_ - dy[b]) / lseg;  // weight of U_b(x_1)
-    const double wa2 = hypot(ax_ - dx[a], ay_ - dy[a]) / lseg;  // weight of U_b(x_2)
-    const double rA = hypot(ax_, ay_);
-    const int i1 = i3[a], i2 = i3[b];
-    const size_t cells = (size_t)n * n;
-    if (rA == 0.0) {
-      for (int c = 0; c < p.c; ++c)
-        p.out[c * cells + node] = p.Ub[(size_t)c * p.M + i1] * wa1 + p.Ub[(size_t)c * p.M + i2] * wa2;
-      continue;
-    }
-    const double bx = ax_ - ax_ / rA * p.m2h, by = ay_ - ay_ / rA * p.m2h;  // x_B − x_p
-    const double gx = (px + bx - p.o0) / p.h, gy = (py + by - p.o1) / p.h;
-    const double fx = floor(gx), fy = floor(gy);
-    const double wx = gx - fx, wy = gy - fy;
-    const int jx0 = wrapn((long long)fx, n), jy0 = wrapn((long long)fy, n);
-    const int jx1 = jx0 + 1 == n ? 0 : jx0 + 1, jy1 = jy0 + 1 == n ? 0 : jy0 + 1;
-    const double rB = hypot(bx, by);
-    for (int c = 0; c < p.c; ++c) {
-      const double* F = p.u + c * cells;
-      const double uA = p.Ub[(size_t)c * p.M + i1] * wa1 + p.Ub[(size_t)c * p.M + i2] * wa2;
-      const double uB = (1 - wx) * (1 - wy) * F[(size_t)jy0 * n + jx0] + wx * (1 - wy) * F[(size_t)jy0 * n + jx1] +
-                        (1 - wx) * wy * F[(size_t)jy1 * n + jx0] + wx * wy * F[(size_t)jy1 * n + jx1];
-      p.out[c * cells + node] = (uA * rB + uB * rA) / p.m2h;
-    }
+    if (mine[0] >= 0) near_tail(p, p.list[base + lane], mine);
   }
 }
 
@@ -346,9 +390,14 @@ ibdl_status near_boundary_impl(Geometry* g, const double* Ub, const double* u, c
   p.o0 = g->origin[0];
   p.o1 = g->origin[1];
   const double r1 = m1 * g->h;
-  p.r1sq = r1 * r1;
+  const double r1sq = r1 * r1;
   const double slab = (p.K - 1) * g->h;
-  p.slabsq = slab * slab;
+  const double slabsq = slab * slab;
+  p.halfL = 0.5 * g->box;
+  std::memcpy(&p.r1key, &r1sq, 8);
+  std::memcpy(&p.slabkey, &slabsq, 8);
+  std::memcpy(&p.slabbits, &slab, 8);
+  std::memcpy(&p.halfbits, &p.halfL, 8);
   p.m2h = m2 * g->h;
   p.X = g->X64;
   p.perm = g->perm;
