@@ -147,6 +147,32 @@ __device__ __forceinline__ PointRanges band_points(const int* cell_start, int n,
 // Bodies take the work unit (row band / column group) and the problem's number of units, so
 // the same code serves one problem (unit = blockIdx.x) and a batch of problems (unit from a
 // (problem, unit) table).
+// One spread work item (point, stencil node): everything but the density, read from the geometry's
+// point tables, which no kernel writes (so a kernel may load them before its dependency wait).
+template <typename T>
+struct SpreadItem {
+  int lr, i, col;
+  T px, py, dpx, dpy, ws, nx, ny;
+};
+template <typename T>
+__device__ __forceinline__ SpreadItem<T> spread_item(const RowParams<T>& p, const PointRanges& pr, int t, int r0) {
+  const int n = p.n, M = p.M;
+  const int s = pr.at(t >> 4);
+  const int ay = (t >> 2) & 3, ax = t & 3;
+  SpreadItem<T> it;
+  it.lr = (((p.base[M + s] + ay) & (n - 1)) - r0) & (n - 1);
+  it.i = p.perm[s];
+  it.col = (p.base[s] + ax) & (n - 1);
+  it.px = p.phi[(0 * 4 + ax) * M + s];
+  it.py = p.phi[(1 * 4 + ay) * M + s];
+  it.dpx = p.dphi[(0 * 4 + ax) * M + s];
+  it.dpy = p.dphi[(1 * 4 + ay) * M + s];
+  it.ws = p.wscale[s];
+  it.nx = p.nrm[s];
+  it.ny = p.nrm[M + s];
+  return it;
+}
+
 template <typename T, int OP>
 __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int unit, int nunits,
                                                    unsigned char* smem_raw) {
@@ -164,6 +190,11 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   // prologue independent of the previous kernel, then wait for it (programmatic launch)
   for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
   load_twiddles(tws, p.tw, n);
+  // the points whose stencil meets the band, and this thread's first work item (16 per point)
+  const PointRanges pr = band_points(p.cell_start, n, r0, R);
+  const int nitems = p.grid_in ? 0 : pr.cnt * 16;
+  SpreadItem<T> it0 = {};
+  if ((int)threadIdx.x < nitems) it0 = spread_item(p, pr, threadIdx.x, r0);
   cudaGridDependencySynchronize();
   // Let the next kernel launch and run its prologue. Triggered only after this kernel's own
   // wait, so every kernel before the previous one has completed by then: a prologue overlaps
@@ -210,25 +241,18 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   }
 
   // one thread per (point, stencil node): 16 work items per point whose stencil meets the band
-  const PointRanges pr = band_points(p.cell_start, n, r0, R);
-  for (int t = threadIdx.x; t < (p.grid_in ? 0 : pr.cnt * 16); t += blockDim.x) {
-    const int s = pr.at(t >> 4);
-    const int ay = (t >> 2) & 3, ax = t & 3;
-    const int by = p.base[M + s];
-    const int row = (by + ay) & (n - 1);
-    const int lr = (row - r0) & (n - 1);
+  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
+    const SpreadItem<T> it = t == (int)threadIdx.x ? it0 : spread_item(p, pr, t, r0);
+    const int lr = it.lr;
     if (lr >= R) continue;
-    const int i = p.perm[s];
-    const int col = (p.base[s] + ax) & (n - 1);
-    const T px = p.phi[(0 * 4 + ax) * M + s], py = p.phi[(1 * 4 + ay) * M + s];
-    const T ws = p.wscale[s];
-    const T nx = p.nrm[s], ny = p.nrm[M + s];
-    const int e = (lr >> 1) * n + col;  // field 0; field f adds f·half·n
+    const int i = it.i;
+    const T px = it.px, py = it.py, ws = it.ws, nx = it.nx, ny = it.ny;
+    const int e = (lr >> 1) * n + it.col;  // field 0; field f adds f·half·n
     const int odd = lr & 1;
     const T pp = px * py;
     if (OP == OP_SCALAR_AN) {
       const T q = T(pin[i]) * ws;
-      const T ddx = p.dphi[(0 * 4 + ax) * M + s] * py, ddy = px * p.dphi[(1 * 4 + ay) * M + s];
+      const T ddx = it.dpx * py, ddy = px * it.dpy;
       // dipole source n·∇δ_h, plus ηδ_h for the completed method
       atomicAdd(acc + 2 * pidx(e) + odd, q * (nx * ddx + ny * ddy + p.eta_src * pp));
     } else if (OP == OP_SCALAR_SD) {
@@ -243,7 +267,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
       const T c3 = ws * (qx * ny + qy * nx);  // A_xy
       atomicAdd(acc + 2 * pidx(e) + odd, c0 * pp);
       if (OP == OP_STOKES_AN) {
-        const T ddx = p.dphi[(0 * 4 + ax) * M + s] * py, ddy = px * p.dphi[(1 * 4 + ay) * M + s];
+        const T ddx = it.dpx * py, ddy = px * it.dpy;
         // g_x = ∂_x S(A_xx) + ∂_y S(A_xy), g_y = ∂_x S(A_xy) + ∂_y S(A_yy); the completed method
         // adds (η/μ) S(Q) to the projected source
         const T ce = p.eta_src * ws * pp;
@@ -466,6 +490,35 @@ struct RowZLoad {
   }
 };
 
+// One gather work item (point, stencil row): the point-table values it needs
+template <typename T>
+struct GatherItem {
+  int lr, i, bx;
+  T py, dy, ws, nx, ny;
+  T px[4], dx[4];
+};
+template <typename T>
+__device__ __forceinline__ GatherItem<T> gather_item(const RowParams<T>& p, const PointRanges& pr, int t, int r0) {
+  const int n = p.n, M = p.M;
+  const int s = pr.at(t >> 2);
+  const int ay = t & 3;
+  GatherItem<T> it;
+  it.lr = (((p.base[M + s] + ay) & (n - 1)) - r0) & (n - 1);
+  it.i = p.perm[s];
+  it.bx = p.base[s];
+  it.py = p.phi[(1 * 4 + ay) * M + s];
+  it.dy = p.dphi[(1 * 4 + ay) * M + s];
+  it.ws = p.wscale[s];
+  it.nx = p.nrm[s];
+  it.ny = p.nrm[M + s];
+#pragma unroll
+  for (int ax = 0; ax < 4; ++ax) {
+    it.px[ax] = p.phi[(0 * 4 + ax) * M + s];
+    it.dx[ax] = p.dphi[(0 * 4 + ax) * M + s];
+  }
+  return it;
+}
+
 template <typename T, int OP, int GMODE>
 __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int unit, unsigned char* smem_raw) {
   constexpr int NOUT = Traits<OP>::NOUT;
@@ -476,6 +529,12 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   cplx<T>* bufB = bufA + padded((size_t)seqs * n);
   const int r0 = unit * R;
   load_twiddles(tws, p.tw, n);
+  // the points whose stencil meets the band and this thread's first work item (4 per point),
+  // loaded before the wait: the point tables are constant
+  const PointRanges pr = band_points(p.cell_start, n, r0, R);
+  const int nitems = GMODE == G_GRID ? 0 : pr.cnt * 4;
+  GatherItem<T> it0 = {};
+  if ((int)threadIdx.x < nitems) it0 = gather_item(p, pr, threadIdx.x, r0);
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
   if (p.stop && *p.stop) return;
@@ -501,17 +560,14 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   double* pout;
   resolve_io(p, pin, pout);
   // one thread per (point, stencil row in the band): the row's partial sum is added to Y
-  const PointRanges pr = band_points(p.cell_start, n, r0, R);
-  for (int t = threadIdx.x; t < pr.cnt * 4; t += blockDim.x) {
-    const int s = pr.at(t >> 2);
-    const int ay = t & 3;
-    const int row = (p.base[M + s] + ay) & (n - 1);
-    const int lr = (row - r0) & (n - 1);
+  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
+    const GatherItem<T> it = t == (int)threadIdx.x ? it0 : gather_item(p, pr, t, r0);
+    const int lr = it.lr;
     if (lr >= R) continue;
-    const int i = p.perm[s];
-    const int bx = p.base[s];
-    const T py = p.phi[(1 * 4 + ay) * M + s];
-    const T dy = (OP == OP_ADJ_AN || OP == OP_STOKES_T) ? p.dphi[(1 * 4 + ay) * M + s] : T(0);
+    const int i = it.i;
+    const int bx = it.bx;
+    const T py = it.py;
+    const T dy = (OP == OP_ADJ_AN || OP == OP_STOKES_T) ? it.dy : T(0);
     const int eb = (lr >> 1) * n, odd = lr & 1;
     if (OP == OP_STOKES_T) {
       // a_s = Σ v_s Φ, G_mk = Σ v_gm ∂_kΦ; out_l += (Δs/h²)[n_l a_s + Σ_k n_k (G_lk + G_kl)]
@@ -519,7 +575,7 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
 #pragma unroll
       for (int ax = 0; ax < 4; ++ax) {
         const int col = (bx + ax) & (n - 1);
-        const T px = p.phi[(0 * 4 + ax) * M + s], dx = p.dphi[(0 * 4 + ax) * M + s];
+        const T px = it.px[ax], dx = it.dx[ax];
         const T vs = u[2 * pidx(eb + col) + odd];
         const T vx = u[2 * pidx(eb + half * n + col) + odd];
         const T vy = u[2 * pidx(eb + 2 * half * n + col) + odd];
@@ -529,7 +585,7 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
         gyx += vy * dx * py;
         gyy += vy * px * dy;
       }
-      const double ws = double(p.wscale[s]), nx = double(p.nrm[s]), ny = double(p.nrm[M + s]);
+      const double ws = double(it.ws), nx = double(it.nx), ny = double(it.ny);
       const double cross = double(gxy) + double(gyx);
       atomicAdd(pout + i, ws * (nx * double(as) + 2.0 * nx * double(gxx) + ny * cross));
       atomicAdd(pout + M + i, ws * (ny * double(as) + nx * cross + 2.0 * ny * double(gyy)));
@@ -539,10 +595,10 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
 #pragma unroll
     for (int ax = 0; ax < 4; ++ax) {
       const int col = (bx + ax) & (n - 1);
-      const T px = p.phi[(0 * 4 + ax) * M + s];
+      const T px = it.px[ax];
       const T v0 = u[2 * pidx(eb + col) + odd];
       if (OP == OP_ADJ_AN) {
-        acc0 += v0 * p.dphi[(0 * 4 + ax) * M + s] * py;
+        acc0 += v0 * it.dx[ax] * py;
         acc1 += v0 * px * dy;
       } else {
         const T pp = px * py;
@@ -555,9 +611,9 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
       atomicAdd(pout + M + i, double(acc1));
     } else if (OP == OP_ADJ_AN || OP == OP_ADJ_SD) {
       // analytic: (S̃)* v = n · (kernel-gradient gather of v); spectral: −Σ_m n_m S*(∂_m v)
-      double val = double(p.nrm[s]) * double(acc0) + double(p.nrm[M + s]) * double(acc1);
+      double val = double(it.nx) * double(acc0) + double(it.ny) * double(acc1);
       if (OP == OP_ADJ_SD) val = -val;
-      if (p.trans) val *= double(p.wscale[s]);  // Δs/h^d · (S̃)* … for Aᵀ
+      if (p.trans) val *= double(it.ws);  // Δs/h^d · (S̃)* … for Aᵀ
       atomicAdd(pout + i, val);
     } else {
       atomicAdd(pout + i, double(acc0));
