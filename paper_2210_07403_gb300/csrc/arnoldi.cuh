@@ -47,6 +47,7 @@ struct GmresState {
   double rnorm;    // ‖r‖ from k_residual
   double cs[KMAX], sn[KMAX], g[KMAX + 1];
   double H[(KMAX + 1) * KMAX];  // column j at H[j·(m+1) + i]
+  double bnorm;                 // ‖U_b‖, recorded by the first cycle of a refinement solve
 };
 
 struct HostStatus {

@@ -73,9 +73,13 @@ __device__ void stage_upper(const GmresState* s, int k, int m, double* Rc, doubl
   for (int t = threadIdx.x; t < k; t += blockDim.x) g[t] = s->g[t];
 }
 
-// start a cycle: V_0 = r/‖r‖, g = ‖r‖ e_1
+// start a cycle: V_0 = r/‖r‖, g = ‖r‖ e_1. With rel > 0 the absolute target is formed here as
+// max(rel·‖r‖, floor_rel·‖U_b‖), ‖U_b‖ being ‖r‖ itself in the first cycle (first = 1, which records
+// it) and the recorded value afterwards: the refinement sweeps set their inner targets without a
+// host round trip.
 __global__ void __launch_bounds__(1024) k_gmres_start(GmresState* st, const double* __restrict__ r, double* V, int nd,
-                                                      double target, int kmax) {
+                                                      double target, int kmax, double rel = 0.0,
+                                                      double floor_rel = 0.0, int first = 0) {
   __shared__ double red[32];
   double s = 0;
   for (int i = threadIdx.x; i < nd; i += blockDim.x) s += r[i] * r[i];
@@ -84,6 +88,11 @@ __global__ void __launch_bounds__(1024) k_gmres_start(GmresState* st, const doub
   const double inv = (beta > 0 && !bad) ? 1.0 / beta : 0.0;
   for (int i = threadIdx.x; i < nd; i += blockDim.x) V[i] = r[i] * inv;
   if (threadIdx.x == 0) {
+    if (rel > 0.0) {
+      const double bn = first ? beta : st->bnorm;
+      if (first) st->bnorm = beta;
+      target = fmax(rel * beta, floor_rel * bn);
+    }
     st->beta = beta;
     st->target = target;
     st->res = beta;
@@ -322,8 +331,25 @@ static int cycle_unroll() {
   return v;
 }
 
+// kernels a graph-driven cycle launched: start, update, and 4 per iteration of each loop body run
+static int64_t cycle_launches(const HostStatus& fin) {
+  const int U = cycle_unroll();
+  const int bodies = fin.body_iters > 0 ? (fin.body_iters + U - 1) / U : 1;
+  return 2 + 4 * (int64_t)U * bodies;
+}
+
+// Relative inner target of a refinement sweep (rel > 0; see k_gmres_start), or none (rel = 0: the
+// absolute target is used).
+struct RelTarget {
+  double rel = 0.0, floor_rel = 0.0;
+  int first = 0;
+};
+
+// Launch the cycle's start kernel, graph and correction update. With sync the status is read back
+// and cr filled; without, the caller reads the state later (cycle_launches counts the kernels).
 static ibdl_status gmres_cycle_graph(Geometry* g, int prec, int op, const double* r0, double* x, double target,
-                                     int m, int budget, cudaStream_t s, CycleResult* cr) {
+                                     int m, int budget, cudaStream_t s, CycleResult* cr, const RelTarget& rt,
+                                     bool sync) {
   const int pi = 2 * op + (prec == IBDL_FP32 ? 1 : 0);
   if (!g->cycle_exec[pi] || g->cycle_m[pi] != m) {
     if (g->cycle_exec[pi]) cudaGraphExecDestroy(g->cycle_exec[pi]);
@@ -335,17 +361,16 @@ static ibdl_status gmres_cycle_graph(Geometry* g, int prec, int op, const double
   HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
   const int nd = geom_nd(g);
   const int steps = m < budget ? m : budget;
-  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, g->V, nd, target, steps);
+  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, g->V, nd, target, steps, rt.rel, rt.floor_rel, rt.first);
   IBDL_CUDA(cudaGetLastError());
   IBDL_CUDA(cudaGraphLaunch(g->cycle_exec[pi], s));
   k_gmres_update_par<<<(nd + 255) / 256, 256, 0, s>>>(st, g->V, x, nd, m);
   IBDL_CUDA(cudaGetLastError());
+  if (!sync) return IBDL_OK;
   IBDL_CUDA(cudaMemcpyAsync(&hs[0], st, sizeof(HostStatus), cudaMemcpyDeviceToHost, s));
   IBDL_CUDA(cudaStreamSynchronize(s));
   const HostStatus fin = hs[0];
-  const int U = cycle_unroll();
-  const int bodies = fin.body_iters > 0 ? (fin.body_iters + U - 1) / U : 1;
-  g->launches += 2 + 4 * (int64_t)U * bodies;
+  g->launches += cycle_launches(fin);
   cr->its = fin.k;
   cr->status = fin.status;
   cr->res = fin.res;
@@ -506,17 +531,18 @@ static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, int op, cudaG
 
 // One GMRES(m) cycle on right-hand side r0 from a zero correction, accumulating into x.
 static ibdl_status gmres_cycle(Geometry* g, int prec, int op, const double* r0, double* x, double target, int m,
-                               int budget, cudaStream_t s, CycleResult* cr) {
+                               int budget, cudaStream_t s, CycleResult* cr, const RelTarget& rt = RelTarget(),
+                               bool sync = true) {
   GmresState* st = reinterpret_cast<GmresState*>(g->gm);
   HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
   const int nd = geom_nd(g);
   double* V = g->V;
-  if (!g->timing) return gmres_cycle_graph(g, prec, op, r0, x, target, m, budget, s, cr);
+  if (!g->timing) return gmres_cycle_graph(g, prec, op, r0, x, target, m, budget, s, cr, rt, sync);
   // host-driven loop (used while stage timing records an event around every kernel)
   const int steps = m < budget ? m : budget;
   ArnoldiCfg acfg;
   IBDL_TRY(arnoldi_cfg(g, m, &acfg));
-  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, V, nd, target, steps);
+  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, V, nd, target, steps, rt.rel, rt.floor_rel, rt.first);
   g->launches += 1;
   IBDL_CUDA(cudaGetLastError());
   cudaEvent_t evs[2] = {g->ev, g->ev};
@@ -612,14 +638,16 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
   double* d = g->vec + 3 * (size_t)nd;
   IBDL_CUDA(cudaMemcpyAsync(b, Ub, sizeof(double) * nd, o->io_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   IBDL_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nd, s));
-  const double bnorm = host_norm(g, b, s);
+  // the refinement solve takes ‖U_b‖ from its first cycle; the plain solve needs it first
+  const bool mixed = o->precision == IBDL_MIXED;
+  const double bnorm = mixed ? 1.0 : host_norm(g, b, s);
   if (!std::isfinite(bnorm)) return fail(IBDL_ERR_NONFINITE, "U_b contains NaN or Inf");
   ibdl_solve_info inf = {};
   ibdl_status ret = IBDL_OK;
   const double target = o->rtol * bnorm;
-  if (bnorm == 0.0) {
+  if (!mixed && bnorm == 0.0) {
     inf.rel_residual = 0.0;
-  } else if (o->precision != IBDL_MIXED) {
+  } else if (!mixed) {
     // plain restarted GMRES(m) with FP64 (or FP32) applies
     int used = 0;
     bool done = false;
@@ -653,44 +681,53 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
     }
     inf.iterations = used;
   } else {
-    // iterative refinement: inner FP32-apply GMRES on the FP64 residual, FP64 update
-    int used = 0;
+    // iterative refinement. A sweep runs one inner GMRES cycle (at most m iterations) with FP32
+    // applications on the current FP64 residual from a zero correction d, to the inner target
+    // max(inner_rtol·‖r‖, ½·rtol·‖U_b‖) formed on the device; then x += d and r = b − A x in FP64.
+    // The host reads the cycle's status and ‖r‖ once per sweep; ‖U_b‖ comes from the first cycle.
+    // A cycle that ends at its restart length is followed by an FP64 residual like any sweep and
+    // does not count against max_refine (which bounds the sweeps whose inner solve converged).
+    GmresState* st = reinterpret_cast<GmresState*>(g->gm);
+    HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
+    int used = 0, refined = 0;
     const double* rhs = b;
-    double rn = bnorm;
-    for (int sweep = 0; sweep < o->max_refine; ++sweep) {
+    double bn = 0.0;
+    bool done = false;
+    for (int sweep = 0; !done; ++sweep) {
       IBDL_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * nd, s));
-      const double inner_target = o->inner_rtol * rn > target ? o->inner_rtol * rn : 0.5 * target;
-      // inner solve, with restarts, until the inner target or the budget
-      const double* irhs = rhs;
-      while (true) {
-        CycleResult cr;
-        IBDL_TRY(gmres_cycle(g, IBDL_FP32, op, irhs, d, inner_target, m, o->maxit - used, s, &cr));
-        used += cr.its;
-        inf.fp32_applies += cr.its;
-        if (cr.status == ST_NONFINITE) return fail(IBDL_ERR_NONFINITE, "non-finite value in the GMRES iteration");
-        if (cr.status != ST_RUNNING || used >= o->maxit) break;
-        // inner restart on the FP32 residual of the correction: r_in = rhs − A₃₂ d
-        GmresState* st = reinterpret_cast<GmresState*>(g->gm);
-        double* Ad = g->vec + 4 * (size_t)nd;
-        IBDL_TRY(apply_any(g, IBDL_FP32, d, Ad, s, nullptr, op));
-        inf.fp32_applies += 1;
-        k_residual<<<1, 1024, 0, s>>>(st, rhs, Ad, g->tmp_m, nd);
-        g->launches += 1;
-        IBDL_CUDA(cudaGetLastError());
-        irhs = g->tmp_m;
-        // a cycle correction accumulates into d through the same update kernel
-        (void)st;
-      }
+      RelTarget rt;
+      rt.rel = o->inner_rtol;
+      rt.floor_rel = 0.5 * o->rtol;
+      rt.first = sweep == 0;
+      CycleResult cr = {};
+      IBDL_TRY(gmres_cycle(g, IBDL_FP32, op, rhs, d, 0.0, m, o->maxit - used, s, &cr, rt, false));
       k_axpy<<<(nd + 255) / 256, 256, 0, s>>>(x, d, nd);
       g->launches += 1;
       IBDL_CUDA(cudaGetLastError());
-      inf.sweeps += 1;
-      IBDL_TRY(true_residual(g, op, b, x, r, d, s, &rn));
+      IBDL_TRY(apply_any(g, IBDL_FP64, x, d, s, nullptr, op));
+      k_residual<<<1, 1024, 0, s>>>(st, b, d, r, nd);
+      g->launches += 1;
+      IBDL_CUDA(cudaGetLastError());
+      IBDL_CUDA(cudaMemcpyAsync(&hs[0], st, sizeof(HostStatus), cudaMemcpyDeviceToHost, s));
+      IBDL_CUDA(cudaStreamSynchronize(s));
+      const HostStatus fin = hs[0];
+      if (!g->timing) g->launches += cycle_launches(fin);
+      if (sweep == 0) bn = fin.beta;
+      used += fin.k;
+      inf.fp32_applies += fin.k;
       inf.fp64_applies += 1;
-      inf.rel_residual = rn / bnorm;
-      if (!std::isfinite(rn)) return fail(IBDL_ERR_NONFINITE, "non-finite residual");
-      if (rn <= target) break;
-      if (used >= o->maxit) break;
+      inf.sweeps += 1;
+      if (fin.status == ST_NONFINITE || !std::isfinite(fin.rnorm))
+        return fail(IBDL_ERR_NONFINITE, sweep == 0 && !std::isfinite(bn) ? "U_b contains NaN or Inf"
+                                                                          : "non-finite value in the GMRES iteration");
+      const double rn = fin.rnorm;
+      if (bn == 0.0) {
+        inf.rel_residual = 0.0;
+        break;
+      }
+      inf.rel_residual = rn / bn;
+      if (fin.status != ST_RUNNING) ++refined;
+      done = rn <= o->rtol * bn || used >= o->maxit || refined >= o->max_refine;
       rhs = r;
     }
     inf.iterations = used;
