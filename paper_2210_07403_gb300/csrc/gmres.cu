@@ -314,6 +314,7 @@ struct CycleResult {
   int its;
   int status;
   double res;
+  double beta;  // ‖r0‖ of the cycle
 };
 
 static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, int op, cudaGraphExec_t* out);
@@ -374,6 +375,7 @@ static ibdl_status gmres_cycle_graph(Geometry* g, int prec, int op, const double
   cr->its = fin.k;
   cr->status = fin.status;
   cr->res = fin.res;
+  cr->beta = fin.beta;
   return IBDL_OK;
 }
 
@@ -592,6 +594,7 @@ static ibdl_status gmres_cycle(Geometry* g, int prec, int op, const double* r0, 
   cr->its = fin.k;
   cr->status = fin.status;
   cr->res = fin.res;
+  cr->beta = fin.beta;
   return IBDL_OK;
 }
 
@@ -611,20 +614,6 @@ static ibdl_status true_residual(Geometry* g, int op, const double* b, const dou
   return IBDL_OK;
 }
 
-static double host_norm(Geometry* g, const double* v_dev, cudaStream_t s) {
-  GmresState* st = reinterpret_cast<GmresState*>(g->gm);
-  const int nd = geom_nd(g);
-  // ‖v‖ via k_residual with Ax = 0 would need a zero vector; use b − 0 trick with the x slot cleared
-  double* zero = g->vec + 4 * (size_t)nd;
-  cudaMemsetAsync(zero, 0, sizeof(double) * nd, s);
-  double* scratch = g->tmp_m;
-  k_residual<<<1, 1024, 0, s>>>(st, v_dev, zero, scratch, nd);
-  g->launches += 1;
-  HostStatus fin;
-  cudaMemcpyAsync(&fin, st, sizeof(HostStatus), cudaMemcpyDeviceToHost, s);
-  cudaStreamSynchronize(s);
-  return fin.rnorm;
-}
 
 ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solve_opts* o, ibdl_solve_info* info,
                        cudaStream_t s, int op) {
@@ -638,23 +627,33 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
   double* d = g->vec + 3 * (size_t)nd;
   IBDL_CUDA(cudaMemcpyAsync(b, Ub, sizeof(double) * nd, o->io_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   IBDL_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nd, s));
-  // the refinement solve takes ‖U_b‖ from its first cycle; the plain solve needs it first
+  // ‖U_b‖ comes from the first cycle (its ‖r0‖), which also forms its own target rtol·‖U_b‖
   const bool mixed = o->precision == IBDL_MIXED;
-  const double bnorm = mixed ? 1.0 : host_norm(g, b, s);
-  if (!std::isfinite(bnorm)) return fail(IBDL_ERR_NONFINITE, "U_b contains NaN or Inf");
   ibdl_solve_info inf = {};
   ibdl_status ret = IBDL_OK;
-  const double target = o->rtol * bnorm;
-  if (!mixed && bnorm == 0.0) {
-    inf.rel_residual = 0.0;
-  } else if (!mixed) {
+  if (!mixed) {
     // plain restarted GMRES(m) with FP64 (or FP32) applies
     int used = 0;
     bool done = false;
     const double* rhs = b;
-    while (!done) {
+    double bnorm = 0.0, target = 0.0;
+    for (int cycle = 0; !done; ++cycle) {
       CycleResult cr;
-      IBDL_TRY(gmres_cycle(g, o->precision, op, rhs, x, target, m, o->maxit - used, s, &cr));
+      RelTarget rt;
+      if (cycle == 0) {
+        rt.rel = o->rtol;
+        rt.first = 1;
+      }
+      IBDL_TRY(gmres_cycle(g, o->precision, op, rhs, x, target, m, o->maxit - used, s, &cr, rt));
+      if (cycle == 0) {
+        bnorm = cr.beta;
+        target = o->rtol * bnorm;
+        if (!std::isfinite(bnorm)) return fail(IBDL_ERR_NONFINITE, "U_b contains NaN or Inf");
+        if (bnorm == 0.0) {
+          inf.rel_residual = 0.0;
+          break;
+        }
+      }
       used += cr.its;
       inf.sweeps += 1;
       if (o->precision == IBDL_FP32)
