@@ -321,13 +321,16 @@ static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, int op, cudaG
 
 // Iterations (application + Arnoldi step) per body of the captured while loop. Inside a body the
 // kernels follow each other with programmatic launch; between bodies the graph waits for the
-// body to finish and re-evaluates the loop condition. IBDL_UNROLL=u (1..8) overrides.
+// body to finish and re-evaluates the loop condition (about 6 µs at 512²), and the slots of the
+// last body after the stop still launch their kernels, which return at once (about 12 µs per
+// slot). 8 was the fastest of 1–16 on the 512² Stokes star (about 13 iterations per refinement
+// sweep, 22 per plain solve) and on the 64² circle (6). IBDL_UNROLL=u (1..16) overrides.
 static int cycle_unroll() {
   static int v = 0;
   if (!v) {
     const char* e = getenv("IBDL_UNROLL");
     const int u = e ? atoi(e) : 0;
-    v = (u >= 1 && u <= 8) ? u : 2;
+    v = (u >= 1 && u <= 16) ? u : 8;
   }
   return v;
 }
