@@ -267,9 +267,13 @@ __device__ void near_tail(const NearParams& p, int node, const int* i3) {
   }
 }
 
-// Each warp takes 32 listed nodes at a time: for each in turn all lanes scan its candidate points
-// and merge; lane k keeps node k's three nearest. Then every lane finishes its own node, so the
-// FP64 arithmetic of the interpolation runs on all 32 lanes instead of one.
+// Each warp takes kNearBatch listed nodes at a time: for each in turn all lanes scan its candidate
+// points and merge; lane k keeps node k's three nearest. Then lanes 0..kNearBatch−1 each finish
+// their own node, so the FP64 arithmetic of the interpolation runs on many lanes instead of one.
+// The warp's nodes are scanned one after another (a latency-bound chain), so the batch trades the
+// chain's length against the lanes the interpolation keeps busy; adjacent batches stay in one block
+// (they share slab points in L1).
+constexpr int kNearBatch = 16;
 __global__ void __launch_bounds__(kPPThreads, 2) k_near(NearParams p) {
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -277,8 +281,8 @@ __global__ void __launch_bounds__(kPPThreads, 2) k_near(NearParams p) {
   const int count = *p.count;
   const int n = p.n;
   const bool whole = 2 * p.K + 3 >= n;
-  for (int base = gw * 32; base < count; base += warps * 32) {
-    const int nb = min(32, count - base);
+  for (int base = gw * kNearBatch; base < count; base += warps * kNearBatch) {
+    const int nb = min(kNearBatch, count - base);
     int mine[3] = {-1, -1, -1};
     for (int k = 0; k < nb; ++k) {
       const int node = p.list[base + k];
