@@ -122,7 +122,9 @@ typedef struct {
   int maxit;            /* maximum total Krylov iterations (all restarts and sweeps)         */
   int precision;        /* IBDL_FP64 (plain), IBDL_FP32 or IBDL_MIXED (FP32 inner, FP64 outer) */
   double inner_rtol;    /* IBDL_MIXED: relative tolerance of each inner FP32-apply GMRES      */
-  int max_refine;       /* IBDL_MIXED: maximum refinement sweeps                             */
+  int max_refine;       /* IBDL_MIXED: maximum refinement sweeps whose inner cycle converged
+                           (a sweep whose inner cycle stops at the restart length is followed
+                           by an FP64 residual restart and does not count)                    */
   int io_on_host;       /* nonzero: U_b and Q are host pointers (copied inside the call)     */
 } ibdl_solve_opts;
 
@@ -173,8 +175,10 @@ ibdl_status ibdl_adjoint(ibdl_geometry* geom, int precision, const double* W, do
 
 /* Solve A Q = U_b by GMRES from a zero initial guess (Sec. 5.1.2 step 1 and Sec. 5.3.2 with
  * g̃ = 0). IBDL_FP64: restarted GMRES(m), FP64 everything. IBDL_MIXED: iterative refinement,
- * each sweep an inner GMRES with FP32 applications and FP64 Arnoldi/Hessenberg, then the FP64
- * residual U_b − A₆₄Q. U_b and Q are [c][M] FP64, device pointers unless opts->io_on_host.
+ * each sweep one inner GMRES cycle with FP32 applications and FP64 Arnoldi/Hessenberg to
+ * max(inner_rtol·‖r‖, ½·rtol·‖U_b‖), then Q += correction and the FP64 residual U_b − A₆₄Q; the
+ * host reads the status once per sweep (once per cycle in FP64). U_b and Q are [c][M] FP64,
+ * device pointers unless opts->io_on_host.
  * Returns IBDL_ERR_NOT_CONVERGED (Q = best iterate) when maxit is reached. `info` may be NULL. */
 ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const ibdl_solve_opts* opts,
                        ibdl_solve_info* info, void* stream);
