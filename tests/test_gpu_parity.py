@@ -213,6 +213,35 @@ def test_solve_restart_cycles():
     assert _rel(Q.cpu().numpy(), ref.x) < 1e-8
 
 
+def test_mixed_solve_short_restart():
+    """Mixed precision with a restart length shorter than an inner solve: a sweep whose inner cycle
+    stops at the restart length is followed by an FP64 residual restart and does not count against
+    max_refine, so the solve still reaches rtol (graph-driven and host-driven alike)."""
+    p = I.star_stokes(128, 200)
+    g = _geom(p)
+    ub = torch.from_numpy(p.Ub.reshape(-1)).cuda()
+    ref = O.solve(O.geometry_from_problem(p), p.Ub, 1e-12)
+    for timing in (False, True):
+        g.set_stage_timing(timing)
+        Q, info, _ = g.solve(ub, rtol=1e-10, precision="mixed", restart=5, maxit=400, max_refine=3)
+        assert info["rel_residual"] <= 1e-10
+        assert info["sweeps"] > 3
+        assert info["fp64_applies"] == info["sweeps"]
+        assert _rel(Q.cpu().numpy(), ref.x) < 1e-8
+    g.set_stage_timing(False)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_zero_rhs(precision):
+    """U_b = 0: Q = 0 with a zero relative residual and no error, the norm of U_b taken from the
+    first cycle on the device."""
+    p = I.circle_laplace(64, 100)
+    g = _geom(p)
+    Q, info, st = g.solve(torch.zeros(100, dtype=torch.float64, device="cuda"), rtol=1e-10, precision=precision)
+    assert st == 0 and info["rel_residual"] == 0.0
+    assert float(Q.abs().max()) == 0.0
+
+
 def test_solve_host_buffers():
     p = I.circle_laplace(64, 100)
     g = _geom(p)
