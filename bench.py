@@ -281,6 +281,7 @@ def extra_workloads(dev, flush, stream, K=5):
     out["stokes_star_probes_1024"] = differentiation_workload(dev, flush, stream, K)
     out["cylinder_array_drag_1024"] = cylinder_drag_workload(dev, flush, stream)
     out["postprocess"] = postprocess_workload(dev, flush, stream)
+    out["size_sweep"] = size_sweep_workload(dev, flush, stream)
     return out
 
 
@@ -429,6 +430,64 @@ def postprocess_workload(dev, flush, stream, K=5, Ns=(256, 512, 1024, 2048)):
     res["stokes_star_1024"] = {"indicator_us": round(t_ind * 1e3, 1), "near_boundary_us": round(t_nb * 1e3, 1),
                                "nodes_replaced": int((out != u).any(0).sum()), "m1": 12, "m2": 14}
     g.close()
+    return res
+
+
+def size_sweep_workload(dev, flush, stream, Ns=(512, 1024, 2048, 4096), napply=50):
+    """The 64² circle problem's geometry on finer grids (Δs ≈ 0.75h, the paper's spacing; its
+    studies run N = 2^6 … 2^14): scalar Laplace, analytic dipole, spectral symbol. Per N and
+    precision: applications/s from CUDA events over `napply` back-to-back applications after an
+    L2 flush, the algorithmic bytes 4N²w (+ boundary vectors) per application against the measured
+    HBM bandwidth, whether the grid fields fit in L2, and FP64 and mixed solve rates to 1e-9.
+    The shared-memory FFT holds whole columns: FP64 up to 2048², FP32 up to 4096²."""
+    import torch
+
+    import ibdl_inputs as I
+    from paper_2210_07403_gb300 import Geometry, IbdlError
+
+    hbm, _ = _peaks()
+    res = {"geometry": "circle R=0.25 at (0.5,0.5), ds ~ 0.75h, Re((z-z0)^3) data, scalar Laplace"}
+    for N in Ns:
+        M = I.points_for_spacing(2 * np.pi * 0.25, 1.0 / N, 0.75)
+        bd = I.circle(M)
+        ub = torch.from_numpy(I.harmonic_cubic(bd.X[0], bd.X[1])).to(dev)
+        g = Geometry(bd.X, bd.n, bd.w, N, delta="cos")
+        row = {"points": M}
+        for prec, w in (("fp32", 4), ("fp64", 8)):
+            try:
+                g.autotune(1 if prec == "fp64" else 2)
+                y = torch.empty_like(ub)
+                for _ in range(5):
+                    g.apply(ub, y, precision=prec)
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(napply):
+                    g.apply(ub, y, precision=prec)
+                e1.record(stream)
+                e1.synchronize()
+                us = e0.elapsed_time(e1) / napply * 1e3
+                alg = 4 * N * N * w + 3 * M * 8
+                row["apply_" + prec] = {"us": round(us, 2), "algorithmic_bytes": alg,
+                                        "achieved_GBps": round(alg / us / 1e3, 1),
+                                        "frac_of_measured_hbm": round(alg / us / 1e3 / hbm, 4) if hbm else None,
+                                        # one scalar field (the packed half spectrum) against the 129 MB L2
+                                        "l2_resident": N * N * w < 100e6}
+            except IbdlError as e:
+                row["apply_" + prec] = {"unsupported": str(e).split(":")[0]}
+        for prec in ("fp64", "mixed"):
+            try:
+                def run():
+                    return g.solve(ub, rtol=SOLVE_RTOL, precision=prec, inner_rtol=INNER_RTOL)
+                run()
+                t, (Q, info, st) = _event_ms(run, 3, flush, stream)
+                row["solve_" + prec] = {"solves_per_s": round(1e3 / t, 2), "iterations": info["iterations"],
+                                        "rel_residual": info["rel_residual"]}
+            except IbdlError as e:
+                row["solve_" + prec] = {"unsupported": str(e).split(":")[0]}
+        res[f"N={N}"] = row
+        g.close()
     return res
 
 
