@@ -17,6 +17,7 @@ for a reader to check against the paper by eye:
   GMRES       unrestarted, zero initial guess, Sec. 5.3.2
   χ, flags    indicator of the enclosed region, Sec. 5.3.5
   interp      near-boundary linear interpolation, Sec. 5.3.4
+  u_g         the grid response to a source g̃ (scalar L⁻¹g̃, Stokes −P̂ĝ/(μ|k|²+λ)), Sec. 5.1.2, Sec. 6.1.1
 
 Readings of points the paper leaves open are listed with each function; all are the same
 readings the CUDA path takes.
@@ -904,3 +905,57 @@ def near_boundary_interp(geom: Geometry, Ub, u, omega, m1: float = 6.0, m2: floa
                   + (1 - ax) * ay * F[(jy + 1) % N, jx % N] + ax * ay * F[(jy + 1) % N, (jx + 1) % N])
             out[comp, iy, ix] = (uA * rB + uB * rA) / (m2 * h)
     return out.reshape(np.shape(u))
+
+
+# ----------------------------------------------------------------------------------------
+# source term g̃ (Sec. 5.1.2 and Eq. "ibdl schur again"; Sec. 6.1.1, Eq. "ibdl stokes")
+# ----------------------------------------------------------------------------------------
+
+
+def source_field(geom: Geometry, g: np.ndarray) -> np.ndarray:
+    """u_g, the grid response to the source g̃ on C alone, with the geometry's symbols.
+
+    Scalar, L u + S̃Q = g̃: u = −L⁻¹S̃Q + L⁻¹g̃, so u_g = L⁻¹g̃, û_g = −ĝ/(|k|² + λ); for λ = 0 the
+    mean of g̃ is dropped (Δ₀⁻¹; reading: the mean enters only the completed method's constraint).
+    Stokes/Brinkman, L u − ∇p + μ∇·(SA) = g̃ with L = μΔ − λ and ∇·u = −S(Q·n): the g̃ part is the
+    divergence-free solution of L u − ∇p = g̃, û_g = −P̂ĝ/(μ|k|² + λ) with the projection P̂ of the
+    operator's own Stokes term; û_g(0) = 0 when λ = 0, −ĝ(0)/λ otherwise."""
+    grid = geom.grid
+    if geom.pde != "stokes":
+        return -minus_Linv(geom, np.asarray(g, dtype=np.float64).reshape(grid.shape))
+    d = grid.dim
+    G = [np.fft.fftn(np.asarray(g, dtype=np.float64).reshape((d,) + grid.shape)[l]) for l in range(d)]
+    lap, der = symbols(grid, geom.symbol)
+    nz = lap != 0
+    inv = np.zeros(grid.shape)
+    inv[nz] = 1.0 / lap[nz]
+    kdotg = sum(-1j * der[m] * G[m] for m in range(d))
+    den = geom.mu * lap + geom.lam
+    u = np.zeros((d,) + grid.shape)
+    for l in range(d):
+        PG = G[l] - (-1j * der[l]) * kdotg * inv
+        U = np.zeros_like(PG)
+        ok = den != 0
+        U[ok] = -PG[ok] / den[ok]
+        u[l] = np.real(np.fft.ifftn(U))
+    return u
+
+
+def forced_rhs(geom: Geometry, Ub: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Right-hand side of the Schur system with a source: U_b − S*u_g (Eq. "ibdl schur again":
+    −S*L⁻¹S̃Q + ½Q = U_b − S*L⁻¹g̃; the Stokes system alike). Completed method (Sec. 5.3.3,
+    Sec. 6.3.3): its c constraint rows are h^d Σ_g g̃_l, replacing whatever U_b held there."""
+    c, M = geom.ncomp, geom.M
+    ug = source_field(geom, g).reshape((c,) + geom.grid.shape)
+    rows = np.asarray(Ub, dtype=np.float64).reshape(-1)[: c * M] - np.concatenate(
+        [interp(geom, ug[l]) for l in range(c)])
+    if geom.naug:
+        gs = np.asarray(g, dtype=np.float64).reshape(c, -1)
+        return np.concatenate([rows, geom.grid.h ** geom.grid.dim * gs.sum(axis=1)])
+    return rows
+
+
+def forced_field(geom: Geometry, Q: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """The grid solution with a source: the field of Q plus u_g (Sec. 5.1.2 step 2)."""
+    u = grid_field(geom, Q)
+    return u + source_field(geom, g).reshape(u.shape)
