@@ -183,6 +183,23 @@ ibdl_status ibdl_adjoint(ibdl_geometry* geom, int precision, const double* W, do
 ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const ibdl_solve_opts* opts,
                        ibdl_solve_info* info, void* stream);
 
+/* A source term g̃ on the box (Sec. 5.1.2, Eq. "ibdl schur again"; Sec. 6.1.1, Eq. "ibdl stokes"):
+ * L u + S̃Q = g̃ (scalar) or L u − ∇p + μ∇·(SA) = g̃ with ∇·u + S(Q·n) = 0 (Stokes, Brinkman). Its
+ * response alone is u_g = L⁻¹g̃ (scalar) or û_g = −P̂ĝ/(μ|k|² + λ) (Stokes: the operator's own
+ * projection and symbols); for λ = 0 the mean of g̃ does not enter u_g. Then
+ *   ibdl_solve_forced:          A Q = U_b − S*u_g (U_b the Dirichlet data; for the Neumann problem
+ *                               −ibdl_single_layer(V_b)), solved as ibdl_solve does; for the
+ *                               completed method the c constraint rows become h^d Σ_g g̃_l (the
+ *                               last c entries of U_b are ignored);
+ *   ibdl_evaluate_field_forced: u_grid = the field of Q (ibdl_evaluate_field) + u_g.
+ * g_grid: device FP64 [c][n][n] (c = 1 scalar, 2 Stokes), 2-D only (IBDL_ERR_UNSUPPORTED in 3-D);
+ * NULL makes both calls their unforced counterparts. u_grid may not overlap g_grid. The geometry
+ * allocates its source-term workspace ((c + 3)·n² + c·M doubles) on the first forced call. */
+ibdl_status ibdl_solve_forced(ibdl_geometry* geom, const double* Ub, const double* g_grid, double* Q,
+                              const ibdl_solve_opts* opts, ibdl_solve_info* info, void* stream);
+ibdl_status ibdl_evaluate_field_forced(ibdl_geometry* geom, const double* Q, const double* g_grid, double* u_grid,
+                                       void* stream);
+
 /* Z = S*(−L⁻¹)(S V): the single-layer operator of the scalar method (the constraint method's
  * Schur complement up to sign, Sec. 2.2.3), with S the Δs-weighted spread and S* the
  * interpolation. It carries Neumann data into the right-hand side of the Neumann equation

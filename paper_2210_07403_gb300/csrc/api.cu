@@ -123,7 +123,8 @@ namespace ibdl {
 
 // shared argument checks and dispatch of ibdl_solve (op = A) and ibdl_solve_transpose (op = Aᵀ)
 static ibdl_status solve_entry(ibdl_geometry* geom, const double* b, double* x, const ibdl_solve_opts* opts,
-                               ibdl_solve_info* info, void* stream, int op, const char* bname, const char* xname) {
+                               ibdl_solve_info* info, void* stream, int op, const char* bname, const char* xname,
+                               const double* gsrc = nullptr) {
   set_error("");
   if (info) std::memset(info, 0, sizeof(*info));
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
@@ -149,7 +150,7 @@ static ibdl_status solve_entry(ibdl_geometry* geom, const double* b, double* x, 
     IBDL_TRY(check_device_ptr(x, xname));
   }
   const int64_t before = geom->g->launches;
-  ibdl_status st = solve_impl(geom->g, b, x, &o, info, static_cast<cudaStream_t>(stream), op);
+  ibdl_status st = solve_impl(geom->g, b, x, &o, info, static_cast<cudaStream_t>(stream), op, gsrc);
   if (info) info->kernel_launches = geom->g->launches - before;
   return st;
 }
@@ -182,6 +183,35 @@ extern "C" {
 ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const ibdl_solve_opts* opts,
                        ibdl_solve_info* info, void* stream) {
   return solve_entry(geom, Ub, Q, opts, info, stream, OPK_A, "U_b", "Q");
+}
+
+// the source term g̃: device FP64 [c][n][n], 2-D; NULL = none
+static ibdl_status check_source(ibdl_geometry* geom, const double* g_grid) {
+  if (!g_grid) return IBDL_OK;
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (geom->g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "a source term g_grid: 2-D only");
+  return check_device_ptr(g_grid, "g_grid");
+}
+
+ibdl_status ibdl_solve_forced(ibdl_geometry* geom, const double* Ub, const double* g_grid, double* Q,
+                              const ibdl_solve_opts* opts, ibdl_solve_info* info, void* stream) {
+  set_error("");
+  IBDL_TRY(check_source(geom, g_grid));
+  return solve_entry(geom, Ub, Q, opts, info, stream, OPK_A, "U_b", "Q", g_grid);
+}
+
+ibdl_status ibdl_evaluate_field_forced(ibdl_geometry* geom, const double* Q, const double* g_grid, double* u_grid,
+                                       void* stream) {
+  set_error("");
+  IBDL_TRY(check_source(geom, g_grid));
+  if (g_grid && u_grid) {
+    const Geometry* g = geom->g;
+    const size_t grid_bytes = sizeof(double) * g->ncomp * (size_t)g->n * g->n;
+    if (spans_overlap(u_grid, grid_bytes, g_grid, grid_bytes)) return fail(IBDL_ERR_INVALID_ARG, "u_grid and g_grid overlap");
+  }
+  IBDL_TRY(ibdl_evaluate_field(geom, Q, u_grid, stream));
+  if (!g_grid) return IBDL_OK;
+  return source_terms_2d(geom->g, g_grid, nullptr, u_grid, static_cast<cudaStream_t>(stream));
 }
 
 ibdl_status ibdl_solve_transpose(ibdl_geometry* geom, const double* G, double* lambda, const ibdl_solve_opts* opts,

@@ -752,10 +752,14 @@ static ibdl_status set_attrs_all() {
   return IBDL_OK;
 }
 
+// run_op mode bits: RUN_LAPLACE solves the plain Laplace problem (λ → 0) without the completed
+// method's terms; RUN_NO_AUG only drops those terms
+enum { RUN_LAPLACE = 1, RUN_NO_AUG = 2 };
+
 template <typename T, int OP>
 static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream_t s, const int* stop,
                           double* grid, const int* idx = nullptr, int vstride = 0, int trans = 0,
-                          const double* grid_in = nullptr, bool laplace = false) {
+                          const double* grid_in = nullptr, int mode = 0) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi];
   if (R == 0 || C == 0)
@@ -774,8 +778,8 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
     rp.eta_src = T(0);
   }
   ColParams<T> cp = col_params<T>(g, stop);
-  if (laplace) {  // the plain Laplace problem (indicator): no screening, no completed-method terms
-    cp.lam = T(0);
+  if (mode & RUN_LAPLACE) cp.lam = T(0);  // the plain Laplace problem (indicator)
+  if (mode & (RUN_LAPLACE | RUN_NO_AUG)) {  // no completed-method terms
     rp.aug = 0;
     rp.eta_src = T(0);
   }
@@ -854,8 +858,93 @@ ibdl_status transform_T_2d(Geometry* g, const double* psi, double* v, cudaStream
 // u = −Δ₀⁻¹S̃Q (mean-zero) with the geometry's δ_h, dipole spread and symbol, whatever its PDE
 ibdl_status laplace_field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s) {
   return g->dipole == IBDL_DIPOLE_ANALYTIC
-             ? run_op<double, OP_SCALAR_AN>(g, Q, g->tmp_m, s, nullptr, u, nullptr, 0, 0, nullptr, true)
-             : run_op<double, OP_SCALAR_SD>(g, Q, g->tmp_m, s, nullptr, u, nullptr, 0, 0, nullptr, true);
+             ? run_op<double, OP_SCALAR_AN>(g, Q, g->tmp_m, s, nullptr, u, nullptr, 0, 0, nullptr, RUN_LAPLACE)
+             : run_op<double, OP_SCALAR_SD>(g, Q, g->tmp_m, s, nullptr, u, nullptr, 0, 0, nullptr, RUN_LAPLACE);
+}
+
+// grid-input fields of the source term for the forward op's Fourier stage: scalar −g̃ (the op's
+// symbol is that of −L⁻¹); Stokes (s, f_x, f_y) = (0, −g̃_x/μ, −g̃_y/μ) in the slots of the dipole
+// source ∇·(SA), whose velocity P̂f̂/|k|² (Brinkman μP̂f̂/(μ|k|² + λ)) is then −P̂ĝ/(μ|k|² + λ)
+__global__ void k_source_fields(const double* __restrict__ gsrc, int stokes, double inv_mu, int64_t cells,
+                                double* __restrict__ f) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x) {
+    if (stokes) {
+      f[i] = 0.0;
+      f[cells + i] = -gsrc[i] * inv_mu;
+      f[2 * cells + i] = -gsrc[cells + i] * inv_mu;
+    } else {
+      f[i] = -gsrc[i];
+    }
+  }
+}
+
+// rows[i] −= w[i] over the c·M boundary rows; with sums (completed method) rows[c·M + l] = hd·sums[l]
+__global__ void k_source_rows(double* __restrict__ rows, const double* __restrict__ w, int cm, int naug,
+                              const double* __restrict__ sums, double hd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cm) rows[i] -= w[i];
+  if (sums && i < naug) rows[cm + i] = hd * sums[i];
+}
+
+// sums[l] = Σ_g g̃_l, one block per component (fixed order, deterministic)
+__global__ void __launch_bounds__(1024) k_grid_sums(const double* __restrict__ gsrc, int64_t cells, double* sums) {
+  __shared__ double red[32];
+  const double* f = gsrc + (int64_t)blockIdx.x * cells;
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < cells; i += blockDim.x) a += f[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) sums[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_add(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+ibdl_status source_terms_2d(Geometry* g, const double* gsrc, double* rhs, double* grid, cudaStream_t s) {
+  const bool stokes = g->pde == IBDL_PDE_STOKES;
+  const int nf = stokes ? 3 : 1, c = g->ncomp;
+  const int64_t cells = (int64_t)g->n * g->n;
+  const int cm = c * (int)g->M;
+  // fields [nf][n][n] | u_g [c][n][n] | S*u_g [c·M] | sums [c]
+  if (!g->src_buf)
+    IBDL_CUDA(cudaMalloc((void**)&g->src_buf, sizeof(double) * ((nf + c) * cells + cm + c)));
+  double* f = g->src_buf;
+  double* ug = f + nf * cells;
+  double* w = ug + c * cells;
+  double* sums = w + cm;
+  const int blocks = (int)std::min<int64_t>((cells + 255) / 256, 152 * 8);
+  k_source_fields<<<blocks, 256, 0, s>>>(gsrc, stokes ? 1 : 0, 1.0 / g->mu, cells, f);
+  IBDL_CUDA(cudaGetLastError());
+  g->launches += 1;
+  if (rhs) {
+    IBDL_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * cm, s));
+    IBDL_TRY((stokes ? run_op<double, OP_STOKES_AN>(g, nullptr, w, s, nullptr, nullptr, nullptr, 0, 0, f, RUN_NO_AUG)
+                     : run_op<double, OP_SCALAR_AN>(g, nullptr, w, s, nullptr, nullptr, nullptr, 0, 0, f, RUN_NO_AUG)));
+    if (g->naug) {
+      k_grid_sums<<<c, 1024, 0, s>>>(gsrc, cells, sums);
+      g->launches += 1;
+    }
+    k_source_rows<<<(cm + 255) / 256, 256, 0, s>>>(rhs, w, cm, g->naug, g->naug ? sums : nullptr, g->h * g->h);
+    IBDL_CUDA(cudaGetLastError());
+    g->launches += 1;
+  }
+  if (grid) {
+    IBDL_TRY((stokes ? run_op<double, OP_STOKES_AN>(g, nullptr, w, s, nullptr, ug, nullptr, 0, 0, f, RUN_NO_AUG)
+                     : run_op<double, OP_SCALAR_AN>(g, nullptr, w, s, nullptr, ug, nullptr, 0, 0, f, RUN_NO_AUG)));
+    k_add<<<blocks, 256, 0, s>>>(grid, ug, c * cells);
+    IBDL_CUDA(cudaGetLastError());
+    g->launches += 1;
+  }
+  return IBDL_OK;
 }
 
 ibdl_status field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s) {

@@ -177,7 +177,7 @@ static void free_geometry(Geometry* g) {
   void* ptrs[] = {g->perm, g->base, g->cell_start, g->t64.phi, g->t64.dphi, g->t64.wscale, g->t64.nrm,
                   g->t32.phi, g->t32.dphi, g->t32.wscale, g->t32.nrm, g->spec, g->tw64, g->tw32,
                   g->lap64, g->der64, g->lap32, g->der32, g->ubuf, g->tmp_m, g->V, g->gm, g->vec,
-                  g->ddphi64, g->vjp_buf, g->X64, g->pp_buf};
+                  g->ddphi64, g->vjp_buf, g->X64, g->pp_buf, g->src_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 4; ++i)

@@ -619,7 +619,7 @@ static ibdl_status true_residual(Geometry* g, int op, const double* b, const dou
 
 
 ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solve_opts* o, ibdl_solve_info* info,
-                       cudaStream_t s, int op) {
+                       cudaStream_t s, int op, const double* gsrc) {
   const auto t0 = std::chrono::steady_clock::now();
   const int m = o->restart;
   IBDL_TRY(ensure_workspace(g, m));
@@ -630,6 +630,8 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
   double* d = g->vec + 3 * (size_t)nd;
   IBDL_CUDA(cudaMemcpyAsync(b, Ub, sizeof(double) * nd, o->io_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   IBDL_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nd, s));
+  // a source term: b = U_b − S*u_g (and the completed method's constraint rows from g̃)
+  if (gsrc) IBDL_TRY(source_terms_2d(g, gsrc, b, nullptr, s));
   // ‖U_b‖ comes from the first cycle (its ‖r0‖), which also forms its own target rtol·‖U_b‖
   const bool mixed = o->precision == IBDL_MIXED;
   ibdl_solve_info inf = {};

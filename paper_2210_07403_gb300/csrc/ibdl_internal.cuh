@@ -114,6 +114,7 @@ struct Geometry {
   double* ubuf;    // evaluate_field / adjoint helpers: [c][n^dim] FP64
   double* tmp_m;   // [c*M] scratch boundary vector
   double* vjp_buf; // boundary derivatives: grid fields u and v, allocated on first use
+  double* src_buf; // source term g̃: grid-input fields, u_g and S*u_g, allocated on first use
 
   // launch plan (2-D and 3-D)
   int rows_per_cta[2];   // band height R for the row kernels, per precision (0 = fp64, 1 = fp32)
@@ -211,12 +212,15 @@ ibdl_status adjoint_3d(Geometry* g, int precision, const double* W, double* Z, c
 ibdl_status plan_2d(Geometry* g);
 ibdl_status plan_3d(Geometry* g);
 ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solve_opts* o,
-                       ibdl_solve_info* info, cudaStream_t s, int op = OPK_A);
+                       ibdl_solve_info* info, cudaStream_t s, int op = OPK_A, const double* gsrc = nullptr);
 // grid fields u = K[sources(Q)] and v = Kᵀ(Σ_j λ_j Φ(x − X_j)) (K = −L⁻¹ scalar, the Stokes
 // multiplier otherwise), then the boundary derivatives; Kᵀ of a given grid field (2-D)
 ibdl_status transform_T_2d(Geometry* g, const double* psi, double* v, cudaStream_t s);
 ibdl_status single_layer_2d(Geometry* g, int precision, const double* V, double* Z, cudaStream_t s);
 ibdl_status field_pair_2d(Geometry* g, const double* Q, const double* lam, double* u, double* v, cudaStream_t s);
+// the source term g̃ (2-D): rhs[0..c·M) −= S*u_g and, for the completed method, rhs[c·M + l] =
+// h^d Σ g̃_l (rhs may be NULL); grid[c][n][n] += u_g (grid may be NULL)
+ibdl_status source_terms_2d(Geometry* g, const double* gsrc, double* rhs, double* grid, cudaStream_t s);
 ibdl_status laplace_field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s);
 ibdl_status laplace_field_3d(Geometry* g, const double* Q, double* u, cudaStream_t s);
 ibdl_status indicator_impl(Geometry* g, double* chi, uint8_t* flags, cudaStream_t s);

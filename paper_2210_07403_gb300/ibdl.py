@@ -78,6 +78,9 @@ SIGNATURES = {
     "ibdl_solve": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(ibdl_solve_opts),
                            POINTER(ibdl_solve_info), c_void_p]),
     "ibdl_evaluate_field": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ibdl_solve_forced": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(ibdl_solve_opts),
+                                  POINTER(ibdl_solve_info), c_void_p]),
+    "ibdl_evaluate_field_forced": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ibdl_default_solve_opts": (None, [POINTER(ibdl_solve_opts)]),
     "ibdl_geometry_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int64)]),
     "ibdl_apply_noalloc": (c_int, [POINTER(ibdl_geometry_desc), c_int, c_void_p, c_void_p, c_void_p]),
@@ -170,6 +173,18 @@ def ibdl_solve(geom, Ub: int, Q: int, opts: ibdl_solve_opts, info: ibdl_solve_in
                check: bool = True) -> int:
     st = load().ibdl_solve(geom, c_void_p(Ub), c_void_p(Q), byref(opts), byref(info), c_void_p(stream))
     return _check(st) if check else st
+
+
+def ibdl_solve_forced(geom, Ub: int, g_grid: int, Q: int, opts: ibdl_solve_opts, info: ibdl_solve_info,
+                      stream: int = 0, check: bool = True) -> int:
+    st = load().ibdl_solve_forced(geom, c_void_p(Ub), c_void_p(g_grid or None), c_void_p(Q), byref(opts),
+                                  byref(info), c_void_p(stream))
+    return _check(st) if check else st
+
+
+def ibdl_evaluate_field_forced(geom, Q: int, g_grid: int, u_grid: int, stream: int = 0) -> int:
+    return _check(load().ibdl_evaluate_field_forced(geom, c_void_p(Q), c_void_p(g_grid or None), c_void_p(u_grid),
+                                                    c_void_p(stream)))
 
 
 def ibdl_apply_transpose(geom, precision: int, G: int, Z: int, stream: int = 0) -> int:
@@ -453,21 +468,43 @@ class Geometry:
         ibdl_adjoint(self._h, _PREC[precision], W.data_ptr(), Z.data_ptr(), _stream_handle(stream))
         return Z
 
-    def evaluate_field(self, Q, stream=None):
+    def _source(self, g):
+        """The source term g̃ as a contiguous CUDA float64 tensor of the field's shape."""
+        t = self._torch
+        if not isinstance(g, t.Tensor):
+            g = t.from_numpy(np.ascontiguousarray(np.asarray(g, dtype=np.float64)))
+        g = g.detach().to(device="cuda", dtype=t.float64).contiguous()
+        assert g.numel() == self.ncomp * self.n ** self.dim
+        return g
+
+    def evaluate_field(self, Q, stream=None, g=None):
+        """The grid solution of Q (scalar u or Stokes velocity); with a source g̃ ([c][n][n]) the
+        response u_g to it is added (Sec. 5.1.2)."""
         Q = self._vec(Q)
         shape = (self.n,) * self.dim
         if self.pde == "stokes":
             shape = (self.dim,) + shape
         u = self._torch.empty(shape, dtype=self._torch.float64, device=Q.device)
-        ibdl_evaluate_field(self._h, Q.data_ptr(), u.data_ptr(), _stream_handle(stream))
+        if g is None:
+            ibdl_evaluate_field(self._h, Q.data_ptr(), u.data_ptr(), _stream_handle(stream))
+        else:
+            g = self._source(g)
+            ibdl_evaluate_field_forced(self._h, Q.data_ptr(), g.data_ptr(), u.data_ptr(), _stream_handle(stream))
         return u
 
     def solve(self, Ub, rtol: float = 1e-8, precision: str = "fp64", restart: int = 50, maxit: int = 200,
-              inner_rtol: float = 1e-4, max_refine: int = 6, Q=None, stream=None, check: bool = True):
-        """Solve A Q = U_b. U_b on the device (torch float64) or a host numpy array / CPU tensor
-        (then the copies happen inside the call, io_on_host). Returns (Q, info dict, status)."""
-        return self._solve(ibdl_solve, Ub, rtol, precision, restart, maxit, inner_rtol, max_refine, Q, stream,
-                           check)
+              inner_rtol: float = 1e-4, max_refine: int = 6, Q=None, stream=None, check: bool = True, g=None):
+        """Solve A Q = U_b (with a source g̃, [c][n][n]: A Q = U_b − S*u_g). U_b on the device (torch
+        float64) or a host numpy array / CPU tensor (then the copies happen inside the call,
+        io_on_host); g̃ on the device. Returns (Q, info dict, status)."""
+        if g is None:
+            entry = ibdl_solve
+        else:
+            gs = self._source(g)
+
+            def entry(h, ub, q, o, info, stream, check=True):
+                return ibdl_solve_forced(h, ub, gs.data_ptr(), q, o, info, stream, check=check)
+        return self._solve(entry, Ub, rtol, precision, restart, maxit, inner_rtol, max_refine, Q, stream, check)
 
     def solve_transpose(self, G, rtol: float = 1e-8, precision: str = "fp64", restart: int = 50,
                         maxit: int = 200, inner_rtol: float = 1e-4, max_refine: int = 6, lam=None, stream=None,
