@@ -18,6 +18,7 @@ for a reader to check against the paper by eye:
   χ, flags    indicator of the enclosed region, Sec. 5.3.5
   interp      near-boundary linear interpolation, Sec. 5.3.4
   u_g         the grid response to a source g̃ (scalar L⁻¹g̃, Stokes −P̂ĝ/(μ|k|²+λ)), Sec. 5.1.2, Sec. 6.1.1
+  n, Δs       normals and weights estimated from the points, Sec. 5.3.1
 
 Readings of points the paper leaves open are listed with each function; all are the same
 readings the CUDA path takes.
@@ -959,3 +960,26 @@ def forced_field(geom: Geometry, Q: np.ndarray, g: np.ndarray) -> np.ndarray:
     """The grid solution with a source: the field of Q plus u_g (Sec. 5.1.2 step 2)."""
     u = grid_field(geom, Q)
     return u + source_field(geom, g).reshape(u.shape)
+
+
+# ----------------------------------------------------------------------------------------
+# normals and weights estimated from the points (Sec. 5.3.1)
+# ----------------------------------------------------------------------------------------
+
+
+def estimate_normals(X: np.ndarray, box: float) -> np.ndarray:
+    """Unit normals of one closed 2-D curve from its ordered points, Sec. 5.3.1 (Eq. "normal vector
+    approximations"): n_i = (Y_{i+1} − Y_{i−1}, −(X_{i+1} − X_{i−1}))/‖X_{i+1} − X_{i−1}‖, differences by
+    minimum image. The normal points to the right of the direction of travel: outward for a
+    counter-clockwise curve (interior domain), inward for a clockwise one (exterior domain)."""
+    X = np.asarray(X, dtype=np.float64)
+    d = min_image(np.roll(X, -1, axis=1) - np.roll(X, 1, axis=1), box)
+    n = np.stack([d[1], -d[0]])
+    return n / np.hypot(d[0], d[1])
+
+
+def estimate_weights(X: np.ndarray, box: float) -> np.ndarray:
+    """Δs_i ≈ ‖X_{i+1} − X_i‖ (Sec. 5.3.1), minimum image, one closed curve."""
+    X = np.asarray(X, dtype=np.float64)
+    d = min_image(np.roll(X, -1, axis=1) - X, box)
+    return np.hypot(d[0], d[1])

@@ -1113,3 +1113,42 @@ def test_forced_rhs_completed_constraint_rows():
     rhs = O.forced_rhs(geom, np.concatenate([p.Ub.reshape(-1), [9.0, 9.0]]), g)
     assert np.abs(rhs[: 2 * geom.M] - p.Ub.reshape(-1)).max() < 1e-12
     assert np.allclose(rhs[2 * geom.M:], p.meta["rhs_aug"], atol=1e-12)
+
+
+# ----------------------------------------------------------------------------------------
+# normals and weights from the points (Sec. 5.3.1)
+# ----------------------------------------------------------------------------------------
+
+
+def test_estimated_normals_and_weights_on_a_circle():
+    """On an equispaced circle the centred chord is perpendicular to the radius, so the estimated
+    normal is the exact radial normal; the weight is the chord 2R sin(π/M). A clockwise ordering
+    gives the inward normals, and a circle crossing the periodic edge gives the same values."""
+    M, R = 37, 0.25
+    bd = I.circle(M, R)
+    n = O.estimate_normals(bd.X, 1.0)
+    assert np.abs(n - bd.n).max() < 1e-14
+    assert np.abs(O.estimate_weights(bd.X, 1.0) - 2 * R * np.sin(np.pi / M)).max() < 1e-15
+    assert np.abs(O.estimate_normals(bd.X[:, ::-1], 1.0) + bd.n[:, ::-1]).max() < 1e-14
+    wrapped = np.mod(bd.X + np.array([[0.4], [0.45]]), 1.0)  # centre (0.9, 0.95): crosses both edges
+    assert np.abs(O.estimate_normals(wrapped, 1.0) - bd.n).max() < 1e-13
+    assert np.abs(O.estimate_weights(wrapped, 1.0) - 2 * R * np.sin(np.pi / M)).max() < 1e-13
+
+
+def test_estimated_geometry_keeps_first_order_accuracy():
+    """The paper's claim for the estimates: the solution stays first-order accurate. Star curve
+    (normals not radial), harmonic data, estimated normals and chord weights."""
+    errs = []
+    for N in (64, 128, 256):
+        M = I.points_for_spacing(1.9124, 1 / N, 1.0)
+        bd = I.star(M)
+        n, w = O.estimate_normals(bd.X, 1.0), O.estimate_weights(bd.X, 1.0)
+        assert np.abs(np.sum(n * bd.n, axis=0) - 1).max() < 0.02  # close to the exact normals
+        geom = O.Geometry(O.Grid(2, N), bd.X, n, w, "cos", "analytic", "spectral", "scalar", 0.0)
+        ub = I.harmonic_cubic(bd.X[0], bd.X[1])
+        Q = O.solve(geom, ub, 1e-12, maxit=80).x
+        x, y = geom.grid.coords()
+        u = O.field_scalar(geom, Q)
+        r = np.hypot(x - 0.5, y - 0.5)
+        errs.append(np.abs(u - I.harmonic_cubic(x, y))[r < 0.12].max())
+    assert O.fitted_order([1 / 64, 1 / 128, 1 / 256], errs) > 0.8
