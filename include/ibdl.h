@@ -90,8 +90,13 @@ typedef struct {
   double origin[3];     /* lower corner of the box (unused entries ignored)                 */
   int64_t n_points;     /* M ≥ 1                                                           */
   const double* X;      /* [dim][M] boundary points                                         */
-  const double* normals;/* [dim][M] unit normals pointing out of Ω                          */
-  const double* weights;/* [M] quadrature weights Δs_i (arclength, Sec. 2.2.2)               */
+  const double* normals;/* [dim][M] unit normals pointing out of Ω; NULL (2-D): estimated      */
+  const double* weights;/* [M] quadrature weights Δs_i (arclength, Sec. 2.2.2); NULL (2-D):  */
+                        /* estimated. Estimates (Sec. 5.3.1) treat the points as one closed
+                           curve in order: n_i ∝ (Y_{i+1} − Y_{i−1}, −(X_{i+1} − X_{i−1})), to the
+                           right of the direction of travel (order an interior boundary
+                           counter-clockwise, an exterior one clockwise), Δs_i = ‖X_{i+1} − X_i‖,
+                           differences by minimum image                                      */
   int pde;              /* IBDL_PDE_*                                                       */
   double lambda;        /* λ ≥ 0: L = Δ − λ (scalar); L = μΔ − λ (Stokes λ = 0, Brinkman λ > 0) */
   double mu;            /* viscosity μ > 0 for IBDL_PDE_STOKES (cancels from A when λ = 0)   */

@@ -164,6 +164,30 @@ ibdl_status fill_geometry_tables(Geometry* g, const double* dX, const double* dN
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// minimum-image difference on a periodic box of side L
+static double min_image(double d, double L) { return d - L * std::nearbyint(d / L); }
+
+// Normals and weights of one closed 2-D curve from its ordered points (Sec. 5.3.1, Eq. "normal
+// vector approximations"): n_i = (Y_{i+1} − Y_{i−1}, −(X_{i+1} − X_{i−1}))/‖X_{i+1} − X_{i−1}‖, pointing to
+// the right of the direction of travel (outward for a counter-clockwise curve), and
+// Δs_i = ‖X_{i+1} − X_i‖; X is [2][M], differences by minimum image. A degenerate chord leaves a
+// non-unit normal or a zero weight, which the validation that follows rejects.
+static void estimate_normals(const double* X, int M, double L, double* n) {
+  for (int i = 0; i < M; ++i) {
+    const int a = i + 1 == M ? 0 : i + 1, b = i == 0 ? M - 1 : i - 1;
+    const double dx = min_image(X[a] - X[b], L), dy = min_image(X[M + a] - X[M + b], L);
+    const double len = std::hypot(dx, dy);
+    n[i] = dy / len;
+    n[M + i] = -dx / len;
+  }
+}
+static void estimate_weights(const double* X, int M, double L, double* w) {
+  for (int i = 0; i < M; ++i) {
+    const int a = i + 1 == M ? 0 : i + 1;
+    w[i] = std::hypot(min_image(X[a] - X[i], L), min_image(X[M + a] - X[M + i], L));
+  }
+}
+
 template <typename P>
 static ibdl_status dalloc(P** p, size_t bytes) {
   *p = nullptr;
@@ -261,7 +285,9 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
   for (int j = 0; j < d->dim; ++j)
     if (!std::isfinite(d->origin[j])) return fail(IBDL_ERR_INVALID_ARG, "origin must be finite");
   if (d->n_points < 1 || d->n_points > (int64_t)1 << 28) return fail(IBDL_ERR_INVALID_ARG, "n_points must be in [1, 2^28]");
-  if (!d->X || !d->normals || !d->weights) return fail(IBDL_ERR_INVALID_ARG, "X, normals and weights are required");
+  if (!d->X) return fail(IBDL_ERR_INVALID_ARG, "X is required");
+  if ((!d->normals || !d->weights) && (d->dim != 2 || d->n_points < 3))
+    return fail(IBDL_ERR_INVALID_ARG, "normals and weights are required in 3-D and for fewer than three points");
   if (d->pde != IBDL_PDE_SCALAR && d->pde != IBDL_PDE_STOKES) return fail(IBDL_ERR_INVALID_ARG, "unknown pde");
   if (d->pde == IBDL_PDE_STOKES && d->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "Stokes is implemented in 2-D only");
   if (!(d->lambda >= 0) || !std::isfinite(d->lambda)) return fail(IBDL_ERR_INVALID_ARG, "lambda must be finite and >= 0");
@@ -285,8 +311,14 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
   std::vector<double> hX((size_t)dim * M), hN((size_t)dim * M), hW(M);
   const cudaMemcpyKind kind = d->inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
   IBDL_CUDA(cudaMemcpy(hX.data(), d->X, hX.size() * sizeof(double), kind));
-  IBDL_CUDA(cudaMemcpy(hN.data(), d->normals, hN.size() * sizeof(double), kind));
-  IBDL_CUDA(cudaMemcpy(hW.data(), d->weights, hW.size() * sizeof(double), kind));
+  if (d->normals)
+    IBDL_CUDA(cudaMemcpy(hN.data(), d->normals, hN.size() * sizeof(double), kind));
+  else
+    estimate_normals(hX.data(), M, d->box, hN.data());
+  if (d->weights)
+    IBDL_CUDA(cudaMemcpy(hW.data(), d->weights, hW.size() * sizeof(double), kind));
+  else
+    estimate_weights(hX.data(), M, d->box, hW.data());
   for (int i = 0; i < M; ++i) {
     double nn = 0;
     for (int j = 0; j < dim; ++j) {

@@ -400,20 +400,23 @@ class Geometry:
         import torch
 
         self._torch = torch
-        on_device = all(isinstance(a, torch.Tensor) and a.is_cuda for a in (X, normals, weights))
+        # normals or weights None (2-D): the library estimates them from the ordered points
+        given = [a for a in (X, normals, weights) if a is not None]
+        on_device = all(isinstance(a, torch.Tensor) and a.is_cuda for a in given)
         if on_device:  # CUDA tensors: the library reads the boundary from device memory
-            X, nrm, w = (a.detach().to(torch.float64).contiguous() for a in (X, normals, weights))
-            ptrs = (X.data_ptr(), nrm.data_ptr(), w.data_ptr())
+            X, nrm, w = (None if a is None else a.detach().to(torch.float64).contiguous() for a in (X, normals, weights))
+            ptrs = tuple(0 if a is None else a.data_ptr() for a in (X, nrm, w))
         else:
-            X, nrm, w = (np.ascontiguousarray(_host(a)) for a in (X, normals, weights))
-            ptrs = (X.ctypes.data, nrm.ctypes.data, w.ctypes.data)
+            X, nrm, w = (None if a is None else np.ascontiguousarray(_host(a)) for a in (X, normals, weights))
+            ptrs = tuple(0 if a is None else a.ctypes.data for a in (X, nrm, w))
+        self._keep = (X, nrm, w)
         dim, M = X.shape
         d = ibdl_geometry_desc()
         d.dim, d.n, d.box = dim, int(n), float(box)
         for j in range(3):
             d.origin[j] = float(origin[j]) if j < len(origin) else 0.0
         d.n_points = M
-        d.X, d.normals, d.weights = ptrs
+        d.X, d.normals, d.weights = (p or None for p in ptrs)
         d.pde, d.lambda_, d.mu = _PDE[pde], float(lam), float(mu)
         d.delta, d.dipole, d.symbol = _DELTA[delta], _DIPOLE[dipole], _SYMBOL[symbol]
         d.inputs_on_device = int(on_device)

@@ -88,6 +88,10 @@ def test_host_side_argument_checks(lib):
     d.dim, d.n = 2, 100  # not a power of two
     assert lib.ibdl_create_geometry(ctypes.byref(d), None, ctypes.byref(out)) == ibdl.IBDL_ERR_INVALID_ARG
     assert "power of two" in ibdl.ibdl_last_error()
+    d.n, d.dim = 64, 3
+    d.X, d.normals, d.weights = 1, None, None  # 3-D needs normals and weights (rejected before any copy)
+    assert lib.ibdl_create_geometry(ctypes.byref(d), None, ctypes.byref(out)) == ibdl.IBDL_ERR_INVALID_ARG
+    assert "required" in ibdl.ibdl_last_error()
     d.n, d.pde, d.dim = 64, ibdl.IBDL_PDE_STOKES, 3
     d.X = d.normals = d.weights = 1  # never dereferenced: the combination is rejected first
     d.mu = 1.0

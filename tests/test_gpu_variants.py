@@ -239,3 +239,36 @@ def test_completed_error_paths():
         g.apply_transpose(v)
     with pytest.raises(IbdlError, match="UNSUPPORTED"):
         g.solve_vjp(v, v)
+
+
+# ----------------------------------------------------------------------------------------
+# normals and weights estimated from the points (Sec. 5.3.1)
+# ----------------------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("case", ["star scalar", "wrapped circle", "stokes clockwise"])
+def test_estimated_normals_and_weights(case):
+    """A geometry given only its points equals one given the oracle's estimates: applications
+    1e-12 against the oracle with those estimates, and a solve 1e-10."""
+    from paper_2210_07403_gb300 import Geometry
+
+    N = 128
+    if case == "star scalar":
+        bd = I.star(I.points_for_spacing(1.9124, 1 / N, 1.0))
+        X, pde = bd.X, "scalar"
+    elif case == "wrapped circle":
+        bd = I.circle(I.points_for_spacing(2 * np.pi * 0.2, 1 / N, 0.8), R=0.2)
+        X, pde = np.mod(bd.X + np.array([[0.45], [0.42]]), 1.0), "scalar"
+    else:  # clockwise order: normals into the enclosed region (an exterior domain's)
+        bd = I.circle(I.points_for_spacing(2 * np.pi * 0.2, 1 / N, 1.0), R=0.2)
+        X, pde = bd.X[:, ::-1].copy(), "stokes"
+    n, w = O.estimate_normals(X, 1.0), O.estimate_weights(X, 1.0)
+    og = O.Geometry(O.Grid(2, N), X, n, w, "cos", "analytic", "spectral", pde, 0.0)
+    g = Geometry(X, None, None, N, pde=pde)
+    q = np.random.default_rng(9).standard_normal(og.ncomp * og.M)
+    assert _rel(g.apply(_cuda(q)).cpu().numpy(), O.apply(og, q)) < 1e-12
+    if pde == "scalar":
+        ub = I.harmonic_cubic(X[0], X[1])
+        Q, info, _ = g.solve(_cuda(ub), rtol=1e-12)
+        assert _rel(Q.cpu().numpy(), O.solve(og, ub, 1e-13, maxit=100).x) < 1e-10
+
