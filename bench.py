@@ -433,13 +433,14 @@ def postprocess_workload(dev, flush, stream, K=5, Ns=(256, 512, 1024, 2048)):
     return res
 
 
-def size_sweep_workload(dev, flush, stream, Ns=(512, 1024, 2048, 4096), napply=50):
+def size_sweep_workload(dev, flush, stream, Ns=(512, 1024, 2048, 4096, 8192), napply=50):
     """The 64² circle problem's geometry on finer grids (Δs ≈ 0.75h, the paper's spacing; its
     studies run N = 2^6 … 2^14): scalar Laplace, analytic dipole, spectral symbol. Per N and
     precision: applications/s from CUDA events over `napply` back-to-back applications after an
     L2 flush, the algorithmic bytes 4N²w (+ boundary vectors) per application against the measured
     HBM bandwidth, whether the grid fields fit in L2, and FP64 and mixed solve rates to 1e-9.
-    The shared-memory FFT holds whole columns: FP64 up to 2048², FP32 up to 4096²."""
+    The shared-memory FFT holds whole columns: FP64 up to 4096², FP32 up to 8192² (beyond 2048² FP64
+    and 4096² FP32 without the staged twiddle and symbol tables)."""
     import torch
 
     import ibdl_inputs as I

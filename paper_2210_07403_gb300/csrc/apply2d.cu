@@ -92,6 +92,7 @@ struct RowParams {
   double eta;             // η
   double hd;              // h^d
   T eta_src;              // weight of the ηSQ source: η (scalar) or η/μ (Stokes, projected part)
+  int tw_smem;            // 1: the twiddles are staged in shared memory; 0: read from p.tw (large n)
 };
 
 template <typename T>
@@ -116,6 +117,7 @@ struct ColParams {
   cplx<T>* spec;
   const cplx<T>* tw;
   const int* stop;
+  int tw_smem;  // 1: twiddles and symbol tables staged in shared memory; 0: read from global (large n)
 };
 
 // Sorted points whose base row lies in the cell rows [r0 − 3, r0 + R) (mod n): at most two
@@ -180,16 +182,17 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   constexpr int NC = Traits<OP>::C;
   const int n = p.n, R = p.R, half = R >> 1, M = p.M;
   const int seqs = NIN * half;
-  cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* bufA = tws + n;
+  cplx<T>* tws_s = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufA = tws_s + (p.tw_smem ? n : 0);
   cplx<T>* bufB = bufA + padded((size_t)seqs * n);
+  const cplx<T>* tws = p.tw_smem ? tws_s : p.tw;
   // accumulation view: field f, local row lr, column x → complex element e = (f·half + lr/2)·n + x
   // of the padded buffer, real part for even lr and imaginary part for odd lr
   T* acc = reinterpret_cast<T*>(bufA);
   const int r0 = unit * R;
   // prologue independent of the previous kernel, then wait for it (programmatic launch)
   for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
-  load_twiddles(tws, p.tw, n);
+  if (p.tw_smem) load_twiddles(tws_s, p.tw, n);
   // the points whose stencil meets the band, and this thread's first work item (16 per point)
   const PointRanges pr = band_points(p.cell_start, n, r0, R);
   const int nitems = p.grid_in ? 0 : pr.cnt * 16;
@@ -397,16 +400,21 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
   constexpr int NOUT = Traits<OP>::NOUT;
   constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
   const int n = p.n, C = p.C, nh = n >> 1;
-  cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* bufA = tws + n;
+  cplx<T>* tws_s = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufA = tws_s + (p.tw_smem ? n : 0);
   cplx<T>* bufB = bufA + padded((size_t)NMAX * C * n);
-  T* lap1 = reinterpret_cast<T*>(bufB + padded((size_t)NMAX * C * n));
-  T* der1 = lap1 + n;
+  T* lap1_s = reinterpret_cast<T*>(bufB + padded((size_t)NMAX * C * n));
+  T* der1_s = lap1_s + n;
+  const cplx<T>* tws = p.tw_smem ? tws_s : p.tw;
+  const T* lap1 = p.tw_smem ? lap1_s : p.lap1;
+  const T* der1 = p.tw_smem ? der1_s : p.der1;
   const int k0 = unit * C;
-  load_twiddles(tws, p.tw, n);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    lap1[i] = p.lap1[i];
-    der1[i] = p.der1[i];
+  if (p.tw_smem) {
+    load_twiddles(tws_s, p.tw, n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      lap1_s[i] = p.lap1[i];
+      der1_s[i] = p.der1[i];
+    }
   }
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
@@ -524,11 +532,12 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   constexpr int NOUT = Traits<OP>::NOUT;
   const int n = p.n, R = p.R, half = R >> 1, M = p.M, nh = n >> 1;
   const int seqs = NOUT * half;
-  cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* bufA = tws + n;
+  cplx<T>* tws_s = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* bufA = tws_s + (p.tw_smem ? n : 0);
   cplx<T>* bufB = bufA + padded((size_t)seqs * n);
+  const cplx<T>* tws = p.tw_smem ? tws_s : p.tw;
   const int r0 = unit * R;
-  load_twiddles(tws, p.tw, n);
+  if (p.tw_smem) load_twiddles(tws_s, p.tw, n);
   // the points whose stencil meets the band and this thread's first work item (4 per point),
   // loaded before the wait: the point tables are constant
   const PointRanges pr = band_points(p.cell_start, n, r0, R);
@@ -662,6 +671,7 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.eta = g->eta;
   rp.hd = g->h * g->h;
   rp.eta_src = T(g->naug ? (g->pde == IBDL_PDE_STOKES ? g->eta / g->mu : g->eta) : 0.0);
+  rp.tw_smem = 1;
   return rp;
 }
 
@@ -682,22 +692,26 @@ static ColParams<T> col_params(Geometry* g, const int* stop) {
   cp.spec = reinterpret_cast<cplx<T>*>(g->spec);
   cp.tw = reinterpret_cast<const cplx<T>*>(pi ? (const void*)g->tw32 : (const void*)g->tw64);
   cp.stop = stop;
+  cp.tw_smem = 1;
   return cp;
 }
 
-// shared memory: twiddles (n) + two padded FFT buffers (+ the two symbol tables in the column pass)
+// shared memory: two padded FFT buffers, plus (staged) the twiddles (n) and, in the column pass,
+// the two symbol tables. Large grids leave the tables in global memory (L1-cached reads) so the
+// buffers fit: FP64 to 4096², FP32 to 8192² for the scalar operator, 2048² / 4096² for Stokes.
 template <typename T, int OP>
-static size_t smem_spread(const Geometry* g, int R) {
-  return (g->n + 2 * padded((size_t)Traits<OP>::NIN * (R / 2) * g->n)) * sizeof(cplx<T>);
+static size_t smem_spread(const Geometry* g, int R, bool staged = true) {
+  return ((staged ? g->n : 0) + 2 * padded((size_t)Traits<OP>::NIN * (R / 2) * g->n)) * sizeof(cplx<T>);
 }
 template <typename T, int OP>
-static size_t smem_gather(const Geometry* g, int R) {
-  return (g->n + 2 * padded((size_t)Traits<OP>::NOUT * (R / 2) * g->n)) * sizeof(cplx<T>);
+static size_t smem_gather(const Geometry* g, int R, bool staged = true) {
+  return ((staged ? g->n : 0) + 2 * padded((size_t)Traits<OP>::NOUT * (R / 2) * g->n)) * sizeof(cplx<T>);
 }
 template <typename T, int OP>
-static size_t smem_col(const Geometry* g, int C) {
+static size_t smem_col(const Geometry* g, int C, bool staged = true) {
   const int nmax = Traits<OP>::NIN > Traits<OP>::NOUT ? Traits<OP>::NIN : Traits<OP>::NOUT;
-  return (g->n + 2 * padded((size_t)nmax * C * g->n)) * sizeof(cplx<T>) + 2 * g->n * sizeof(T);
+  return ((staged ? g->n : 0) + 2 * padded((size_t)nmax * C * g->n)) * sizeof(cplx<T>) +
+         (staged ? 2 * g->n * sizeof(T) : 0);
 }
 
 static const size_t kSmemLimit = 227 * 1024;
@@ -764,7 +778,11 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi];
   if (R == 0 || C == 0)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
-  const size_t s1 = smem_spread<T, OP>(g, R), s2 = smem_col<T, OP>(g, C), s3 = smem_gather<T, OP>(g, R);
+  // stage the twiddles (and symbol tables) in shared memory when they fit beside the buffers
+  const bool row_staged = smem_spread<T, OP>(g, R) <= kSmemLimit && smem_gather<T, OP>(g, R) <= kSmemLimit;
+  const bool col_staged = smem_col<T, OP>(g, C) <= kSmemLimit;
+  const size_t s1 = smem_spread<T, OP>(g, R, row_staged), s2 = smem_col<T, OP>(g, C, col_staged),
+               s3 = smem_gather<T, OP>(g, R, row_staged);
   if (s1 > kSmemLimit || s2 > kSmemLimit || s3 > kSmemLimit)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
   RowParams<T> rp = row_params<T>(g, in, out, stop, grid);
@@ -777,7 +795,9 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
     rp.aug = 0;
     rp.eta_src = T(0);
   }
+  rp.tw_smem = row_staged ? 1 : 0;
   ColParams<T> cp = col_params<T>(g, stop);
+  cp.tw_smem = col_staged ? 1 : 0;
   if (mode & RUN_LAPLACE) cp.lam = T(0);  // the plain Laplace problem (indicator)
   if (mode & (RUN_LAPLACE | RUN_NO_AUG)) {  // no completed-method terms
     rp.aug = 0;
@@ -1150,8 +1170,9 @@ static TuneKey tune_key(const Geometry* g, int pi) { return {g->n, g->nf_in, g->
 ibdl_status autotune_2d(Geometry* g, int pi, bool fixed_threads, cudaStream_t s, const double* Q, double* Y) {
   const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
   const size_t cs = pi ? sizeof(float2) : sizeof(double2);
-  auto row_bytes = [&](int r) { return (g->n + 2 * padded((size_t)nf * (r / 2) * g->n)) * cs; };
-  auto col_bytes = [&](int c) { return (g->n + 2 * padded((size_t)nf * c * g->n)) * cs + 2 * g->n * cs / 2; };
+  // feasible without the staged tables (each launch stages them when they fit)
+  auto row_bytes = [&](int r) { return 2 * padded((size_t)nf * (r / 2) * g->n) * cs; };
+  auto col_bytes = [&](int c) { return 2 * padded((size_t)nf * c * g->n) * cs; };
   const int saved_R = g->rows_per_cta[pi], saved_C = g->cols_per_cta[pi], saved_T = g->threads[pi];
   const int saved_timing = g->timing;
   g->timing = 0;
@@ -1246,8 +1267,9 @@ ibdl_status plan_2d(Geometry* g) {
     const size_t cs = pi ? sizeof(float2) : sizeof(double2);
     const int target = pi ? 2048 : 1024;
     int R = clampp2(2 * (target / (n * g->nf_in)), 2, n / 16 > 2 ? n / 16 : 2);
-    auto row_bytes = [&](int r) { return (g->n + 2 * padded((size_t)nf * (r / 2) * g->n)) * cs; };
-    auto col_bytes = [&](int c) { return (g->n + 2 * padded((size_t)nf * c * g->n)) * cs + 2 * g->n * cs / 2; };
+    // feasible without the staged tables (each launch stages them when they fit)
+    auto row_bytes = [&](int r) { return 2 * padded((size_t)nf * (r / 2) * g->n) * cs; };
+    auto col_bytes = [&](int c) { return 2 * padded((size_t)nf * c * g->n) * cs; };
     while (R > 2 && row_bytes(R) > kSmemLimit) R /= 2;
     if (row_bytes(R) > kSmemLimit) R = 0;
     int C = clampp2(target / (n * nf), 1, n / 32 > 1 ? n / 32 : 1);

@@ -242,6 +242,22 @@ def test_solve_zero_rhs(precision):
     assert float(Q.abs().max()) == 0.0
 
 
+@pytest.mark.parametrize("N,pde,precision,tol", [(4096, "scalar", "fp64", 1e-12), (8192, "scalar", "fp32", 2e-5),
+                                                   (2048, "stokes", "fp64", 1e-12), (4096, "stokes", "fp32", 2e-5)])
+def test_large_grids_global_tables(N, pde, precision, tol):
+    """Grids whose FFT buffers leave no room for the staged twiddles and symbol tables: the
+    kernels read those from global memory. Applications against the oracle at full size."""
+    from paper_2210_07403_gb300 import Geometry
+
+    M = I.points_for_spacing(2 * np.pi * 0.25, 1.0 / N, 1.0)
+    bd = I.circle(M)
+    og = O.Geometry(O.Grid(2, N), bd.X, bd.n, bd.w, "cos", "analytic", "spectral", pde, 0.0)
+    g = Geometry(bd.X, bd.n, bd.w, N, pde=pde)
+    q = np.random.default_rng(N).standard_normal(og.ncomp * M)
+    y = g.apply(torch.from_numpy(q).cuda(), precision=precision).cpu().numpy()
+    assert _rel(y, O.apply(og, q)) < tol
+
+
 def test_solve_host_buffers():
     p = I.circle_laplace(64, 100)
     g = _geom(p)
