@@ -280,6 +280,7 @@ def extra_workloads(dev, flush, stream, K=5):
     g.close()
     out["stokes_star_probes_1024"] = differentiation_workload(dev, flush, stream, K)
     out["cylinder_array_drag_1024"] = cylinder_drag_workload(dev, flush, stream)
+    out["cylinder_array_drag_2048"] = cylinder_drag_workload(dev, flush, stream, N=2048)
     out["postprocess"] = postprocess_workload(dev, flush, stream)
     out["size_sweep"] = size_sweep_workload(dev, flush, stream)
     return out

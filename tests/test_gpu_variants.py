@@ -225,6 +225,32 @@ def test_cylinder_drag_1024(c):
     assert abs(D - ref) < 0.01 * ref
 
 
+@pytest.mark.parametrize("c,tol", [(0.05, 0.004), (0.3, 0.005)])
+def test_cylinder_drag_2048(c, tol):
+    """At 2048² (FP64 Stokes beyond the staged-table size) the drag moves toward the published
+    boundary-integral values (golden file): within 0.4 % at c = 0.05 and 0.5 % at c = 0.3, against
+    −0.18 % and +0.95 % at 1024²; mixed precision gives the same drag to 1e-8."""
+    import os
+
+    ref = None
+    with open(os.path.join(os.path.dirname(__file__), "golden", "cylinder_drag.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#") and float(line.split()[0]) == c:
+                ref = float(line.split()[2])
+    p = I.cylinder_array(2048, c)
+    g = _geom(p)
+    b = _cuda(np.concatenate([p.Ub.reshape(-1), p.meta["rhs_aug"]]))
+    w = _cuda(p.bd.w)
+    D = {}
+    for prec, rtol in (("fp64", 1e-10), ("mixed", 1e-10)):
+        x, info, st = g.solve(b, rtol=rtol, precision=prec, inner_rtol=1e-5, maxit=400)
+        assert st == 0
+        U = float(g.evaluate_field(x)[0][:, 0].sum()) / 2048
+        D[prec] = float(-10.0 * (x[: g.M] * w).sum()) / U
+    assert abs(D["fp64"] - ref) < tol * ref
+    assert abs(D["mixed"] - D["fp64"]) < 1e-8 * D["fp64"]
+
+
 def test_completed_error_paths():
     from paper_2210_07403_gb300 import IbdlError
 
