@@ -197,9 +197,9 @@ ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const i
  *                               completed method the c constraint rows become h^d Σ_g g̃_l (the
  *                               last c entries of U_b are ignored);
  *   ibdl_evaluate_field_forced: u_grid = the field of Q (ibdl_evaluate_field) + u_g.
- * g_grid: device FP64 [c][n][n] (c = 1 scalar, 2 Stokes), 2-D only (IBDL_ERR_UNSUPPORTED in 3-D);
- * NULL makes both calls their unforced counterparts. u_grid may not overlap g_grid. The geometry
- * allocates its source-term workspace ((c + 3)·n² + c·M doubles) on the first forced call. */
+ * g_grid: device FP64 [c][n^dim] (c = 1 scalar, 2 Stokes; 2-D and 3-D); NULL makes both calls
+ * their unforced counterparts. u_grid may not overlap g_grid. The geometry allocates its
+ * source-term workspace (about (c + 3)·n^dim + c·M doubles) on the first forced call. */
 ibdl_status ibdl_solve_forced(ibdl_geometry* geom, const double* Ub, const double* g_grid, double* Q,
                               const ibdl_solve_opts* opts, ibdl_solve_info* info, void* stream);
 ibdl_status ibdl_evaluate_field_forced(ibdl_geometry* geom, const double* Q, const double* g_grid, double* u_grid,

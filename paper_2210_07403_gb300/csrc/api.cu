@@ -185,11 +185,10 @@ ibdl_status ibdl_solve(ibdl_geometry* geom, const double* Ub, double* Q, const i
   return solve_entry(geom, Ub, Q, opts, info, stream, OPK_A, "U_b", "Q");
 }
 
-// the source term g̃: device FP64 [c][n][n], 2-D; NULL = none
+// the source term g̃: device FP64 [c][n^dim]; NULL = none
 static ibdl_status check_source(ibdl_geometry* geom, const double* g_grid) {
   if (!g_grid) return IBDL_OK;
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
-  if (geom->g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "a source term g_grid: 2-D only");
   return check_device_ptr(g_grid, "g_grid");
 }
 
@@ -206,12 +205,12 @@ ibdl_status ibdl_evaluate_field_forced(ibdl_geometry* geom, const double* Q, con
   IBDL_TRY(check_source(geom, g_grid));
   if (g_grid && u_grid) {
     const Geometry* g = geom->g;
-    const size_t grid_bytes = sizeof(double) * g->ncomp * (size_t)g->n * g->n;
+    const size_t grid_bytes = sizeof(double) * g->ncomp * (size_t)g->n * g->n * (g->dim == 3 ? g->n : 1);
     if (spans_overlap(u_grid, grid_bytes, g_grid, grid_bytes)) return fail(IBDL_ERR_INVALID_ARG, "u_grid and g_grid overlap");
   }
   IBDL_TRY(ibdl_evaluate_field(geom, Q, u_grid, stream));
   if (!g_grid) return IBDL_OK;
-  return source_terms_2d(geom->g, g_grid, nullptr, u_grid, static_cast<cudaStream_t>(stream));
+  return source_terms(geom->g, g_grid, nullptr, u_grid, static_cast<cudaStream_t>(stream));
 }
 
 ibdl_status ibdl_solve_transpose(ibdl_geometry* geom, const double* G, double* lambda, const ibdl_solve_opts* opts,

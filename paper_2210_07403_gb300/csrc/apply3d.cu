@@ -17,6 +17,8 @@
 #include <cstdlib>
 #include <type_traits>
 
+#include <algorithm>
+
 #include "fft.cuh"
 
 namespace ibdl {
@@ -59,6 +61,7 @@ struct Row3Params {
   // values multiplied by Δs/h³ in place of the spread's Δs/h³ · W⁻¹)
   int trans;
   double jump;  // jump term coefficient: ½ (Dirichlet) or −½ (Neumann)
+  const double* grid_in;  // optional [NIN][n][n][n]: the row bands are read from it instead of spread
 };
 
 struct Col3Params {
@@ -152,13 +155,23 @@ __global__ void __launch_bounds__(kThreads3) k3_spread_rowfft(Row3Params p) {
   const double* pin;
   double* pout;
   resolve_io3(p, pin, pout);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) pout[i] = p.jump * pin[i];
+  if (!p.grid_in)  // jump term: out = ±½·in (the gather adds S*u afterwards); none for grid input
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) pout[i] = p.jump * pin[i];
   for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
   load_twiddles(tws, static_cast<const cplx<T>*>(p.tw), n);
   __syncthreads();
 
+  if (p.grid_in) {  // rows of a grid field ([NIN][z][y][x]) in place of the spread
+    for (int t = threadIdx.x; t < NIN * R * n; t += blockDim.x) {
+      const int f = t / (R * n);
+      const int rem = t - f * R * n;
+      const int lr = rem / n, x = rem - lr * n;
+      acc[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)] =
+          T(p.grid_in[(((size_t)f * n + z) * n + y0 + lr) * n + x]);
+    }
+  }
   const Ranges3 rg = band_points3(p.cell_start, n, z, y0, R);
-  for (int t = threadIdx.x; t < rg.total * 16; t += blockDim.x) {
+  for (int t = threadIdx.x; t < (p.grid_in ? 0 : rg.total * 16); t += blockDim.x) {
     const int s = rg.at(t >> 4);
     const int ay = (t >> 2) & 3, ax = t & 3;
     const int az = (z - p.base[2 * M + s]) & (n - 1);  // the one stencil plane at z (0..3)
@@ -542,7 +555,8 @@ ibdl_status plan_3d(Geometry* g) {
 
 template <typename T, int OP>
 static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStream_t s, const int* stop, double* grid,
-                           const int* idx = nullptr, int vstride = 0, int trans = 0, bool laplace = false) {
+                           const int* idx = nullptr, int vstride = 0, int trans = 0, bool laplace = false,
+                           const double* grid_in = nullptr) {
   constexpr int NIN = Traits3<OP>::NIN, NOUT = Traits3<OP>::NOUT;
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi], Cz = g->zcols_per_cta[pi];
@@ -572,6 +586,7 @@ static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStrea
   rp.vstride = vstride;
   rp.trans = trans;
   rp.jump = g->bc == IBDL_BC_NEUMANN ? -0.5 : 0.5;
+  rp.grid_in = grid_in;
   Col3Params cp;
   cp.n = n;
   cp.log2n = rp.log2n;
@@ -646,6 +661,50 @@ ibdl_status laplace_field_3d(Geometry* g, const double* Q, double* u, cudaStream
 
 ibdl_status field_3d(Geometry* g, const double* Q, double* u, cudaStream_t s) {
   return apply3_t<double>(g, Q, g->tmp_m, s, nullptr, u);
+}
+
+namespace {
+
+__global__ void k3_negate(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = -a[i];
+}
+
+__global__ void k3_axpy(double* __restrict__ y, const double* __restrict__ x, double a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+
+}  // namespace
+
+// the source term g̃ of the scalar 3-D problem: u_g = L⁻¹g̃ from −g̃ through the −L⁻¹ symbol of the
+// forward op's Fourier stage; rhs[0..M) −= S*u_g (rhs may be NULL), grid += u_g (grid may be NULL)
+ibdl_status source_terms_3d(Geometry* g, const double* gsrc, double* rhs, double* grid, cudaStream_t s) {
+  const int64_t cells = (int64_t)g->n * g->n * g->n;
+  const int M = (int)g->M;
+  // −g̃ [n³] | u_g [n³] | S*u_g [M]
+  if (!g->src_buf) IBDL_CUDA(cudaMalloc((void**)&g->src_buf, sizeof(double) * (2 * cells + M)));
+  double* f = g->src_buf;
+  double* ug = f + cells;
+  double* w = ug + cells;
+  const int blocks = (int)std::min<int64_t>((cells + 255) / 256, 152 * 8);
+  k3_negate<<<blocks, 256, 0, s>>>(gsrc, f, cells);
+  IBDL_CUDA(cudaGetLastError());
+  g->launches += 1;
+  if (rhs) {
+    IBDL_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * M, s));
+    IBDL_TRY((run_op3<double, OP3_SCALAR_AN>(g, nullptr, w, s, nullptr, nullptr, nullptr, 0, 0, false, f)));
+    k3_axpy<<<(M + 255) / 256, 256, 0, s>>>(rhs, w, -1.0, M);
+    IBDL_CUDA(cudaGetLastError());
+    g->launches += 1;
+  }
+  if (grid) {
+    IBDL_TRY((run_op3<double, OP3_SCALAR_AN>(g, nullptr, w, s, nullptr, ug, nullptr, 0, 0, false, f)));
+    k3_axpy<<<blocks, 256, 0, s>>>(grid, ug, 1.0, cells);
+    IBDL_CUDA(cudaGetLastError());
+    g->launches += 1;
+  }
+  return IBDL_OK;
 }
 
 ibdl_status adjoint_3d(Geometry* g, int precision, const double* W, double* Z, cudaStream_t s) {

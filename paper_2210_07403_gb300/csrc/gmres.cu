@@ -631,7 +631,7 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
   IBDL_CUDA(cudaMemcpyAsync(b, Ub, sizeof(double) * nd, o->io_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   IBDL_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nd, s));
   // a source term: b = U_b − S*u_g (and the completed method's constraint rows from g̃)
-  if (gsrc) IBDL_TRY(source_terms_2d(g, gsrc, b, nullptr, s));
+  if (gsrc) IBDL_TRY(source_terms(g, gsrc, b, nullptr, s));
   // ‖U_b‖ comes from the first cycle (its ‖r0‖), which also forms its own target rtol·‖U_b‖
   const bool mixed = o->precision == IBDL_MIXED;
   ibdl_solve_info inf = {};

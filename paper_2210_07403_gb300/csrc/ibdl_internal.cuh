@@ -221,6 +221,10 @@ ibdl_status field_pair_2d(Geometry* g, const double* Q, const double* lam, doubl
 // the source term g̃ (2-D): rhs[0..c·M) −= S*u_g and, for the completed method, rhs[c·M + l] =
 // h^d Σ g̃_l (rhs may be NULL); grid[c][n][n] += u_g (grid may be NULL)
 ibdl_status source_terms_2d(Geometry* g, const double* gsrc, double* rhs, double* grid, cudaStream_t s);
+ibdl_status source_terms_3d(Geometry* g, const double* gsrc, double* rhs, double* grid, cudaStream_t s);
+inline ibdl_status source_terms(Geometry* g, const double* gsrc, double* rhs, double* grid, cudaStream_t s) {
+  return g->dim == 2 ? source_terms_2d(g, gsrc, rhs, grid, s) : source_terms_3d(g, gsrc, rhs, grid, s);
+}
 ibdl_status laplace_field_2d(Geometry* g, const double* Q, double* u, cudaStream_t s);
 ibdl_status laplace_field_3d(Geometry* g, const double* Q, double* u, cudaStream_t s);
 ibdl_status indicator_impl(Geometry* g, double* chi, uint8_t* flags, cudaStream_t s);
