@@ -85,7 +85,10 @@ typedef struct ibdl_geometry ibdl_geometry; /* opaque, library-owned */
 
 typedef struct {
   int dim;              /* 2 or 3                                                          */
-  int n;                /* grid nodes per axis: a power of two, 16..8192 (2-D), 16..256 (3-D) */
+  int n;                /* grid nodes per axis: a power of two, 16..8192 (2-D), 16..256 (3-D);
+                           the shared-memory FFT runs 2-D scalar problems to 4096 (FP64) and
+                           8192 (FP32), Stokes to 2048 (FP64) and 4096 (FP32); a call at a
+                           larger size returns IBDL_ERR_UNSUPPORTED                         */
   double box;           /* side length of the periodic box, > 0                             */
   double origin[3];     /* lower corner of the box (unused entries ignored)                 */
   int64_t n_points;     /* M ≥ 1                                                           */

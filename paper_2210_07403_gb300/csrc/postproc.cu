@@ -19,12 +19,14 @@
 //
 // Kernels (the interpolation): k_mark flags the nodes within ceil(m1) + 2 cells of some point
 // (a superset of the nodes to replace), k_compact lists the flagged nodes of Ω, and k_near
-// gives each listed node one warp. The warp scans the points whose cell row lies within K rows
-// of the node (rows of the geometry's cell-sorted order), keeps the three nearest per lane,
-// merges them across the warp, and rescans all M points when the row slab cannot guarantee the
-// result (the third distance not below W = (K − 1)·h). Within the slab a point whose |dx| is not
-// below W is dropped after one FP64 subtraction and comparison: the kernel is bound by the FP64
-// pipe, so the work per point decides its time.
+// takes the listed nodes in batches of kNearBatch per warp. For each node in turn the warp scans
+// the points whose cell row lies within K rows of the node (rows of the geometry's cell-sorted
+// order), keeps the three nearest per lane, merges them across the warp, and rescans all M
+// points when the row slab cannot guarantee the result (the third distance not below
+// W = (K − 1)·h); lane k keeps node k's result and finally interpolates it. Within the slab a point
+// whose |dx| is not below W is dropped after one FP64 subtraction and an integer comparison; the
+// distance comparisons run on the integer pipe (non-negative doubles order as their bits), so the
+// FP64 unit only forms the distances.
 #include <climits>
 #include <cmath>
 #include <cstring>
