@@ -1,7 +1,8 @@
 // The Arnoldi step of GMRES (Sec. 5.3.2) on one thread-block cluster, FP64.
 //
 // Step j orthogonalises w = A v_j (stored at V_{j+1}) against V_0..V_j by classical Gram–Schmidt
-// applied twice (CGS2), normalises it, applies the stored Givens rotations to the new Hessenberg
+// whose second pass comes from the basis' Gram matrix (one cluster reduction per step; see
+// arnoldi_body), normalises it, applies the stored Givens rotations to the new Hessenberg
 // column, forms the new rotation and updates the residual estimate |g_{j+1}|.
 //
 // CTA r of the cluster owns the slice [r·slice, (r+1)·slice) of every vector. Written for
@@ -9,7 +10,8 @@
 // cycles whatever the number of active lanes, and a dependent FP64 operation waits about 65
 // cycles (square root and division are sequences of them). So
 //   - with STAGED the CTA copies its slice of V_0..V_j into shared memory before it waits for the
-//     application (programmatic launch): those vectors and the rotation state are final by then;
+//     application (programmatic launch), and every CTA copies the Gram block of v_0..v_{j−1}:
+//     those vectors, the Gram matrix and the rotation state are final by then;
 //   - dot products give L lanes to each basis vector (all lanes busy), each lane two
 //     accumulators over a strided part of the slice, then an 8-way tree of the partial sums;
 //     no shuffle reductions (a full-warp FP64 add per level);
@@ -19,10 +21,10 @@
 //   - the old rotations are applied by one warp as a scan of the affine recurrence
 //     x_{i+1} = −s_i x_i + c_i h_{i+1} (x_0 = h_0), whose values give the rotated column
 //     H_i = c_i x_i + s_i h_{i+1}; 5 shuffle levels replace the 2j dependent operations.
-// Partial sums of the cluster are combined through distributed shared memory (one buffer per
-// pass). ‖w₂‖² = ‖w₁‖² − Σ h₂,ᵢ² (w₂ = w₁ − V h₂ with V orthonormal; h₂ holds rounding-level
-// values only). Two cluster barriers per step, and a split arrive/wait one so no CTA exits while
-// another may still read its shared memory.
+// Partial sums of the cluster are combined through distributed shared memory. One cluster barrier
+// per step, and a split arrive/wait one so no CTA exits while another may still read its shared
+// memory. On the 512² Stokes star the step takes 14.5 µs standalone (16.8 µs with CGS2's two
+// reductions), and the solves keep their iteration counts.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -48,6 +50,7 @@ struct GmresState {
   double cs[KMAX], sn[KMAX], g[KMAX + 1];
   double H[(KMAX + 1) * KMAX];  // column j at H[j·(m+1) + i]
   double bnorm;                 // ‖U_b‖, recorded by the first cycle of a refinement solve
+  double G[KMAX * KMAX];        // Gram matrix v_iᵀv_k of the basis, G[i·KMAX + k] (filled one column per step)
 };
 
 struct HostStatus {
@@ -63,9 +66,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 constexpr int ATH = 512;
 
-// shared memory (doubles) of a staged step: w's slice, then m + 1 basis rows
-__host__ __device__ constexpr size_t arnoldi_staged_doubles(int m, int slice) {
-  return (size_t)(m + 2) * (size_t)slice;
+// dynamic shared memory (doubles) of a step: w's slice, then (staged) m + 1 basis rows, then the
+// (m + 1)² Gram block
+__host__ __device__ constexpr size_t arnoldi_dyn_doubles(int m, int slice, bool staged) {
+  return (size_t)(staged ? m + 2 : 1) * (size_t)slice + (size_t)(m + 1) * (size_t)(m + 1);
 }
 
 // 1/√x for finite x > 2^−1000, by Newton–Raphson iteration for the reciprocal square root,
@@ -82,52 +86,6 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
   r = fma(-m * y, y, 1.0);
   y = fma(0.5 * y, r, y);
   return __hiloint2double(__double2hiint(y) - k * (1 << 20), __double2loint(y));
-}
-
-// Dot products of the slice rows 0..ndots−1 with w (row d ≤ j is V_d, row j + 1 is w itself),
-// this CTA's partial sums written to out[d]. L = min(64, 512/ndots) lanes per row, lane l
-// summing elements l, l + L, … with two accumulators; the L partials of a row are then summed in
-// groups of 8 and the group sums by one thread per row. pw holds ≥ 512 doubles, pw2 ≥ 136.
-__device__ __forceinline__ void slice_dots(const double* rows, size_t rstride, const double* ws, int cnt, int j,
-                                           int ndots, double* pw, double* pw2, double* out) {
-  const int tid = threadIdx.x;
-  const int L = min(64, ATH / ndots), R = (L + 7) >> 3;
-  if (tid < ndots * L) {
-    const int d = tid / L, l = tid - d * L;
-    const double* row = d <= j ? rows + (size_t)d * rstride : ws;
-    double a0 = 0.0, a1 = 0.0;
-    int e = l;
-    for (; e + L < cnt; e += 2 * L) {
-      a0 += row[e] * ws[e];
-      a1 += row[e + L] * ws[e + L];
-    }
-    if (e < cnt) a0 += row[e] * ws[e];
-    pw[tid] = a0 + a1;
-  }
-  __syncthreads();
-  if (tid < ndots * R) {
-    const int d = tid / R, r = tid - d * R;
-    const int b0 = d * L + 8 * r, b1 = min(d * L + L, b0 + 8);
-    double a0 = 0.0, a1 = 0.0;
-    int q = b0;
-    for (; q + 1 < b1; q += 2) {
-      a0 += pw[q];
-      a1 += pw[q + 1];
-    }
-    if (q < b1) a0 += pw[q];
-    pw2[tid] = a0 + a1;
-  }
-  __syncthreads();
-  if (tid < ndots) {
-    double a0 = 0.0, a1 = 0.0;
-    int r = 0;
-    for (; r + 1 < R; r += 2) {
-      a0 += pw2[tid * R + r];
-      a1 += pw2[tid * R + r + 1];
-    }
-    if (r < R) a0 += pw2[tid * R + r];
-    out[tid] = a0 + a1;
-  }
 }
 
 // ws[e] −= Σ_{i≤j} h[i]·V_i[e] over the slice, the sum over i split into groups of threads
@@ -170,23 +128,88 @@ __device__ __forceinline__ void slice_update(const double* rows, size_t rstride,
   __syncthreads();
 }
 
+// Dot products of the pairs (a_d, b_d) over the slice, d < ndots: d ≤ j: (V_d, w); d = j + 1:
+// (w, w); j + 2 ≤ d ≤ 2j + 2: (V_{d−j−2}, V_j) (the last one V_j·V_j). Lanes, accumulators and the
+// tree of partial sums as in slice_dots.
+__device__ __forceinline__ void slice_dots_pairs(const double* rows, size_t rstride, const double* ws, int cnt,
+                                                 int j, int ndots, double* pw, double* pw2, double* out) {
+  const int tid = threadIdx.x;
+  const int L = min(64, ATH / ndots), R = (L + 7) >> 3;
+  if (tid < ndots * L) {
+    const int d = tid / L, l = tid - d * L;
+    const double* a;
+    const double* b;
+    if (d <= j) {
+      a = rows + (size_t)d * rstride;
+      b = ws;
+    } else if (d == j + 1) {
+      a = ws;
+      b = ws;
+    } else {
+      a = rows + (size_t)(d - j - 2) * rstride;
+      b = rows + (size_t)j * rstride;
+    }
+    double a0 = 0.0, a1 = 0.0;
+    int e = l;
+    for (; e + L < cnt; e += 2 * L) {
+      a0 += a[e] * b[e];
+      a1 += a[e + L] * b[e + L];
+    }
+    if (e < cnt) a0 += a[e] * b[e];
+    pw[tid] = a0 + a1;
+  }
+  __syncthreads();
+  if (tid < ndots * R) {
+    const int d = tid / R, r = tid - d * R;
+    const int b0 = d * L + 8 * r, b1 = min(d * L + L, b0 + 8);
+    double a0 = 0.0, a1 = 0.0;
+    int q = b0;
+    for (; q + 1 < b1; q += 2) {
+      a0 += pw[q];
+      a1 += pw[q + 1];
+    }
+    if (q < b1) a0 += pw[q];
+    pw2[tid] = a0 + a1;
+  }
+  __syncthreads();
+  if (tid < ndots) {
+    double a0 = 0.0, a1 = 0.0;
+    int r = 0;
+    for (; r + 1 < R; r += 2) {
+      a0 += pw2[tid * R + r];
+      a1 += pw2[tid * R + r + 1];
+    }
+    if (r < R) a0 += pw2[tid * R + r];
+    out[tid] = a0 + a1;
+  }
+}
+
 // Returns −1 (every thread) when the step was skipped because the cycle had already stopped;
 // otherwise, on CTA 0 thread 0, 1 if this step stopped the cycle and 0 if it continues.
 // Control flow is uniform over the cluster (the skip decision reads state no kernel of the
 // running application writes).
+//
+// Classical Gram–Schmidt with the second pass taken from the Gram matrix G = VᵀV of the basis:
+// with t = V_jᵀw, CGS2's second coefficients are V_jᵀ(w − V_j t) = t − G t, so the new column is
+// h = (2I − G)t and w₂ = w − V_j h needs one projection and one update. G's new column
+// (v_iᵀv_j, i ≤ j) comes from the same cluster reduction as t and ‖w‖², so a step makes one
+// reduction instead of two; ‖w₂‖² = ‖w‖² − hᵀt to second order in G − I. The rounding of the single
+// subtraction leaves v_{j+1} off orthogonal by about ε‖w‖/‖w₂‖; the next step's G sees it and
+// corrects the projection, so the departure does not accumulate.
 template <bool STAGED, int CL>
 __device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, int nd, int m, int slice) {
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double dsm[];
-  __shared__ double part1[KMAX + 2], part2[KMAX + 2], h[KMAX + 2], hs[KMAX + 2];
+  __shared__ double part[2 * KMAX + 4], t[KMAX + 2], gc[KMAX + 2], h[KMAX + 2];
   __shared__ double pw[ATH], pw2[2 * KMAX + 8];
-  __shared__ double csl[KMAX], snl[KMAX], sc[6];
+  __shared__ double csl[KMAX], snl[KMAX], sc[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rank = (int)cluster.block_rank();
   const int lo = rank * slice;
   const int cnt = nd - lo < slice ? (nd - lo > 0 ? nd - lo : 0) : slice;
   double* ws = dsm;
   double* Vs = dsm + slice;
+  double* Gs = dsm + (STAGED ? (size_t)(m + 2) * slice : (size_t)slice);  // [(m+1)][(m+1)]
   const double* rows = STAGED ? Vs : V + lo;
   const size_t rstride = STAGED ? (size_t)slice : (size_t)nd;
 
@@ -197,10 +220,14 @@ __device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, in
   const bool skip = st->stop || j >= st->kmax || j >= m;
   if (!skip) {
     if (STAGED)
-      for (int t = tid; t < (j + 1) * cnt; t += ATH) {
-        const int i = t / cnt, e = t - i * cnt;
+      for (int q = tid; q < (j + 1) * cnt; q += ATH) {
+        const int i = q / cnt, e = q - i * cnt;
         Vs[(size_t)i * slice + e] = V[(size_t)i * nd + lo + e];
       }
+    for (int q = tid; q < j * j; q += ATH) {  // the Gram block of v_0..v_{j−1}
+      const int a = q / j, b = q - a * j;
+      Gs[a * (m + 1) + b] = st->G[a * KMAX + b];
+    }
     if (rank == 0) {
       if (tid < j) {
         csl[tid] = st->cs[tid];
@@ -220,68 +247,70 @@ __device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, in
   for (int e = tid; e < cnt; e += ATH) ws[e] = w[e];
   __syncthreads();
 
-  // pass 1: h₁ = Vᵀ w, w₁ = w − V h₁
-  slice_dots(rows, rstride, ws, cnt, j, j + 1, pw, pw2, part1);
+  // one reduction: t = V_jᵀw, ‖w‖², and G's column j (v_iᵀv_j, i ≤ j)
+  const int ndots = 2 * j + 3;
+  slice_dots_pairs(rows, rstride, ws, cnt, j, ndots, pw, pw2, part);
   cluster.sync();
-  if (tid <= j) {
+  if (tid < ndots) {
     double v[CL];
 #pragma unroll
-    for (int r = 0; r < CL; ++r) v[r] = cluster.map_shared_rank(part1, r)[tid];
+    for (int r = 0; r < CL; ++r) v[r] = cluster.map_shared_rank(part, r)[tid];
 #pragma unroll
-    for (int s = CL / 2; s > 0; s >>= 1)
+    for (int s2 = CL / 2; s2 > 0; s2 >>= 1)
 #pragma unroll
-      for (int r = 0; r < s; ++r) v[r] += v[r + s];
-    h[tid] = v[0];
-    hs[tid] = v[0];
-  }
-  __syncthreads();
-  slice_update(rows, rstride, ws, cnt, j, h, pw);
-
-  // pass 2: h₂ = Vᵀ w₁ and ‖w₁‖² (slot j + 1) in one reduction, w₂ = w₁ − V h₂
-  slice_dots(rows, rstride, ws, cnt, j, j + 2, pw, pw2, part2);
-  cluster.sync();
-  if (tid <= j + 1) {
-    double v[CL];
-#pragma unroll
-    for (int r = 0; r < CL; ++r) v[r] = cluster.map_shared_rank(part2, r)[tid];
-#pragma unroll
-    for (int s = CL / 2; s > 0; s >>= 1)
-#pragma unroll
-      for (int r = 0; r < s; ++r) v[r] += v[r + s];
-    h[tid] = v[0];
-    if (tid <= j) hs[tid] += v[0];
+      for (int r = 0; r < s2; ++r) v[r] += v[r + s2];
+    if (tid <= j)
+      t[tid] = v[0];
+    else if (tid == j + 1)
+      sc[6] = v[0];
+    else
+      gc[tid - j - 2] = v[0];
   }
   // every remote read of this step is done: arrive now, wait before leaving
   asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
   __syncthreads();
-  slice_update(rows, rstride, ws, cnt, j, h, pw);
+  // h = (2I − G) t, one warp per row of G (rows and columns j from this step's reduction)
+  for (int i = warp; i <= j; i += ATH / 32) {
+    double a = 0.0;
+    for (int k = lane; k <= j; k += 32) {
+      const double gik = (i < j && k < j) ? Gs[i * (m + 1) + k] : (i == j ? gc[k] : gc[i]);
+      a += gik * t[k];
+    }
+    a = warp_sum(a);
+    if (lane == 0) h[i] = 2.0 * t[i] - a;
+  }
+  __syncthreads();
   if (warp == 0) {
     double q = 0.0;
-    for (int i = lane; i <= j; i += 32) q += h[i] * h[i];
+    for (int i = lane; i <= j; i += 32) q += h[i] * t[i];
     q = warp_sum(q);
     if (lane == 0) {
-      const double hn2 = h[j + 1] - q;
+      const double hn2 = sc[6] - q;
       const double y = hn2 > 0x1p-1000 && hn2 <= 1e300 ? rsqrt_newton(hn2) : 0.0;
       sc[1] = isfinite(hn2) ? hn2 * y : hn2;  // NaN/Inf passed on to the status test
       sc[2] = y;
     }
   }
-  __syncthreads();
+  slice_update(rows, rstride, ws, cnt, j, h, pw);
   const double hn = sc[1], inv = sc[2];
   for (int e = tid; e < cnt; e += ATH) w[e] = ws[e] * inv;
+  if (rank == 0 && tid <= j) {  // G's column and row j for the later steps of the cycle
+    st->G[tid * KMAX + j] = gc[tid];
+    st->G[j * KMAX + tid] = gc[tid];
+  }
 
   int ret = 0;
   if (rank == 0 && warp == 0) {
-    // old rotations on the new column by a scan over the affine maps f_i(x) = −s_i x + c_i hs_{i+1}
+    // old rotations on the new column by a scan over the affine maps f_i(x) = −s_i x + c_i h_{i+1}
     const int i0 = 2 * lane, i1 = i0 + 1;
     double a0 = 1.0, b0 = 0.0, a1 = 1.0, b1 = 0.0;
     if (i0 < j) {
       a0 = -snl[i0];
-      b0 = csl[i0] * hs[i0 + 1];
+      b0 = csl[i0] * h[i0 + 1];
     }
     if (i1 < j) {
       a1 = -snl[i1];
-      b1 = csl[i1] * hs[i1 + 1];
+      b1 = csl[i1] * h[i1 + 1];
     }
     double A = a1 * a0, B = a1 * b0 + b1;  // f_{i1} ∘ f_{i0}
 #pragma unroll
@@ -297,12 +326,12 @@ __device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, in
       Ae = 1.0;
       Be = 0.0;
     }
-    const double x0 = hs[0];
+    const double x0 = h[0];
     const double xa = Ae * x0 + Be;  // x_{i0}
     const double xb = a0 * xa + b0;  // x_{i1}
     double* hc = st->H + (size_t)j * (m + 1);
-    if (i0 < j) hc[i0] = csl[i0] * xa + snl[i0] * hs[i0 + 1];
-    if (i1 < j) hc[i1] = csl[i1] * xb + snl[i1] * hs[i1 + 1];
+    if (i0 < j) hc[i0] = csl[i0] * xa + snl[i0] * h[i0 + 1];
+    if (i1 < j) hc[i1] = csl[i1] * xb + snl[i1] * h[i1 + 1];
     if (j == i0 || j == i1) {
       // the new rotation zeroes hn below x_j
       const double a = j == i0 ? xa : xb, b = hn;

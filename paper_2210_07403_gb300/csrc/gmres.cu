@@ -437,9 +437,9 @@ static ibdl_status arnoldi_cfg(Geometry* g, int m, ArnoldiCfg* c) {
   const int nd = geom_nd(g);
   c->cl = cl_choice;
   c->slice = (nd + c->cl - 1) / c->cl;
-  const size_t staged_bytes = arnoldi_staged_doubles(m, c->slice) * sizeof(double);
+  const size_t staged_bytes = arnoldi_dyn_doubles(m, c->slice, true) * sizeof(double);
   c->staged = staged_bytes <= 200 * 1024;
-  c->dyn = c->staged ? staged_bytes : (size_t)c->slice * sizeof(double);
+  c->dyn = c->staged ? staged_bytes : arnoldi_dyn_doubles(m, c->slice, false) * sizeof(double);
   if (c->dyn > 200 * 1024) return fail(IBDL_ERR_UNSUPPORTED, "too many boundary unknowns for the Arnoldi kernel");
   return IBDL_OK;
 }
@@ -834,9 +834,9 @@ static ibdl_status build_batch_graph(Batch* B, int prec, cudaGraphExec_t* out) {
     const int nd = (int)(B->off[b + 1] - B->off[b]);
     maxslice = std::max(maxslice, (nd + B->cl - 1) / B->cl);
   }
-  const size_t staged_bytes = arnoldi_staged_doubles(B->m, maxslice) * sizeof(double);
+  const size_t staged_bytes = arnoldi_dyn_doubles(B->m, maxslice, true) * sizeof(double);
   const bool staged = staged_bytes <= 200 * 1024;
-  const size_t dyn = staged ? staged_bytes : (size_t)maxslice * sizeof(double);
+  const size_t dyn = staged ? staged_bytes : arnoldi_dyn_doubles(B->m, maxslice, false) * sizeof(double);
   if (dyn > 200 * 1024) return fail(IBDL_ERR_UNSUPPORTED, "too many boundary unknowns for the Arnoldi kernel");
   static bool attrs = false;
   if (!attrs) {
