@@ -20,11 +20,15 @@
 //     FP64, taken once per CTA;
 //   - the old rotations are applied by one warp as a scan of the affine recurrence
 //     x_{i+1} = −s_i x_i + c_i h_{i+1} (x_0 = h_0), whose values give the rotated column
-//     H_i = c_i x_i + s_i h_{i+1}; 5 shuffle levels replace the 2j dependent operations.
+//     H_i = c_i x_i + s_i h_{i+1}; 5 shuffle levels replace the 2j dependent operations;
+//   - that warp, about 2 µs of dependent FP64 operations, runs beside the vector update (named
+//     barriers hand it ‖w₂‖), and short reductions (the ranks' partial sums, the Gram product)
+//     are spread over several warps so that no single SM sub-partition issues them all.
 // Partial sums of the cluster are combined through distributed shared memory. One cluster barrier
 // per step, and a split arrive/wait one so no CTA exits while another may still read its shared
-// memory. On the 512² Stokes star the step takes 14.5 µs standalone (16.8 µs with CGS2's two
-// reductions), and the solves keep their iteration counts.
+// memory. On the 512² Stokes star the step takes 12.4 µs standalone (14.4 µs with the rotation
+// after the update, 16.8 µs with CGS2's two reductions), and the solves keep their iteration
+// counts.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -65,6 +69,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 constexpr int ATH = 512;
+constexpr int ALEAD = ATH - 32;  // the thread of CTA 0 that returns a step's result (lane 0 of the rotation warp)
 
 // dynamic shared memory (doubles) of a step: w's slice, then (staged) m + 1 basis rows, then the
 // (m + 1)² Gram block
@@ -88,14 +93,20 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
   return __hiloint2double(__double2hiint(y) - k * (1 << 20), __double2loint(y));
 }
 
-// ws[e] −= Σ_{i≤j} h[i]·V_i[e] over the slice, the sum over i split into groups of threads
+// named barrier `id` over `n` threads (n a multiple of 32); id 0 is __syncthreads'
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+// ws[e] −= Σ_{i≤j} h[i]·V_i[e] over the slice, the sum over i split into groups of threads; run by
+// threads 0..NT−1, which synchronise on named barrier 1
+template <int NT>
 __device__ __forceinline__ void slice_update(const double* rows, size_t rstride, double* ws, int cnt, int j,
                                              const double* h, double* pw) {
   const int tid = threadIdx.x;
   auto vat = [&](int i, int e) -> double { return rows[(size_t)i * rstride + e]; };
-  const int G = cnt > 0 ? min(8, ATH / cnt) : 0;
+  const int G = cnt > 0 ? min(8, NT / cnt) : 0;
   if (G <= 1) {
-    for (int e = tid; e < cnt; e += ATH) {
+    for (int e = tid; e < cnt; e += NT) {
       double a0 = ws[e], a1 = 0.0;
       int i = 0;
       for (; i + 1 <= j; i += 2) {
@@ -105,7 +116,7 @@ __device__ __forceinline__ void slice_update(const double* rows, size_t rstride,
       if (i <= j) a0 -= h[i] * vat(i, e);
       ws[e] = a0 + a1;
     }
-    __syncthreads();
+    bar_sync(1, NT);
     return;
   }
   const int g = tid / cnt, e = tid - g * cnt;
@@ -119,13 +130,13 @@ __device__ __forceinline__ void slice_update(const double* rows, size_t rstride,
     if (i <= j) a0 += h[i] * vat(i, e);
     pw[g * cnt + e] = a0 + a1;
   }
-  __syncthreads();
+  bar_sync(1, NT);
   if (tid < cnt) {
     double s = 0.0;
     for (int q = 0; q < G; ++q) s += pw[q * cnt + tid];
     ws[tid] -= s;
   }
-  __syncthreads();
+  bar_sync(1, NT);
 }
 
 // Dot products of the pairs (a_d, b_d) over the slice, d < ndots: d ≤ j: (V_d, w); d = j + 1:
@@ -185,7 +196,7 @@ __device__ __forceinline__ void slice_dots_pairs(const double* rows, size_t rstr
 }
 
 // Returns −1 (every thread) when the step was skipped because the cycle had already stopped;
-// otherwise, on CTA 0 thread 0, 1 if this step stopped the cycle and 0 if it continues.
+// otherwise, on CTA 0 thread ALEAD, 1 if this step stopped the cycle and 0 if it continues.
 // Control flow is uniform over the cluster (the skip decision reads state no kernel of the
 // running application writes).
 //
@@ -202,7 +213,7 @@ __device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, in
   extern __shared__ double dsm[];
   __shared__ double part[2 * KMAX + 4], t[KMAX + 2], gc[KMAX + 2], h[KMAX + 2];
   __shared__ double pw[ATH], pw2[2 * KMAX + 8];
-  __shared__ double csl[KMAX], snl[KMAX], sc[8];
+  __shared__ double csl[KMAX], snl[KMAX], sc[8], qsum[4 * (2 * KMAX + 4)];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rank = (int)cluster.block_rank();
   const int lo = rank * slice;
@@ -251,36 +262,70 @@ __device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, in
   const int ndots = 2 * j + 3;
   slice_dots_pairs(rows, rstride, ws, cnt, j, ndots, pw, pw2, part);
   cluster.sync();
-  if (tid < ndots) {
-    double v[CL];
+  {  // the CL ranks' partial sums: quarter qq of the ranks per thread, then the four quarters
+    constexpr int QR = CL % 4 == 0 ? 4 : 1, PER = CL / QR;
+    for (int q = tid; q < QR * ndots; q += ATH) {
+      const int qq = q / ndots, d = q - qq * ndots;
+      double v[PER];
 #pragma unroll
-    for (int r = 0; r < CL; ++r) v[r] = cluster.map_shared_rank(part, r)[tid];
+      for (int r = 0; r < PER; ++r) v[r] = cluster.map_shared_rank(part, qq * PER + r)[d];
 #pragma unroll
-    for (int s2 = CL / 2; s2 > 0; s2 >>= 1)
+      for (int s2 = PER / 2; s2 > 0; s2 >>= 1)
 #pragma unroll
-      for (int r = 0; r < s2; ++r) v[r] += v[r + s2];
-    if (tid <= j)
-      t[tid] = v[0];
-    else if (tid == j + 1)
-      sc[6] = v[0];
-    else
-      gc[tid - j - 2] = v[0];
-  }
-  // every remote read of this step is done: arrive now, wait before leaving
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-  __syncthreads();
-  // h = (2I − G) t, one warp per row of G (rows and columns j from this step's reduction)
-  for (int i = warp; i <= j; i += ATH / 32) {
-    double a = 0.0;
-    for (int k = lane; k <= j; k += 32) {
-      const double gik = (i < j && k < j) ? Gs[i * (m + 1) + k] : (i == j ? gc[k] : gc[i]);
-      a += gik * t[k];
+        for (int r = 0; r < s2; ++r) v[r] += v[r + s2];
+      qsum[qq * ndots + d] = v[0];
     }
-    a = warp_sum(a);
-    if (lane == 0) h[i] = 2.0 * t[i] - a;
+    // every remote read of this step is done: arrive now, wait before leaving
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    __syncthreads();
+    if (tid < ndots) {
+      double v = qsum[tid];
+      if (QR == 4) v = (v + qsum[ndots + tid]) + (qsum[2 * ndots + tid] + qsum[3 * ndots + tid]);
+      if (tid <= j)
+        t[tid] = v;
+      else if (tid == j + 1)
+        sc[6] = v;
+      else
+        gc[tid - j - 2] = v;
+    }
   }
   __syncthreads();
-  if (warp == 0) {
+  {  // h = (2I − G) t: lanes own the rows, warps 4c..4c+3 split the k range of row chunk c in four
+    const int nr = j + 1, chunks = (nr + 31) >> 5, K4 = (nr + 3) >> 2;
+    if (warp < 4 * chunks) {
+      const int i = 32 * (warp >> 2) + lane;
+      const int k0 = (warp & 3) * K4, k1 = min(nr, k0 + K4);
+      // G is symmetric: read G[k][i] so that the lanes' rows are contiguous
+      auto gik = [&](int k) -> double {
+        return (i < j && k < j) ? Gs[k * (m + 1) + i] : (i == j ? gc[k] : gc[i]);
+      };
+      double a0 = 0.0, a1 = 0.0;
+      if (i < nr) {
+        int k = k0;
+        for (; k + 1 < k1; k += 2) {
+          a0 += gik(k) * t[k];
+          a1 += gik(k + 1) * t[k + 1];
+        }
+        if (k < k1) a0 += gik(k) * t[k];
+      }
+      pw[warp * 32 + lane] = a0 + a1;
+    }
+    __syncthreads();
+    if (tid < nr) {
+      const double* pr = pw + (tid >> 5) * 128 + (tid & 31);
+      h[tid] = 2.0 * t[tid] - ((pr[0] + pr[32]) + (pr[64] + pr[96]));
+    }
+    __syncthreads();
+  }
+
+  // Three roles from here, so that the rotation (one warp of CTA 0, a chain of dependent FP64
+  // operations) runs beside the vector update instead of after it:
+  //   warps 0..WQ−1: w₂ = w − V_j h over the slice, then v_{j+1} = w₂ / ‖w₂‖;
+  //   warp WQ: ‖w₂‖ and its reciprocal (named barrier 2 to the update warps, 3 to warp WG);
+  //   warp WG (CTA 0): the old rotations on h, then, with ‖w₂‖, the new rotation and the status.
+  constexpr int WQ = ATH / 32 - 2, WG = ATH / 32 - 1;
+  int ret = 0;
+  if (warp == WQ) {
     double q = 0.0;
     for (int i = lane; i <= j; i += 32) q += h[i] * t[i];
     q = warp_sum(q);
@@ -290,86 +335,94 @@ __device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, in
       sc[1] = isfinite(hn2) ? hn2 * y : hn2;  // NaN/Inf passed on to the status test
       sc[2] = y;
     }
-  }
-  slice_update(rows, rstride, ws, cnt, j, h, pw);
-  const double hn = sc[1], inv = sc[2];
-  for (int e = tid; e < cnt; e += ATH) w[e] = ws[e] * inv;
-  if (rank == 0 && tid <= j) {  // G's column and row j for the later steps of the cycle
-    st->G[tid * KMAX + j] = gc[tid];
-    st->G[j * KMAX + tid] = gc[tid];
-  }
-
-  int ret = 0;
-  if (rank == 0 && warp == 0) {
-    // old rotations on the new column by a scan over the affine maps f_i(x) = −s_i x + c_i h_{i+1}
-    const int i0 = 2 * lane, i1 = i0 + 1;
-    double a0 = 1.0, b0 = 0.0, a1 = 1.0, b1 = 0.0;
-    if (i0 < j) {
-      a0 = -snl[i0];
-      b0 = csl[i0] * h[i0 + 1];
-    }
-    if (i1 < j) {
-      a1 = -snl[i1];
-      b1 = csl[i1] * h[i1 + 1];
-    }
-    double A = a1 * a0, B = a1 * b0 + b1;  // f_{i1} ∘ f_{i0}
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const double Ap = __shfl_up_sync(0xffffffffu, A, off), Bp = __shfl_up_sync(0xffffffffu, B, off);
-      if (lane >= off) {
-        B = A * Bp + B;
-        A = A * Ap;
-      }
-    }
-    double Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
-    if (lane == 0) {
-      Ae = 1.0;
-      Be = 0.0;
-    }
-    const double x0 = h[0];
-    const double xa = Ae * x0 + Be;  // x_{i0}
-    const double xb = a0 * xa + b0;  // x_{i1}
-    double* hc = st->H + (size_t)j * (m + 1);
-    if (i0 < j) hc[i0] = csl[i0] * xa + snl[i0] * h[i0 + 1];
-    if (i1 < j) hc[i1] = csl[i1] * xb + snl[i1] * h[i1 + 1];
-    if (j == i0 || j == i1) {
-      // the new rotation zeroes hn below x_j
-      const double a = j == i0 ? xa : xb, b = hn;
-      const double q = a * a + b * b;
-      const double ir = q > 0x1p-1000 && q <= 1e300 ? rsqrt_newton(q) : (q > 0.0 ? 1.0 / sqrt(q) : 0.0);
-      const double r = q * ir;
-      const double c = q > 0.0 ? a * ir : 1.0, sn = b * ir;
-      hc[j] = r;
-      hc[j + 1] = 0.0;
-      st->cs[j] = c;
-      st->sn[j] = sn;
-      const double gj = sc[0];
-      st->g[j + 1] = -sn * gj;
-      st->g[j] = c * gj;
-      const double res = fabs(sn * gj);
-      st->res = res;
-      st->k = j + 1;
-      int stop = 0;
-      if (!isfinite(res) || !isfinite(hn) || !isfinite(a)) {
-        st->status = ST_NONFINITE;
-        stop = 1;
-      } else if (res <= sc[4]) {
-        st->status = ST_CONVERGED;
-        stop = 1;
-      } else if (hn == 0.0) {
-        st->status = ST_BREAKDOWN;
-        stop = 1;
-      } else if (j + 1 >= (int)sc[5]) {
-        stop = 1;  // cycle full
-      }
-      if (stop) st->stop = 1;
-      sc[3] = stop;
-    }
     __syncwarp();
-    if (lane == 0) ret = (int)sc[3];
+    bar_arrive(2, ATH);
+    if (rank == 0) bar_arrive(3, 64);
+  } else if (warp == WG) {
+    bar_arrive(2, ATH);
+    if (rank == 0) {
+      // old rotations on the new column by a scan over the affine maps f_i(x) = −s_i x + c_i h_{i+1}
+      const int i0 = 2 * lane, i1 = i0 + 1;
+      double a0 = 1.0, b0 = 0.0, a1 = 1.0, b1 = 0.0;
+      if (i0 < j) {
+        a0 = -snl[i0];
+        b0 = csl[i0] * h[i0 + 1];
+      }
+      if (i1 < j) {
+        a1 = -snl[i1];
+        b1 = csl[i1] * h[i1 + 1];
+      }
+      double A = a1 * a0, B = a1 * b0 + b1;  // f_{i1} ∘ f_{i0}
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const double Ap = __shfl_up_sync(0xffffffffu, A, off), Bp = __shfl_up_sync(0xffffffffu, B, off);
+        if (lane >= off) {
+          B = A * Bp + B;
+          A = A * Ap;
+        }
+      }
+      double Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+      if (lane == 0) {
+        Ae = 1.0;
+        Be = 0.0;
+      }
+      const double x0 = h[0];
+      const double xa = Ae * x0 + Be;  // x_{i0}
+      const double xb = a0 * xa + b0;  // x_{i1}
+      double* hc = st->H + (size_t)j * (m + 1);
+      if (i0 < j) hc[i0] = csl[i0] * xa + snl[i0] * h[i0 + 1];
+      if (i1 < j) hc[i1] = csl[i1] * xb + snl[i1] * h[i1 + 1];
+      __syncwarp();
+      bar_sync(3, 64);  // ‖w₂‖ from warp WQ
+      if (j == i0 || j == i1) {
+        // the new rotation zeroes hn below x_j
+        const double hn = sc[1];
+        const double a = j == i0 ? xa : xb, b = hn;
+        const double q = a * a + b * b;
+        const double ir = q > 0x1p-1000 && q <= 1e300 ? rsqrt_newton(q) : (q > 0.0 ? 1.0 / sqrt(q) : 0.0);
+        const double r = q * ir;
+        const double c = q > 0.0 ? a * ir : 1.0, sn = b * ir;
+        hc[j] = r;
+        hc[j + 1] = 0.0;
+        st->cs[j] = c;
+        st->sn[j] = sn;
+        const double gj = sc[0];
+        st->g[j + 1] = -sn * gj;
+        st->g[j] = c * gj;
+        const double res = fabs(sn * gj);
+        st->res = res;
+        st->k = j + 1;
+        int stop = 0;
+        if (!isfinite(res) || !isfinite(hn) || !isfinite(a)) {
+          st->status = ST_NONFINITE;
+          stop = 1;
+        } else if (res <= sc[4]) {
+          st->status = ST_CONVERGED;
+          stop = 1;
+        } else if (hn == 0.0) {
+          st->status = ST_BREAKDOWN;
+          stop = 1;
+        } else if (j + 1 >= (int)sc[5]) {
+          stop = 1;  // cycle full
+        }
+        if (stop) st->stop = 1;
+        sc[3] = stop;
+      }
+      __syncwarp();
+      if (lane == 0) ret = (int)sc[3];
+    }
+  } else {
+    slice_update<WQ * 32>(rows, rstride, ws, cnt, j, h, pw);
+    bar_sync(2, ATH);
+    const double inv = sc[2];
+    for (int e = tid; e < cnt; e += WQ * 32) w[e] = ws[e] * inv;
+    if (rank == 0 && tid <= j) {  // G's column and row j for the later steps of the cycle
+      st->G[tid * KMAX + j] = gc[tid];
+      st->G[j * KMAX + tid] = gc[tid];
+    }
   }
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-  return (rank == 0 && tid == 0) ? ret : 0;
+  return (rank == 0 && tid == ALEAD) ? ret : 0;
 }
 
 }  // namespace ibdl

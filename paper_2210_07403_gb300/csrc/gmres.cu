@@ -120,7 +120,7 @@ template <bool STAGED, int CL>
 __global__ void __launch_bounds__(ATH)
     k_arnoldi_cluster(GmresState* st, double* V, int j, int nd, int m, int slice, cudaGraphConditionalHandle cond) {
   const int r = arnoldi_body<STAGED, CL>(st, V, j, nd, m, slice);
-  if (cond && cg::this_cluster().block_rank() == 0 && threadIdx.x == 0) {
+  if (cond && cg::this_cluster().block_rank() == 0 && threadIdx.x == ALEAD) {
     if (r < 0) {
       st->stop = 1;
       cudaGraphSetConditional(cond, 0);
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(ATH)
     if (it > ctl->max_bodies || atomicAdd(&ctl->running, 0) <= 0) batch_end_loop(ctl, cond);
   }
   const int r = arnoldi_body<STAGED, CL>(st + b, V + voff[b], -1, nd_arr[b], m, slice_arr[b]);
-  if (lead && r == 1) {
+  if (cg::this_cluster().block_rank() == 0 && threadIdx.x == ALEAD && r == 1) {
     if (atomicSub(&ctl->running, 1) == 1) batch_end_loop(ctl, cond);
   }
 }
