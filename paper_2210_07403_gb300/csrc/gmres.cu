@@ -17,6 +17,7 @@
 #include <cooperative_groups.h>
 
 #include <chrono>
+#include <cstddef>
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
@@ -772,7 +773,7 @@ static ibdl_status batch_workspace(Batch* B, int m, const ArnoldiCfg& c) {
   IBDL_CUDA(cudaMalloc((void**)&B->V, sizeof(double) * vtot));
   if (!B->st) IBDL_CUDA(cudaMalloc(&B->st, sizeof(GmresState) * B->count));
   if (!B->ctl) IBDL_CUDA(cudaMalloc(&B->ctl, sizeof(BatchCtl)));
-  if (!B->host_st) IBDL_CUDA(cudaMallocHost(&B->host_st, sizeof(GmresState) * B->count));
+  if (!B->host_st) IBDL_CUDA(cudaMallocHost(&B->host_st, sizeof(HostStatus) * B->count));
   if (!B->vec) IBDL_CUDA(cudaMalloc((void**)&B->vec, sizeof(double) * 5 * B->total));
   if (!B->target) IBDL_CUDA(cudaMalloc((void**)&B->target, sizeof(double) * B->count));
   if (!B->active) IBDL_CUDA(cudaMalloc((void**)&B->active, sizeof(int) * B->count));
@@ -897,6 +898,16 @@ static ibdl_status build_batch_graph(Batch* B, int prec, cudaGraphExec_t* out) {
   return ret;
 }
 
+// the status header (HostStatus, the leading fields of GmresState) of every problem into
+// B->host_st: one strided copy of count × 48 bytes instead of the whole states
+static_assert(offsetof(GmresState, rnorm) == offsetof(HostStatus, rnorm) && sizeof(HostStatus) <= sizeof(GmresState),
+              "HostStatus mirrors the head of GmresState");
+static ibdl_status batch_status_to_host(Batch* B, cudaStream_t s) {
+  IBDL_CUDA(cudaMemcpy2DAsync(B->host_st, sizeof(HostStatus), B->st, sizeof(GmresState), sizeof(HostStatus),
+                              (size_t)B->count, cudaMemcpyDeviceToHost, s));
+  return IBDL_OK;
+}
+
 // one batched GMRES cycle on right-hand sides rhs (concatenated) from zero corrections, added
 // into x; per-problem targets in B->target, activity in B->active; returns the states on the host
 static ibdl_status batch_cycle(Batch* B, int prec, const double* rhs, double* x, int kmax, cudaStream_t s) {
@@ -910,7 +921,7 @@ static ibdl_status batch_cycle(Batch* B, int prec, const double* rhs, double* x,
   IBDL_CUDA(cudaGraphLaunch(B->exec[pi], s));
   kb_gmres_update<<<B->count, 256, 0, s>>>(st, B->V, B->d_voff, x, B->d_off, B->d_nd, B->m);
   IBDL_CUDA(cudaGetLastError());
-  IBDL_CUDA(cudaMemcpyAsync(B->host_st, st, sizeof(GmresState) * B->count, cudaMemcpyDeviceToHost, s));
+  IBDL_TRY(batch_status_to_host(B, s));
   IBDL_CUDA(cudaStreamSynchronize(s));
   BatchCtl hc;
   IBDL_CUDA(cudaMemcpy(&hc, ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost));
@@ -926,9 +937,9 @@ static ibdl_status batch_residual(Batch* B, const double* bvec, const double* x,
   kb_residual<<<B->count, 256, 0, s>>>(st, bvec, x ? Ax : nullptr, r, B->d_off, B->d_nd);
   B->launches += 1;
   IBDL_CUDA(cudaGetLastError());
-  IBDL_CUDA(cudaMemcpyAsync(B->host_st, st, sizeof(GmresState) * B->count, cudaMemcpyDeviceToHost, s));
+  IBDL_TRY(batch_status_to_host(B, s));
   IBDL_CUDA(cudaStreamSynchronize(s));
-  const GmresState* hs = static_cast<const GmresState*>(B->host_st);
+  const HostStatus* hs = static_cast<const HostStatus*>(B->host_st);
   rn.resize(B->count);
   for (int b = 0; b < B->count; ++b) rn[b] = hs[b].rnorm;
   return IBDL_OK;
@@ -972,7 +983,7 @@ ibdl_status batch_solve_impl(Batch* B, const double* Ub, double* Q, const ibdl_s
       if (active[b]) return true;
     return false;
   };
-  const GmresState* hs = static_cast<const GmresState*>(B->host_st);
+  const HostStatus* hs = static_cast<const HostStatus*>(B->host_st);
   int used = 0;  // loop bodies (the longest problem's iterations), counted against maxit
   if (o->precision != IBDL_MIXED) {
     // restarted GMRES(m) on every problem at once

@@ -166,7 +166,7 @@ struct Batch {
   double* V;
   void* st;              // device GmresState[count]
   void* ctl;             // device control block of the batched while loop
-  void* host_st;         // pinned copy of the states
+  void* host_st;         // pinned copy of the states' status headers (HostStatus per problem)
   double* vec;           // [5][total]: b, x, r, d, scratch
   double* target;        // device [count]
   int* active;           // device [count]
