@@ -203,10 +203,13 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   // wait, so every kernel before the previous one has completed by then: a prologue overlaps
   // its direct predecessor only (its wait still covers this grid's completion and writes).
   cudaTriggerProgrammaticLaunchCompletion();
-  if (p.stop && *p.stop) return;
+  // In a GMRES cycle the step just before this kernel writes the stop flag and the Krylov index:
+  // both loads go out together, then the branch
+  const int stopped = p.stop ? *p.stop : 0;
   const double* pin;
   double* pout;
   resolve_io(p, pin, pout);
+  if (stopped) return;
 
   // jump term: out = ±½·in (the gather kernel adds S*u afterwards); none for grid input
   if (!p.grid_in)
@@ -416,9 +419,13 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
       der1_s[i] = p.der1[i];
     }
   }
+  // The stop flag is final before the wait: it is written by the GMRES step (or the cycle start)
+  // at least two kernels back, which has completed once the direct predecessor passed its own
+  // wait and triggered this launch. So no dependent load follows the wait.
+  const bool stopped = p.stop && *p.stop;
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
-  if (p.stop && *p.stop) return;
+  if (stopped) return;
   __syncthreads();
   const ColumnIO<T> cio{p.spec, n, nh, k0, p.lc, C, p.R};
   // forward transform along y: the first stage reads the half spectra directly
@@ -544,9 +551,15 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   const int nitems = GMODE == G_GRID ? 0 : pr.cnt * 4;
   GatherItem<T> it0 = {};
   if ((int)threadIdx.x < nitems) it0 = gather_item(p, pr, threadIdx.x, r0);
+  // the stop flag and the Krylov index (the output column) are final before the wait: the GMRES
+  // step that writes them is three kernels back (see the column pass)
+  const bool stopped = p.stop && *p.stop;
+  const double* pin;
+  double* pout;
+  resolve_io(p, pin, pout);
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
-  if (p.stop && *p.stop) return;
+  if (stopped) return;
   __syncthreads();
   const RowZLoad<T> zl{p.spec, n, nh, r0, half, R};
   const cplx<T>* res = fft_run<T, true>(bufA, bufB, p.log2n, seqs, tws, zl, NoIO());
@@ -565,9 +578,6 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
     return;
   }
 
-  const double* pin;
-  double* pout;
-  resolve_io(p, pin, pout);
   // one thread per (point, stencil row in the band): the row's partial sum is added to Y
   for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
     const GatherItem<T> it = t == (int)threadIdx.x ? it0 : gather_item(p, pr, t, r0);
