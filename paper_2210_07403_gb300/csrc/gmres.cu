@@ -408,15 +408,18 @@ static cudaError_t arnoldi_attrs() {
   return e;
 }
 
-// Cluster size: 16 when a 16-CTA cluster of this kernel fits on the device, else 8. The basis
-// slices are staged in shared memory when w's slice and m + 1 basis rows fit.
+// Cluster size: 16 when a 16-CTA cluster of this kernel fits on the device, else 8
+// (IBDL_ARNOLDI_CLUSTER=8 selects 8 on any device). The basis slices are staged in shared memory
+// when w's slice and m + 1 basis rows fit.
 static ibdl_status arnoldi_cfg(Geometry* g, int m, ArnoldiCfg* c) {
   static int cl_choice = 0;
   if (!cl_choice) {
     IBDL_CUDA((arnoldi_attrs<true, 8>()));
     IBDL_CUDA((arnoldi_attrs<false, 8>()));
     cl_choice = 8;
-    if (arnoldi_attrs<true, 16>() == cudaSuccess && arnoldi_attrs<false, 16>() == cudaSuccess) {
+    const char* force = getenv("IBDL_ARNOLDI_CLUSTER");
+    const bool force8 = force && atoi(force) == 8;
+    if (!force8 && arnoldi_attrs<true, 16>() == cudaSuccess && arnoldi_attrs<false, 16>() == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(16);
       cfg.blockDim = dim3(ATH);
