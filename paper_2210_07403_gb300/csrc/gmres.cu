@@ -80,8 +80,11 @@ __device__ void stage_upper(const GmresState* s, int k, int m, double* Rc, doubl
 // host round trip.
 __global__ void __launch_bounds__(1024) k_gmres_start(GmresState* st, const double* __restrict__ r, double* V, int nd,
                                                       double target, int kmax, double rel = 0.0,
-                                                      double floor_rel = 0.0, int first = 0) {
+                                                      double floor_rel = 0.0, int first = 0,
+                                                      double* zero_x = nullptr) {
   __shared__ double red[32];
+  if (zero_x)  // the cycle's correction starts at zero (a refinement sweep)
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) zero_x[i] = 0.0;
   double s = 0;
   for (int i = threadIdx.x; i < nd; i += blockDim.x) s += r[i] * r[i];
   const double beta = sqrt(block_sum(s, red));
@@ -315,7 +318,17 @@ struct CycleResult {
   int its;
   int status;
   double res;
-  double beta;  // ‖r0‖ of the cycle
+  double beta;          // ‖r0‖ of the cycle
+  bool copied = false;  // the OutCopy ran after the cycle's update (so the caller's copy is current)
+};
+
+// A device copy enqueued after a cycle's update and before its status read, so that a solve whose
+// last cycle this is needs no further copy and synchronisation (the solution into the caller's
+// device buffer).
+struct OutCopy {
+  void* dst;
+  const void* src;
+  size_t bytes;
 };
 
 static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, int op, cudaGraphExec_t* out);
@@ -354,7 +367,7 @@ struct RelTarget {
 // and cr filled; without, the caller reads the state later (cycle_launches counts the kernels).
 static ibdl_status gmres_cycle_graph(Geometry* g, int prec, int op, const double* r0, double* x, double target,
                                      int m, int budget, cudaStream_t s, CycleResult* cr, const RelTarget& rt,
-                                     bool sync) {
+                                     bool sync, bool zero_x, const OutCopy* oc) {
   const int pi = 2 * op + (prec == IBDL_FP32 ? 1 : 0);
   if (!g->cycle_exec[pi] || g->cycle_m[pi] != m) {
     if (g->cycle_exec[pi]) cudaGraphExecDestroy(g->cycle_exec[pi]);
@@ -366,12 +379,17 @@ static ibdl_status gmres_cycle_graph(Geometry* g, int prec, int op, const double
   HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
   const int nd = geom_nd(g);
   const int steps = m < budget ? m : budget;
-  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, g->V, nd, target, steps, rt.rel, rt.floor_rel, rt.first);
+  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, g->V, nd, target, steps, rt.rel, rt.floor_rel, rt.first,
+                                   zero_x ? x : nullptr);
   IBDL_CUDA(cudaGetLastError());
   IBDL_CUDA(cudaGraphLaunch(g->cycle_exec[pi], s));
   k_gmres_update_par<<<(nd + 255) / 256, 256, 0, s>>>(st, g->V, x, nd, m);
   IBDL_CUDA(cudaGetLastError());
   if (!sync) return IBDL_OK;
+  if (oc) {
+    IBDL_CUDA(cudaMemcpyAsync(oc->dst, oc->src, oc->bytes, cudaMemcpyDeviceToDevice, s));
+    cr->copied = true;
+  }
   IBDL_CUDA(cudaMemcpyAsync(&hs[0], st, sizeof(HostStatus), cudaMemcpyDeviceToHost, s));
   IBDL_CUDA(cudaStreamSynchronize(s));
   const HostStatus fin = hs[0];
@@ -541,17 +559,18 @@ static ibdl_status build_cycle_graph(Geometry* g, int prec, int m, int op, cudaG
 // One GMRES(m) cycle on right-hand side r0 from a zero correction, accumulating into x.
 static ibdl_status gmres_cycle(Geometry* g, int prec, int op, const double* r0, double* x, double target, int m,
                                int budget, cudaStream_t s, CycleResult* cr, const RelTarget& rt = RelTarget(),
-                               bool sync = true) {
+                               bool sync = true, bool zero_x = false, const OutCopy* oc = nullptr) {
   GmresState* st = reinterpret_cast<GmresState*>(g->gm);
   HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
   const int nd = geom_nd(g);
   double* V = g->V;
-  if (!g->timing) return gmres_cycle_graph(g, prec, op, r0, x, target, m, budget, s, cr, rt, sync);
+  if (!g->timing) return gmres_cycle_graph(g, prec, op, r0, x, target, m, budget, s, cr, rt, sync, zero_x, oc);
   // host-driven loop (used while stage timing records an event around every kernel)
   const int steps = m < budget ? m : budget;
   ArnoldiCfg acfg;
   IBDL_TRY(arnoldi_cfg(g, m, &acfg));
-  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, V, nd, target, steps, rt.rel, rt.floor_rel, rt.first);
+  k_gmres_start<<<1, 1024, 0, s>>>(st, r0, V, nd, target, steps, rt.rel, rt.floor_rel, rt.first,
+                                   zero_x ? x : nullptr);
   g->launches += 1;
   IBDL_CUDA(cudaGetLastError());
   cudaEvent_t evs[2] = {g->ev, g->ev};
@@ -640,6 +659,10 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
   const bool mixed = o->precision == IBDL_MIXED;
   ibdl_solve_info inf = {};
   ibdl_status ret = IBDL_OK;
+  // a device Q is copied before each cycle's (sweep's) status read, so the last one leaves it current
+  const OutCopy qcopy = {Q, x, sizeof(double) * nd};
+  const OutCopy* oc = o->io_on_host ? nullptr : &qcopy;
+  bool q_current = false;
   if (!mixed) {
     // plain restarted GMRES(m) with FP64 (or FP32) applies
     int used = 0;
@@ -653,7 +676,8 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
         rt.rel = o->rtol;
         rt.first = 1;
       }
-      IBDL_TRY(gmres_cycle(g, o->precision, op, rhs, x, target, m, o->maxit - used, s, &cr, rt));
+      IBDL_TRY(gmres_cycle(g, o->precision, op, rhs, x, target, m, o->maxit - used, s, &cr, rt, true, false, oc));
+      q_current = cr.copied;  // the restart's residual below leaves x as it is
       if (cycle == 0) {
         bnorm = cr.beta;
         target = o->rtol * bnorm;
@@ -702,13 +726,12 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
     double bn = 0.0;
     bool done = false;
     for (int sweep = 0; !done; ++sweep) {
-      IBDL_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * nd, s));
       RelTarget rt;
       rt.rel = o->inner_rtol;
       rt.floor_rel = 0.5 * o->rtol;
       rt.first = sweep == 0;
       CycleResult cr = {};
-      IBDL_TRY(gmres_cycle(g, IBDL_FP32, op, rhs, d, 0.0, m, o->maxit - used, s, &cr, rt, false));
+      IBDL_TRY(gmres_cycle(g, IBDL_FP32, op, rhs, d, 0.0, m, o->maxit - used, s, &cr, rt, false, true));
       k_axpy<<<(nd + 255) / 256, 256, 0, s>>>(x, d, nd);
       g->launches += 1;
       IBDL_CUDA(cudaGetLastError());
@@ -716,6 +739,8 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
       k_residual<<<1, 1024, 0, s>>>(st, b, d, r, nd);
       g->launches += 1;
       IBDL_CUDA(cudaGetLastError());
+      if (oc) IBDL_CUDA(cudaMemcpyAsync(oc->dst, oc->src, oc->bytes, cudaMemcpyDeviceToDevice, s));
+      q_current = oc != nullptr;
       IBDL_CUDA(cudaMemcpyAsync(&hs[0], st, sizeof(HostStatus), cudaMemcpyDeviceToHost, s));
       IBDL_CUDA(cudaStreamSynchronize(s));
       const HostStatus fin = hs[0];
@@ -742,8 +767,10 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
     if (inf.rel_residual > o->rtol && ret == IBDL_OK)
       ret = fail(IBDL_ERR_NOT_CONVERGED, "mixed-precision refinement did not reach rtol");
   }
-  IBDL_CUDA(cudaMemcpyAsync(Q, x, sizeof(double) * nd, o->io_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
-  IBDL_CUDA(cudaStreamSynchronize(s));
+  if (!q_current) {
+    IBDL_CUDA(cudaMemcpyAsync(Q, x, sizeof(double) * nd, o->io_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    IBDL_CUDA(cudaStreamSynchronize(s));
+  }
   inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = inf;
   return ret;
