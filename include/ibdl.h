@@ -33,6 +33,14 @@
  * ibdl_last_error() returns a message describing the last error on the calling thread.
  *
  * Threads: a geometry may be used by one thread at a time; distinct geometries are independent.
+ *
+ * Environment (read once per process; for experiments, none is needed for correct results):
+ *   IBDL_NO_PDL=1            launch kernels without programmatic dependent launch;
+ *   IBDL_UNROLL=u (1..16)    GMRES iterations per body of a cycle's captured while loop (8);
+ *   IBDL_ARNOLDI_CLUSTER=8   run the Arnoldi step on 8-CTA clusters even where 16 fit;
+ *   IBDL_PLAN_R, IBDL_PLAN_C, IBDL_THREADS   2-D launch shape before autotuning (rows per CTA of
+ *                            the row kernels, columns per CTA of the column pass, threads);
+ *   IBDL_PLAN3_R, IBDL_PLAN3_C, IBDL_PLAN3_CZ   the same for the 3-D kernels.
  */
 #ifndef IBDL_H
 #define IBDL_H
