@@ -1,6 +1,6 @@
 """In-tree build of libibdl.so for GB300 (sm_103a) with nvcc.
 
-Every translation unit is compiled in parallel with one ``-gencode`` and linked into
+Every translation unit of csrc/ is compiled in parallel with one ``-gencode`` and linked into
 ``paper_2210_07403_gb300/libibdl.so`` (static CUDA runtime, no PyTorch dependency). Objects go to
 ``paper_2210_07403_gb300/_build/``. The build is skipped when the library is newer than every
 source and header.
@@ -19,7 +19,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libibdl.so")
-SOURCES = ["api.cu", "geometry.cu", "apply2d.cu", "apply3d.cu", "gmres.cu", "noalloc.cu", "batch.cu", "vjp.cu", "postproc.cu"]
+# every translation unit in csrc/: the host and driver units plus one unit per 2-D grid size
+# (apply2d_n*.cu) and per batched operator family (apply2d_batch_*.cu), compiled in parallel
+SOURCES = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
@@ -61,8 +63,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    # the slowest units first, so that they do not start last
+    order = sorted(SOURCES, key=lambda f: (not f.startswith("apply"), f))
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(SOURCES), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(compile_one, order))
     if verbose:
         for obj, log in results:
             sys.stderr.write(f"--- {os.path.basename(obj)}\n{log}")

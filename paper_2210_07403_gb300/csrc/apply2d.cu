@@ -1,660 +1,46 @@
-// Two-dimensional IBDL operator: spread → FFT → Fourier symbol → inverse FFT → interpolate.
-//
-// One application A Q = S* u + ½Q, u = −L⁻¹ S̃ Q (Sec. 5.3.2) or the Stokes velocity (Sec. 6.3.3),
-// runs as three kernels, each owning a disjoint piece of the grid (no global atomics on the grid
-// and no grid memset):
-//
-//   k_spread_rowfft   band of R rows: accumulate the dipole sources of every point whose 4×4
-//                     stencil meets the band (shared-memory atomics), FFT along x with two real
-//                     rows packed as one complex row, unpack to the packed half spectrum.
-//   k_colpass         group of C kx columns: FFT along y, Fourier symbol, inverse FFT along y.
-//   k_rowifft_gather  band of R rows: inverse FFT along x, then interpolate (S*) the band's part
-//                     of every point's stencil and add it to Y (which the first kernel set to ½Q).
-//
-// Packed half spectrum: for a real row a, A_k (k = 0..n/2) is stored in n/2 slots with slot 0
-// holding (A_0, A_{n/2}), both real. Along y, the kx = 0 and kx = n/2 columns are therefore one
-// complex column a + i b with a, b real columns; the column pass separates them by Hermitian
-// symmetry before the symbol and repacks after it.
-//
-// Band-major storage: the n rows of a field form bands of R rows (the row kernels' work unit),
-// and element (row, k) of field f sits at (f·n + band·R)·(n/2) + k·R + (row mod R). A row band is
-// one contiguous block, and a column reads R contiguous values per band (128 bytes at R = 16 in
-// FP32) whatever the number of columns a CTA takes.
+// Two-dimensional IBDL operator, host side: launch shapes, the application of each operator and
+// precision, batched launch tables, the autotuner and the source-term helpers. The kernels are in
+// apply2d_kernels.cuh; each grid size n = 2^L is compiled in its own unit (apply2d_n*.cu) and
+// reached through launch_apply_2d<T, OP, L>.
 #include <algorithm>
 #include <cstdlib>
 #include <mutex>
-#include <vector>
 #include <type_traits>
 #include <utility>
+#include <vector>
 
-#include "fft.cuh"
+#include "apply2d_launch.cuh"
 
 namespace ibdl {
 
-enum { OP_SCALAR_AN = 0, OP_SCALAR_SD = 1, OP_STOKES_AN = 2, OP_STOKES_SD = 3, OP_ADJ_AN = 4,
-       OP_ADJ_SD = 5, OP_STOKES_T = 6, OP_SL = 7 };
+IBDL_DECLARE_2D(4)
+IBDL_DECLARE_2D(5)
+IBDL_DECLARE_2D(6)
+IBDL_DECLARE_2D(7)
+IBDL_DECLARE_2D(8)
+IBDL_DECLARE_2D(9)
+IBDL_DECLARE_2D(10)
+IBDL_DECLARE_2D(11)
+IBDL_DECLARE_2D(12)
+IBDL_DECLARE_2D(13)
 
-// grid fields entering / leaving the Fourier stage, and boundary components in / out
-template <int OP>
-struct Traits;
-template <>
-struct Traits<OP_SCALAR_AN> { static constexpr int NIN = 1, NOUT = 1, C = 1; };  // f = S̃Q
-// (NMAX = max(NIN, NOUT) sizes the shared buffers of the column pass)
-template <>
-struct Traits<OP_SCALAR_SD> { static constexpr int NIN = 2, NOUT = 1, C = 1; };  // S(Qn_x), S(Qn_y)
-template <>
-struct Traits<OP_STOKES_AN> { static constexpr int NIN = 3, NOUT = 2, C = 2; };  // s, g_x, g_y
-template <>
-struct Traits<OP_STOKES_SD> { static constexpr int NIN = 4, NOUT = 2, C = 2; };  // s, A11, A22, A12
-template <>
-struct Traits<OP_ADJ_AN> { static constexpr int NIN = 1, NOUT = 1, C = 1; };     // S W
-template <>
-struct Traits<OP_ADJ_SD> { static constexpr int NIN = 1, NOUT = 2, C = 1; };     // S W → ∂_x v, ∂_y v
-// Stokes transpose (analytic dipole): ψ_x, ψ_y → v_s, v_gx, v_gy
-template <>
-struct Traits<OP_STOKES_T> { static constexpr int NIN = 2, NOUT = 3, C = 2; };
-// single layer S*(−L⁻¹)(S V): plain spread, −L⁻¹, plain interpolation, no jump term
-template <>
-struct Traits<OP_SL> { static constexpr int NIN = 1, NOUT = 1, C = 1; };
+extern template ibdl_status batch_launch_2d<float, OP_SCALAR_AN>(Batch*, int, const double*, double*, cudaStream_t);
+extern template ibdl_status batch_launch_2d<float, OP_SCALAR_SD>(Batch*, int, const double*, double*, cudaStream_t);
+extern template ibdl_status batch_launch_2d<float, OP_STOKES_AN>(Batch*, int, const double*, double*, cudaStream_t);
+extern template ibdl_status batch_launch_2d<float, OP_STOKES_SD>(Batch*, int, const double*, double*, cudaStream_t);
+extern template ibdl_status batch_launch_2d<double, OP_SCALAR_AN>(Batch*, int, const double*, double*, cudaStream_t);
+extern template ibdl_status batch_launch_2d<double, OP_SCALAR_SD>(Batch*, int, const double*, double*, cudaStream_t);
+extern template ibdl_status batch_launch_2d<double, OP_STOKES_AN>(Batch*, int, const double*, double*, cudaStream_t);
+extern template ibdl_status batch_launch_2d<double, OP_STOKES_SD>(Batch*, int, const double*, double*, cudaStream_t);
 
-enum { G_INTERP = 0, G_GRID = 1 };
+static int log2i(int n) { return __builtin_ctz(n); }
 
-constexpr int kThreads = 512;
-
-template <typename T>
-struct RowParams {
-  int n, log2n, R;
-  int M;
-  const int* cell_start;
-  const int* base;
-  const int* perm;
-  const T* phi;
-  const T* dphi;
-  const T* wscale;
-  const T* nrm;
-  const double* in;   // [c][M] density
-  double* out;        // [c][M] result (first kernel stores ½·in, last kernel adds S*u)
-  cplx<T>* spec;      // [nf][n][n/2]
-  const cplx<T>* tw;  // [n]
-  const int* stop;    // optional: skip all work when *stop != 0
-  double* grid;       // G_GRID: [nf][n][n]
-  const int* idx;     // optional: in += (*idx)·vstride, out += (*idx + 1)·vstride (Krylov basis)
-  int vstride;
-  int64_t io_off;     // batched launches: in = in_base + io_off, out = out_base + io_off
-  // scalar adjoint ops only: 1 = the Euclidean transpose Aᵀ = W A* W⁻¹ (W⁻¹λ spread with weight
-  // Δs/h^d is λ spread with weight h^−d = 1 · h^−d: the spread weight is 1 and the gathered values
-  // carry Δs/h^d instead of 1)
-  int trans;
-  const double* grid_in;  // optional [NIN][n][n]: the band rows are read from it instead of spread
-  double jump;            // jump term coefficient: ½ (Dirichlet), −½ (Neumann), 0 (single layer)
-  // completed method (Sec. 5.3.3, Sec. 6.3.3): the vectors hold ū after the c·M density values
-  int aug;                // 1: add ū_l to the boundary rows, write the rows η Σ_i Δs_i Q_{l,i}
-  double eta;             // η
-  double hd;              // h^d
-  T eta_src;              // weight of the ηSQ source: η (scalar) or η/μ (Stokes, projected part)
-  int tw_smem;            // 1: the twiddles are staged in shared memory; 0: read from p.tw (large n)
-};
-
-template <typename T>
-__device__ __forceinline__ void resolve_io(const RowParams<T>& p, const double*& in, double*& out) {
-  in = p.in;
-  out = p.out;
-  if (p.idx) {
-    const int k = *p.idx;
-    in += (size_t)k * p.vstride;
-    out += (size_t)(k + 1) * p.vstride;
-  }
-}
-
-template <typename T>
-struct ColParams {
-  int n, log2n, C, lc;
-  int R;  // rows per band of the band-major spectrum
-  T lam, scale;
-  T mu;   // viscosity (Brinkman: L = μΔ − λ)
-  const T* lap1;
-  const T* der1;
-  cplx<T>* spec;
-  const cplx<T>* tw;
-  const int* stop;
-  int tw_smem;  // 1: twiddles and symbol tables staged in shared memory; 0: read from global (large n)
-};
-
-// Sorted points whose base row lies in the cell rows [r0 − 3, r0 + R) (mod n): at most two
-// contiguous ranges of the cell-sorted order.
-struct PointRanges {
-  int s0, cnt1, s2, cnt;
-  __device__ int at(int t) const { return t < cnt1 ? s0 + t : s2 + (t - cnt1); }
-};
-__device__ __forceinline__ PointRanges band_points(const int* cell_start, int n, int r0, int R) {
-  PointRanges pr;
-  const int lo = r0 - 3, hi = r0 + R;
-  if (lo >= 0) {
-    pr.s0 = cell_start[lo];
-    pr.cnt1 = cell_start[hi] - pr.s0;
-    pr.s2 = 0;
-    pr.cnt = pr.cnt1;
-  } else {
-    pr.s0 = cell_start[lo + n];
-    pr.cnt1 = cell_start[n] - pr.s0;
-    pr.s2 = cell_start[0];
-    pr.cnt = pr.cnt1 + (cell_start[hi] - pr.s2);
-  }
-  return pr;
-}
-
-// ------------------------------------------------------------------------------------------
-// kernel 1: spread + forward FFT along x
-// ------------------------------------------------------------------------------------------
-// Bodies take the work unit (row band / column group) and the problem's number of units, so
-// the same code serves one problem (unit = blockIdx.x) and a batch of problems (unit from a
-// (problem, unit) table).
-// One spread work item (point, stencil node): everything but the density, read from the geometry's
-// point tables, which no kernel writes (so a kernel may load them before its dependency wait).
-template <typename T>
-struct SpreadItem {
-  int lr, i, col;
-  T px, py, dpx, dpy, ws, nx, ny;
-};
-template <typename T>
-__device__ __forceinline__ SpreadItem<T> spread_item(const RowParams<T>& p, const PointRanges& pr, int t, int r0) {
-  const int n = p.n, M = p.M;
-  const int s = pr.at(t >> 4);
-  const int ay = (t >> 2) & 3, ax = t & 3;
-  SpreadItem<T> it;
-  it.lr = (((p.base[M + s] + ay) & (n - 1)) - r0) & (n - 1);
-  it.i = p.perm[s];
-  it.col = (p.base[s] + ax) & (n - 1);
-  it.px = p.phi[(0 * 4 + ax) * M + s];
-  it.py = p.phi[(1 * 4 + ay) * M + s];
-  it.dpx = p.dphi[(0 * 4 + ax) * M + s];
-  it.dpy = p.dphi[(1 * 4 + ay) * M + s];
-  it.ws = p.wscale[s];
-  it.nx = p.nrm[s];
-  it.ny = p.nrm[M + s];
-  return it;
-}
-
-template <typename T, int OP>
-__device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int unit, int nunits,
-                                                   unsigned char* smem_raw) {
-  constexpr int NIN = Traits<OP>::NIN;
-  constexpr int NC = Traits<OP>::C;
-  const int n = p.n, R = p.R, half = R >> 1, M = p.M;
-  const int seqs = NIN * half;
-  cplx<T>* tws_s = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* bufA = tws_s + (p.tw_smem ? n : 0);
-  cplx<T>* bufB = bufA + padded((size_t)seqs * n);
-  const cplx<T>* tws = p.tw_smem ? tws_s : p.tw;
-  // accumulation view: field f, local row lr, column x → complex element e = (f·half + lr/2)·n + x
-  // of the padded buffer, real part for even lr and imaginary part for odd lr
-  T* acc = reinterpret_cast<T*>(bufA);
-  const int r0 = unit * R;
-  // prologue independent of the previous kernel, then wait for it (programmatic launch)
-  for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
-  if (p.tw_smem) load_twiddles(tws_s, p.tw, n);
-  // the points whose stencil meets the band, and this thread's first work item (16 per point)
-  const PointRanges pr = band_points(p.cell_start, n, r0, R);
-  const int nitems = p.grid_in ? 0 : pr.cnt * 16;
-  SpreadItem<T> it0 = {};
-  if ((int)threadIdx.x < nitems) it0 = spread_item(p, pr, threadIdx.x, r0);
-  cudaGridDependencySynchronize();
-  // Let the next kernel launch and run its prologue. Triggered only after this kernel's own
-  // wait, so every kernel before the previous one has completed by then: a prologue overlaps
-  // its direct predecessor only (its wait still covers this grid's completion and writes).
-  cudaTriggerProgrammaticLaunchCompletion();
-  // In a GMRES cycle the step just before this kernel writes the stop flag and the Krylov index:
-  // both loads go out together, then the branch
-  const int stopped = p.stop ? *p.stop : 0;
-  const double* pin;
-  double* pout;
-  resolve_io(p, pin, pout);
-  if (stopped) return;
-
-  // jump term: out = ±½·in (the gather kernel adds S*u afterwards); none for grid input
-  if (!p.grid_in)
-    for (int i = unit * blockDim.x + threadIdx.x; i < NC * M; i += nunits * blockDim.x)
-      pout[i] = p.jump * pin[i] + (p.aug ? pin[NC * M + i / M] : 0.0);
-  if (p.aug && unit == 0) {
-    // constraint rows of the completed method: η Σ_i Δs_i Q_{l,i} (Δs = wscale·h^d); the
-    // partial sums use the second FFT buffer, which the FFT's first stage writes later
-    double* red = reinterpret_cast<double*>(bufB);
-    for (int l = 0; l < NC; ++l) {
-      double v = 0.0;
-      for (int s = threadIdx.x; s < M; s += blockDim.x) v += double(p.wscale[s]) * pin[(size_t)l * M + p.perm[s]];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-      __syncthreads();
-      if (threadIdx.x < 32) {
-        double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0) pout[NC * M + l] = p.eta * p.hd * t;
-      }
-      __syncthreads();
-    }
-  }
-  __syncthreads();
-
-  if (p.grid_in) {
-    for (int t = threadIdx.x; t < NIN * R * n; t += blockDim.x) {
-      const int f = t / (R * n);
-      const int rem = t - f * R * n;
-      const int lr = rem / n, x = rem - lr * n;
-      acc[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)] = T(p.grid_in[((size_t)f * n + r0 + lr) * n + x]);
-    }
-  }
-
-  // one thread per (point, stencil node): 16 work items per point whose stencil meets the band
-  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
-    const SpreadItem<T> it = t == (int)threadIdx.x ? it0 : spread_item(p, pr, t, r0);
-    const int lr = it.lr;
-    if (lr >= R) continue;
-    const int i = it.i;
-    const T px = it.px, py = it.py, ws = it.ws, nx = it.nx, ny = it.ny;
-    const int e = (lr >> 1) * n + it.col;  // field 0; field f adds f·half·n
-    const int odd = lr & 1;
-    const T pp = px * py;
-    if (OP == OP_SCALAR_AN) {
-      const T q = T(pin[i]) * ws;
-      const T ddx = it.dpx * py, ddy = px * it.dpy;
-      // dipole source n·∇δ_h, plus ηδ_h for the completed method
-      atomicAdd(acc + 2 * pidx(e) + odd, q * (nx * ddx + ny * ddy + p.eta_src * pp));
-    } else if (OP == OP_SCALAR_SD) {
-      const T q = T(pin[i]) * ws * pp;
-      atomicAdd(acc + 2 * pidx(e) + odd, q * nx);
-      atomicAdd(acc + 2 * pidx(e + half * n) + odd, q * ny);
-    } else if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
-      const T qx = T(pin[i]), qy = T(pin[M + i]);
-      const T c0 = ws * (qx * nx + qy * ny);  // Q·n
-      const T c1 = ws * (T(2) * qx * nx);     // A_xx
-      const T c2 = ws * (T(2) * qy * ny);     // A_yy
-      const T c3 = ws * (qx * ny + qy * nx);  // A_xy
-      atomicAdd(acc + 2 * pidx(e) + odd, c0 * pp);
-      if (OP == OP_STOKES_AN) {
-        const T ddx = it.dpx * py, ddy = px * it.dpy;
-        // g_x = ∂_x S(A_xx) + ∂_y S(A_xy), g_y = ∂_x S(A_xy) + ∂_y S(A_yy); the completed method
-        // adds (η/μ) S(Q) to the projected source
-        const T ce = p.eta_src * ws * pp;
-        atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * ddx + c3 * ddy + ce * qx);
-        atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c3 * ddx + c2 * ddy + ce * qy);
-      } else {
-        atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * pp);
-        atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c2 * pp);
-        atomicAdd(acc + 2 * pidx(e + 3 * half * n) + odd, c3 * pp);
-      }
-    } else if (OP == OP_STOKES_T) {
-      // ψ_l = Σ_j μ_{l,j} Φ(x − X_j): the transpose of S*, unweighted
-      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * pp);
-      atomicAdd(acc + 2 * pidx(e + half * n) + odd, T(pin[M + i]) * pp);
-    } else {
-      // plain spread of W (A*: weight Δs/h^d), or of λ (Aᵀ: weight 1, Δs/h^d moves to the gather)
-      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * (p.trans ? T(1) : ws) * pp);
-    }
-  }
-  __syncthreads();
-
-  const cplx<T>* res = fft_run<T, false>(bufA, bufB, p.log2n, seqs, tws);
-
-  // unpack Z = FFT(a + i b) of the row pair (2j, 2j + 1) into A = FFT(a) (even rows) and
-  // B = FFT(b) (odd rows), k = 0..n/2, packed format; thread t writes element t of the field's
-  // band-major block, k·R + rr, so consecutive threads write consecutive addresses
-  const int nh = n >> 1, lnh = p.log2n - 1, lR = __ffs(R) - 1;
-  for (int t = threadIdx.x; t < NIN * nh * R; t += blockDim.x) {
-    const int rr = t & (R - 1), k = (t >> lR) & (nh - 1), f = t >> (lR + lnh);
-    const int zb = (f * half + (rr >> 1)) * n;
-    cplx<T> v;
-    if (k == 0) {
-      const cplx<T> z0 = res[pidx(zb)], zh = res[pidx(zb + nh)];
-      v = (rr & 1) ? mk(z0.y, zh.y) : mk(z0.x, zh.x);
-    } else {
-      const cplx<T> zk = res[pidx(zb + k)], zc = res[pidx(zb + n - k)];
-      v = (rr & 1) ? mk(T(0.5) * (zk.y + zc.y), T(0.5) * (zc.x - zk.x))
-                   : mk(T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y));
-    }
-    p.spec[((size_t)f * n + r0) * nh + (t - f * (nh << lR))] = v;
-  }
-}
-
-template <typename T, int OP>
-__global__ void __launch_bounds__(kThreads) k_spread_rowfft(RowParams<T> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  spread_rowfft_body<T, OP>(p, blockIdx.x, gridDim.x, smem_raw);
-}
-
-// ------------------------------------------------------------------------------------------
-// Fourier symbols: NIN transformed fields in → NOUT out at wavenumber indices (kx, ky)
-// ------------------------------------------------------------------------------------------
-template <typename T, int OP>
-__device__ __forceinline__ void apply_symbol(const ColParams<T>& p, const T* lap1, const T* der1, int kx, int ky,
-                                             const cplx<T>* in, cplx<T>* out) {
-  const T lap = lap1[kx] + lap1[ky];
-  const T dkx = der1[kx], dky = der1[ky];
-  if (OP == OP_SCALAR_AN || OP == OP_SCALAR_SD || OP == OP_ADJ_AN || OP == OP_ADJ_SD || OP == OP_SL) {
-    // −L⁻¹ ↦ 1/(|k|² + λ), zero mode dropped when λ = 0 (Δ₀⁻¹)
-    const T den = lap + p.lam;
-    const T sig = den != T(0) ? p.scale / den : T(0);
-    if (OP == OP_SCALAR_AN || OP == OP_ADJ_AN || OP == OP_SL) {
-      out[0] = cscale(in[0], sig);
-    } else if (OP == OP_SCALAR_SD) {
-      // ∇·F ↦ i(k̃_x F̂_x + k̃_y F̂_y)
-      const cplx<T> d = cadd(cscale(in[0], dkx), cscale(in[1], dky));
-      out[0] = cscale(cmuli(d), sig);
-    } else {
-      const cplx<T> v = cscale(in[0], sig);
-      out[0] = cscale(cmuli(v), dkx);
-      out[1] = cscale(cmuli(v), dky);
-    }
-  } else if (OP == OP_STOKES_T) {
-    // transpose of the Stokes multiplier (conjugate symbol): v̂_s = −i k̃·ψ̂/|k|², v̂_g = P̂ψ̂/|k|²
-    const T inv = lap != T(0) ? T(1) / lap : T(0);
-    const cplx<T> kp = cadd(cscale(in[0], dkx), cscale(in[1], dky));
-    const T sc = inv * p.scale;
-    // Brinkman (λ > 0): the projected part carries μ/(μ|k|² + λ) in place of 1/|k|²
-    const T sg = p.lam > T(0) ? p.mu / (p.mu * lap + p.lam) * p.scale : sc;
-    out[0] = cscale(cmuli(kp), -sc);
-    out[1] = cscale(csub(in[0], cscale(kp, dkx * inv)), sg);
-    out[2] = cscale(csub(in[1], cscale(kp, dky * inv)), sg);
-  } else {
-    // Stokes, interior, η = 0: û = (i k̃ ŝ + P̂ ĝ)/|k|², P̂ = I − k̃k̃ᵀ/|k|²
-    const T inv = lap != T(0) ? T(1) / lap : T(0);
-    cplx<T> gx, gy;
-    if (OP == OP_STOKES_AN) {
-      gx = in[1];
-      gy = in[2];
-    } else {  // ĝ_l = i k̃_m Â_lm with fields A11, A22, A12 in slots 1, 2, 3
-      gx = cmuli(cadd(cscale(in[1], dkx), cscale(in[3], dky)));
-      gy = cmuli(cadd(cscale(in[3], dkx), cscale(in[2], dky)));
-    }
-    const cplx<T> kg = cadd(cscale(gx, dkx), cscale(gy, dky));
-    const cplx<T> is = cmuli(in[0]);
-    const T sc = inv * p.scale;
-    if (p.lam > T(0)) {
-      // Brinkman (Sec. 6.3.2): û = i k̃ ŝ/|k|² + μ P̂ ĝ/(μ|k|² + λ), defined at k = 0 as well
-      const T sg = p.mu / (p.mu * lap + p.lam) * p.scale;
-      out[0] = cadd(cscale(is, dkx * sc), cscale(csub(gx, cscale(kg, dkx * inv)), sg));
-      out[1] = cadd(cscale(is, dky * sc), cscale(csub(gy, cscale(kg, dky * inv)), sg));
-    } else {
-      out[0] = cscale(cadd(cscale(is, dkx), csub(gx, cscale(kg, dkx * inv))), sc);
-      out[1] = cscale(cadd(cscale(is, dky), csub(gy, cscale(kg, dky * inv))), sc);
-    }
-  }
-}
-
-// ------------------------------------------------------------------------------------------
-// kernel 2: FFT along y, symbol, inverse FFT along y, for C kx columns per CTA
-// ------------------------------------------------------------------------------------------
-// element m of column sequence bi = f·C + c, straight from / to the band-major half spectra
-template <typename T>
-struct ColumnIO {
-  cplx<T>* spec;
-  int n, nh, k0, lc, C, R;
-  __device__ __forceinline__ size_t at(int bi, int m) const {
-    return ((size_t)(bi >> lc) * n + (m & ~(R - 1))) * nh + (size_t)(k0 + (bi & (C - 1))) * R + (m & (R - 1));
-  }
-  __device__ __forceinline__ cplx<T> load(int bi, int m) const { return spec[at(bi, m)]; }
-  __device__ __forceinline__ void store(int bi, int m, cplx<T> v) const { spec[at(bi, m)] = v; }
-};
-
-template <typename T, int OP>
-__device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, unsigned char* smem_raw) {
-  constexpr int NIN = Traits<OP>::NIN;
-  constexpr int NOUT = Traits<OP>::NOUT;
-  constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
-  const int n = p.n, C = p.C, nh = n >> 1;
-  cplx<T>* tws_s = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* bufA = tws_s + (p.tw_smem ? n : 0);
-  cplx<T>* bufB = bufA + padded((size_t)NMAX * C * n);
-  T* lap1_s = reinterpret_cast<T*>(bufB + padded((size_t)NMAX * C * n));
-  T* der1_s = lap1_s + n;
-  const cplx<T>* tws = p.tw_smem ? tws_s : p.tw;
-  const T* lap1 = p.tw_smem ? lap1_s : p.lap1;
-  const T* der1 = p.tw_smem ? der1_s : p.der1;
-  const int k0 = unit * C;
-  if (p.tw_smem) {
-    load_twiddles(tws_s, p.tw, n);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      lap1_s[i] = p.lap1[i];
-      der1_s[i] = p.der1[i];
-    }
-  }
-  // The stop flag is final before the wait: it is written by the GMRES step (or the cycle start)
-  // at least two kernels back, which has completed once the direct predecessor passed its own
-  // wait and triggered this launch. So no dependent load follows the wait.
-  const bool stopped = p.stop && *p.stop;
-  cudaGridDependencySynchronize();
-  cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
-  if (stopped) return;
-  __syncthreads();
-  const ColumnIO<T> cio{p.spec, n, nh, k0, p.lc, C, p.R};
-  // forward transform along y: the first stage reads the half spectra directly
-  cplx<T>* res = fft_run<T, false>(bufA, bufB, p.log2n, NIN * C, tws, cio, NoIO());
-  cplx<T>* other = res == bufA ? bufB : bufA;
-
-  for (int t = threadIdx.x; t < (C << p.log2n); t += blockDim.x) {
-    const int c = t >> p.log2n, ky = t & (n - 1);
-    const int kx = k0 + c;
-    cplx<T> in[NIN], out[NOUT];
-    if (kx != 0) {
-#pragma unroll
-      for (int f = 0; f < NIN; ++f) in[f] = res[pidx((f * C + c) * n + ky)];
-      apply_symbol<T, OP>(p, lap1, der1, kx, ky, in, out);
-#pragma unroll
-      for (int f = 0; f < NOUT; ++f) res[pidx((f * C + c) * n + ky)] = out[f];
-    } else if (ky <= nh) {
-      // packed kx = 0 | kx = n/2 column: P = Â + i B̂ with Â, B̂ Hermitian in ky
-      const int j = ky, jp = (n - ky) & (n - 1);
-      cplx<T> Aj[NIN], Ajp[NIN], Bj[NIN], Bjp[NIN];
-#pragma unroll
-      for (int f = 0; f < NIN; ++f) {
-        const cplx<T> P = res[pidx((f * C + c) * n + j)];
-        const cplx<T> Pp = res[pidx((f * C + c) * n + jp)];
-        // Â(j) = (P(j) + conj P(−j))/2, B̂(j) = −i (P(j) − conj P(−j))/2
-        Aj[f] = mk(T(0.5) * (P.x + Pp.x), T(0.5) * (P.y - Pp.y));
-        Bj[f] = mk(T(0.5) * (P.y + Pp.y), T(0.5) * (Pp.x - P.x));
-        Ajp[f] = mk(T(0.5) * (Pp.x + P.x), T(0.5) * (Pp.y - P.y));
-        Bjp[f] = mk(T(0.5) * (Pp.y + P.y), T(0.5) * (P.x - Pp.x));
-      }
-      cplx<T> oA[NOUT], oB[NOUT], oAp[NOUT], oBp[NOUT];
-      apply_symbol<T, OP>(p, lap1, der1, 0, j, Aj, oA);
-      apply_symbol<T, OP>(p, lap1, der1, nh, j, Bj, oB);
-      apply_symbol<T, OP>(p, lap1, der1, 0, jp, Ajp, oAp);
-      apply_symbol<T, OP>(p, lap1, der1, nh, jp, Bjp, oBp);
-#pragma unroll
-      for (int f = 0; f < NOUT; ++f) {
-        res[pidx((f * C + c) * n + j)] = cadd(oA[f], cmuli(oB[f]));
-        if (jp != j) res[pidx((f * C + c) * n + jp)] = cadd(oAp[f], cmuli(oBp[f]));
-      }
-    }
-  }
-  __syncthreads();
-  // inverse transform along y: the last stage writes the half spectra directly
-  fft_run<T, true>(res, other, p.log2n, NOUT * C, tws, NoIO(), cio);
-}
-
-template <typename T, int OP>
-__global__ void __launch_bounds__(kThreads) k_colpass(ColParams<T> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  colpass_body<T, OP>(p, blockIdx.x, smem_raw);
-}
-
-// ------------------------------------------------------------------------------------------
-// kernel 3: inverse FFT along x, then interpolation (or write the grid)
-// ------------------------------------------------------------------------------------------
-// Z_m = A_m + i B_m (m = 0..n−1) for the row pair (r0 + 2j, r0 + 2j + 1) of field f, sequence
-// sq = f·half + j, rebuilt on the fly from the band-major half spectra (A_{n−k} = conj A_k):
-// A_k at band offset k·R + 2j, B_k next to it.
-template <typename T>
-struct RowZLoad {
-  const cplx<T>* spec;
-  int n, nh, r0, half, R;
-  __device__ __forceinline__ cplx<T> load(int sq, int m) const {
-    const int f = sq / half, j = sq - f * half;
-    const cplx<T>* band = spec + ((size_t)f * n + r0) * nh + 2 * j;
-    if (m == 0 || m == nh) {
-      const cplx<T> A = band[0], B = band[1];
-      return m == 0 ? mk(A.x, B.x) : mk(A.y, B.y);
-    }
-    if (m < nh) {
-      const cplx<T> A = band[(size_t)m * R], B = band[(size_t)m * R + 1];
-      return mk(A.x - B.y, A.y + B.x);
-    }
-    const cplx<T> A = band[(size_t)(n - m) * R], B = band[(size_t)(n - m) * R + 1];
-    return mk(A.x + B.y, B.x - A.y);
-  }
-};
-
-// One gather work item (point, stencil row): the point-table values it needs
-template <typename T>
-struct GatherItem {
-  int lr, i, bx;
-  T py, dy, ws, nx, ny;
-  T px[4], dx[4];
-};
-template <typename T>
-__device__ __forceinline__ GatherItem<T> gather_item(const RowParams<T>& p, const PointRanges& pr, int t, int r0) {
-  const int n = p.n, M = p.M;
-  const int s = pr.at(t >> 2);
-  const int ay = t & 3;
-  GatherItem<T> it;
-  it.lr = (((p.base[M + s] + ay) & (n - 1)) - r0) & (n - 1);
-  it.i = p.perm[s];
-  it.bx = p.base[s];
-  it.py = p.phi[(1 * 4 + ay) * M + s];
-  it.dy = p.dphi[(1 * 4 + ay) * M + s];
-  it.ws = p.wscale[s];
-  it.nx = p.nrm[s];
-  it.ny = p.nrm[M + s];
-#pragma unroll
-  for (int ax = 0; ax < 4; ++ax) {
-    it.px[ax] = p.phi[(0 * 4 + ax) * M + s];
-    it.dx[ax] = p.dphi[(0 * 4 + ax) * M + s];
-  }
-  return it;
-}
-
-template <typename T, int OP, int GMODE>
-__device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int unit, unsigned char* smem_raw) {
-  constexpr int NOUT = Traits<OP>::NOUT;
-  const int n = p.n, R = p.R, half = R >> 1, M = p.M, nh = n >> 1;
-  const int seqs = NOUT * half;
-  cplx<T>* tws_s = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* bufA = tws_s + (p.tw_smem ? n : 0);
-  cplx<T>* bufB = bufA + padded((size_t)seqs * n);
-  const cplx<T>* tws = p.tw_smem ? tws_s : p.tw;
-  const int r0 = unit * R;
-  if (p.tw_smem) load_twiddles(tws_s, p.tw, n);
-  // the points whose stencil meets the band and this thread's first work item (4 per point),
-  // loaded before the wait: the point tables are constant
-  const PointRanges pr = band_points(p.cell_start, n, r0, R);
-  const int nitems = GMODE == G_GRID ? 0 : pr.cnt * 4;
-  GatherItem<T> it0 = {};
-  if ((int)threadIdx.x < nitems) it0 = gather_item(p, pr, threadIdx.x, r0);
-  // the stop flag and the Krylov index (the output column) are final before the wait: the GMRES
-  // step that writes them is three kernels back (see the column pass)
-  const bool stopped = p.stop && *p.stop;
-  const double* pin;
-  double* pout;
-  resolve_io(p, pin, pout);
-  cudaGridDependencySynchronize();
-  cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
-  if (stopped) return;
-  __syncthreads();
-  const RowZLoad<T> zl{p.spec, n, nh, r0, half, R};
-  const cplx<T>* res = fft_run<T, true>(bufA, bufB, p.log2n, seqs, tws, zl, NoIO());
-  // real values: field f, local row lr, column x at element e = (f·half + lr/2)·n + x, part lr & 1
-  const T* u = reinterpret_cast<const T*>(res);
-
-  if (GMODE == G_GRID) {
-    for (int t = threadIdx.x; t < NOUT * R * n; t += blockDim.x) {
-      const int f = t / (R * n);
-      const int rem = t - f * R * n;
-      const int lr = rem / n, x = rem - lr * n;
-      // the completed method's field is u₀ + ū (ū after the density in the input vector)
-      const double ub = p.aug ? p.in[(size_t)Traits<OP>::C * M + f] : 0.0;
-      p.grid[((size_t)f * n + r0 + lr) * n + x] = double(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)]) + ub;
-    }
-    return;
-  }
-
-  // one thread per (point, stencil row in the band): the row's partial sum is added to Y
-  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
-    const GatherItem<T> it = t == (int)threadIdx.x ? it0 : gather_item(p, pr, t, r0);
-    const int lr = it.lr;
-    if (lr >= R) continue;
-    const int i = it.i;
-    const int bx = it.bx;
-    const T py = it.py;
-    const T dy = (OP == OP_ADJ_AN || OP == OP_STOKES_T) ? it.dy : T(0);
-    const int eb = (lr >> 1) * n, odd = lr & 1;
-    if (OP == OP_STOKES_T) {
-      // a_s = Σ v_s Φ, G_mk = Σ v_gm ∂_kΦ; out_l += (Δs/h²)[n_l a_s + Σ_k n_k (G_lk + G_kl)]
-      T as = 0, gxx = 0, gxy = 0, gyx = 0, gyy = 0;
-#pragma unroll
-      for (int ax = 0; ax < 4; ++ax) {
-        const int col = (bx + ax) & (n - 1);
-        const T px = it.px[ax], dx = it.dx[ax];
-        const T vs = u[2 * pidx(eb + col) + odd];
-        const T vx = u[2 * pidx(eb + half * n + col) + odd];
-        const T vy = u[2 * pidx(eb + 2 * half * n + col) + odd];
-        as += vs * px * py;
-        gxx += vx * dx * py;
-        gxy += vx * px * dy;
-        gyx += vy * dx * py;
-        gyy += vy * px * dy;
-      }
-      const double ws = double(it.ws), nx = double(it.nx), ny = double(it.ny);
-      const double cross = double(gxy) + double(gyx);
-      atomicAdd(pout + i, ws * (nx * double(as) + 2.0 * nx * double(gxx) + ny * cross));
-      atomicAdd(pout + M + i, ws * (ny * double(as) + nx * cross + 2.0 * ny * double(gyy)));
-      continue;
-    }
-    T acc0 = 0, acc1 = 0;
-#pragma unroll
-    for (int ax = 0; ax < 4; ++ax) {
-      const int col = (bx + ax) & (n - 1);
-      const T px = it.px[ax];
-      const T v0 = u[2 * pidx(eb + col) + odd];
-      if (OP == OP_ADJ_AN) {
-        acc0 += v0 * it.dx[ax] * py;
-        acc1 += v0 * px * dy;
-      } else {
-        const T pp = px * py;
-        acc0 += v0 * pp;
-        if (NOUT == 2) acc1 += u[2 * pidx(eb + half * n + col) + odd] * pp;
-      }
-    }
-    if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
-      atomicAdd(pout + i, double(acc0));
-      atomicAdd(pout + M + i, double(acc1));
-    } else if (OP == OP_ADJ_AN || OP == OP_ADJ_SD) {
-      // analytic: (S̃)* v = n · (kernel-gradient gather of v); spectral: −Σ_m n_m S*(∂_m v)
-      double val = double(it.nx) * double(acc0) + double(it.ny) * double(acc1);
-      if (OP == OP_ADJ_SD) val = -val;
-      if (p.trans) val *= double(it.ws);  // Δs/h^d · (S̃)* … for Aᵀ
-      atomicAdd(pout + i, val);
-    } else {
-      atomicAdd(pout + i, double(acc0));
-    }
-  }
-}
-
-template <typename T, int OP, int GMODE>
-__global__ void __launch_bounds__(kThreads) k_rowifft_gather(RowParams<T> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  rowifft_gather_body<T, OP, GMODE>(p, blockIdx.x, smem_raw);
-}
-
-// ------------------------------------------------------------------------------------------
-// host side
-// ------------------------------------------------------------------------------------------
 template <typename T>
 static RowParams<T> row_params(Geometry* g, const double* in, double* out, const int* stop, double* grid) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   RowParams<T> rp;
   rp.n = g->n;
-  rp.log2n = __builtin_ctz(g->n);
+  rp.log2n = log2i(g->n);
   rp.R = g->rows_per_cta[pi];
   rp.M = (int)g->M;
   rp.cell_start = g->cell_start;
@@ -681,7 +67,6 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.eta = g->eta;
   rp.hd = g->h * g->h;
   rp.eta_src = T(g->naug ? (g->pde == IBDL_PDE_STOKES ? g->eta / g->mu : g->eta) : 0.0);
-  rp.tw_smem = 1;
   return rp;
 }
 
@@ -690,9 +75,8 @@ static ColParams<T> col_params(Geometry* g, const int* stop) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   ColParams<T> cp;
   cp.n = g->n;
-  cp.log2n = __builtin_ctz(g->n);
+  cp.log2n = log2i(g->n);
   cp.C = g->cols_per_cta[pi];
-  cp.lc = __builtin_ctz(cp.C ? cp.C : 1);
   cp.R = g->rows_per_cta[pi];
   cp.lam = T(g->lambda);
   cp.mu = T(g->mu);
@@ -702,77 +86,28 @@ static ColParams<T> col_params(Geometry* g, const int* stop) {
   cp.spec = reinterpret_cast<cplx<T>*>(g->spec);
   cp.tw = reinterpret_cast<const cplx<T>*>(pi ? (const void*)g->tw32 : (const void*)g->tw64);
   cp.stop = stop;
-  cp.tw_smem = 1;
   return cp;
 }
 
-// shared memory: two padded FFT buffers, plus (staged) the twiddles (n) and, in the column pass,
-// the two symbol tables. Large grids leave the tables in global memory (L1-cached reads) so the
-// buffers fit: FP64 to 4096², FP32 to 8192² for the scalar operator, 2048² / 4096² for Stokes.
+// Launch shape of one operator at one precision: threads and shared memory of the three kernels
+// for the geometry's band height R and column group C, or an error if they do not fit.
 template <typename T, int OP>
-static size_t smem_spread(const Geometry* g, int R, bool staged = true) {
-  return ((staged ? g->n : 0) + 2 * padded((size_t)Traits<OP>::NIN * (R / 2) * g->n)) * sizeof(cplx<T>);
-}
-template <typename T, int OP>
-static size_t smem_gather(const Geometry* g, int R, bool staged = true) {
-  return ((staged ? g->n : 0) + 2 * padded((size_t)Traits<OP>::NOUT * (R / 2) * g->n)) * sizeof(cplx<T>);
-}
-template <typename T, int OP>
-static size_t smem_col(const Geometry* g, int C, bool staged = true) {
-  const int nmax = Traits<OP>::NIN > Traits<OP>::NOUT ? Traits<OP>::NIN : Traits<OP>::NOUT;
-  return ((staged ? g->n : 0) + 2 * padded((size_t)nmax * C * g->n)) * sizeof(cplx<T>) +
-         (staged ? 2 * g->n * sizeof(T) : 0);
-}
-
-static const size_t kSmemLimit = 227 * 1024;
-
-// Programmatic dependent launch: the kernel may start while the previous kernel on the stream
-// drains; it runs its prologue and then waits in cudaGridDependencySynchronize(). IBDL_NO_PDL=1
-// turns it off.
-static bool use_pdl() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = getenv("IBDL_NO_PDL");
-    v = (e && atoi(e) != 0) ? 0 : 1;
-  }
-  return v == 1;
-}
-
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_k(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, bool pdl,
-                            Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at;
-  at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at.val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = &at;
-  cfg.numAttrs = pdl && use_pdl() ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
-
-template <typename T, int OP>
-static ibdl_status set_attrs() {
-  IBDL_CUDA(cudaFuncSetAttribute(k_spread_rowfft<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-  IBDL_CUDA(cudaFuncSetAttribute(k_colpass<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-  IBDL_CUDA(cudaFuncSetAttribute(k_rowifft_gather<T, OP, G_INTERP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-  IBDL_CUDA(cudaFuncSetAttribute(k_rowifft_gather<T, OP, G_GRID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-  return IBDL_OK;
-}
-
-template <typename T>
-static ibdl_status set_attrs_all() {
-  IBDL_TRY((set_attrs<T, OP_SCALAR_AN>()));
-  IBDL_TRY((set_attrs<T, OP_SCALAR_SD>()));
-  IBDL_TRY((set_attrs<T, OP_STOKES_AN>()));
-  IBDL_TRY((set_attrs<T, OP_STOKES_SD>()));
-  IBDL_TRY((set_attrs<T, OP_ADJ_AN>()));
-  IBDL_TRY((set_attrs<T, OP_ADJ_SD>()));
-  IBDL_TRY((set_attrs<T, OP_STOKES_T>()));
-  IBDL_TRY((set_attrs<T, OP_SL>()));
+static ibdl_status launch_shape(const Geometry* g, int R, int C, Launch2D* lc) {
+  constexpr int NIN = Traits<OP>::NIN, NOUT = Traits<OP>::NOUT, NMAX = NIN > NOUT ? NIN : NOUT;
+  const int L = log2i(g->n), qt = threads_per_seq_2d(L);
+  if (R < 2 || C < 1)
+    return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
+  lc->R = R;
+  lc->C = C;
+  lc->smem_row = smem_rows_2d<T>(NIN, R, L);
+  lc->smem_gather = smem_rows_2d<T>(NOUT, R, L);
+  lc->smem_col = smem_cols_2d<T>(NMAX, C, L);
+  lc->threads_row = (R / 2) * qt;
+  lc->threads_col = C * qt;
+  if (lc->smem_row > kSmemLimit2d || lc->smem_gather > kSmemLimit2d || lc->smem_col > kSmemLimit2d)
+    return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
+  if (lc->threads_row > kMaxThreads2d || lc->threads_col > kMaxThreads2d)
+    return fail(IBDL_ERR_UNSUPPORTED, "launch shape exceeds the thread limit");
   return IBDL_OK;
 }
 
@@ -785,16 +120,10 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
                           double* grid, const int* idx = nullptr, int vstride = 0, int trans = 0,
                           const double* grid_in = nullptr, int mode = 0) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
-  const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi];
-  if (R == 0 || C == 0)
-    return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
-  // stage the twiddles (and symbol tables) in shared memory when they fit beside the buffers
-  const bool row_staged = smem_spread<T, OP>(g, R) <= kSmemLimit && smem_gather<T, OP>(g, R) <= kSmemLimit;
-  const bool col_staged = smem_col<T, OP>(g, C) <= kSmemLimit;
-  const size_t s1 = smem_spread<T, OP>(g, R, row_staged), s2 = smem_col<T, OP>(g, C, col_staged),
-               s3 = smem_gather<T, OP>(g, R, row_staged);
-  if (s1 > kSmemLimit || s2 > kSmemLimit || s3 > kSmemLimit)
-    return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
+  Launch2D lc;
+  IBDL_TRY((launch_shape<T, OP>(g, g->rows_per_cta[pi], g->cols_per_cta[pi], &lc)));
+  lc.pdl = !g->timing;
+  lc.grid_mode = grid ? G_GRID : G_INTERP;
   RowParams<T> rp = row_params<T>(g, in, out, stop, grid);
   rp.idx = idx;
   rp.vstride = vstride;
@@ -805,29 +134,25 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
     rp.aug = 0;
     rp.eta_src = T(0);
   }
-  rp.tw_smem = row_staged ? 1 : 0;
   ColParams<T> cp = col_params<T>(g, stop);
-  cp.tw_smem = col_staged ? 1 : 0;
   if (mode & RUN_LAPLACE) cp.lam = T(0);  // the plain Laplace problem (indicator)
   if (mode & (RUN_LAPLACE | RUN_NO_AUG)) {  // no completed-method terms
     rp.aug = 0;
     rp.eta_src = T(0);
   }
-  const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
-  if (g->timing) timing_mark(g, s, -1);
-  const int nt = g->threads[pi] ? g->threads[pi] : kThreads;
-  IBDL_CUDA(launch_k(k_spread_rowfft<T, OP>, g->n / R, nt, s1, s, !g->timing, rp));
-  if (g->timing) timing_mark(g, s, st0);
-  IBDL_CUDA(launch_k(k_colpass<T, OP>, (g->n / 2) / C, nt, s2, s, !g->timing, cp));
-  if (g->timing) timing_mark(g, s, st0 + 1);
-  if (grid)
-    IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_GRID>, g->n / R, nt, s3, s, !g->timing, rp));
-  else
-    IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_INTERP>, g->n / R, nt, s3, s, !g->timing, rp));
-  if (g->timing) timing_mark(g, s, st0 + 2);
-  g->launches += 3;
-  IBDL_CUDA(cudaGetLastError());
-  return IBDL_OK;
+  switch (log2i(g->n)) {
+    case 4: return launch_apply_2d<T, OP, 4>(g, rp, cp, lc, s);
+    case 5: return launch_apply_2d<T, OP, 5>(g, rp, cp, lc, s);
+    case 6: return launch_apply_2d<T, OP, 6>(g, rp, cp, lc, s);
+    case 7: return launch_apply_2d<T, OP, 7>(g, rp, cp, lc, s);
+    case 8: return launch_apply_2d<T, OP, 8>(g, rp, cp, lc, s);
+    case 9: return launch_apply_2d<T, OP, 9>(g, rp, cp, lc, s);
+    case 10: return launch_apply_2d<T, OP, 10>(g, rp, cp, lc, s);
+    case 11: return launch_apply_2d<T, OP, 11>(g, rp, cp, lc, s);
+    case 12: return launch_apply_2d<T, OP, 12>(g, rp, cp, lc, s);
+    case 13: return launch_apply_2d<T, OP, 13>(g, rp, cp, lc, s);
+    default: return fail(IBDL_ERR_UNSUPPORTED, "2-D grid size outside 16 … 8192");
+  }
 }
 
 template <typename T>
@@ -991,68 +316,16 @@ ibdl_status adjoint_2d(Geometry* g, int precision, const double* W, double* Z, c
 }
 
 // ------------------------------------------------------------------------------------------
-// batched launches: one grid per stage covers every problem of a batch; CTA i runs work unit
-// units[i] = (problem, unit) with that problem's parameter block
+// batched launches: one grid per stage covers every problem of a batch (kernels and launches in
+// apply2d_batch_*.cu); here the per-problem parameter blocks and (problem, unit) tables
 // ------------------------------------------------------------------------------------------
-template <typename T, int OP>
-__global__ void __launch_bounds__(kThreads) kb_spread_rowfft(const RowParams<T>* __restrict__ P, const int2* units,
-                                                             const double* in_base, double* out_base) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int2 u = units[blockIdx.x];
-  RowParams<T> p = P[u.x];
-  p.in = in_base + p.io_off;
-  p.out = out_base + p.io_off;
-  spread_rowfft_body<T, OP>(p, u.y, p.n / p.R, smem_raw);
-}
-
-template <typename T, int OP>
-__global__ void __launch_bounds__(kThreads) kb_colpass(const ColParams<T>* __restrict__ P, const int2* units) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int2 u = units[blockIdx.x];
-  const ColParams<T> p = P[u.x];
-  colpass_body<T, OP>(p, u.y, smem_raw);
-}
-
-template <typename T, int OP>
-__global__ void __launch_bounds__(kThreads) kb_rowifft_gather(const RowParams<T>* __restrict__ P, const int2* units,
-                                                              const double* in_base, double* out_base) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int2 u = units[blockIdx.x];
-  RowParams<T> p = P[u.x];
-  p.in = in_base + p.io_off;
-  p.out = out_base + p.io_off;
-  rowifft_gather_body<T, OP, G_INTERP>(p, u.y, smem_raw);
-}
-
-template <typename T, int OP>
-static ibdl_status batch_launch(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
-  const int pi = std::is_same<T, float>::value ? 1 : 0;
-  static bool attrs = false;
-  if (!attrs) {
-    IBDL_CUDA(cudaFuncSetAttribute(kb_spread_rowfft<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-    IBDL_CUDA(cudaFuncSetAttribute(kb_colpass<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-    IBDL_CUDA(cudaFuncSetAttribute(kb_rowifft_gather<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-    attrs = true;
-  }
-  const RowParams<T>* rp = static_cast<const RowParams<T>*>(B->rowp[pi][mode]);
-  const ColParams<T>* cp = static_cast<const ColParams<T>*>(B->colp[pi]);
-  kb_spread_rowfft<T, OP><<<B->nrow_units[pi], kThreads, B->smem_row[pi], s>>>(rp, B->row_units[pi], in_base, out_base);
-  IBDL_CUDA(launch_k(kb_colpass<T, OP>, B->ncol_units[pi], kThreads, B->smem_col[pi], s, true, cp,
-                     (const int2*)B->col_units[pi]));
-  IBDL_CUDA(launch_k(kb_rowifft_gather<T, OP>, B->nrow_units[pi], kThreads, B->smem_gather[pi], s, true, rp,
-                     (const int2*)B->row_units[pi], in_base, out_base));
-  B->launches += 3;
-  IBDL_CUDA(cudaGetLastError());
-  return IBDL_OK;
-}
-
 template <typename T>
 static ibdl_status batch_apply_t(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
   if (B->pde == IBDL_PDE_STOKES)
-    return B->dipole == IBDL_DIPOLE_ANALYTIC ? batch_launch<T, OP_STOKES_AN>(B, mode, in_base, out_base, s)
-                                             : batch_launch<T, OP_STOKES_SD>(B, mode, in_base, out_base, s);
-  return B->dipole == IBDL_DIPOLE_ANALYTIC ? batch_launch<T, OP_SCALAR_AN>(B, mode, in_base, out_base, s)
-                                           : batch_launch<T, OP_SCALAR_SD>(B, mode, in_base, out_base, s);
+    return B->dipole == IBDL_DIPOLE_ANALYTIC ? batch_launch_2d<T, OP_STOKES_AN>(B, mode, in_base, out_base, s)
+                                             : batch_launch_2d<T, OP_STOKES_SD>(B, mode, in_base, out_base, s);
+  return B->dipole == IBDL_DIPOLE_ANALYTIC ? batch_launch_2d<T, OP_SCALAR_AN>(B, mode, in_base, out_base, s)
+                                           : batch_launch_2d<T, OP_SCALAR_SD>(B, mode, in_base, out_base, s);
 }
 
 ibdl_status batch_apply_2d(Batch* B, int precision, int mode, const double* in_base, double* out_base, cudaStream_t s) {
@@ -1061,21 +334,22 @@ ibdl_status batch_apply_2d(Batch* B, int precision, int mode, const double* in_b
 }
 
 template <typename T, int OP>
-static void batch_smem(Batch* B, Geometry* g, int pi) {
-  const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi];
-  const size_t a = smem_spread<T, OP>(g, R), b = smem_col<T, OP>(g, C), c = smem_gather<T, OP>(g, R);
-  if (a > B->smem_row[pi]) B->smem_row[pi] = a;
-  if (b > B->smem_col[pi]) B->smem_col[pi] = b;
-  if (c > B->smem_gather[pi]) B->smem_gather[pi] = c;
+static ibdl_status batch_shape(Batch* B, Geometry* g, int pi) {
+  Launch2D lc;
+  IBDL_TRY((launch_shape<T, OP>(g, g->rows_per_cta[pi], g->cols_per_cta[pi], &lc)));
+  B->smem_row[pi] = std::max(B->smem_row[pi], lc.smem_row);
+  B->smem_col[pi] = std::max(B->smem_col[pi], lc.smem_col);
+  B->smem_gather[pi] = std::max(B->smem_gather[pi], lc.smem_gather);
+  B->threads_row[pi] = std::max(B->threads_row[pi], lc.threads_row);
+  B->threads_col[pi] = std::max(B->threads_col[pi], lc.threads_col);
+  return IBDL_OK;
 }
 
 template <typename T>
-static void batch_smem_any(Batch* B, Geometry* g, int pi) {
-  if (B->pde == IBDL_PDE_STOKES) {
-    if (B->dipole == IBDL_DIPOLE_ANALYTIC) batch_smem<T, OP_STOKES_AN>(B, g, pi); else batch_smem<T, OP_STOKES_SD>(B, g, pi);
-  } else {
-    if (B->dipole == IBDL_DIPOLE_ANALYTIC) batch_smem<T, OP_SCALAR_AN>(B, g, pi); else batch_smem<T, OP_SCALAR_SD>(B, g, pi);
-  }
+static ibdl_status batch_shape_any(Batch* B, Geometry* g, int pi) {
+  if (B->pde == IBDL_PDE_STOKES)
+    return B->dipole == IBDL_DIPOLE_ANALYTIC ? batch_shape<T, OP_STOKES_AN>(B, g, pi) : batch_shape<T, OP_STOKES_SD>(B, g, pi);
+  return B->dipole == IBDL_DIPOLE_ANALYTIC ? batch_shape<T, OP_SCALAR_AN>(B, g, pi) : batch_shape<T, OP_SCALAR_SD>(B, g, pi);
 }
 
 template <typename T>
@@ -1084,10 +358,12 @@ static ibdl_status batch_prepare_t(Batch* B, const int* kptr /* device &st[b].k,
   std::vector<RowParams<T>> user(B->count), kry(B->count);
   std::vector<ColParams<T>> col(B->count);
   std::vector<int2> ru, cu;
+  B->smem_row[pi] = B->smem_col[pi] = B->smem_gather[pi] = 0;
+  B->threads_row[pi] = B->threads_col[pi] = 0;
   for (int b = 0; b < B->count; ++b) {
     Geometry* g = B->geoms[b];
-    if (g->rows_per_cta[pi] == 0 || g->cols_per_cta[pi] == 0)
-      return fail(IBDL_ERR_UNSUPPORTED, "a batch problem's grid is too large for the shared-memory FFT");
+    if (batch_shape_any<T>(B, g, pi) != IBDL_OK)
+      return fail(IBDL_ERR_UNSUPPORTED, "problem " + std::to_string(b) + ": its grid is too large for a batched launch");
     user[b] = row_params<T>(g, nullptr, nullptr, nullptr, nullptr);
     user[b].io_off = B->off[b];
     kry[b] = user[b];
@@ -1101,7 +377,6 @@ static ibdl_status batch_prepare_t(Batch* B, const int* kptr /* device &st[b].k,
     }
     for (int u = 0; u < g->n / g->rows_per_cta[pi]; ++u) ru.push_back(make_int2(b, u));
     for (int u = 0; u < (g->n / 2) / g->cols_per_cta[pi]; ++u) cu.push_back(make_int2(b, u));
-    batch_smem_any<T>(B, g, pi);
   }
   auto upload = [&](void** dst, const void* src, size_t bytes) -> ibdl_status {
     if (*dst) cudaFree(*dst);
@@ -1134,8 +409,31 @@ ibdl_status batch_prepare_2d(Batch* B) {
   return IBDL_OK;
 }
 
-// Band height R (rows per CTA, even) and kx columns per CTA C, per precision, within the
-// shared-memory limit for the widest field count this geometry uses.
+// ------------------------------------------------------------------------------------------
+// launch shapes. A row kernel's CTA has (R/2)·QT threads and a column kernel's C·QT, with
+// QT = n/8 threads per transform (n/16 at n = 8192); both hold one padded sequence of n + n/8
+// complex values per field and row pair (column) in shared memory.
+// ------------------------------------------------------------------------------------------
+static int nf_row_max(const Geometry* g) { return g->nf_in > g->nf_out ? g->nf_in : g->nf_out; }
+
+// largest power of two in [lo, hi] not above v (lo if none)
+static int pow2_in(int v, int lo, int hi) {
+  int r = lo;
+  while (r * 2 <= hi && r * 2 <= v) r *= 2;
+  return r;
+}
+
+static bool row_fits(const Geometry* g, int pi, int R) {
+  const int L = log2i(g->n);
+  const size_t bytes = pi ? smem_rows_2d<float>(nf_row_max(g), R, L) : smem_rows_2d<double>(nf_row_max(g), R, L);
+  return R >= 2 && R <= g->n / 2 && bytes <= kSmemLimit2d && (R / 2) * threads_per_seq_2d(L) <= kMaxThreads2d;
+}
+static bool col_fits(const Geometry* g, int pi, int C) {
+  const int L = log2i(g->n);
+  const size_t bytes = pi ? smem_cols_2d<float>(nf_row_max(g), C, L) : smem_cols_2d<double>(nf_row_max(g), C, L);
+  return C >= 1 && C <= g->n / 2 && bytes <= kSmemLimit2d && C * threads_per_seq_2d(L) <= kMaxThreads2d;
+}
+
 // ------------------------------------------------------------------------------------------
 // autotuner: time candidate launch shapes of the 2-D application on a geometry's own data and
 // keep the fastest; results are cached per (n, fields in, fields out, pde, dipole, precision)
@@ -1148,7 +446,7 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int R, C, threads;
+  int R, C;
 };
 static std::vector<std::pair<TuneKey, TuneVal>> g_tuned;
 static std::mutex g_tune_mu;
@@ -1175,49 +473,38 @@ static void tuned_store(const TuneKey& k, const TuneVal& v) {
 
 static TuneKey tune_key(const Geometry* g, int pi) { return {g->n, g->nf_in, g->nf_out, g->pde, g->dipole, pi}; }
 
-// Candidates R ∈ {2..16}, C ∈ {1..8} that fit shared memory and keep R ≤ n/2, and (unless
-// fixed_threads) 256 or 512 threads; each timed as the median of 5 applications after one warm-up.
-ibdl_status autotune_2d(Geometry* g, int pi, bool fixed_threads, cudaStream_t s, const double* Q, double* Y) {
-  const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
-  const size_t cs = pi ? sizeof(float2) : sizeof(double2);
-  // feasible without the staged tables (each launch stages them when they fit)
-  auto row_bytes = [&](int r) { return 2 * padded((size_t)nf * (r / 2) * g->n) * cs; };
-  auto col_bytes = [&](int c) { return 2 * padded((size_t)nf * c * g->n) * cs; };
-  const int saved_R = g->rows_per_cta[pi], saved_C = g->cols_per_cta[pi], saved_T = g->threads[pi];
+// Candidates R ∈ {2 … 64}, C ∈ {1 … 32} within shared memory and 512 threads per CTA, each timed
+// as the median of 5 applications after one warm-up.
+ibdl_status autotune_2d(Geometry* g, int pi, bool /*fixed_threads*/, cudaStream_t s, const double* Q, double* Y) {
+  const int saved_R = g->rows_per_cta[pi], saved_C = g->cols_per_cta[pi];
   const int saved_timing = g->timing;
   g->timing = 0;
   cudaEvent_t e0, e1;
   IBDL_CUDA(cudaEventCreate(&e0));
   IBDL_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  TuneVal bestv{saved_R, saved_C, saved_T};
+  TuneVal bestv{saved_R, saved_C};
   ibdl_status err = IBDL_OK;
-  const int threads_opts[2] = {256, 512};
-  for (int R = 2; R <= 16 && err == IBDL_OK; R *= 2) {
-    if (R > g->n / 2 || row_bytes(R) > kSmemLimit) continue;
-    for (int C = 1; C <= 8 && err == IBDL_OK; C *= 2) {
-      if (C > g->n / 2 || col_bytes(C) > kSmemLimit) continue;
-      for (int ti = 0; ti < 2 && err == IBDL_OK; ++ti) {
-        const int T = fixed_threads ? 0 : threads_opts[ti];
-        if (fixed_threads && ti == 1) break;
-        g->rows_per_cta[pi] = R;
-        g->cols_per_cta[pi] = C;
-        g->threads[pi] = T;
-        float ms[5];
+  for (int R = 2; R <= 64 && err == IBDL_OK; R *= 2) {
+    if (!row_fits(g, pi, R)) continue;
+    for (int C = 1; C <= 32 && err == IBDL_OK; C *= 2) {
+      if (!col_fits(g, pi, C)) continue;
+      g->rows_per_cta[pi] = R;
+      g->cols_per_cta[pi] = C;
+      float ms[5];
+      err = apply_2d(g, pi ? IBDL_FP32 : IBDL_FP64, Q, Y, s, nullptr);
+      for (int k = 0; k < 5 && err == IBDL_OK; ++k) {
+        cudaEventRecord(e0, s);
         err = apply_2d(g, pi ? IBDL_FP32 : IBDL_FP64, Q, Y, s, nullptr);
-        for (int k = 0; k < 5 && err == IBDL_OK; ++k) {
-          cudaEventRecord(e0, s);
-          err = apply_2d(g, pi ? IBDL_FP32 : IBDL_FP64, Q, Y, s, nullptr);
-          cudaEventRecord(e1, s);
-          if (cudaEventSynchronize(e1) != cudaSuccess) err = fail(IBDL_ERR_CUDA, "autotune: event synchronize");
-          cudaEventElapsedTime(&ms[k], e0, e1);
-        }
-        if (err != IBDL_OK) break;
-        std::sort(ms, ms + 5);
-        if (ms[2] < best) {
-          best = ms[2];
-          bestv = {R, C, T};
-        }
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) err = fail(IBDL_ERR_CUDA, "autotune: event synchronize");
+        cudaEventElapsedTime(&ms[k], e0, e1);
+      }
+      if (err != IBDL_OK) break;
+      std::sort(ms, ms + 5);
+      if (ms[2] < best) {
+        best = ms[2];
+        bestv = {R, C};
       }
     }
   }
@@ -1226,89 +513,54 @@ ibdl_status autotune_2d(Geometry* g, int pi, bool fixed_threads, cudaStream_t s,
   g->timing = saved_timing;
   g->rows_per_cta[pi] = bestv.R;
   g->cols_per_cta[pi] = bestv.C;
-  g->threads[pi] = bestv.threads;
   if (err == IBDL_OK) tuned_store(tune_key(g, pi), bestv);
   return err;
 }
 
-// Shapes from the volume rule: about `target` complex elements of FFT per CTA, at least 16 row
-// bands and 16 column groups, R ≤ n/2 (distinct wrapped band rows), within shared memory.
+// Shapes from the volume rule: about `target` complex elements of FFT per CTA (so about
+// target/8 lane-threads), R ≤ n/2, within shared memory and the thread limit.
 void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target) {
-  const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
   const int n = g->n;
-  auto clampp2 = [](int v, int lo, int hi) {
-    v = v < lo ? lo : (v > hi ? hi : v);
-    int r = 1;
-    while (r * 2 <= v) r *= 2;
-    return r;
-  };
-  const size_t cs = pi ? sizeof(float2) : sizeof(double2);
-  auto row_bytes = [&](int r) { return (g->n + 2 * padded((size_t)nf * (r / 2) * g->n)) * cs; };
-  auto col_bytes = [&](int c) { return (g->n + 2 * padded((size_t)nf * c * g->n)) * cs + 2 * g->n * cs / 2; };
-  int R = clampp2(2 * (row_target / (n * g->nf_in)), 2, n / 16 > 2 ? n / 16 : 2);
-  while (R > 2 && row_bytes(R) > kSmemLimit) R /= 2;
-  int C = clampp2(col_target / (n * nf), 1, n / 32 > 1 ? n / 32 : 1);
-  while (C > 1 && col_bytes(C) > kSmemLimit) C /= 2;
-  if (row_bytes(R) <= kSmemLimit && col_bytes(C) <= kSmemLimit) {
+  int R = 2 * pow2_in(row_target / (n * g->nf_in), 1, n / 4 > 1 ? n / 4 : 1);
+  while (R > 2 && !row_fits(g, pi, R)) R /= 2;
+  int C = pow2_in(col_target / (n * nf_row_max(g)), 1, n / 2);
+  while (C > 1 && !col_fits(g, pi, C)) C /= 2;
+  if (row_fits(g, pi, R) && col_fits(g, pi, C)) {
     g->rows_per_cta[pi] = R;
     g->cols_per_cta[pi] = C;
   }
 }
 
+// Default shapes: about 256 threads per CTA, but at least 2·152 CTAs per kernel where the grid
+// allows (one GB300 has 152 SMs); the autotuner refines them. IBDL_PLAN_R and IBDL_PLAN_C
+// override (for tuning experiments).
 ibdl_status plan_2d(Geometry* g) {
-  static bool attrs = false;  // opt in to large dynamic shared memory once per kernel instance
-  if (!attrs) {
-    IBDL_TRY(set_attrs_all<double>());
-    IBDL_TRY(set_attrs_all<float>());
-    attrs = true;
-  }
-  // Work units sized by FFT volume: about 2048 complex elements per CTA in FP32 and 1024 in FP64
-  // (one radix-8 butterfly per thread per stage or fewer), keeping at least 16 row bands and 16
-  // column groups per problem; R ≤ n/2 keeps the wrapped band rows [r0 − 3, r0 + R) distinct.
-  const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
-  const int n = g->n;
-  auto clampp2 = [](int v, int lo, int hi) {
-    v = v < lo ? lo : (v > hi ? hi : v);
-    int r = 1;
-    while (r * 2 <= v) r *= 2;
-    return r;
-  };
+  const int n = g->n, L = log2i(n), qt = threads_per_seq_2d(L);
+  const int min_ctas = 2 * 152;
   for (int pi = 0; pi < 2; ++pi) {
-    const size_t cs = pi ? sizeof(float2) : sizeof(double2);
-    const int target = pi ? 2048 : 1024;
-    int R = clampp2(2 * (target / (n * g->nf_in)), 2, n / 16 > 2 ? n / 16 : 2);
-    // feasible without the staged tables (each launch stages them when they fit)
-    auto row_bytes = [&](int r) { return 2 * padded((size_t)nf * (r / 2) * g->n) * cs; };
-    auto col_bytes = [&](int c) { return 2 * padded((size_t)nf * c * g->n) * cs; };
-    while (R > 2 && row_bytes(R) > kSmemLimit) R /= 2;
-    if (row_bytes(R) > kSmemLimit) R = 0;
-    int C = clampp2(target / (n * nf), 1, n / 32 > 1 ? n / 32 : 1);
-    while (C > 1 && col_bytes(C) > kSmemLimit) C /= 2;
-    if (col_bytes(C) > kSmemLimit) C = 0;
-    if ((g->n / 2) % (C ? C : 1)) C = 1;
-    // launch-shape overrides for tuning experiments (IBDL_PLAN_R, IBDL_PLAN_C, IBDL_THREADS)
+    int R = 2 * pow2_in(256 / qt, 1, n / 4 > 1 ? n / 4 : 1);
+    while (R > 2 && (n / R < std::min(min_ctas, n / 2) || !row_fits(g, pi, R))) R /= 2;
+    if (!row_fits(g, pi, R)) R = 0;
+    int C = pow2_in(256 / qt, 1, n / 2);
+    while (C > 1 && ((n / 2) / C < std::min(min_ctas, n / 4) || !col_fits(g, pi, C))) C /= 2;
+    if (!col_fits(g, pi, C)) C = 0;
     if (const char* e = getenv("IBDL_PLAN_R")) {
       const int v = atoi(e);
-      // R ≤ n/2 keeps the wrapped band rows [r0 − 3, r0 + R) distinct (no point counted twice)
-      if (v >= 2 && v <= g->n / 2 && (v & (v - 1)) == 0 && row_bytes(v) <= kSmemLimit) R = v;
+      if ((v & (v - 1)) == 0 && row_fits(g, pi, v)) R = v;
     }
     if (const char* e = getenv("IBDL_PLAN_C")) {
       const int v = atoi(e);
-      if (v >= 1 && v <= g->n / 2 && (v & (v - 1)) == 0 && col_bytes(v) <= kSmemLimit) C = v;
+      if (v >= 1 && (v & (v - 1)) == 0 && col_fits(g, pi, v)) C = v;
     }
+    if (R == 0 || C == 0) R = C = 0;
     g->rows_per_cta[pi] = R;
     g->cols_per_cta[pi] = C;
     g->threads[pi] = 0;
     TuneVal tv;
-    if (tuned_lookup(tune_key(g, pi), &tv)) {
+    if (R && tuned_lookup(tune_key(g, pi), &tv)) {
       g->rows_per_cta[pi] = tv.R;
       g->cols_per_cta[pi] = tv.C;
-      g->threads[pi] = tv.threads;
     }
-  }
-  if (const char* e = getenv("IBDL_THREADS")) {
-    const int v = atoi(e);
-    if (v >= 32 && v <= kThreads && v % 32 == 0) g->threads[0] = g->threads[1] = v;
   }
   if (g->rows_per_cta[0] == 0 && g->rows_per_cta[1] == 0)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT");

@@ -1,0 +1,7 @@
+// Batched launches of the two-dimensional stokes operator in double (both dipole forms).
+#include "apply2d_launch.cuh"
+
+namespace ibdl {
+template ibdl_status batch_launch_2d<double, OP_STOKES_AN>(Batch*, int, const double*, double*, cudaStream_t);
+template ibdl_status batch_launch_2d<double, OP_STOKES_SD>(Batch*, int, const double*, double*, cudaStream_t);
+}  // namespace ibdl

@@ -1,0 +1,953 @@
+// Device side of the two-dimensional IBDL operator: spread → FFT → Fourier symbol → inverse FFT →
+// interpolate, specialised on the grid size n = 2^L at compile time.
+//
+// One application A Q = S* u + ½Q, u = −L⁻¹ S̃ Q (Sec. 5.3.2) or the Stokes velocity (Sec. 6.3.3),
+// runs as three kernels, each owning a disjoint piece of the grid (no global atomics on the grid
+// and no grid memset):
+//
+//   k_spread_rowfft   band of R rows: accumulate the dipole sources of every point whose 4×4
+//                     stencil meets the band (shared-memory atomics), FFT along x with two real
+//                     rows packed as one complex row, unpack to the packed half spectrum.
+//   k_colpass         group of C kx columns: FFT along y, Fourier symbol, inverse FFT along y.
+//   k_rowifft_gather  band of R rows: inverse FFT along x, then interpolate (S*) the band's part
+//                     of every point's stencil and add it to Y (which the first kernel set to ½Q).
+//
+// The transforms are the register FFT of fft8.cuh: a thread holds eight elements (per lane) of
+// a sequence; a CTA has (R/2)·QT threads in the row kernels and C·QT in the column pass (QT
+// threads per sequence), and one padded shared-memory buffer per sequence, used for the spread's
+// accumulation, the exchanges between FFT stages and the final layout.
+//
+// Packed half spectrum: for a real row a, A_k (k = 0..n/2) is stored in n/2 slots with slot 0
+// holding (A_0, A_{n/2}), both real. Along y, the kx = 0 and kx = n/2 columns are therefore one
+// complex column a + i b with a, b real columns; the column pass separates them by Hermitian
+// symmetry before the symbol and repacks after it.
+//
+// Band-major storage: the n rows of a field form bands of R rows (the row kernels' work unit),
+// and element (row, k) of field f sits at (f·n + band·R)·(n/2) + k·R + (row mod R). A row band is
+// one contiguous block, and a column reads R contiguous values per band.
+#pragma once
+
+#include <type_traits>
+#include <utility>
+
+#include "fft8.cuh"
+
+namespace ibdl {
+
+enum { OP_SCALAR_AN = 0, OP_SCALAR_SD = 1, OP_STOKES_AN = 2, OP_STOKES_SD = 3, OP_ADJ_AN = 4,
+       OP_ADJ_SD = 5, OP_STOKES_T = 6, OP_SL = 7 };
+
+// grid fields entering / leaving the Fourier stage, and boundary components in / out
+template <int OP>
+struct Traits;
+template <>
+struct Traits<OP_SCALAR_AN> { static constexpr int NIN = 1, NOUT = 1, C = 1; };  // f = S̃Q
+template <>
+struct Traits<OP_SCALAR_SD> { static constexpr int NIN = 2, NOUT = 1, C = 1; };  // S(Qn_x), S(Qn_y)
+template <>
+struct Traits<OP_STOKES_AN> { static constexpr int NIN = 3, NOUT = 2, C = 2; };  // s, g_x, g_y
+template <>
+struct Traits<OP_STOKES_SD> { static constexpr int NIN = 4, NOUT = 2, C = 2; };  // s, A11, A22, A12
+template <>
+struct Traits<OP_ADJ_AN> { static constexpr int NIN = 1, NOUT = 1, C = 1; };     // S W
+template <>
+struct Traits<OP_ADJ_SD> { static constexpr int NIN = 1, NOUT = 2, C = 1; };     // S W → ∂_x v, ∂_y v
+// Stokes transpose (analytic dipole): ψ_x, ψ_y → v_s, v_gx, v_gy
+template <>
+struct Traits<OP_STOKES_T> { static constexpr int NIN = 2, NOUT = 3, C = 2; };
+// single layer S*(−L⁻¹)(S V): plain spread, −L⁻¹, plain interpolation, no jump term
+template <>
+struct Traits<OP_SL> { static constexpr int NIN = 1, NOUT = 1, C = 1; };
+
+enum { G_INTERP = 0, G_GRID = 1 };
+
+// At most 512 threads per CTA in every 2-D kernel (at least 128 registers per thread).
+constexpr int kMaxThreads2d = 512;
+constexpr int kMinL2d = 4, kMaxL2d = 13;
+
+// lanes per thread and threads per sequence of the n = 2^L transforms
+__host__ __device__ constexpr int lanes_per_thread_2d(int L) { return L >= 13 ? 2 : 1; }
+__host__ __device__ constexpr int threads_per_seq_2d(int L) { return (1 << L) / 8 / lanes_per_thread_2d(L); }
+
+// Per-precision register policy: NF fields of a kernel, FL of them transformed in lockstep;
+// twiddles in registers when they fit the budget, else read from the table at each use.
+template <typename T, int L, int NF>
+struct Cfg2 {
+  static constexpr int V = lanes_per_thread_2d(L);
+  static constexpr int QT = threads_per_seq_2d(L);
+  static constexpr bool F32 = sizeof(T) == 4;
+  static constexpr int FL = F32 ? (V == 1 ? (NF <= 3 ? NF : 2) : 1) : 1;
+  static constexpr int NG = (NF + FL - 1) / FL;  // field groups
+  static constexpr int NTW = F8<L, V>::NTW;
+  static constexpr bool TWR = F32 ? (NTW * V <= 21) : (NTW * V <= 11);
+  using TW = std::conditional_t<TWR, TwRegs<T, L>, TwTable<T, L>>;
+};
+
+template <typename T>
+struct RowParams {
+  int n, log2n, R;
+  int M;
+  const int* cell_start;
+  const int* base;
+  const int* perm;
+  const T* phi;
+  const T* dphi;
+  const T* wscale;
+  const T* nrm;
+  const double* in;   // [c][M] density
+  double* out;        // [c][M] result (first kernel stores ½·in, last kernel adds S*u)
+  cplx<T>* spec;      // [nf][n][n/2]
+  const cplx<T>* tw;  // [n] e^{−2πi j/n}
+  const int* stop;    // optional: skip all work when *stop != 0
+  double* grid;       // G_GRID: [nf][n][n]
+  const int* idx;     // optional: in += (*idx)·vstride, out += (*idx + 1)·vstride (Krylov basis)
+  int vstride;
+  int64_t io_off;     // batched launches: in = in_base + io_off, out = out_base + io_off
+  // scalar adjoint ops only: 1 = the Euclidean transpose Aᵀ = W A* W⁻¹ (W⁻¹λ spread with weight
+  // Δs/h^d is λ spread with weight h^−d = 1 · h^−d: the spread weight is 1 and the gathered values
+  // carry Δs/h^d instead of 1)
+  int trans;
+  const double* grid_in;  // optional [NIN][n][n]: the band rows are read from it instead of spread
+  double jump;            // jump term coefficient: ½ (Dirichlet), −½ (Neumann), 0 (single layer)
+  // completed method (Sec. 5.3.3, Sec. 6.3.3): the vectors hold ū after the c·M density values
+  int aug;                // 1: add ū_l to the boundary rows, write the rows η Σ_i Δs_i Q_{l,i}
+  double eta;             // η
+  double hd;              // h^d
+  T eta_src;              // weight of the ηSQ source: η (scalar) or η/μ (Stokes, projected part)
+};
+
+template <typename T>
+__device__ __forceinline__ void resolve_io(const RowParams<T>& p, const double*& in, double*& out) {
+  in = p.in;
+  out = p.out;
+  if (p.idx) {
+    const int k = *p.idx;
+    in += (size_t)k * p.vstride;
+    out += (size_t)(k + 1) * p.vstride;
+  }
+}
+
+template <typename T>
+struct ColParams {
+  int n, log2n, C;
+  int R;  // rows per band of the band-major spectrum
+  T lam, scale;
+  T mu;   // viscosity (Brinkman: L = μΔ − λ)
+  const T* lap1;
+  const T* der1;
+  cplx<T>* spec;
+  const cplx<T>* tw;
+  const int* stop;
+};
+
+// Sorted points whose base row lies in the cell rows [r0 − 3, r0 + R) (mod n): at most two
+// contiguous ranges of the cell-sorted order.
+struct PointRanges {
+  int s0, cnt1, s2, cnt;
+  __device__ int at(int t) const { return t < cnt1 ? s0 + t : s2 + (t - cnt1); }
+};
+__device__ __forceinline__ PointRanges band_points(const int* cell_start, int n, int r0, int R) {
+  PointRanges pr;
+  const int lo = r0 - 3, hi = r0 + R;
+  if (lo >= 0) {
+    pr.s0 = cell_start[lo];
+    pr.cnt1 = cell_start[hi] - pr.s0;
+    pr.s2 = 0;
+    pr.cnt = pr.cnt1;
+  } else {
+    pr.s0 = cell_start[lo + n];
+    pr.cnt1 = cell_start[n] - pr.s0;
+    pr.s2 = cell_start[0];
+    pr.cnt = pr.cnt1 + (cell_start[hi] - pr.s2);
+  }
+  return pr;
+}
+
+// ------------------------------------------------------------------------------------------
+// kernel 1: spread + forward FFT along x
+// ------------------------------------------------------------------------------------------
+// Bodies take the work unit (row band / column group) and the problem's number of units, so
+// the same code serves one problem (unit = blockIdx.x) and a batch of problems (unit from a
+// (problem, unit) table).
+// One spread work item (point, stencil node): everything but the density, read from the geometry's
+// point tables, which no kernel writes (so a kernel may load them before its dependency wait).
+template <typename T>
+struct SpreadItem {
+  int lr, i, col;
+  T px, py, dpx, dpy, ws, nx, ny;
+};
+template <typename T>
+__device__ __forceinline__ SpreadItem<T> spread_item(const RowParams<T>& p, const PointRanges& pr, int t, int r0) {
+  const int n = p.n, M = p.M;
+  const int s = pr.at(t >> 4);
+  const int ay = (t >> 2) & 3, ax = t & 3;
+  SpreadItem<T> it;
+  it.lr = (((p.base[M + s] + ay) & (n - 1)) - r0) & (n - 1);
+  it.i = p.perm[s];
+  it.col = (p.base[s] + ax) & (n - 1);
+  it.px = p.phi[(0 * 4 + ax) * M + s];
+  it.py = p.phi[(1 * 4 + ay) * M + s];
+  it.dpx = p.dphi[(0 * 4 + ax) * M + s];
+  it.dpy = p.dphi[(1 * 4 + ay) * M + s];
+  it.ws = p.wscale[s];
+  it.nx = p.nrm[s];
+  it.ny = p.nrm[M + s];
+  return it;
+}
+
+template <typename T, int OP, int L>
+__device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int unit, int nunits,
+                                                   unsigned char* smem_raw) {
+  constexpr int NIN = Traits<OP>::NIN;
+  constexpr int NC = Traits<OP>::C;
+  using CF = Cfg2<T, L, NIN>;
+  using F = F8<L, CF::V>;
+  constexpr int n = F::N, V = CF::V, QT = CF::QT, FL = CF::FL;
+  const int R = p.R, half = R >> 1, M = p.M;
+  // sequence (field f, row pair rp) at buf + (f·half + rp)·PN; accumulation view: field f, local
+  // row lr, column x → real part (even lr) or imaginary part (odd lr) of element
+  // (f·half + lr/2)·n + x in the padded layout
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  T* acc = reinterpret_cast<T*>(buf);
+  const int r0 = unit * R;
+  const int rp = threadIdx.x / QT, j0 = threadIdx.x - rp * QT;
+  const bool active = rp < half;
+  // prologue independent of the previous kernel, then wait for it (programmatic launch)
+  for (int i = threadIdx.x; i < NIN * half * F::PN * 2; i += blockDim.x) acc[i] = T(0);
+  typename CF::TW tw[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) tw[v].load(p.tw, j0 + v * QT);
+  // the points whose stencil meets the band, and this thread's first work item (16 per point)
+  const PointRanges pr = band_points(p.cell_start, n, r0, R);
+  const int nitems = p.grid_in ? 0 : pr.cnt * 16;
+  SpreadItem<T> it0 = {};
+  if ((int)threadIdx.x < nitems) it0 = spread_item(p, pr, threadIdx.x, r0);
+  cudaGridDependencySynchronize();
+  // Let the next kernel launch and run its prologue. Triggered only after this kernel's own
+  // wait, so every kernel before the previous one has completed by then: a prologue overlaps
+  // its direct predecessor only (its wait still covers this grid's completion and writes).
+  cudaTriggerProgrammaticLaunchCompletion();
+  // In a GMRES cycle the step just before this kernel writes the stop flag and the Krylov index:
+  // both loads go out together, then the branch
+  const int stopped = p.stop ? *p.stop : 0;
+  const double* pin;
+  double* pout;
+  resolve_io(p, pin, pout);
+  if (stopped) return;
+
+  // jump term: out = ±½·in (the gather kernel adds S*u afterwards); none for grid input
+  if (!p.grid_in)
+    for (int i = unit * blockDim.x + threadIdx.x; i < NC * M; i += nunits * blockDim.x)
+      pout[i] = p.jump * pin[i] + (p.aug ? pin[NC * M + i / M] : 0.0);
+  __syncthreads();  // the accumulation buffer is cleared
+  if (p.aug && unit == 0) {
+    // constraint rows of the completed method: η Σ_i Δs_i Q_{l,i} (Δs = wscale·h^d); the block
+    // size is a power of two (a partial warp below 32 threads), the partial sums go to the
+    // reduction slots after the sequence buffers
+    double* red = reinterpret_cast<double*>(buf + (size_t)NIN * half * F::PN);
+    const int wl = blockDim.x < 32 ? blockDim.x : 32;
+    const unsigned wmask = wl == 32 ? 0xffffffffu : ((1u << wl) - 1u);
+    for (int l = 0; l < NC; ++l) {
+      double v = 0.0;
+      for (int s = threadIdx.x; s < M; s += blockDim.x) v += double(p.wscale[s]) * pin[(size_t)l * M + p.perm[s]];
+      for (int o = wl >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(wmask, v, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+      __syncthreads();
+      if (threadIdx.x < wl) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double t = (int)threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+        for (int o = wl >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(wmask, t, o);
+        if (threadIdx.x == 0) pout[NC * M + l] = p.eta * p.hd * t;
+      }
+      __syncthreads();
+    }
+  }
+
+  if (p.grid_in) {
+    for (int t = threadIdx.x; t < NIN * R * n; t += blockDim.x) {
+      const int f = t / (R * n);
+      const int rem = t - f * R * n;
+      const int lr = rem / n, x = rem - lr * n;
+      acc[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)] = T(p.grid_in[((size_t)f * n + r0 + lr) * n + x]);
+    }
+  }
+
+  // one thread per (point, stencil node): 16 work items per point whose stencil meets the band
+  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
+    const SpreadItem<T> it = t == (int)threadIdx.x ? it0 : spread_item(p, pr, t, r0);
+    const int lr = it.lr;
+    if (lr >= R) continue;
+    const int i = it.i;
+    const T px = it.px, py = it.py, ws = it.ws, nx = it.nx, ny = it.ny;
+    const int e = (lr >> 1) * n + it.col;  // field 0; field f adds f·half·n
+    const int odd = lr & 1;
+    const T pp = px * py;
+    if (OP == OP_SCALAR_AN) {
+      const T q = T(pin[i]) * ws;
+      const T ddx = it.dpx * py, ddy = px * it.dpy;
+      // dipole source n·∇δ_h, plus ηδ_h for the completed method
+      atomicAdd(acc + 2 * pidx(e) + odd, q * (nx * ddx + ny * ddy + p.eta_src * pp));
+    } else if (OP == OP_SCALAR_SD) {
+      const T q = T(pin[i]) * ws * pp;
+      atomicAdd(acc + 2 * pidx(e) + odd, q * nx);
+      atomicAdd(acc + 2 * pidx(e + half * n) + odd, q * ny);
+    } else if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
+      const T qx = T(pin[i]), qy = T(pin[M + i]);
+      const T c0 = ws * (qx * nx + qy * ny);  // Q·n
+      const T c1 = ws * (T(2) * qx * nx);     // A_xx
+      const T c2 = ws * (T(2) * qy * ny);     // A_yy
+      const T c3 = ws * (qx * ny + qy * nx);  // A_xy
+      atomicAdd(acc + 2 * pidx(e) + odd, c0 * pp);
+      if (OP == OP_STOKES_AN) {
+        const T ddx = it.dpx * py, ddy = px * it.dpy;
+        // g_x = ∂_x S(A_xx) + ∂_y S(A_xy), g_y = ∂_x S(A_xy) + ∂_y S(A_yy); the completed method
+        // adds (η/μ) S(Q) to the projected source
+        const T ce = p.eta_src * ws * pp;
+        atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * ddx + c3 * ddy + ce * qx);
+        atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c3 * ddx + c2 * ddy + ce * qy);
+      } else {
+        atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * pp);
+        atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c2 * pp);
+        atomicAdd(acc + 2 * pidx(e + 3 * half * n) + odd, c3 * pp);
+      }
+    } else if (OP == OP_STOKES_T) {
+      // ψ_l = Σ_j μ_{l,j} Φ(x − X_j): the transpose of S*, unweighted
+      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * pp);
+      atomicAdd(acc + 2 * pidx(e + half * n) + odd, T(pin[M + i]) * pp);
+    } else {
+      // plain spread of W (A*: weight Δs/h^d), or of λ (Aᵀ: weight 1, Δs/h^d moves to the gather)
+      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * (p.trans ? T(1) : ws) * pp);
+    }
+  }
+  __syncthreads();
+
+  // forward FFT of every (field, row pair) sequence, FL fields in lockstep; each lane reads and
+  // writes back only its own positions, so only the exchanges inside need barriers
+  static_for<0, CF::NG>([&](auto gi) {
+    constexpr int G = decltype(gi)::value;
+    constexpr int FG = (NIN - G * FL) < FL ? (NIN - G * FL) : FL;
+    cplx<T>* sb = buf + ((size_t)(G * FL) * half + rp) * F::PN;
+    cplx<T> x[FG][V][8];
+    if (active) {
+#pragma unroll
+      for (int f = 0; f < FG; ++f)
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) x[f][v][s] = sb[f * half * F::PN + ppos(j0 + v * QT + s * F::Q)];
+    }
+    f8_fft<T, false, L, V, FG>(x, sb, half * F::PN, j0, tw, active);
+    if (active) {
+#pragma unroll
+      for (int f = 0; f < FG; ++f)
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) sb[f * half * F::PN + ppos(j0 + v * QT + s * F::Q)] = x[f][v][s];
+    }
+  });
+  __syncthreads();
+
+  // unpack Z = FFT(a + i b) of the row pair (2j, 2j + 1) into A = FFT(a) (even rows) and
+  // B = FFT(b) (odd rows), k = 0..n/2, packed format; thread t writes element t of the field's
+  // band-major block, k·R + rr, so consecutive threads write consecutive addresses
+  const cplx<T>* res = buf;
+  constexpr int nh = n >> 1, lnh = L - 1;
+  const int lR = __ffs(R) - 1;
+  for (int t = threadIdx.x; t < NIN * nh * R; t += blockDim.x) {
+    const int rr = t & (R - 1), k = (t >> lR) & (nh - 1), f = t >> (lR + lnh);
+    const int zb = (f * half + (rr >> 1)) * n;
+    cplx<T> v;
+    if (k == 0) {
+      const cplx<T> z0 = res[pidx(zb)], zh = res[pidx(zb + nh)];
+      v = (rr & 1) ? mk(z0.y, zh.y) : mk(z0.x, zh.x);
+    } else {
+      const cplx<T> zk = res[pidx(zb + k)], zc = res[pidx(zb + n - k)];
+      v = (rr & 1) ? mk(T(0.5) * (zk.y + zc.y), T(0.5) * (zc.x - zk.x))
+                   : mk(T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y));
+    }
+    p.spec[((size_t)f * n + r0) * nh + (t - f * (nh << lR))] = v;
+  }
+}
+
+template <typename T, int OP, int L>
+__global__ void __launch_bounds__(kMaxThreads2d) k_spread_rowfft(RowParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  spread_rowfft_body<T, OP, L>(p, blockIdx.x, gridDim.x, smem_raw);
+}
+
+// ------------------------------------------------------------------------------------------
+// Fourier symbols: NIN transformed fields in → NOUT out; lap = |k̃|² (sum of the per-axis
+// Laplacian symbols), dkx, dky the per-axis derivative symbols
+// ------------------------------------------------------------------------------------------
+template <typename T, int OP>
+__device__ __forceinline__ void apply_symbol(const ColParams<T>& p, T lap, T dkx, T dky, const cplx<T>* in,
+                                             cplx<T>* out) {
+  if (OP == OP_SCALAR_AN || OP == OP_SCALAR_SD || OP == OP_ADJ_AN || OP == OP_ADJ_SD || OP == OP_SL) {
+    // −L⁻¹ ↦ 1/(|k|² + λ), zero mode dropped when λ = 0 (Δ₀⁻¹)
+    const T den = lap + p.lam;
+    const T sig = den != T(0) ? p.scale / den : T(0);
+    if (OP == OP_SCALAR_AN || OP == OP_ADJ_AN || OP == OP_SL) {
+      out[0] = cscale(in[0], sig);
+    } else if (OP == OP_SCALAR_SD) {
+      // ∇·F ↦ i(k̃_x F̂_x + k̃_y F̂_y)
+      const cplx<T> d = cadd(cscale(in[0], dkx), cscale(in[1], dky));
+      out[0] = cscale(cmuli(d), sig);
+    } else {
+      const cplx<T> v = cscale(in[0], sig);
+      out[0] = cscale(cmuli(v), dkx);
+      out[1] = cscale(cmuli(v), dky);
+    }
+  } else if (OP == OP_STOKES_T) {
+    // transpose of the Stokes multiplier (conjugate symbol): v̂_s = −i k̃·ψ̂/|k|², v̂_g = P̂ψ̂/|k|²
+    const T inv = lap != T(0) ? T(1) / lap : T(0);
+    const cplx<T> kp = cadd(cscale(in[0], dkx), cscale(in[1], dky));
+    const T sc = inv * p.scale;
+    // Brinkman (λ > 0): the projected part carries μ/(μ|k|² + λ) in place of 1/|k|²
+    const T sg = p.lam > T(0) ? p.mu / (p.mu * lap + p.lam) * p.scale : sc;
+    out[0] = cscale(cmuli(kp), -sc);
+    out[1] = cscale(csub(in[0], cscale(kp, dkx * inv)), sg);
+    out[2] = cscale(csub(in[1], cscale(kp, dky * inv)), sg);
+  } else {
+    // Stokes, interior, η = 0: û = (i k̃ ŝ + P̂ ĝ)/|k|², P̂ = I − k̃k̃ᵀ/|k|²
+    const T inv = lap != T(0) ? T(1) / lap : T(0);
+    cplx<T> gx, gy;
+    if (OP == OP_STOKES_AN) {
+      gx = in[1];
+      gy = in[2];
+    } else {  // ĝ_l = i k̃_m Â_lm with fields A11, A22, A12 in slots 1, 2, 3
+      gx = cmuli(cadd(cscale(in[1], dkx), cscale(in[3], dky)));
+      gy = cmuli(cadd(cscale(in[3], dkx), cscale(in[2], dky)));
+    }
+    const cplx<T> kg = cadd(cscale(gx, dkx), cscale(gy, dky));
+    const cplx<T> is = cmuli(in[0]);
+    const T sc = inv * p.scale;
+    if (p.lam > T(0)) {
+      // Brinkman (Sec. 6.3.2): û = i k̃ ŝ/|k|² + μ P̂ ĝ/(μ|k|² + λ), defined at k = 0 as well
+      const T sg = p.mu / (p.mu * lap + p.lam) * p.scale;
+      out[0] = cadd(cscale(is, dkx * sc), cscale(csub(gx, cscale(kg, dkx * inv)), sg));
+      out[1] = cadd(cscale(is, dky * sc), cscale(csub(gy, cscale(kg, dky * inv)), sg));
+    } else {
+      out[0] = cscale(cadd(cscale(is, dkx), csub(gx, cscale(kg, dkx * inv))), sc);
+      out[1] = cscale(cadd(cscale(is, dky), csub(gy, cscale(kg, dky * inv))), sc);
+    }
+  }
+}
+
+// symbol at (kx, ky) for a column other than the packed one
+template <typename T, int OP, int NI, int NO>
+__device__ __forceinline__ void symbol_point(const ColParams<T>& p, T lapx, T derx, T lapy, T dery,
+                                             const cplx<T> (&in)[NI], cplx<T> (&out)[NO]) {
+  apply_symbol<T, OP>(p, lapx + lapy, derx, dery, in, out);
+}
+
+// symbol on the packed kx = 0 | kx = n/2 column at ky, from P(ky) and P(−ky) of every input field:
+// P = Â + i B̂ with Â, B̂ Hermitian in ky; output Â' + i B̂' at ky
+template <typename T, int OP, int NI, int NO>
+__device__ __forceinline__ void symbol_packed(const ColParams<T>& p, T lap0, T der0, T lapn, T dern, T lapy,
+                                              T dery, const cplx<T> (&P)[NI], const cplx<T> (&Pm)[NI],
+                                              cplx<T> (&out)[NO]) {
+  cplx<T> A[NI], B[NI], oA[NO], oB[NO];
+#pragma unroll
+  for (int f = 0; f < NI; ++f) {
+    // Â(j) = (P(j) + conj P(−j))/2, B̂(j) = −i (P(j) − conj P(−j))/2
+    A[f] = mk(T(0.5) * (P[f].x + Pm[f].x), T(0.5) * (P[f].y - Pm[f].y));
+    B[f] = mk(T(0.5) * (P[f].y + Pm[f].y), T(0.5) * (Pm[f].x - P[f].x));
+  }
+  apply_symbol<T, OP>(p, lap0 + lapy, der0, dery, A, oA);
+  apply_symbol<T, OP>(p, lapn + lapy, dern, dery, B, oB);
+#pragma unroll
+  for (int f = 0; f < NO; ++f) out[f] = cadd(oA[f], cmuli(oB[f]));
+}
+
+// ------------------------------------------------------------------------------------------
+// kernel 2: FFT along y, symbol, inverse FFT along y, for C kx columns per CTA
+// ------------------------------------------------------------------------------------------
+// offset of element (row m) of column k of field f in the band-major half spectra
+template <int L>
+__device__ __forceinline__ size_t col_at(int f, int m, int k, int R) {
+  constexpr int n = 1 << L, nh = n / 2;
+  return ((size_t)f * n + (m & ~(R - 1))) * nh + (size_t)k * R + (m & (R - 1));
+}
+
+template <typename T, int OP, int L>
+__device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, unsigned char* smem_raw) {
+  constexpr int NIN = Traits<OP>::NIN;
+  constexpr int NOUT = Traits<OP>::NOUT;
+  constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
+  using CF = Cfg2<T, L, NMAX>;
+  using F = F8<L, CF::V>;
+  constexpr int n = F::N, nh = n / 2, V = CF::V, QT = CF::QT, FL = CF::FL, Q = F::Q, PN = F::PN;
+  const int C = p.C, R = p.R;
+  const int k0 = unit * C;
+  const int c = threadIdx.x / QT, j0 = threadIdx.x - c * QT;
+  const bool active = c < C;
+  const int kx = k0 + c;
+  // sequence (field f, column c) at buf + (f·C + c)·PN
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  typename CF::TW tw[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) tw[v].load(p.tw, j0 + v * QT);
+  // per-axis symbols: kx of this column (the packed column also needs kx = n/2) and, with one
+  // field in and out, ky of the lane's rows, loaded before the wait; with more fields the ky
+  // values are read at use (registers go to the fields)
+  constexpr bool PREF = NIN == 1 && NOUT == 1;
+  const bool packed = k0 == 0;  // uniform over the CTA: column 0 holds kx = 0 and kx = n/2
+  T lapx = 0, derx = 0, lapn = 0, dern = 0;
+  T lapy[PREF ? V : 1][8], dery[PREF ? V : 1][8];
+  if (active) {
+    lapx = p.lap1[kx];
+    derx = p.der1[kx];
+    lapn = p.lap1[nh];
+    dern = p.der1[nh];
+    if constexpr (PREF) {
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          lapy[v][s] = p.lap1[j0 + v * QT + s * Q];
+          dery[v][s] = p.der1[j0 + v * QT + s * Q];
+        }
+    }
+  }
+  // The stop flag is final before the wait: it is written by the GMRES step (or the cycle start)
+  // at least two kernels back, which has completed once the direct predecessor passed its own
+  // wait and triggered this launch. So no dependent load follows the wait.
+  const bool stopped = p.stop && *p.stop;
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
+  if (stopped) return;
+
+  if constexpr (NIN == 1 && NOUT == 1) {
+    // one field in and out: the symbol is applied to the registers between the transforms
+    cplx<T>* sb = buf + (size_t)c * PN;
+    cplx<T> x[1][V][8];
+    if (active) {
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) x[0][v][s] = p.spec[col_at<L>(0, j0 + v * QT + s * Q, kx, R)];
+    }
+    f8_fft<T, false, L, V, 1>(x, sb, 0, j0, tw, active);
+    if (packed) {
+      // the packed column needs P(−ky): every lane stores its own positions (free of conflicts
+      // with the last exchange, which read only those), then reads the partner's
+      if (active) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) sb[ppos(j0 + v * QT + s * Q)] = x[0][v][s];
+      }
+      __syncthreads();
+    }
+    if (active) {
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const cplx<T> in[1] = {x[0][v][s]};
+          cplx<T> out[1];
+          if (kx == 0) {
+            const int ky = j0 + v * QT + s * Q;
+            const cplx<T> pm[1] = {sb[ppos((n - ky) & (n - 1))]};
+            symbol_packed<T, OP>(p, lapx, derx, lapn, dern, lapy[v][s], dery[v][s], in, pm, out);
+          } else {
+            symbol_point<T, OP>(p, lapx, derx, lapy[v][s], dery[v][s], in, out);
+          }
+          x[0][v][s] = out[0];
+        }
+    }
+    // (the inverse transform's first exchange barrier orders the partner reads before its writes)
+    f8_fft<T, true, L, V, 1>(x, sb, 0, j0, tw, active);
+    if (active) {
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) p.spec[col_at<L>(0, j0 + v * QT + s * Q, kx, R)] = x[0][v][s];
+    }
+  } else {
+    // forward transforms of the NIN input fields (FL in lockstep), results left in shared memory
+    static_for<0, (NIN + FL - 1) / FL>([&](auto gi) {
+      constexpr int G = decltype(gi)::value;
+      constexpr int FG = (NIN - G * FL) < FL ? (NIN - G * FL) : FL;
+      cplx<T>* sb = buf + ((size_t)(G * FL) * C + c) * PN;
+      cplx<T> x[FG][V][8];
+      if (active) {
+#pragma unroll
+        for (int f = 0; f < FG; ++f)
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int s = 0; s < 8; ++s) x[f][v][s] = p.spec[col_at<L>(G * FL + f, j0 + v * QT + s * Q, kx, R)];
+      }
+      f8_fft<T, false, L, V, FG>(x, sb, C * PN, j0, tw, active);
+      if (active) {
+#pragma unroll
+        for (int f = 0; f < FG; ++f)
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int s = 0; s < 8; ++s) sb[(size_t)f * C * PN + ppos(j0 + v * QT + s * Q)] = x[f][v][s];
+      }
+    });
+    // symbol at the lane's own points, in place (each lane reads and writes only its own
+    // positions); the packed column reads its partners (P(−ky)) between two barriers
+    if (!packed) {
+      if (active) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            const int ky = j0 + v * QT + s * Q;
+            cplx<T> in[NIN], o[NOUT];
+#pragma unroll
+            for (int f = 0; f < NIN; ++f) in[f] = buf[((size_t)f * C + c) * PN + ppos(ky)];
+            symbol_point<T, OP>(p, lapx, derx, p.lap1[ky], p.der1[ky], in, o);
+#pragma unroll
+            for (int f = 0; f < NOUT; ++f) buf[((size_t)f * C + c) * PN + ppos(ky)] = o[f];
+          }
+      }
+    } else {
+      __syncthreads();
+      cplx<T> o[V][8][NOUT];
+      if (active) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            const int ky = j0 + v * QT + s * Q;
+            cplx<T> in[NIN];
+#pragma unroll
+            for (int f = 0; f < NIN; ++f) in[f] = buf[((size_t)f * C + c) * PN + ppos(ky)];
+            if (kx == 0) {
+              cplx<T> pm[NIN];
+#pragma unroll
+              for (int f = 0; f < NIN; ++f) pm[f] = buf[((size_t)f * C + c) * PN + ppos((n - ky) & (n - 1))];
+              symbol_packed<T, OP>(p, lapx, derx, lapn, dern, p.lap1[ky], p.der1[ky], in, pm, o[v][s]);
+            } else {
+              symbol_point<T, OP>(p, lapx, derx, p.lap1[ky], p.der1[ky], in, o[v][s]);
+            }
+          }
+      }
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int s = 0; s < 8; ++s)
+#pragma unroll
+            for (int f = 0; f < NOUT; ++f) buf[((size_t)f * C + c) * PN + ppos(j0 + v * QT + s * Q)] = o[v][s][f];
+      }
+    }
+    // inverse transforms of the NOUT output fields, straight to the half spectra
+    static_for<0, (NOUT + FL - 1) / FL>([&](auto gi) {
+      constexpr int G = decltype(gi)::value;
+      constexpr int FG = (NOUT - G * FL) < FL ? (NOUT - G * FL) : FL;
+      cplx<T>* sb = buf + ((size_t)(G * FL) * C + c) * PN;
+      cplx<T> x[FG][V][8];
+      if (active) {
+#pragma unroll
+        for (int f = 0; f < FG; ++f)
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int s = 0; s < 8; ++s) x[f][v][s] = sb[(size_t)f * C * PN + ppos(j0 + v * QT + s * Q)];
+      }
+      f8_fft<T, true, L, V, FG>(x, sb, C * PN, j0, tw, active);
+      if (active) {
+#pragma unroll
+        for (int f = 0; f < FG; ++f)
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int s = 0; s < 8; ++s) p.spec[col_at<L>(G * FL + f, j0 + v * QT + s * Q, kx, R)] = x[f][v][s];
+      }
+    });
+  }
+}
+
+template <typename T, int OP, int L>
+__global__ void __launch_bounds__(kMaxThreads2d) k_colpass(ColParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  colpass_body<T, OP, L>(p, blockIdx.x, smem_raw);
+}
+
+// ------------------------------------------------------------------------------------------
+// kernel 3: inverse FFT along x, then interpolation (or write the grid)
+// ------------------------------------------------------------------------------------------
+// Z_m = A_m + i B_m (m = 0..n−1) for the row pair (r0 + 2j, r0 + 2j + 1) of field f, rebuilt from
+// the band-major half spectra (A_{n−k} = conj A_k): A_k at band offset k·R + 2j, B_k next to it.
+template <typename T, int L>
+__device__ __forceinline__ cplx<T> row_z(const cplx<T>* __restrict__ spec, int f, int r0, int jj, int R, int m) {
+  constexpr int n = 1 << L, nh = n / 2;
+  const cplx<T>* band = spec + ((size_t)f * n + r0) * nh + 2 * jj;
+  if (m == 0 || m == nh) {
+    const cplx<T> A = band[0], B = band[1];
+    return m == 0 ? mk(A.x, B.x) : mk(A.y, B.y);
+  }
+  if (m < nh) {
+    const cplx<T> A = band[(size_t)m * R], B = band[(size_t)m * R + 1];
+    return mk(A.x - B.y, A.y + B.x);
+  }
+  const cplx<T> A = band[(size_t)(n - m) * R], B = band[(size_t)(n - m) * R + 1];
+  return mk(A.x + B.y, B.x - A.y);
+}
+
+// One gather work item (point, stencil row): the point-table values it needs
+template <typename T>
+struct GatherItem {
+  int lr, i, bx;
+  T py, dy, ws, nx, ny;
+  T px[4], dx[4];
+};
+template <typename T>
+__device__ __forceinline__ GatherItem<T> gather_item(const RowParams<T>& p, const PointRanges& pr, int t, int r0) {
+  const int n = p.n, M = p.M;
+  const int s = pr.at(t >> 2);
+  const int ay = t & 3;
+  GatherItem<T> it;
+  it.lr = (((p.base[M + s] + ay) & (n - 1)) - r0) & (n - 1);
+  it.i = p.perm[s];
+  it.bx = p.base[s];
+  it.py = p.phi[(1 * 4 + ay) * M + s];
+  it.dy = p.dphi[(1 * 4 + ay) * M + s];
+  it.ws = p.wscale[s];
+  it.nx = p.nrm[s];
+  it.ny = p.nrm[M + s];
+#pragma unroll
+  for (int ax = 0; ax < 4; ++ax) {
+    it.px[ax] = p.phi[(0 * 4 + ax) * M + s];
+    it.dx[ax] = p.dphi[(0 * 4 + ax) * M + s];
+  }
+  return it;
+}
+
+template <typename T, int OP, int GMODE, int L>
+__device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int unit, unsigned char* smem_raw) {
+  constexpr int NOUT = Traits<OP>::NOUT;
+  using CF = Cfg2<T, L, NOUT>;
+  using F = F8<L, CF::V>;
+  constexpr int n = F::N, V = CF::V, QT = CF::QT, FL = CF::FL, Q = F::Q, PN = F::PN;
+  const int R = p.R, half = R >> 1, M = p.M;
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int r0 = unit * R;
+  const int rp = threadIdx.x / QT, j0 = threadIdx.x - rp * QT;
+  const bool active = rp < half;
+  typename CF::TW tw[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) tw[v].load(p.tw, j0 + v * QT);
+  // the points whose stencil meets the band and this thread's first work item (4 per point),
+  // loaded before the wait: the point tables are constant
+  const PointRanges pr = band_points(p.cell_start, n, r0, R);
+  const int nitems = GMODE == G_GRID ? 0 : pr.cnt * 4;
+  GatherItem<T> it0 = {};
+  if ((int)threadIdx.x < nitems) it0 = gather_item(p, pr, threadIdx.x, r0);
+  // the stop flag and the Krylov index (the output column) are final before the wait: the GMRES
+  // step that writes them is three kernels back (see the column pass)
+  const bool stopped = p.stop && *p.stop;
+  const double* pin;
+  double* pout;
+  resolve_io(p, pin, pout);
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
+  if (stopped) return;
+
+  // inverse FFT of every (field, row pair) sequence, its first stage fed from the half spectra
+  static_for<0, (NOUT + FL - 1) / FL>([&](auto gi) {
+    constexpr int G = decltype(gi)::value;
+    constexpr int FG = (NOUT - G * FL) < FL ? (NOUT - G * FL) : FL;
+    cplx<T>* sb = buf + ((size_t)(G * FL) * half + rp) * PN;
+    cplx<T> x[FG][V][8];
+    if (active) {
+#pragma unroll
+      for (int f = 0; f < FG; ++f)
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) x[f][v][s] = row_z<T, L>(p.spec, G * FL + f, r0, rp, R, j0 + v * QT + s * Q);
+    }
+    f8_fft<T, true, L, V, FG>(x, sb, half * PN, j0, tw, active);
+    if (active) {
+#pragma unroll
+      for (int f = 0; f < FG; ++f)
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) sb[(size_t)f * half * PN + ppos(j0 + v * QT + s * Q)] = x[f][v][s];
+    }
+  });
+  __syncthreads();
+  // real values: field f, local row lr, column x at element e = (f·half + lr/2)·n + x, part lr & 1
+  const T* u = reinterpret_cast<const T*>(buf);
+
+  if (GMODE == G_GRID) {
+    for (int t = threadIdx.x; t < NOUT * R * n; t += blockDim.x) {
+      const int f = t / (R * n);
+      const int rem = t - f * R * n;
+      const int lr = rem / n, x = rem - lr * n;
+      // the completed method's field is u₀ + ū (ū after the density in the input vector)
+      const double ub = p.aug ? p.in[(size_t)Traits<OP>::C * M + f] : 0.0;
+      p.grid[((size_t)f * n + r0 + lr) * n + x] = double(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)]) + ub;
+    }
+    return;
+  }
+
+  // one thread per (point, stencil row in the band): the row's partial sum is added to Y
+  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
+    const GatherItem<T> it = t == (int)threadIdx.x ? it0 : gather_item(p, pr, t, r0);
+    const int lr = it.lr;
+    if (lr >= R) continue;
+    const int i = it.i;
+    const int bx = it.bx;
+    const T py = it.py;
+    const T dy = (OP == OP_ADJ_AN || OP == OP_STOKES_T) ? it.dy : T(0);
+    const int eb = (lr >> 1) * n, odd = lr & 1;
+    if (OP == OP_STOKES_T) {
+      // a_s = Σ v_s Φ, G_mk = Σ v_gm ∂_kΦ; out_l += (Δs/h²)[n_l a_s + Σ_k n_k (G_lk + G_kl)]
+      T as = 0, gxx = 0, gxy = 0, gyx = 0, gyy = 0;
+#pragma unroll
+      for (int ax = 0; ax < 4; ++ax) {
+        const int col = (bx + ax) & (n - 1);
+        const T px = it.px[ax], dx = it.dx[ax];
+        const T vs = u[2 * pidx(eb + col) + odd];
+        const T vx = u[2 * pidx(eb + half * n + col) + odd];
+        const T vy = u[2 * pidx(eb + 2 * half * n + col) + odd];
+        as += vs * px * py;
+        gxx += vx * dx * py;
+        gxy += vx * px * dy;
+        gyx += vy * dx * py;
+        gyy += vy * px * dy;
+      }
+      const double ws = double(it.ws), nx = double(it.nx), ny = double(it.ny);
+      const double cross = double(gxy) + double(gyx);
+      atomicAdd(pout + i, ws * (nx * double(as) + 2.0 * nx * double(gxx) + ny * cross));
+      atomicAdd(pout + M + i, ws * (ny * double(as) + nx * cross + 2.0 * ny * double(gyy)));
+      continue;
+    }
+    T acc0 = 0, acc1 = 0;
+#pragma unroll
+    for (int ax = 0; ax < 4; ++ax) {
+      const int col = (bx + ax) & (n - 1);
+      const T px = it.px[ax];
+      const T v0 = u[2 * pidx(eb + col) + odd];
+      if (OP == OP_ADJ_AN) {
+        acc0 += v0 * it.dx[ax] * py;
+        acc1 += v0 * px * dy;
+      } else {
+        const T pp = px * py;
+        acc0 += v0 * pp;
+        if (NOUT == 2) acc1 += u[2 * pidx(eb + half * n + col) + odd] * pp;
+      }
+    }
+    if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
+      atomicAdd(pout + i, double(acc0));
+      atomicAdd(pout + M + i, double(acc1));
+    } else if (OP == OP_ADJ_AN || OP == OP_ADJ_SD) {
+      // analytic: (S̃)* v = n · (kernel-gradient gather of v); spectral: −Σ_m n_m S*(∂_m v)
+      double val = double(it.nx) * double(acc0) + double(it.ny) * double(acc1);
+      if (OP == OP_ADJ_SD) val = -val;
+      if (p.trans) val *= double(it.ws);  // Δs/h^d · (S̃)* … for Aᵀ
+      atomicAdd(pout + i, val);
+    } else {
+      atomicAdd(pout + i, double(acc0));
+    }
+  }
+}
+
+template <typename T, int OP, int GMODE, int L>
+__global__ void __launch_bounds__(kMaxThreads2d) k_rowifft_gather(RowParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rowifft_gather_body<T, OP, GMODE, L>(p, blockIdx.x, smem_raw);
+}
+
+// ------------------------------------------------------------------------------------------
+// batched launches: one grid per stage covers every problem of a batch; CTA i runs work unit
+// units[i] = (problem, unit) with that problem's parameter block and transform size
+// ------------------------------------------------------------------------------------------
+template <typename T, int OP, int L>
+__device__ __forceinline__ void kb_row_dispatch(const RowParams<T>& p, int unit, unsigned char* smem, bool fwd) {
+  if constexpr (L <= kMaxL2d) {
+    if (p.log2n == L) {
+      if (fwd)
+        spread_rowfft_body<T, OP, L>(p, unit, p.n / p.R, smem);
+      else
+        rowifft_gather_body<T, OP, G_INTERP, L>(p, unit, smem);
+    } else {
+      kb_row_dispatch<T, OP, L + 1>(p, unit, smem, fwd);
+    }
+  }
+}
+
+template <typename T, int OP, int L>
+__device__ __forceinline__ void kb_col_dispatch(const ColParams<T>& p, int unit, unsigned char* smem) {
+  if constexpr (L <= kMaxL2d) {
+    if (p.log2n == L)
+      colpass_body<T, OP, L>(p, unit, smem);
+    else
+      kb_col_dispatch<T, OP, L + 1>(p, unit, smem);
+  }
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kMaxThreads2d) kb_spread_rowfft(const RowParams<T>* __restrict__ P, const int2* units,
+                                                                  const double* in_base, double* out_base) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 u = units[blockIdx.x];
+  RowParams<T> p = P[u.x];
+  p.in = in_base + p.io_off;
+  p.out = out_base + p.io_off;
+  kb_row_dispatch<T, OP, kMinL2d>(p, u.y, smem_raw, true);
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kMaxThreads2d) kb_colpass(const ColParams<T>* __restrict__ P, const int2* units) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 u = units[blockIdx.x];
+  const ColParams<T> p = P[u.x];
+  kb_col_dispatch<T, OP, kMinL2d>(p, u.y, smem_raw);
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kMaxThreads2d) kb_rowifft_gather(const RowParams<T>* __restrict__ P, const int2* units,
+                                                                   const double* in_base, double* out_base) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 u = units[blockIdx.x];
+  RowParams<T> p = P[u.x];
+  p.in = in_base + p.io_off;
+  p.out = out_base + p.io_off;
+  kb_row_dispatch<T, OP, kMinL2d>(p, u.y, smem_raw, false);
+}
+
+// ------------------------------------------------------------------------------------------
+// shared memory and thread counts (host and device)
+// ------------------------------------------------------------------------------------------
+__host__ __device__ constexpr size_t padded_seq_2d(int L) { return (size_t(1) << L) + (size_t(1) << L) / 8; }
+// row kernels: one padded sequence per field and row pair, then 32 doubles of reduction slots
+// (the completed method's constraint rows in the spread kernel)
+constexpr size_t kRowReduceBytes2d = 32 * sizeof(double);
+template <typename T>
+__host__ __device__ constexpr size_t smem_rows_2d(int nf, int R, int L) {
+  return (size_t)nf * (R / 2) * padded_seq_2d(L) * 2 * sizeof(T) + kRowReduceBytes2d;
+}
+template <typename T>
+__host__ __device__ constexpr size_t smem_cols_2d(int nf, int C, int L) {
+  return (size_t)nf * C * padded_seq_2d(L) * 2 * sizeof(T);
+}
+
+// Launch of one application's three kernels for a compile-time size (defined in the per-size
+// translation units apply2d_n*.cu).
+struct Launch2D {
+  int R, C;                 // rows per band, kx columns per CTA
+  size_t smem_row, smem_col, smem_gather;
+  int threads_row, threads_col;
+  bool pdl;
+  int grid_mode;            // G_INTERP or G_GRID
+};
+
+template <typename T, int OP, int L>
+ibdl_status launch_apply_2d(Geometry* g, const RowParams<T>& rp, const ColParams<T>& cp, const Launch2D& lc,
+                            cudaStream_t s);
+template <typename T, int OP, int L>
+ibdl_status set_attrs_2d();
+
+}  // namespace ibdl

@@ -1,0 +1,6 @@
+// Kernels of the two-dimensional operator for the 128² grid (every operator, both precisions).
+#include "apply2d_launch.cuh"
+
+namespace ibdl {
+IBDL_INSTANTIATE_2D(7)
+}  // namespace ibdl

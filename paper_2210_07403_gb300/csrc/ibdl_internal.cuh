@@ -160,6 +160,7 @@ struct Batch {
   int2* col_units[2];
   int nrow_units[2], ncol_units[2];
   size_t smem_row[2], smem_col[2], smem_gather[2];
+  int threads_row[2], threads_col[2];  // CTA sizes of the row and column launches
   // batched GMRES
   int m;                 // restart length the workspace was sized for (0: none yet)
   int64_t* voff;         // host [count]: offset of problem b's basis in V
