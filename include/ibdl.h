@@ -39,7 +39,8 @@
  *   IBDL_UNROLL=u (1..16)    GMRES iterations per body of a cycle's captured while loop (8);
  *   IBDL_ARNOLDI_CLUSTER=8   run the Arnoldi step on 8-CTA clusters even where 16 fit;
  *   IBDL_PLAN_R, IBDL_PLAN_C, IBDL_THREADS   2-D launch shape before autotuning (rows per CTA of
- *                            the row kernels, columns per CTA of the column pass, threads);
+ *                            the row kernels, columns per CTA of the column pass, least threads
+ *                            per CTA of the row kernels);
  *   IBDL_PLAN3_R, IBDL_PLAN3_C, IBDL_PLAN3_CZ   the same for the 3-D kernels.
  */
 #ifndef IBDL_H

@@ -90,11 +90,18 @@ static ColParams<T> col_params(Geometry* g, const int* stop) {
 }
 
 // Launch shape of one operator at one precision: threads and shared memory of the three kernels
-// for the geometry's band height R and column group C, or an error if they do not fit.
+// for band height R, column group C and the row kernels' least thread count `floor`, or an error
+// if they do not fit.
+static int row_threads(int nf, int R, int L, int floor) {
+  const int need = field_groups_2d(nf, L) * (R / 2) * threads_per_seq_2d(L);
+  return need > floor ? need : (floor < kMaxThreads2d ? floor : kMaxThreads2d);
+}
+static int col_threads(int nf, int C, int L) { return field_groups_2d(nf, L) * C * threads_per_seq_2d(L); }
+
 template <typename T, int OP>
-static ibdl_status launch_shape(const Geometry* g, int R, int C, Launch2D* lc) {
+static ibdl_status launch_shape(const Geometry* g, int R, int C, int floor, Launch2D* lc) {
   constexpr int NIN = Traits<OP>::NIN, NOUT = Traits<OP>::NOUT, NMAX = NIN > NOUT ? NIN : NOUT;
-  const int L = log2i(g->n), qt = threads_per_seq_2d(L);
+  const int L = log2i(g->n);
   if (R < 2 || C < 1)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
   lc->R = R;
@@ -102,11 +109,12 @@ static ibdl_status launch_shape(const Geometry* g, int R, int C, Launch2D* lc) {
   lc->smem_row = smem_rows_2d<T>(NIN, R, L);
   lc->smem_gather = smem_rows_2d<T>(NOUT, R, L);
   lc->smem_col = smem_cols_2d<T>(NMAX, C, L);
-  lc->threads_row = (R / 2) * qt;
-  lc->threads_col = C * qt;
+  lc->threads_row = row_threads(NIN, R, L, floor);
+  lc->threads_gather = row_threads(NOUT, R, L, floor);
+  lc->threads_col = col_threads(NMAX, C, L);
   if (lc->smem_row > kSmemLimit2d || lc->smem_gather > kSmemLimit2d || lc->smem_col > kSmemLimit2d)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
-  if (lc->threads_row > kMaxThreads2d || lc->threads_col > kMaxThreads2d)
+  if (lc->threads_row > kMaxThreads2d || lc->threads_gather > kMaxThreads2d || lc->threads_col > kMaxThreads2d)
     return fail(IBDL_ERR_UNSUPPORTED, "launch shape exceeds the thread limit");
   return IBDL_OK;
 }
@@ -121,7 +129,7 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
                           const double* grid_in = nullptr, int mode = 0) {
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   Launch2D lc;
-  IBDL_TRY((launch_shape<T, OP>(g, g->rows_per_cta[pi], g->cols_per_cta[pi], &lc)));
+  IBDL_TRY((launch_shape<T, OP>(g, g->rows_per_cta[pi], g->cols_per_cta[pi], g->threads[pi], &lc)));
   lc.pdl = !g->timing;
   lc.grid_mode = grid ? G_GRID : G_INTERP;
   RowParams<T> rp = row_params<T>(g, in, out, stop, grid);
@@ -336,12 +344,13 @@ ibdl_status batch_apply_2d(Batch* B, int precision, int mode, const double* in_b
 template <typename T, int OP>
 static ibdl_status batch_shape(Batch* B, Geometry* g, int pi) {
   Launch2D lc;
-  IBDL_TRY((launch_shape<T, OP>(g, g->rows_per_cta[pi], g->cols_per_cta[pi], &lc)));
+  IBDL_TRY((launch_shape<T, OP>(g, g->rows_per_cta[pi], g->cols_per_cta[pi], g->threads[pi], &lc)));
   B->smem_row[pi] = std::max(B->smem_row[pi], lc.smem_row);
   B->smem_col[pi] = std::max(B->smem_col[pi], lc.smem_col);
   B->smem_gather[pi] = std::max(B->smem_gather[pi], lc.smem_gather);
   B->threads_row[pi] = std::max(B->threads_row[pi], lc.threads_row);
   B->threads_col[pi] = std::max(B->threads_col[pi], lc.threads_col);
+  B->threads_gather[pi] = std::max(B->threads_gather[pi], lc.threads_gather);
   return IBDL_OK;
 }
 
@@ -359,7 +368,7 @@ static ibdl_status batch_prepare_t(Batch* B, const int* kptr /* device &st[b].k,
   std::vector<ColParams<T>> col(B->count);
   std::vector<int2> ru, cu;
   B->smem_row[pi] = B->smem_col[pi] = B->smem_gather[pi] = 0;
-  B->threads_row[pi] = B->threads_col[pi] = 0;
+  B->threads_row[pi] = B->threads_col[pi] = B->threads_gather[pi] = 0;
   for (int b = 0; b < B->count; ++b) {
     Geometry* g = B->geoms[b];
     if (batch_shape_any<T>(B, g, pi) != IBDL_OK)
@@ -424,14 +433,14 @@ static int pow2_in(int v, int lo, int hi) {
 }
 
 static bool row_fits(const Geometry* g, int pi, int R) {
-  const int L = log2i(g->n);
-  const size_t bytes = pi ? smem_rows_2d<float>(nf_row_max(g), R, L) : smem_rows_2d<double>(nf_row_max(g), R, L);
-  return R >= 2 && R <= g->n / 2 && bytes <= kSmemLimit2d && (R / 2) * threads_per_seq_2d(L) <= kMaxThreads2d;
+  const int L = log2i(g->n), nf = nf_row_max(g);
+  const size_t bytes = pi ? smem_rows_2d<float>(nf, R, L) : smem_rows_2d<double>(nf, R, L);
+  return R >= 2 && R <= g->n / 2 && bytes <= kSmemLimit2d && row_threads(nf, R, L, 0) <= kMaxThreads2d;
 }
 static bool col_fits(const Geometry* g, int pi, int C) {
-  const int L = log2i(g->n);
-  const size_t bytes = pi ? smem_cols_2d<float>(nf_row_max(g), C, L) : smem_cols_2d<double>(nf_row_max(g), C, L);
-  return C >= 1 && C <= g->n / 2 && bytes <= kSmemLimit2d && C * threads_per_seq_2d(L) <= kMaxThreads2d;
+  const int L = log2i(g->n), nf = nf_row_max(g);
+  const size_t bytes = pi ? smem_cols_2d<float>(nf, C, L) : smem_cols_2d<double>(nf, C, L);
+  return C >= 1 && C <= g->n / 2 && bytes <= kSmemLimit2d && col_threads(nf, C, L) <= kMaxThreads2d;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -446,7 +455,7 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int R, C;
+  int R, C, floor;
 };
 static std::vector<std::pair<TuneKey, TuneVal>> g_tuned;
 static std::mutex g_tune_mu;
@@ -473,47 +482,65 @@ static void tuned_store(const TuneKey& k, const TuneVal& v) {
 
 static TuneKey tune_key(const Geometry* g, int pi) { return {g->n, g->nf_in, g->nf_out, g->pde, g->dipole, pi}; }
 
-// Candidates R ∈ {2 … 64}, C ∈ {1 … 32} within shared memory and 512 threads per CTA, each timed
-// as the median of 5 applications after one warm-up.
+// The row kernels' shape (band height R ∈ {2 … 64} and least thread count ∈ {0, 256, 512}) is
+// tuned first with the column group fixed, then the column group C ∈ {1 … 32}: the kernels are
+// independent, so the two sweeps find the best pair. Candidates must fit shared memory and 512
+// threads per CTA; each is timed as the median of 5 applications after one warm-up.
 ibdl_status autotune_2d(Geometry* g, int pi, bool /*fixed_threads*/, cudaStream_t s, const double* Q, double* Y) {
-  const int saved_R = g->rows_per_cta[pi], saved_C = g->cols_per_cta[pi];
   const int saved_timing = g->timing;
   g->timing = 0;
   cudaEvent_t e0, e1;
   IBDL_CUDA(cudaEventCreate(&e0));
   IBDL_CUDA(cudaEventCreate(&e1));
-  float best = 1e30f;
-  TuneVal bestv{saved_R, saved_C};
   ibdl_status err = IBDL_OK;
+  auto time_shape = [&](int R, int C, int floor, float* med) -> ibdl_status {
+    g->rows_per_cta[pi] = R;
+    g->cols_per_cta[pi] = C;
+    g->threads[pi] = floor;
+    float ms[5];
+    IBDL_TRY(apply_2d(g, pi ? IBDL_FP32 : IBDL_FP64, Q, Y, s, nullptr));
+    for (int k = 0; k < 5; ++k) {
+      cudaEventRecord(e0, s);
+      IBDL_TRY(apply_2d(g, pi ? IBDL_FP32 : IBDL_FP64, Q, Y, s, nullptr));
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return fail(IBDL_ERR_CUDA, "autotune: event synchronize");
+      cudaEventElapsedTime(&ms[k], e0, e1);
+    }
+    std::sort(ms, ms + 5);
+    *med = ms[2];
+    return IBDL_OK;
+  };
+  TuneVal best{g->rows_per_cta[pi], g->cols_per_cta[pi], g->threads[pi]};
+  float best_ms = 1e30f;
+  const int floors[3] = {0, 256, 512};
   for (int R = 2; R <= 64 && err == IBDL_OK; R *= 2) {
     if (!row_fits(g, pi, R)) continue;
-    for (int C = 1; C <= 32 && err == IBDL_OK; C *= 2) {
-      if (!col_fits(g, pi, C)) continue;
-      g->rows_per_cta[pi] = R;
-      g->cols_per_cta[pi] = C;
-      float ms[5];
-      err = apply_2d(g, pi ? IBDL_FP32 : IBDL_FP64, Q, Y, s, nullptr);
-      for (int k = 0; k < 5 && err == IBDL_OK; ++k) {
-        cudaEventRecord(e0, s);
-        err = apply_2d(g, pi ? IBDL_FP32 : IBDL_FP64, Q, Y, s, nullptr);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) err = fail(IBDL_ERR_CUDA, "autotune: event synchronize");
-        cudaEventElapsedTime(&ms[k], e0, e1);
+    for (int fi = 0; fi < 3 && err == IBDL_OK; ++fi) {
+      float ms = 0;
+      err = time_shape(R, best.C, floors[fi], &ms);
+      if (err == IBDL_OK && ms < best_ms) {
+        best_ms = ms;
+        best.R = R;
+        best.floor = floors[fi];
       }
-      if (err != IBDL_OK) break;
-      std::sort(ms, ms + 5);
-      if (ms[2] < best) {
-        best = ms[2];
-        bestv = {R, C};
-      }
+    }
+  }
+  for (int C = 1; C <= 32 && err == IBDL_OK; C *= 2) {
+    if (!col_fits(g, pi, C)) continue;
+    float ms = 0;
+    err = time_shape(best.R, C, best.floor, &ms);
+    if (err == IBDL_OK && ms < best_ms) {
+      best_ms = ms;
+      best.C = C;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   g->timing = saved_timing;
-  g->rows_per_cta[pi] = bestv.R;
-  g->cols_per_cta[pi] = bestv.C;
-  if (err == IBDL_OK) tuned_store(tune_key(g, pi), bestv);
+  g->rows_per_cta[pi] = best.R;
+  g->cols_per_cta[pi] = best.C;
+  g->threads[pi] = best.floor;
+  if (err == IBDL_OK) tuned_store(tune_key(g, pi), best);
   return err;
 }
 
@@ -531,9 +558,9 @@ void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target) {
   }
 }
 
-// Default shapes: about 256 threads per CTA, but at least 2·152 CTAs per kernel where the grid
-// allows (one GB300 has 152 SMs); the autotuner refines them. IBDL_PLAN_R and IBDL_PLAN_C
-// override (for tuning experiments).
+// Default shapes: about 256 FFT lanes per CTA, but at least 2·152 CTAs per kernel where the grid
+// allows (one GB300 has 152 SMs), and at least 256 threads in the row kernels; the autotuner
+// refines them. IBDL_PLAN_R and IBDL_PLAN_C override (for tuning experiments).
 ibdl_status plan_2d(Geometry* g) {
   const int n = g->n, L = log2i(n), qt = threads_per_seq_2d(L);
   const int min_ctas = 2 * 152;
@@ -555,12 +582,17 @@ ibdl_status plan_2d(Geometry* g) {
     if (R == 0 || C == 0) R = C = 0;
     g->rows_per_cta[pi] = R;
     g->cols_per_cta[pi] = C;
-    g->threads[pi] = 0;
+    g->threads[pi] = 256;  // the row kernels' loops (clearing, spreading, unpacking) get 256 threads
     TuneVal tv;
     if (R && tuned_lookup(tune_key(g, pi), &tv)) {
       g->rows_per_cta[pi] = tv.R;
       g->cols_per_cta[pi] = tv.C;
+      g->threads[pi] = tv.floor;
     }
+  }
+  if (const char* e = getenv("IBDL_THREADS")) {
+    const int v = atoi(e);
+    if (v >= 0 && v <= kMaxThreads2d && v % 32 == 0) g->threads[0] = g->threads[1] = v;
   }
   if (g->rows_per_cta[0] == 0 && g->rows_per_cta[1] == 0)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT");

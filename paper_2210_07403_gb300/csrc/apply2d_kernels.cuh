@@ -69,17 +69,22 @@ constexpr int kMinL2d = 4, kMaxL2d = 13;
 __host__ __device__ constexpr int lanes_per_thread_2d(int L) { return L >= 13 ? 2 : 1; }
 __host__ __device__ constexpr int threads_per_seq_2d(int L) { return (1 << L) / 8 / lanes_per_thread_2d(L); }
 
-// Per-precision register policy: NF fields of a kernel, FL of them transformed in lockstep;
-// twiddles in registers when they fit the budget, else read from the table at each use.
+// Thread groups across the NF fields of a kernel: one group per field when NF·QT threads fit in a
+// CTA (each thread transforms one field), else a single group that transforms the fields one
+// after another.
+__host__ __device__ constexpr int field_groups_2d(int nf, int L) {
+  return nf * threads_per_seq_2d(L) <= kMaxThreads2d ? nf : 1;
+}
+
+// Per-precision register policy: twiddles in registers when they fit the budget, else read from
+// the table at each use.
 template <typename T, int L, int NF>
 struct Cfg2 {
   static constexpr int V = lanes_per_thread_2d(L);
   static constexpr int QT = threads_per_seq_2d(L);
-  static constexpr bool F32 = sizeof(T) == 4;
-  static constexpr int FL = F32 ? (V == 1 ? (NF <= 3 ? NF : 2) : 1) : 1;
-  static constexpr int NG = (NF + FL - 1) / FL;  // field groups
+  static constexpr int NGRP = field_groups_2d(NF, L);
   static constexpr int NTW = F8<L, V>::NTW;
-  static constexpr bool TWR = F32 ? (NTW * V <= 21) : (NTW * V <= 11);
+  static constexpr bool TWR = sizeof(T) == 4 ? (NTW * V <= 21) : (NTW * V <= 14);
   using TW = std::conditional_t<TWR, TwRegs<T, L>, TwTable<T, L>>;
 };
 
@@ -202,7 +207,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   constexpr int NC = Traits<OP>::C;
   using CF = Cfg2<T, L, NIN>;
   using F = F8<L, CF::V>;
-  constexpr int n = F::N, V = CF::V, QT = CF::QT, FL = CF::FL;
+  constexpr int n = F::N, V = CF::V, QT = CF::QT, NGRP = CF::NGRP;
   const int R = p.R, half = R >> 1, M = p.M;
   // sequence (field f, row pair rp) at buf + (f·half + rp)·PN; accumulation view: field f, local
   // row lr, column x → real part (even lr) or imaginary part (odd lr) of element
@@ -210,8 +215,11 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   T* acc = reinterpret_cast<T*>(buf);
   const int r0 = unit * R;
-  const int rp = threadIdx.x / QT, j0 = threadIdx.x - rp * QT;
-  const bool active = rp < half;
+  // FFT lanes: thread (group g, row pair rp, lane j0); threads past NGRP·half·QT only help with
+  // the loops (clearing, spreading, unpacking)
+  const int q = threadIdx.x / QT, j0 = threadIdx.x - q * QT;
+  const int g = q / half, rp = q - g * half;
+  const bool active = g < NGRP;
   // prologue independent of the previous kernel, then wait for it (programmatic launch)
   for (int i = threadIdx.x; i < NIN * half * F::PN * 2; i += blockDim.x) acc[i] = T(0);
   typename CF::TW tw[V];
@@ -321,31 +329,27 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   }
   __syncthreads();
 
-  // forward FFT of every (field, row pair) sequence, FL fields in lockstep; each lane reads and
-  // writes back only its own positions, so only the exchanges inside need barriers
-  static_for<0, CF::NG>([&](auto gi) {
-    constexpr int G = decltype(gi)::value;
-    constexpr int FG = (NIN - G * FL) < FL ? (NIN - G * FL) : FL;
-    cplx<T>* sb = buf + ((size_t)(G * FL) * half + rp) * F::PN;
-    cplx<T> x[FG][V][8];
+  // forward FFT of every (field, row pair) sequence; each lane reads and writes back only its own
+  // positions, so only the exchanges inside need barriers
+#pragma unroll
+  for (int k = 0; k < NIN / NGRP; ++k) {
+    const int f = g + k * NGRP;
+    cplx<T>* sb = buf + ((size_t)f * half + rp) * F::PN;
+    cplx<T> x[1][V][8];
     if (active) {
 #pragma unroll
-      for (int f = 0; f < FG; ++f)
+      for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-#pragma unroll
-          for (int s = 0; s < 8; ++s) x[f][v][s] = sb[f * half * F::PN + ppos(j0 + v * QT + s * F::Q)];
+        for (int s = 0; s < 8; ++s) x[0][v][s] = sb[ppos(j0 + v * QT + s * F::Q)];
     }
-    f8_fft<T, false, L, V, FG>(x, sb, half * F::PN, j0, tw, active);
+    f8_fft<T, false, L, V, 1>(x, sb, 0, j0, tw, active);
     if (active) {
 #pragma unroll
-      for (int f = 0; f < FG; ++f)
+      for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-#pragma unroll
-          for (int s = 0; s < 8; ++s) sb[f * half * F::PN + ppos(j0 + v * QT + s * F::Q)] = x[f][v][s];
+        for (int s = 0; s < 8; ++s) sb[ppos(j0 + v * QT + s * F::Q)] = x[0][v][s];
     }
-  });
+  }
   __syncthreads();
 
   // unpack Z = FFT(a + i b) of the row pair (2j, 2j + 1) into A = FFT(a) (even rows) and
@@ -477,11 +481,13 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
   constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
   using CF = Cfg2<T, L, NMAX>;
   using F = F8<L, CF::V>;
-  constexpr int n = F::N, nh = n / 2, V = CF::V, QT = CF::QT, FL = CF::FL, Q = F::Q, PN = F::PN;
+  constexpr int n = F::N, nh = n / 2, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q, PN = F::PN;
   const int C = p.C, R = p.R;
   const int k0 = unit * C;
-  const int c = threadIdx.x / QT, j0 = threadIdx.x - c * QT;
-  const bool active = c < C;
+  // thread (group g, column c, lane j0)
+  const int q = threadIdx.x / QT, j0 = threadIdx.x - q * QT;
+  const int g = q / C, c = q - g * C;
+  const bool active = g < NGRP;
   const int kx = k0 + c;
   // sequence (field f, column c) at buf + (f·C + c)·PN
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -566,38 +572,38 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
         for (int s = 0; s < 8; ++s) p.spec[col_at<L>(0, j0 + v * QT + s * Q, kx, R)] = x[0][v][s];
     }
   } else {
-    // forward transforms of the NIN input fields (FL in lockstep), results left in shared memory
-    static_for<0, (NIN + FL - 1) / FL>([&](auto gi) {
-      constexpr int G = decltype(gi)::value;
-      constexpr int FG = (NIN - G * FL) < FL ? (NIN - G * FL) : FL;
-      cplx<T>* sb = buf + ((size_t)(G * FL) * C + c) * PN;
-      cplx<T> x[FG][V][8];
-      if (active) {
+    // forward transforms of the NIN input fields, results left in shared memory
 #pragma unroll
-        for (int f = 0; f < FG; ++f)
+    for (int k = 0; k < (NIN + NGRP - 1) / NGRP; ++k) {
+      const int f = g + k * NGRP;
+      const bool act = active && f < NIN;
+      cplx<T>* sb = buf + ((size_t)f * C + c) * PN;
+      cplx<T> x[1][V][8];
+      if (act) {
 #pragma unroll
-          for (int v = 0; v < V; ++v)
+        for (int v = 0; v < V; ++v)
 #pragma unroll
-            for (int s = 0; s < 8; ++s) x[f][v][s] = p.spec[col_at<L>(G * FL + f, j0 + v * QT + s * Q, kx, R)];
+          for (int s = 0; s < 8; ++s) x[0][v][s] = p.spec[col_at<L>(f, j0 + v * QT + s * Q, kx, R)];
       }
-      f8_fft<T, false, L, V, FG>(x, sb, C * PN, j0, tw, active);
-      if (active) {
+      f8_fft<T, false, L, V, 1>(x, sb, 0, j0, tw, act);
+      if (act) {
 #pragma unroll
-        for (int f = 0; f < FG; ++f)
+        for (int v = 0; v < V; ++v)
 #pragma unroll
-          for (int v = 0; v < V; ++v)
-#pragma unroll
-            for (int s = 0; s < 8; ++s) sb[(size_t)f * C * PN + ppos(j0 + v * QT + s * Q)] = x[f][v][s];
+          for (int s = 0; s < 8; ++s) sb[ppos(j0 + v * QT + s * Q)] = x[0][v][s];
       }
-    });
-    // symbol at the lane's own points, in place (each lane reads and writes only its own
-    // positions); the packed column reads its partners (P(−ky)) between two barriers
+    }
+    __syncthreads();
+    // symbol at the points of the lane's positions, split over the groups (point s to group
+    // s mod NGRP), in place; the packed column reads its partners (P(−ky)) and writes after a
+    // second barrier
     if (!packed) {
       if (active) {
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
           for (int s = 0; s < 8; ++s) {
+            if (s % NGRP != g) continue;
             const int ky = j0 + v * QT + s * Q;
             cplx<T> in[NIN], o[NOUT];
 #pragma unroll
@@ -608,13 +614,13 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
           }
       }
     } else {
-      __syncthreads();
       cplx<T> o[V][8][NOUT];
       if (active) {
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
           for (int s = 0; s < 8; ++s) {
+            if (s % NGRP != g) continue;
             const int ky = j0 + v * QT + s * Q;
             cplx<T> in[NIN];
 #pragma unroll
@@ -634,35 +640,35 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
-          for (int s = 0; s < 8; ++s)
+          for (int s = 0; s < 8; ++s) {
+            if (s % NGRP != g) continue;
 #pragma unroll
             for (int f = 0; f < NOUT; ++f) buf[((size_t)f * C + c) * PN + ppos(j0 + v * QT + s * Q)] = o[v][s][f];
+          }
       }
     }
+    __syncthreads();
     // inverse transforms of the NOUT output fields, straight to the half spectra
-    static_for<0, (NOUT + FL - 1) / FL>([&](auto gi) {
-      constexpr int G = decltype(gi)::value;
-      constexpr int FG = (NOUT - G * FL) < FL ? (NOUT - G * FL) : FL;
-      cplx<T>* sb = buf + ((size_t)(G * FL) * C + c) * PN;
-      cplx<T> x[FG][V][8];
-      if (active) {
 #pragma unroll
-        for (int f = 0; f < FG; ++f)
+    for (int k = 0; k < (NOUT + NGRP - 1) / NGRP; ++k) {
+      const int f = g + k * NGRP;
+      const bool act = active && f < NOUT;
+      cplx<T>* sb = buf + ((size_t)f * C + c) * PN;
+      cplx<T> x[1][V][8];
+      if (act) {
 #pragma unroll
-          for (int v = 0; v < V; ++v)
+        for (int v = 0; v < V; ++v)
 #pragma unroll
-            for (int s = 0; s < 8; ++s) x[f][v][s] = sb[(size_t)f * C * PN + ppos(j0 + v * QT + s * Q)];
+          for (int s = 0; s < 8; ++s) x[0][v][s] = sb[ppos(j0 + v * QT + s * Q)];
       }
-      f8_fft<T, true, L, V, FG>(x, sb, C * PN, j0, tw, active);
-      if (active) {
+      f8_fft<T, true, L, V, 1>(x, sb, 0, j0, tw, act);
+      if (act) {
 #pragma unroll
-        for (int f = 0; f < FG; ++f)
+        for (int v = 0; v < V; ++v)
 #pragma unroll
-          for (int v = 0; v < V; ++v)
-#pragma unroll
-            for (int s = 0; s < 8; ++s) p.spec[col_at<L>(G * FL + f, j0 + v * QT + s * Q, kx, R)] = x[f][v][s];
+          for (int s = 0; s < 8; ++s) p.spec[col_at<L>(f, j0 + v * QT + s * Q, kx, R)] = x[0][v][s];
       }
-    });
+    }
   }
 }
 
@@ -727,12 +733,14 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   constexpr int NOUT = Traits<OP>::NOUT;
   using CF = Cfg2<T, L, NOUT>;
   using F = F8<L, CF::V>;
-  constexpr int n = F::N, V = CF::V, QT = CF::QT, FL = CF::FL, Q = F::Q, PN = F::PN;
+  constexpr int n = F::N, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q, PN = F::PN;
   const int R = p.R, half = R >> 1, M = p.M;
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   const int r0 = unit * R;
-  const int rp = threadIdx.x / QT, j0 = threadIdx.x - rp * QT;
-  const bool active = rp < half;
+  // FFT lanes: thread (group g, row pair rp, lane j0); threads past NGRP·half·QT only gather
+  const int q = threadIdx.x / QT, j0 = threadIdx.x - q * QT;
+  const int g = q / half, rp = q - g * half;
+  const bool active = g < NGRP;
   typename CF::TW tw[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) tw[v].load(p.tw, j0 + v * QT);
@@ -753,29 +761,25 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   if (stopped) return;
 
   // inverse FFT of every (field, row pair) sequence, its first stage fed from the half spectra
-  static_for<0, (NOUT + FL - 1) / FL>([&](auto gi) {
-    constexpr int G = decltype(gi)::value;
-    constexpr int FG = (NOUT - G * FL) < FL ? (NOUT - G * FL) : FL;
-    cplx<T>* sb = buf + ((size_t)(G * FL) * half + rp) * PN;
-    cplx<T> x[FG][V][8];
+#pragma unroll
+  for (int k = 0; k < NOUT / NGRP; ++k) {
+    const int f = g + k * NGRP;
+    cplx<T>* sb = buf + ((size_t)f * half + rp) * PN;
+    cplx<T> x[1][V][8];
     if (active) {
 #pragma unroll
-      for (int f = 0; f < FG; ++f)
+      for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-#pragma unroll
-          for (int s = 0; s < 8; ++s) x[f][v][s] = row_z<T, L>(p.spec, G * FL + f, r0, rp, R, j0 + v * QT + s * Q);
+        for (int s = 0; s < 8; ++s) x[0][v][s] = row_z<T, L>(p.spec, f, r0, rp, R, j0 + v * QT + s * Q);
     }
-    f8_fft<T, true, L, V, FG>(x, sb, half * PN, j0, tw, active);
+    f8_fft<T, true, L, V, 1>(x, sb, 0, j0, tw, active);
     if (active) {
 #pragma unroll
-      for (int f = 0; f < FG; ++f)
+      for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-#pragma unroll
-          for (int s = 0; s < 8; ++s) sb[(size_t)f * half * PN + ppos(j0 + v * QT + s * Q)] = x[f][v][s];
+        for (int s = 0; s < 8; ++s) sb[ppos(j0 + v * QT + s * Q)] = x[0][v][s];
     }
-  });
+  }
   __syncthreads();
   // real values: field f, local row lr, column x at element e = (f·half + lr/2)·n + x, part lr & 1
   const T* u = reinterpret_cast<const T*>(buf);
@@ -939,7 +943,7 @@ __host__ __device__ constexpr size_t smem_cols_2d(int nf, int C, int L) {
 struct Launch2D {
   int R, C;                 // rows per band, kx columns per CTA
   size_t smem_row, smem_col, smem_gather;
-  int threads_row, threads_col;
+  int threads_row, threads_col, threads_gather;
   bool pdl;
   int grid_mode;            // G_INTERP or G_GRID
 };

@@ -83,9 +83,10 @@ ibdl_status launch_apply_2d(Geometry* g, const RowParams<T>& rp, const ColParams
   IBDL_CUDA(launch_k(k_colpass<T, OP, L>, (n / 2) / lc.C, lc.threads_col, lc.smem_col, s, lc.pdl, cp));
   if (g->timing) timing_mark(g, s, st0 + 1);
   if (lc.grid_mode == G_GRID)
-    IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_GRID, L>, n / lc.R, lc.threads_row, lc.smem_gather, s, lc.pdl, rp));
+    IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_GRID, L>, n / lc.R, lc.threads_gather, lc.smem_gather, s, lc.pdl,
+                       rp));
   else
-    IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_INTERP, L>, n / lc.R, lc.threads_row, lc.smem_gather, s, lc.pdl,
+    IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_INTERP, L>, n / lc.R, lc.threads_gather, lc.smem_gather, s, lc.pdl,
                        rp));
   if (g->timing) timing_mark(g, s, st0 + 2);
   g->launches += 3;
@@ -144,7 +145,7 @@ ibdl_status batch_launch_2d(Batch* B, int mode, const double* in_base, double* o
                      (const int2*)B->row_units[pi], in_base, out_base));
   IBDL_CUDA(launch_k(kb_colpass<T, OP>, B->ncol_units[pi], B->threads_col[pi], B->smem_col[pi], s, true, cp,
                      (const int2*)B->col_units[pi]));
-  IBDL_CUDA(launch_k(kb_rowifft_gather<T, OP>, B->nrow_units[pi], B->threads_row[pi], B->smem_gather[pi], s, true, rp,
+  IBDL_CUDA(launch_k(kb_rowifft_gather<T, OP>, B->nrow_units[pi], B->threads_gather[pi], B->smem_gather[pi], s, true, rp,
                      (const int2*)B->row_units[pi], in_base, out_base));
   B->launches += 3;
   IBDL_CUDA(cudaGetLastError());

@@ -121,7 +121,7 @@ struct Geometry {
   int cols_per_cta[2];   // kx columns per CTA in the column kernels (3-D: the y passes)
   int zcols_per_cta[2];  // 3-D: kx columns per CTA in the z pass
   size_t smem_row[2], smem_col[2], smem_row_inv[2];
-  int threads[2];        // threads per CTA of the 2-D kernels per precision (0: the default)
+  int threads[2];        // 2-D: least threads per CTA of the row kernels, per precision (0: none)
 
   // GMRES workspace (allocated lazily, sized for `krylov_m`)
   int krylov_m;
@@ -160,7 +160,7 @@ struct Batch {
   int2* col_units[2];
   int nrow_units[2], ncol_units[2];
   size_t smem_row[2], smem_col[2], smem_gather[2];
-  int threads_row[2], threads_col[2];  // CTA sizes of the row and column launches
+  int threads_row[2], threads_col[2], threads_gather[2];  // CTA sizes of the three launches
   // batched GMRES
   int m;                 // restart length the workspace was sized for (0: none yet)
   int64_t* voff;         // host [count]: offset of problem b's basis in V
