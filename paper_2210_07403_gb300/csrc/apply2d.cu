@@ -545,8 +545,9 @@ ibdl_status autotune_2d(Geometry* g, int pi, bool /*fixed_threads*/, cudaStream_
 }
 
 // Shapes from the volume rule: about `target` complex elements of FFT per CTA (so about
-// target/8 lane-threads), R ≤ n/2, within shared memory and the thread limit.
-void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target) {
+// target/8 lane-threads), R ≤ n/2, within shared memory and the thread limit; `floor` is the row
+// kernels' least thread count.
+void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target, int floor) {
   const int n = g->n;
   int R = 2 * pow2_in(row_target / (n * g->nf_in), 1, n / 4 > 1 ? n / 4 : 1);
   while (R > 2 && !row_fits(g, pi, R)) R /= 2;
@@ -555,6 +556,7 @@ void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target) {
   if (row_fits(g, pi, R) && col_fits(g, pi, C)) {
     g->rows_per_cta[pi] = R;
     g->cols_per_cta[pi] = C;
+    g->threads[pi] = floor;
   }
 }
 

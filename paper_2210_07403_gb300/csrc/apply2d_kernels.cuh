@@ -200,7 +200,10 @@ __device__ __forceinline__ SpreadItem<T> spread_item(const RowParams<T>& p, cons
   return it;
 }
 
-template <typename T, int OP, int L>
+// PF: load the FFT twiddles (and, in the column pass, the symbol rows) before the dependency
+// wait, for latency (single problems); batched launches load them where they are used, which
+// keeps registers down and occupancy up.
+template <typename T, int OP, int L, bool PF = true>
 __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int unit, int nunits,
                                                    unsigned char* smem_raw) {
   constexpr int NIN = Traits<OP>::NIN;
@@ -223,8 +226,10 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   // prologue independent of the previous kernel, then wait for it (programmatic launch)
   for (int i = threadIdx.x; i < NIN * half * F::PN * 2; i += blockDim.x) acc[i] = T(0);
   typename CF::TW tw[V];
+  if constexpr (PF) {
 #pragma unroll
-  for (int v = 0; v < V; ++v) tw[v].load(p.tw, j0 + v * QT);
+    for (int v = 0; v < V; ++v) tw[v].load(p.tw, j0 + v * QT);
+  }
   // the points whose stencil meets the band, and this thread's first work item (16 per point)
   const PointRanges pr = band_points(p.cell_start, n, r0, R);
   const int nitems = p.grid_in ? 0 : pr.cnt * 16;
@@ -329,6 +334,10 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   }
   __syncthreads();
 
+  if constexpr (!PF) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) tw[v].load(p.tw, j0 + v * QT);
+  }
   // forward FFT of every (field, row pair) sequence; each lane reads and writes back only its own
   // positions, so only the exchanges inside need barriers
 #pragma unroll
@@ -370,7 +379,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
       v = (rr & 1) ? mk(T(0.5) * (zk.y + zc.y), T(0.5) * (zc.x - zk.x))
                    : mk(T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y));
     }
-    p.spec[((size_t)f * n + r0) * nh + (t - f * (nh << lR))] = v;
+    p.spec[(f * n + r0) * nh + (t - f * (nh << lR))] = v;
   }
 }
 
@@ -384,13 +393,18 @@ __global__ void __launch_bounds__(kMaxThreads2d) k_spread_rowfft(RowParams<T> p)
 // Fourier symbols: NIN transformed fields in → NOUT out; lap = |k̃|² (sum of the per-axis
 // Laplacian symbols), dkx, dky the per-axis derivative symbols
 // ------------------------------------------------------------------------------------------
+// a/b: the hardware reciprocal estimate in FP32 (within 2 ulp, well inside the FP32 application's
+// rounding), IEEE division in FP64
+__device__ __forceinline__ float sym_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sym_div(double a, double b) { return a / b; }
+
 template <typename T, int OP>
 __device__ __forceinline__ void apply_symbol(const ColParams<T>& p, T lap, T dkx, T dky, const cplx<T>* in,
                                              cplx<T>* out) {
   if (OP == OP_SCALAR_AN || OP == OP_SCALAR_SD || OP == OP_ADJ_AN || OP == OP_ADJ_SD || OP == OP_SL) {
     // −L⁻¹ ↦ 1/(|k|² + λ), zero mode dropped when λ = 0 (Δ₀⁻¹)
     const T den = lap + p.lam;
-    const T sig = den != T(0) ? p.scale / den : T(0);
+    const T sig = den != T(0) ? sym_div(p.scale, den) : T(0);
     if (OP == OP_SCALAR_AN || OP == OP_ADJ_AN || OP == OP_SL) {
       out[0] = cscale(in[0], sig);
     } else if (OP == OP_SCALAR_SD) {
@@ -404,17 +418,17 @@ __device__ __forceinline__ void apply_symbol(const ColParams<T>& p, T lap, T dkx
     }
   } else if (OP == OP_STOKES_T) {
     // transpose of the Stokes multiplier (conjugate symbol): v̂_s = −i k̃·ψ̂/|k|², v̂_g = P̂ψ̂/|k|²
-    const T inv = lap != T(0) ? T(1) / lap : T(0);
+    const T inv = lap != T(0) ? sym_div(T(1), lap) : T(0);
     const cplx<T> kp = cadd(cscale(in[0], dkx), cscale(in[1], dky));
     const T sc = inv * p.scale;
     // Brinkman (λ > 0): the projected part carries μ/(μ|k|² + λ) in place of 1/|k|²
-    const T sg = p.lam > T(0) ? p.mu / (p.mu * lap + p.lam) * p.scale : sc;
+    const T sg = p.lam > T(0) ? sym_div(p.mu, p.mu * lap + p.lam) * p.scale : sc;
     out[0] = cscale(cmuli(kp), -sc);
     out[1] = cscale(csub(in[0], cscale(kp, dkx * inv)), sg);
     out[2] = cscale(csub(in[1], cscale(kp, dky * inv)), sg);
   } else {
     // Stokes, interior, η = 0: û = (i k̃ ŝ + P̂ ĝ)/|k|², P̂ = I − k̃k̃ᵀ/|k|²
-    const T inv = lap != T(0) ? T(1) / lap : T(0);
+    const T inv = lap != T(0) ? sym_div(T(1), lap) : T(0);
     cplx<T> gx, gy;
     if (OP == OP_STOKES_AN) {
       gx = in[1];
@@ -428,7 +442,7 @@ __device__ __forceinline__ void apply_symbol(const ColParams<T>& p, T lap, T dkx
     const T sc = inv * p.scale;
     if (p.lam > T(0)) {
       // Brinkman (Sec. 6.3.2): û = i k̃ ŝ/|k|² + μ P̂ ĝ/(μ|k|² + λ), defined at k = 0 as well
-      const T sg = p.mu / (p.mu * lap + p.lam) * p.scale;
+      const T sg = sym_div(p.mu, p.mu * lap + p.lam) * p.scale;
       out[0] = cadd(cscale(is, dkx * sc), cscale(csub(gx, cscale(kg, dkx * inv)), sg));
       out[1] = cadd(cscale(is, dky * sc), cscale(csub(gy, cscale(kg, dky * inv)), sg));
     } else {
@@ -468,13 +482,14 @@ __device__ __forceinline__ void symbol_packed(const ColParams<T>& p, T lap0, T d
 // kernel 2: FFT along y, symbol, inverse FFT along y, for C kx columns per CTA
 // ------------------------------------------------------------------------------------------
 // offset of element (row m) of column k of field f in the band-major half spectra
+// (a geometry's half spectra hold at most 4·8192·4096 < 2^31 elements, so 32-bit offsets suffice)
 template <int L>
-__device__ __forceinline__ size_t col_at(int f, int m, int k, int R) {
+__device__ __forceinline__ int col_at(int f, int m, int k, int R) {
   constexpr int n = 1 << L, nh = n / 2;
-  return ((size_t)f * n + (m & ~(R - 1))) * nh + (size_t)k * R + (m & (R - 1));
+  return (f * n + (m & ~(R - 1))) * nh + k * R + (m & (R - 1));
 }
 
-template <typename T, int OP, int L>
+template <typename T, int OP, int L, bool PF = true>
 __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, unsigned char* smem_raw) {
   constexpr int NIN = Traits<OP>::NIN;
   constexpr int NOUT = Traits<OP>::NOUT;
@@ -497,7 +512,7 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
   // per-axis symbols: kx of this column (the packed column also needs kx = n/2) and, with one
   // field in and out, ky of the lane's rows, loaded before the wait; with more fields the ky
   // values are read at use (registers go to the fields)
-  constexpr bool PREF = NIN == 1 && NOUT == 1;
+  constexpr bool PREF = PF && NIN == 1 && NOUT == 1;
   const bool packed = k0 == 0;  // uniform over the CTA: column 0 holds kx = 0 and kx = n/2
   T lapx = 0, derx = 0, lapn = 0, dern = 0;
   T lapy[PREF ? V : 1][8], dery[PREF ? V : 1][8];
@@ -553,12 +568,13 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
         for (int s = 0; s < 8; ++s) {
           const cplx<T> in[1] = {x[0][v][s]};
           cplx<T> out[1];
+          const int ky = j0 + v * QT + s * Q;
+          const T ly = PREF ? lapy[PREF ? v : 0][s] : p.lap1[ky], dy = PREF ? dery[PREF ? v : 0][s] : p.der1[ky];
           if (kx == 0) {
-            const int ky = j0 + v * QT + s * Q;
             const cplx<T> pm[1] = {sb[ppos((n - ky) & (n - 1))]};
-            symbol_packed<T, OP>(p, lapx, derx, lapn, dern, lapy[v][s], dery[v][s], in, pm, out);
+            symbol_packed<T, OP>(p, lapx, derx, lapn, dern, ly, dy, in, pm, out);
           } else {
-            symbol_point<T, OP>(p, lapx, derx, lapy[v][s], dery[v][s], in, out);
+            symbol_point<T, OP>(p, lapx, derx, ly, dy, in, out);
           }
           x[0][v][s] = out[0];
         }
@@ -686,17 +702,14 @@ __global__ void __launch_bounds__(kMaxThreads2d) k_colpass(ColParams<T> p) {
 template <typename T, int L>
 __device__ __forceinline__ cplx<T> row_z(const cplx<T>* __restrict__ spec, int f, int r0, int jj, int R, int m) {
   constexpr int n = 1 << L, nh = n / 2;
-  const cplx<T>* band = spec + ((size_t)f * n + r0) * nh + 2 * jj;
+  const cplx<T>* band = spec + ((f * n + r0) * nh + 2 * jj);
   if (m == 0 || m == nh) {
     const cplx<T> A = band[0], B = band[1];
     return m == 0 ? mk(A.x, B.x) : mk(A.y, B.y);
   }
-  if (m < nh) {
-    const cplx<T> A = band[(size_t)m * R], B = band[(size_t)m * R + 1];
-    return mk(A.x - B.y, A.y + B.x);
-  }
-  const cplx<T> A = band[(size_t)(n - m) * R], B = band[(size_t)(n - m) * R + 1];
-  return mk(A.x + B.y, B.x - A.y);
+  const int k = m < nh ? m : n - m;
+  const cplx<T> A = band[k * R], B = band[k * R + 1];
+  return m < nh ? mk(A.x - B.y, A.y + B.x) : mk(A.x + B.y, B.x - A.y);
 }
 
 // One gather work item (point, stencil row): the point-table values it needs
@@ -728,7 +741,7 @@ __device__ __forceinline__ GatherItem<T> gather_item(const RowParams<T>& p, cons
   return it;
 }
 
-template <typename T, int OP, int GMODE, int L>
+template <typename T, int OP, int GMODE, int L, bool PF = true>
 __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int unit, unsigned char* smem_raw) {
   constexpr int NOUT = Traits<OP>::NOUT;
   using CF = Cfg2<T, L, NOUT>;
@@ -749,7 +762,7 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   const PointRanges pr = band_points(p.cell_start, n, r0, R);
   const int nitems = GMODE == G_GRID ? 0 : pr.cnt * 4;
   GatherItem<T> it0 = {};
-  if ((int)threadIdx.x < nitems) it0 = gather_item(p, pr, threadIdx.x, r0);
+  if (PF && (int)threadIdx.x < nitems) it0 = gather_item(p, pr, threadIdx.x, r0);
   // the stop flag and the Krylov index (the output column) are final before the wait: the GMRES
   // step that writes them is three kernels back (see the column pass)
   const bool stopped = p.stop && *p.stop;
@@ -798,7 +811,7 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
 
   // one thread per (point, stencil row in the band): the row's partial sum is added to Y
   for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
-    const GatherItem<T> it = t == (int)threadIdx.x ? it0 : gather_item(p, pr, t, r0);
+    const GatherItem<T> it = (PF && t == (int)threadIdx.x) ? it0 : gather_item(p, pr, t, r0);
     const int lr = it.lr;
     if (lr >= R) continue;
     const int i = it.i;
@@ -868,31 +881,35 @@ __global__ void __launch_bounds__(kMaxThreads2d) k_rowifft_gather(RowParams<T> p
 // batched launches: one grid per stage covers every problem of a batch; CTA i runs work unit
 // units[i] = (problem, unit) with that problem's parameter block and transform size
 // ------------------------------------------------------------------------------------------
-template <typename T, int OP, int L>
+// The batched kernels are compiled for sizes up to 2^LMAX: a batch whose grids are all small runs
+// the variant without the large-grid bodies (whose registers would otherwise bound every CTA).
+constexpr int kBatchSmallL2d = 9;
+
+template <typename T, int OP, int L, int LMAX>
 __device__ __forceinline__ void kb_row_dispatch(const RowParams<T>& p, int unit, unsigned char* smem, bool fwd) {
-  if constexpr (L <= kMaxL2d) {
+  if constexpr (L <= LMAX) {
     if (p.log2n == L) {
       if (fwd)
-        spread_rowfft_body<T, OP, L>(p, unit, p.n / p.R, smem);
+        spread_rowfft_body<T, OP, L, false>(p, unit, p.n / p.R, smem);
       else
-        rowifft_gather_body<T, OP, G_INTERP, L>(p, unit, smem);
+        rowifft_gather_body<T, OP, G_INTERP, L, false>(p, unit, smem);
     } else {
-      kb_row_dispatch<T, OP, L + 1>(p, unit, smem, fwd);
+      kb_row_dispatch<T, OP, L + 1, LMAX>(p, unit, smem, fwd);
     }
   }
 }
 
-template <typename T, int OP, int L>
+template <typename T, int OP, int L, int LMAX>
 __device__ __forceinline__ void kb_col_dispatch(const ColParams<T>& p, int unit, unsigned char* smem) {
-  if constexpr (L <= kMaxL2d) {
+  if constexpr (L <= LMAX) {
     if (p.log2n == L)
-      colpass_body<T, OP, L>(p, unit, smem);
+      colpass_body<T, OP, L, false>(p, unit, smem);
     else
-      kb_col_dispatch<T, OP, L + 1>(p, unit, smem);
+      kb_col_dispatch<T, OP, L + 1, LMAX>(p, unit, smem);
   }
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int LMAX>
 __global__ void __launch_bounds__(kMaxThreads2d) kb_spread_rowfft(const RowParams<T>* __restrict__ P, const int2* units,
                                                                   const double* in_base, double* out_base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -900,18 +917,18 @@ __global__ void __launch_bounds__(kMaxThreads2d) kb_spread_rowfft(const RowParam
   RowParams<T> p = P[u.x];
   p.in = in_base + p.io_off;
   p.out = out_base + p.io_off;
-  kb_row_dispatch<T, OP, kMinL2d>(p, u.y, smem_raw, true);
+  kb_row_dispatch<T, OP, kMinL2d, LMAX>(p, u.y, smem_raw, true);
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int LMAX>
 __global__ void __launch_bounds__(kMaxThreads2d) kb_colpass(const ColParams<T>* __restrict__ P, const int2* units) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int2 u = units[blockIdx.x];
   const ColParams<T> p = P[u.x];
-  kb_col_dispatch<T, OP, kMinL2d>(p, u.y, smem_raw);
+  kb_col_dispatch<T, OP, kMinL2d, LMAX>(p, u.y, smem_raw);
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int LMAX>
 __global__ void __launch_bounds__(kMaxThreads2d) kb_rowifft_gather(const RowParams<T>* __restrict__ P, const int2* units,
                                                                    const double* in_base, double* out_base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -919,7 +936,7 @@ __global__ void __launch_bounds__(kMaxThreads2d) kb_rowifft_gather(const RowPara
   RowParams<T> p = P[u.x];
   p.in = in_base + p.io_off;
   p.out = out_base + p.io_off;
-  kb_row_dispatch<T, OP, kMinL2d>(p, u.y, smem_raw, false);
+  kb_row_dispatch<T, OP, kMinL2d, LMAX>(p, u.y, smem_raw, false);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -132,24 +132,34 @@ ibdl_status launch_apply_2d(Geometry* g, const RowParams<T>& rp, const ColParams
 // tables; each CTA reads its problem's parameter block and runs the body of that problem's size.
 // mode 0: the caller's vectors; mode 1: the batched GMRES Krylov basis. Instantiated in
 // apply2d_batch_*.cu.
-template <typename T, int OP>
-ibdl_status batch_launch_2d(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
+template <typename T, int OP, int LMAX>
+ibdl_status batch_launch_range(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
   constexpr int pi = std::is_same<T, float>::value ? 1 : 0;
   static std::atomic<unsigned long long> d1{0}, d2{0}, d3{0};
-  IBDL_CUDA(opt_in_smem(kb_spread_rowfft<T, OP>, d1));
-  IBDL_CUDA(opt_in_smem(kb_colpass<T, OP>, d2));
-  IBDL_CUDA(opt_in_smem(kb_rowifft_gather<T, OP>, d3));
+  IBDL_CUDA(opt_in_smem(kb_spread_rowfft<T, OP, LMAX>, d1));
+  IBDL_CUDA(opt_in_smem(kb_colpass<T, OP, LMAX>, d2));
+  IBDL_CUDA(opt_in_smem(kb_rowifft_gather<T, OP, LMAX>, d3));
   const RowParams<T>* rp = static_cast<const RowParams<T>*>(B->rowp[pi][mode]);
   const ColParams<T>* cp = static_cast<const ColParams<T>*>(B->colp[pi]);
-  IBDL_CUDA(launch_k(kb_spread_rowfft<T, OP>, B->nrow_units[pi], B->threads_row[pi], B->smem_row[pi], s, false, rp,
-                     (const int2*)B->row_units[pi], in_base, out_base));
-  IBDL_CUDA(launch_k(kb_colpass<T, OP>, B->ncol_units[pi], B->threads_col[pi], B->smem_col[pi], s, true, cp,
+  IBDL_CUDA(launch_k(kb_spread_rowfft<T, OP, LMAX>, B->nrow_units[pi], B->threads_row[pi], B->smem_row[pi], s, false,
+                     rp, (const int2*)B->row_units[pi], in_base, out_base));
+  IBDL_CUDA(launch_k(kb_colpass<T, OP, LMAX>, B->ncol_units[pi], B->threads_col[pi], B->smem_col[pi], s, true, cp,
                      (const int2*)B->col_units[pi]));
-  IBDL_CUDA(launch_k(kb_rowifft_gather<T, OP>, B->nrow_units[pi], B->threads_gather[pi], B->smem_gather[pi], s, true, rp,
-                     (const int2*)B->row_units[pi], in_base, out_base));
+  IBDL_CUDA(launch_k(kb_rowifft_gather<T, OP, LMAX>, B->nrow_units[pi], B->threads_gather[pi], B->smem_gather[pi], s,
+                     true, rp, (const int2*)B->row_units[pi], in_base, out_base));
   B->launches += 3;
   IBDL_CUDA(cudaGetLastError());
   return IBDL_OK;
+}
+
+// Batched launches of one operator and precision: one launch per stage over the (problem, unit)
+// tables; each CTA reads its problem's parameter block and runs the body of that problem's size.
+// mode 0: the caller's vectors; mode 1: the batched GMRES Krylov basis. Instantiated in
+// apply2d_batch_*.cu.
+template <typename T, int OP>
+ibdl_status batch_launch_2d(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
+  return B->max_log2n <= kBatchSmallL2d ? batch_launch_range<T, OP, kBatchSmallL2d>(B, mode, in_base, out_base, s)
+                                        : batch_launch_range<T, OP, kMaxL2d>(B, mode, in_base, out_base, s);
 }
 
 }  // namespace ibdl

@@ -91,6 +91,7 @@ ibdl_status ibdl_create_batch(const ibdl_geometry_desc* descs, int count, void* 
       return fail(st, msg);
     }
     B->off[i + 1] = B->off[i] + B->geoms[i]->ncomp * B->geoms[i]->M;
+    B->max_log2n = std::max(B->max_log2n, __builtin_ctz(B->geoms[i]->n));
   }
   B->total = B->off[count];
   ibdl_status st = batch_prepare_2d(B);
@@ -134,17 +135,19 @@ ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* str
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // two knobs for the whole batch: the FFT volume per CTA of the row kernels and of the column
+  // three knobs for the whole batch: the FFT volume per CTA of the row kernels and of the column
   // kernel (the band-major spectra make tall row bands and narrow column groups a useful pair),
-  // timed on the batched application itself (throughput, not one problem's latency)
+  // and the row kernels' least thread count, timed on the batched application itself
+  // (throughput, not one problem's latency)
   const int targets[5] = {512, 1024, 2048, 4096, 8192};
+  const int floors[2] = {0, 256};
   for (int pi = 0; pi < 2 && st == IBDL_OK; ++pi) {
     if (!(precision_mask & (pi ? 2 : 1))) continue;
     float best = 1e30f;
-    int best_t = targets[0], best_c = targets[0];
-    for (int ti = 0; ti < 25 && st == IBDL_OK; ++ti) {
-      const int tr = targets[ti / 5], tc = targets[ti % 5];
-      for (int i = 0; i < B->count; ++i) shape_for_target_2d(B->geoms[i], pi, tr, tc);
+    int best_t = targets[0], best_c = targets[0], best_f = 0;
+    for (int ti = 0; ti < 50 && st == IBDL_OK; ++ti) {
+      const int tr = targets[(ti / 2) / 5], tc = targets[(ti / 2) % 5], fl = floors[ti % 2];
+      for (int i = 0; i < B->count; ++i) shape_for_target_2d(B->geoms[i], pi, tr, tc, fl);
       st = batch_prepare_2d(B);
       if (st != IBDL_OK) break;
       float ms[3];
@@ -162,10 +165,11 @@ ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* str
         best = ms[1];
         best_t = tr;
         best_c = tc;
+        best_f = fl;
       }
     }
     if (st == IBDL_OK)
-      for (int i = 0; i < B->count; ++i) shape_for_target_2d(B->geoms[i], pi, best_t, best_c);
+      for (int i = 0; i < B->count; ++i) shape_for_target_2d(B->geoms[i], pi, best_t, best_c, best_f);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -161,6 +161,7 @@ struct Batch {
   int nrow_units[2], ncol_units[2];
   size_t smem_row[2], smem_col[2], smem_gather[2];
   int threads_row[2], threads_col[2], threads_gather[2];  // CTA sizes of the three launches
+  int max_log2n;         // log2 of the largest grid size in the batch
   // batched GMRES
   int m;                 // restart length the workspace was sized for (0: none yet)
   int64_t* voff;         // host [count]: offset of problem b's basis in V
@@ -183,8 +184,9 @@ struct Batch {
 
 ibdl_status batch_prepare_2d(Batch* B);
 ibdl_status autotune_2d(Geometry* g, int pi, bool fixed_threads, cudaStream_t s, const double* Q, double* Y);
-// launch shape from FFT volumes per CTA: rows per band from row_target, kx columns from col_target
-void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target);
+// launch shape from FFT volumes per CTA: rows per band from row_target, kx columns from col_target;
+// floor: the row kernels' least thread count
+void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target, int floor);
 size_t batch_state_bytes();  // sizeof the per-problem GMRES state (stop, status, k are its first ints)
 ibdl_status batch_apply_2d(Batch* B, int precision, int mode, const double* in_base, double* out_base,
                            cudaStream_t s);
