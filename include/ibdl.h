@@ -88,16 +88,22 @@ enum { IBDL_SYMBOL_SPECTRAL = 0, /* −Δ ↦ |k|², ∂ ↦ ik (0 at the Nyquis
 
 /* arithmetic of the grid work inside one operator application */
 enum { IBDL_FP64 = 0, IBDL_FP32 = 1,
-       IBDL_MIXED = 2 /* solve only: FP32 applies, FP64 Arnoldi and FP64 refinement residual */ };
+       IBDL_MIXED = 2,  /* solve only: FP32 applies, FP64 Arnoldi, refinement residual as chosen by
+                           ibdl_solve_opts.residual                                           */
+       IBDL_FP32X2 = 3  /* float-float: every value of the FFT and Fourier stage an unevaluated
+                           sum of two FP32 numbers (about 48 significand bits, an application
+                           within about 1e-13 of FP64), the point work in FP64; 2-D operator
+                           applications (A and Aᵀ, grids to 4096²) and the refinement residual */ };
 
 typedef struct ibdl_geometry ibdl_geometry; /* opaque, library-owned */
 
 typedef struct {
   int dim;              /* 2 or 3                                                          */
   int n;                /* grid nodes per axis: a power of two, 16..8192 (2-D), 16..256 (3-D);
-                           the shared-memory FFT runs 2-D scalar problems to 4096 (FP64) and
-                           8192 (FP32), Stokes to 2048 (FP64) and 4096 (FP32); a call at a
-                           larger size returns IBDL_ERR_UNSUPPORTED                         */
+                           the shared-memory FFT runs 2-D scalar problems to 8192 in every
+                           precision, Stokes to 4096 (FP64, float-float) and 8192 (FP32), the
+                           divergence-dipole Stokes operator to 2048 (FP64) and 4096 (FP32); a
+                           call at a larger size returns IBDL_ERR_UNSUPPORTED                 */
   double box;           /* side length of the periodic box, > 0                             */
   double origin[3];     /* lower corner of the box (unused entries ignored)                 */
   int64_t n_points;     /* M ≥ 1                                                           */
@@ -143,6 +149,10 @@ typedef struct {
                            (a sweep whose inner cycle stops at the restart length is followed
                            by an FP64 residual restart and does not count)                    */
   int io_on_host;       /* nonzero: U_b and Q are host pointers (copied inside the call)     */
+  int residual;         /* IBDL_MIXED: arithmetic of the refinement residual's application,
+                           IBDL_FP64 (0) or IBDL_FP32X2 (float-float, for 2-D grids to 4096²;
+                           other geometries use FP64); the residual's subtraction and norm are
+                           FP64 either way                                                    */
 } ibdl_solve_opts;
 
 typedef struct {
@@ -150,11 +160,13 @@ typedef struct {
   int fp64_applies;     /* operator applications with FP64 grid arithmetic                   */
   int fp32_applies;     /* operator applications with FP32 grid arithmetic                   */
   int sweeps;           /* refinement sweeps (IBDL_MIXED), restart cycles otherwise          */
-  double rel_residual;  /* final ‖U_b − A₆₄Q‖₂/‖U_b‖₂ with an FP64 application (plain: the    */
-                        /* GMRES estimate of the last cycle)                                 */
+  double rel_residual;  /* final ‖U_b − AQ‖₂/‖U_b‖₂ with an FP64 (or, IBDL_MIXED with residual */
+                        /* IBDL_FP32X2, float-float) application (plain: the GMRES estimate  */
+                        /* of the last cycle)                                                */
   double seconds;       /* wall time of the call                                             */
   int64_t kernel_launches; /* CUDA kernels this call launched (including ones that found the  */
                         /* solve already converged and returned at once)                     */
+  int fp32x2_applies;   /* operator applications with float-float grid arithmetic            */
 } ibdl_solve_info;
 
 /* Stage timing (off by default). When enabled, every operator application records CUDA events
@@ -181,7 +193,8 @@ ibdl_status ibdl_destroy_geometry(ibdl_geometry* geom);
 
 /* Y = A Q = S*u + ½Q with u = −L⁻¹S̃Q (scalar, Sec. 5.3.2 Eq. "ibdl schur again") or the
  * Stokes velocity of Sec. 6.3.3. Q and Y are device FP64 arrays [c][M] (they may not alias);
- * `precision` (IBDL_FP64 or IBDL_FP32) selects the grid arithmetic. Asynchronous on `stream`. */
+ * `precision` (IBDL_FP64, IBDL_FP32, or IBDL_FP32X2 for 2-D geometries) selects the grid
+ * arithmetic. Asynchronous on `stream`. */
 ibdl_status ibdl_apply(ibdl_geometry* geom, int precision, const double* Q, double* Y, void* stream);
 
 /* Z = A* W, the adjoint of A with respect to the Δs-weighted boundary inner product
@@ -221,7 +234,7 @@ ibdl_status ibdl_evaluate_field_forced(ibdl_geometry* geom, const double* Q, con
  * Schur complement up to sign, Sec. 2.2.3), with S the Δs-weighted spread and S* the
  * interpolation. It carries Neumann data into the right-hand side of the Neumann equation
  * (Sec. 5.2, Eq. "Neumann saddle point", g̃ = 0): rhs = −Z(V_b). Scalar PDE, 2-D; V and Z are
- * device FP64 [M] that may not alias; asynchronous. */
+ * device FP64 [M] that may not alias; `precision` IBDL_FP64 or IBDL_FP32; asynchronous. */
 ibdl_status ibdl_single_layer(ibdl_geometry* geom, int precision, const double* V, double* Z, void* stream);
 
 /* Differentiation. The paper states no derivative; these follow from the operators of
@@ -238,7 +251,7 @@ ibdl_status ibdl_single_layer(ibdl_geometry* geom, int precision, const double* 
  * ibdl_apply_transpose: Z = Aᵀ G (Euclidean transpose; [c][M] FP64 device arrays that may not
  * alias). Scalar: Aᵀ = W A* W⁻¹ (W = diag Δs, A* as in ibdl_adjoint) = ½G + (Δs/h^d)(S̃)*(−L⁻¹)ψ,
  * ψ = Σ_j G_j Φ(x − X_j). Stokes: ½G + the spread transpose of Kᵀψ, ψ_l = Σ_j G_{l,j} Φ(x − X_j),
- * K̂ᵀ the conjugate symbol. Asynchronous.
+ * K̂ᵀ the conjugate symbol. `precision` as ibdl_apply. Asynchronous.
  *
  * ibdl_solve_transpose: solve Aᵀ λ = G with the GMRES of ibdl_solve (same options, precision
  * modes, graphs and convergence rule, on ‖G − Aᵀλ‖ ≤ rtol‖G‖). G and lambda are [c][M] FP64,
@@ -309,15 +322,16 @@ ibdl_status ibdl_near_boundary(ibdl_geometry* geom, const double* Ub, const doub
 ibdl_status ibdl_evaluate_field(ibdl_geometry* geom, const double* Q, double* u_grid, void* stream);
 
 /* Default solve options: rtol 1e-8, restart 50, maxit 200, IBDL_FP64, inner_rtol 1e-4,
- * max_refine 6, device I/O. */
+ * max_refine 6, device I/O, float-float refinement residual. */
 void ibdl_default_solve_opts(ibdl_solve_opts* opts);
 
 /* Autotuner (2-D; 3-D shapes follow a fixed volume rule): time candidate launch shapes of the
- * operator application on this geometry (rows per row band 2–16, kx columns per column group
- * 1–8, 256 or 512 threads) with CUDA events and keep the fastest, for FP64 (precision_mask bit
- * 0) and/or FP32 (bit 1). The choice is cached in the process per grid size, field counts, PDE,
- * dipole form and precision; geometries and batches created later with the same key start from
- * it. Allocates and frees a small scratch vector. Synchronises `stream`. */
+ * operator application on this geometry (rows per row band 2–64 with a least thread count of the
+ * row kernels of 0, 256 or 512, then kx columns per column group 1–32, within 512 threads and the
+ * shared memory of a CTA) with CUDA events and keep the fastest, for FP64 (precision_mask bit
+ * 0), FP32 (bit 1) and/or float-float (bit 2). The choice is cached in the process per grid size,
+ * field counts, PDE, dipole form and precision; geometries created later with the same key start
+ * from it. Allocates and frees a small scratch vector. Synchronises `stream`. */
 ibdl_status ibdl_autotune(ibdl_geometry* geom, int precision_mask, void* stream);
 
 /* Geometry facts: number of density components c and points M. */
@@ -344,13 +358,14 @@ ibdl_status ibdl_batch_sizes(const ibdl_batch* batch, int* count, int64_t* offse
 
 /* Autotune a batch: time the whole batched application for each pair of candidate FFT volumes
  * per CTA, one for the row kernels and one for the column kernel (512 to 8192 complex elements
- * each; every problem's rows per band and columns per group follow from them), keep the
- * fastest pair per precision, and rebuild the batched launch tables. Allocates and frees a
- * scratch vector. Synchronises `stream`. */
+ * each; every problem's rows per band and columns per group follow from them) and each least
+ * thread count of the row kernels (0 or 256), keep the fastest per precision (precision_mask
+ * bits as ibdl_autotune), and rebuild the batched launch tables. Allocates and frees a scratch
+ * vector. Synchronises `stream`. */
 ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* stream);
 
-/* Y = A Q for every problem of the batch (concatenated device FP64 arrays; FP64 or FP32 grid
- * arithmetic). Asynchronous. */
+/* Y = A Q for every problem of the batch (concatenated device FP64 arrays; FP64, FP32 or
+ * float-float grid arithmetic). Asynchronous. */
 ibdl_status ibdl_batch_apply(ibdl_batch* batch, int precision, const double* Q, double* Y, void* stream);
 
 /* Solve every problem (options as ibdl_solve; maxit bounds the longest problem's iterations).

@@ -83,7 +83,8 @@ ibdl_status ibdl_destroy_geometry(ibdl_geometry* geom) {
 ibdl_status ibdl_apply(ibdl_geometry* geom, int precision, const double* Q, double* Y, void* stream) {
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
-  if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
+  if (precision != IBDL_FP64 && precision != IBDL_FP32 && precision != IBDL_FP32X2)
+    return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64, IBDL_FP32 or IBDL_FP32X2");
   Geometry* g = geom->g;
   IBDL_TRY(check_device_ptr(Q, "Q"));
   IBDL_TRY(check_device_ptr(Y, "Y"));
@@ -115,6 +116,7 @@ void ibdl_default_solve_opts(ibdl_solve_opts* o) {
   o->inner_rtol = 1e-4;
   o->max_refine = 6;
   o->io_on_host = 0;
+  o->residual = IBDL_FP32X2;
 }
 
 }  // extern "C"
@@ -140,6 +142,8 @@ static ibdl_status solve_entry(ibdl_geometry* geom, const double* b, double* x, 
     return fail(IBDL_ERR_INVALID_ARG, "unknown precision");
   if (o.precision == IBDL_MIXED && (!(o.inner_rtol > 0) || !(o.inner_rtol < 1) || o.max_refine < 1))
     return fail(IBDL_ERR_INVALID_ARG, "mixed precision needs inner_rtol in (0, 1) and max_refine >= 1");
+  if (o.residual != IBDL_FP64 && o.residual != IBDL_FP32X2)
+    return fail(IBDL_ERR_INVALID_ARG, "residual must be IBDL_FP64 or IBDL_FP32X2");
   if (!b || !x) return fail(IBDL_ERR_INVALID_ARG, std::string(bname) + " and " + xname + " are required");
   if (op == OPK_AT && geom->g->naug)
     return fail(IBDL_ERR_UNSUPPORTED, "ibdl_solve_transpose: not for the completed method (eta > 0)");
@@ -222,7 +226,8 @@ ibdl_status ibdl_apply_transpose(ibdl_geometry* geom, int precision, const doubl
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
   if (geom->g->naug) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_apply_transpose: not for the completed method (eta > 0)");
-  if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
+  if (precision != IBDL_FP64 && precision != IBDL_FP32 && precision != IBDL_FP32X2)
+    return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64, IBDL_FP32 or IBDL_FP32X2");
   Geometry* g = geom->g;
   if (g->pde == IBDL_PDE_STOKES && g->dipole != IBDL_DIPOLE_ANALYTIC)
     return fail(IBDL_ERR_UNSUPPORTED, "ibdl_apply_transpose: Stokes with the analytic dipole only");
@@ -325,7 +330,7 @@ ibdl_status ibdl_geometry_sizes(const ibdl_geometry* geom, int* ncomp, int64_t* 
 ibdl_status ibdl_autotune(ibdl_geometry* geom, int precision_mask, void* stream) {
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
-  if (precision_mask < 1 || precision_mask > 3) return fail(IBDL_ERR_INVALID_ARG, "precision_mask must be 1, 2 or 3");
+  if (precision_mask < 1 || precision_mask > 7) return fail(IBDL_ERR_INVALID_ARG, "precision_mask must be in 1 … 7");
   Geometry* g = geom->g;
   if (g->dim != 2) return IBDL_OK;  // 3-D shapes come from the volume rule only
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -334,8 +339,8 @@ ibdl_status ibdl_autotune(ibdl_geometry* geom, int precision_mask, void* stream)
   IBDL_CUDA(cudaMalloc((void**)&buf, sizeof(double) * 2 * nd));
   ibdl_status st = IBDL_OK;
   if (cudaMemsetAsync(buf, 0, sizeof(double) * nd, s) != cudaSuccess) st = fail(IBDL_ERR_CUDA, "memset");
-  for (int pi = 0; pi < 2 && st == IBDL_OK; ++pi)
-    if (precision_mask & (pi ? 2 : 1)) st = autotune_2d(g, pi, false, s, buf, buf + nd);
+  for (int pi = 0; pi < 3 && st == IBDL_OK; ++pi)
+    if (precision_mask & (1 << pi)) st = autotune_2d(g, pi, false, s, buf, buf + nd);
   cudaStreamSynchronize(s);
   cudaFree(buf);
   return st;

@@ -23,21 +23,51 @@ IBDL_DECLARE_2D(10)
 IBDL_DECLARE_2D(11)
 IBDL_DECLARE_2D(12)
 IBDL_DECLARE_2D(13)
+#define IBDL_DECLARE_2D_FF(L) IBDL_DECLARE_2D_FWD(ff, L) IBDL_DECLARE_2D_TRANS(ff, L)
+IBDL_DECLARE_2D_FF(4)
+IBDL_DECLARE_2D_FF(5)
+IBDL_DECLARE_2D_FF(6)
+IBDL_DECLARE_2D_FF(7)
+IBDL_DECLARE_2D_FF(8)
+IBDL_DECLARE_2D_FF(9)
+IBDL_DECLARE_2D_FF(10)
+IBDL_DECLARE_2D_FF(11)
+IBDL_DECLARE_2D_FF(12)
 
-extern template ibdl_status batch_launch_2d<float, OP_SCALAR_AN>(Batch*, int, const double*, double*, cudaStream_t);
-extern template ibdl_status batch_launch_2d<float, OP_SCALAR_SD>(Batch*, int, const double*, double*, cudaStream_t);
-extern template ibdl_status batch_launch_2d<float, OP_STOKES_AN>(Batch*, int, const double*, double*, cudaStream_t);
-extern template ibdl_status batch_launch_2d<float, OP_STOKES_SD>(Batch*, int, const double*, double*, cudaStream_t);
-extern template ibdl_status batch_launch_2d<double, OP_SCALAR_AN>(Batch*, int, const double*, double*, cudaStream_t);
-extern template ibdl_status batch_launch_2d<double, OP_SCALAR_SD>(Batch*, int, const double*, double*, cudaStream_t);
-extern template ibdl_status batch_launch_2d<double, OP_STOKES_AN>(Batch*, int, const double*, double*, cudaStream_t);
-extern template ibdl_status batch_launch_2d<double, OP_STOKES_SD>(Batch*, int, const double*, double*, cudaStream_t);
+// precision slot and tables of a grid arithmetic type
+template <typename T>
+struct Slot2;
+template <>
+struct Slot2<double> {
+  static constexpr int pi = 0;
+  static const PointTable<double>& points(const Geometry* g) { return g->t64; }
+  static const void* tw(const Geometry* g) { return g->tw64; }
+  static const void* lap(const Geometry* g) { return g->lap64; }
+  static const void* der(const Geometry* g) { return g->der64; }
+};
+template <>
+struct Slot2<float> {
+  static constexpr int pi = 1;
+  static const PointTable<float>& points(const Geometry* g) { return g->t32; }
+  static const void* tw(const Geometry* g) { return g->tw32; }
+  static const void* lap(const Geometry* g) { return g->lap32; }
+  static const void* der(const Geometry* g) { return g->der32; }
+};
+template <>
+struct Slot2<ff> {
+  static constexpr int pi = 2;
+  static const PointTable<double>& points(const Geometry* g) { return g->t64; }
+  static const void* tw(const Geometry* g) { return g->twff; }
+  static const void* lap(const Geometry* g) { return g->lapff; }
+  static const void* der(const Geometry* g) { return g->derff; }
+};
 
 static int log2i(int n) { return __builtin_ctz(n); }
 
 template <typename T>
 static RowParams<T> row_params(Geometry* g, const double* in, double* out, const int* stop, double* grid) {
-  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  using PT = typename Prec2<T>::PT;
+  const int pi = Slot2<T>::pi;
   RowParams<T> rp;
   rp.n = g->n;
   rp.log2n = log2i(g->n);
@@ -46,7 +76,7 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.cell_start = g->cell_start;
   rp.base = g->base;
   rp.perm = g->perm;
-  const PointTable<T>& tb = *reinterpret_cast<const PointTable<T>*>(pi ? (const void*)&g->t32 : (const void*)&g->t64);
+  const PointTable<PT>& tb = Slot2<T>::points(g);
   rp.phi = tb.phi;
   rp.dphi = tb.dphi;
   rp.wscale = tb.wscale;
@@ -54,7 +84,7 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.in = in;
   rp.out = out;
   rp.spec = reinterpret_cast<cplx<T>*>(g->spec);
-  rp.tw = reinterpret_cast<const cplx<T>*>(pi ? (const void*)g->tw32 : (const void*)g->tw64);
+  rp.tw = static_cast<const cplx<T>*>(Slot2<T>::tw(g));
   rp.stop = stop;
   rp.grid = grid;
   rp.idx = nullptr;
@@ -66,13 +96,13 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.aug = g->naug > 0;
   rp.eta = g->eta;
   rp.hd = g->h * g->h;
-  rp.eta_src = T(g->naug ? (g->pde == IBDL_PDE_STOKES ? g->eta / g->mu : g->eta) : 0.0);
+  rp.eta_src = PT(g->naug ? (g->pde == IBDL_PDE_STOKES ? g->eta / g->mu : g->eta) : 0.0);
   return rp;
 }
 
 template <typename T>
 static ColParams<T> col_params(Geometry* g, const int* stop) {
-  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  const int pi = Slot2<T>::pi;
   ColParams<T> cp;
   cp.n = g->n;
   cp.log2n = log2i(g->n);
@@ -81,10 +111,10 @@ static ColParams<T> col_params(Geometry* g, const int* stop) {
   cp.lam = T(g->lambda);
   cp.mu = T(g->mu);
   cp.scale = T(1.0 / ((double)g->n * (double)g->n));
-  cp.lap1 = reinterpret_cast<const T*>(pi ? (const void*)g->lap32 : (const void*)g->lap64);
-  cp.der1 = reinterpret_cast<const T*>(pi ? (const void*)g->der32 : (const void*)g->der64);
+  cp.lap1 = static_cast<const T*>(Slot2<T>::lap(g));
+  cp.der1 = static_cast<const T*>(Slot2<T>::der(g));
   cp.spec = reinterpret_cast<cplx<T>*>(g->spec);
-  cp.tw = reinterpret_cast<const cplx<T>*>(pi ? (const void*)g->tw32 : (const void*)g->tw64);
+  cp.tw = static_cast<const cplx<T>*>(Slot2<T>::tw(g));
   cp.stop = stop;
   return cp;
 }
@@ -119,6 +149,21 @@ static ibdl_status launch_shape(const Geometry* g, int R, int C, int floor, Laun
   return IBDL_OK;
 }
 
+// the per-size launch for n = 2^L; float-float exists to 4096² and not for the single layer
+template <typename T, int OP, int L>
+static ibdl_status launch_for_size(int lg, Geometry* g, const RowParams<T>& rp, const ColParams<T>& cp,
+                                   const Launch2D& lc, cudaStream_t s) {
+  constexpr bool is_ff = std::is_same<T, ff>::value;
+  if constexpr (L > kMaxL2d) {
+    return fail(IBDL_ERR_UNSUPPORTED, "2-D grid size outside 16 … 8192");
+  } else if constexpr (is_ff && (L > kMaxLff || OP == OP_SL)) {
+    return fail(IBDL_ERR_UNSUPPORTED, "float-float applications: grids to 4096², not the single layer");
+  } else {
+    if (lg == L) return launch_apply_2d<T, OP, L>(g, rp, cp, lc, s);
+    return launch_for_size<T, OP, L + 1>(lg, g, rp, cp, lc, s);
+  }
+}
+
 // run_op mode bits: RUN_LAPLACE solves the plain Laplace problem (λ → 0) without the completed
 // method's terms; RUN_NO_AUG only drops those terms
 enum { RUN_LAPLACE = 1, RUN_NO_AUG = 2 };
@@ -127,7 +172,8 @@ template <typename T, int OP>
 static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream_t s, const int* stop,
                           double* grid, const int* idx = nullptr, int vstride = 0, int trans = 0,
                           const double* grid_in = nullptr, int mode = 0) {
-  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  const int pi = Slot2<T>::pi;
+  if (pi == 2 && !g->twff) return fail(IBDL_ERR_UNSUPPORTED, "this geometry has no float-float tables");
   Launch2D lc;
   IBDL_TRY((launch_shape<T, OP>(g, g->rows_per_cta[pi], g->cols_per_cta[pi], g->threads[pi], &lc)));
   lc.pdl = !g->timing;
@@ -140,27 +186,15 @@ static ibdl_status run_op(Geometry* g, const double* in, double* out, cudaStream
   if (OP == OP_SL) rp.jump = 0.0;
   if (OP != OP_SCALAR_AN && OP != OP_STOKES_AN) {  // the completed method exists for these two only
     rp.aug = 0;
-    rp.eta_src = T(0);
+    rp.eta_src = 0;
   }
   ColParams<T> cp = col_params<T>(g, stop);
   if (mode & RUN_LAPLACE) cp.lam = T(0);  // the plain Laplace problem (indicator)
   if (mode & (RUN_LAPLACE | RUN_NO_AUG)) {  // no completed-method terms
     rp.aug = 0;
-    rp.eta_src = T(0);
+    rp.eta_src = 0;
   }
-  switch (log2i(g->n)) {
-    case 4: return launch_apply_2d<T, OP, 4>(g, rp, cp, lc, s);
-    case 5: return launch_apply_2d<T, OP, 5>(g, rp, cp, lc, s);
-    case 6: return launch_apply_2d<T, OP, 6>(g, rp, cp, lc, s);
-    case 7: return launch_apply_2d<T, OP, 7>(g, rp, cp, lc, s);
-    case 8: return launch_apply_2d<T, OP, 8>(g, rp, cp, lc, s);
-    case 9: return launch_apply_2d<T, OP, 9>(g, rp, cp, lc, s);
-    case 10: return launch_apply_2d<T, OP, 10>(g, rp, cp, lc, s);
-    case 11: return launch_apply_2d<T, OP, 11>(g, rp, cp, lc, s);
-    case 12: return launch_apply_2d<T, OP, 12>(g, rp, cp, lc, s);
-    case 13: return launch_apply_2d<T, OP, 13>(g, rp, cp, lc, s);
-    default: return fail(IBDL_ERR_UNSUPPORTED, "2-D grid size outside 16 … 8192");
-  }
+  return launch_for_size<T, OP, kMinL2d>(log2i(g->n), g, rp, cp, lc, s);
 }
 
 template <typename T>
@@ -185,12 +219,14 @@ static ibdl_status apply_t(Geometry* g, const double* Q, double* Y, cudaStream_t
 // Y = A Q with Q = V + (*idx)·nd and Y = V + (*idx + 1)·nd read on the device (Krylov basis)
 ibdl_status apply_2d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
                              const int* stop, int op) {
+  if (precision == IBDL_FP32X2) return apply_t<ff>(g, V, V, s, stop, nullptr, idx, nd, op);
   return precision == IBDL_FP32 ? apply_t<float>(g, V, V, s, stop, nullptr, idx, nd, op)
                                 : apply_t<double>(g, V, V, s, stop, nullptr, idx, nd, op);
 }
 
 ibdl_status apply_2d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s, const int* stop,
                      int op) {
+  if (precision == IBDL_FP32X2) return apply_t<ff>(g, Q, Y, s, stop, nullptr, nullptr, 0, op);
   return precision == IBDL_FP32 ? apply_t<float>(g, Q, Y, s, stop, nullptr, nullptr, 0, op)
                                 : apply_t<double>(g, Q, Y, s, stop, nullptr, nullptr, 0, op);
 }
@@ -205,6 +241,7 @@ ibdl_status field_pair_2d(Geometry* g, const double* Q, const double* lam, doubl
 // Z = S*(−L⁻¹)(S V) (scalar PDE)
 ibdl_status single_layer_2d(Geometry* g, int precision, const double* V, double* Z, cudaStream_t s) {
   if (g->pde != IBDL_PDE_SCALAR) return fail(IBDL_ERR_UNSUPPORTED, "single layer: scalar PDE only");
+  if (precision == IBDL_FP32X2) return fail(IBDL_ERR_UNSUPPORTED, "single layer: FP64 or FP32");
   return precision == IBDL_FP32 ? run_op<float, OP_SL>(g, V, Z, s, nullptr, nullptr)
                                 : run_op<double, OP_SL>(g, V, Z, s, nullptr, nullptr);
 }
@@ -327,6 +364,36 @@ ibdl_status adjoint_2d(Geometry* g, int precision, const double* W, double* Z, c
 // batched launches: one grid per stage covers every problem of a batch (kernels and launches in
 // apply2d_batch_*.cu); here the per-problem parameter blocks and (problem, unit) tables
 // ------------------------------------------------------------------------------------------
+// a batched stage for the problems of size 2^L (those that exist for this type)
+template <typename T, int OP, int L>
+static ibdl_status batch_stage_for_size(int lg, Batch* B, int stage, int mode, const double* in_base, double* out_base,
+                                        cudaStream_t s, bool pdl) {
+  constexpr bool is_ff = std::is_same<T, ff>::value;
+  if constexpr (L > (is_ff ? kMaxLff : kMaxL2d)) {
+    return fail(IBDL_ERR_UNSUPPORTED, "batched float-float applications: grids to 4096²");
+  } else {
+    if (lg == L) return batch_stage_2d<T, OP, L>(B, stage, mode, in_base, out_base, s, pdl);
+    return batch_stage_for_size<T, OP, L + 1>(lg, B, stage, mode, in_base, out_base, s, pdl);
+  }
+}
+
+// One batched application: for each stage, one launch per grid size present (a size's kernels
+// wait, by programmatic launch, for the launch before them; only the first launch of the
+// application is an ordinary stream-ordered launch).
+template <typename T, int OP>
+static ibdl_status batch_launch_2d(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
+  const int pi = Slot2<T>::pi;
+  bool first = true;
+  for (int stage = 0; stage < 3; ++stage)
+    for (int L = kMinL2d; L <= kMaxL2d; ++L) {
+      if (B->lv[pi][L].row_count == 0) continue;
+      IBDL_TRY((batch_stage_for_size<T, OP, kMinL2d>(L, B, stage, mode, in_base, out_base, s, !first)));
+      first = false;
+    }
+  IBDL_CUDA(cudaGetLastError());
+  return IBDL_OK;
+}
+
 template <typename T>
 static ibdl_status batch_apply_t(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
   if (B->pde == IBDL_PDE_STOKES)
@@ -337,6 +404,10 @@ static ibdl_status batch_apply_t(Batch* B, int mode, const double* in_base, doub
 }
 
 ibdl_status batch_apply_2d(Batch* B, int precision, int mode, const double* in_base, double* out_base, cudaStream_t s) {
+  if (precision == IBDL_FP32X2) {
+    if (B->max_log2n > kMaxLff) return fail(IBDL_ERR_UNSUPPORTED, "batched float-float applications: grids to 4096²");
+    return batch_apply_t<ff>(B, mode, in_base, out_base, s);
+  }
   return precision == IBDL_FP32 ? batch_apply_t<float>(B, mode, in_base, out_base, s)
                                 : batch_apply_t<double>(B, mode, in_base, out_base, s);
 }
@@ -345,12 +416,13 @@ template <typename T, int OP>
 static ibdl_status batch_shape(Batch* B, Geometry* g, int pi) {
   Launch2D lc;
   IBDL_TRY((launch_shape<T, OP>(g, g->rows_per_cta[pi], g->cols_per_cta[pi], g->threads[pi], &lc)));
-  B->smem_row[pi] = std::max(B->smem_row[pi], lc.smem_row);
-  B->smem_col[pi] = std::max(B->smem_col[pi], lc.smem_col);
-  B->smem_gather[pi] = std::max(B->smem_gather[pi], lc.smem_gather);
-  B->threads_row[pi] = std::max(B->threads_row[pi], lc.threads_row);
-  B->threads_col[pi] = std::max(B->threads_col[pi], lc.threads_col);
-  B->threads_gather[pi] = std::max(B->threads_gather[pi], lc.threads_gather);
+  BatchSize& z = B->lv[pi][log2i(g->n)];
+  z.smem_row = std::max(z.smem_row, lc.smem_row);
+  z.smem_col = std::max(z.smem_col, lc.smem_col);
+  z.smem_gather = std::max(z.smem_gather, lc.smem_gather);
+  z.threads_row = std::max(z.threads_row, lc.threads_row);
+  z.threads_col = std::max(z.threads_col, lc.threads_col);
+  z.threads_gather = std::max(z.threads_gather, lc.threads_gather);
   return IBDL_OK;
 }
 
@@ -363,12 +435,16 @@ static ibdl_status batch_shape_any(Batch* B, Geometry* g, int pi) {
 
 template <typename T>
 static ibdl_status batch_prepare_t(Batch* B, const int* kptr /* device &st[b].k, stride in bytes */, size_t kstride) {
-  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  const int pi = Slot2<T>::pi;
   std::vector<RowParams<T>> user(B->count), kry(B->count);
   std::vector<ColParams<T>> col(B->count);
   std::vector<int2> ru, cu;
-  B->smem_row[pi] = B->smem_col[pi] = B->smem_gather[pi] = 0;
-  B->threads_row[pi] = B->threads_col[pi] = B->threads_gather[pi] = 0;
+  for (int L = 0; L < 14; ++L) B->lv[pi][L] = BatchSize{};
+  // float-float batches exist to 4096²: larger ones keep empty tables (their residuals use FP64)
+  if (std::is_same<T, ff>::value && B->max_log2n > kMaxLff) {
+    B->nrow_units[pi] = B->ncol_units[pi] = 0;
+    return IBDL_OK;
+  }
   for (int b = 0; b < B->count; ++b) {
     Geometry* g = B->geoms[b];
     if (batch_shape_any<T>(B, g, pi) != IBDL_OK)
@@ -384,8 +460,20 @@ static ibdl_status batch_prepare_t(Batch* B, const int* kptr /* device &st[b].k,
       kry[b].vstride = (int)(g->ncomp * g->M);
       kry[b].io_off = B->voff[b];
     }
-    for (int u = 0; u < g->n / g->rows_per_cta[pi]; ++u) ru.push_back(make_int2(b, u));
-    for (int u = 0; u < (g->n / 2) / g->cols_per_cta[pi]; ++u) cu.push_back(make_int2(b, u));
+  }
+  // unit tables grouped by grid size (one launch per size and stage)
+  for (int L = kMinL2d; L <= kMaxL2d; ++L) {
+    BatchSize& z = B->lv[pi][L];
+    z.row_start = (int)ru.size();
+    z.col_start = (int)cu.size();
+    for (int b = 0; b < B->count; ++b) {
+      Geometry* g = B->geoms[b];
+      if (log2i(g->n) != L) continue;
+      for (int u = 0; u < g->n / g->rows_per_cta[pi]; ++u) ru.push_back(make_int2(b, u));
+      for (int u = 0; u < (g->n / 2) / g->cols_per_cta[pi]; ++u) cu.push_back(make_int2(b, u));
+    }
+    z.row_count = (int)ru.size() - z.row_start;
+    z.col_count = (int)cu.size() - z.col_start;
   }
   auto upload = [&](void** dst, const void* src, size_t bytes) -> ibdl_status {
     if (*dst) cudaFree(*dst);
@@ -415,6 +503,7 @@ ibdl_status batch_prepare_2d(Batch* B) {
   }
   IBDL_TRY(batch_prepare_t<double>(B, kptr, kstride));
   IBDL_TRY(batch_prepare_t<float>(B, kptr, kstride));
+  IBDL_TRY(batch_prepare_t<ff>(B, kptr, kstride));
   return IBDL_OK;
 }
 
@@ -434,12 +523,12 @@ static int pow2_in(int v, int lo, int hi) {
 
 static bool row_fits(const Geometry* g, int pi, int R) {
   const int L = log2i(g->n), nf = nf_row_max(g);
-  const size_t bytes = pi ? smem_rows_2d<float>(nf, R, L) : smem_rows_2d<double>(nf, R, L);
+  const size_t bytes = pi == 1 ? smem_rows_2d<float>(nf, R, L) : smem_rows_2d<double>(nf, R, L);
   return R >= 2 && R <= g->n / 2 && bytes <= kSmemLimit2d && row_threads(nf, R, L, 0) <= kMaxThreads2d;
 }
 static bool col_fits(const Geometry* g, int pi, int C) {
   const int L = log2i(g->n), nf = nf_row_max(g);
-  const size_t bytes = pi ? smem_cols_2d<float>(nf, C, L) : smem_cols_2d<double>(nf, C, L);
+  const size_t bytes = pi == 1 ? smem_cols_2d<float>(nf, C, L) : smem_cols_2d<double>(nf, C, L);
   return C >= 1 && C <= g->n / 2 && bytes <= kSmemLimit2d && col_threads(nf, C, L) <= kMaxThreads2d;
 }
 
@@ -498,10 +587,10 @@ ibdl_status autotune_2d(Geometry* g, int pi, bool /*fixed_threads*/, cudaStream_
     g->cols_per_cta[pi] = C;
     g->threads[pi] = floor;
     float ms[5];
-    IBDL_TRY(apply_2d(g, pi ? IBDL_FP32 : IBDL_FP64, Q, Y, s, nullptr));
+    IBDL_TRY(apply_2d(g, slot_precision(pi), Q, Y, s, nullptr));
     for (int k = 0; k < 5; ++k) {
       cudaEventRecord(e0, s);
-      IBDL_TRY(apply_2d(g, pi ? IBDL_FP32 : IBDL_FP64, Q, Y, s, nullptr));
+      IBDL_TRY(apply_2d(g, slot_precision(pi), Q, Y, s, nullptr));
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) return fail(IBDL_ERR_CUDA, "autotune: event synchronize");
       cudaEventElapsedTime(&ms[k], e0, e1);
@@ -566,7 +655,7 @@ void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target, in
 ibdl_status plan_2d(Geometry* g) {
   const int n = g->n, L = log2i(n), qt = threads_per_seq_2d(L);
   const int min_ctas = 2 * 152;
-  for (int pi = 0; pi < 2; ++pi) {
+  for (int pi = 0; pi < 3; ++pi) {
     int R = 2 * pow2_in(256 / qt, 1, n / 4 > 1 ? n / 4 : 1);
     while (R > 2 && (n / R < std::min(min_ctas, n / 2) || !row_fits(g, pi, R))) R /= 2;
     if (!row_fits(g, pi, R)) R = 0;
@@ -594,7 +683,7 @@ ibdl_status plan_2d(Geometry* g) {
   }
   if (const char* e = getenv("IBDL_THREADS")) {
     const int v = atoi(e);
-    if (v >= 0 && v <= kMaxThreads2d && v % 32 == 0) g->threads[0] = g->threads[1] = v;
+    if (v >= 0 && v <= kMaxThreads2d && v % 32 == 0) g->threads[0] = g->threads[1] = g->threads[2] = v;
   }
   if (g->rows_per_cta[0] == 0 && g->rows_per_cta[1] == 0)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT");

@@ -30,9 +30,29 @@
 #include <type_traits>
 #include <utility>
 
+#include "ff.cuh"
 #include "fft8.cuh"
 
 namespace ibdl {
+
+// Grid arithmetic type T and its point type PT: the point tables, the spread's shared-memory
+// accumulation and the gather's partial sums use PT (FP32 for FP32, FP64 for FP64 and for
+// float-float, whose point work is O(M) and whose accuracy the FP64 tables carry).
+template <typename T>
+struct Prec2 {
+  using PT = T;
+  static __device__ __forceinline__ cplx<T> acc_load(const cplx<T>* b, int i) { return b[i]; }
+  static __device__ __forceinline__ PT to_pt(T v) { return v; }
+};
+template <>
+struct Prec2<ff> {
+  using PT = double;
+  static __device__ __forceinline__ cplx<ff> acc_load(const cplx<ff>* b, int i) {
+    const cplx<double> d = reinterpret_cast<const cplx<double>*>(b)[i];
+    return mk(ff(d.x), ff(d.y));
+  }
+  static __device__ __forceinline__ double to_pt(ff v) { return double(v); }
+};
 
 enum { OP_SCALAR_AN = 0, OP_SCALAR_SD = 1, OP_STOKES_AN = 2, OP_STOKES_SD = 3, OP_ADJ_AN = 4,
        OP_ADJ_SD = 5, OP_STOKES_T = 6, OP_SL = 7 };
@@ -90,15 +110,16 @@ struct Cfg2 {
 
 template <typename T>
 struct RowParams {
+  using PT = typename Prec2<T>::PT;
   int n, log2n, R;
   int M;
   const int* cell_start;
   const int* base;
   const int* perm;
-  const T* phi;
-  const T* dphi;
-  const T* wscale;
-  const T* nrm;
+  const PT* phi;
+  const PT* dphi;
+  const PT* wscale;
+  const PT* nrm;
   const double* in;   // [c][M] density
   double* out;        // [c][M] result (first kernel stores ½·in, last kernel adds S*u)
   cplx<T>* spec;      // [nf][n][n/2]
@@ -118,7 +139,7 @@ struct RowParams {
   int aug;                // 1: add ū_l to the boundary rows, write the rows η Σ_i Δs_i Q_{l,i}
   double eta;             // η
   double hd;              // h^d
-  T eta_src;              // weight of the ηSQ source: η (scalar) or η/μ (Stokes, projected part)
+  PT eta_src;             // weight of the ηSQ source: η (scalar) or η/μ (Stokes, projected part)
 };
 
 template <typename T>
@@ -182,11 +203,12 @@ struct SpreadItem {
   T px, py, dpx, dpy, ws, nx, ny;
 };
 template <typename T>
-__device__ __forceinline__ SpreadItem<T> spread_item(const RowParams<T>& p, const PointRanges& pr, int t, int r0) {
+__device__ __forceinline__ SpreadItem<typename Prec2<T>::PT> spread_item(const RowParams<T>& p, const PointRanges& pr,
+                                                                         int t, int r0) {
   const int n = p.n, M = p.M;
   const int s = pr.at(t >> 4);
   const int ay = (t >> 2) & 3, ax = t & 3;
-  SpreadItem<T> it;
+  SpreadItem<typename Prec2<T>::PT> it;
   it.lr = (((p.base[M + s] + ay) & (n - 1)) - r0) & (n - 1);
   it.i = p.perm[s];
   it.col = (p.base[s] + ax) & (n - 1);
@@ -210,13 +232,14 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   constexpr int NC = Traits<OP>::C;
   using CF = Cfg2<T, L, NIN>;
   using F = F8<L, CF::V>;
+  using PT = typename Prec2<T>::PT;
   constexpr int n = F::N, V = CF::V, QT = CF::QT, NGRP = CF::NGRP;
   const int R = p.R, half = R >> 1, M = p.M;
-  // sequence (field f, row pair rp) at buf + (f·half + rp)·PN; accumulation view: field f, local
-  // row lr, column x → real part (even lr) or imaginary part (odd lr) of element
-  // (f·half + lr/2)·n + x in the padded layout
+  // sequence (field f, row pair rp) at buf + (f·half + rp)·PN; accumulation view (point type PT,
+  // the same bytes per element): field f, local row lr, column x → real part (even lr) or
+  // imaginary part (odd lr) of element (f·half + lr/2)·n + x in the padded layout
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
-  T* acc = reinterpret_cast<T*>(buf);
+  PT* acc = reinterpret_cast<PT*>(buf);
   const int r0 = unit * R;
   // FFT lanes: thread (group g, row pair rp, lane j0); threads past NGRP·half·QT only help with
   // the loops (clearing, spreading, unpacking)
@@ -224,7 +247,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   const int g = q / half, rp = q - g * half;
   const bool active = g < NGRP;
   // prologue independent of the previous kernel, then wait for it (programmatic launch)
-  for (int i = threadIdx.x; i < NIN * half * F::PN * 2; i += blockDim.x) acc[i] = T(0);
+  for (int i = threadIdx.x; i < NIN * half * F::PN * 2; i += blockDim.x) acc[i] = PT(0);
   typename CF::TW tw[V];
   if constexpr (PF) {
 #pragma unroll
@@ -233,7 +256,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   // the points whose stencil meets the band, and this thread's first work item (16 per point)
   const PointRanges pr = band_points(p.cell_start, n, r0, R);
   const int nitems = p.grid_in ? 0 : pr.cnt * 16;
-  SpreadItem<T> it0 = {};
+  SpreadItem<PT> it0 = {};
   if ((int)threadIdx.x < nitems) it0 = spread_item(p, pr, threadIdx.x, r0);
   cudaGridDependencySynchronize();
   // Let the next kernel launch and run its prologue. Triggered only after this kernel's own
@@ -281,41 +304,41 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
       const int f = t / (R * n);
       const int rem = t - f * R * n;
       const int lr = rem / n, x = rem - lr * n;
-      acc[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)] = T(p.grid_in[((size_t)f * n + r0 + lr) * n + x]);
+      acc[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)] = PT(p.grid_in[((size_t)f * n + r0 + lr) * n + x]);
     }
   }
 
   // one thread per (point, stencil node): 16 work items per point whose stencil meets the band
   for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
-    const SpreadItem<T> it = t == (int)threadIdx.x ? it0 : spread_item(p, pr, t, r0);
+    const SpreadItem<PT> it = t == (int)threadIdx.x ? it0 : spread_item(p, pr, t, r0);
     const int lr = it.lr;
     if (lr >= R) continue;
     const int i = it.i;
-    const T px = it.px, py = it.py, ws = it.ws, nx = it.nx, ny = it.ny;
+    const PT px = it.px, py = it.py, ws = it.ws, nx = it.nx, ny = it.ny;
     const int e = (lr >> 1) * n + it.col;  // field 0; field f adds f·half·n
     const int odd = lr & 1;
-    const T pp = px * py;
+    const PT pp = px * py;
     if (OP == OP_SCALAR_AN) {
-      const T q = T(pin[i]) * ws;
-      const T ddx = it.dpx * py, ddy = px * it.dpy;
+      const PT q = PT(pin[i]) * ws;
+      const PT ddx = it.dpx * py, ddy = px * it.dpy;
       // dipole source n·∇δ_h, plus ηδ_h for the completed method
       atomicAdd(acc + 2 * pidx(e) + odd, q * (nx * ddx + ny * ddy + p.eta_src * pp));
     } else if (OP == OP_SCALAR_SD) {
-      const T q = T(pin[i]) * ws * pp;
+      const PT q = PT(pin[i]) * ws * pp;
       atomicAdd(acc + 2 * pidx(e) + odd, q * nx);
       atomicAdd(acc + 2 * pidx(e + half * n) + odd, q * ny);
     } else if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
-      const T qx = T(pin[i]), qy = T(pin[M + i]);
-      const T c0 = ws * (qx * nx + qy * ny);  // Q·n
-      const T c1 = ws * (T(2) * qx * nx);     // A_xx
-      const T c2 = ws * (T(2) * qy * ny);     // A_yy
-      const T c3 = ws * (qx * ny + qy * nx);  // A_xy
+      const PT qx = PT(pin[i]), qy = PT(pin[M + i]);
+      const PT c0 = ws * (qx * nx + qy * ny);  // Q·n
+      const PT c1 = ws * (PT(2) * qx * nx);    // A_xx
+      const PT c2 = ws * (PT(2) * qy * ny);    // A_yy
+      const PT c3 = ws * (qx * ny + qy * nx);  // A_xy
       atomicAdd(acc + 2 * pidx(e) + odd, c0 * pp);
       if (OP == OP_STOKES_AN) {
-        const T ddx = it.dpx * py, ddy = px * it.dpy;
+        const PT ddx = it.dpx * py, ddy = px * it.dpy;
         // g_x = ∂_x S(A_xx) + ∂_y S(A_xy), g_y = ∂_x S(A_xy) + ∂_y S(A_yy); the completed method
         // adds (η/μ) S(Q) to the projected source
-        const T ce = p.eta_src * ws * pp;
+        const PT ce = p.eta_src * ws * pp;
         atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * ddx + c3 * ddy + ce * qx);
         atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c3 * ddx + c2 * ddy + ce * qy);
       } else {
@@ -325,11 +348,11 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
       }
     } else if (OP == OP_STOKES_T) {
       // ψ_l = Σ_j μ_{l,j} Φ(x − X_j): the transpose of S*, unweighted
-      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * pp);
-      atomicAdd(acc + 2 * pidx(e + half * n) + odd, T(pin[M + i]) * pp);
+      atomicAdd(acc + 2 * pidx(e) + odd, PT(pin[i]) * pp);
+      atomicAdd(acc + 2 * pidx(e + half * n) + odd, PT(pin[M + i]) * pp);
     } else {
       // plain spread of W (A*: weight Δs/h^d), or of λ (Aᵀ: weight 1, Δs/h^d moves to the gather)
-      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * (p.trans ? T(1) : ws) * pp);
+      atomicAdd(acc + 2 * pidx(e) + odd, PT(pin[i]) * (p.trans ? PT(1) : ws) * pp);
     }
   }
   __syncthreads();
@@ -349,7 +372,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
 #pragma unroll
       for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) x[0][v][s] = sb[ppos(j0 + v * QT + s * F::Q)];
+        for (int s = 0; s < 8; ++s) x[0][v][s] = Prec2<T>::acc_load(sb, ppos(j0 + v * QT + s * F::Q));
     }
     f8_fft<T, false, L, V, 1>(x, sb, 0, j0, tw, active);
     if (active) {
@@ -394,9 +417,10 @@ __global__ void __launch_bounds__(kMaxThreads2d) k_spread_rowfft(RowParams<T> p)
 // Laplacian symbols), dkx, dky the per-axis derivative symbols
 // ------------------------------------------------------------------------------------------
 // a/b: the hardware reciprocal estimate in FP32 (within 2 ulp, well inside the FP32 application's
-// rounding), IEEE division in FP64
+// rounding), IEEE division in FP64, a corrected quotient in float-float
 __device__ __forceinline__ float sym_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double sym_div(double a, double b) { return a / b; }
+__device__ __forceinline__ ff sym_div(ff a, ff b) { return a / b; }
 
 template <typename T, int OP>
 __device__ __forceinline__ void apply_symbol(const ColParams<T>& p, T lap, T dkx, T dky, const cplx<T>* in,
@@ -514,7 +538,7 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
   // values are read at use (registers go to the fields)
   constexpr bool PREF = PF && NIN == 1 && NOUT == 1;
   const bool packed = k0 == 0;  // uniform over the CTA: column 0 holds kx = 0 and kx = n/2
-  T lapx = 0, derx = 0, lapn = 0, dern = 0;
+  T lapx = T(0), derx = T(0), lapn = T(0), dern = T(0);
   T lapy[PREF ? V : 1][8], dery[PREF ? V : 1][8];
   if (active) {
     lapx = p.lap1[kx];
@@ -720,11 +744,12 @@ struct GatherItem {
   T px[4], dx[4];
 };
 template <typename T>
-__device__ __forceinline__ GatherItem<T> gather_item(const RowParams<T>& p, const PointRanges& pr, int t, int r0) {
+__device__ __forceinline__ GatherItem<typename Prec2<T>::PT> gather_item(const RowParams<T>& p, const PointRanges& pr,
+                                                                         int t, int r0) {
   const int n = p.n, M = p.M;
   const int s = pr.at(t >> 2);
   const int ay = t & 3;
-  GatherItem<T> it;
+  GatherItem<typename Prec2<T>::PT> it;
   it.lr = (((p.base[M + s] + ay) & (n - 1)) - r0) & (n - 1);
   it.i = p.perm[s];
   it.bx = p.base[s];
@@ -746,6 +771,7 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   constexpr int NOUT = Traits<OP>::NOUT;
   using CF = Cfg2<T, L, NOUT>;
   using F = F8<L, CF::V>;
+  using PT = typename Prec2<T>::PT;
   constexpr int n = F::N, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q, PN = F::PN;
   const int R = p.R, half = R >> 1, M = p.M;
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -761,7 +787,7 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   // loaded before the wait: the point tables are constant
   const PointRanges pr = band_points(p.cell_start, n, r0, R);
   const int nitems = GMODE == G_GRID ? 0 : pr.cnt * 4;
-  GatherItem<T> it0 = {};
+  GatherItem<PT> it0 = {};
   if (PF && (int)threadIdx.x < nitems) it0 = gather_item(p, pr, threadIdx.x, r0);
   // the stop flag and the Krylov index (the output column) are final before the wait: the GMRES
   // step that writes them is three kernels back (see the column pass)
@@ -804,31 +830,33 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
       const int lr = rem / n, x = rem - lr * n;
       // the completed method's field is u₀ + ū (ū after the density in the input vector)
       const double ub = p.aug ? p.in[(size_t)Traits<OP>::C * M + f] : 0.0;
-      p.grid[((size_t)f * n + r0 + lr) * n + x] = double(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)]) + ub;
+      p.grid[((size_t)f * n + r0 + lr) * n + x] =
+          double(Prec2<T>::to_pt(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)])) + ub;
     }
     return;
   }
 
   // one thread per (point, stencil row in the band): the row's partial sum is added to Y
   for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
-    const GatherItem<T> it = (PF && t == (int)threadIdx.x) ? it0 : gather_item(p, pr, t, r0);
+    const GatherItem<PT> it = (PF && t == (int)threadIdx.x) ? it0 : gather_item(p, pr, t, r0);
     const int lr = it.lr;
     if (lr >= R) continue;
     const int i = it.i;
     const int bx = it.bx;
-    const T py = it.py;
-    const T dy = (OP == OP_ADJ_AN || OP == OP_STOKES_T) ? it.dy : T(0);
+    const PT py = it.py;
+    const PT dy = (OP == OP_ADJ_AN || OP == OP_STOKES_T) ? it.dy : PT(0);
     const int eb = (lr >> 1) * n, odd = lr & 1;
+    auto uval = [&](int e) { return Prec2<T>::to_pt(u[2 * pidx(e) + odd]); };
     if (OP == OP_STOKES_T) {
       // a_s = Σ v_s Φ, G_mk = Σ v_gm ∂_kΦ; out_l += (Δs/h²)[n_l a_s + Σ_k n_k (G_lk + G_kl)]
-      T as = 0, gxx = 0, gxy = 0, gyx = 0, gyy = 0;
+      PT as = 0, gxx = 0, gxy = 0, gyx = 0, gyy = 0;
 #pragma unroll
       for (int ax = 0; ax < 4; ++ax) {
         const int col = (bx + ax) & (n - 1);
-        const T px = it.px[ax], dx = it.dx[ax];
-        const T vs = u[2 * pidx(eb + col) + odd];
-        const T vx = u[2 * pidx(eb + half * n + col) + odd];
-        const T vy = u[2 * pidx(eb + 2 * half * n + col) + odd];
+        const PT px = it.px[ax], dx = it.dx[ax];
+        const PT vs = uval(eb + col);
+        const PT vx = uval(eb + half * n + col);
+        const PT vy = uval(eb + 2 * half * n + col);
         as += vs * px * py;
         gxx += vx * dx * py;
         gxy += vx * px * dy;
@@ -841,19 +869,19 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
       atomicAdd(pout + M + i, ws * (ny * double(as) + nx * cross + 2.0 * ny * double(gyy)));
       continue;
     }
-    T acc0 = 0, acc1 = 0;
+    PT acc0 = 0, acc1 = 0;
 #pragma unroll
     for (int ax = 0; ax < 4; ++ax) {
       const int col = (bx + ax) & (n - 1);
-      const T px = it.px[ax];
-      const T v0 = u[2 * pidx(eb + col) + odd];
+      const PT px = it.px[ax];
+      const PT v0 = uval(eb + col);
       if (OP == OP_ADJ_AN) {
         acc0 += v0 * it.dx[ax] * py;
         acc1 += v0 * px * dy;
       } else {
-        const T pp = px * py;
+        const PT pp = px * py;
         acc0 += v0 * pp;
-        if (NOUT == 2) acc1 += u[2 * pidx(eb + half * n + col) + odd] * pp;
+        if (NOUT == 2) acc1 += uval(eb + half * n + col) * pp;
       }
     }
     if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
@@ -881,35 +909,10 @@ __global__ void __launch_bounds__(kMaxThreads2d) k_rowifft_gather(RowParams<T> p
 // batched launches: one grid per stage covers every problem of a batch; CTA i runs work unit
 // units[i] = (problem, unit) with that problem's parameter block and transform size
 // ------------------------------------------------------------------------------------------
-// The batched kernels are compiled for sizes up to 2^LMAX: a batch whose grids are all small runs
-// the variant without the large-grid bodies (whose registers would otherwise bound every CTA).
-constexpr int kBatchSmallL2d = 9;
-
-template <typename T, int OP, int L, int LMAX>
-__device__ __forceinline__ void kb_row_dispatch(const RowParams<T>& p, int unit, unsigned char* smem, bool fwd) {
-  if constexpr (L <= LMAX) {
-    if (p.log2n == L) {
-      if (fwd)
-        spread_rowfft_body<T, OP, L, false>(p, unit, p.n / p.R, smem);
-      else
-        rowifft_gather_body<T, OP, G_INTERP, L, false>(p, unit, smem);
-    } else {
-      kb_row_dispatch<T, OP, L + 1, LMAX>(p, unit, smem, fwd);
-    }
-  }
-}
-
-template <typename T, int OP, int L, int LMAX>
-__device__ __forceinline__ void kb_col_dispatch(const ColParams<T>& p, int unit, unsigned char* smem) {
-  if constexpr (L <= LMAX) {
-    if (p.log2n == L)
-      colpass_body<T, OP, L, false>(p, unit, smem);
-    else
-      kb_col_dispatch<T, OP, L + 1, LMAX>(p, unit, smem);
-  }
-}
-
-template <typename T, int OP, int LMAX>
+// One batched kernel per stage and grid size: a CTA runs unit units[i] = (problem, unit) of a
+// problem of this size with that problem's parameter block (the bodies load twiddles, symbol rows
+// and the first gather item where they are used, which keeps registers down and occupancy up).
+template <typename T, int OP, int L>
 __global__ void __launch_bounds__(kMaxThreads2d) kb_spread_rowfft(const RowParams<T>* __restrict__ P, const int2* units,
                                                                   const double* in_base, double* out_base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -917,18 +920,18 @@ __global__ void __launch_bounds__(kMaxThreads2d) kb_spread_rowfft(const RowParam
   RowParams<T> p = P[u.x];
   p.in = in_base + p.io_off;
   p.out = out_base + p.io_off;
-  kb_row_dispatch<T, OP, kMinL2d, LMAX>(p, u.y, smem_raw, true);
+  spread_rowfft_body<T, OP, L, false>(p, u.y, p.n / p.R, smem_raw);
 }
 
-template <typename T, int OP, int LMAX>
+template <typename T, int OP, int L>
 __global__ void __launch_bounds__(kMaxThreads2d) kb_colpass(const ColParams<T>* __restrict__ P, const int2* units) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int2 u = units[blockIdx.x];
   const ColParams<T> p = P[u.x];
-  kb_col_dispatch<T, OP, kMinL2d, LMAX>(p, u.y, smem_raw);
+  colpass_body<T, OP, L, false>(p, u.y, smem_raw);
 }
 
-template <typename T, int OP, int LMAX>
+template <typename T, int OP, int L>
 __global__ void __launch_bounds__(kMaxThreads2d) kb_rowifft_gather(const RowParams<T>* __restrict__ P, const int2* units,
                                                                    const double* in_base, double* out_base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -936,7 +939,7 @@ __global__ void __launch_bounds__(kMaxThreads2d) kb_rowifft_gather(const RowPara
   RowParams<T> p = P[u.x];
   p.in = in_base + p.io_off;
   p.out = out_base + p.io_off;
-  kb_row_dispatch<T, OP, kMinL2d, LMAX>(p, u.y, smem_raw, false);
+  rowifft_gather_body<T, OP, G_INTERP, L, false>(p, u.y, smem_raw);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -66,7 +66,7 @@ ibdl_status set_attrs_2d() {
   IBDL_CUDA(opt_in_smem(k_spread_rowfft<T, OP, L>, d1));
   IBDL_CUDA(opt_in_smem(k_colpass<T, OP, L>, d2));
   IBDL_CUDA(opt_in_smem(k_rowifft_gather<T, OP, G_INTERP, L>, d3));
-  IBDL_CUDA(opt_in_smem(k_rowifft_gather<T, OP, G_GRID, L>, d4));
+  if constexpr (!std::is_same<T, ff>::value) IBDL_CUDA(opt_in_smem(k_rowifft_gather<T, OP, G_GRID, L>, d4));
   return IBDL_OK;
 }
 
@@ -82,30 +82,76 @@ ibdl_status launch_apply_2d(Geometry* g, const RowParams<T>& rp, const ColParams
   if (g->timing) timing_mark(g, s, st0);
   IBDL_CUDA(launch_k(k_colpass<T, OP, L>, (n / 2) / lc.C, lc.threads_col, lc.smem_col, s, lc.pdl, cp));
   if (g->timing) timing_mark(g, s, st0 + 1);
-  if (lc.grid_mode == G_GRID)
-    IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_GRID, L>, n / lc.R, lc.threads_gather, lc.smem_gather, s, lc.pdl,
-                       rp));
-  else
+  if constexpr (std::is_same<T, ff>::value) {
+    // float-float serves boundary applications only (the refinement residual)
+    if (lc.grid_mode == G_GRID) return fail(IBDL_ERR_UNSUPPORTED, "float-float grid output");
     IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_INTERP, L>, n / lc.R, lc.threads_gather, lc.smem_gather, s, lc.pdl,
                        rp));
+  } else if (lc.grid_mode == G_GRID) {
+    IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_GRID, L>, n / lc.R, lc.threads_gather, lc.smem_gather, s, lc.pdl,
+                       rp));
+  } else {
+    IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_INTERP, L>, n / lc.R, lc.threads_gather, lc.smem_gather, s, lc.pdl,
+                       rp));
+  }
   if (g->timing) timing_mark(g, s, st0 + 2);
   g->launches += 3;
   IBDL_CUDA(cudaGetLastError());
   return IBDL_OK;
 }
 
-// every operator and both precisions at one size
+// One batched stage (0 spread + row FFT, 1 column pass, 2 inverse row FFT + gather) for the
+// problems of grid size 2^L: a launch over their (problem, unit) range of the batch's tables.
+template <typename T, int OP, int L>
+ibdl_status batch_stage_2d(Batch* B, int stage, int mode, const double* in_base, double* out_base, cudaStream_t s,
+                           bool pdl) {
+  constexpr int pi = std::is_same<T, float>::value ? 1 : (std::is_same<T, ff>::value ? 2 : 0);
+  const BatchSize& z = B->lv[pi][L];
+  const RowParams<T>* rp = static_cast<const RowParams<T>*>(B->rowp[pi][mode]);
+  const ColParams<T>* cp = static_cast<const ColParams<T>*>(B->colp[pi]);
+  if (stage == 0) {
+    static std::atomic<unsigned long long> d{0};
+    IBDL_CUDA(opt_in_smem(kb_spread_rowfft<T, OP, L>, d));
+    IBDL_CUDA(launch_k(kb_spread_rowfft<T, OP, L>, z.row_count, z.threads_row, z.smem_row, s, pdl, rp,
+                       (const int2*)B->row_units[pi] + z.row_start, in_base, out_base));
+  } else if (stage == 1) {
+    static std::atomic<unsigned long long> d{0};
+    IBDL_CUDA(opt_in_smem(kb_colpass<T, OP, L>, d));
+    IBDL_CUDA(launch_k(kb_colpass<T, OP, L>, z.col_count, z.threads_col, z.smem_col, s, pdl, cp,
+                       (const int2*)B->col_units[pi] + z.col_start));
+  } else {
+    static std::atomic<unsigned long long> d{0};
+    IBDL_CUDA(opt_in_smem(kb_rowifft_gather<T, OP, L>, d));
+    IBDL_CUDA(launch_k(kb_rowifft_gather<T, OP, L>, z.row_count, z.threads_gather, z.smem_gather, s, pdl, rp,
+                       (const int2*)B->row_units[pi] + z.row_start, in_base, out_base));
+  }
+  B->launches += 1;
+  return IBDL_OK;
+}
+
+// every operator at one size: FP32 and FP64 (with grid output), float-float (boundary output
+// only, and not the single layer), and the batched stages of the four forward operators
 #define IBDL_INSTANTIATE_2D_OP(T, OP, L)                                                                  \
   template ibdl_status launch_apply_2d<T, OP, L>(Geometry*, const RowParams<T>&, const ColParams<T>&,    \
                                                  const Launch2D&, cudaStream_t);
-#define IBDL_INSTANTIATE_2D_T(T, L)          \
+#define IBDL_INSTANTIATE_2D_B(T, OP, L) \
+  template ibdl_status batch_stage_2d<T, OP, L>(Batch*, int, int, const double*, double*, cudaStream_t, bool);
+#define IBDL_INSTANTIATE_2D_FWD(T, L)         \
   IBDL_INSTANTIATE_2D_OP(T, OP_SCALAR_AN, L) \
   IBDL_INSTANTIATE_2D_OP(T, OP_SCALAR_SD, L) \
   IBDL_INSTANTIATE_2D_OP(T, OP_STOKES_AN, L) \
   IBDL_INSTANTIATE_2D_OP(T, OP_STOKES_SD, L) \
-  IBDL_INSTANTIATE_2D_OP(T, OP_ADJ_AN, L)    \
-  IBDL_INSTANTIATE_2D_OP(T, OP_ADJ_SD, L)    \
-  IBDL_INSTANTIATE_2D_OP(T, OP_STOKES_T, L)  \
+  IBDL_INSTANTIATE_2D_B(T, OP_SCALAR_AN, L)  \
+  IBDL_INSTANTIATE_2D_B(T, OP_SCALAR_SD, L)  \
+  IBDL_INSTANTIATE_2D_B(T, OP_STOKES_AN, L)  \
+  IBDL_INSTANTIATE_2D_B(T, OP_STOKES_SD, L)
+#define IBDL_INSTANTIATE_2D_TRANS(T, L)   \
+  IBDL_INSTANTIATE_2D_OP(T, OP_ADJ_AN, L) \
+  IBDL_INSTANTIATE_2D_OP(T, OP_ADJ_SD, L) \
+  IBDL_INSTANTIATE_2D_OP(T, OP_STOKES_T, L)
+#define IBDL_INSTANTIATE_2D_T(T, L) \
+  IBDL_INSTANTIATE_2D_FWD(T, L)     \
+  IBDL_INSTANTIATE_2D_TRANS(T, L)   \
   IBDL_INSTANTIATE_2D_OP(T, OP_SL, L)
 #define IBDL_INSTANTIATE_2D(L)   \
   IBDL_INSTANTIATE_2D_T(float, L) \
@@ -115,51 +161,30 @@ ibdl_status launch_apply_2d(Geometry* g, const RowParams<T>& rp, const ColParams
 #define IBDL_DECLARE_2D_OP(T, OP, L)                                                                           \
   extern template ibdl_status launch_apply_2d<T, OP, L>(Geometry*, const RowParams<T>&, const ColParams<T>&, \
                                                         const Launch2D&, cudaStream_t);
-#define IBDL_DECLARE_2D_T(T, L)          \
+#define IBDL_DECLARE_2D_B(T, OP, L) \
+  extern template ibdl_status batch_stage_2d<T, OP, L>(Batch*, int, int, const double*, double*, cudaStream_t, bool);
+#define IBDL_DECLARE_2D_FWD(T, L)         \
   IBDL_DECLARE_2D_OP(T, OP_SCALAR_AN, L) \
   IBDL_DECLARE_2D_OP(T, OP_SCALAR_SD, L) \
   IBDL_DECLARE_2D_OP(T, OP_STOKES_AN, L) \
   IBDL_DECLARE_2D_OP(T, OP_STOKES_SD, L) \
-  IBDL_DECLARE_2D_OP(T, OP_ADJ_AN, L)    \
-  IBDL_DECLARE_2D_OP(T, OP_ADJ_SD, L)    \
-  IBDL_DECLARE_2D_OP(T, OP_STOKES_T, L)  \
+  IBDL_DECLARE_2D_B(T, OP_SCALAR_AN, L)  \
+  IBDL_DECLARE_2D_B(T, OP_SCALAR_SD, L)  \
+  IBDL_DECLARE_2D_B(T, OP_STOKES_AN, L)  \
+  IBDL_DECLARE_2D_B(T, OP_STOKES_SD, L)
+#define IBDL_DECLARE_2D_TRANS(T, L)   \
+  IBDL_DECLARE_2D_OP(T, OP_ADJ_AN, L) \
+  IBDL_DECLARE_2D_OP(T, OP_ADJ_SD, L) \
+  IBDL_DECLARE_2D_OP(T, OP_STOKES_T, L)
+#define IBDL_DECLARE_2D_T(T, L) \
+  IBDL_DECLARE_2D_FWD(T, L)     \
+  IBDL_DECLARE_2D_TRANS(T, L)   \
   IBDL_DECLARE_2D_OP(T, OP_SL, L)
 #define IBDL_DECLARE_2D(L)   \
   IBDL_DECLARE_2D_T(float, L) \
   IBDL_DECLARE_2D_T(double, L)
 
-// Batched launches of one operator and precision: one launch per stage over the (problem, unit)
-// tables; each CTA reads its problem's parameter block and runs the body of that problem's size.
-// mode 0: the caller's vectors; mode 1: the batched GMRES Krylov basis. Instantiated in
-// apply2d_batch_*.cu.
-template <typename T, int OP, int LMAX>
-ibdl_status batch_launch_range(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
-  constexpr int pi = std::is_same<T, float>::value ? 1 : 0;
-  static std::atomic<unsigned long long> d1{0}, d2{0}, d3{0};
-  IBDL_CUDA(opt_in_smem(kb_spread_rowfft<T, OP, LMAX>, d1));
-  IBDL_CUDA(opt_in_smem(kb_colpass<T, OP, LMAX>, d2));
-  IBDL_CUDA(opt_in_smem(kb_rowifft_gather<T, OP, LMAX>, d3));
-  const RowParams<T>* rp = static_cast<const RowParams<T>*>(B->rowp[pi][mode]);
-  const ColParams<T>* cp = static_cast<const ColParams<T>*>(B->colp[pi]);
-  IBDL_CUDA(launch_k(kb_spread_rowfft<T, OP, LMAX>, B->nrow_units[pi], B->threads_row[pi], B->smem_row[pi], s, false,
-                     rp, (const int2*)B->row_units[pi], in_base, out_base));
-  IBDL_CUDA(launch_k(kb_colpass<T, OP, LMAX>, B->ncol_units[pi], B->threads_col[pi], B->smem_col[pi], s, true, cp,
-                     (const int2*)B->col_units[pi]));
-  IBDL_CUDA(launch_k(kb_rowifft_gather<T, OP, LMAX>, B->nrow_units[pi], B->threads_gather[pi], B->smem_gather[pi], s,
-                     true, rp, (const int2*)B->row_units[pi], in_base, out_base));
-  B->launches += 3;
-  IBDL_CUDA(cudaGetLastError());
-  return IBDL_OK;
-}
-
-// Batched launches of one operator and precision: one launch per stage over the (problem, unit)
-// tables; each CTA reads its problem's parameter block and runs the body of that problem's size.
-// mode 0: the caller's vectors; mode 1: the batched GMRES Krylov basis. Instantiated in
-// apply2d_batch_*.cu.
-template <typename T, int OP>
-ibdl_status batch_launch_2d(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
-  return B->max_log2n <= kBatchSmallL2d ? batch_launch_range<T, OP, kBatchSmallL2d>(B, mode, in_base, out_base, s)
-                                        : batch_launch_range<T, OP, kMaxL2d>(B, mode, in_base, out_base, s);
-}
+// float-float is compiled for grids up to 4096²
+constexpr int kMaxLff = 12;
 
 }  // namespace ibdl

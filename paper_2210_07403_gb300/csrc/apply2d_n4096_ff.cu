@@ -1,0 +1,8 @@
+// Float-float kernels of the two-dimensional operator for the 4096² grid: the forward operators
+// (single problems and batched stages) and the transposes.
+#include "apply2d_launch.cuh"
+
+namespace ibdl {
+IBDL_INSTANTIATE_2D_FWD(ff, 12)
+IBDL_INSTANTIATE_2D_TRANS(ff, 12)
+}  // namespace ibdl

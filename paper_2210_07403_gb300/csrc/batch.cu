@@ -25,13 +25,13 @@ static void free_batch(Batch* B) {
       if (B->geoms[i]) destroy_geometry(B->geoms[i]);
     delete[] B->geoms;
   }
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < 3; ++p) {
     for (int m = 0; m < 2; ++m)
       if (B->rowp[p][m]) cudaFree(B->rowp[p][m]);
     if (B->colp[p]) cudaFree(B->colp[p]);
     if (B->row_units[p]) cudaFree(B->row_units[p]);
     if (B->col_units[p]) cudaFree(B->col_units[p]);
-    if (B->exec[p]) cudaGraphExecDestroy(B->exec[p]);
+    if (p < 2 && B->exec[p]) cudaGraphExecDestroy(B->exec[p]);
   }
   void* dev[] = {B->V, B->st, B->ctl, B->vec, B->target, B->active, B->d_off, B->d_voff, B->d_nd, B->d_slice};
   for (void* p : dev)
@@ -125,7 +125,7 @@ ibdl_status ibdl_batch_sizes(const ibdl_batch* batch, int* count, int64_t* offse
 ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* stream) {
   set_error("");
   if (!batch || !batch->b) return fail(IBDL_ERR_INVALID_ARG, "batch is NULL");
-  if (precision_mask < 1 || precision_mask > 3) return fail(IBDL_ERR_INVALID_ARG, "precision_mask must be 1, 2 or 3");
+  if (precision_mask < 1 || precision_mask > 7) return fail(IBDL_ERR_INVALID_ARG, "precision_mask must be in 1 … 7");
   Batch* B = batch->b;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* buf = nullptr;
@@ -141,8 +141,9 @@ ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* str
   // (throughput, not one problem's latency)
   const int targets[5] = {512, 1024, 2048, 4096, 8192};
   const int floors[2] = {0, 256};
-  for (int pi = 0; pi < 2 && st == IBDL_OK; ++pi) {
-    if (!(precision_mask & (pi ? 2 : 1))) continue;
+  for (int pi = 0; pi < 3 && st == IBDL_OK; ++pi) {
+    if (!(precision_mask & (1 << pi))) continue;
+    if (pi == 2 && B->max_log2n > 12) continue;  // float-float batches exist to 4096²
     float best = 1e30f;
     int best_t = targets[0], best_c = targets[0], best_f = 0;
     for (int ti = 0; ti < 50 && st == IBDL_OK; ++ti) {
@@ -151,10 +152,10 @@ ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* str
       st = batch_prepare_2d(B);
       if (st != IBDL_OK) break;
       float ms[3];
-      st = batch_apply_2d(B, pi ? IBDL_FP32 : IBDL_FP64, 0, buf, buf + B->total, s);
+      st = batch_apply_2d(B, slot_precision(pi), 0, buf, buf + B->total, s);
       for (int k = 0; k < 3 && st == IBDL_OK; ++k) {
         cudaEventRecord(e0, s);
-        st = batch_apply_2d(B, pi ? IBDL_FP32 : IBDL_FP64, 0, buf, buf + B->total, s);
+        st = batch_apply_2d(B, slot_precision(pi), 0, buf, buf + B->total, s);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(IBDL_ERR_CUDA, "batch autotune: event synchronize");
         cudaEventElapsedTime(&ms[k], e0, e1);
@@ -188,7 +189,8 @@ ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* str
 ibdl_status ibdl_batch_apply(ibdl_batch* batch, int precision, const double* Q, double* Y, void* stream) {
   set_error("");
   if (!batch || !batch->b) return fail(IBDL_ERR_INVALID_ARG, "batch is NULL");
-  if (precision != IBDL_FP64 && precision != IBDL_FP32) return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64 or IBDL_FP32");
+  if (precision != IBDL_FP64 && precision != IBDL_FP32 && precision != IBDL_FP32X2)
+    return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64, IBDL_FP32 or IBDL_FP32X2");
   IBDL_TRY(check_dev(Q, "Q"));
   IBDL_TRY(check_dev(Y, "Y"));
   const int64_t T = batch->b->total;

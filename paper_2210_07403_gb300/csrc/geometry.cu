@@ -4,6 +4,7 @@
 #include <cstring>
 #include <vector>
 
+#include "ff.cuh"
 #include "fft.cuh"
 
 namespace ibdl {
@@ -119,6 +120,17 @@ __global__ void k_twiddles(int n, double2* tw64, float2* tw32) {
   tw32[j] = make_float2((float)c, (float)s);
 }
 
+// float-float copies of the FP64 twiddles and symbols (hi = fl32(x), lo = fl32(x − hi))
+__global__ void k_ff_tables(int n, const double2* tw64, const double* lap64, const double* der64, ff* twff, ff* lapff,
+                            ff* derff) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  twff[2 * j] = ff(tw64[j].x);
+  twff[2 * j + 1] = ff(tw64[j].y);
+  lapff[j] = ff(lap64[j]);
+  derff[j] = ff(der64[j]);
+}
+
 // per-axis symbols at FFT index j, m = j (j < n/2) or j − n, k = 2π m/box:
 //   spectral: lap = k², der = k (0 at the Nyquist index j = n/2)
 //   fd2:      lap = (4/h²) sin²(k h/2) = (4/h²) sin²(π m/n), der = sin(k h)/h = sin(2π m/n)/h
@@ -158,6 +170,9 @@ ibdl_status fill_geometry_tables(Geometry* g, const double* dX, const double* dN
                                              g->h, g->perm, g->base, g->t64, g->t32, g->ddphi64);
   k_twiddles<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->tw64, g->tw32);
   k_symbols<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->box, g->symbol, g->lap64, g->der64, g->lap32, g->der32);
+  if (g->twff)
+    k_ff_tables<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->tw64, g->lap64, g->der64, static_cast<ff*>(g->twff),
+                                                  static_cast<ff*>(g->lapff), static_cast<ff*>(g->derff));
   IBDL_CUDA(cudaGetLastError());
   return IBDL_OK;
 }
@@ -201,7 +216,7 @@ static void free_geometry(Geometry* g) {
   void* ptrs[] = {g->perm, g->base, g->cell_start, g->t64.phi, g->t64.dphi, g->t64.wscale, g->t64.nrm,
                   g->t32.phi, g->t32.dphi, g->t32.wscale, g->t32.nrm, g->spec, g->tw64, g->tw32,
                   g->lap64, g->der64, g->lap32, g->der32, g->ubuf, g->tmp_m, g->V, g->gm, g->vec,
-                  g->ddphi64, g->vjp_buf, g->X64, g->pp_buf, g->src_buf};
+                  g->ddphi64, g->vjp_buf, g->X64, g->pp_buf, g->src_buf, g->twff, g->lapff, g->derff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 4; ++i)
@@ -409,6 +424,11 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
     GTRY(dalloc(&g->der64, sizeof(double) * n));
     GTRY(dalloc(&g->lap32, sizeof(float) * n));
     GTRY(dalloc(&g->der32, sizeof(float) * n));
+    if (dim == 2) {
+      GTRY(dalloc(&g->twff, 2 * sizeof(ff) * n));
+      GTRY(dalloc(&g->lapff, sizeof(ff) * n));
+      GTRY(dalloc(&g->derff, sizeof(ff) * n));
+    }
     GTRY(dalloc(&g->tmp_m, sizeof(double) * (g->ncomp * M + g->ncomp)));  // room for ū / constraint rows
 
     const int tb = 256;
@@ -422,6 +442,9 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
                                                g->origin[2], h, g->perm, g->base, g->t64, g->t32, g->ddphi64);
     k_twiddles<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->tw64, g->tw32);
     k_symbols<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->box, g->symbol, g->lap64, g->der64, g->lap32, g->der32);
+    if (g->twff)
+      k_ff_tables<<<(n + tb - 1) / tb, tb, 0, s>>>(n, g->tw64, g->lap64, g->der64, static_cast<ff*>(g->twff),
+                                                    static_cast<ff*>(g->lapff), static_cast<ff*>(g->derff));
     GCUDA(cudaGetLastError());
     GCUDA(cudaStreamSynchronize(s));
     GCUDA(cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming));

@@ -1,9 +1,10 @@
 // GMRES for A Q = U_b (Sec. 5.3.2: the Schur operator is not symmetric) on the device.
 //
 // Arnoldi runs on one 16-CTA cluster per iteration (8 where 16 is unavailable; arnoldi.cuh):
-// classical Gram–Schmidt applied twice (CGS2) against the basis in FP64, the new Hessenberg
-// column is reduced by the stored Givens rotations, and the residual estimate |g_{k}| is compared
-// with the target on the device. When the target is met (or the cycle is full, or a non-finite
+// classical Gram–Schmidt against the basis in FP64 with one cluster reduction per step (the
+// second projection of CGS2 is taken from the basis' Gram matrix, h = (2I − G)t), the new
+// Hessenberg column is reduced by the stored Givens rotations, and the residual estimate |g_{k}|
+// is compared with the target on the device. When the target is met (or the cycle is full, or a non-finite
 // value appears) the step raises a stop flag that every kernel of the following iterations reads
 // first.
 //
@@ -13,7 +14,8 @@
 // per kernel, the host queuing iteration j+1 before it reads iteration j's status).
 //
 // Mixed precision: iterative refinement. Each sweep solves A₃₂ d = r with FP32 grid arithmetic
-// and the same FP64 Arnoldi/Hessenberg, then forms the FP64 residual r = U_b − A₆₄ Q.
+// and the same FP64 Arnoldi/Hessenberg, then forms the residual r = U_b − A Q with an application
+// in float-float (default) or FP64 arithmetic and the subtraction and norm in FP64.
 #include <cooperative_groups.h>
 
 #include <chrono>
@@ -721,6 +723,8 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
     // does not count against max_refine (which bounds the sweeps whose inner solve converged).
     GmresState* st = reinterpret_cast<GmresState*>(g->gm);
     HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
+    // the residual's application: float-float (2-D) or FP64; its subtraction and norm are FP64
+    const int res_prec = o->residual == IBDL_FP32X2 && g->dim == 2 && g->n <= 4096 ? IBDL_FP32X2 : IBDL_FP64;
     int used = 0, refined = 0;
     const double* rhs = b;
     double bn = 0.0;
@@ -735,7 +739,7 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
       k_axpy<<<(nd + 255) / 256, 256, 0, s>>>(x, d, nd);
       g->launches += 1;
       IBDL_CUDA(cudaGetLastError());
-      IBDL_TRY(apply_any(g, IBDL_FP64, x, d, s, nullptr, op));
+      IBDL_TRY(apply_any(g, res_prec, x, d, s, nullptr, op));
       k_residual<<<1, 1024, 0, s>>>(st, b, d, r, nd);
       g->launches += 1;
       IBDL_CUDA(cudaGetLastError());
@@ -748,7 +752,7 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
       if (sweep == 0) bn = fin.beta;
       used += fin.k;
       inf.fp32_applies += fin.k;
-      inf.fp64_applies += 1;
+      (res_prec == IBDL_FP32X2 ? inf.fp32x2_applies : inf.fp64_applies) += 1;
       inf.sweeps += 1;
       if (fin.status == ST_NONFINITE || !std::isfinite(fin.rnorm))
         return fail(IBDL_ERR_NONFINITE, sweep == 0 && !std::isfinite(bn) ? "U_b contains NaN or Inf"
@@ -959,11 +963,12 @@ static ibdl_status batch_cycle(Batch* B, int prec, const double* rhs, double* x,
   return IBDL_OK;
 }
 
-// r = b − A₆₄x for every problem (r may be NULL), norms into the host states (synchronous)
+// r = b − A x for every problem (r may be NULL), the application in FP64 or float-float
+// (`precision`), the subtraction and norms in FP64, norms into the host states (synchronous)
 static ibdl_status batch_residual(Batch* B, const double* bvec, const double* x, double* r, double* Ax,
-                                  std::vector<double>& rn, cudaStream_t s) {
+                                  std::vector<double>& rn, cudaStream_t s, int precision = IBDL_FP64) {
   GmresState* st = static_cast<GmresState*>(B->st);
-  if (x) IBDL_TRY(batch_apply_2d(B, IBDL_FP64, 0, x, Ax, s));
+  if (x) IBDL_TRY(batch_apply_2d(B, precision, 0, x, Ax, s));
   kb_residual<<<B->count, 256, 0, s>>>(st, bvec, x ? Ax : nullptr, r, B->d_off, B->d_nd);
   B->launches += 1;
   IBDL_CUDA(cudaGetLastError());
@@ -1050,7 +1055,9 @@ ibdl_status batch_solve_impl(Batch* B, const double* Ub, double* Q, const ibdl_s
       rhs = r;
     }
   } else {
-    // iterative refinement: inner FP32-apply GMRES cycles on the FP64 residuals
+    // iterative refinement: inner FP32-apply GMRES cycles on the residuals (applications in
+    // float-float or FP64, subtraction and norms in FP64)
+    const int res_prec = o->residual == IBDL_FP32X2 && B->max_log2n <= 12 ? IBDL_FP32X2 : IBDL_FP64;
     const double* rhs = bvec;
     rn = bn;
     for (int sweep = 0; sweep < o->max_refine && any_active() && used < o->maxit; ++sweep) {
@@ -1075,10 +1082,10 @@ ibdl_status batch_solve_impl(Batch* B, const double* Ub, double* Q, const ibdl_s
       kb_axpy<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(x, d, T);
       B->launches += 1;
       IBDL_CUDA(cudaGetLastError());
-      IBDL_TRY(batch_residual(B, bvec, x, r, tmp, rn, s));
+      IBDL_TRY(batch_residual(B, bvec, x, r, tmp, rn, s, res_prec));
       for (int b = 0; b < C; ++b) {
         if (!active[b]) continue;
-        inf[b].fp64_applies += 1;
+        (res_prec == IBDL_FP32X2 ? inf[b].fp32x2_applies : inf[b].fp64_applies) += 1;
         inf[b].rel_residual = rn[b] / bn[b];
         if (rn[b] <= o->rtol * bn[b]) {
           active[b] = 0;

@@ -111,17 +111,22 @@ struct Geometry {
   // lap = symbol of −∂² along one axis, der = k̃ with ∂ ↦ i k̃ (0 at Nyquist)
   double *lap64, *der64;
   float *lap32, *der32;
+  // float-float copies of the twiddles and symbols (2-D): [n] complex pairs and [n] pairs
+  void* twff;
+  void* lapff;
+  void* derff;
   double* ubuf;    // evaluate_field / adjoint helpers: [c][n^dim] FP64
   double* tmp_m;   // [c*M] scratch boundary vector
   double* vjp_buf; // boundary derivatives: grid fields u and v, allocated on first use
   double* src_buf; // source term g̃: grid-input fields, u_g and S*u_g, allocated on first use
 
   // launch plan (2-D and 3-D)
-  int rows_per_cta[2];   // band height R for the row kernels, per precision (0 = fp64, 1 = fp32)
-  int cols_per_cta[2];   // kx columns per CTA in the column kernels (3-D: the y passes)
+  // per precision slot (0 = fp64, 1 = fp32, 2 = float-float, 2-D only)
+  int rows_per_cta[3];   // band height R for the row kernels
+  int cols_per_cta[3];   // kx columns per CTA in the column kernels (3-D: the y passes)
   int zcols_per_cta[2];  // 3-D: kx columns per CTA in the z pass
   size_t smem_row[2], smem_col[2], smem_row_inv[2];
-  int threads[2];        // 2-D: least threads per CTA of the row kernels, per precision (0: none)
+  int threads[3];        // 2-D: least threads per CTA of the row kernels (0: none)
 
   // GMRES workspace (allocated lazily, sized for `krylov_m`)
   int krylov_m;
@@ -144,6 +149,13 @@ struct Geometry {
   int ev_cap, ev_used;
 };
 
+// Launch shapes of one grid size's batched kernels, and that size's range of the unit tables.
+struct BatchSize {
+  int row_start, row_count, col_start, col_count;
+  int threads_row, threads_col, threads_gather;
+  size_t smem_row, smem_col, smem_gather;
+};
+
 // A batch of independent 2-D problems (same PDE and dipole form; any grid size, point count,
 // λ, delta and symbol per problem). Boundary vectors of all problems are concatenated: problem b
 // owns [off[b], off[b] + c·M_b).
@@ -153,14 +165,16 @@ struct Batch {
   Geometry** geoms;      // host array of per-problem geometries (tables, spectra, symbols)
   int64_t* off;          // host [count + 1]
   int64_t total;
-  // batched-launch data per precision p (0 fp64, 1 fp32) and mode (0 user buffers, 1 Krylov basis)
-  void* rowp[2][2];      // device RowParams<T>[count]
-  void* colp[2];         // device ColParams<T>[count]
-  int2* row_units[2];    // device (problem, unit) tables
-  int2* col_units[2];
-  int nrow_units[2], ncol_units[2];
-  size_t smem_row[2], smem_col[2], smem_gather[2];
-  int threads_row[2], threads_col[2], threads_gather[2];  // CTA sizes of the three launches
+  // batched-launch data per precision slot p (0 fp64, 1 fp32, 2 float-float) and mode (0 user
+  // buffers, 1 Krylov basis)
+  void* rowp[3][2];      // device RowParams<T>[count]
+  void* colp[3];         // device ColParams<T>[count]
+  int2* row_units[3];    // device (problem, unit) tables
+  int2* col_units[3];
+  int nrow_units[3], ncol_units[3];
+  // per precision slot and grid size 2^L: the problems' unit ranges in the tables (sorted by size)
+  // and the launch shapes of that size's batched kernels
+  BatchSize lv[3][14];
   int max_log2n;         // log2 of the largest grid size in the batch
   // batched GMRES
   int m;                 // restart length the workspace was sized for (0: none yet)
@@ -197,6 +211,10 @@ ibdl_status batch_solve_impl(Batch* B, const double* Ub, double* Q, const ibdl_s
 void timing_mark(Geometry* g, cudaStream_t s, int stage);
 ibdl_status set_stage_timing(Geometry* g, int enable);
 ibdl_status get_stage_times(Geometry* g, double* ms, int64_t* launches);
+
+// precision slot of the per-precision launch plans: 0 FP64, 1 FP32, 2 float-float
+inline int prec_slot(int precision) { return precision == IBDL_FP32 ? 1 : (precision == IBDL_FP32X2 ? 2 : 0); }
+inline int slot_precision(int slot) { return slot == 1 ? IBDL_FP32 : (slot == 2 ? IBDL_FP32X2 : IBDL_FP64); }
 
 // ------------------------------------------------------------------------------------------
 // launchers implemented in the .cu files
@@ -250,6 +268,7 @@ inline int geom_nd(const Geometry* g) { return (int)(g->ncomp * g->M) + g->naug;
 
 inline ibdl_status apply_any(Geometry* g, int precision, const double* Q, double* Y,
                              cudaStream_t s, const int* stop_flag, int op = OPK_A) {
+  if (precision == IBDL_FP32X2 && g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "float-float applications are 2-D only");
   return g->dim == 2 ? apply_2d(g, precision, Q, Y, s, stop_flag, op)
                      : apply_3d(g, precision, Q, Y, s, stop_flag, op);
 }

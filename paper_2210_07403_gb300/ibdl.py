@@ -36,13 +36,13 @@ IBDL_PDE_SCALAR, IBDL_PDE_STOKES = 0, 1
 IBDL_DELTA_COS, IBDL_DELTA_SQRT = 0, 1
 IBDL_DIPOLE_ANALYTIC, IBDL_DIPOLE_SPECTRAL_DIV = 0, 1
 IBDL_SYMBOL_SPECTRAL, IBDL_SYMBOL_FD2 = 0, 1
-IBDL_FP64, IBDL_FP32, IBDL_MIXED = 0, 1, 2
+IBDL_FP64, IBDL_FP32, IBDL_MIXED, IBDL_FP32X2 = 0, 1, 2, 3
 
 _PDE = {"scalar": IBDL_PDE_SCALAR, "stokes": IBDL_PDE_STOKES}
 _DELTA = {"cos": IBDL_DELTA_COS, "sqrt": IBDL_DELTA_SQRT}
 _DIPOLE = {"analytic": IBDL_DIPOLE_ANALYTIC, "spectral_div": IBDL_DIPOLE_SPECTRAL_DIV}
 _SYMBOL = {"spectral": IBDL_SYMBOL_SPECTRAL, "fd2": IBDL_SYMBOL_FD2}
-_PREC = {"fp64": IBDL_FP64, "fp32": IBDL_FP32, "mixed": IBDL_MIXED}
+_PREC = {"fp64": IBDL_FP64, "fp32": IBDL_FP32, "mixed": IBDL_MIXED, "fp32x2": IBDL_FP32X2}
 IBDL_BC_DIRICHLET, IBDL_BC_NEUMANN = 0, 1
 _BC = {"dirichlet": IBDL_BC_DIRICHLET, "neumann": IBDL_BC_NEUMANN}
 
@@ -57,13 +57,13 @@ class ibdl_geometry_desc(ctypes.Structure):
 
 class ibdl_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", c_double), ("restart", c_int), ("maxit", c_int), ("precision", c_int),
-                ("inner_rtol", c_double), ("max_refine", c_int), ("io_on_host", c_int)]
+                ("inner_rtol", c_double), ("max_refine", c_int), ("io_on_host", c_int), ("residual", c_int)]
 
 
 class ibdl_solve_info(ctypes.Structure):
     _fields_ = [("iterations", c_int), ("fp64_applies", c_int), ("fp32_applies", c_int),
                 ("sweeps", c_int), ("rel_residual", c_double), ("seconds", c_double),
-                ("kernel_launches", c_int64)]
+                ("kernel_launches", c_int64), ("fp32x2_applies", c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -274,11 +274,11 @@ def ibdl_batch_solve(batch, Ub: int, Q: int, opts: ibdl_solve_opts, infos, strea
     return _check(st) if check else st
 
 
-def ibdl_autotune(geom, precision_mask: int = 3, stream: int = 0) -> int:
+def ibdl_autotune(geom, precision_mask: int = 7, stream: int = 0) -> int:
     return _check(load().ibdl_autotune(geom, int(precision_mask), c_void_p(stream)))
 
 
-def ibdl_batch_autotune(batch, precision_mask: int = 3, stream: int = 0) -> int:
+def ibdl_batch_autotune(batch, precision_mask: int = 7, stream: int = 0) -> int:
     return _check(load().ibdl_batch_autotune(batch, int(precision_mask), c_void_p(stream)))
 
 
@@ -352,7 +352,8 @@ class Batch:
         self._h = ibdl_create_batch(descs, _stream_handle(stream))
         self.count, self.offsets, self.total = ibdl_batch_sizes(self._h)
 
-    def autotune(self, precision_mask: int = 3, stream=None):
+    def autotune(self, precision_mask: int = 7, stream=None):
+        """precision_mask bits: 1 FP64, 2 FP32, 4 float-float."""
         ibdl_batch_autotune(self._h, precision_mask, _stream_handle(stream))
 
     def split(self, v):
@@ -365,11 +366,14 @@ class Batch:
         return Y
 
     def solve(self, Ub, rtol: float = 1e-8, precision: str = "fp64", restart: int = 50, maxit: int = 200,
-              inner_rtol: float = 1e-4, max_refine: int = 6, Q=None, stream=None, check: bool = True):
+              inner_rtol: float = 1e-4, max_refine: int = 6, Q=None, stream=None, check: bool = True,
+              residual: str = "fp32x2"):
+        """residual: arithmetic of the mixed-precision refinement residual's application ("fp32x2"
+        float-float, or "fp64")."""
         t = self._torch
         o = ibdl_default_solve_opts()
         o.rtol, o.restart, o.maxit, o.precision = rtol, restart, maxit, _PREC[precision]
-        o.inner_rtol, o.max_refine = inner_rtol, max_refine
+        o.inner_rtol, o.max_refine, o.residual = inner_rtol, max_refine, _PREC[residual]
         if not Ub.is_cuda:
             o.io_on_host = 1
         if Q is None:
@@ -496,10 +500,12 @@ class Geometry:
         return u
 
     def solve(self, Ub, rtol: float = 1e-8, precision: str = "fp64", restart: int = 50, maxit: int = 200,
-              inner_rtol: float = 1e-4, max_refine: int = 6, Q=None, stream=None, check: bool = True, g=None):
+              inner_rtol: float = 1e-4, max_refine: int = 6, Q=None, stream=None, check: bool = True, g=None,
+              residual: str = "fp32x2"):
         """Solve A Q = U_b (with a source g̃, [c][n][n]: A Q = U_b − S*u_g). U_b on the device (torch
         float64) or a host numpy array / CPU tensor (then the copies happen inside the call,
-        io_on_host); g̃ on the device. Returns (Q, info dict, status)."""
+        io_on_host); g̃ on the device. residual: arithmetic of the mixed-precision refinement
+        residual's application ("fp32x2" float-float, or "fp64"). Returns (Q, info dict, status)."""
         if g is None:
             entry = ibdl_solve
         else:
@@ -507,14 +513,15 @@ class Geometry:
 
             def entry(h, ub, q, o, info, stream, check=True):
                 return ibdl_solve_forced(h, ub, gs.data_ptr(), q, o, info, stream, check=check)
-        return self._solve(entry, Ub, rtol, precision, restart, maxit, inner_rtol, max_refine, Q, stream, check)
+        return self._solve(entry, Ub, rtol, precision, restart, maxit, inner_rtol, max_refine, Q, stream, check,
+                           residual)
 
     def solve_transpose(self, G, rtol: float = 1e-8, precision: str = "fp64", restart: int = 50,
                         maxit: int = 200, inner_rtol: float = 1e-4, max_refine: int = 6, lam=None, stream=None,
-                        check: bool = True):
+                        check: bool = True, residual: str = "fp32x2"):
         """Solve Aᵀ λ = G (scalar PDE), same options as ``solve``. Returns (λ, info dict, status)."""
         return self._solve(ibdl_solve_transpose, G, rtol, precision, restart, maxit, inner_rtol, max_refine, lam,
-                           stream, check)
+                           stream, check, residual)
 
     def apply_transpose(self, G, Z=None, precision: str = "fp64", stream=None):
         G = self._vec(G)
@@ -588,11 +595,12 @@ class Geometry:
                            _stream_handle(stream))
         return out
 
-    def _solve(self, entry, Ub, rtol, precision, restart, maxit, inner_rtol, max_refine, Q, stream, check):
+    def _solve(self, entry, Ub, rtol, precision, restart, maxit, inner_rtol, max_refine, Q, stream, check,
+               residual="fp32x2"):
         t = self._torch
         o = ibdl_default_solve_opts()
         o.rtol, o.restart, o.maxit, o.precision = rtol, restart, maxit, _PREC[precision]
-        o.inner_rtol, o.max_refine = inner_rtol, max_refine
+        o.inner_rtol, o.max_refine, o.residual = inner_rtol, max_refine, _PREC[residual]
         host = isinstance(Ub, np.ndarray) or (hasattr(Ub, "is_cuda") and not Ub.is_cuda)
         if host:
             Ub = t.as_tensor(np.ascontiguousarray(np.asarray(Ub, dtype=np.float64)).reshape(-1)) \
@@ -608,7 +616,8 @@ class Geometry:
         st = entry(self._h, Ub.data_ptr(), Q.data_ptr(), o, info, _stream_handle(stream), check=check)
         return Q, info.as_dict(), st
 
-    def autotune(self, precision_mask: int = 3, stream=None):
+    def autotune(self, precision_mask: int = 7, stream=None):
+        """precision_mask bits: 1 FP64, 2 FP32, 4 float-float (2-D)."""
         ibdl_autotune(self._h, precision_mask, _stream_handle(stream))
 
     def set_stage_timing(self, enable: bool = True):

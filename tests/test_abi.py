@@ -48,8 +48,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(ibdl_geometry_desc), offsetof(ibdl_geometry_desc, n_points),
          offsetof(ibdl_geometry_desc, lambda), offsetof(ibdl_geometry_desc, inputs_on_device),
          offsetof(ibdl_geometry_desc, weights));
-  printf("%zu %zu %zu\n", sizeof(ibdl_solve_opts), offsetof(ibdl_solve_opts, inner_rtol), offsetof(ibdl_solve_opts, io_on_host));
-  printf("%zu %zu\n", sizeof(ibdl_solve_info), offsetof(ibdl_solve_info, seconds));
+  printf("%zu %zu %zu %zu\n", sizeof(ibdl_solve_opts), offsetof(ibdl_solve_opts, inner_rtol), offsetof(ibdl_solve_opts, io_on_host),
+         offsetof(ibdl_solve_opts, residual));
+  printf("%zu %zu %zu\n", sizeof(ibdl_solve_info), offsetof(ibdl_solve_info, seconds), offsetof(ibdl_solve_info, fp32x2_applies));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -61,8 +62,9 @@ int main(void) {
     D, O, S = ibdl.ibdl_geometry_desc, ibdl.ibdl_solve_opts, ibdl.ibdl_solve_info
     assert list(map(int, out[0].split())) == [ctypes.sizeof(D), D.n_points.offset, D.lambda_.offset,
                                              D.inputs_on_device.offset, D.weights.offset]
-    assert list(map(int, out[1].split())) == [ctypes.sizeof(O), O.inner_rtol.offset, O.io_on_host.offset]
-    assert list(map(int, out[2].split())) == [ctypes.sizeof(S), S.seconds.offset]
+    assert list(map(int, out[1].split())) == [ctypes.sizeof(O), O.inner_rtol.offset, O.io_on_host.offset,
+                                             O.residual.offset]
+    assert list(map(int, out[2].split())) == [ctypes.sizeof(S), S.seconds.offset, S.fp32x2_applies.offset]
 
 
 def test_host_side_argument_checks(lib):
@@ -71,6 +73,7 @@ def test_host_side_argument_checks(lib):
 
     o = ibdl.ibdl_default_solve_opts()
     assert (o.rtol, o.restart, o.maxit, o.precision) == (1e-8, 50, 200, ibdl.IBDL_FP64)
+    assert o.residual == ibdl.IBDL_FP32X2
     assert lib.ibdl_create_geometry(None, None, ctypes.byref(ctypes.c_void_p())) == ibdl.IBDL_ERR_INVALID_ARG
     assert "null" in ibdl.ibdl_last_error().lower()
     assert lib.ibdl_apply(None, 0, None, None, None) == ibdl.IBDL_ERR_INVALID_ARG

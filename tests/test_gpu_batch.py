@@ -24,7 +24,12 @@ def _lib():
 
 
 def _rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+    """The larger of the relative 2-norm error ‖a − b‖₂/‖b‖₂ and the element-wise error
+    max|a − b|/max|b|, so every tolerance below bounds both (an error at a few points cannot hide
+    in the norm)."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    d = np.abs(a - b)
+    return float(max(np.linalg.norm(d) / np.linalg.norm(b), d.max() / np.abs(b).max()))
 
 
 def _mixed_batch(dipole="analytic"):
@@ -43,7 +48,7 @@ def _mixed_batch(dipole="analytic"):
 
 
 @pytest.mark.parametrize("dipole", ["analytic", "spectral_div"])
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32x2", 1e-12), ("fp32", 2e-5)])
 def test_batch_apply(dipole, precision, tol):
     from paper_2210_07403_gb300.ibdl import Batch
 

@@ -6,6 +6,9 @@ Tolerances (relative, ‖gpu − oracle‖₂/‖oracle‖₂ unless stated):
                         accuracy target states).
   FP32 grid arithmetic  2e-5 for one application (single-precision FFT rounding O(log N · 6e-8)
                         amplified by the O(10) ratio of ‖S̃‖‖L⁻¹‖‖S*‖ to ‖A‖).
+  Float-float           1e-12 for one application, the FP64 bound (its FFT rounding is
+                        O(log N · 2^−47), the point work is FP64).
+Every comparison bounds both the relative 2-norm and the element-wise error max|Δ|/max|ref|.
   Mixed-precision solve 1e-8 against the oracle solution (refinement drives the FP64 residual
                         below rtol·‖U_b‖ with rtol chosen so that the error bound holds).
 """
@@ -32,7 +35,12 @@ def _lib():
 
 
 def _rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+    """The larger of the relative 2-norm error ‖a − b‖₂/‖b‖₂ and the element-wise error
+    max|a − b|/max|b|, so every tolerance below bounds both (an error at a few points cannot hide
+    in the norm)."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    d = np.abs(a - b)
+    return float(max(np.linalg.norm(d) / np.linalg.norm(b), d.max() / np.abs(b).max()))
 
 
 def _geom(p):
@@ -65,7 +73,7 @@ SCALAR_CASES = [
 
 
 @pytest.mark.parametrize("case", SCALAR_CASES)
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32x2", 1e-12), ("fp32", 2e-5)])
 def test_scalar_apply(case, precision, tol):
     N, M, delta, dipole, symbol, lam = case
     p = _scalar_problem(N, M, delta, dipole, symbol, lam)
@@ -79,7 +87,7 @@ def test_scalar_apply(case, precision, tol):
 
 
 @pytest.mark.parametrize("dipole", ["analytic", "spectral_div"])
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32x2", 1e-12), ("fp32", 2e-5)])
 def test_stokes_apply(dipole, precision, tol):
     p = _stokes_problem(128, 200, dipole=dipole)
     g = _geom(p)
@@ -167,14 +175,18 @@ def test_solve_stokes_full_size_fp64_and_mixed():
     ub = torch.from_numpy(p.Ub.reshape(-1)).cuda()
     Q64, info64, _ = g.solve(ub, rtol=1e-12, maxit=80)
     assert _rel(Q64.cpu().numpy(), ref.x) < 1e-10
-    Qm, infom, _ = g.solve(ub, rtol=1e-10, precision="mixed", maxit=200)
-    assert infom["rel_residual"] <= 1e-10
-    assert _rel(Qm.cpu().numpy(), ref.x) < 1e-8
-    assert infom["fp32_applies"] > infom["fp64_applies"]
-    # sampled operator outputs at full size
+    # mixed precision with the float-float refinement residual (the default) and with the FP64 one
+    for residual in ("fp32x2", "fp64"):
+        Qm, infom, _ = g.solve(ub, rtol=1e-10, precision="mixed", maxit=200, residual=residual)
+        assert infom["rel_residual"] <= 1e-10
+        assert _rel(Qm.cpu().numpy(), ref.x) < 1e-8
+        assert infom["fp32_applies"] > infom["fp64_applies"] + infom["fp32x2_applies"]
+        assert infom["fp32x2_applies" if residual == "fp32x2" else "fp64_applies"] == infom["sweeps"]
+    # sampled operator outputs at full size, FP64 and float-float
     q = np.random.default_rng(5).standard_normal(2 * p.bd.M)
-    y = g.apply(torch.from_numpy(q).cuda()).cpu().numpy()
-    assert _rel(y, O.apply(og, q)) < 1e-12
+    for precision in ("fp64", "fp32x2"):
+        y = g.apply(torch.from_numpy(q).cuda(), precision=precision).cpu().numpy()
+        assert _rel(y, O.apply(og, q)) < 1e-12
 
 
 def test_solve_host_driven_loop_matches_graph():
@@ -215,7 +227,7 @@ def test_solve_restart_cycles():
 
 def test_mixed_solve_short_restart():
     """Mixed precision with a restart length shorter than an inner solve: a sweep whose inner cycle
-    stops at the restart length is followed by an FP64 residual restart and does not count against
+    stops at the restart length is followed by a residual restart and does not count against
     max_refine, so the solve still reaches rtol (graph-driven and host-driven alike)."""
     p = I.star_stokes(128, 200)
     g = _geom(p)
@@ -226,7 +238,7 @@ def test_mixed_solve_short_restart():
         Q, info, _ = g.solve(ub, rtol=1e-10, precision="mixed", restart=5, maxit=400, max_refine=3)
         assert info["rel_residual"] <= 1e-10
         assert info["sweeps"] > 3
-        assert info["fp64_applies"] == info["sweeps"]
+        assert info["fp32x2_applies"] == info["sweeps"] and info["fp64_applies"] == 0
         assert _rel(Q.cpu().numpy(), ref.x) < 1e-8
     g.set_stage_timing(False)
 

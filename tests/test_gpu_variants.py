@@ -25,7 +25,12 @@ def _lib():
 
 
 def _rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+    """The larger of the relative 2-norm error ‖a − b‖₂/‖b‖₂ and the element-wise error
+    max|a − b|/max|b|, so every tolerance below bounds both (an error at a few points cannot hide
+    in the norm)."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    d = np.abs(a - b)
+    return float(max(np.linalg.norm(d) / np.linalg.norm(b), d.max() / np.abs(b).max()))
 
 
 def _cuda(v):
@@ -47,7 +52,7 @@ BRINKMAN = [
 
 
 @pytest.mark.parametrize("case", BRINKMAN)
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32x2", 1e-12), ("fp32", 2e-5)])
 def test_brinkman_apply(case, precision, tol):
     N, M, lam, mu, delta, dipole, symbol = case
     p = I.circle_brinkman(N, M, lam=lam, mu=mu, delta=delta, dipole=dipole, symbol=symbol)
@@ -102,7 +107,7 @@ NEUMANN = [
 
 
 @pytest.mark.parametrize("case", NEUMANN)
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32x2", 1e-12), ("fp32", 2e-5)])
 def test_neumann_apply_and_single_layer(case, precision, tol):
     N, alpha, lam, delta, dipole, symbol = case
     p = I.paper_circle_neumann(N, alpha, lam, delta, symbol, dipole)
@@ -110,7 +115,8 @@ def test_neumann_apply_and_single_layer(case, precision, tol):
     rng = np.random.default_rng(N + 1)
     q = rng.standard_normal(og.M)
     assert _rel(g.apply(_cuda(q), precision=precision).cpu().numpy(), O.apply(og, q)) < tol
-    assert _rel(g.single_layer(_cuda(q), precision=precision).cpu().numpy(), O.single_layer(og, q)) < tol
+    if precision != "fp32x2":  # the single layer runs in FP64 or FP32
+        assert _rel(g.single_layer(_cuda(q), precision=precision).cpu().numpy(), O.single_layer(og, q)) < tol
     if dipole == "analytic":
         assert _rel(g.apply_transpose(_cuda(q), precision=precision).cpu().numpy(),
                     O.transpose_apply(og, q)) < tol
@@ -174,7 +180,7 @@ def _completed_scalar(N=64):
 
 
 @pytest.mark.parametrize("kind", ["stokes", "scalar"])
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32x2", 1e-12), ("fp32", 2e-5)])
 def test_completed_apply_and_field(kind, precision, tol):
     if kind == "stokes":
         p = I.cylinder_array(128, 0.2)
