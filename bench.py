@@ -6,15 +6,17 @@ analytic dipole spread, spectral symbols; boundary data = rigid rotation + seede
 |m| ≤ 8, amplitude 0.1, made flux free (synthetic, seed 2).
 
 A step is one mixed-precision solve (FP32 operator applications inside GMRES, FP64 Arnoldi,
-FP64 refinement residual) to the relative residual that keeps the solution within 1e-8 of the
-FP64 plain GPU solve. `value` is solves/s over all ranks (each rank solves its own replica:
+refinement residual from a float-float application with FP64 subtraction) to the relative
+residual that keeps the solution within 1e-8 of the FP64 plain GPU solve and of the FP64 oracle. `value` is solves/s over all ranks (each rank solves its own replica:
 weak scaling, no collective). L2 is flushed (a 256 MiB write) before every timed step and the
 flush is outside the per-step CUDA-event timing.
 
 Also reported: FP32/FP64 operator applications per second, the FP64 plain GPU solve rate, the
 per-kernel device times (stage timing events), the roofline of the dominant kernel, SM clocks
 sampled during the timed region, the end-to-end rate through the C ABI with host buffers, and
-the FP64 CPU oracle timed on this host (`cpu_baseline`).
+the FP64 CPU oracle timed on this host on one core and on all cores (`cpu_baseline`), and the
+error of every workload's solution against the FP64 oracle's (solved in a background process
+while the GPU runs).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -25,6 +27,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -41,13 +44,23 @@ REF_RTOL = 1e-13           # the FP64 plain GPU reference solution
 ACCURACY = 1e-8
 
 
-def _config():
+def _workload():
     return {"workload": WORKLOAD, "grid": f"{N_GRID}x{N_GRID}", "n_points": N_POINTS, "pde": "stokes",
-            "delta": "cos", "dipole": "analytic", "symbol": "spectral", "solve_rtol": SOLVE_RTOL,
-            "precision": "mixed: fp32 applies, fp64 arnoldi + refinement", "inner_rtol": INNER_RTOL,
-            "gmres": "restart 50, each cycle one CUDA graph with a device-side while loop",
-            "launch_shapes": "autotuned on the GPU before the warm-up",
-            "l2": "flushed before each timed step (256 MiB write, untimed)", "seed": 2}
+            "delta": "cos", "dipole": "analytic", "symbol": "spectral", "solve_rtol": SOLVE_RTOL, "seed": 2}
+
+
+def _config():
+    return dict(_workload(),
+                precision="mixed: fp32 applies, fp64 arnoldi, float-float refinement residual (fp64 subtraction)",
+                inner_rtol=INNER_RTOL, gmres="restart 50, each cycle one CUDA graph with a device-side while loop",
+                launch_shapes="autotuned on the GPU before the warm-up",
+                l2="flushed before each timed step (256 MiB write, untimed)")
+
+
+def _reference_config():
+    return dict(_workload(), precision="fp64 throughout (numpy oracle)",
+                gmres="full GMRES from the definition: modified Gram-Schmidt, least squares by numpy",
+                transforms="numpy.fft", where="host CPU, one process, single-threaded BLAS")
 
 
 def _problem():
@@ -67,23 +80,97 @@ import ibdl_inputs as I
 from oracle import ibdl_oracle as O
 p = I.star_stokes({n}, {m})
 g = O.geometry_from_problem(p)
-times = []
-t_end = time.perf_counter() + {budget}
-while len(times) < {max_solves} and (not times or time.perf_counter() < t_end):
+t_start = {t_start!r}
+if t_start:
+    while time.time() < t_start:
+        time.sleep(0.005)
+t_end = time.time() + {budget}
+times, stamps = [], []
+while len(times) < {max_solves} and (not times or time.time() < t_end):
     t0 = time.perf_counter()
     r = O.solve(g, p.Ub, {rtol}, maxit=100)
     times.append(time.perf_counter() - t0)
-print(json.dumps({{"times": times, "iterations": r.iterations}}))
+    stamps.append(time.time())
+print(json.dumps({{"times": times, "iterations": r.iterations, "last": stamps[-1]}}))
 """
+
+_BLAS1 = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def _oracle_cmd(budget_s, max_solves, rtol, t_start=0.0):
+    code = _ORACLE_SNIPPET.format(root=ROOT, n=N_GRID, m=N_POINTS, budget=budget_s, max_solves=max_solves,
+                                  rtol=rtol, t_start=t_start)
+    return [sys.executable, "-c", code]
 
 
 def run_oracle(budget_s: float, max_solves: int, rtol: float = SOLVE_RTOL):
     """Time the oracle's FP64 solve of the workload in a fresh single-threaded process."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _ORACLE_SNIPPET.format(root=ROOT, n=N_GRID, m=N_POINTS, budget=budget_s, max_solves=max_solves,
-                                  rtol=rtol)
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    out = subprocess.run(_oracle_cmd(budget_s, max_solves, rtol), capture_output=True, text=True,
+                         env=dict(os.environ, **_BLAS1), check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_all_cores(budget_s: float, procs: int, rtol: float = SOLVE_RTOL):
+    """The oracle on every host core: `procs` single-threaded processes solve the workload from a
+    common start time for `budget_s` seconds; throughput = all completed solves / (last finish −
+    start)."""
+    t_start = time.time() + 4.0  # every process has imported numpy and built its geometry by then
+    ps = [subprocess.Popen(_oracle_cmd(budget_s, 1000, rtol, t_start), stdout=subprocess.PIPE, text=True,
+                           env=dict(os.environ, **_BLAS1)) for _ in range(procs)]
+    res = [json.loads(p.communicate()[0].strip().splitlines()[-1]) for p in ps]
+    n = sum(len(r["times"]) for r in res)
+    span = max(r["last"] for r in res) - t_start
+    return {"solves": n, "seconds": span, "value": n / span, "procs": procs}
+
+
+# Oracle solutions of the workloads the bench solves on the GPU, for their errors against the
+# oracle: the 512² star, three problems of the ellipse batch, the 128³ sphere, the 1024² circle
+# of the size sweep and the cylinder array at c = 0.2 (1024²), each to rtol 1e-12.
+_REFERENCE_SNIPPET = r"""
+import sys
+import numpy as np
+sys.path.insert(0, {root!r})
+import ibdl_inputs as I
+from oracle import ibdl_oracle as O
+out = {{}}
+p = I.star_stokes({n}, {m})
+out["star"] = O.solve(O.geometry_from_problem(p), p.Ub, 1e-12, maxit=100).x
+probs = I.ellipse_batch(256)
+for b in (0, 77, 255):
+    q = probs[b]
+    out["batch%d" % b] = O.solve(O.geometry_from_problem(q), q.Ub, 1e-12, maxit=100).x
+p = I.sphere_poisson()
+out["sphere"] = O.solve(O.geometry_from_problem(p), p.Ub, 1e-12, maxit=100).x
+N = 1024
+bd = I.circle(I.points_for_spacing(2 * np.pi * 0.25, 1.0 / N, 0.75))
+ub = I.harmonic_cubic(bd.X[0], bd.X[1])
+q = I.Problem("sweep", 2, N, 1.0, (0.0, 0.0), bd, ub[None, :], "scalar", delta="cos")
+out["sweep1024"] = O.solve(O.geometry_from_problem(q), ub, 1e-12, maxit=100).x
+p = I.cylinder_array(1024, 0.2)
+b = np.concatenate([p.Ub.reshape(-1), p.meta["rhs_aug"]])
+out["cyl0.2"] = O.solve(O.geometry_from_problem(p), b, 1e-12, maxit=200).x
+np.savez({path!r}, **out)
+"""
+
+
+def start_oracle_references(path: str):
+    """Start the oracle solutions of the workloads in a background single-threaded process."""
+    code = _REFERENCE_SNIPPET.format(root=ROOT, n=N_GRID, m=N_POINTS, path=path)
+    return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.DEVNULL, stderr=subprocess.PIPE,
+                            env=dict(os.environ, **_BLAS1))
+
+
+def _err(x, ref) -> float:
+    x = np.asarray(x, dtype=np.float64).reshape(-1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(-1)
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
 
 
 # ------------------------------------------------------------------------------------------
@@ -99,11 +186,10 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"ibdl_bench_clocks_{os.getpid()}_{index}.csv")
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={_SMI_FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -207,9 +293,10 @@ def _event_ms(fn, K, flush, stream):
     return float(np.median(ms)), out
 
 
-def extra_workloads(dev, flush, stream, K=5):
+def extra_workloads(dev, flush, stream, sols, K=5):
     """The other workload shapes (context, not the headline): the 64² circle, the 256-problem
-    ellipse batch (with its HBM roofline: the batch does not fit in L2) and the 128³ sphere."""
+    ellipse batch (with its HBM roofline: the batch does not fit in L2) and the 128³ sphere.
+    `sols` receives the GPU solutions compared with the oracle's at the end (sols[key][prec])."""
     import torch
 
     import ibdl_inputs as I
@@ -244,12 +331,16 @@ def extra_workloads(dev, flush, stream, K=5):
         achieved = 4 * cells * w / (t * 1e-3) / 1e9
         res["apply_" + prec] = {"us": round(t * 1e3, 1), "algorithmic_bytes": 4 * cells * w,
                                 "achieved_GBps": round(achieved, 1), "frac_of_measured_hbm": round(achieved / peak, 4)}
+    offs = np.cumsum([0] + [q.ncomp * q.bd.M for q in probs])
+    sols["batch"] = {}
     for prec in ("fp64", "mixed"):
         def run():
             return B.solve(ub, rtol=SOLVE_RTOL, precision=prec, inner_rtol=INNER_RTOL)
         for _ in range(2):
             run()
         t, (Q, infos, st) = _event_ms(run, K, flush, stream)
+        Qh = Q.cpu().numpy()
+        sols["batch"][prec] = {b: Qh[offs[b]:offs[b + 1]] for b in (0, 77, 255)}
         res["solve_" + prec] = {"problems_per_s": round(len(probs) / (t * 1e-3), 1), "ms_per_batch": round(t, 3),
                                 "max_iterations": max(i["iterations"] for i in infos),
                                 "max_rel_residual": max(i["rel_residual"] for i in infos), "status": st}
@@ -267,23 +358,40 @@ def extra_workloads(dev, flush, stream, K=5):
             g.apply(ub, y, precision=prec)
         t, _ = _event_ms(lambda: g.apply(ub, y, precision=prec), K, flush, stream)
         res["apply_" + prec + "_us"] = round(t * 1e3, 1)
+    sols["sphere"] = {}
     for prec in ("fp64", "mixed"):
         def run():
             return g.solve(ub, rtol=SOLVE_RTOL, precision=prec, inner_rtol=INNER_RTOL)
         for _ in range(2):
             run()
         t, (Q, info, st) = _event_ms(run, K, flush, stream)
+        sols["sphere"][prec] = Q.cpu().numpy()
         res["solve_" + prec] = {"solves_per_s": round(1e3 / t, 1), "iterations": info["iterations"],
                                 "fp64_applies": info["fp64_applies"], "rel_residual": info["rel_residual"]}
     res["speedup_mixed_vs_fp64"] = round(res["solve_mixed"]["solves_per_s"] / res["solve_fp64"]["solves_per_s"], 3)
     out["sphere_128"] = res
     g.close()
     out["stokes_star_probes_1024"] = differentiation_workload(dev, flush, stream, K)
-    out["cylinder_array_drag_1024"] = cylinder_drag_workload(dev, flush, stream)
+    out["cylinder_array_drag_1024"] = cylinder_drag_workload(dev, flush, stream, sols=sols)
     out["cylinder_array_drag_2048"] = cylinder_drag_workload(dev, flush, stream, N=2048)
     out["postprocess"] = postprocess_workload(dev, flush, stream)
-    out["size_sweep"] = size_sweep_workload(dev, flush, stream)
+    out["size_sweep"] = size_sweep_workload(dev, flush, stream, sols=sols)
     return out
+
+
+def oracle_errors(out: dict, sols: dict, ref: dict, headline: dict):
+    """Errors of the GPU solutions against the oracle's (relative 2-norm), into the result."""
+    headline["error_vs_oracle"] = {k: _err(v, ref["star"]) for k, v in sols["star"].items()}
+    if not out:
+        return
+    w = out
+    w["ellipse_batch_256"]["error_vs_oracle"] = {
+        prec: {f"problem_{b}": _err(x, ref[f"batch{b}"]) for b, x in per.items()} for prec, per in sols["batch"].items()}
+    w["sphere_128"]["error_vs_oracle"] = {prec: _err(x, ref["sphere"]) for prec, x in sols["sphere"].items()}
+    w["size_sweep"]["N=1024"]["error_vs_oracle"] = {prec: _err(x, ref["sweep1024"])
+                                                    for prec, x in sols["sweep1024"].items()}
+    w["cylinder_array_drag_1024"]["c=0.2"]["error_vs_oracle"] = {prec: _err(x, ref["cyl0.2"])
+                                                                 for prec, x in sols["cyl0.2"].items()}
 
 
 def differentiation_workload(dev, flush, stream, K=5):
@@ -347,7 +455,7 @@ def _published_drag():
     return out
 
 
-def cylinder_drag_workload(dev, flush, stream, K=3, N=1024, cs=(0.05, 0.1, 0.2, 0.3, 0.4, 0.5)):
+def cylinder_drag_workload(dev, flush, stream, K=3, N=1024, cs=(0.05, 0.1, 0.2, 0.3, 0.4, 0.5), sols=None):
     """The paper's Stokes flow past a periodic array of cylinders (Sec. 6.5.3) at N², completed
     method (η = 10, Δs ≈ Δx): the dimensionless drag D = B₁/(μU) per area fraction c against the
     published values, and the solve rate in FP64 (rtol 1e-10) and mixed precision (rtol 1e-9)."""
@@ -369,6 +477,8 @@ def cylinder_drag_workload(dev, flush, stream, K=3, N=1024, cs=(0.05, 0.1, 0.2, 
                 return g.solve(b, rtol=rtol, precision=prec, inner_rtol=INNER_RTOL, maxit=400)
             run()
             t, (x, info, st) = _event_ms(run, K, flush, stream)
+            if sols is not None and c == 0.2:
+                sols.setdefault("cyl0.2", {})[prec] = x.cpu().numpy()
             u = g.evaluate_field(x)
             U = float(u[0][:, 0].sum()) / N
             D = float(-p.eta * (x[: g.M] * w).sum()) / U
@@ -434,14 +544,13 @@ def postprocess_workload(dev, flush, stream, K=5, Ns=(256, 512, 1024, 2048)):
     return res
 
 
-def size_sweep_workload(dev, flush, stream, Ns=(512, 1024, 2048, 4096, 8192), napply=50):
+def size_sweep_workload(dev, flush, stream, Ns=(512, 1024, 2048, 4096, 8192), napply=50, sols=None):
     """The 64² circle problem's geometry on finer grids (Δs ≈ 0.75h, the paper's spacing; its
     studies run N = 2^6 … 2^14): scalar Laplace, analytic dipole, spectral symbol. Per N and
     precision: applications/s from CUDA events over `napply` back-to-back applications after an
     L2 flush, the algorithmic bytes 4N²w (+ boundary vectors) per application against the measured
-    HBM bandwidth, whether the grid fields fit in L2, and FP64 and mixed solve rates to 1e-9.
-    The shared-memory FFT holds whole columns: FP64 up to 4096², FP32 up to 8192² (beyond 2048² FP64
-    and 4096² FP32 without the staged twiddle and symbol tables)."""
+    HBM bandwidth, whether the grid fields fit in L2, and FP64 and mixed solve rates to 1e-9 (the
+    mixed solves' refinement residual is float-float to 4096², FP64 at 8192²)."""
     import torch
 
     import ibdl_inputs as I
@@ -455,9 +564,9 @@ def size_sweep_workload(dev, flush, stream, Ns=(512, 1024, 2048, 4096, 8192), na
         ub = torch.from_numpy(I.harmonic_cubic(bd.X[0], bd.X[1])).to(dev)
         g = Geometry(bd.X, bd.n, bd.w, N, delta="cos")
         row = {"points": M}
+        g.autotune(7)  # FP64, FP32 and float-float (the mixed solves' residual; to 4096²)
         for prec, w in (("fp32", 4), ("fp64", 8)):
             try:
-                g.autotune(1 if prec == "fp64" else 2)
                 y = torch.empty_like(ub)
                 for _ in range(5):
                     g.apply(ub, y, precision=prec)
@@ -484,8 +593,12 @@ def size_sweep_workload(dev, flush, stream, Ns=(512, 1024, 2048, 4096, 8192), na
                     return g.solve(ub, rtol=SOLVE_RTOL, precision=prec, inner_rtol=INNER_RTOL)
                 run()
                 t, (Q, info, st) = _event_ms(run, 3, flush, stream)
+                if sols is not None and N == 1024:
+                    sols.setdefault("sweep1024", {})[prec] = Q.cpu().numpy()
                 row["solve_" + prec] = {"solves_per_s": round(1e3 / t, 2), "iterations": info["iterations"],
                                         "rel_residual": info["rel_residual"]}
+                if prec == "mixed":
+                    row["solve_mixed"]["residual"] = "fp32x2" if info["fp32x2_applies"] else "fp64"
             except IbdlError as e:
                 row["solve_" + prec] = {"unsupported": str(e).split(":")[0]}
         res[f"N={N}"] = row
@@ -537,6 +650,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     from paper_2210_07403_gb300 import ibdl
 
     b.build()
+    # oracle solutions of the workloads, in the background while the GPU runs (rank 0 only)
+    ref_path = os.path.join(tempfile.gettempdir(), f"ibdl_bench_oracle_{os.getpid()}.npz")
+    ref_proc = start_oracle_references(ref_path) if rank == 0 and not args.no_oracle_errors else None
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     p = _problem()
@@ -600,11 +716,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     err_mixed = max(float(torch.linalg.norm(q - q_ref) / torch.linalg.norm(q_ref)) for q, _, _ in outs)
     info_m = outs[-1][1]
+    sols = {"star": {"mixed": outs[-1][0].cpu().numpy()}}
     launches = int(sum(o[1]["kernel_launches"] for o in outs))
 
     # FP64 plain GPU solves (the comparison path)
     ms_fp64, outs64 = timed(lambda: solve("fp64"), K)
     err_fp64 = max(float(torch.linalg.norm(q - q_ref) / torch.linalg.norm(q_ref)) for q, _, _ in outs64)
+    sols["star"]["fp64"] = outs64[-1][0].cpu().numpy()
 
     # per-stage device time of a mixed solve (a separate pass: stage timing records an event
     # around every kernel and drives GMRES from the host, so it is kept out of the timed steps)
@@ -653,7 +771,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                                                  world, dev)
     if rank != 0:
         return None
-    extras = None if args.no_extras else extra_workloads(dev, flush, stream)
+    extras = None if args.no_extras else extra_workloads(dev, flush, stream, sols)
     cufft = None if args.no_extras else cufft_compare(dev, stream)
 
     # dominant kernel of the timed mixed solves, and its average launch from the apply loop
@@ -669,18 +787,35 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "avg_launch_us": round(dom_ms * 1e3, 2), "algorithmic_bytes": int(bytes_dom),
             "note": "grid fields are L2-resident between kernels of one application (6 MB FP32)"}
 
+    # errors against the oracle (its solutions were computed in the background meanwhile)
+    mixed_block = {}
+    if ref_proc is not None:
+        _, err_txt = ref_proc.communicate()
+        if ref_proc.returncode == 0:
+            with np.load(ref_path) as z:
+                ref = {k: z[k] for k in z.files}
+            os.remove(ref_path)
+            oracle_errors(extras or {}, sols, ref, mixed_block)
+        else:
+            mixed_block["error_vs_oracle"] = {"unavailable": err_txt.strip().splitlines()[-1] if err_txt else "failed"}
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         o = run_oracle(budget_s=12.0, max_solves=8)
         tm = float(np.mean(o["times"]))
-        cpu = {"value": round(1.0 / tm, 4), "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": f"{len(o['times'])} FP64 numpy oracle solves of the 512² Stokes star to rtol "
-                         f"{SOLVE_RTOL:g} ({o['iterations']} GMRES iterations each), single thread"}
+        procs = host_cores()
+        allc = run_oracle_all_cores(budget_s=10.0, procs=procs)
+        cpu = {"value": round(allc["value"], 4), "unit": "solves/s", "cores": procs, "kind": "oracle",
+               "sample": f"{allc['solves']} FP64 numpy oracle solves of the 512² Stokes star to rtol {SOLVE_RTOL:g} "
+                         f"({o['iterations']} GMRES iterations each) by {procs} single-threaded processes, one per "
+                         f"host core, in {allc['seconds']:.1f} s",
+               "single_core": {"value": round(1.0 / tm, 4), "unit": "solves/s", "cores": 1,
+                               "sample": f"{len(o['times'])} solves in one single-threaded process"}}
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(t_mixed / K * 1e3, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 applies + f64 arnoldi/refinement",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 applies + f64 arnoldi + f32x2 refinement residual",
         "data": "synthetic (seeded star boundary and Fourier-mode boundary data)", "config": _config(),
         "applies_per_s": {"fp32": round(1e3 / float(np.mean(ms_a32)), 1),
                           "fp64": round(1e3 / float(np.mean(ms_a64)), 1),
@@ -689,10 +824,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                               "timed with CUDA events, programmatic launch between kernels"),
         "fp64_plain": {"solves_per_s": round(K / (sum(ms_fp64) / 1e3), 3), "error_vs_ref": err_fp64,
                        "iterations": outs64[-1][1]["iterations"]},
-        "mixed": {"error_vs_fp64_plain": err_mixed, "iterations": info_m["iterations"],
-                  "fp32_applies": info_m["fp32_applies"], "fp64_applies": info_m["fp64_applies"],
-                  "sweeps": info_m["sweeps"], "rel_residual": info_m["rel_residual"],
-                  "accuracy_ok": err_mixed <= ACCURACY},
+        "mixed": dict({"error_vs_fp64_plain": err_mixed, "iterations": info_m["iterations"],
+                       "fp32_applies": info_m["fp32_applies"], "fp64_applies": info_m["fp64_applies"],
+                       "fp32x2_applies": info_m["fp32x2_applies"],
+                       "sweeps": info_m["sweeps"], "rel_residual": info_m["rel_residual"],
+                       "accuracy_ok": err_mixed <= ACCURACY}, **mixed_block),
         "speedup_mixed_vs_fp64_plain": round(sum(ms_fp64) / sum(ms_mixed), 3),
         "stage_ms_per_solve_host_driven": {k: round(v[0] / K, 4) for k, v in stages_mixed.items()},
         "stage_launches_per_solve": {k: round(v[1] / K, 2) for k, v in stages_mixed.items()},
@@ -727,7 +863,7 @@ def run_reference(args, rank: int):
     return {
         "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": args.gpus, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(sum(times) / K * 1e3, 2), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _reference_config(),
         "impl": "reference",
         "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "kind": "oracle", "cores": 1,
                          "sample": f"{K} FP64 numpy oracle solves of the 512² Stokes star, single thread"},
@@ -743,6 +879,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workload shapes")
+    ap.add_argument("--no-oracle-errors", action="store_true",
+                    help="skip the oracle solutions the workloads' errors are measured against")
     ap.add_argument("--host-driven", action="store_true",
                     help="drive GMRES from the host with one launch per kernel (for profilers that do not "
                          "see kernels inside CUDA-graph conditional bodies); slower")

@@ -375,12 +375,13 @@ ibdl_status ibdl_batch_solve(ibdl_batch* batch, const double* Ub, double* Q, con
                              ibdl_solve_info* infos, void* stream);
 
 /* Y = A Q for a 2-D problem without allocating any memory (the paper has no counterpart: this
- * entry point exists for callers that cannot call cudaMalloc, e.g. code inside a region being
- * captured into a CUDA graph, or a real-time loop that must not take the allocator's locks; such
- * callers cannot create an ibdl_geometry, which allocates). `desc` describes the geometry as for
- * ibdl_create_geometry, with X, normals and weights in device memory (inputs_on_device = 1); their
- * values are not checked (finite coordinates, unit normals and positive weights are the caller's
- * responsibility). Q and Y are device FP64 arrays [c][M]; `precision` is IBDL_FP64 or IBDL_FP32.
+ * entry point exists for callers that cannot call cudaMalloc, e.g. a latency-bound loop that must
+ * not take the allocator's locks, or a plug-in whose host application owns all device memory
+ * through its own allocator; such callers cannot create an ibdl_geometry, which allocates its
+ * tables and work buffers). `desc` describes the geometry as for
+ * ibdl_create_geometry, with X, normals and weights in device memory (inputs_on_device = 1); the
+ * descriptor's scalars are checked as there, the arrays' values are not (finite coordinates, unit
+ * normals and positive weights are the caller's responsibility). Q and Y are device FP64 arrays [c][M]; `precision` is IBDL_FP64 or IBDL_FP32.
  * All work space comes from one fixed 8 MiB array inside the library, per GPU, held from library
  * load to process exit: problems needing more (about nf·n²·8 bytes of spectra with nf = 1 to 4
  * fields, plus about 250 bytes per point) are rejected with IBDL_ERR_INVALID_ARG and a message

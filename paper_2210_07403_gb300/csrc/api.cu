@@ -340,7 +340,8 @@ ibdl_status ibdl_autotune(ibdl_geometry* geom, int precision_mask, void* stream)
   ibdl_status st = IBDL_OK;
   if (cudaMemsetAsync(buf, 0, sizeof(double) * nd, s) != cudaSuccess) st = fail(IBDL_ERR_CUDA, "memset");
   for (int pi = 0; pi < 3 && st == IBDL_OK; ++pi)
-    if (precision_mask & (1 << pi)) st = autotune_2d(g, pi, false, s, buf, buf + nd);
+    if ((precision_mask & (1 << pi)) && !(pi == 2 && (g->n > 4096 || !g->twff)))  // float-float: to 4096²
+      st = autotune_2d(g, pi, false, s, buf, buf + nd);
   cudaStreamSynchronize(s);
   cudaFree(buf);
   return st;

@@ -1,12 +1,12 @@
 // ibdl_apply_noalloc: the 2-D operator application A Q with no memory allocation at all.
 //
-// Who needs it: code that runs where allocating device memory is not allowed or not possible,
-// for example a caller inside a region being captured into a CUDA graph (cudaMalloc is not a
-// capturable operation), a real-time loop that must not take the allocator's locks or risk its
-// latency, or a host that has handed all device memory to another allocator. Such a caller cannot
-// create an ibdl_geometry (creating one allocates its tables and work buffers), so this entry point
-// takes the geometry description directly and keeps everything it needs in one fixed array that is
-// part of the library image.
+// Who needs it: code that runs where allocating device memory is not allowed or not possible, for
+// example a real-time or latency-bound loop that must not take the allocator's locks or wait on
+// it, a plug-in whose host application owns all device memory through its own allocator, or a
+// process that has already given the GPU's memory away and must not fail for want of more. Such
+// a caller cannot create an ibdl_geometry (creating one allocates its tables and work buffers), so
+// this entry point takes the geometry description directly and keeps everything it needs in one
+// fixed array that is part of the library image.
 //
 // The array: g_noalloc_scratch below, kNoAllocScratchBytes (8 MiB) per GPU, created when the
 // library is loaded and held by every GPU that loads it until the process exits. Each call carves
@@ -17,6 +17,7 @@
 // Sharing: all calls on one GPU use the same array and it keeps the last call's contents. Two calls
 // whose work overlaps on the GPU (different streams, or different host threads) race on it and
 // give wrong results; serialise them on one stream.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -88,17 +89,18 @@ extern "C" ibdl_status ibdl_apply_noalloc(const ibdl_geometry_desc* d, int preci
   if (!d) return fail(IBDL_ERR_INVALID_ARG, "descriptor is NULL");
   if (d->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_apply_noalloc handles 2-D problems only");
   if (d->n < 16 || d->n > 8192 || (d->n & (d->n - 1))) return fail(IBDL_ERR_INVALID_ARG, "n must be a power of two in [16, 8192]");
-  if (!(d->box > 0) || !(d->box < 1e300)) return fail(IBDL_ERR_INVALID_ARG, "box must be positive and finite");
-  if (!(d->origin[0] == d->origin[0]) || !(d->origin[1] == d->origin[1])) return fail(IBDL_ERR_INVALID_ARG, "origin is NaN");
+  if (!(d->box > 0) || !std::isfinite(d->box)) return fail(IBDL_ERR_INVALID_ARG, "box must be positive and finite");
+  if (!std::isfinite(d->origin[0]) || !std::isfinite(d->origin[1])) return fail(IBDL_ERR_INVALID_ARG, "origin must be finite");
   if (d->n_points < 1 || d->n_points > (int64_t)1 << 28) return fail(IBDL_ERR_INVALID_ARG, "n_points must be in [1, 2^28]");
   if (!d->inputs_on_device) return fail(IBDL_ERR_INVALID_ARG, "X, normals and weights must be device pointers (inputs_on_device = 1)");
   if (d->pde != IBDL_PDE_SCALAR && d->pde != IBDL_PDE_STOKES) return fail(IBDL_ERR_INVALID_ARG, "unknown pde");
-  if (!(d->lambda >= 0)) return fail(IBDL_ERR_INVALID_ARG, "lambda must be >= 0");
+  if (!(d->lambda >= 0) || !std::isfinite(d->lambda)) return fail(IBDL_ERR_INVALID_ARG, "lambda must be finite and >= 0");
   if (d->bc != IBDL_BC_DIRICHLET && d->bc != IBDL_BC_NEUMANN) return fail(IBDL_ERR_INVALID_ARG, "unknown boundary condition");
   if (d->eta != 0) return fail(IBDL_ERR_UNSUPPORTED, "ibdl_apply_noalloc: the completed method (eta > 0) is not supported");
   if (d->bc == IBDL_BC_NEUMANN && d->pde != IBDL_PDE_SCALAR)
     return fail(IBDL_ERR_UNSUPPORTED, "Neumann conditions are implemented for the scalar PDE");
-  if (d->pde == IBDL_PDE_STOKES && !(d->mu > 0)) return fail(IBDL_ERR_INVALID_ARG, "mu must be > 0");
+  if (d->pde == IBDL_PDE_STOKES && (!(d->mu > 0) || !std::isfinite(d->mu)))
+    return fail(IBDL_ERR_INVALID_ARG, "mu must be finite and > 0");
   if (d->delta != IBDL_DELTA_COS && d->delta != IBDL_DELTA_SQRT) return fail(IBDL_ERR_INVALID_ARG, "unknown delta");
   if (d->dipole != IBDL_DIPOLE_ANALYTIC && d->dipole != IBDL_DIPOLE_SPECTRAL_DIV) return fail(IBDL_ERR_INVALID_ARG, "unknown dipole");
   if (d->symbol != IBDL_SYMBOL_SPECTRAL && d->symbol != IBDL_SYMBOL_FD2) return fail(IBDL_ERR_INVALID_ARG, "unknown symbol");

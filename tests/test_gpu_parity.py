@@ -394,3 +394,17 @@ def test_autotune_keeps_parity(pde):
         assert _rel(y, O.apply(og, q)) < tol
     Q, info, _ = g.solve(torch.from_numpy(p.Ub.reshape(-1)).cuda(), rtol=1e-10)
     assert _rel(Q.cpu().numpy(), O.solve(og, p.Ub, 1e-12, maxit=80).x) < 1e-9
+
+
+def test_applications_repeat():
+    """Run to run: the spread sums shared-memory atomics and the gather adds partial sums with
+    global atomics, in an order that varies between runs. Repeated applications of the 512² Stokes
+    star still agree to rounding: 1e-13 in FP64 and float-float, 1e-6 in FP32 (relative 2-norm
+    and element-wise)."""
+    p = _stokes_problem(512, 800)
+    g = _geom(p)
+    q = torch.from_numpy(np.random.default_rng(11).standard_normal(2 * p.bd.M)).cuda()
+    for precision, tol in (("fp64", 1e-13), ("fp32x2", 1e-13), ("fp32", 1e-6)):
+        ys = [g.apply(q, precision=precision).cpu().numpy() for _ in range(4)]
+        for y in ys[1:]:
+            assert _rel(y, ys[0]) < tol, precision

@@ -1,6 +1,7 @@
 """ibdl_apply_noalloc, the operator application that allocates nothing (for callers that cannot
-call cudaMalloc, such as code being captured into a CUDA graph or a real-time loop), against the
-regular ibdl_apply through the C ABI.
+call cudaMalloc, such as a latency-bound loop that must not take the allocator's locks or a plug-in
+whose host application owns all device memory), against the regular ibdl_apply through the C ABI
+and against the FP64 oracle.
 
 Collected last on purpose: if it fails, a run that stops at the first failure has already run
 every other test. It also passes on its own in a fresh process (the fixture builds and loads the
@@ -50,6 +51,9 @@ CASES = [
     ("circle_laplace", lambda: I.circle_laplace(64, 100)),
     ("star_stokes_256", lambda: I.star_stokes(256, 400)),
     ("circle_spectral_div_fd2", lambda: I.circle_laplace(128, 201, delta="sqrt", dipole="spectral_div", symbol="fd2", lam=4.0)),
+    # the largest documented case: three FP64 half spectra of 512² (6 MiB) and the tables of 800
+    # points, close to the array's 8 MiB
+    ("star_stokes_512", lambda: I.star_stokes(512, 800)),
 ]
 
 
@@ -60,13 +64,17 @@ def test_noalloc_matches_apply(ibdl, name, make, precision, tol):
 
     dev = torch.device("cuda", 0)
     p = make()
+    from oracle import ibdl_oracle as O
+
     geom = Geometry.from_problem(p)
+    og = O.geometry_from_problem(p)
     d, keep = _desc(ibdl, p, dev)
     prec = ibdl._PREC[precision]
     stream = torch.cuda.current_stream().cuda_stream
     rng = np.random.default_rng(len(name))
     for _ in range(2):  # two calls in a row: the shared array keeps the previous call's contents
-        q = torch.from_numpy(rng.standard_normal(p.ncomp * p.bd.M)).to(dev)
+        qh = rng.standard_normal(p.ncomp * p.bd.M)
+        q = torch.from_numpy(qh).to(dev)
         y_ref = geom.apply(q, precision=precision)
         y = torch.full_like(q, float("nan"))
         st = ibdl.load().ibdl_apply_noalloc(ctypes.byref(d), prec, ctypes.c_void_p(q.data_ptr()),
@@ -75,6 +83,10 @@ def test_noalloc_matches_apply(ibdl, name, make, precision, tol):
         torch.cuda.synchronize()
         rel = float(torch.linalg.norm(y - y_ref) / torch.linalg.norm(y_ref))
         assert rel < tol, (name, precision, rel)
+        # and against the oracle, in the relative 2-norm and element by element
+        yh, yo = y.cpu().numpy(), O.apply(og, qh)
+        assert np.linalg.norm(yh - yo) / np.linalg.norm(yo) < tol, (name, precision)
+        assert np.abs(yh - yo).max() < tol * np.abs(yo).max(), (name, precision)
     geom.close()
     del keep
 
