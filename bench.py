@@ -231,16 +231,20 @@ class ClockSampler:
 # our arm
 # ------------------------------------------------------------------------------------------
 
+# the sources of the 2-D kernels: a traffic record is valid for the kernels built from these
+KERNEL_SOURCES = ("apply2d_kernels.cuh", "fft8.cuh", "fft.cuh", "ff.cuh")
+
+
 def _stored_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu capture summary, if that capture
-    was taken on the current kernel source (the file records a hash of csrc/apply2d.cu + fft.cuh)."""
+    was taken on the current kernel source (the file records a hash of KERNEL_SOURCES)."""
     import hashlib
 
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             rec = json.load(f)
         h = hashlib.sha256()
-        for name in ("apply2d.cu", "fft.cuh"):
+        for name in KERNEL_SOURCES:
             with open(os.path.join(ROOT, "paper_2210_07403_gb300", "csrc", name), "rb") as f:
                 h.update(f.read())
         if rec.get("source_sha256") != h.hexdigest():
@@ -760,7 +764,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "us_p90": round(float(np.percentile(per, 90)), 2),
                 "per_s": round(1e6 / float(np.median(per)), 1)}
 
-    b2b = {prec: back_to_back(prec) for prec in ("fp32", "fp64")}
+    b2b = {prec: back_to_back(prec) for prec in ("fp32", "fp32x2", "fp64")}
 
     # end to end through the C ABI with host buffers (copies inside the call)
     ms_e2e, outs_e2e = timed(lambda: solve("mixed", host=True), K)

@@ -122,11 +122,13 @@ static ColParams<T> col_params(Geometry* g, const int* stop) {
 // Launch shape of one operator at one precision: threads and shared memory of the three kernels
 // for band height R, column group C and the row kernels' least thread count `floor`, or an error
 // if they do not fit.
-static int row_threads(int nf, int R, int L, int floor) {
-  const int need = field_groups_2d(nf, L) * (R / 2) * threads_per_seq_2d(L);
+static int row_threads(int nf, int R, int L, bool f32, int floor) {
+  const int need = field_groups_2d(nf, L, f32) * (R / 2) * threads_per_seq_2d(L, f32);
   return need > floor ? need : (floor < kMaxThreads2d ? floor : kMaxThreads2d);
 }
-static int col_threads(int nf, int C, int L) { return field_groups_2d(nf, L) * C * threads_per_seq_2d(L); }
+static int col_threads(int nf, int C, int L, bool f32) {
+  return field_groups_2d(nf, L, f32) * C * threads_per_seq_2d(L, f32);
+}
 
 template <typename T, int OP>
 static ibdl_status launch_shape(const Geometry* g, int R, int C, int floor, Launch2D* lc) {
@@ -139,9 +141,10 @@ static ibdl_status launch_shape(const Geometry* g, int R, int C, int floor, Laun
   lc->smem_row = smem_rows_2d<T>(NIN, R, L);
   lc->smem_gather = smem_rows_2d<T>(NOUT, R, L);
   lc->smem_col = smem_cols_2d<T>(NMAX, C, L);
-  lc->threads_row = row_threads(NIN, R, L, floor);
-  lc->threads_gather = row_threads(NOUT, R, L, floor);
-  lc->threads_col = col_threads(NMAX, C, L);
+  constexpr bool f32 = sizeof(T) == 4;
+  lc->threads_row = row_threads(NIN, R, L, f32, floor);
+  lc->threads_gather = row_threads(NOUT, R, L, f32, floor);
+  lc->threads_col = col_threads(NMAX, C, L, f32);
   if (lc->smem_row > kSmemLimit2d || lc->smem_gather > kSmemLimit2d || lc->smem_col > kSmemLimit2d)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
   if (lc->threads_row > kMaxThreads2d || lc->threads_gather > kMaxThreads2d || lc->threads_col > kMaxThreads2d)
@@ -524,12 +527,12 @@ static int pow2_in(int v, int lo, int hi) {
 static bool row_fits(const Geometry* g, int pi, int R) {
   const int L = log2i(g->n), nf = nf_row_max(g);
   const size_t bytes = pi == 1 ? smem_rows_2d<float>(nf, R, L) : smem_rows_2d<double>(nf, R, L);
-  return R >= 2 && R <= g->n / 2 && bytes <= kSmemLimit2d && row_threads(nf, R, L, 0) <= kMaxThreads2d;
+  return R >= 2 && R <= g->n / 2 && bytes <= kSmemLimit2d && row_threads(nf, R, L, pi == 1, 0) <= kMaxThreads2d;
 }
 static bool col_fits(const Geometry* g, int pi, int C) {
   const int L = log2i(g->n), nf = nf_row_max(g);
   const size_t bytes = pi == 1 ? smem_cols_2d<float>(nf, C, L) : smem_cols_2d<double>(nf, C, L);
-  return C >= 1 && C <= g->n / 2 && bytes <= kSmemLimit2d && col_threads(nf, C, L) <= kMaxThreads2d;
+  return C >= 1 && C <= g->n / 2 && bytes <= kSmemLimit2d && col_threads(nf, C, L, pi == 1) <= kMaxThreads2d;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -653,9 +656,10 @@ void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target, in
 // allows (one GB300 has 152 SMs), and at least 256 threads in the row kernels; the autotuner
 // refines them. IBDL_PLAN_R and IBDL_PLAN_C override (for tuning experiments).
 ibdl_status plan_2d(Geometry* g) {
-  const int n = g->n, L = log2i(n), qt = threads_per_seq_2d(L);
+  const int n = g->n, L = log2i(n);
   const int min_ctas = 2 * 152;
   for (int pi = 0; pi < 3; ++pi) {
+    const int qt = threads_per_seq_2d(L, pi == 1);
     int R = 2 * pow2_in(256 / qt, 1, n / 4 > 1 ? n / 4 : 1);
     while (R > 2 && (n / R < std::min(min_ctas, n / 2) || !row_fits(g, pi, R))) R /= 2;
     if (!row_fits(g, pi, R)) R = 0;

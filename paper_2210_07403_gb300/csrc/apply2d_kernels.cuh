@@ -49,7 +49,7 @@ struct Prec2<ff> {
   using PT = double;
   static __device__ __forceinline__ cplx<ff> acc_load(const cplx<ff>* b, int i) {
     const cplx<double> d = reinterpret_cast<const cplx<double>*>(b)[i];
-    return mk(ff(d.x), ff(d.y));
+    return mk(ff_from_double(d.x), ff_from_double(d.y));
   }
   static __device__ __forceinline__ double to_pt(ff v) { return double(v); }
 };
@@ -85,26 +85,36 @@ enum { G_INTERP = 0, G_GRID = 1 };
 constexpr int kMaxThreads2d = 512;
 constexpr int kMinL2d = 4, kMaxL2d = 13;
 
-// lanes per thread and threads per sequence of the n = 2^L transforms
-__host__ __device__ constexpr int lanes_per_thread_2d(int L) { return L >= 13 ? 2 : 1; }
-__host__ __device__ constexpr int threads_per_seq_2d(int L) { return (1 << L) / 8 / lanes_per_thread_2d(L); }
+// Lanes per thread and threads per sequence of the n = 2^L transforms. Large grids give a thread
+// several lanes, so that a CTA of at most 512 threads can hold more than one column or row pair:
+// the band-major spectra then move in pieces of R·C elements per band (at least one 32-byte
+// sector). FP32 (8-byte elements): 2 lanes from 2048², 4 at 8192²; FP64 and float-float
+// (16-byte elements): 2 lanes at 8192².
+__host__ __device__ constexpr int lanes_per_thread_2d(int L, bool f32) {
+  return f32 ? (L >= 13 ? 4 : (L >= 11 ? 2 : 1)) : (L >= 13 ? 2 : 1);
+}
+__host__ __device__ constexpr int threads_per_seq_2d(int L, bool f32) { return (1 << L) / 8 / lanes_per_thread_2d(L, f32); }
 
 // Thread groups across the NF fields of a kernel: one group per field when NF·QT threads fit in a
 // CTA (each thread transforms one field), else a single group that transforms the fields one
 // after another.
-__host__ __device__ constexpr int field_groups_2d(int nf, int L) {
-  return nf * threads_per_seq_2d(L) <= kMaxThreads2d ? nf : 1;
+__host__ __device__ constexpr int field_groups_2d(int nf, int L, bool f32) {
+  return nf * threads_per_seq_2d(L, f32) <= kMaxThreads2d ? nf : 1;
 }
 
 // Per-precision register policy: twiddles in registers when they fit the budget, else read from
 // the table at each use.
 template <typename T, int L, int NF>
 struct Cfg2 {
-  static constexpr int V = lanes_per_thread_2d(L);
-  static constexpr int QT = threads_per_seq_2d(L);
-  static constexpr int NGRP = field_groups_2d(NF, L);
+  static constexpr bool F32 = sizeof(T) == 4;
+  static constexpr int V = lanes_per_thread_2d(L, F32);
+  static constexpr int QT = threads_per_seq_2d(L, F32);
+  static constexpr int NGRP = field_groups_2d(NF, L, F32);
   static constexpr int NTW = F8<L, V>::NTW;
-  static constexpr bool TWR = sizeof(T) == 4 ? (NTW * V <= 21) : (NTW * V <= 14);
+  // register budget for twiddles: 42 FP32 registers; 56 in FP64; 28 in float-float, whose
+  // arithmetic needs the most temporaries
+  static constexpr bool TWR =
+      F32 ? (NTW * V <= 21) : (std::is_same<T, ff>::value ? (NTW * V <= 7) : (NTW * V <= 14));
   using TW = std::conditional_t<TWR, TwRegs<T, L>, TwTable<T, L>>;
 };
 
@@ -187,6 +197,27 @@ __device__ __forceinline__ PointRanges band_points(const int* cell_start, int n,
     pr.cnt = pr.cnt1 + (cell_start[hi] - pr.s2);
   }
   return pr;
+}
+
+// Two adjacent complex values of a band-major spectrum (A_k and B_k of a row pair, at an even
+// element offset): one 16-byte access in FP32, two otherwise.
+__device__ __forceinline__ void store_pair(cplx<float>* p, cplx<float> a, cplx<float> b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+template <typename T>
+__device__ __forceinline__ void store_pair(cplx<T>* p, cplx<T> a, cplx<T> b) {
+  p[0] = a;
+  p[1] = b;
+}
+__device__ __forceinline__ void load_pair(const cplx<float>* p, cplx<float>& a, cplx<float>& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = mk(v.x, v.y);
+  b = mk(v.z, v.w);
+}
+template <typename T>
+__device__ __forceinline__ void load_pair(const cplx<T>* p, cplx<T>& a, cplx<T>& b) {
+  a = p[0];
+  b = p[1];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -384,25 +415,27 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   }
   __syncthreads();
 
-  // unpack Z = FFT(a + i b) of the row pair (2j, 2j + 1) into A = FFT(a) (even rows) and
-  // B = FFT(b) (odd rows), k = 0..n/2, packed format; thread t writes element t of the field's
-  // band-major block, k·R + rr, so consecutive threads write consecutive addresses
+  // unpack Z = FFT(a + i b) of the row pair (2j, 2j + 1) into A = FFT(a) (even row) and
+  // B = FFT(b) (odd row), k = 0..n/2, packed format: thread t takes wavenumber k = t mod n/2 of
+  // one (field, row pair), reads Z_k and Z_{n−k} once and writes A_k and B_k, adjacent in the
+  // band-major block (offset k·R + 2j), with one store
   const cplx<T>* res = buf;
   constexpr int nh = n >> 1, lnh = L - 1;
-  const int lR = __ffs(R) - 1;
-  for (int t = threadIdx.x; t < NIN * nh * R; t += blockDim.x) {
-    const int rr = t & (R - 1), k = (t >> lR) & (nh - 1), f = t >> (lR + lnh);
-    const int zb = (f * half + (rr >> 1)) * n;
-    cplx<T> v;
+  for (int t = threadIdx.x; t < NIN * half * nh; t += blockDim.x) {
+    const int k = t & (nh - 1), q2 = t >> lnh;
+    const int f = q2 / half, jj = q2 - f * half;
+    const int zb = (f * half + jj) * F::PN;
+    cplx<T> a, b;
     if (k == 0) {
-      const cplx<T> z0 = res[pidx(zb)], zh = res[pidx(zb + nh)];
-      v = (rr & 1) ? mk(z0.y, zh.y) : mk(z0.x, zh.x);
+      const cplx<T> z0 = res[zb], zh = res[zb + ppos(nh)];
+      a = mk(z0.x, zh.x);
+      b = mk(z0.y, zh.y);
     } else {
-      const cplx<T> zk = res[pidx(zb + k)], zc = res[pidx(zb + n - k)];
-      v = (rr & 1) ? mk(T(0.5) * (zk.y + zc.y), T(0.5) * (zc.x - zk.x))
-                   : mk(T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y));
+      const cplx<T> zk = res[zb + ppos(k)], zc = res[zb + ppos(n - k)];
+      a = mk(T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y));
+      b = mk(T(0.5) * (zk.y + zc.y), T(0.5) * (zc.x - zk.x));
     }
-    p.spec[(f * n + r0) * nh + (t - f * (nh << lR))] = v;
+    store_pair(p.spec + ((f * n + r0) * nh + k * R + 2 * jj), a, b);
   }
 }
 
@@ -727,12 +760,13 @@ template <typename T, int L>
 __device__ __forceinline__ cplx<T> row_z(const cplx<T>* __restrict__ spec, int f, int r0, int jj, int R, int m) {
   constexpr int n = 1 << L, nh = n / 2;
   const cplx<T>* band = spec + ((f * n + r0) * nh + 2 * jj);
+  cplx<T> A, B;
   if (m == 0 || m == nh) {
-    const cplx<T> A = band[0], B = band[1];
+    load_pair(band, A, B);
     return m == 0 ? mk(A.x, B.x) : mk(A.y, B.y);
   }
   const int k = m < nh ? m : n - m;
-  const cplx<T> A = band[k * R], B = band[k * R + 1];
+  load_pair(band + k * R, A, B);
   return m < nh ? mk(A.x - B.y, A.y + B.x) : mk(A.x + B.y, B.x - A.y);
 }
 

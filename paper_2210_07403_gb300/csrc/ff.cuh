@@ -61,6 +61,27 @@ __device__ __forceinline__ ff operator/(ff a, ff b) {
   return ff_fast_two_sum(q1, q2);
 }
 __device__ __forceinline__ ff& operator+=(ff& a, ff b) { return a = a + b; }
+
+// The float-float value of a double by integer arithmetic on its bits, so the conversion does not
+// use the FP64 pipe. With d = ±M·2^(e−1075) (e the biased exponent, M the 53-bit significand):
+// Mh = ⌊(M + 2^28)/2^29⌋ ≤ 2^24 (the leading 24 bits, rounded; converts to FP32 exactly) gives
+// hi = ±Mh·2^(e−1046), and r = M − 2^29·Mh (|r| ≤ 2^28) gives lo = ±fl32(r)·2^(e−1075), so
+// |d − hi − lo| ≤ 2^−24·|lo| ≤ 2^−48·|d|. Both scales are normal floats and hi does not overflow
+// for 949 ≤ e ≤ 1149 (2^−74 ≤ |d| < 2^127); zero and values outside that range are converted
+// through FP64.
+__device__ __forceinline__ ff ff_from_double(double d) {
+  const long long b = __double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e < 949 || e > 1149) return ff(d);
+  const long long M = (b & 0xfffffffffffffLL) | (1LL << 52);
+  const long long Mh = (M + (1LL << 28)) >> 29;
+  const int r = (int)(M - (Mh << 29));
+  const float s_hi = __int_as_float((e - 1046 + 127) << 23);  // 2^(e − 1046)
+  const float s_lo = __int_as_float((e - 1075 + 127) << 23);  // 2^(e − 1075)
+  const float hi = __int2float_rn((int)Mh) * s_hi;
+  const float lo = __int2float_rn(r) * s_lo;
+  return b < 0 ? ff(-hi, -lo) : ff(hi, lo);
+}
 __device__ __forceinline__ bool operator==(ff a, ff b) { return a.hi == b.hi && a.lo == b.lo; }
 __device__ __forceinline__ bool operator!=(ff a, ff b) { return !(a == b); }
 // comparisons of normalised values: the high parts decide unless they are equal

@@ -144,6 +144,62 @@ __device__ __forceinline__ void f8_stage(cplx<T> (&x)[8], const TW& tw) {
 // padded position of element e of a sequence (see pidx); e < N
 __device__ __forceinline__ int ppos(int e) { return e + (e >> 3); }
 
+// The same transform for one sequence with the radix-8 stages as a loop over a runtime
+// sub-length p and the twiddles read from the table (index r·k·n/(8p), k = j mod p): one copy of
+// the stage code instead of one per stage. For float-float, whose unrolled stages would not fit
+// the instruction cache.
+template <typename T, bool INV, int L, int V>
+__device__ __forceinline__ void f8_fft_rolled(cplx<T> (&x)[1][V][8], cplx<T>* buf, int j0,
+                                              const cplx<T>* __restrict__ tab, bool active) {
+  using F = F8<L, V>;
+#pragma unroll 1
+  for (int S = 0; S < F::S8; ++S) {
+    const int p = 1 << (3 * S);
+    if (active) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if (S > 0) {
+          const int step = ((j0 + v * F::QT) & (p - 1)) << (L - 3 - 3 * S);
+#pragma unroll
+          for (int r = 1; r < 8; ++r) x[0][v][r] = cmul_tw<T, INV>(x[0][v][r], tab[r * step]);
+        }
+        dft8<T, INV>(x[0][v]);
+      }
+    }
+    if (S + 1 < F::NST) {
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int j = j0 + v * F::QT, k = j & (p - 1);
+          const int base = (j - k) * 8 + k;
+#pragma unroll
+          for (int t = 0; t < 8; ++t) buf[ppos(base + t * p)] = x[0][v][t];
+        }
+      }
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int j = j0 + v * F::QT;
+#pragma unroll
+          for (int s = 0; s < 8; ++s) x[0][v][s] = buf[ppos(j + s * F::Q)];
+        }
+      }
+    }
+  }
+  if constexpr (F::LT > 0) {
+    if (active) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        TwTable<T, L> tw;
+        tw.load(tab, j0 + v * F::QT);
+        f8_stage<T, INV, L, F::S8>(x[0][v], tw);
+      }
+    }
+  }
+}
+
 // Transform of the FL sequences whose lanes j0 + v·QT (v < V) this thread holds: x[f][v][s] is
 // element j + s·Q on entry and its transform on exit. buf + f·fstride is the padded shared buffer
 // of sequence f. Every thread of the block must call it (it synchronises the block); `active` is
@@ -154,6 +210,11 @@ template <typename T, bool INV, int L, int V, int FL, class TW>
 __device__ __forceinline__ void f8_fft(cplx<T> (&x)[FL][V][8], cplx<T>* buf, int fstride, int j0,
                                        const TW (&tw)[V], bool active) {
   using F = F8<L, V>;
+  if constexpr (FL == 1 && std::is_same<TW, TwTable<T, L>>::value && sizeof(T) == 8 && !std::is_same<T, double>::value) {
+    // float-float (8-byte elements that are not double): the stage loop
+    f8_fft_rolled<T, INV, L, V>(reinterpret_cast<cplx<T>(&)[1][V][8]>(x), buf, j0, tw[0].tab, active);
+    return;
+  }
   static_for<0, F::NST>([&](auto st) {
     constexpr int S = decltype(st)::value;
     if (active) {
