@@ -41,7 +41,10 @@
  *   IBDL_PLAN_R, IBDL_PLAN_C, IBDL_THREADS   2-D launch shape before autotuning (rows per CTA of
  *                            the row kernels, columns per CTA of the column pass, least threads
  *                            per CTA of the row kernels);
- *   IBDL_PLAN3_R, IBDL_PLAN3_C, IBDL_PLAN3_CZ   the same for the 3-D kernels.
+ *   IBDL_PLAN3_R, IBDL_PLAN3_C, IBDL_PLAN3_CZ   the same for the 3-D kernels;
+ *   IBDL_BATCH_PERSISTENT=1  batched column passes of the scalar operator on persistent CTAs
+ *                            that load the next unit before transforming the current one,
+ *                            instead of one CTA per unit (read when a batch is created).
  */
 #ifndef IBDL_H
 #define IBDL_H

@@ -527,7 +527,9 @@ static int pow2_in(int v, int lo, int hi) {
 static bool row_fits(const Geometry* g, int pi, int R) {
   const int L = log2i(g->n), nf = nf_row_max(g);
   const size_t bytes = pi == 1 ? smem_rows_2d<float>(nf, R, L) : smem_rows_2d<double>(nf, R, L);
-  return R >= 2 && R <= g->n / 2 && bytes <= kSmemLimit2d && row_threads(nf, R, L, pi == 1, 0) <= kMaxThreads2d;
+  // R ≤ n/8 (the column pass's lanes then address their rows with one stride per band)
+  return R >= 2 && R <= std::max(2, g->n / 8) && bytes <= kSmemLimit2d &&
+         row_threads(nf, R, L, pi == 1, 0) <= kMaxThreads2d;
 }
 static bool col_fits(const Geometry* g, int pi, int C) {
   const int L = log2i(g->n), nf = nf_row_max(g);
@@ -637,7 +639,7 @@ ibdl_status autotune_2d(Geometry* g, int pi, bool /*fixed_threads*/, cudaStream_
 }
 
 // Shapes from the volume rule: about `target` complex elements of FFT per CTA (so about
-// target/8 lane-threads), R ≤ n/2, within shared memory and the thread limit; `floor` is the row
+// target/8 lane-threads), R ≤ n/8, within shared memory and the thread limit; `floor` is the row
 // kernels' least thread count.
 void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target, int floor) {
   const int n = g->n;

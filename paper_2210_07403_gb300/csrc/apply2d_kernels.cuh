@@ -403,14 +403,14 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
 #pragma unroll
       for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) x[0][v][s] = Prec2<T>::acc_load(sb, ppos(j0 + v * QT + s * F::Q));
+        for (int s = 0; s < 8; ++s) x[0][v][s] = Prec2<T>::acc_load(sb, ppos_strided<F::Q>(j0 + v * QT, s));
     }
     f8_fft<T, false, L, V, 1>(x, sb, 0, j0, tw, active);
     if (active) {
 #pragma unroll
       for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) sb[ppos(j0 + v * QT + s * F::Q)] = x[0][v][s];
+        for (int s = 0; s < 8; ++s) sb[ppos_strided<F::Q>(j0 + v * QT, s)] = x[0][v][s];
     }
   }
   __syncthreads();
@@ -545,6 +545,13 @@ __device__ __forceinline__ int col_at(int f, int m, int k, int R) {
   constexpr int n = 1 << L, nh = n / 2;
   return (f * n + (m & ~(R - 1))) * nh + k * R + (m & (R - 1));
 }
+// row j + s·Q of a lane (j < Q = n/8): with R ≤ Q (the planner keeps it so) the rows j + s·Q
+// lie in bands s·Q/R apart at the same offset, so the element is col_at(f, j, k, R) + s·Q·n/2
+template <int L>
+__device__ __forceinline__ int col_at_s(int f, int j, int s, int k, int R) {
+  constexpr int Q = (1 << L) / 8, nh = (1 << L) / 2;
+  return col_at<L>(f, j, k, R) + s * (Q * nh);
+}
 
 template <typename T, int OP, int L, bool PF = true>
 __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, unsigned char* smem_raw) {
@@ -604,7 +611,7 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
 #pragma unroll
       for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) x[0][v][s] = p.spec[col_at<L>(0, j0 + v * QT + s * Q, kx, R)];
+        for (int s = 0; s < 8; ++s) x[0][v][s] = p.spec[col_at_s<L>(0, j0 + v * QT, s, kx, R)];
     }
     f8_fft<T, false, L, V, 1>(x, sb, 0, j0, tw, active);
     if (packed) {
@@ -614,7 +621,7 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
-          for (int s = 0; s < 8; ++s) sb[ppos(j0 + v * QT + s * Q)] = x[0][v][s];
+          for (int s = 0; s < 8; ++s) sb[ppos_strided<Q>(j0 + v * QT, s)] = x[0][v][s];
       }
       __syncthreads();
     }
@@ -642,7 +649,7 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
 #pragma unroll
       for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) p.spec[col_at<L>(0, j0 + v * QT + s * Q, kx, R)] = x[0][v][s];
+        for (int s = 0; s < 8; ++s) p.spec[col_at_s<L>(0, j0 + v * QT, s, kx, R)] = x[0][v][s];
     }
   } else {
     // forward transforms of the NIN input fields, results left in shared memory
@@ -656,14 +663,14 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
-          for (int s = 0; s < 8; ++s) x[0][v][s] = p.spec[col_at<L>(f, j0 + v * QT + s * Q, kx, R)];
+          for (int s = 0; s < 8; ++s) x[0][v][s] = p.spec[col_at_s<L>(f, j0 + v * QT, s, kx, R)];
       }
       f8_fft<T, false, L, V, 1>(x, sb, 0, j0, tw, act);
       if (act) {
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
-          for (int s = 0; s < 8; ++s) sb[ppos(j0 + v * QT + s * Q)] = x[0][v][s];
+          for (int s = 0; s < 8; ++s) sb[ppos_strided<Q>(j0 + v * QT, s)] = x[0][v][s];
       }
     }
     __syncthreads();
@@ -716,7 +723,7 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
           for (int s = 0; s < 8; ++s) {
             if (s % NGRP != g) continue;
 #pragma unroll
-            for (int f = 0; f < NOUT; ++f) buf[((size_t)f * C + c) * PN + ppos(j0 + v * QT + s * Q)] = o[v][s][f];
+            for (int f = 0; f < NOUT; ++f) buf[((size_t)f * C + c) * PN + ppos_strided<Q>(j0 + v * QT, s)] = o[v][s][f];
           }
       }
     }
@@ -732,16 +739,121 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
-          for (int s = 0; s < 8; ++s) x[0][v][s] = sb[ppos(j0 + v * QT + s * Q)];
+          for (int s = 0; s < 8; ++s) x[0][v][s] = sb[ppos_strided<Q>(j0 + v * QT, s)];
       }
       f8_fft<T, true, L, V, 1>(x, sb, 0, j0, tw, act);
       if (act) {
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
-          for (int s = 0; s < 8; ++s) p.spec[col_at<L>(f, j0 + v * QT + s * Q, kx, R)] = x[0][v][s];
+          for (int s = 0; s < 8; ++s) p.spec[col_at_s<L>(f, j0 + v * QT, s, kx, R)] = x[0][v][s];
       }
     }
+  }
+}
+
+// Persistent batched column pass of a one-field operator (the scalar operator's batches): a
+// CTA takes the units blockIdx.x, blockIdx.x + gridDim.x, … of this size's range (all of one
+// grid size, so equal work: a static round-robin balances them) and loads the next unit's
+// columns into registers before it transforms the current one, so that one unit's HBM latency
+// overlaps the previous unit's transforms.
+template <typename T, int L>
+__device__ __forceinline__ void colpass1_load(const ColParams<T>& p, int unit, int c, int j0, bool active,
+                                              cplx<T> (&x)[1][Cfg2<T, L, 1>::V][8]) {
+  using CF = Cfg2<T, L, 1>;
+  constexpr int V = CF::V, QT = CF::QT, Q = (1 << L) / 8;
+  const int kx = unit * p.C + c;
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int s = 0; s < 8; ++s) x[0][v][s] = p.spec[col_at_s<L>(0, j0 + v * QT, s, kx, p.R)];
+  }
+}
+
+template <typename T, int OP, int L>
+__global__ void __launch_bounds__(kMaxThreads2d) kbp_colpass(const ColParams<T>* __restrict__ P, const int2* units,
+                                                             int nunits) {
+  static_assert(Traits<OP>::NIN == 1 && Traits<OP>::NOUT == 1, "one field in and out");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using CF = Cfg2<T, L, 1>;
+  using F = F8<L, CF::V>;
+  constexpr int n = F::N, nh = n / 2, V = CF::V, QT = CF::QT, Q = F::Q, PN = F::PN;
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  int u = blockIdx.x;
+  if (u >= nunits) return;
+  const int q = threadIdx.x / QT, j0 = threadIdx.x - q * QT;
+  TwTable<T, L> tw[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) tw[v].load(P[units[u].x].tw, j0 + v * QT);
+  int2 cu = units[u];
+  ColParams<T> p = P[cu.x];
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
+  cplx<T> x[1][V][8];
+  colpass1_load<T, L>(p, cu.y, q % p.C, j0, q < p.C && !(p.stop && *p.stop), x);
+  for (;;) {
+    const int c = q % p.C, k0 = cu.y * p.C, kx = k0 + c;
+    const bool stopped = p.stop && *p.stop;  // uniform over the CTA
+    const bool active = q < p.C && !stopped;
+    // the next unit: its parameters and its columns, loaded before this unit's transforms
+    const int un = u + gridDim.x;
+    const bool more = un < nunits;
+    int2 nu = make_int2(0, 0);
+    ColParams<T> pn = p;
+    cplx<T> xn[1][V][8];
+    if (more) {
+      nu = units[un];
+      pn = P[nu.x];
+      colpass1_load<T, L>(pn, nu.y, q % pn.C, j0, q < pn.C && !(pn.stop && *pn.stop), xn);
+    }
+    if (!stopped) {
+      cplx<T>* sb = buf + (size_t)(q < p.C ? c : 0) * PN;
+      f8_fft<T, false, L, V, 1>(x, sb, 0, j0, tw, active);
+      const T lapx = p.lap1[kx], derx = p.der1[kx], lapn = p.lap1[nh], dern = p.der1[nh];
+      if (k0 == 0) {
+        if (active) {
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int s = 0; s < 8; ++s) sb[ppos_strided<Q>(j0 + v * QT, s)] = x[0][v][s];
+        }
+        __syncthreads();
+      }
+      if (active) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            const cplx<T> in[1] = {x[0][v][s]};
+            cplx<T> out[1];
+            const int ky = j0 + v * QT + s * Q;
+            if (kx == 0) {
+              const cplx<T> pm[1] = {sb[ppos((n - ky) & (n - 1))]};
+              symbol_packed<T, OP>(p, lapx, derx, lapn, dern, p.lap1[ky], p.der1[ky], in, pm, out);
+            } else {
+              symbol_point<T, OP>(p, lapx, derx, p.lap1[ky], p.der1[ky], in, out);
+            }
+            x[0][v][s] = out[0];
+          }
+      }
+      f8_fft<T, true, L, V, 1>(x, sb, 0, j0, tw, active);
+      if (active) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) p.spec[col_at_s<L>(0, j0 + v * QT, s, kx, p.R)] = x[0][v][s];
+      }
+    }
+    if (!more) break;
+    __syncthreads();  // this unit's shared-memory reads are done before the next unit's writes
+    u = un;
+    cu = nu;
+    p = pn;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int s = 0; s < 8; ++s) x[0][v][s] = xn[0][v][s];
   }
 }
 
@@ -850,7 +962,7 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
 #pragma unroll
       for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) sb[ppos(j0 + v * QT + s * Q)] = x[0][v][s];
+        for (int s = 0; s < 8; ++s) sb[ppos_strided<Q>(j0 + v * QT, s)] = x[0][v][s];
     }
   }
   __syncthreads();

@@ -4,6 +4,7 @@
 // parallel).
 #pragma once
 
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <type_traits>
@@ -115,6 +116,23 @@ ibdl_status batch_stage_2d(Batch* B, int stage, int mode, const double* in_base,
     IBDL_CUDA(launch_k(kb_spread_rowfft<T, OP, L>, z.row_count, z.threads_row, z.smem_row, s, pdl, rp,
                        (const int2*)B->row_units[pi] + z.row_start, in_base, out_base));
   } else if (stage == 1) {
+    if constexpr (Traits<OP>::NIN == 1 && Traits<OP>::NOUT == 1) {
+      if (B->persistent) {
+        // persistent CTAs (as many as fit on the GPU at once) walk the size's units
+        static std::atomic<unsigned long long> d{0};
+        IBDL_CUDA(opt_in_smem(kbp_colpass<T, OP, L>, d));
+        int per_sm = 0, dev = 0, sms = 0;
+        IBDL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kbp_colpass<T, OP, L>, z.threads_col,
+                                                                z.smem_col));
+        IBDL_CUDA(cudaGetDevice(&dev));
+        IBDL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int grid = std::max(1, std::min(z.col_count, std::max(per_sm, 1) * sms));
+        IBDL_CUDA(launch_k(kbp_colpass<T, OP, L>, grid, z.threads_col, z.smem_col, s, pdl, cp,
+                           (const int2*)B->col_units[pi] + z.col_start, z.col_count));
+        B->launches += 1;
+        return IBDL_OK;
+      }
+    }
     static std::atomic<unsigned long long> d{0};
     IBDL_CUDA(opt_in_smem(kb_colpass<T, OP, L>, d));
     IBDL_CUDA(launch_k(kb_colpass<T, OP, L>, z.col_count, z.threads_col, z.smem_col, s, pdl, cp,

@@ -3,6 +3,7 @@
 // the per-problem parameter blocks and (problem, unit) tables of the batched launches, and the
 // batched GMRES state.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -79,6 +80,10 @@ ibdl_status ibdl_create_batch(const ibdl_geometry_desc* descs, int count, void* 
   B->dipole = descs[0].dipole;
   B->ncomp = descs[0].pde == IBDL_PDE_STOKES ? 2 : 1;
   B->geoms = new Geometry*[count]();
+  {
+    const char* e = getenv("IBDL_BATCH_PERSISTENT");
+    B->persistent = (e && atoi(e) != 0) ? 1 : 0;
+  }
   B->off = new int64_t[count + 1];
   B->voff = new int64_t[count];
   cudaStream_t s = static_cast<cudaStream_t>(stream);

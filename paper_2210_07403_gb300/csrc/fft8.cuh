@@ -143,6 +143,14 @@ __device__ __forceinline__ void f8_stage(cplx<T> (&x)[8], const TW& tw) {
 
 // padded position of element e of a sequence (see pidx); e < N
 __device__ __forceinline__ int ppos(int e) { return e + (e >> 3); }
+// padded position of j + s·Q: ppos(j) + s·(Q + Q/8) when Q is a multiple of 8 (n ≥ 64)
+template <int Q>
+__device__ __forceinline__ int ppos_strided(int j, int s) {
+  if constexpr (Q % 8 == 0)
+    return ppos(j) + s * (Q + Q / 8);
+  else
+    return ppos(j + s * Q);
+}
 
 // The same transform for one sequence with the radix-8 stages as a loop over a runtime
 // sub-length p and the twiddles read from the table (index r·k·n/(8p), k = j mod p): one copy of
@@ -230,11 +238,14 @@ __device__ __forceinline__ void f8_fft(cplx<T> (&x)[FL][V][8], cplx<T>* buf, int
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int j = j0 + v * F::QT, k = j & (p - 1);
-          const int base = (j - k) * 8 + k;
+          // base + t·p (t < 8) keeps base's low three bits when p ≥ 8 (and is 8j + t when
+          // p = 1), so its padded position is ppos(base) plus a constant per t
+          const int pb = ppos((j - k) * 8 + k);
+          constexpr int dt = p == 1 ? 1 : p + p / 8;
 #pragma unroll
           for (int f = 0; f < FL; ++f)
 #pragma unroll
-            for (int t = 0; t < 8; ++t) buf[f * fstride + ppos(base + t * p)] = x[f][v][t];
+            for (int t = 0; t < 8; ++t) buf[f * fstride + pb + t * dt] = x[f][v][t];
         }
       }
       __syncthreads();
@@ -245,7 +256,7 @@ __device__ __forceinline__ void f8_fft(cplx<T> (&x)[FL][V][8], cplx<T>* buf, int
 #pragma unroll
           for (int f = 0; f < FL; ++f)
 #pragma unroll
-            for (int s = 0; s < 8; ++s) x[f][v][s] = buf[f * fstride + ppos(j + s * F::Q)];
+            for (int s = 0; s < 8; ++s) x[f][v][s] = buf[f * fstride + ppos_strided<F::Q>(j, s)];
         }
       }
     }

@@ -176,6 +176,7 @@ struct Batch {
   // and the launch shapes of that size's batched kernels
   BatchSize lv[3][14];
   int max_log2n;         // log2 of the largest grid size in the batch
+  int persistent;        // 1: persistent column-pass CTAs for one-field operators (IBDL_BATCH_PERSISTENT=1)
   // batched GMRES
   int m;                 // restart length the workspace was sized for (0: none yet)
   int64_t* voff;         // host [count]: offset of problem b's basis in V
