@@ -61,6 +61,30 @@ def test_batch_apply(dipole, precision, tol):
         assert _rel(y[sl], O.apply(O.geometry_from_problem(p), q[sl])) < tol
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32x2", 1e-12), ("fp32", 2e-5)])
+def test_batch_apply_persistent_column_pass(precision, tol, monkeypatch):
+    """The persistent batched column pass (IBDL_BATCH_PERSISTENT=1, read when the batch is
+    created): CTAs that walk their size's units match the oracle as the one-CTA-per-unit launches
+    do, and a batched mixed solve with it converges to the oracle's solution."""
+    from paper_2210_07403_gb300.ibdl import Batch
+
+    monkeypatch.setenv("IBDL_BATCH_PERSISTENT", "1")
+    probs = _mixed_batch()
+    B = Batch(probs)
+    q = np.random.default_rng(4).standard_normal(B.total)
+    y = B.apply(torch.from_numpy(q).cuda(), precision=precision).cpu().numpy()
+    for b, p in enumerate(probs):
+        sl = slice(B.offsets[b], B.offsets[b + 1])
+        assert _rel(y[sl], O.apply(O.geometry_from_problem(p), q[sl])) < tol
+    if precision == "fp32":
+        ub = torch.from_numpy(np.concatenate([p.Ub.reshape(-1) for p in probs])).cuda()
+        Q, _, _ = B.solve(ub, rtol=1e-10, precision="mixed")
+        Q = Q.cpu().numpy()
+        for b, p in enumerate(probs):
+            sl = slice(B.offsets[b], B.offsets[b + 1])
+            assert _rel(Q[sl], O.solve(O.geometry_from_problem(p), p.Ub, 1e-12).x) < 1e-8
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_batch_solve(precision):
     from paper_2210_07403_gb300.ibdl import Batch
