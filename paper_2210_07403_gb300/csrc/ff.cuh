@@ -67,11 +67,13 @@ __device__ __forceinline__ ff& operator+=(ff& a, ff b) { return a = a + b; }
 // Mh = ⌊(M + 2^28)/2^29⌋ ≤ 2^24 (the leading 24 bits, rounded; converts to FP32 exactly) gives
 // hi = ±Mh·2^(e−1046), and r = M − 2^29·Mh (|r| ≤ 2^28) gives lo = ±fl32(r)·2^(e−1075), so
 // |d − hi − lo| ≤ 2^−24·|lo| ≤ 2^−48·|d|. Both scales are normal floats and hi does not overflow
-// for 949 ≤ e ≤ 1149 (2^−74 ≤ |d| < 2^127); zero and values outside that range are converted
+// for 949 ≤ e ≤ 1149 (2^−74 ≤ |d| < 2^127). Zero (most nodes of a spread grid) and subnormal
+// doubles (below 2^−1022) give (0, 0); the remaining values outside that range are converted
 // through FP64.
 __device__ __forceinline__ ff ff_from_double(double d) {
   const long long b = __double_as_longlong(d);
   const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return ff(0.0f, 0.0f);
   if (e < 949 || e > 1149) return ff(d);
   const long long M = (b & 0xfffffffffffffLL) | (1LL << 52);
   const long long Mh = (M + (1LL << 28)) >> 29;

@@ -254,11 +254,12 @@ def test_solve_zero_rhs(precision):
     assert float(Q.abs().max()) == 0.0
 
 
-@pytest.mark.parametrize("N,pde,precision,tol", [(4096, "scalar", "fp64", 1e-12), (8192, "scalar", "fp32", 2e-5),
-                                                   (2048, "stokes", "fp64", 1e-12), (4096, "stokes", "fp32", 2e-5)])
-def test_large_grids_global_tables(N, pde, precision, tol):
-    """Grids whose FFT buffers leave no room for the staged twiddles and symbol tables: the
-    kernels read those from global memory. Applications against the oracle at full size."""
+@pytest.mark.parametrize("N,pde,precision,tol", [(8192, "scalar", "fp64", 1e-12), (8192, "scalar", "fp32", 2e-5),
+                                                   (4096, "scalar", "fp32x2", 1e-12), (4096, "stokes", "fp64", 1e-12),
+                                                   (4096, "stokes", "fp32x2", 1e-12), (8192, "stokes", "fp32", 2e-5)])
+def test_large_grids(N, pde, precision, tol):
+    """The largest grids of each precision (one padded column or row pair per field in shared
+    memory; threads holding several lanes): applications against the oracle at full size."""
     from paper_2210_07403_gb300 import Geometry
 
     M = I.points_for_spacing(2 * np.pi * 0.25, 1.0 / N, 1.0)
@@ -268,6 +269,22 @@ def test_large_grids_global_tables(N, pde, precision, tol):
     q = np.random.default_rng(N).standard_normal(og.ncomp * M)
     y = g.apply(torch.from_numpy(q).cuda(), precision=precision).cpu().numpy()
     assert _rel(y, O.apply(og, q)) < tol
+    g.close()
+
+
+def test_grid_limits_are_refused():
+    """Beyond the shared-memory FFT: the Stokes operator in FP64 at 8192² (three FP64 fields of a
+    column need 442 KB) and float-float at 8192² return IBDL_ERR_UNSUPPORTED; no launch is made."""
+    from paper_2210_07403_gb300 import Geometry, IbdlError
+
+    N = 8192
+    bd = I.circle(I.points_for_spacing(2 * np.pi * 0.25, 1.0 / N, 1.0))
+    for pde, precision in (("stokes", "fp64"), ("scalar", "fp32x2")):
+        g = Geometry(bd.X, bd.n, bd.w, N, pde=pde)
+        q = torch.zeros(g.nd, dtype=torch.float64, device="cuda")
+        with pytest.raises(IbdlError, match="UNSUPPORTED"):
+            g.apply(q, precision=precision)
+        g.close()
 
 
 @pytest.mark.parametrize("case", ["star 512", "cylinder c=0.5", "star 256 restart 64", "circle restart 4"])
