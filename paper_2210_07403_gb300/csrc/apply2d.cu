@@ -2,9 +2,13 @@
 // precision, batched launch tables, the autotuner and the source-term helpers. The kernels are in
 // apply2d_kernels.cuh; each grid size n = 2^L is compiled in its own unit (apply2d_n*.cu) and
 // reached through launch_apply_2d<T, OP, L>.
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <mutex>
+#include <string>
 #include <type_traits>
 #include <utility>
 #include <vector>
@@ -116,6 +120,7 @@ static ColParams<T> col_params(Geometry* g, const int* stop) {
   cp.spec = reinterpret_cast<cplx<T>*>(g->spec);
   cp.tw = static_cast<const cplx<T>*>(Slot2<T>::tw(g));
   cp.stop = stop;
+  cp.err = g->err_dev;
   return cp;
 }
 
@@ -229,6 +234,7 @@ ibdl_status apply_2d_indexed(Geometry* g, int precision, double* V, const int* i
 
 ibdl_status apply_2d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s, const int* stop,
                      int op) {
+  IBDL_TRY(take_device_error(g));  // a failure of an earlier, completed application
   if (precision == IBDL_FP32X2) return apply_t<ff>(g, Q, Y, s, stop, nullptr, nullptr, 0, op);
   return precision == IBDL_FP32 ? apply_t<float>(g, Q, Y, s, stop, nullptr, nullptr, 0, op)
                                 : apply_t<double>(g, Q, Y, s, stop, nullptr, nullptr, 0, op);
@@ -436,6 +442,57 @@ static ibdl_status batch_shape_any(Batch* B, Geometry* g, int pi) {
   return B->dipole == IBDL_DIPOLE_ANALYTIC ? batch_shape<T, OP_SCALAR_AN>(B, g, pi) : batch_shape<T, OP_SCALAR_SD>(B, g, pi);
 }
 
+// The staged FP32 column pass of a batch: per grid size whose problems share one column group
+// (the kernel keeps a lane's twiddles across its units), the stage shape; per problem its tensor
+// map. Sizes with mixed column groups, or whose group does not fit, keep the direct pass.
+template <int OP>
+static void batch_staged_shapes(Batch* B) {
+  constexpr int NIN = Traits<OP>::NIN, NOUT = Traits<OP>::NOUT, NMAX = NIN > NOUT ? NIN : NOUT;
+  for (int L = kMinL2d; L <= kMaxL2d; ++L) {
+    BatchSize& z = B->lv[1][L];
+    z.col_staged = 0;
+    if (!B->col_stage || z.col_count == 0) continue;
+    int C = -1, R = 0;
+    bool same = true;
+    for (int b = 0; b < B->count; ++b) {
+      const Geometry* g = B->geoms[b];
+      if (log2i(g->n) != L) continue;
+      if (C < 0) C = g->cols_per_cta[1];
+      same = same && g->cols_per_cta[1] == C;
+      R = std::max(R, g->rows_per_cta[1]);
+    }
+    ColStageShape sh;
+    // (every R of the size must fit the box: the largest one decides)
+    if (!same || !col_stage_shape(NIN, NMAX, C, R, L, col_stages_env(), &sh)) continue;
+    z.col_staged = 1;
+    z.stages = sh.stages;
+    z.stage_bytes = sh.stage_bytes;
+    z.smem_staged = sh.smem;
+  }
+}
+
+static ibdl_status batch_prepare_staged(Batch* B) {
+  if (B->tmaps) cudaFree(B->tmaps);
+  B->tmaps = nullptr;
+  if (B->pde == IBDL_PDE_STOKES)
+    B->dipole == IBDL_DIPOLE_ANALYTIC ? batch_staged_shapes<OP_STOKES_AN>(B) : batch_staged_shapes<OP_STOKES_SD>(B);
+  else
+    B->dipole == IBDL_DIPOLE_ANALYTIC ? batch_staged_shapes<OP_SCALAR_AN>(B) : batch_staged_shapes<OP_SCALAR_SD>(B);
+  bool any = false;
+  for (int L = kMinL2d; L <= kMaxL2d; ++L) any = any || B->lv[1][L].col_staged;
+  if (!any) return IBDL_OK;
+  std::vector<CUtensorMap> maps(B->count);
+  std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+  for (int b = 0; b < B->count; ++b) {
+    Geometry* g = B->geoms[b];
+    if (!B->lv[1][log2i(g->n)].col_staged) continue;
+    IBDL_TRY(encode_col_map(g->spec, g->n, g->rows_per_cta[1], g->cols_per_cta[1], spec_fields_fp32(g), &maps[b]));
+  }
+  IBDL_CUDA(cudaMalloc((void**)&B->tmaps, sizeof(CUtensorMap) * B->count));
+  IBDL_CUDA(cudaMemcpy(B->tmaps, maps.data(), sizeof(CUtensorMap) * B->count, cudaMemcpyHostToDevice));
+  return IBDL_OK;
+}
+
 template <typename T>
 static ibdl_status batch_prepare_t(Batch* B, const int* kptr /* device &st[b].k, stride in bytes */, size_t kstride) {
   const int pi = Slot2<T>::pi;
@@ -492,6 +549,7 @@ static ibdl_status batch_prepare_t(Batch* B, const int* kptr /* device &st[b].k,
   IBDL_TRY(upload(reinterpret_cast<void**>(&B->col_units[pi]), cu.data(), sizeof(int2) * cu.size()));
   B->nrow_units[pi] = (int)ru.size();
   B->ncol_units[pi] = (int)cu.size();
+  if constexpr (std::is_same<T, float>::value) IBDL_TRY(batch_prepare_staged(B));
   return IBDL_OK;
 }
 
@@ -550,6 +608,7 @@ struct TuneKey {
 };
 struct TuneVal {
   int R, C, floor;
+  int staged;  // FP32: the staged column pass (1) or the direct one (0)
 };
 static std::vector<std::pair<TuneKey, TuneVal>> g_tuned;
 static std::mutex g_tune_mu;
@@ -604,7 +663,7 @@ ibdl_status autotune_2d(Geometry* g, int pi, bool /*fixed_threads*/, cudaStream_
     *med = ms[2];
     return IBDL_OK;
   };
-  TuneVal best{g->rows_per_cta[pi], g->cols_per_cta[pi], g->threads[pi]};
+  TuneVal best{g->rows_per_cta[pi], g->cols_per_cta[pi], g->threads[pi], g->col_stage};
   float best_ms = 1e30f;
   const int floors[3] = {0, 256, 512};
   for (int R = 2; R <= 64 && err == IBDL_OK; R *= 2) {
@@ -619,13 +678,21 @@ ibdl_status autotune_2d(Geometry* g, int pi, bool /*fixed_threads*/, cudaStream_
       }
     }
   }
-  for (int C = 1; C <= 32 && err == IBDL_OK; C *= 2) {
-    if (!col_fits(g, pi, C)) continue;
-    float ms = 0;
-    err = time_shape(best.R, C, best.floor, &ms);
-    if (err == IBDL_OK && ms < best_ms) {
-      best_ms = ms;
-      best.C = C;
+  // the column group, and for FP32 (unless IBDL_COL_STAGED fixes it) the column pass's form:
+  // direct loads or the staged pass
+  const int saved_stage = g->col_stage;
+  for (int staged = 0; staged < 2 && err == IBDL_OK; ++staged) {
+    if (staged && (pi != 1 || g->col_stage_forced)) break;
+    if (pi == 1 && !g->col_stage_forced) g->col_stage = staged;
+    for (int C = 1; C <= 32 && err == IBDL_OK; C *= 2) {
+      if (!col_fits(g, pi, C)) continue;
+      float ms = 0;
+      err = time_shape(best.R, C, best.floor, &ms);
+      if (err == IBDL_OK && ms < best_ms) {
+        best_ms = ms;
+        best.C = C;
+        best.staged = g->col_stage;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -634,6 +701,7 @@ ibdl_status autotune_2d(Geometry* g, int pi, bool /*fixed_threads*/, cudaStream_
   g->rows_per_cta[pi] = best.R;
   g->cols_per_cta[pi] = best.C;
   g->threads[pi] = best.floor;
+  g->col_stage = pi == 1 ? best.staged : saved_stage;
   if (err == IBDL_OK) tuned_store(tune_key(g, pi), best);
   return err;
 }
@@ -660,6 +728,7 @@ void shape_for_target_2d(Geometry* g, int pi, int row_target, int col_target, in
 ibdl_status plan_2d(Geometry* g) {
   const int n = g->n, L = log2i(n);
   const int min_ctas = 2 * 152;
+  int tuned_stage = 0;
   for (int pi = 0; pi < 3; ++pi) {
     const int qt = threads_per_seq_2d(L, pi == 1);
     int R = 2 * pow2_in(256 / qt, 1, n / 4 > 1 ? n / 4 : 1);
@@ -685,6 +754,7 @@ ibdl_status plan_2d(Geometry* g) {
       g->rows_per_cta[pi] = tv.R;
       g->cols_per_cta[pi] = tv.C;
       g->threads[pi] = tv.floor;
+      if (pi == 1) tuned_stage = tv.staged;
     }
   }
   if (const char* e = getenv("IBDL_THREADS")) {
@@ -693,6 +763,67 @@ ibdl_status plan_2d(Geometry* g) {
   }
   if (g->rows_per_cta[0] == 0 && g->rows_per_cta[1] == 0)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT");
+  // the FP32 column pass: IBDL_COL_STAGED if set, else the tuned form of this key (direct untuned)
+  const int env = col_stage_env();
+  g->col_stage_forced = env >= 0;
+  g->col_stage = env >= 0 ? env : tuned_stage;
+  return IBDL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// tensor maps of the staged column pass
+// ------------------------------------------------------------------------------------------
+int col_stage_env() {
+  const char* e = getenv("IBDL_COL_STAGED");
+  if (!e || !*e) return -1;
+  return atoi(e) != 0 ? 1 : 0;
+}
+
+int spec_fields_fp32(const Geometry* g) {
+  return (int)(g->spec_bytes / ((size_t)g->n * (g->n / 2) * sizeof(float2)));
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (the library links no
+// driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+ibdl_status encode_col_map(void* spec, int n, int R, int C, int nf, CUtensorMap* out) {
+  const int nb = n / R;
+  if (R < 2 || n % R || C < 1 || 2 * C * R > 256 || nf < 1 || (reinterpret_cast<uintptr_t>(spec) & 15))
+    return fail(IBDL_ERR_UNSUPPORTED, "staged column pass: unsupported band height or column group");
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled_fn();
+  if (!fn) return fail(IBDL_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[3] = {(cuuint64_t)R * n, (cuuint64_t)nb, (cuuint64_t)nf};
+  const cuuint64_t strides[2] = {(cuuint64_t)R * n * sizeof(float), (cuuint64_t)n * (n / 2) * sizeof(float2)};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * C * R), (cuuint32_t)(nb < 256 ? nb : 256), 1};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  const CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, spec, dims, strides, box, estride,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(IBDL_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return IBDL_OK;
+}
+
+ibdl_status col_stage_map(Geometry* g, int R, int C, const CUtensorMap** out) {
+  if (g->tmap_R != R || g->tmap_C != C) {
+    IBDL_TRY(encode_col_map(g->spec, g->n, R, C, spec_fields_fp32(g), &g->tmap_col));
+    g->tmap_R = R;
+    g->tmap_C = C;
+  }
+  *out = &g->tmap_col;
   return IBDL_OK;
 }
 

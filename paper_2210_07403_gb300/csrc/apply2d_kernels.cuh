@@ -32,6 +32,7 @@
 
 #include "ff.cuh"
 #include "fft8.cuh"
+#include "tma.cuh"
 
 namespace ibdl {
 
@@ -174,6 +175,7 @@ struct ColParams {
   cplx<T>* spec;
   const cplx<T>* tw;
   const int* stop;
+  int* err;  // the staged column pass sets it to 1 when a bounded wait runs out
 };
 
 // Sorted points whose base row lies in the cell rows [r0 − 3, r0 + R) (mod n): at most two
@@ -553,6 +555,25 @@ __device__ __forceinline__ int col_at_s(int f, int j, int s, int k, int R) {
   return col_at<L>(f, j, k, R) + s * (Q * nh);
 }
 
+// Column kernels: the C columns of a thread group are interleaved across consecutive threads
+// (column c = t mod C, lane j0 = t / C for thread t of the group), so a warp holds 32/C lanes of
+// each of C adjacent columns: its accesses to the band-major spectra cover whole 32-byte sectors
+// (C·R adjacent values per band), and each column's exchange buffer starts col_skew_2d elements
+// after the previous one's padded end, which puts the C columns of a warp in different
+// shared-memory banks (each exchange then takes the least number of wavefronts: checked by
+// counting banks per warp for every size, C and R on the CPU).
+__host__ __device__ constexpr int col_skew_2d(int C, int esize) {
+  return C >= 2 ? (esize == 8 ? 16 : 8) / C : 0;
+}
+template <int QT>
+__device__ __forceinline__ void col_lane_2d(int C, int& g, int& c, int& j0) {
+  const int per = C * QT;
+  g = (int)threadIdx.x / per;
+  const int t = (int)threadIdx.x - g * per;
+  c = t & (C - 1);
+  j0 = t >> (__ffs(C) - 1);
+}
+
 template <typename T, int OP, int L, bool PF = true>
 __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, unsigned char* smem_raw) {
   constexpr int NIN = Traits<OP>::NIN;
@@ -560,15 +581,16 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
   constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
   using CF = Cfg2<T, L, NMAX>;
   using F = F8<L, CF::V>;
-  constexpr int n = F::N, nh = n / 2, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q, PN = F::PN;
+  constexpr int n = F::N, nh = n / 2, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q, PN0 = F::PN;
   const int C = p.C, R = p.R;
   const int k0 = unit * C;
-  // thread (group g, column c, lane j0)
-  const int q = threadIdx.x / QT, j0 = threadIdx.x - q * QT;
-  const int g = q / C, c = q - g * C;
+  // thread (group g, column c, lane j0), the group's C columns interleaved across threads
+  int g, c, j0;
+  col_lane_2d<QT>(C, g, c, j0);
   const bool active = g < NGRP;
   const int kx = k0 + c;
   // sequence (field f, column c) at buf + (f·C + c)·PN
+  const int PN = PN0 + col_skew_2d(C, (int)sizeof(cplx<T>));
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   typename CF::TW tw[V];
 #pragma unroll
@@ -864,6 +886,299 @@ __global__ void __launch_bounds__(kMaxThreads2d) k_colpass(ColParams<T> p) {
 }
 
 // ------------------------------------------------------------------------------------------
+// kernel 2, staged form (FP32): persistent CTAs walk the column units of one grid size (of one
+// problem, or of every problem of that size in a batch). Each unit's C columns of all input fields,
+// and its problem's symbol tables, are copied into shared memory by the tensor memory accelerator
+// NS units ahead of their use, so that the loads of the next units overlap the transforms of the
+// current one; the column values then come from shared memory instead of scattered global loads.
+// ------------------------------------------------------------------------------------------
+// A stage holds one unit as the tensor map's boxes land: field f, band b = m/R, column c, row
+// m mod R of the band at complex offset (f·(n/R) + b)·C·R + c·R + (m mod R) = f·n·C + (m/R)·C·R +
+// c·R + (m mod R); then lap1[0 … n) and der1[0 … n) (floats). The tensor map of a problem's FP32
+// half spectra has dimensions (x: R·n floats of a band, y: n/R bands, z: fields) and a box of
+// (2·C·R, min(n/R, 256), 1): one copy per field and 256 bands.
+struct ColStageArgs {
+  const ColParams<float>* P;  // batch: parameter block per problem (NULL: the single problem)
+  const CUtensorMap* maps;    // batch: tensor map per problem, in global memory
+  const int2* units;          // batch: (problem, column unit) of this grid size
+  int nunits;                 // units to walk
+  int stages;                 // NS (2 … 4)
+  int stage_bytes;            // bytes per stage (a multiple of 128)
+  int* err;                   // set to 1 when a stage's copies do not arrive within the wait limit
+};
+
+template <int OP, int L>
+__global__ void __launch_bounds__(kMaxThreads2d)
+    kt_colpass(const __grid_constant__ ColParams<float> p1, const __grid_constant__ CUtensorMap map1,
+               const ColStageArgs A) {
+  using T = float;
+  constexpr int NIN = Traits<OP>::NIN;
+  constexpr int NOUT = Traits<OP>::NOUT;
+  constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
+  using CF = Cfg2<T, L, NMAX>;
+  using F = F8<L, CF::V>;
+  constexpr int n = F::N, nh = n / 2, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q, PN0 = F::PN;
+  // the stages start on a 128-byte boundary (the launch adds 128 bytes of slack for it)
+  extern __shared__ __align__(16) unsigned char smem_stage[];
+  unsigned char* base = smem_stage + ((128u - (smem_addr(smem_stage) & 127u)) & 127u);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base);  // NS barriers in the first 128 bytes
+  unsigned char* stages = base + 128;
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(stages + (size_t)A.stages * A.stage_bytes);
+  const int NS = A.stages;
+  const int cnt = (int)blockIdx.x < A.nunits ? (A.nunits - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  if (cnt == 0) return;  // (the host launches at most one CTA per unit)
+
+  auto unit_of = [&](int i, const ColParams<T>*& q, const CUtensorMap*& m, int& cu) {
+    const int u = (int)blockIdx.x + i * (int)gridDim.x;
+    if (A.P) {
+      const int2 t = A.units[u];
+      q = A.P + t.x;
+      m = A.maps + t.x;
+      cu = t.y;
+    } else {
+      q = &p1;
+      m = &map1;
+      cu = u;
+    }
+  };
+  // thread 0: start the copies of this CTA's unit i into stage s
+  auto issue = [&](int i, int s) {
+    const ColParams<T>* q;
+    const CUtensorMap* m;
+    int cu;
+    unit_of(i, q, m, cu);
+    const int C = q->C, R = q->R, nb = n / R, box1 = nb < 256 ? nb : 256;
+    unsigned char* st = stages + (size_t)s * A.stage_bytes;
+    const uint32_t dbytes = (uint32_t)NIN * C * n * sizeof(cplx<T>);
+    mbar_arrive_expect_tx(&bar[s], dbytes + 2u * n * sizeof(T));
+    if (A.P) tmap_acquire(m);
+    for (int f = 0; f < NIN; ++f)
+      for (int y0 = 0; y0 < nb; y0 += box1)
+        tma_load_3d(st + ((size_t)f * nb + y0) * C * R * sizeof(cplx<T>), m, &bar[s], 2 * cu * C * R, y0, f);
+    bulk_load(st + dbytes, q->lap1, n * sizeof(T), &bar[s]);
+    bulk_load(st + dbytes + n * sizeof(T), q->der1, n * sizeof(T), &bar[s]);
+  };
+
+  // prologue independent of the previous kernel: barriers and twiddles (every problem of one
+  // size has the same twiddle values)
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
+    mbar_init_fence();
+  }
+  typename CF::TW tw[V];
+  {
+    const ColParams<T>* q0;
+    const CUtensorMap* m0;
+    int c0;
+    unit_of(0, q0, m0, c0);
+    // (every unit of a launch has the same column group C, so a lane keeps its twiddles)
+    int gg, cc, jj;
+    col_lane_2d<QT>(q0->C, gg, cc, jj);
+    const cplx<T>* twp = q0->tw;
+#pragma unroll
+    for (int v = 0; v < V; ++v) tw[v].load(twp, jj + v * QT);
+  }
+  __syncthreads();
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NS && i < cnt; ++i) issue(i, i);
+
+  for (int i = 0; i < cnt; ++i) {
+    const int s = i % NS;
+    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((i / NS) & 1));
+    if (__syncthreads_or(!ok)) {
+      // the copies did not arrive: record it, wait (bounded) for the copies still in flight, stop
+      if (threadIdx.x == 0) {
+        if (A.err) atomicExch(A.err, 1);
+        for (int k = i; k < i + NS && k < cnt; ++k) mbar_wait_bounded(&bar[k % NS], (uint32_t)((k / NS) & 1));
+      }
+      return;
+    }
+    const ColParams<T>* q;
+    const CUtensorMap* m;
+    int cu;
+    unit_of(i, q, m, cu);
+    const ColParams<T> qv = *q;
+    const int C = qv.C, R = qv.R, k0 = cu * C;
+    int g, c, j0;
+    col_lane_2d<QT>(C, g, c, j0);
+    const bool active = g < NGRP;
+    const int kx = k0 + c;
+    const int PN = PN0 + col_skew_2d(C, (int)sizeof(cplx<T>));
+    const bool packed = k0 == 0;
+    const bool stopped = qv.stop && *qv.stop;  // uniform over the CTA (one problem per unit)
+    const unsigned char* st = stages + (size_t)s * A.stage_bytes;
+    const cplx<T>* sx = reinterpret_cast<const cplx<T>*>(st);
+    const T* slap = reinterpret_cast<const T*>(st + (size_t)NIN * C * n * sizeof(cplx<T>));
+    const T* sder = slap + n;
+    // staged element (field f, row j + s·Q, column c) = sx[f·n·C + xb(j) + s·Q·C]
+    auto xb = [&](int j) { return (j / R) * C * R + c * R + (j & (R - 1)); };
+    const T lapx = slap[kx], derx = sder[kx], lapn = slap[nh], dern = sder[nh];
+    cplx<T> x[1][V][8];
+    if constexpr (NIN == 1 && NOUT == 1) {
+      cplx<T>* sb = buf + (size_t)c * PN;
+      if (!stopped) {
+        if (active) {
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const int b = xb(j0 + v * QT);
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8) x[0][v][s8] = sx[b + s8 * Q * C];
+          }
+        }
+        f8_fft<T, false, L, V, 1>(x, sb, 0, j0, tw, active);
+        if (packed) {
+          if (active) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+#pragma unroll
+              for (int s8 = 0; s8 < 8; ++s8) sb[ppos_strided<Q>(j0 + v * QT, s8)] = x[0][v][s8];
+          }
+          __syncthreads();
+        }
+        if (active) {
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8) {
+              const cplx<T> in[1] = {x[0][v][s8]};
+              cplx<T> out[1];
+              const int ky = j0 + v * QT + s8 * Q;
+              if (kx == 0) {
+                const cplx<T> pm[1] = {sb[ppos((n - ky) & (n - 1))]};
+                symbol_packed<T, OP>(qv, lapx, derx, lapn, dern, slap[ky], sder[ky], in, pm, out);
+              } else {
+                symbol_point<T, OP>(qv, lapx, derx, slap[ky], sder[ky], in, out);
+              }
+              x[0][v][s8] = out[0];
+            }
+        }
+      }
+      // stage s is read: its next copies may start
+      __syncthreads();
+      if (threadIdx.x == 0 && i + NS < cnt) issue(i + NS, s);
+      if (!stopped) {
+        f8_fft<T, true, L, V, 1>(x, sb, 0, j0, tw, active);
+        if (active) {
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8) qv.spec[col_at_s<L>(0, j0 + v * QT, s8, kx, R)] = x[0][v][s8];
+        }
+      }
+    } else {
+      if (!stopped) {
+        // forward transforms of the NIN input fields, results left in the exchange buffers
+#pragma unroll
+        for (int k = 0; k < (NIN + NGRP - 1) / NGRP; ++k) {
+          const int f = g + k * NGRP;
+          const bool act = active && f < NIN;
+          cplx<T>* sb = buf + ((size_t)f * C + c) * PN;
+          if (act) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              const int b = f * n * C + xb(j0 + v * QT);
+#pragma unroll
+              for (int s8 = 0; s8 < 8; ++s8) x[0][v][s8] = sx[b + s8 * Q * C];
+            }
+          }
+          f8_fft<T, false, L, V, 1>(x, sb, 0, j0, tw, act);
+          if (act) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+#pragma unroll
+              for (int s8 = 0; s8 < 8; ++s8) sb[ppos_strided<Q>(j0 + v * QT, s8)] = x[0][v][s8];
+          }
+        }
+        __syncthreads();
+        // symbol at the points of the lane's positions, split over the groups (point s to group
+        // s mod NGRP), in place; the packed column reads its partners first and writes after a
+        // second barrier
+        if (!packed) {
+          if (active) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+#pragma unroll
+              for (int s8 = 0; s8 < 8; ++s8) {
+                if (s8 % NGRP != g) continue;
+                const int ky = j0 + v * QT + s8 * Q;
+                cplx<T> in[NIN], o[NOUT];
+#pragma unroll
+                for (int f = 0; f < NIN; ++f) in[f] = buf[((size_t)f * C + c) * PN + ppos(ky)];
+                symbol_point<T, OP>(qv, lapx, derx, slap[ky], sder[ky], in, o);
+#pragma unroll
+                for (int f = 0; f < NOUT; ++f) buf[((size_t)f * C + c) * PN + ppos(ky)] = o[f];
+              }
+          }
+        } else {
+          cplx<T> o[V][8][NOUT];
+          if (active) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+#pragma unroll
+              for (int s8 = 0; s8 < 8; ++s8) {
+                if (s8 % NGRP != g) continue;
+                const int ky = j0 + v * QT + s8 * Q;
+                cplx<T> in[NIN];
+#pragma unroll
+                for (int f = 0; f < NIN; ++f) in[f] = buf[((size_t)f * C + c) * PN + ppos(ky)];
+                if (kx == 0) {
+                  cplx<T> pm[NIN];
+#pragma unroll
+                  for (int f = 0; f < NIN; ++f) pm[f] = buf[((size_t)f * C + c) * PN + ppos((n - ky) & (n - 1))];
+                  symbol_packed<T, OP>(qv, lapx, derx, lapn, dern, slap[ky], sder[ky], in, pm, o[v][s8]);
+                } else {
+                  symbol_point<T, OP>(qv, lapx, derx, slap[ky], sder[ky], in, o[v][s8]);
+                }
+              }
+          }
+          __syncthreads();
+          if (active) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+#pragma unroll
+              for (int s8 = 0; s8 < 8; ++s8) {
+                if (s8 % NGRP != g) continue;
+#pragma unroll
+                for (int f = 0; f < NOUT; ++f)
+                  buf[((size_t)f * C + c) * PN + ppos_strided<Q>(j0 + v * QT, s8)] = o[v][s8][f];
+              }
+          }
+        }
+      }
+      // stage s is read (and the symbol's results are written): its next copies may start
+      __syncthreads();
+      if (threadIdx.x == 0 && i + NS < cnt) issue(i + NS, s);
+      if (!stopped) {
+        // inverse transforms of the NOUT output fields, straight to the half spectra
+#pragma unroll
+        for (int k = 0; k < (NOUT + NGRP - 1) / NGRP; ++k) {
+          const int f = g + k * NGRP;
+          const bool act = active && f < NOUT;
+          cplx<T>* sb = buf + ((size_t)f * C + c) * PN;
+          if (act) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+#pragma unroll
+              for (int s8 = 0; s8 < 8; ++s8) x[0][v][s8] = sb[ppos_strided<Q>(j0 + v * QT, s8)];
+          }
+          f8_fft<T, true, L, V, 1>(x, sb, 0, j0, tw, act);
+          if (act) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+#pragma unroll
+              for (int s8 = 0; s8 < 8; ++s8) qv.spec[col_at_s<L>(f, j0 + v * QT, s8, kx, R)] = x[0][v][s8];
+          }
+        }
+      }
+    }
+    // the next unit's first exchange writes follow its own wait barrier, which orders them after
+    // this unit's last reads of the exchange buffers
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // kernel 3: inverse FFT along x, then interpolation (or write the grid)
 // ------------------------------------------------------------------------------------------
 // Z_m = A_m + i B_m (m = 0..n−1) for the row pair (r0 + 2j, r0 + 2j + 1) of field f, rebuilt from
@@ -1101,7 +1416,7 @@ __host__ __device__ constexpr size_t smem_rows_2d(int nf, int R, int L) {
 }
 template <typename T>
 __host__ __device__ constexpr size_t smem_cols_2d(int nf, int C, int L) {
-  return (size_t)nf * C * padded_seq_2d(L) * 2 * sizeof(T);
+  return (size_t)nf * C * (padded_seq_2d(L) + col_skew_2d(C, 2 * sizeof(T))) * 2 * sizeof(T);
 }
 
 // Launch of one application's three kernels for a compile-time size (defined in the per-size

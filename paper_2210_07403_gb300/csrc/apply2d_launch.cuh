@@ -7,8 +7,10 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdlib>
+#include <mutex>
 #include <type_traits>
 #include <utility>
+#include <vector>
 
 #include "apply2d_kernels.cuh"
 
@@ -61,6 +63,107 @@ inline cudaError_t opt_in_smem(K kernel, std::atomic<unsigned long long>& done) 
   return e;
 }
 
+// Persistent launches: as many CTAs of `kernel` as fit on the device at once (at most `units`),
+// from an occupancy query cached per kernel, device, thread count and shared memory size.
+template <typename K>
+inline int persistent_grid(K kernel, int threads, size_t smem, int units) {
+  struct Entry {
+    int dev, threads;
+    size_t smem;
+    int blocks;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  int blocks = -1;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& e : cache)
+      if (e.dev == dev && e.threads == threads && e.smem == smem) blocks = e.blocks;
+  }
+  if (blocks < 0) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) per_sm = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+    blocks = std::max(per_sm, 1) * std::max(sms, 1);
+    std::lock_guard<std::mutex> lock(mu);
+    cache.push_back({dev, threads, smem, blocks});
+  }
+  return std::max(1, std::min(units, blocks));
+}
+
+// Shared memory of the staged column pass: 128 bytes of alignment slack, 128 bytes of barriers,
+// NS stages of one unit (NIN fields of C columns, then the two symbol tables; a multiple of 128
+// bytes) and the exchange buffers (NMAX fields of C skewed columns). Up to `want` stages (at
+// least 2); false if two do not fit or the box would be wider than 256 floats.
+struct ColStageShape {
+  int stages, stage_bytes;
+  size_t smem;
+};
+inline bool col_stage_shape(int nin, int nmax, int C, int R, int L, int want, ColStageShape* sh) {
+  const size_t n = size_t(1) << L;
+  // the box's inner extent 2·C·R floats is at most 256 elements
+  if (C < 1 || (C & (C - 1)) || R < 2 || 2 * C * R > 256) return false;
+  size_t sb = (size_t)nin * C * n * sizeof(float2) + 2 * n * sizeof(float);
+  sb = (sb + 127) & ~size_t(127);
+  const size_t xb = (size_t)nmax * C * (padded_seq_2d(L) + col_skew_2d(C, (int)sizeof(float2))) * sizeof(float2);
+  for (int ns = std::max(2, std::min(want, 4)); ns >= 2; --ns) {
+    const size_t tot = 256 + ns * sb + xb;
+    if (tot <= kSmemLimit2d) {
+      sh->stages = ns;
+      sh->stage_bytes = (int)sb;
+      sh->smem = tot;
+      return true;
+    }
+  }
+  return false;
+}
+// IBDL_COL_STAGES: stages of the staged column pass (2 … 4, default 3)
+inline int col_stages_env() {
+  static int v = 0;
+  if (v == 0) {
+    const char* e = getenv("IBDL_COL_STAGES");
+    int k = e ? atoi(e) : 3;
+    v = k < 2 ? 2 : (k > 4 ? 4 : k);
+  }
+  return v;
+}
+
+// The staged FP32 column pass of one application: persistent CTAs over the (n/2)/C units.
+template <int OP, int L>
+ibdl_status launch_col_staged(Geometry* g, const ColParams<float>& cp, cudaStream_t s, bool pdl) {
+  constexpr int NIN = Traits<OP>::NIN, NOUT = Traits<OP>::NOUT, NMAX = NIN > NOUT ? NIN : NOUT;
+  constexpr int n = 1 << L;
+  const CUtensorMap* map = nullptr;
+  IBDL_TRY(col_stage_map(g, cp.R, cp.C, &map));
+  ColStageShape sh;
+  if (!col_stage_shape(NIN, NMAX, cp.C, cp.R, L, col_stages_env(), &sh))
+    return fail(IBDL_ERR_UNSUPPORTED, "staged column pass: the column group does not fit shared memory");
+  static std::atomic<unsigned long long> d{0};
+  IBDL_CUDA(opt_in_smem(kt_colpass<OP, L>, d));
+  const int threads = field_groups_2d(NMAX, L, true) * cp.C * threads_per_seq_2d(L, true);
+  const int units = (n / 2) / cp.C;
+  const int grid = persistent_grid(kt_colpass<OP, L>, threads, sh.smem, units);
+  ColStageArgs a;
+  a.P = nullptr;
+  a.maps = nullptr;
+  a.units = nullptr;
+  a.nunits = units;
+  a.stages = sh.stages;
+  a.stage_bytes = sh.stage_bytes;
+  a.err = cp.err;
+  IBDL_CUDA(launch_k(kt_colpass<OP, L>, grid, threads, sh.smem, s, pdl, cp, *map, a));
+  return IBDL_OK;
+}
+
+// whether a geometry's FP32 column pass runs staged: its mode is on and the unit fits
+inline bool col_staged_for(const Geometry* g, const ColParams<float>& cp, int nin, int nmax, int L) {
+  if (g->col_stage != 1) return false;
+  ColStageShape sh;
+  return col_stage_shape(nin, nmax, cp.C, cp.R, L, 2, &sh);
+}
+
 template <typename T, int OP, int L>
 ibdl_status set_attrs_2d() {
   static std::atomic<unsigned long long> d1{0}, d2{0}, d3{0}, d4{0};
@@ -81,7 +184,13 @@ ibdl_status launch_apply_2d(Geometry* g, const RowParams<T>& rp, const ColParams
   if (g->timing) timing_mark(g, s, -1);
   IBDL_CUDA(launch_k(k_spread_rowfft<T, OP, L>, n / lc.R, lc.threads_row, lc.smem_row, s, lc.pdl, rp));
   if (g->timing) timing_mark(g, s, st0);
-  IBDL_CUDA(launch_k(k_colpass<T, OP, L>, (n / 2) / lc.C, lc.threads_col, lc.smem_col, s, lc.pdl, cp));
+  bool staged = false;
+  if constexpr (std::is_same<T, float>::value) {
+    constexpr int NIN = Traits<OP>::NIN, NOUT = Traits<OP>::NOUT;
+    staged = col_staged_for(g, cp, NIN, NIN > NOUT ? NIN : NOUT, L);
+    if (staged) IBDL_TRY((launch_col_staged<OP, L>(g, cp, s, lc.pdl)));
+  }
+  if (!staged) IBDL_CUDA(launch_k(k_colpass<T, OP, L>, (n / 2) / lc.C, lc.threads_col, lc.smem_col, s, lc.pdl, cp));
   if (g->timing) timing_mark(g, s, st0 + 1);
   if constexpr (std::is_same<T, ff>::value) {
     // float-float serves boundary applications only (the refinement residual)
@@ -129,6 +238,27 @@ ibdl_status batch_stage_2d(Batch* B, int stage, int mode, const double* in_base,
         const int grid = std::max(1, std::min(z.col_count, std::max(per_sm, 1) * sms));
         IBDL_CUDA(launch_k(kbp_colpass<T, OP, L>, grid, z.threads_col, z.smem_col, s, pdl, cp,
                            (const int2*)B->col_units[pi] + z.col_start, z.col_count));
+        B->launches += 1;
+        return IBDL_OK;
+      }
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      if (z.col_staged) {
+        // the staged pass: persistent CTAs over the size's units, each problem's tensor map
+        static std::atomic<unsigned long long> d{0};
+        IBDL_CUDA(opt_in_smem(kt_colpass<OP, L>, d));
+        ColStageArgs a;
+        a.P = cp;
+        a.maps = B->tmaps;
+        a.units = (const int2*)B->col_units[pi] + z.col_start;
+        a.nunits = z.col_count;
+        a.stages = z.stages;
+        a.stage_bytes = z.stage_bytes;
+        a.err = B->geoms[0]->err_dev;
+        ColParams<float> none = {};
+        CUtensorMap nomap = {};
+        const int grid = persistent_grid(kt_colpass<OP, L>, z.threads_col, z.smem_staged, z.col_count);
+        IBDL_CUDA(launch_k(kt_colpass<OP, L>, grid, z.threads_col, z.smem_staged, s, pdl, none, nomap, a));
         B->launches += 1;
         return IBDL_OK;
       }

@@ -18,6 +18,7 @@
 #include <type_traits>
 
 #include <algorithm>
+#include <atomic>
 
 #include "fft.cuh"
 
@@ -515,11 +516,16 @@ static ibdl_status set_attrs3_all() {
 }
 
 ibdl_status plan_3d(Geometry* g) {
-  static bool attrs = false;
-  if (!attrs) {
+  // the shared-memory opt-in belongs to each function on the current device: one bit per device
+  // records it (setting it twice is harmless, so threads racing on a first call need no lock)
+  static std::atomic<unsigned long long> attrs{0};
+  int dev = 0;
+  IBDL_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (!bit || !(attrs.load(std::memory_order_acquire) & bit)) {
     IBDL_TRY(set_attrs3_all<double>());
     IBDL_TRY(set_attrs3_all<float>());
-    attrs = true;
+    if (bit) attrs.fetch_or(bit, std::memory_order_acq_rel);
   }
   // Work units sized by FFT volume per CTA: R y-rows per row band, C kx columns per y-pass CTA,
   // Cz per z-pass CTA (which holds 2·Cz columns: ky and −ky).

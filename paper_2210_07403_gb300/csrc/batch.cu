@@ -34,7 +34,8 @@ static void free_batch(Batch* B) {
     if (B->col_units[p]) cudaFree(B->col_units[p]);
     if (p < 2 && B->exec[p]) cudaGraphExecDestroy(B->exec[p]);
   }
-  void* dev[] = {B->V, B->st, B->ctl, B->vec, B->target, B->active, B->d_off, B->d_voff, B->d_nd, B->d_slice};
+  void* dev[] = {B->V,      B->st,    B->ctl,  B->vec,     B->target, B->active,
+                 B->d_off,  B->d_voff, B->d_nd, B->d_slice, B->tmaps};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (B->host_st) cudaFreeHost(B->host_st);
@@ -83,6 +84,12 @@ ibdl_status ibdl_create_batch(const ibdl_geometry_desc* descs, int count, void* 
   {
     const char* e = getenv("IBDL_BATCH_PERSISTENT");
     B->persistent = (e && atoi(e) != 0) ? 1 : 0;
+  }
+  {
+    // the FP32 column pass: IBDL_COL_STAGED if set, else direct until the batch autotuner chooses
+    const int e = col_stage_env();
+    B->col_stage_forced = e >= 0;
+    B->col_stage = e > 0 ? 1 : 0;
   }
   B->off = new int64_t[count + 1];
   B->voff = new int64_t[count];
@@ -176,6 +183,28 @@ ibdl_status ibdl_batch_autotune(ibdl_batch* batch, int precision_mask, void* str
     }
     if (st == IBDL_OK)
       for (int i = 0; i < B->count; ++i) shape_for_target_2d(B->geoms[i], pi, best_t, best_c, best_f);
+    if (st == IBDL_OK && pi == 1 && !B->col_stage_forced) {
+      // FP32: the direct or the staged column pass at the chosen shapes, whichever is faster
+      float t[2] = {1e30f, 1e30f};
+      for (int mode = 0; mode < 2 && st == IBDL_OK; ++mode) {
+        B->col_stage = mode;
+        st = batch_prepare_2d(B);
+        if (st != IBDL_OK) break;
+        float ms[3];
+        st = batch_apply_2d(B, IBDL_FP32, 0, buf, buf + B->total, s);
+        for (int k = 0; k < 3 && st == IBDL_OK; ++k) {
+          cudaEventRecord(e0, s);
+          st = batch_apply_2d(B, IBDL_FP32, 0, buf, buf + B->total, s);
+          cudaEventRecord(e1, s);
+          if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(IBDL_ERR_CUDA, "batch autotune: event synchronize");
+          cudaEventElapsedTime(&ms[k], e0, e1);
+        }
+        if (st != IBDL_OK) break;
+        std::sort(ms, ms + 3);
+        t[mode] = ms[1];
+      }
+      B->col_stage = t[1] < t[0] ? 1 : 0;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

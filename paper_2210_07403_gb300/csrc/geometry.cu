@@ -222,6 +222,7 @@ static void free_geometry(Geometry* g) {
   for (int i = 0; i < 4; ++i)
     if (g->cycle_exec[i]) cudaGraphExecDestroy(g->cycle_exec[i]);
   if (g->host_status) cudaFreeHost(g->host_status);
+  if (g->err_host) cudaFreeHost(g->err_host);
   if (g->ev) cudaEventDestroy(g->ev);
   if (g->ev_pool) {
     for (int i = 0; i < g->ev_cap; ++i) cudaEventDestroy(g->ev_pool[i]);
@@ -448,6 +449,10 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
     GCUDA(cudaGetLastError());
     GCUDA(cudaStreamSynchronize(s));
     GCUDA(cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming));
+    // the flag of the staged column pass's bounded waits, written by the device only on failure
+    GCUDA(cudaHostAlloc((void**)&g->err_host, sizeof(int), cudaHostAllocMapped));
+    *g->err_host = 0;
+    GCUDA(cudaHostGetDevicePointer((void**)&g->err_dev, g->err_host, 0));
     GTRY(dim == 2 ? plan_2d(g) : plan_3d(g));
   }
   g->X64 = dX;  // kept: the near-boundary interpolation decides on the caller's coordinates

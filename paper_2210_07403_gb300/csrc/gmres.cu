@@ -777,7 +777,8 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
   }
   inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = inf;
-  return ret;
+  const ibdl_status dev = take_device_error(g);
+  return dev != IBDL_OK ? dev : ret;
 }
 
 }  // namespace ibdl
@@ -1108,7 +1109,8 @@ ibdl_status batch_solve_impl(Batch* B, const double* Ub, double* Q, const ibdl_s
       inf[b].seconds = secs;
       infos[b] = inf[b];
     }
-  return ret;
+  const ibdl_status dev = take_device_error(B->geoms[0]);  // the batch's staged passes report here
+  return dev != IBDL_OK ? dev : ret;
 }
 
 }  // namespace ibdl

@@ -1,6 +1,7 @@
 // Internal declarations of the IBDL CUDA library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,8 +34,10 @@ ibdl_status cuda_fail(cudaError_t e, const char* what);
 // ------------------------------------------------------------------------------------------
 // complex arithmetic
 // ------------------------------------------------------------------------------------------
+// aligned to its own size, so that a complex FP32 value moves as one 64-bit access and a complex
+// FP64 or float-float value as one 128-bit access (every array of them starts on such a boundary)
 template <typename T>
-struct cplx {
+struct alignas(2 * sizeof(T)) cplx {
   T x, y;
 };
 
@@ -141,6 +144,16 @@ struct Geometry {
   cudaGraphExec_t cycle_exec[4];
   int cycle_m[4];
 
+  // staged column pass of FP32 applications (2-D): on (1) or off (0), whether IBDL_COL_STAGED
+  // fixed it (else the autotuner chooses), the tensor map of the FP32 half spectra for the
+  // column group it was encoded for, and the flag its bounded waits set (pinned host memory
+  // mapped into the device, so the host reads it without a copy)
+  int col_stage, col_stage_forced;
+  int tmap_R, tmap_C;
+  CUtensorMap tmap_col;
+  int* err_host;
+  int* err_dev;
+
   // counters and optional stage timing (events around every kernel)
   int64_t launches;
   int timing;
@@ -154,6 +167,9 @@ struct BatchSize {
   int row_start, row_count, col_start, col_count;
   int threads_row, threads_col, threads_gather;
   size_t smem_row, smem_col, smem_gather;
+  // FP32: the staged column pass (its units all have one column group), stages and stage bytes
+  int col_staged, stages, stage_bytes;
+  size_t smem_staged;
 };
 
 // A batch of independent 2-D problems (same PDE and dipole form; any grid size, point count,
@@ -177,6 +193,9 @@ struct Batch {
   BatchSize lv[3][14];
   int max_log2n;         // log2 of the largest grid size in the batch
   int persistent;        // 1: persistent column-pass CTAs for one-field operators (IBDL_BATCH_PERSISTENT=1)
+  int col_stage;         // FP32 column pass: 1 staged (tensor-memory-accelerator copies), 0 direct loads
+  int col_stage_forced;  // IBDL_COL_STAGED fixed it (else the batch autotuner chooses)
+  CUtensorMap* tmaps;    // device [count]: each problem's FP32 half-spectrum tensor map (staged pass)
   // batched GMRES
   int m;                 // restart length the workspace was sized for (0: none yet)
   int64_t* voff;         // host [count]: offset of problem b's basis in V
@@ -198,6 +217,15 @@ struct Batch {
 };
 
 ibdl_status batch_prepare_2d(Batch* B);
+// tensor map of FP32 half spectra [nf][n][n/2] in band-major order for the staged column pass:
+// dimensions (R·n floats of a band, n/R bands, nf fields), box (2·C·R, min(n/R, 256), 1)
+ibdl_status encode_col_map(void* spec, int n, int R, int C, int nf, CUtensorMap* out);
+// the geometry's map for (R, C), re-encoded when either changed
+ibdl_status col_stage_map(Geometry* g, int R, int C, const CUtensorMap** out);
+// fields of FP32 half spectra a geometry's workspace holds
+int spec_fields_fp32(const Geometry* g);
+// IBDL_COL_STAGED: unset −1 (not fixed), "0" off, otherwise on
+int col_stage_env();
 ibdl_status autotune_2d(Geometry* g, int pi, bool fixed_threads, cudaStream_t s, const double* Q, double* Y);
 // launch shape from FFT volumes per CTA: rows per band from row_target, kx columns from col_target;
 // floor: the row kernels' least thread count
@@ -263,6 +291,16 @@ ibdl_status apply_2d_indexed(Geometry* g, int precision, double* V, const int* i
                              const int* stop, int op = OPK_A);
 ibdl_status apply_3d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
                              const int* stop, int op = OPK_A);
+
+// IBDL_ERR_TIMEOUT (and the flag cleared) if a staged column pass of this geometry gave up waiting
+// for its copies since the last check; the flag lives in mapped host memory, so no copy is needed
+inline ibdl_status take_device_error(Geometry* g) {
+  if (g->err_host && *reinterpret_cast<volatile int*>(g->err_host)) {
+    *reinterpret_cast<volatile int*>(g->err_host) = 0;
+    return fail(IBDL_ERR_TIMEOUT, "a staged column pass gave up waiting for its shared-memory copies");
+  }
+  return IBDL_OK;
+}
 
 // length of a boundary vector of the (possibly augmented) system: c·M density values, then ū
 inline int geom_nd(const Geometry* g) { return (int)(g->ncomp * g->M) + g->naug; }

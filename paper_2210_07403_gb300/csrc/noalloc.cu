@@ -167,6 +167,7 @@ extern "C" ibdl_status ibdl_apply_noalloc(const ibdl_geometry_desc* d, int preci
                                           std::to_string(kNoAllocScratchBytes) + " (8 MiB): use a smaller grid or fewer points, or ibdl_apply");
 
   IBDL_TRY(plan_2d(&g));
+  g.col_stage = 0;  // the view has no error flag for the staged column pass: the direct pass runs
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   IBDL_TRY(fill_geometry_tables(&g, d->X, d->normals, d->weights, key, count, cursor, s));
   return apply_2d(&g, precision, Q, Y, s, nullptr);
