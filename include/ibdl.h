@@ -44,7 +44,16 @@
  *   IBDL_PLAN3_R, IBDL_PLAN3_C, IBDL_PLAN3_CZ   the same for the 3-D kernels;
  *   IBDL_BATCH_PERSISTENT=1  batched column passes of the scalar operator on persistent CTAs
  *                            that load the next unit before transforming the current one,
- *                            instead of one CTA per unit (read when a batch is created).
+ *                            instead of one CTA per unit (read when a batch is created);
+ *   IBDL_COL_STAGED=0|1      FP32 column pass with direct loads (0) or staged in shared memory by
+ *                            tensor-memory-accelerator copies (1), read when a geometry or batch
+ *                            is created; unset, the direct pass runs until ibdl_autotune /
+ *                            ibdl_batch_autotune choose the faster one;
+ *   IBDL_COL_STAGES=2..4     stages (units copied ahead) of the staged column pass (3).
+ *
+ * IBDL_ERR_TIMEOUT: the staged column pass bounds each wait for its copies (1 s); a wait that
+ * runs out stops that CTA and sets a flag, reported by the next solve or application on the
+ * geometry (a batch: by its next solve).
  */
 #ifndef IBDL_H
 #define IBDL_H

@@ -280,7 +280,13 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   const int g = q / half, rp = q - g * half;
   const bool active = g < NGRP;
   // prologue independent of the previous kernel, then wait for it (programmatic launch)
-  for (int i = threadIdx.x; i < NIN * half * F::PN * 2; i += blockDim.x) acc[i] = PT(0);
+  {
+    // clear the accumulation buffer (NIN·half padded sequences, a multiple of 16 bytes) with
+    // 16-byte stores
+    uint4* z = reinterpret_cast<uint4*>(buf);
+    const int nz = (int)((size_t)NIN * half * F::PN * sizeof(cplx<T>) / 16);
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
   typename CF::TW tw[V];
   if constexpr (PF) {
 #pragma unroll
@@ -342,8 +348,14 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   }
 
   // one thread per (point, stencil node): 16 work items per point whose stencil meets the band
+  // (the next item's table values are loaded before this item's additions, so a band with more
+  // items than threads waits for the tables once, not once per round)
+  SpreadItem<PT> cur = it0;
   for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
-    const SpreadItem<PT> it = t == (int)threadIdx.x ? it0 : spread_item(p, pr, t, r0);
+    SpreadItem<PT> nxt = {};
+    if (t + (int)blockDim.x < nitems) nxt = spread_item(p, pr, t + blockDim.x, r0);
+    const SpreadItem<PT> it = cur;
+    cur = nxt;
     const int lr = it.lr;
     if (lr >= R) continue;
     const int i = it.i;
@@ -557,13 +569,18 @@ __device__ __forceinline__ int col_at_s(int f, int j, int s, int k, int R) {
 
 // Column kernels: the C columns of a thread group are interleaved across consecutive threads
 // (column c = t mod C, lane j0 = t / C for thread t of the group), so a warp holds 32/C lanes of
-// each of C adjacent columns: its accesses to the band-major spectra cover whole 32-byte sectors
-// (C·R adjacent values per band), and each column's exchange buffer starts col_skew_2d elements
-// after the previous one's padded end, which puts the C columns of a warp in different
-// shared-memory banks (each exchange then takes the least number of wavefronts: checked by
-// counting banks per warp for every size, C and R on the CPU).
-__host__ __device__ constexpr int col_skew_2d(int C, int esize) {
-  return C >= 2 ? (esize == 8 ? 16 : 8) / C : 0;
+// each of C adjacent columns (one lane of each of 32 columns when C ≥ 32): its accesses to the
+// band-major spectra cover whole 32-byte sectors (C·R adjacent values per band). Each column's
+// exchange buffer holds the padded sequence and is rounded up to a stride ≡ max(1, w/C) (mod w)
+// elements, w = 16 for 8-byte and 8 for 16-byte elements, which puts the C columns of a warp in
+// different shared-memory banks: every exchange then takes the least number of wavefronts the
+// warp's bytes need (checked by counting banks per warp for every size, C ≤ 32 and R ≤ 8 on the
+// CPU, against a search over all strides).
+__host__ __device__ constexpr int col_stride_2d(int L, int C, int esize) {
+  const int pn = (1 << L) + (1 << L) / 8;
+  const int w = esize == 8 ? 16 : 8;
+  const int t = (w / C > 1 ? w / C : 1) % w;
+  return C < 2 ? pn : pn + (((t - pn) % w) + w) % w;
 }
 template <int QT>
 __device__ __forceinline__ void col_lane_2d(int C, int& g, int& c, int& j0) {
@@ -581,7 +598,7 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
   constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
   using CF = Cfg2<T, L, NMAX>;
   using F = F8<L, CF::V>;
-  constexpr int n = F::N, nh = n / 2, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q, PN0 = F::PN;
+  constexpr int n = F::N, nh = n / 2, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q;
   const int C = p.C, R = p.R;
   const int k0 = unit * C;
   // thread (group g, column c, lane j0), the group's C columns interleaved across threads
@@ -590,7 +607,7 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
   const bool active = g < NGRP;
   const int kx = k0 + c;
   // sequence (field f, column c) at buf + (f·C + c)·PN
-  const int PN = PN0 + col_skew_2d(C, (int)sizeof(cplx<T>));
+  const int PN = col_stride_2d(L, C, (int)sizeof(cplx<T>));
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   typename CF::TW tw[V];
 #pragma unroll
@@ -917,7 +934,7 @@ __global__ void __launch_bounds__(kMaxThreads2d)
   constexpr int NMAX = NIN > NOUT ? NIN : NOUT;
   using CF = Cfg2<T, L, NMAX>;
   using F = F8<L, CF::V>;
-  constexpr int n = F::N, nh = n / 2, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q, PN0 = F::PN;
+  constexpr int n = F::N, nh = n / 2, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q;
   // the stages start on a 128-byte boundary (the launch adds 128 bytes of slack for it)
   extern __shared__ __align__(16) unsigned char smem_stage[];
   unsigned char* base = smem_stage + ((128u - (smem_addr(smem_stage) & 127u)) & 127u);
@@ -1005,7 +1022,7 @@ __global__ void __launch_bounds__(kMaxThreads2d)
     col_lane_2d<QT>(C, g, c, j0);
     const bool active = g < NGRP;
     const int kx = k0 + c;
-    const int PN = PN0 + col_skew_2d(C, (int)sizeof(cplx<T>));
+    const int PN = col_stride_2d(L, C, (int)sizeof(cplx<T>));
     const bool packed = k0 == 0;
     const bool stopped = qv.stop && *qv.stop;  // uniform over the CTA (one problem per unit)
     const unsigned char* st = stages + (size_t)s * A.stage_bytes;
@@ -1298,8 +1315,14 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   }
 
   // one thread per (point, stencil row in the band): the row's partial sum is added to Y
+  // (the next item's table values are loaded before this item's sums, as in the spread)
+  GatherItem<PT> cur = it0;
+  if (!PF && (int)threadIdx.x < nitems) cur = gather_item(p, pr, threadIdx.x, r0);
   for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
-    const GatherItem<PT> it = (PF && t == (int)threadIdx.x) ? it0 : gather_item(p, pr, t, r0);
+    GatherItem<PT> nxt = {};
+    if (t + (int)blockDim.x < nitems) nxt = gather_item(p, pr, t + blockDim.x, r0);
+    const GatherItem<PT> it = cur;
+    cur = nxt;
     const int lr = it.lr;
     if (lr >= R) continue;
     const int i = it.i;
@@ -1416,7 +1439,7 @@ __host__ __device__ constexpr size_t smem_rows_2d(int nf, int R, int L) {
 }
 template <typename T>
 __host__ __device__ constexpr size_t smem_cols_2d(int nf, int C, int L) {
-  return (size_t)nf * C * (padded_seq_2d(L) + col_skew_2d(C, 2 * sizeof(T))) * 2 * sizeof(T);
+  return (size_t)nf * C * col_stride_2d(L, C, 2 * sizeof(T)) * 2 * sizeof(T);
 }
 
 // Launch of one application's three kernels for a compile-time size (defined in the per-size

@@ -107,7 +107,7 @@ inline bool col_stage_shape(int nin, int nmax, int C, int R, int L, int want, Co
   if (C < 1 || (C & (C - 1)) || R < 2 || 2 * C * R > 256) return false;
   size_t sb = (size_t)nin * C * n * sizeof(float2) + 2 * n * sizeof(float);
   sb = (sb + 127) & ~size_t(127);
-  const size_t xb = (size_t)nmax * C * (padded_seq_2d(L) + col_skew_2d(C, (int)sizeof(float2))) * sizeof(float2);
+  const size_t xb = (size_t)nmax * C * col_stride_2d(L, C, (int)sizeof(float2)) * sizeof(float2);
   for (int ns = std::max(2, std::min(want, 4)); ns >= 2; --ns) {
     const size_t tot = 256 + ns * sb + xb;
     if (tot <= kSmemLimit2d) {
