@@ -232,7 +232,7 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------
 
 # the sources of the 2-D kernels: a traffic record is valid for the kernels built from these
-KERNEL_SOURCES = ("apply2d_kernels.cuh", "fft8.cuh", "fft.cuh", "ff.cuh")
+KERNEL_SOURCES = ("apply2d_kernels.cuh", "fft8.cuh", "fft.cuh", "ff.cuh", "tma.cuh", "ibdl_internal.cuh")
 
 
 def _stored_traffic(kernel: str):
