@@ -378,6 +378,9 @@ def extra_workloads(dev, flush, stream, sols, K=5):
     out["stokes_star_probes_1024"] = differentiation_workload(dev, flush, stream, K)
     out["cylinder_array_drag_1024"] = cylinder_drag_workload(dev, flush, stream, sols=sols)
     out["cylinder_array_drag_2048"] = cylinder_drag_workload(dev, flush, stream, N=2048)
+    # the paper's own resolution: FP64 applications one field per launch (three FP64 fields of a
+    # column do not fit shared memory together at 8192²)
+    out["cylinder_array_drag_8192"] = cylinder_drag_workload(dev, flush, stream, K=1, N=8192, cs=(0.05, 0.2, 0.4))
     out["postprocess"] = postprocess_workload(dev, flush, stream)
     out["size_sweep"] = size_sweep_workload(dev, flush, stream, sols=sols)
     return out
@@ -847,6 +850,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "cufft_transforms_only": cufft,
         "wall_s_timed_region": round(t_wall, 3),
         "gmres_driver": "host (one launch per kernel)" if args.host_driven else "CUDA graph per cycle",
+        "launch_plan": {prec: geom.launch_plan(prec) for prec in ("fp32", "fp32x2", "fp64")},
         "cpu_baseline": cpu,
     }
     geom.close()

@@ -349,6 +349,15 @@ ibdl_status ibdl_autotune(ibdl_geometry* geom, int precision_mask, void* stream)
 /* Geometry facts: number of density components c and points M. */
 ibdl_status ibdl_geometry_sizes(const ibdl_geometry* geom, int* ncomp, int64_t* n_points);
 
+/* The 2-D launch plan of one grid arithmetic (IBDL_FP64, IBDL_FP32 or IBDL_FP32X2; the paper has no
+ * counterpart: this reports the library's own choices, e.g. after ibdl_autotune): rows per row
+ * band, kx columns per column group, least threads per CTA of the row kernels, whether FP32
+ * column passes are staged by tensor-memory-accelerator copies (0/1) and whether applications
+ * run one field per launch (0/1). Any output pointer may be NULL. IBDL_ERR_UNSUPPORTED for 3-D
+ * geometries. No device work. */
+ibdl_status ibdl_launch_plan(const ibdl_geometry* geom, int precision, int* rows, int* cols, int* threads,
+                             int* staged, int* split);
+
 /* ---- batches of independent 2-D problems -------------------------------------------------
  * A batch holds `count` problems with the same pde and dipole form and any grid size, point
  * count, λ, delta and symbol. Boundary vectors of all problems are concatenated in problem order

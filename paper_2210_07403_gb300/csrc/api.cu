@@ -327,6 +327,23 @@ ibdl_status ibdl_geometry_sizes(const ibdl_geometry* geom, int* ncomp, int64_t* 
   return IBDL_OK;
 }
 
+ibdl_status ibdl_launch_plan(const ibdl_geometry* geom, int precision, int* rows, int* cols, int* threads,
+                             int* staged, int* split) {
+  set_error("");
+  if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");
+  if (precision != IBDL_FP64 && precision != IBDL_FP32 && precision != IBDL_FP32X2)
+    return fail(IBDL_ERR_INVALID_ARG, "precision must be IBDL_FP64, IBDL_FP32 or IBDL_FP32X2");
+  const Geometry* g = geom->g;
+  if (g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "launch plans are reported for 2-D geometries");
+  const int pi = prec_slot(precision);
+  if (rows) *rows = g->rows_per_cta[pi];
+  if (cols) *cols = g->cols_per_cta[pi];
+  if (threads) *threads = g->threads[pi];
+  if (staged) *staged = pi == 1 ? g->col_stage : 0;
+  if (split) *split = g->split[pi];
+  return IBDL_OK;
+}
+
 ibdl_status ibdl_autotune(ibdl_geometry* geom, int precision_mask, void* stream) {
   set_error("");
   if (!geom || !geom->g) return fail(IBDL_ERR_INVALID_ARG, "geometry is NULL");

@@ -95,6 +95,7 @@ static RowParams<T> row_params(Geometry* g, const double* in, double* out, const
   rp.vstride = 0;
   rp.io_off = 0;
   rp.trans = 0;
+  rp.fsel = 0;
   rp.grid_in = nullptr;
   rp.jump = g->bc == IBDL_BC_NEUMANN ? -0.5 : 0.5;
   rp.aug = g->naug > 0;
@@ -137,8 +138,12 @@ static int col_threads(int nf, int C, int L, bool f32) {
 
 template <typename T, int OP>
 static ibdl_status launch_shape(const Geometry* g, int R, int C, int floor, Launch2D* lc) {
-  constexpr int NIN = Traits<OP>::NIN, NOUT = Traits<OP>::NOUT, NMAX = NIN > NOUT ? NIN : NOUT;
+  // one field per launch: every kernel holds one field
+  const bool split = g->split[Slot2<T>::pi] != 0;
+  const int NIN = split ? 1 : Traits<OP>::NIN, NOUT = split ? 1 : Traits<OP>::NOUT;
+  const int NMAX = NIN > NOUT ? NIN : NOUT;
   const int L = log2i(g->n);
+  lc->split = split;
   if (R < 2 || C < 1)
     return fail(IBDL_ERR_UNSUPPORTED, "grid too large for the shared-memory FFT at this precision");
   lc->R = R;
@@ -386,15 +391,17 @@ static ibdl_status batch_stage_for_size(int lg, Batch* B, int stage, int mode, c
   }
 }
 
-// One batched application: for each stage, one launch per grid size present (a size's kernels
-// wait, by programmatic launch, for the launch before them; only the first launch of the
-// application is an ordinary stream-ordered launch).
+// One batched application: for each grid size present, its three stages, one launch each (a
+// launch waits, by programmatic launch, for the launch before it; only the first launch of the
+// application is an ordinary stream-ordered launch). The sizes are independent, so they run one
+// after another: a size's spectra are then read back by its column pass and gather while they
+// are still in L2, instead of after every other size's spread has written its own.
 template <typename T, int OP>
 static ibdl_status batch_launch_2d(Batch* B, int mode, const double* in_base, double* out_base, cudaStream_t s) {
   const int pi = Slot2<T>::pi;
   bool first = true;
-  for (int stage = 0; stage < 3; ++stage)
-    for (int L = kMinL2d; L <= kMaxL2d; ++L) {
+  for (int L = kMinL2d; L <= kMaxL2d; ++L)
+    for (int stage = 0; stage < 3; ++stage) {
       if (B->lv[pi][L].row_count == 0) continue;
       IBDL_TRY((batch_stage_for_size<T, OP, kMinL2d>(L, B, stage, mode, in_base, out_base, s, !first)));
       first = false;
@@ -423,6 +430,7 @@ ibdl_status batch_apply_2d(Batch* B, int precision, int mode, const double* in_b
 
 template <typename T, int OP>
 static ibdl_status batch_shape(Batch* B, Geometry* g, int pi) {
+  if (g->split[pi]) return fail(IBDL_ERR_UNSUPPORTED, "batched launches hold every field of a band at once");
   Launch2D lc;
   IBDL_TRY((launch_shape<T, OP>(g, g->rows_per_cta[pi], g->cols_per_cta[pi], g->threads[pi], &lc)));
   BatchSize& z = B->lv[pi][log2i(g->n)];
@@ -582,15 +590,18 @@ static int pow2_in(int v, int lo, int hi) {
   return r;
 }
 
+// fields a row band or column group holds at once
+static int nf_held(const Geometry* g, int pi) { return g->split[pi] ? 1 : nf_row_max(g); }
+
 static bool row_fits(const Geometry* g, int pi, int R) {
-  const int L = log2i(g->n), nf = nf_row_max(g);
+  const int L = log2i(g->n), nf = nf_held(g, pi);
   const size_t bytes = pi == 1 ? smem_rows_2d<float>(nf, R, L) : smem_rows_2d<double>(nf, R, L);
   // R ≤ n/8 (the column pass's lanes then address their rows with one stride per band)
   return R >= 2 && R <= std::max(2, g->n / 8) && bytes <= kSmemLimit2d &&
          row_threads(nf, R, L, pi == 1, 0) <= kMaxThreads2d;
 }
 static bool col_fits(const Geometry* g, int pi, int C) {
-  const int L = log2i(g->n), nf = nf_row_max(g);
+  const int L = log2i(g->n), nf = nf_held(g, pi);
   const size_t bytes = pi == 1 ? smem_cols_2d<float>(nf, C, L) : smem_cols_2d<double>(nf, C, L);
   return C >= 1 && C <= g->n / 2 && bytes <= kSmemLimit2d && col_threads(nf, C, L, pi == 1) <= kMaxThreads2d;
 }
@@ -601,9 +612,10 @@ static bool col_fits(const Geometry* g, int pi, int C) {
 // so geometries created later with the same key start from the tuned shape
 // ------------------------------------------------------------------------------------------
 struct TuneKey {
-  int n, nf_in, nf_out, pde, dipole, pi;
+  int n, nf_in, nf_out, pde, dipole, pi, split;
   bool operator==(const TuneKey& o) const {
-    return n == o.n && nf_in == o.nf_in && nf_out == o.nf_out && pde == o.pde && dipole == o.dipole && pi == o.pi;
+    return n == o.n && nf_in == o.nf_in && nf_out == o.nf_out && pde == o.pde && dipole == o.dipole && pi == o.pi &&
+           split == o.split;
   }
 };
 struct TuneVal {
@@ -633,12 +645,14 @@ static void tuned_store(const TuneKey& k, const TuneVal& v) {
   g_tuned.push_back({k, v});
 }
 
-static TuneKey tune_key(const Geometry* g, int pi) { return {g->n, g->nf_in, g->nf_out, g->pde, g->dipole, pi}; }
+static TuneKey tune_key(const Geometry* g, int pi) {
+  return {g->n, g->nf_in, g->nf_out, g->pde, g->dipole, pi, g->split[pi]};
+}
 
 // The row kernels' shape (band height R ∈ {2 … 64} and least thread count ∈ {0, 256, 512}) is
 // tuned first with the column group fixed, then the column group C ∈ {1 … 32}: the kernels are
 // independent, so the two sweeps find the best pair. Candidates must fit shared memory and 512
-// threads per CTA; each is timed as the median of 5 applications after one warm-up.
+// threads per CTA; each is timed on back-to-back applications (below) after one warm-up.
 ibdl_status autotune_2d(Geometry* g, int pi, bool /*fixed_threads*/, cudaStream_t s, const double* Q, double* Y) {
   const int saved_timing = g->timing;
   g->timing = 0;
@@ -650,14 +664,24 @@ ibdl_status autotune_2d(Geometry* g, int pi, bool /*fixed_threads*/, cudaStream_
     g->rows_per_cta[pi] = R;
     g->cols_per_cta[pi] = C;
     g->threads[pi] = floor;
-    float ms[5];
+    // applications back to back, as a solve runs them (each launch overlapping its predecessor's
+    // tail by programmatic launch): chains of about 1 ms (1 … 8 applications, the length from one
+    // timed application), the median of 5 chains per application
+    float ms[5], one = 0.f;
     IBDL_TRY(apply_2d(g, slot_precision(pi), Q, Y, s, nullptr));
+    cudaEventRecord(e0, s);
+    IBDL_TRY(apply_2d(g, slot_precision(pi), Q, Y, s, nullptr));
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return fail(IBDL_ERR_CUDA, "autotune: event synchronize");
+    cudaEventElapsedTime(&one, e0, e1);
+    const int chain = one > 0.f ? std::max(1, std::min(8, (int)(1.0f / one))) : 8;
     for (int k = 0; k < 5; ++k) {
       cudaEventRecord(e0, s);
-      IBDL_TRY(apply_2d(g, slot_precision(pi), Q, Y, s, nullptr));
+      for (int c = 0; c < chain; ++c) IBDL_TRY(apply_2d(g, slot_precision(pi), Q, Y, s, nullptr));
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) return fail(IBDL_ERR_CUDA, "autotune: event synchronize");
       cudaEventElapsedTime(&ms[k], e0, e1);
+      ms[k] /= chain;
     }
     std::sort(ms, ms + 5);
     *med = ms[2];
@@ -729,14 +753,24 @@ ibdl_status plan_2d(Geometry* g) {
   const int n = g->n, L = log2i(n);
   const int min_ctas = 2 * 152;
   int tuned_stage = 0;
+  const char* se = getenv("IBDL_SPLIT_FIELDS");
+  const bool force_split = se && atoi(se) != 0 && nf_row_max(g) > 1;
   for (int pi = 0; pi < 3; ++pi) {
     const int qt = threads_per_seq_2d(L, pi == 1);
-    int R = 2 * pow2_in(256 / qt, 1, n / 4 > 1 ? n / 4 : 1);
-    while (R > 2 && (n / R < std::min(min_ctas, n / 2) || !row_fits(g, pi, R))) R /= 2;
-    if (!row_fits(g, pi, R)) R = 0;
-    int C = pow2_in(256 / qt, 1, n / 2);
-    while (C > 1 && ((n / 2) / C < std::min(min_ctas, n / 4) || !col_fits(g, pi, C))) C /= 2;
-    if (!col_fits(g, pi, C)) C = 0;
+    int R = 0, C = 0;
+    // all fields of a band or column group at once where they fit shared memory, else one field
+    // per launch (multi-field operators only)
+    for (int split = force_split ? 1 : 0; split < 2; ++split) {
+      if (split && nf_row_max(g) == 1) break;
+      g->split[pi] = split;
+      R = 2 * pow2_in(256 / qt, 1, n / 4 > 1 ? n / 4 : 1);
+      while (R > 2 && (n / R < std::min(min_ctas, n / 2) || !row_fits(g, pi, R))) R /= 2;
+      if (!row_fits(g, pi, R)) R = 0;
+      C = pow2_in(256 / qt, 1, n / 2);
+      while (C > 1 && ((n / 2) / C < std::min(min_ctas, n / 4) || !col_fits(g, pi, C))) C /= 2;
+      if (!col_fits(g, pi, C)) C = 0;
+      if (R && C) break;
+    }
     if (const char* e = getenv("IBDL_PLAN_R")) {
       const int v = atoi(e);
       if ((v & (v - 1)) == 0 && row_fits(g, pi, v)) R = v;
@@ -750,7 +784,7 @@ ibdl_status plan_2d(Geometry* g) {
     g->cols_per_cta[pi] = C;
     g->threads[pi] = 256;  // the row kernels' loops (clearing, spreading, unpacking) get 256 threads
     TuneVal tv;
-    if (R && tuned_lookup(tune_key(g, pi), &tv)) {
+    if (R && tuned_lookup(tune_key(g, pi), &tv) && row_fits(g, pi, tv.R) && col_fits(g, pi, tv.C)) {
       g->rows_per_cta[pi] = tv.R;
       g->cols_per_cta[pi] = tv.C;
       g->threads[pi] = tv.floor;

@@ -151,6 +151,7 @@ struct RowParams {
   double eta;             // η
   double hd;              // h^d
   PT eta_src;             // weight of the ηSQ source: η (scalar) or η/μ (Stokes, projected part)
+  int fsel;               // one-field launches: the field this launch spreads or interpolates
 };
 
 template <typename T>
@@ -258,12 +259,16 @@ __device__ __forceinline__ SpreadItem<typename Prec2<T>::PT> spread_item(const R
 // PF: load the FFT twiddles (and, in the column pass, the symbol rows) before the dependency
 // wait, for latency (single problems); batched launches load them where they are used, which
 // keeps registers down and occupancy up.
-template <typename T, int OP, int L, bool PF = true>
+// SPLIT: one input field (p.fsel) per launch, for grids whose row bands of every field do not
+// fit shared memory together: the band holds that field only, and the first launch (field 0)
+// also writes the jump term and the completed method's rows.
+template <typename T, int OP, int L, bool PF = true, bool SPLIT = false>
 __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int unit, int nunits,
                                                    unsigned char* smem_raw) {
   constexpr int NIN = Traits<OP>::NIN;
+  constexpr int NB = SPLIT ? 1 : NIN;  // fields held in shared memory
   constexpr int NC = Traits<OP>::C;
-  using CF = Cfg2<T, L, NIN>;
+  using CF = Cfg2<T, L, NB>;
   using F = F8<L, CF::V>;
   using PT = typename Prec2<T>::PT;
   constexpr int n = F::N, V = CF::V, QT = CF::QT, NGRP = CF::NGRP;
@@ -284,7 +289,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
     // clear the accumulation buffer (NIN·half padded sequences, a multiple of 16 bytes) with
     // 16-byte stores
     uint4* z = reinterpret_cast<uint4*>(buf);
-    const int nz = (int)((size_t)NIN * half * F::PN * sizeof(cplx<T>) / 16);
+    const int nz = (int)((size_t)NB * half * F::PN * sizeof(cplx<T>) / 16);
     for (int i = threadIdx.x; i < nz; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   typename CF::TW tw[V];
@@ -310,16 +315,17 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   resolve_io(p, pin, pout);
   if (stopped) return;
 
+  const bool first = !SPLIT || p.fsel == 0;
   // jump term: out = ±½·in (the gather kernel adds S*u afterwards); none for grid input
-  if (!p.grid_in)
+  if (!p.grid_in && first)
     for (int i = unit * blockDim.x + threadIdx.x; i < NC * M; i += nunits * blockDim.x)
       pout[i] = p.jump * pin[i] + (p.aug ? pin[NC * M + i / M] : 0.0);
   __syncthreads();  // the accumulation buffer is cleared
-  if (p.aug && unit == 0) {
+  if (p.aug && unit == 0 && first) {
     // constraint rows of the completed method: η Σ_i Δs_i Q_{l,i} (Δs = wscale·h^d); the block
     // size is a power of two (a partial warp below 32 threads), the partial sums go to the
     // reduction slots after the sequence buffers
-    double* red = reinterpret_cast<double*>(buf + (size_t)NIN * half * F::PN);
+    double* red = reinterpret_cast<double*>(buf + (size_t)NB * half * F::PN);
     const int wl = blockDim.x < 32 ? blockDim.x : 32;
     const unsigned wmask = wl == 32 ? 0xffffffffu : ((1u << wl) - 1u);
     for (int l = 0; l < NC; ++l) {
@@ -339,11 +345,12 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   }
 
   if (p.grid_in) {
-    for (int t = threadIdx.x; t < NIN * R * n; t += blockDim.x) {
+    for (int t = threadIdx.x; t < NB * R * n; t += blockDim.x) {
       const int f = t / (R * n);
       const int rem = t - f * R * n;
       const int lr = rem / n, x = rem - lr * n;
-      acc[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)] = PT(p.grid_in[((size_t)f * n + r0 + lr) * n + x]);
+      const int fi = SPLIT ? p.fsel : f;  // the input field
+      acc[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)] = PT(p.grid_in[((size_t)fi * n + r0 + lr) * n + x]);
     }
   }
 
@@ -363,41 +370,49 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
     const int e = (lr >> 1) * n + it.col;  // field 0; field f adds f·half·n
     const int odd = lr & 1;
     const PT pp = px * py;
+    // add v to field f's band (SPLIT: only field p.fsel, held in the first slot)
+    auto add = [&](int f, PT v) {
+      if (SPLIT) {
+        if (f == p.fsel) atomicAdd(acc + 2 * pidx(e) + odd, v);
+      } else {
+        atomicAdd(acc + 2 * pidx(e + f * half * n) + odd, v);
+      }
+    };
     if (OP == OP_SCALAR_AN) {
       const PT q = PT(pin[i]) * ws;
       const PT ddx = it.dpx * py, ddy = px * it.dpy;
       // dipole source n·∇δ_h, plus ηδ_h for the completed method
-      atomicAdd(acc + 2 * pidx(e) + odd, q * (nx * ddx + ny * ddy + p.eta_src * pp));
+      add(0, q * (nx * ddx + ny * ddy + p.eta_src * pp));
     } else if (OP == OP_SCALAR_SD) {
       const PT q = PT(pin[i]) * ws * pp;
-      atomicAdd(acc + 2 * pidx(e) + odd, q * nx);
-      atomicAdd(acc + 2 * pidx(e + half * n) + odd, q * ny);
+      add(0, q * nx);
+      add(1, q * ny);
     } else if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
       const PT qx = PT(pin[i]), qy = PT(pin[M + i]);
       const PT c0 = ws * (qx * nx + qy * ny);  // Q·n
       const PT c1 = ws * (PT(2) * qx * nx);    // A_xx
       const PT c2 = ws * (PT(2) * qy * ny);    // A_yy
       const PT c3 = ws * (qx * ny + qy * nx);  // A_xy
-      atomicAdd(acc + 2 * pidx(e) + odd, c0 * pp);
+      add(0, c0 * pp);
       if (OP == OP_STOKES_AN) {
         const PT ddx = it.dpx * py, ddy = px * it.dpy;
         // g_x = ∂_x S(A_xx) + ∂_y S(A_xy), g_y = ∂_x S(A_xy) + ∂_y S(A_yy); the completed method
         // adds (η/μ) S(Q) to the projected source
         const PT ce = p.eta_src * ws * pp;
-        atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * ddx + c3 * ddy + ce * qx);
-        atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c3 * ddx + c2 * ddy + ce * qy);
+        add(1, c1 * ddx + c3 * ddy + ce * qx);
+        add(2, c3 * ddx + c2 * ddy + ce * qy);
       } else {
-        atomicAdd(acc + 2 * pidx(e + half * n) + odd, c1 * pp);
-        atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, c2 * pp);
-        atomicAdd(acc + 2 * pidx(e + 3 * half * n) + odd, c3 * pp);
+        add(1, c1 * pp);
+        add(2, c2 * pp);
+        add(3, c3 * pp);
       }
     } else if (OP == OP_STOKES_T) {
       // ψ_l = Σ_j μ_{l,j} Φ(x − X_j): the transpose of S*, unweighted
-      atomicAdd(acc + 2 * pidx(e) + odd, PT(pin[i]) * pp);
-      atomicAdd(acc + 2 * pidx(e + half * n) + odd, PT(pin[M + i]) * pp);
+      add(0, PT(pin[i]) * pp);
+      add(1, PT(pin[M + i]) * pp);
     } else {
       // plain spread of W (A*: weight Δs/h^d), or of λ (Aᵀ: weight 1, Δs/h^d moves to the gather)
-      atomicAdd(acc + 2 * pidx(e) + odd, PT(pin[i]) * (p.trans ? PT(1) : ws) * pp);
+      add(0, PT(pin[i]) * (p.trans ? PT(1) : ws) * pp);
     }
   }
   __syncthreads();
@@ -409,7 +424,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   // forward FFT of every (field, row pair) sequence; each lane reads and writes back only its own
   // positions, so only the exchanges inside need barriers
 #pragma unroll
-  for (int k = 0; k < NIN / NGRP; ++k) {
+  for (int k = 0; k < NB / NGRP; ++k) {
     const int f = g + k * NGRP;
     cplx<T>* sb = buf + ((size_t)f * half + rp) * F::PN;
     cplx<T> x[1][V][8];
@@ -435,10 +450,11 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   // band-major block (offset k·R + 2j), with one store
   const cplx<T>* res = buf;
   constexpr int nh = n >> 1, lnh = L - 1;
-  for (int t = threadIdx.x; t < NIN * half * nh; t += blockDim.x) {
+  for (int t = threadIdx.x; t < NB * half * nh; t += blockDim.x) {
     const int k = t & (nh - 1), q2 = t >> lnh;
     const int f = q2 / half, jj = q2 - f * half;
     const int zb = (f * half + jj) * F::PN;
+    const int fo = SPLIT ? p.fsel : f;  // the spectrum field written
     cplx<T> a, b;
     if (k == 0) {
       const cplx<T> z0 = res[zb], zh = res[zb + ppos(nh)];
@@ -449,7 +465,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
       a = mk(T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y));
       b = mk(T(0.5) * (zk.y + zc.y), T(0.5) * (zc.x - zk.x));
     }
-    store_pair(p.spec + ((f * n + r0) * nh + k * R + 2 * jj), a, b);
+    store_pair(p.spec + ((fo * n + r0) * nh + k * R + 2 * jj), a, b);
   }
 }
 
@@ -457,6 +473,12 @@ template <typename T, int OP, int L>
 __global__ void __launch_bounds__(kMaxThreads2d) k_spread_rowfft(RowParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   spread_rowfft_body<T, OP, L>(p, blockIdx.x, gridDim.x, smem_raw);
+}
+// one input field (p.fsel) per launch
+template <typename T, int OP, int L>
+__global__ void __launch_bounds__(kMaxThreads2d) k_spread_rowfft1(RowParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  spread_rowfft_body<T, OP, L, true, true>(p, blockIdx.x, gridDim.x, smem_raw);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -903,6 +925,88 @@ __global__ void __launch_bounds__(kMaxThreads2d) k_colpass(ColParams<T> p) {
 }
 
 // ------------------------------------------------------------------------------------------
+// kernel 2, one field at a time: for grids whose columns of every field do not fit shared memory
+// together, the column stage runs as the forward transform of each input field (in place), one
+// pointwise symbol launch over the whole spectrum, and the inverse transform of each output field
+// ------------------------------------------------------------------------------------------
+template <typename T, int L, bool INV>
+__global__ void __launch_bounds__(kMaxThreads2d) k_colfft(ColParams<T> p, int field) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using CF = Cfg2<T, L, 1>;
+  using F = F8<L, CF::V>;
+  constexpr int V = CF::V, QT = CF::QT, Q = F::Q;
+  const int C = p.C, R = p.R, kx0 = blockIdx.x * C;
+  int g, c, j0;
+  col_lane_2d<QT>(C, g, c, j0);
+  const bool active = g < 1;
+  const int kx = kx0 + c;
+  cplx<T>* sb = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)c * col_stride_2d(L, C, (int)sizeof(cplx<T>));
+  typename CF::TW tw[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) tw[v].load(p.tw, j0 + v * QT);
+  const bool stopped = p.stop && *p.stop;  // final before the wait (see the column pass)
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
+  if (stopped) return;
+  cplx<T> x[1][V][8];
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int s8 = 0; s8 < 8; ++s8) x[0][v][s8] = p.spec[col_at_s<L>(field, j0 + v * QT, s8, kx, R)];
+  }
+  f8_fft<T, INV, L, V, 1>(x, sb, 0, j0, tw, active);
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int s8 = 0; s8 < 8; ++s8) p.spec[col_at_s<L>(field, j0 + v * QT, s8, kx, R)] = x[0][v][s8];
+  }
+}
+
+// The Fourier symbol at every (ky, kx) of the transformed spectra, NIN fields in and NOUT out, in
+// place, one thread per point in memory order (band b, column kx, row r of the band); the packed
+// kx = 0 | n/2 column is taken in pairs (ky, −ky) by the thread of the smaller ky.
+template <typename T, int OP, int L>
+__global__ void __launch_bounds__(256) k_symbol2d(ColParams<T> p) {
+  constexpr int NIN = Traits<OP>::NIN, NOUT = Traits<OP>::NOUT;
+  constexpr int n = 1 << L, nh = n / 2;
+  const bool stopped = p.stop && *p.stop;
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
+  if (stopped) return;
+  const int R = p.R;
+  const size_t fstride = (size_t)n * nh;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * nh; idx += gridDim.x * blockDim.x) {
+    const int r = idx & (R - 1), kx = (idx / R) & (nh - 1), ky = (idx / (nh * R)) * R + r;
+    if (kx == 0 && ky > nh) continue;
+    cplx<T> in[NIN], o[NOUT];
+#pragma unroll
+    for (int f = 0; f < NIN; ++f) in[f] = p.spec[f * fstride + idx];
+    if (kx != 0) {
+      symbol_point<T, OP>(p, p.lap1[kx], p.der1[kx], p.lap1[ky], p.der1[ky], in, o);
+#pragma unroll
+      for (int f = 0; f < NOUT; ++f) p.spec[f * fstride + idx] = o[f];
+    } else {
+      const int ky2 = (n - ky) & (n - 1);
+      const int idx2 = (ky2 & ~(R - 1)) * nh + (ky2 & (R - 1));  // (ky2, kx = 0)
+      cplx<T> pm[NIN], o2[NOUT];
+#pragma unroll
+      for (int f = 0; f < NIN; ++f) pm[f] = p.spec[f * fstride + idx2];
+      const T lap0 = p.lap1[0], der0 = p.der1[0], lapn = p.lap1[nh], dern = p.der1[nh];
+      symbol_packed<T, OP>(p, lap0, der0, lapn, dern, p.lap1[ky], p.der1[ky], in, pm, o);
+      if (ky2 != ky) symbol_packed<T, OP>(p, lap0, der0, lapn, dern, p.lap1[ky2], p.der1[ky2], pm, in, o2);
+#pragma unroll
+      for (int f = 0; f < NOUT; ++f) p.spec[f * fstride + idx] = o[f];
+      if (ky2 != ky) {
+#pragma unroll
+        for (int f = 0; f < NOUT; ++f) p.spec[f * fstride + idx2] = o2[f];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // kernel 2, staged form (FP32): persistent CTAs walk the column units of one grid size (of one
 // problem, or of every problem of that size in a batch). Each unit's C columns of all input fields,
 // and its problem's symbol tables, are copied into shared memory by the tensor memory accelerator
@@ -1244,10 +1348,13 @@ __device__ __forceinline__ GatherItem<typename Prec2<T>::PT> gather_item(const R
   return it;
 }
 
-template <typename T, int OP, int GMODE, int L, bool PF = true>
+// SPLIT: one output field (p.fsel) per launch (see the spread kernel); its contribution to every
+// boundary component is added to Y (the operator is linear in the interpolated fields).
+template <typename T, int OP, int GMODE, int L, bool PF = true, bool SPLIT = false>
 __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int unit, unsigned char* smem_raw) {
   constexpr int NOUT = Traits<OP>::NOUT;
-  using CF = Cfg2<T, L, NOUT>;
+  constexpr int NB = SPLIT ? 1 : NOUT;  // fields held in shared memory
+  using CF = Cfg2<T, L, NB>;
   using F = F8<L, CF::V>;
   using PT = typename Prec2<T>::PT;
   constexpr int n = F::N, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q, PN = F::PN;
@@ -1279,15 +1386,16 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
 
   // inverse FFT of every (field, row pair) sequence, its first stage fed from the half spectra
 #pragma unroll
-  for (int k = 0; k < NOUT / NGRP; ++k) {
+  for (int k = 0; k < NB / NGRP; ++k) {
     const int f = g + k * NGRP;
     cplx<T>* sb = buf + ((size_t)f * half + rp) * PN;
     cplx<T> x[1][V][8];
+    const int fs = SPLIT ? p.fsel : f;  // the spectrum field read
     if (active) {
 #pragma unroll
       for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) x[0][v][s] = row_z<T, L>(p.spec, f, r0, rp, R, j0 + v * QT + s * Q);
+        for (int s = 0; s < 8; ++s) x[0][v][s] = row_z<T, L>(p.spec, fs, r0, rp, R, j0 + v * QT + s * Q);
     }
     f8_fft<T, true, L, V, 1>(x, sb, 0, j0, tw, active);
     if (active) {
@@ -1302,13 +1410,14 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   const T* u = reinterpret_cast<const T*>(buf);
 
   if (GMODE == G_GRID) {
-    for (int t = threadIdx.x; t < NOUT * R * n; t += blockDim.x) {
+    for (int t = threadIdx.x; t < NB * R * n; t += blockDim.x) {
       const int f = t / (R * n);
       const int rem = t - f * R * n;
       const int lr = rem / n, x = rem - lr * n;
+      const int fo = SPLIT ? p.fsel : f;  // the grid field written
       // the completed method's field is u₀ + ū (ū after the density in the input vector)
-      const double ub = p.aug ? p.in[(size_t)Traits<OP>::C * M + f] : 0.0;
-      p.grid[((size_t)f * n + r0 + lr) * n + x] =
+      const double ub = p.aug ? p.in[(size_t)Traits<OP>::C * M + fo] : 0.0;
+      p.grid[((size_t)fo * n + r0 + lr) * n + x] =
           double(Prec2<T>::to_pt(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)])) + ub;
     }
     return;
@@ -1331,6 +1440,49 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
     const PT dy = (OP == OP_ADJ_AN || OP == OP_STOKES_T) ? it.dy : PT(0);
     const int eb = (lr >> 1) * n, odd = lr & 1;
     auto uval = [&](int e) { return Prec2<T>::to_pt(u[2 * pidx(e) + odd]); };
+    if constexpr (SPLIT) {
+      // the value, x-gradient and y-gradient gathers of field p.fsel (first slot)
+      PT a = 0, gx = 0, gy = 0;
+#pragma unroll
+      for (int ax = 0; ax < 4; ++ax) {
+        const int col = (bx + ax) & (n - 1);
+        const PT px = it.px[ax], v0 = uval(eb + col);
+        a += v0 * px * py;
+        if (OP == OP_STOKES_T) {
+          gx += v0 * it.dx[ax] * py;
+          gy += v0 * px * dy;
+        }
+      }
+      const int fs = p.fsel;
+      if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
+        atomicAdd(pout + (size_t)fs * M + i, double(a));  // field l is velocity component l
+      } else if (OP == OP_ADJ_SD) {
+        // −n_m S*(∂_m v) with field m = ∂_m v
+        double val = -(fs == 0 ? double(it.nx) : double(it.ny)) * double(a);
+        if (p.trans) val *= double(it.ws);
+        atomicAdd(pout + i, val);
+      } else if (OP == OP_STOKES_T) {
+        // field 0 = v_s (a_s), 1 = v_gx (G_xx, G_xy), 2 = v_gy (G_yx, G_yy): their terms of
+        // (Δs/h²)[n_l a_s + Σ_k n_k (G_lk + G_kl)]
+        const double ws = double(it.ws), nx = double(it.nx), ny = double(it.ny);
+        double ox, oy;
+        if (fs == 0) {
+          ox = nx * double(a);
+          oy = ny * double(a);
+        } else if (fs == 1) {
+          ox = 2.0 * nx * double(gx) + ny * double(gy);
+          oy = nx * double(gy);
+        } else {
+          ox = ny * double(gx);
+          oy = nx * double(gx) + 2.0 * ny * double(gy);
+        }
+        atomicAdd(pout + i, ws * ox);
+        atomicAdd(pout + M + i, ws * oy);
+      } else {
+        atomicAdd(pout + i, double(a));
+      }
+      continue;
+    }
     if (OP == OP_STOKES_T) {
       // a_s = Σ v_s Φ, G_mk = Σ v_gm ∂_kΦ; out_l += (Δs/h²)[n_l a_s + Σ_k n_k (G_lk + G_kl)]
       PT as = 0, gxx = 0, gxy = 0, gyx = 0, gyy = 0;
@@ -1387,6 +1539,12 @@ template <typename T, int OP, int GMODE, int L>
 __global__ void __launch_bounds__(kMaxThreads2d) k_rowifft_gather(RowParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   rowifft_gather_body<T, OP, GMODE, L>(p, blockIdx.x, smem_raw);
+}
+// one output field (p.fsel) per launch
+template <typename T, int OP, int GMODE, int L>
+__global__ void __launch_bounds__(kMaxThreads2d) k_rowifft_gather1(RowParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rowifft_gather_body<T, OP, GMODE, L, true, true>(p, blockIdx.x, smem_raw);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1450,6 +1608,7 @@ struct Launch2D {
   int threads_row, threads_col, threads_gather;
   bool pdl;
   int grid_mode;            // G_INTERP or G_GRID
+  bool split;               // one field per launch (the shapes above are those of one field)
 };
 
 template <typename T, int OP, int L>

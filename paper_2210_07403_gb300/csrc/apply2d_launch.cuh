@@ -174,12 +174,87 @@ ibdl_status set_attrs_2d() {
   return IBDL_OK;
 }
 
+// One application one field per launch (grids whose fields do not fit shared memory together):
+// a spread + row FFT launch per input field, the forward column transform of each input field,
+// one symbol launch over the spectrum, the inverse column transform of each output field, and an
+// inverse row FFT + interpolation launch per output field (which add into Y). 2·NIN + 2·NOUT + 1
+// launches, chained by programmatic launch.
+template <typename T, int OP, int L>
+ibdl_status launch_apply_split_2d(Geometry* g, const RowParams<T>& rp, const ColParams<T>& cp, const Launch2D& lc,
+                                  cudaStream_t s) {
+  constexpr int NIN = Traits<OP>::NIN, NOUT = Traits<OP>::NOUT;
+  constexpr int n = 1 << L;
+  static std::atomic<unsigned long long> d1{0}, d2{0}, d3{0}, d4{0}, d5{0};
+  const int st0 = std::is_same<T, float>::value ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
+  if (g->timing) timing_mark(g, s, -1);
+  RowParams<T> r = rp;
+  if constexpr (NIN > 1) {
+    IBDL_CUDA(opt_in_smem(k_spread_rowfft1<T, OP, L>, d1));
+    for (int f = 0; f < NIN; ++f) {
+      r.fsel = f;
+      IBDL_CUDA(launch_k(k_spread_rowfft1<T, OP, L>, n / lc.R, lc.threads_row, lc.smem_row, s, lc.pdl, r));
+    }
+  } else {
+    IBDL_CUDA(launch_k(k_spread_rowfft<T, OP, L>, n / lc.R, lc.threads_row, lc.smem_row, s, lc.pdl, rp));
+  }
+  if (g->timing) timing_mark(g, s, st0);
+  IBDL_CUDA(opt_in_smem(k_colfft<T, L, false>, d2));
+  IBDL_CUDA(opt_in_smem(k_colfft<T, L, true>, d3));
+  for (int f = 0; f < NIN; ++f)
+    IBDL_CUDA(launch_k(k_colfft<T, L, false>, (n / 2) / lc.C, lc.threads_col, lc.smem_col, s, lc.pdl, cp, f));
+  const int sgrid = (int)std::min<long>((long)n * (n / 2) / 256, 152L * 16);
+  IBDL_CUDA(launch_k(k_symbol2d<T, OP, L>, sgrid > 0 ? sgrid : 1, 256, 0, s, lc.pdl, cp));
+  for (int f = 0; f < NOUT; ++f)
+    IBDL_CUDA(launch_k(k_colfft<T, L, true>, (n / 2) / lc.C, lc.threads_col, lc.smem_col, s, lc.pdl, cp, f));
+  if (g->timing) timing_mark(g, s, st0 + 1);
+  if constexpr (NOUT > 1) {
+    if (lc.grid_mode == G_GRID) {
+      if constexpr (!std::is_same<T, ff>::value) {
+        IBDL_CUDA(opt_in_smem(k_rowifft_gather1<T, OP, G_GRID, L>, d4));
+        for (int f = 0; f < NOUT; ++f) {
+          r.fsel = f;
+          IBDL_CUDA(launch_k(k_rowifft_gather1<T, OP, G_GRID, L>, n / lc.R, lc.threads_gather, lc.smem_gather, s,
+                             lc.pdl, r));
+        }
+      } else {
+        return fail(IBDL_ERR_UNSUPPORTED, "float-float grid output");
+      }
+    } else {
+      IBDL_CUDA(opt_in_smem(k_rowifft_gather1<T, OP, G_INTERP, L>, d5));
+      for (int f = 0; f < NOUT; ++f) {
+        r.fsel = f;
+        IBDL_CUDA(launch_k(k_rowifft_gather1<T, OP, G_INTERP, L>, n / lc.R, lc.threads_gather, lc.smem_gather, s,
+                           lc.pdl, r));
+      }
+    }
+  } else {
+    if constexpr (std::is_same<T, ff>::value) {
+      if (lc.grid_mode == G_GRID) return fail(IBDL_ERR_UNSUPPORTED, "float-float grid output");
+      IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_INTERP, L>, n / lc.R, lc.threads_gather, lc.smem_gather, s, lc.pdl,
+                         rp));
+    } else if (lc.grid_mode == G_GRID) {
+      IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_GRID, L>, n / lc.R, lc.threads_gather, lc.smem_gather, s, lc.pdl,
+                         rp));
+    } else {
+      IBDL_CUDA(launch_k(k_rowifft_gather<T, OP, G_INTERP, L>, n / lc.R, lc.threads_gather, lc.smem_gather, s, lc.pdl,
+                         rp));
+    }
+  }
+  if (g->timing) timing_mark(g, s, st0 + 2);
+  g->launches += (NIN > 1 ? NIN : 1) + NIN + 1 + NOUT + (NOUT > 1 ? NOUT : 1);
+  IBDL_CUDA(cudaGetLastError());
+  return IBDL_OK;
+}
+
 template <typename T, int OP, int L>
 ibdl_status launch_apply_2d(Geometry* g, const RowParams<T>& rp, const ColParams<T>& cp, const Launch2D& lc,
                             cudaStream_t s) {
   constexpr int pi = std::is_same<T, float>::value ? 1 : 0;
   constexpr int n = 1 << L;
   IBDL_TRY((set_attrs_2d<T, OP, L>()));
+  if constexpr (Traits<OP>::NIN > 1 || Traits<OP>::NOUT > 1) {
+    if (lc.split) return launch_apply_split_2d<T, OP, L>(g, rp, cp, lc, s);
+  }
   const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
   IBDL_CUDA(launch_k(k_spread_rowfft<T, OP, L>, n / lc.R, lc.threads_row, lc.smem_row, s, lc.pdl, rp));

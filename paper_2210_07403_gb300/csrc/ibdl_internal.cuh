@@ -130,6 +130,8 @@ struct Geometry {
   int zcols_per_cta[2];  // 3-D: kx columns per CTA in the z pass
   size_t smem_row[2], smem_col[2], smem_row_inv[2];
   int threads[3];        // 2-D: least threads per CTA of the row kernels (0: none)
+  int split[3];          // 2-D: one field per launch (the fields' row bands or columns do not fit
+                         // shared memory together, or IBDL_SPLIT_FIELDS=1)
 
   // GMRES workspace (allocated lazily, sized for `krylov_m`)
   int krylov_m;

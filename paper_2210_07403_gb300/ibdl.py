@@ -83,6 +83,8 @@ SIGNATURES = {
     "ibdl_evaluate_field_forced": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ibdl_default_solve_opts": (None, [POINTER(ibdl_solve_opts)]),
     "ibdl_geometry_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int64)]),
+    "ibdl_launch_plan": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                                 POINTER(c_int)]),
     "ibdl_apply_noalloc": (c_int, [POINTER(ibdl_geometry_desc), c_int, c_void_p, c_void_p, c_void_p]),
     "ibdl_create_batch": (c_int, [POINTER(ibdl_geometry_desc), c_int, c_void_p, POINTER(c_void_p)]),
     "ibdl_destroy_batch": (c_int, [c_void_p]),
@@ -237,6 +239,12 @@ def ibdl_default_solve_opts() -> ibdl_solve_opts:
     o = ibdl_solve_opts()
     load().ibdl_default_solve_opts(byref(o))
     return o
+
+
+def ibdl_launch_plan(geom, precision: int):
+    v = [c_int() for _ in range(5)]
+    _check(load().ibdl_launch_plan(geom, precision, *[byref(x) for x in v]))
+    return dict(zip(("rows", "cols", "threads", "staged", "split"), (x.value for x in v)))
 
 
 def ibdl_geometry_sizes(geom):
@@ -622,6 +630,10 @@ class Geometry:
 
     def set_stage_timing(self, enable: bool = True):
         ibdl_set_stage_timing(self._h, int(enable))
+
+    def launch_plan(self, precision: str = "fp32"):
+        """The 2-D launch plan of one grid arithmetic: rows, cols, threads, staged, split."""
+        return ibdl_launch_plan(self._h, _PREC[precision])
 
     def stage_times(self):
         """{stage name: (total device ms, launches)} since the previous call."""
