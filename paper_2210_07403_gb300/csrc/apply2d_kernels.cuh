@@ -119,6 +119,31 @@ struct Cfg2 {
   using TW = std::conditional_t<TWR, TwRegs<T, L>, TwTable<T, L>>;
 };
 
+// Column kernels (and the row kernels, with the row pairs of a band in place of the columns):
+// the C columns of a thread group are interleaved across consecutive threads
+// (column c = t mod C, lane j0 = t / C for thread t of the group), so a warp holds 32/C lanes of
+// each of C adjacent columns (one lane of each of 32 columns when C ≥ 32): its accesses to the
+// band-major spectra cover whole 32-byte sectors (C·R adjacent values per band). Each column's
+// exchange buffer holds the padded sequence and is rounded up to a stride ≡ max(1, w/C) (mod w)
+// elements, w = 16 for 8-byte and 8 for 16-byte elements, which puts the C columns of a warp in
+// different shared-memory banks: every exchange then takes the least number of wavefronts the
+// warp's bytes need (checked by counting banks per warp for every size, C ≤ 32 and R ≤ 8 on the
+// CPU, against a search over all strides).
+__host__ __device__ constexpr int col_stride_2d(int L, int C, int esize) {
+  const int pn = (1 << L) + (1 << L) / 8;
+  const int w = esize == 8 ? 16 : 8;
+  const int t = (w / C > 1 ? w / C : 1) % w;
+  return C < 2 ? pn : pn + (((t - pn) % w) + w) % w;
+}
+template <int QT>
+__device__ __forceinline__ void col_lane_2d(int C, int& g, int& c, int& j0) {
+  const int per = C * QT;
+  g = (int)threadIdx.x / per;
+  const int t = (int)threadIdx.x - g * per;
+  c = t & (C - 1);
+  j0 = t >> (__ffs(C) - 1);
+}
+
 template <typename T>
 struct RowParams {
   using PT = typename Prec2<T>::PT;
@@ -273,23 +298,27 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   using PT = typename Prec2<T>::PT;
   constexpr int n = F::N, V = CF::V, QT = CF::QT, NGRP = CF::NGRP;
   const int R = p.R, half = R >> 1, M = p.M;
-  // sequence (field f, row pair rp) at buf + (f·half + rp)·PN; accumulation view (point type PT,
-  // the same bytes per element): field f, local row lr, column x → real part (even lr) or
-  // imaginary part (odd lr) of element (f·half + lr/2)·n + x in the padded layout
+  // sequence (field f, row pair rp) at buf + (f·half + rp)·PN (the padded sequence rounded up as
+  // for the column groups, with the row pairs of a group interleaved across threads like the
+  // columns); accumulation view (point type PT, the same bytes per element): field f, local row
+  // lr, column x → real part (even lr) or imaginary part (odd lr) of element ppos(x) of sequence
+  // f·half + lr/2
+  const int PN = col_stride_2d(L, half, (int)sizeof(cplx<T>));
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   PT* acc = reinterpret_cast<PT*>(buf);
+  auto aidx = [&](int seq, int x) { return 2 * (seq * PN + ppos(x)); };
   const int r0 = unit * R;
   // FFT lanes: thread (group g, row pair rp, lane j0); threads past NGRP·half·QT only help with
   // the loops (clearing, spreading, unpacking)
-  const int q = threadIdx.x / QT, j0 = threadIdx.x - q * QT;
-  const int g = q / half, rp = q - g * half;
+  int g, rp, j0;
+  col_lane_2d<QT>(half, g, rp, j0);
   const bool active = g < NGRP;
   // prologue independent of the previous kernel, then wait for it (programmatic launch)
   {
     // clear the accumulation buffer (NIN·half padded sequences, a multiple of 16 bytes) with
     // 16-byte stores
     uint4* z = reinterpret_cast<uint4*>(buf);
-    const int nz = (int)((size_t)NB * half * F::PN * sizeof(cplx<T>) / 16);
+    const int nz = (int)((size_t)NB * half * PN * sizeof(cplx<T>) / 16);
     for (int i = threadIdx.x; i < nz; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   typename CF::TW tw[V];
@@ -325,7 +354,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
     // constraint rows of the completed method: η Σ_i Δs_i Q_{l,i} (Δs = wscale·h^d); the block
     // size is a power of two (a partial warp below 32 threads), the partial sums go to the
     // reduction slots after the sequence buffers
-    double* red = reinterpret_cast<double*>(buf + (size_t)NB * half * F::PN);
+    double* red = reinterpret_cast<double*>(buf + (size_t)NB * half * PN);
     const int wl = blockDim.x < 32 ? blockDim.x : 32;
     const unsigned wmask = wl == 32 ? 0xffffffffu : ((1u << wl) - 1u);
     for (int l = 0; l < NC; ++l) {
@@ -350,7 +379,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
       const int rem = t - f * R * n;
       const int lr = rem / n, x = rem - lr * n;
       const int fi = SPLIT ? p.fsel : f;  // the input field
-      acc[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)] = PT(p.grid_in[((size_t)fi * n + r0 + lr) * n + x]);
+      acc[aidx(f * half + (lr >> 1), x) + (lr & 1)] = PT(p.grid_in[((size_t)fi * n + r0 + lr) * n + x]);
     }
   }
 
@@ -367,15 +396,14 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
     if (lr >= R) continue;
     const int i = it.i;
     const PT px = it.px, py = it.py, ws = it.ws, nx = it.nx, ny = it.ny;
-    const int e = (lr >> 1) * n + it.col;  // field 0; field f adds f·half·n
-    const int odd = lr & 1;
+    const int e0 = aidx(lr >> 1, it.col) + (lr & 1);  // field 0; field f adds 2·f·half·PN
     const PT pp = px * py;
     // add v to field f's band (SPLIT: only field p.fsel, held in the first slot)
     auto add = [&](int f, PT v) {
       if (SPLIT) {
-        if (f == p.fsel) atomicAdd(acc + 2 * pidx(e) + odd, v);
+        if (f == p.fsel) atomicAdd(acc + e0, v);
       } else {
-        atomicAdd(acc + 2 * pidx(e + f * half * n) + odd, v);
+        atomicAdd(acc + e0 + 2 * f * half * PN, v);
       }
     };
     if (OP == OP_SCALAR_AN) {
@@ -426,7 +454,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
 #pragma unroll
   for (int k = 0; k < NB / NGRP; ++k) {
     const int f = g + k * NGRP;
-    cplx<T>* sb = buf + ((size_t)f * half + rp) * F::PN;
+    cplx<T>* sb = buf + ((size_t)f * half + rp) * PN;
     cplx<T> x[1][V][8];
     if (active) {
 #pragma unroll
@@ -453,7 +481,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   for (int t = threadIdx.x; t < NB * half * nh; t += blockDim.x) {
     const int k = t & (nh - 1), q2 = t >> lnh;
     const int f = q2 / half, jj = q2 - f * half;
-    const int zb = (f * half + jj) * F::PN;
+    const int zb = (f * half + jj) * PN;
     const int fo = SPLIT ? p.fsel : f;  // the spectrum field written
     cplx<T> a, b;
     if (k == 0) {
@@ -587,30 +615,6 @@ template <int L>
 __device__ __forceinline__ int col_at_s(int f, int j, int s, int k, int R) {
   constexpr int Q = (1 << L) / 8, nh = (1 << L) / 2;
   return col_at<L>(f, j, k, R) + s * (Q * nh);
-}
-
-// Column kernels: the C columns of a thread group are interleaved across consecutive threads
-// (column c = t mod C, lane j0 = t / C for thread t of the group), so a warp holds 32/C lanes of
-// each of C adjacent columns (one lane of each of 32 columns when C ≥ 32): its accesses to the
-// band-major spectra cover whole 32-byte sectors (C·R adjacent values per band). Each column's
-// exchange buffer holds the padded sequence and is rounded up to a stride ≡ max(1, w/C) (mod w)
-// elements, w = 16 for 8-byte and 8 for 16-byte elements, which puts the C columns of a warp in
-// different shared-memory banks: every exchange then takes the least number of wavefronts the
-// warp's bytes need (checked by counting banks per warp for every size, C ≤ 32 and R ≤ 8 on the
-// CPU, against a search over all strides).
-__host__ __device__ constexpr int col_stride_2d(int L, int C, int esize) {
-  const int pn = (1 << L) + (1 << L) / 8;
-  const int w = esize == 8 ? 16 : 8;
-  const int t = (w / C > 1 ? w / C : 1) % w;
-  return C < 2 ? pn : pn + (((t - pn) % w) + w) % w;
-}
-template <int QT>
-__device__ __forceinline__ void col_lane_2d(int C, int& g, int& c, int& j0) {
-  const int per = C * QT;
-  g = (int)threadIdx.x / per;
-  const int t = (int)threadIdx.x - g * per;
-  c = t & (C - 1);
-  j0 = t >> (__ffs(C) - 1);
 }
 
 template <typename T, int OP, int L, bool PF = true>
@@ -1357,13 +1361,15 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   using CF = Cfg2<T, L, NB>;
   using F = F8<L, CF::V>;
   using PT = typename Prec2<T>::PT;
-  constexpr int n = F::N, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q, PN = F::PN;
+  constexpr int n = F::N, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q;
   const int R = p.R, half = R >> 1, M = p.M;
+  // sequences and lanes as in the spread kernel (row pairs interleaved across threads)
+  const int PN = col_stride_2d(L, half, (int)sizeof(cplx<T>));
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   const int r0 = unit * R;
   // FFT lanes: thread (group g, row pair rp, lane j0); threads past NGRP·half·QT only gather
-  const int q = threadIdx.x / QT, j0 = threadIdx.x - q * QT;
-  const int g = q / half, rp = q - g * half;
+  int g, rp, j0;
+  col_lane_2d<QT>(half, g, rp, j0);
   const bool active = g < NGRP;
   typename CF::TW tw[V];
 #pragma unroll
@@ -1418,7 +1424,7 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
       // the completed method's field is u₀ + ū (ū after the density in the input vector)
       const double ub = p.aug ? p.in[(size_t)Traits<OP>::C * M + fo] : 0.0;
       p.grid[((size_t)fo * n + r0 + lr) * n + x] =
-          double(Prec2<T>::to_pt(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)])) + ub;
+          double(Prec2<T>::to_pt(u[2 * ((f * half + (lr >> 1)) * PN + ppos(x)) + (lr & 1)])) + ub;
     }
     return;
   }
@@ -1438,15 +1444,16 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
     const int bx = it.bx;
     const PT py = it.py;
     const PT dy = (OP == OP_ADJ_AN || OP == OP_STOKES_T) ? it.dy : PT(0);
-    const int eb = (lr >> 1) * n, odd = lr & 1;
-    auto uval = [&](int e) { return Prec2<T>::to_pt(u[2 * pidx(e) + odd]); };
+    // value of sequence lr/2 + field·half at column x (part lr & 1)
+    const int eb = 2 * (lr >> 1) * PN + (lr & 1), fs2 = 2 * half * PN;
+    auto uval = [&](int f, int x) { return Prec2<T>::to_pt(u[eb + f * fs2 + 2 * ppos(x)]); };
     if constexpr (SPLIT) {
       // the value, x-gradient and y-gradient gathers of field p.fsel (first slot)
       PT a = 0, gx = 0, gy = 0;
 #pragma unroll
       for (int ax = 0; ax < 4; ++ax) {
         const int col = (bx + ax) & (n - 1);
-        const PT px = it.px[ax], v0 = uval(eb + col);
+        const PT px = it.px[ax], v0 = uval(0, col);
         a += v0 * px * py;
         if (OP == OP_STOKES_T) {
           gx += v0 * it.dx[ax] * py;
@@ -1490,9 +1497,9 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
       for (int ax = 0; ax < 4; ++ax) {
         const int col = (bx + ax) & (n - 1);
         const PT px = it.px[ax], dx = it.dx[ax];
-        const PT vs = uval(eb + col);
-        const PT vx = uval(eb + half * n + col);
-        const PT vy = uval(eb + 2 * half * n + col);
+        const PT vs = uval(0, col);
+        const PT vx = uval(1, col);
+        const PT vy = uval(2, col);
         as += vs * px * py;
         gxx += vx * dx * py;
         gxy += vx * px * dy;
@@ -1510,14 +1517,14 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
     for (int ax = 0; ax < 4; ++ax) {
       const int col = (bx + ax) & (n - 1);
       const PT px = it.px[ax];
-      const PT v0 = uval(eb + col);
+      const PT v0 = uval(0, col);
       if (OP == OP_ADJ_AN) {
         acc0 += v0 * it.dx[ax] * py;
         acc1 += v0 * px * dy;
       } else {
         const PT pp = px * py;
         acc0 += v0 * pp;
-        if (NOUT == 2) acc1 += uval(eb + half * n + col) * pp;
+        if (NOUT == 2) acc1 += uval(1, col) * pp;
       }
     }
     if (OP == OP_STOKES_AN || OP == OP_STOKES_SD) {
@@ -1593,7 +1600,7 @@ __host__ __device__ constexpr size_t padded_seq_2d(int L) { return (size_t(1) <<
 constexpr size_t kRowReduceBytes2d = 32 * sizeof(double);
 template <typename T>
 __host__ __device__ constexpr size_t smem_rows_2d(int nf, int R, int L) {
-  return (size_t)nf * (R / 2) * padded_seq_2d(L) * 2 * sizeof(T) + kRowReduceBytes2d;
+  return (size_t)nf * (R / 2) * col_stride_2d(L, R / 2, 2 * sizeof(T)) * 2 * sizeof(T) + kRowReduceBytes2d;
 }
 template <typename T>
 __host__ __device__ constexpr size_t smem_cols_2d(int nf, int C, int L) {
