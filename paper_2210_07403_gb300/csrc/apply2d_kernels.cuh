@@ -144,6 +144,25 @@ __device__ __forceinline__ void col_lane_2d(int C, int& g, int& c, int& j0) {
   j0 = t >> (__ffs(C) - 1);
 }
 
+// Row kernels interleave their row pairs like the column groups, except where a thread holds four
+// lanes (FP32 at 8192²): measured slower there (848 against 903 µs per application), they keep one
+// row pair per run of consecutive threads and the plain padded stride.
+__host__ __device__ constexpr bool row_interleave_2d(int L, bool f32) { return lanes_per_thread_2d(L, f32) < 4; }
+__host__ __device__ constexpr int row_stride_2d(int L, int half, int esize) {
+  return row_interleave_2d(L, esize == 8) ? col_stride_2d(L, half, esize) : (1 << L) + (1 << L) / 8;
+}
+template <int QT, bool IL>
+__device__ __forceinline__ void row_lane_2d(int half, int& g, int& rp, int& j0) {
+  if constexpr (IL) {
+    col_lane_2d<QT>(half, g, rp, j0);
+  } else {
+    const int q = (int)threadIdx.x / QT;
+    j0 = (int)threadIdx.x - q * QT;
+    g = q / half;
+    rp = q - g * half;
+  }
+}
+
 template <typename T>
 struct RowParams {
   using PT = typename Prec2<T>::PT;
@@ -303,7 +322,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   // columns); accumulation view (point type PT, the same bytes per element): field f, local row
   // lr, column x → real part (even lr) or imaginary part (odd lr) of element ppos(x) of sequence
   // f·half + lr/2
-  const int PN = col_stride_2d(L, half, (int)sizeof(cplx<T>));
+  const int PN = row_stride_2d(L, half, (int)sizeof(cplx<T>));
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   PT* acc = reinterpret_cast<PT*>(buf);
   auto aidx = [&](int seq, int x) { return 2 * (seq * PN + ppos(x)); };
@@ -311,7 +330,7 @@ __device__ __forceinline__ void spread_rowfft_body(const RowParams<T>& p, int un
   // FFT lanes: thread (group g, row pair rp, lane j0); threads past NGRP·half·QT only help with
   // the loops (clearing, spreading, unpacking)
   int g, rp, j0;
-  col_lane_2d<QT>(half, g, rp, j0);
+  row_lane_2d<QT, row_interleave_2d(L, sizeof(T) == 4)>(half, g, rp, j0);
   const bool active = g < NGRP;
   // prologue independent of the previous kernel, then wait for it (programmatic launch)
   {
@@ -1364,12 +1383,12 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   constexpr int n = F::N, V = CF::V, QT = CF::QT, NGRP = CF::NGRP, Q = F::Q;
   const int R = p.R, half = R >> 1, M = p.M;
   // sequences and lanes as in the spread kernel (row pairs interleaved across threads)
-  const int PN = col_stride_2d(L, half, (int)sizeof(cplx<T>));
+  const int PN = row_stride_2d(L, half, (int)sizeof(cplx<T>));
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   const int r0 = unit * R;
   // FFT lanes: thread (group g, row pair rp, lane j0); threads past NGRP·half·QT only gather
   int g, rp, j0;
-  col_lane_2d<QT>(half, g, rp, j0);
+  row_lane_2d<QT, row_interleave_2d(L, sizeof(T) == 4)>(half, g, rp, j0);
   const bool active = g < NGRP;
   typename CF::TW tw[V];
 #pragma unroll
@@ -1600,7 +1619,7 @@ __host__ __device__ constexpr size_t padded_seq_2d(int L) { return (size_t(1) <<
 constexpr size_t kRowReduceBytes2d = 32 * sizeof(double);
 template <typename T>
 __host__ __device__ constexpr size_t smem_rows_2d(int nf, int R, int L) {
-  return (size_t)nf * (R / 2) * col_stride_2d(L, R / 2, 2 * sizeof(T)) * 2 * sizeof(T) + kRowReduceBytes2d;
+  return (size_t)nf * (R / 2) * row_stride_2d(L, R / 2, 2 * sizeof(T)) * 2 * sizeof(T) + kRowReduceBytes2d;
 }
 template <typename T>
 __host__ __device__ constexpr size_t smem_cols_2d(int nf, int C, int L) {
