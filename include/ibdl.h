@@ -104,18 +104,19 @@ enum { IBDL_FP64 = 0, IBDL_FP32 = 1,
                            ibdl_solve_opts.residual                                           */
        IBDL_FP32X2 = 3  /* float-float: every value of the FFT and Fourier stage an unevaluated
                            sum of two FP32 numbers (about 48 significand bits, an application
-                           within about 1e-13 of FP64), the point work in FP64; 2-D operator
-                           applications (A and Aᵀ, grids to 4096²) and the refinement residual */ };
+                           within about 1e-13 of FP64), the point work in FP64; operator
+                           applications (A and Aᵀ; 2-D grids to 4096², every 3-D grid) and the
+                           refinement residual                                                */ };
 
 typedef struct ibdl_geometry ibdl_geometry; /* opaque, library-owned */
 
 typedef struct {
   int dim;              /* 2 or 3                                                          */
   int n;                /* grid nodes per axis: a power of two, 16..8192 (2-D), 16..256 (3-D);
-                           the shared-memory FFT runs 2-D scalar problems to 8192 in every
-                           precision, Stokes to 4096 (FP64, float-float) and 8192 (FP32), the
-                           divergence-dipole Stokes operator to 2048 (FP64) and 4096 (FP32); a
-                           call at a larger size returns IBDL_ERR_UNSUPPORTED                 */
+                           every 2-D operator runs to 8192 in FP64 and FP32 (one field per
+                           launch where a band's or column's fields do not fit shared memory
+                           together) and to 4096 in float-float; a float-float call at 8192
+                           returns IBDL_ERR_UNSUPPORTED                                       */
   double box;           /* side length of the periodic box, > 0                             */
   double origin[3];     /* lower corner of the box (unused entries ignored)                 */
   int64_t n_points;     /* M ≥ 1                                                           */
@@ -162,9 +163,9 @@ typedef struct {
                            by an FP64 residual restart and does not count)                    */
   int io_on_host;       /* nonzero: U_b and Q are host pointers (copied inside the call)     */
   int residual;         /* IBDL_MIXED: arithmetic of the refinement residual's application,
-                           IBDL_FP64 (0) or IBDL_FP32X2 (float-float, for 2-D grids to 4096²;
-                           other geometries use FP64); the residual's subtraction and norm are
-                           FP64 either way                                                    */
+                           IBDL_FP64 (0) or IBDL_FP32X2 (float-float, for 2-D grids to 4096²
+                           and every 3-D grid; 8192² grids use FP64); the residual's
+                           subtraction and norm are FP64 either way                           */
 } ibdl_solve_opts;
 
 typedef struct {
@@ -205,7 +206,7 @@ ibdl_status ibdl_destroy_geometry(ibdl_geometry* geom);
 
 /* Y = A Q = S*u + ½Q with u = −L⁻¹S̃Q (scalar, Sec. 5.3.2 Eq. "ibdl schur again") or the
  * Stokes velocity of Sec. 6.3.3. Q and Y are device FP64 arrays [c][M] (they may not alias);
- * `precision` (IBDL_FP64, IBDL_FP32, or IBDL_FP32X2 for 2-D geometries) selects the grid
+ * `precision` (IBDL_FP64, IBDL_FP32 or IBDL_FP32X2) selects the grid
  * arithmetic. Asynchronous on `stream`. */
 ibdl_status ibdl_apply(ibdl_geometry* geom, int precision, const double* Q, double* Y, void* stream);
 

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <atomic>
 
+#include "ff.cuh"
 #include "fft.cuh"
 
 namespace ibdl {
@@ -38,6 +39,20 @@ template <>
 struct Traits3<OP3_ADJ_SD> { static constexpr int NIN = 1, NOUT = 3; };     // S W → ∂_m v
 
 enum { G3_INTERP = 0, G3_GRID = 1 };
+
+// Point type of a grid arithmetic: the point tables, the spread's accumulation and the gather's
+// sums. Float-float grids keep FP64 points (the spread accumulates in FP64 and converts each
+// value once before the FFT; the gather sums in FP64), as in 2-D.
+template <typename T>
+struct Prec3 {
+  using PT = T;
+  static __device__ __forceinline__ PT to_pt(T v) { return v; }
+};
+template <>
+struct Prec3<ff> {
+  using PT = double;
+  static __device__ __forceinline__ double to_pt(ff v) { return double(v); }
+};
 constexpr int kThreads3 = 256;
 
 struct Row3Params {
@@ -139,18 +154,19 @@ template <typename T, int OP>
 __global__ void __launch_bounds__(kThreads3) k3_spread_rowfft(Row3Params p) {
   if (p.stop && *p.stop) return;
   constexpr int NIN = Traits3<OP>::NIN;
+  using PT = typename Prec3<T>::PT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = p.n, R = p.R, half = R >> 1, M = p.M;
   const int seqs = NIN * half;
-  const T* phi = static_cast<const T*>(p.phi);
-  const T* dphi = static_cast<const T*>(p.dphi);
-  const T* wsc = static_cast<const T*>(p.wscale);
-  const T* nrm = static_cast<const T*>(p.nrm);
+  const PT* phi = static_cast<const PT*>(p.phi);
+  const PT* dphi = static_cast<const PT*>(p.dphi);
+  const PT* wsc = static_cast<const PT*>(p.wscale);
+  const PT* nrm = static_cast<const PT*>(p.nrm);
   cplx<T>* spec = static_cast<cplx<T>*>(p.spec);
   cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufA = tws + n;
   cplx<T>* bufB = bufA + padded((size_t)seqs * n);
-  T* acc = reinterpret_cast<T*>(bufA);
+  PT* acc = reinterpret_cast<PT*>(bufA);  // (the same bytes per complex element as cplx<T>)
   const int bands = n / R;
   const int z = blockIdx.x / bands, y0 = (blockIdx.x - z * bands) * R;
   const double* pin;
@@ -158,7 +174,7 @@ __global__ void __launch_bounds__(kThreads3) k3_spread_rowfft(Row3Params p) {
   resolve_io3(p, pin, pout);
   if (!p.grid_in)  // jump term: out = ±½·in (the gather adds S*u afterwards); none for grid input
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) pout[i] = p.jump * pin[i];
-  for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = T(0);
+  for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n) * 2; i += blockDim.x) acc[i] = PT(0);
   load_twiddles(tws, static_cast<const cplx<T>*>(p.tw), n);
   __syncthreads();
 
@@ -168,7 +184,7 @@ __global__ void __launch_bounds__(kThreads3) k3_spread_rowfft(Row3Params p) {
       const int rem = t - f * R * n;
       const int lr = rem / n, x = rem - lr * n;
       acc[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)] =
-          T(p.grid_in[(((size_t)f * n + z) * n + y0 + lr) * n + x]);
+          PT(p.grid_in[(((size_t)f * n + z) * n + y0 + lr) * n + x]);
     }
   }
   const Ranges3 rg = band_points3(p.cell_start, n, z, y0, R);
@@ -181,28 +197,36 @@ __global__ void __launch_bounds__(kThreads3) k3_spread_rowfft(Row3Params p) {
     if (lr >= R || az > 3) continue;
     const int i = p.perm[s];
     const int col = (p.base[s] + ax) & (n - 1);
-    const T px = phi[(0 * 4 + ax) * M + s], py = phi[(1 * 4 + ay) * M + s], pz = phi[(2 * 4 + az) * M + s];
-    const T ws = wsc[s];
+    const PT px = phi[(0 * 4 + ax) * M + s], py = phi[(1 * 4 + ay) * M + s], pz = phi[(2 * 4 + az) * M + s];
+    const PT ws = wsc[s];
     const int e = (lr >> 1) * n + col;
     const int odd = lr & 1;
-    const T ppp = px * py * pz;
+    const PT ppp = px * py * pz;
     if (OP == OP3_SCALAR_AN) {
-      const T q = T(pin[i]) * ws;
-      const T gx = dphi[(0 * 4 + ax) * M + s] * py * pz;
-      const T gy = px * dphi[(1 * 4 + ay) * M + s] * pz;
-      const T gz = px * py * dphi[(2 * 4 + az) * M + s];
+      const PT q = PT(pin[i]) * ws;
+      const PT gx = dphi[(0 * 4 + ax) * M + s] * py * pz;
+      const PT gy = px * dphi[(1 * 4 + ay) * M + s] * pz;
+      const PT gz = px * py * dphi[(2 * 4 + az) * M + s];
       atomicAdd(acc + 2 * pidx(e) + odd, q * (nrm[s] * gx + nrm[M + s] * gy + nrm[2 * M + s] * gz));
     } else if (OP == OP3_SCALAR_SD) {
-      const T q = T(pin[i]) * ws * ppp;
+      const PT q = PT(pin[i]) * ws * ppp;
       atomicAdd(acc + 2 * pidx(e) + odd, q * nrm[s]);
       atomicAdd(acc + 2 * pidx(e + half * n) + odd, q * nrm[M + s]);
       atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, q * nrm[2 * M + s]);
     } else {
-      const T wsp = p.trans ? T(1) : ws;  // A*: W with weight Δs/h³; Aᵀ: λ with weight 1
-      atomicAdd(acc + 2 * pidx(e) + odd, T(pin[i]) * wsp * ppp);
+      const PT wsp = p.trans ? PT(1) : ws;  // A*: W with weight Δs/h³; Aᵀ: λ with weight 1
+      atomicAdd(acc + 2 * pidx(e) + odd, PT(pin[i]) * wsp * ppp);
     }
   }
   __syncthreads();
+  if constexpr (!std::is_same<T, PT>::value) {
+    // float-float: each FP64 accumulated value becomes the nearest float-float, in place
+    for (int i = threadIdx.x; i < (int)padded((size_t)seqs * n); i += blockDim.x) {
+      const double2 d = reinterpret_cast<const double2*>(bufA)[i];
+      bufA[i] = mk(ff_from_double(d.x), ff_from_double(d.y));
+    }
+    __syncthreads();
+  }
   const cplx<T>* res = fft_run<T, false>(bufA, bufB, p.log2n, seqs, tws);
   const int nh = n >> 1, lnh = p.log2n - 1;
   for (int t = threadIdx.x; t < seqs * nh; t += blockDim.x) {
@@ -406,12 +430,13 @@ template <typename T, int OP, int GMODE>
 __global__ void __launch_bounds__(kThreads3) k3_rowifft_gather(Row3Params p) {
   if (p.stop && *p.stop) return;
   constexpr int NOUT = Traits3<OP>::NOUT;
+  using PT = typename Prec3<T>::PT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = p.n, R = p.R, half = R >> 1, M = p.M, nh = n >> 1;
   const int seqs = NOUT * half;
-  const T* phi = static_cast<const T*>(p.phi);
-  const T* dphi = static_cast<const T*>(p.dphi);
-  const T* nrm = static_cast<const T*>(p.nrm);
+  const PT* phi = static_cast<const PT*>(p.phi);
+  const PT* dphi = static_cast<const PT*>(p.dphi);
+  const PT* nrm = static_cast<const PT*>(p.nrm);
   cplx<T>* tws = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufA = tws + n;
   cplx<T>* bufB = bufA + padded((size_t)seqs * n);
@@ -427,7 +452,8 @@ __global__ void __launch_bounds__(kThreads3) k3_rowifft_gather(Row3Params p) {
       const int f = t / (R * n);
       const int rem = t - f * R * n;
       const int lr = rem / n, x = rem - lr * n;
-      p.grid[(((size_t)f * n + z) * n + y0 + lr) * n + x] = double(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)]);
+      p.grid[(((size_t)f * n + z) * n + y0 + lr) * n + x] =
+          double(Prec3<T>::to_pt(u[2 * pidx((f * half + (lr >> 1)) * n + x) + (lr & 1)]));
     }
     return;
   }
@@ -444,31 +470,32 @@ __global__ void __launch_bounds__(kThreads3) k3_rowifft_gather(Row3Params p) {
     if (lr >= R || az > 3) continue;
     const int i = p.perm[s];
     const int bx = p.base[s];
-    const T py = phi[(1 * 4 + ay) * M + s], pz = phi[(2 * 4 + az) * M + s];
+    const PT py = phi[(1 * 4 + ay) * M + s], pz = phi[(2 * 4 + az) * M + s];
     const int eb = (lr >> 1) * n, odd = lr & 1;
-    T a0 = 0, a1 = 0, a2 = 0;
+    auto uval = [&](int e) { return Prec3<T>::to_pt(u[2 * pidx(e) + odd]); };
+    PT a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
     for (int ax = 0; ax < 4; ++ax) {
       const int col = (bx + ax) & (n - 1);
-      const T px = phi[(0 * 4 + ax) * M + s];
-      const T v0 = u[2 * pidx(eb + col) + odd];
+      const PT px = phi[(0 * 4 + ax) * M + s];
+      const PT v0 = uval(eb + col);
       if (OP == OP3_ADJ_AN) {
         a0 += v0 * dphi[(0 * 4 + ax) * M + s] * py * pz;
         a1 += v0 * px * dphi[(1 * 4 + ay) * M + s] * pz;
         a2 += v0 * px * py * dphi[(2 * 4 + az) * M + s];
       } else {
-        const T w3 = px * py * pz;
+        const PT w3 = px * py * pz;
         a0 += v0 * w3;
         if (NOUT == 3) {
-          a1 += u[2 * pidx(eb + half * n + col) + odd] * w3;
-          a2 += u[2 * pidx(eb + 2 * half * n + col) + odd] * w3;
+          a1 += uval(eb + half * n + col) * w3;
+          a2 += uval(eb + 2 * half * n + col) * w3;
         }
       }
     }
     if (OP == OP3_ADJ_AN || OP == OP3_ADJ_SD) {
       double val = double(nrm[s]) * double(a0) + double(nrm[M + s]) * double(a1) + double(nrm[2 * M + s]) * double(a2);
       if (OP == OP3_ADJ_SD) val = -val;
-      if (p.trans) val *= double(static_cast<const T*>(p.wscale)[s]);
+      if (p.trans) val *= double(static_cast<const PT*>(p.wscale)[s]);
       atomicAdd(pout + i, val);
     } else {
       atomicAdd(pout + i, double(a0));
@@ -525,6 +552,7 @@ ibdl_status plan_3d(Geometry* g) {
   if (!bit || !(attrs.load(std::memory_order_acquire) & bit)) {
     IBDL_TRY(set_attrs3_all<double>());
     IBDL_TRY(set_attrs3_all<float>());
+    IBDL_TRY(set_attrs3_all<ff>());
     if (bit) attrs.fetch_or(bit, std::memory_order_acq_rel);
   }
   // Work units sized by FFT volume per CTA: R y-rows per row band, C kx columns per y-pass CTA,
@@ -532,10 +560,11 @@ ibdl_status plan_3d(Geometry* g) {
   const int nf = g->nf_in > g->nf_out ? g->nf_in : g->nf_out;
   const int n = g->n;
   auto clampp2 = [](int v, int lo, int hi) { v = v < lo ? lo : (v > hi ? hi : v); int r = 1; while (r * 2 <= v) r *= 2; return r; };
-  for (int pi = 0; pi < 2; ++pi) {
+  for (int pi = 0; pi < 3; ++pi) {
     const bool f32 = pi == 1;
-    // FP32 CTAs take about 2048 complex elements, FP64 about 1024 (measured on the 128³ sphere);
-    // R ≤ n/2 keeps the wrapped band rows [y0 − 3, y0 + R) distinct (no point counted twice)
+    // FP32 CTAs take about 2048 complex elements, FP64 (and float-float, the same element size)
+    // about 1024 (measured on the 128³ sphere); R ≤ n/2 keeps the wrapped band rows
+    // [y0 − 3, y0 + R) distinct (no point counted twice)
     const int target = f32 ? 2048 : 1024;
     int R = clampp2(2 * (target / (n * nf)), 2, n / 2);
     int C = clampp2(target / (n * nf), 1, n / 2);
@@ -564,12 +593,17 @@ static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStrea
                            const int* idx = nullptr, int vstride = 0, int trans = 0, bool laplace = false,
                            const double* grid_in = nullptr) {
   constexpr int NIN = Traits3<OP>::NIN, NOUT = Traits3<OP>::NOUT;
-  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  constexpr bool is_ff = std::is_same<T, ff>::value;
+  const int pi = std::is_same<T, float>::value ? 1 : (is_ff ? 2 : 0);
   const int R = g->rows_per_cta[pi], C = g->cols_per_cta[pi], Cz = g->zcols_per_cta[pi];
   if (R == 0 || C == 0 || Cz == 0)
     return fail(IBDL_ERR_UNSUPPORTED, "3-D grid too large for the shared-memory FFT at this precision");
   const int n = g->n;
-  const PointTable<T>& tb = *reinterpret_cast<const PointTable<T>*>(pi ? (const void*)&g->t32 : (const void*)&g->t64);
+  if (is_ff && !g->twff) return fail(IBDL_ERR_UNSUPPORTED, "this geometry has no float-float tables");
+  // point tables: FP32 for FP32 grids, FP64 for FP64 and float-float grids
+  using PT = typename Prec3<T>::PT;
+  const PointTable<PT>& tb =
+      *reinterpret_cast<const PointTable<PT>*>(pi == 1 ? (const void*)&g->t32 : (const void*)&g->t64);
   Row3Params rp;
   rp.n = n;
   rp.log2n = __builtin_ctz(n);
@@ -585,7 +619,7 @@ static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStrea
   rp.in = in;
   rp.out = out;
   rp.spec = g->spec;
-  rp.tw = pi ? (const void*)g->tw32 : (const void*)g->tw64;
+  rp.tw = pi == 1 ? (const void*)g->tw32 : (pi == 2 ? (const void*)g->twff : (const void*)g->tw64);
   rp.stop = stop;
   rp.grid = grid;
   rp.idx = idx;
@@ -600,13 +634,13 @@ static ibdl_status run_op3(Geometry* g, const double* in, double* out, cudaStrea
   cp.lc = __builtin_ctz(C);
   cp.lam = laplace ? 0.0 : g->lambda;
   cp.scale = 1.0 / ((double)n * n * n);
-  cp.lap1 = pi ? (const void*)g->lap32 : (const void*)g->lap64;
-  cp.der1 = pi ? (const void*)g->der32 : (const void*)g->der64;
+  cp.lap1 = pi == 1 ? (const void*)g->lap32 : (pi == 2 ? (const void*)g->lapff : (const void*)g->lap64);
+  cp.der1 = pi == 1 ? (const void*)g->der32 : (pi == 2 ? (const void*)g->derff : (const void*)g->der64);
   cp.spec = g->spec;
   cp.tw = rp.tw;
   cp.stop = stop;
   const int rows_grid = n * (n / R), col_grid = n * ((n / 2) / C), z_grid = (n / 2 + 1) * ((n / 2) / Cz);
-  const int st0 = pi ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
+  const int st0 = pi == 1 ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
   k3_spread_rowfft<T, OP><<<rows_grid, kThreads3, smem_rows3<T>(n, NIN, R), s>>>(rp);
   if (g->timing) timing_mark(g, s, st0);
@@ -642,12 +676,14 @@ static ibdl_status apply3_t(Geometry* g, const double* Q, double* Y, cudaStream_
 
 ibdl_status apply_3d(Geometry* g, int precision, const double* Q, double* Y, cudaStream_t s, const int* stop,
                      int op) {
+  if (precision == IBDL_FP32X2) return apply3_t<ff>(g, Q, Y, s, stop, nullptr, nullptr, 0, op);
   return precision == IBDL_FP32 ? apply3_t<float>(g, Q, Y, s, stop, nullptr, nullptr, 0, op)
                                 : apply3_t<double>(g, Q, Y, s, stop, nullptr, nullptr, 0, op);
 }
 
 ibdl_status apply_3d_indexed(Geometry* g, int precision, double* V, const int* idx, int nd, cudaStream_t s,
                              const int* stop, int op) {
+  if (precision == IBDL_FP32X2) return apply3_t<ff>(g, V, V, s, stop, nullptr, idx, nd, op);
   return precision == IBDL_FP32 ? apply3_t<float>(g, V, V, s, stop, nullptr, idx, nd, op)
                                 : apply3_t<double>(g, V, V, s, stop, nullptr, idx, nd, op);
 }

@@ -425,11 +425,10 @@ ibdl_status create_geometry(const ibdl_geometry_desc* d, cudaStream_t s, Geometr
     GTRY(dalloc(&g->der64, sizeof(double) * n));
     GTRY(dalloc(&g->lap32, sizeof(float) * n));
     GTRY(dalloc(&g->der32, sizeof(float) * n));
-    if (dim == 2) {
-      GTRY(dalloc(&g->twff, 2 * sizeof(ff) * n));
-      GTRY(dalloc(&g->lapff, sizeof(ff) * n));
-      GTRY(dalloc(&g->derff, sizeof(ff) * n));
-    }
+    // float-float twiddles and symbols (2-D and 3-D)
+    GTRY(dalloc(&g->twff, 2 * sizeof(ff) * n));
+    GTRY(dalloc(&g->lapff, sizeof(ff) * n));
+    GTRY(dalloc(&g->derff, sizeof(ff) * n));
     GTRY(dalloc(&g->tmp_m, sizeof(double) * (g->ncomp * M + g->ncomp)));  // room for ū / constraint rows
 
     const int tb = 256;

@@ -724,7 +724,8 @@ ibdl_status solve_impl(Geometry* g, const double* Ub, double* Q, const ibdl_solv
     GmresState* st = reinterpret_cast<GmresState*>(g->gm);
     HostStatus* hs = reinterpret_cast<HostStatus*>(g->host_status);
     // the residual's application: float-float (2-D) or FP64; its subtraction and norm are FP64
-    const int res_prec = o->residual == IBDL_FP32X2 && g->dim == 2 && g->n <= 4096 ? IBDL_FP32X2 : IBDL_FP64;
+    // (float-float grids are built to 4096² in 2-D and for every 3-D size)
+    const int res_prec = o->residual == IBDL_FP32X2 && (g->dim == 3 || g->n <= 4096) ? IBDL_FP32X2 : IBDL_FP64;
     int used = 0, refined = 0;
     const double* rhs = b;
     double bn = 0.0;

@@ -127,7 +127,7 @@ struct Geometry {
   // per precision slot (0 = fp64, 1 = fp32, 2 = float-float, 2-D only)
   int rows_per_cta[3];   // band height R for the row kernels
   int cols_per_cta[3];   // kx columns per CTA in the column kernels (3-D: the y passes)
-  int zcols_per_cta[2];  // 3-D: kx columns per CTA in the z pass
+  int zcols_per_cta[3];  // 3-D: kx columns per CTA in the z pass
   size_t smem_row[2], smem_col[2], smem_row_inv[2];
   int threads[3];        // 2-D: least threads per CTA of the row kernels (0: none)
   int split[3];          // 2-D: one field per launch (the fields' row bands or columns do not fit
@@ -309,7 +309,6 @@ inline int geom_nd(const Geometry* g) { return (int)(g->ncomp * g->M) + g->naug;
 
 inline ibdl_status apply_any(Geometry* g, int precision, const double* Q, double* Y,
                              cudaStream_t s, const int* stop_flag, int op = OPK_A) {
-  if (precision == IBDL_FP32X2 && g->dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "float-float applications are 2-D only");
   return g->dim == 2 ? apply_2d(g, precision, Q, Y, s, stop_flag, op)
                      : apply_3d(g, precision, Q, Y, s, stop_flag, op);
 }

@@ -356,7 +356,7 @@ def _sphere_problem(N, delta="cos", dipole="analytic", lam=0.0, M=None):
 
 @pytest.mark.parametrize("N,delta,dipole,lam", [(16, "cos", "analytic", 0.0), (32, "sqrt", "analytic", 5.0),
                                                 (32, "cos", "spectral_div", 0.0), (16, "sqrt", "spectral_div", 2.0)])
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32x2", 1e-12), ("fp32", 2e-5)])
 def test_3d_apply(N, delta, dipole, lam, precision, tol):
     p = _sphere_problem(N, delta, dipole, lam)
     g = _geom(p)
@@ -364,6 +364,9 @@ def test_3d_apply(N, delta, dipole, lam, precision, tol):
     q = np.random.default_rng(N).standard_normal(p.bd.M)
     y = g.apply(torch.from_numpy(q).cuda(), precision=precision).cpu().numpy()
     assert _rel(y, O.apply(og, q)) < tol
+    # the Euclidean transpose Aᵀ = W A* W⁻¹ in the same arithmetic
+    z = g.apply_transpose(torch.from_numpy(q).cuda(), precision=precision).cpu().numpy()
+    assert _rel(z, O.transpose_apply(og, q)) < tol
 
 
 def test_3d_field_and_adjoint():
@@ -388,15 +391,19 @@ def test_3d_solve_sphere():
     assert _rel(Q.cpu().numpy(), ref.x) < 1e-10
     Qm, infom, _ = g.solve(torch.from_numpy(p.Ub.reshape(-1)).cuda(), rtol=1e-10, precision="mixed")
     assert _rel(Qm.cpu().numpy(), ref.x) < 1e-8
+    assert infom["fp32x2_applies"] > 0 and infom["fp64_applies"] == 0  # the float-float residual
 
 
 def test_3d_full_size_apply():
-    """The 128³ sphere workload with 12 000 Fibonacci points: one FP64 application."""
+    """The 128³ sphere workload with 12 000 Fibonacci points: one FP64 and one float-float
+    application."""
     p = I.sphere_poisson()
     g = _geom(p)
     q = np.random.default_rng(11).standard_normal(p.bd.M)
-    y = g.apply(torch.from_numpy(q).cuda()).cpu().numpy()
-    assert _rel(y, O.apply(O.geometry_from_problem(p), q)) < 1e-12
+    ref = O.apply(O.geometry_from_problem(p), q)
+    for prec in ("fp64", "fp32x2"):
+        y = g.apply(torch.from_numpy(q).cuda(), precision=prec).cpu().numpy()
+        assert _rel(y, ref) < 1e-12
 
 
 @pytest.mark.parametrize("pde", ["scalar", "stokes"])
