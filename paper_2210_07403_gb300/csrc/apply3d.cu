@@ -47,6 +47,13 @@ ibdl_status plan_3d(Geometry* g) {
     int R = clampp2(2 * (target / (n * nf)), 2, n / 2);
     int C = clampp2(target / (n * nf), 1, n / 2);
     int Cz = clampp2(target / 2 / (n * nf), 1, n / 2);
+    // the column passes interleave a pass's kThreads3/(n/8) sequences across the threads of each
+    // warp: fewer sequences than that leave every warp partly idle, and an FP64 warp instruction
+    // costs its issue slot whatever the number of active lanes, so a y pass holds at least
+    // that many columns (fields × C) and a z pass that many (fields × 2 × Cz)
+    const int sp = kThreads3 / (n / 8);
+    C = std::max(C, clampp2(sp / nf, 1, n / 2));
+    Cz = std::max(Cz, clampp2(sp / (2 * nf), 1, n / 2));
     if (const char* e = getenv("IBDL_PLAN3_R")) R = clampp2(atoi(e), 2, n / 2);
     if (const char* e = getenv("IBDL_PLAN3_C")) C = clampp2(atoi(e), 1, n / 2);
     if (const char* e = getenv("IBDL_PLAN3_CZ")) Cz = clampp2(atoi(e), 1, n / 2);

@@ -104,21 +104,40 @@ struct Cfg3 {
   using TW = std::conditional_t<TWR, TwRegs<T, L>, TwTable<T, L>>;
 };
 
-template <typename T, bool INV, int L, class LD, class ST>
+// Stride (elements) between the exchange buffers of sequences interleaved across threads: the
+// padded sequence rounded up to ≡ max(1, w/W) (mod w), w = 16 for 8-byte and 8 for 16-byte
+// elements, W = min(32, the sequences of a pass) interleaved in a warp: the rule of the 2-D column
+// groups, which puts the warp's sequences in different shared-memory banks.
+__host__ __device__ constexpr int seq_stride3(int L, int esize) {
+  const int pn = (1 << L) + (1 << L) / 8;
+  const int sp = kThreads3 / ((1 << L) / 8);
+  const int W = sp < 32 ? sp : 32;
+  const int w = esize == 8 ? 16 : 8;
+  const int t = (w / W > 1 ? w / W : 1) % w;
+  return pn + (((t - pn) % w) + w) % w;
+}
+
+// IL: the sequences of a pass interleaved across threads (sequence = thread mod SP, lane = thread /
+// SP), each exchanging through buf + b·seq_stride3: consecutive threads then touch the same
+// element of consecutive sequences, which the column passes' global accesses want (adjacent kx
+// columns are adjacent in memory). Otherwise sequence b is thread / QT, at buf + b·(n + n/8).
+template <typename T, bool INV, int L, bool IL = false, class LD, class ST>
 __device__ __forceinline__ void fft3_run(cplx<T>* buf, int nseq, const cplx<T>* __restrict__ twg, const LD& ld,
                                          const ST& st) {
   using CF = Cfg3<T, L>;
   using F = F8<L, CF::V>;
   constexpr int V = CF::V, QT = CF::QT, Q = F::Q, SP = kThreads3 / QT;
   static_assert(kThreads3 % QT == 0, "whole sequences per pass");
-  const int sl = (int)threadIdx.x / QT, j0 = (int)threadIdx.x - sl * QT;
+  constexpr int PS = IL ? seq_stride3(L, (int)sizeof(cplx<T>)) : F::PN;
+  const int sl = IL ? (int)threadIdx.x % SP : (int)threadIdx.x / QT;
+  const int j0 = IL ? (int)threadIdx.x / SP : (int)threadIdx.x - sl * QT;
   typename CF::TW tw[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) tw[v].load(twg, j0 + v * QT);
   for (int b0 = 0; b0 < nseq; b0 += SP) {
     const int b = b0 + sl;
     const bool act = b < nseq;
-    cplx<T>* sb = buf + (size_t)(act ? b : 0) * F::PN;
+    cplx<T>* sb = buf + (size_t)(act ? b : 0) * PS;
     cplx<T> x[1][V][8];
     if (act) {
 #pragma unroll
@@ -268,34 +287,54 @@ __global__ void __launch_bounds__(kThreads3) k3_spread_rowfft(Row3Params p) {
     }
   }
   const Ranges3 rg = band_points3(p.cell_start, n, z, y0, R);
-  for (int t = threadIdx.x; t < (p.grid_in ? 0 : rg.total * 16); t += blockDim.x) {
-    const int s = rg.at(t >> 4);
-    const int ay = (t >> 2) & 3, ax = t & 3;
+  // one thread per (point, stencil row ay): the point's plane and row weights and its density are
+  // read once, then the four nodes along x of that row are added
+  for (int t = threadIdx.x; t < (p.grid_in ? 0 : rg.total * 4); t += blockDim.x) {
+    const int s = rg.at(t >> 2);
+    const int ay = t & 3;
     const int az = (z - p.base[2 * M + s]) & (n - 1);  // the one stencil plane at z (0..3)
     const int row = (p.base[M + s] + ay) & (n - 1);
     const int lr = (row - y0) & (n - 1);
     if (lr >= R || az > 3) continue;
     const int i = p.perm[s];
-    const int col = (p.base[s] + ax) & (n - 1);
-    const PT px = phi[(0 * 4 + ax) * M + s], py = phi[(1 * 4 + ay) * M + s], pz = phi[(2 * 4 + az) * M + s];
+    const int bx = p.base[s];
+    const PT py = phi[(1 * 4 + ay) * M + s], pz = phi[(2 * 4 + az) * M + s];
     const PT ws = wsc[s];
-    const int e = (lr >> 1) * n + col;
+    const int eb = (lr >> 1) * n;
     const int odd = lr & 1;
-    const PT ppp = px * py * pz;
+    const PT qv = PT(pin[i]);
+    PT c0 = 0, cy = 0, cz = 0, n0 = 0, n1 = 0, n2 = 0;
     if (OP == OP3_SCALAR_AN) {
-      const PT q = PT(pin[i]) * ws;
-      const PT gx = dphi[(0 * 4 + ax) * M + s] * py * pz;
-      const PT gy = px * dphi[(1 * 4 + ay) * M + s] * pz;
-      const PT gz = px * py * dphi[(2 * 4 + az) * M + s];
-      atomicAdd(acc + 2 * pidx(e) + odd, q * (nrm[s] * gx + nrm[M + s] * gy + nrm[2 * M + s] * gz));
+      // n·∇δ_h = n_x φ'(x)φ(y)φ(z) + n_y φ(x)φ'(y)φ(z) + n_z φ(x)φ(y)φ'(z): per node along x,
+      // c0·φ'(x) + (cy + cz)·φ(x)
+      n0 = nrm[s];
+      n1 = nrm[M + s];
+      n2 = nrm[2 * M + s];
+      c0 = qv * ws * n0 * py * pz;
+      cy = qv * ws * n1 * dphi[(1 * 4 + ay) * M + s] * pz;
+      cz = qv * ws * n2 * py * dphi[(2 * 4 + az) * M + s];
     } else if (OP == OP3_SCALAR_SD) {
-      const PT q = PT(pin[i]) * ws * ppp;
-      atomicAdd(acc + 2 * pidx(e) + odd, q * nrm[s]);
-      atomicAdd(acc + 2 * pidx(e + half * n) + odd, q * nrm[M + s]);
-      atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, q * nrm[2 * M + s]);
+      n0 = nrm[s];
+      n1 = nrm[M + s];
+      n2 = nrm[2 * M + s];
+      c0 = qv * ws * py * pz;
     } else {
-      const PT wsp = p.trans ? PT(1) : ws;  // A*: W with weight Δs/h³; Aᵀ: λ with weight 1
-      atomicAdd(acc + 2 * pidx(e) + odd, PT(pin[i]) * wsp * ppp);
+      c0 = qv * (p.trans ? PT(1) : ws) * py * pz;  // A*: W with weight Δs/h³; Aᵀ: λ with weight 1
+    }
+#pragma unroll
+    for (int ax = 0; ax < 4; ++ax) {
+      const int e = eb + ((bx + ax) & (n - 1));
+      const PT px = phi[(0 * 4 + ax) * M + s];
+      if (OP == OP3_SCALAR_AN) {
+        atomicAdd(acc + 2 * pidx(e) + odd, c0 * dphi[(0 * 4 + ax) * M + s] + (cy + cz) * px);
+      } else if (OP == OP3_SCALAR_SD) {
+        const PT q = c0 * px;
+        atomicAdd(acc + 2 * pidx(e) + odd, q * n0);
+        atomicAdd(acc + 2 * pidx(e + half * n) + odd, q * n1);
+        atomicAdd(acc + 2 * pidx(e + 2 * half * n) + odd, q * n2);
+      } else {
+        atomicAdd(acc + 2 * pidx(e) + odd, c0 * px);
+      }
     }
   }
   __syncthreads();
@@ -356,8 +395,8 @@ __global__ void __launch_bounds__(kThreads3) k3_ypass(Col3Params p) {
   const int z = blockIdx.x / groups, k0 = (blockIdx.x - z * groups) * C;
   cplx<T>* bufA = reinterpret_cast<cplx<T>*>(smem_raw);
   const YColumnIO<T> io{static_cast<cplx<T>*>(p.spec), n, nh, z, k0, p.lc, C};
-  fft3_run<T, INV, L>(bufA, p.nf * C, static_cast<const cplx<T>*>(p.tw), GlobLd3<YColumnIO<T>>{io},
-                      GlobSt3<YColumnIO<T>>{io});
+  fft3_run<T, INV, L, true>(bufA, p.nf * C, static_cast<const cplx<T>*>(p.tw), GlobLd3<YColumnIO<T>>{io},
+                            GlobSt3<YColumnIO<T>>{io});
 }
 
 // ------------------------------------------------------------------------------------------
@@ -414,7 +453,8 @@ __global__ void __launch_bounds__(kThreads3) k3_zpass(Col3Params p) {
   const int ky1 = pair, ky2 = (n - pair) & (n - 1);
   const int nq = ky1 == ky2 ? 1 : 2;  // y-frequency columns in this CTA
   cplx<T>* bufA = reinterpret_cast<cplx<T>*>(smem_raw);
-  T* lap1 = reinterpret_cast<T*>(bufA + padded((size_t)NMAX * 2 * C * n));
+  constexpr int PS = seq_stride3(L, (int)sizeof(cplx<T>));  // sequences interleaved (fft3_run)
+  T* lap1 = reinterpret_cast<T*>(bufA + (size_t)NMAX * 2 * C * PS);
   T* der1 = lap1 + n;
   const cplx<T>* twg = static_cast<const cplx<T>*>(p.tw);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -425,11 +465,11 @@ __global__ void __launch_bounds__(kThreads3) k3_zpass(Col3Params p) {
   const ZColumnIO<T> io{static_cast<cplx<T>*>(p.spec), n, nh, ky1, ky2, k0, lc, C};
   // with one column (ky = −ky) only the q = 0 sequences exist: sequence index bi maps to
   // (f·2 + 0)·C + c, so transform all 2·C slots per field and ignore q = 1 (it aliases q = 0)
-  fft3_run<T, false, L>(bufA, NIN * 2 * C, twg, GlobLd3<ZColumnIO<T>>{io}, SmemSt3<T>());
+  fft3_run<T, false, L, true>(bufA, NIN * 2 * C, twg, GlobLd3<ZColumnIO<T>>{io}, SmemSt3<T>());
   __syncthreads();
   cplx<T>* res = bufA;
   const T lam = T(p.lam), scale = T(p.scale);
-  auto at = [&](int f, int q, int c, int kz) { return pidx((((f * 2 + q) << lc) + c) * n + kz); };
+  auto at = [&](int f, int q, int c, int kz) { return (((f * 2 + q) << lc) + c) * PS + ppos(kz); };
   for (int t = threadIdx.x; t < nq * C * n; t += blockDim.x) {
     const int kz = t & (n - 1);
     const int qc = t >> L;
@@ -479,7 +519,7 @@ __global__ void __launch_bounds__(kThreads3) k3_zpass(Col3Params p) {
     }
   }
   __syncthreads();
-  fft3_run<T, true, L>(bufA, NOUT * 2 * C, twg, SmemLd3<T>(), GlobSt3<ZColumnIO<T>>{io});
+  fft3_run<T, true, L, true>(bufA, NOUT * 2 * C, twg, SmemLd3<T>(), GlobSt3<ZColumnIO<T>>{io});
 }
 
 // ------------------------------------------------------------------------------------------
@@ -592,11 +632,12 @@ __host__ __device__ constexpr size_t smem_rows3(int n, int nf, int R) {
 }
 template <typename T>
 __host__ __device__ constexpr size_t smem_y3(int n, int nf, int C) {
-  return padded((size_t)nf * C * n) * sizeof(cplx<T>);
+  return (size_t)nf * C * seq_stride3(__builtin_ctz(n), (int)sizeof(cplx<T>)) * sizeof(cplx<T>);
 }
 template <typename T>
 __host__ __device__ constexpr size_t smem_z3(int n, int nf, int C) {
-  return padded((size_t)nf * 2 * C * n) * sizeof(cplx<T>) + 2 * n * sizeof(T);
+  return (size_t)nf * 2 * C * seq_stride3(__builtin_ctz(n), (int)sizeof(cplx<T>)) * sizeof(cplx<T>) +
+         2 * n * sizeof(T);
 }
 
 // Opt a kernel in to the full dynamic shared memory once per device (a per-device bit records it;
