@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -19,8 +20,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libibdl.so")
-# every translation unit in csrc/: the host and driver units plus one unit per 2-D grid size
-# (apply2d_n*.cu) and per batched operator family (apply2d_batch_*.cu), compiled in parallel
+# every translation unit in csrc/: the host and driver units plus the per-size kernel units
+# (apply2d_n*.cu: one per 2-D grid size and precision, or both precisions for the small sizes;
+# apply3d_n*.cu: one per 3-D grid size), compiled in parallel
 SOURCES = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
@@ -63,8 +65,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    # the slowest units first, so that they do not start last
-    order = sorted(SOURCES, key=lambda f: (not f.startswith("apply"), f))
+    # the slowest units first, so that they do not start last: the per-size kernel units by
+    # decreasing grid size, then the other kernel units, then the host units
+    def cost(f):
+        m = re.match(r"apply[23]d_n(\d+)", f)
+        return (not f.startswith("apply"), -(int(m.group(1)) ** (2 if f.startswith("apply2d") else 1.5)) if m else 0, f)
+
+    order = sorted(SOURCES, key=cost)
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(SOURCES), os.cpu_count() or 1))) as ex:
         results = list(ex.map(compile_one, order))
     if verbose:

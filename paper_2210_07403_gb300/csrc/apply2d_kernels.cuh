@@ -680,12 +680,14 @@ __device__ __forceinline__ void colpass_body(const ColParams<T>& p, int unit, un
     }
   }
   // The stop flag is final before the wait: it is written by the GMRES step (or the cycle start)
-  // at least two kernels back, which has completed once the direct predecessor passed its own
-  // wait and triggered this launch. So no dependent load follows the wait.
+  // at least two kernels back, which has completed once the direct predecessor (the spread,
+  // which always waits) passed its own wait and triggered this launch. So no dependent load
+  // follows the wait, and a slot after the stop returns without waiting: the kernels after it
+  // only read the same final flag.
   const bool stopped = p.stop && *p.stop;
+  if (stopped) return;
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
-  if (stopped) return;
 
   if constexpr (NIN == 1 && NOUT == 1) {
     // one field in and out: the symbol is applied to the registers between the transforms
@@ -845,7 +847,7 @@ template <typename T, int L>
 __device__ __forceinline__ void colpass1_load(const ColParams<T>& p, int unit, int c, int j0, bool active,
                                               cplx<T> (&x)[1][Cfg2<T, L, 1>::V][8]) {
   using CF = Cfg2<T, L, 1>;
-  constexpr int V = CF::V, QT = CF::QT, Q = (1 << L) / 8;
+  constexpr int V = CF::V, QT = CF::QT;
   const int kx = unit * p.C + c;
   if (active) {
 #pragma unroll
@@ -957,7 +959,7 @@ __global__ void __launch_bounds__(kMaxThreads2d) k_colfft(ColParams<T> p, int fi
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using CF = Cfg2<T, L, 1>;
   using F = F8<L, CF::V>;
-  constexpr int V = CF::V, QT = CF::QT, Q = F::Q;
+  constexpr int V = CF::V, QT = CF::QT;
   const int C = p.C, R = p.R, kx0 = blockIdx.x * C;
   int g, c, j0;
   col_lane_2d<QT>(C, g, c, j0);
@@ -968,9 +970,9 @@ __global__ void __launch_bounds__(kMaxThreads2d) k_colfft(ColParams<T> p, int fi
 #pragma unroll
   for (int v = 0; v < V; ++v) tw[v].load(p.tw, j0 + v * QT);
   const bool stopped = p.stop && *p.stop;  // final before the wait (see the column pass)
+  if (stopped) return;
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();
-  if (stopped) return;
   cplx<T> x[1][V][8];
   if (active) {
 #pragma unroll
@@ -994,10 +996,10 @@ template <typename T, int OP, int L>
 __global__ void __launch_bounds__(256) k_symbol2d(ColParams<T> p) {
   constexpr int NIN = Traits<OP>::NIN, NOUT = Traits<OP>::NOUT;
   constexpr int n = 1 << L, nh = n / 2;
-  const bool stopped = p.stop && *p.stop;
+  const bool stopped = p.stop && *p.stop;  // final before the wait (see the column pass)
+  if (stopped) return;
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();
-  if (stopped) return;
   const int R = p.R;
   const size_t fstride = (size_t)n * nh;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * nh; idx += gridDim.x * blockDim.x) {
@@ -1400,14 +1402,15 @@ __device__ __forceinline__ void rowifft_gather_body(const RowParams<T>& p, int u
   GatherItem<PT> it0 = {};
   if (PF && (int)threadIdx.x < nitems) it0 = gather_item(p, pr, threadIdx.x, r0);
   // the stop flag and the Krylov index (the output column) are final before the wait: the GMRES
-  // step that writes them is three kernels back (see the column pass)
+  // step that writes them is three kernels back and completed before the column pass was
+  // launched (see the column pass)
   const bool stopped = p.stop && *p.stop;
+  if (stopped) return;
   const double* pin;
   double* pout;
   resolve_io(p, pin, pout);
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();  // after the wait (see the spread kernel)
-  if (stopped) return;
 
   // inverse FFT of every (field, row pair) sequence, its first stage fed from the half spectra
 #pragma unroll

@@ -1,6 +1,7 @@
-// Kernels of the two-dimensional operator for the 2048² grid (every operator, both precisions).
+// Kernels of the two-dimensional operator for the 2048² grid in FP32 (every operator); the FP64
+// kernels of this size are in apply2d_n2048_fp64.cu, so the two compile in parallel.
 #include "apply2d_launch.cuh"
 
 namespace ibdl {
-IBDL_INSTANTIATE_2D(11)
+IBDL_INSTANTIATE_2D_T(float, 11)
 }  // namespace ibdl

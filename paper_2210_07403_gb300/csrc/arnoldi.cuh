@@ -229,7 +229,9 @@ __device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, in
   // application has completed)
   if (j < 0) j = st->k;
   const bool skip = st->stop || j >= st->kmax || j >= m;
-  if (!skip) {
+  // a slot after the stop: return without waiting (the kernels after it read the same final state)
+  if (skip) return -1;
+  {
     if (STAGED)
       for (int q = tid; q < (j + 1) * cnt; q += ATH) {
         const int i = q / cnt, e = q - i * cnt;
@@ -253,7 +255,6 @@ __device__ __forceinline__ int arnoldi_body(GmresState* st, double* V, int j, in
   }
   cudaGridDependencySynchronize();  // programmatic launch: wait for the application
   cudaTriggerProgrammaticLaunchCompletion();
-  if (skip) return -1;
   double* w = V + (size_t)(j + 1) * nd + lo;
   for (int e = tid; e < cnt; e += ATH) ws[e] = w[e];
   __syncthreads();
