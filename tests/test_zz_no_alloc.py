@@ -106,3 +106,61 @@ def test_noalloc_rejects_oversized_problem(ibdl):
                                         ctypes.c_void_p(y.data_ptr()), None)
     assert st == ibdl.IBDL_ERR_INVALID_ARG
     del keep
+
+
+def test_noalloc_in_cuda_graph(ibdl):
+    """The call captured into a CUDA graph (its use case: a caller whose loop is one captured
+    graph), then replayed with new densities written into the same input buffer. Each replay
+    rebuilds the point tables and applies the operator; its result is compared with the regular
+    application and the FP64 oracle. Neither torch's allocator nor the driver's free-memory count
+    may change over the replays."""
+    from oracle import ibdl_oracle as O
+    from paper_2210_07403_gb300 import Geometry
+
+    dev = torch.device("cuda", 0)
+    p = I.star_stokes(256, 400)
+    geom = Geometry.from_problem(p)
+    og = O.geometry_from_problem(p)
+    d, keep = _desc(ibdl, p, dev)
+    lib = ibdl.load()
+    nd = p.ncomp * p.bd.M
+    q = torch.zeros(nd, dtype=torch.float64, device=dev)
+    y = torch.zeros_like(q)
+    s = torch.cuda.Stream()
+
+    def call(stream_handle):
+        return lib.ibdl_apply_noalloc(ctypes.byref(d), ibdl.IBDL_FP32, ctypes.c_void_p(q.data_ptr()),
+                                      ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(stream_handle))
+
+    # the first call outside any capture (its one-time set-up makes no stream call)
+    assert call(s.cuda_stream) == ibdl.IBDL_OK, ibdl.ibdl_last_error()
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s, capture_error_mode="thread_local"):
+        st = call(s.cuda_stream)
+    assert st == ibdl.IBDL_OK, ibdl.ibdl_last_error()
+
+    rng = np.random.default_rng(7)
+    qs = [rng.standard_normal(nd) for _ in range(4)]
+    refs = [geom.apply(torch.from_numpy(qh).to(dev), precision="fp32").cpu().numpy() for qh in qs]
+    torch.cuda.synchronize()
+
+    def replay(qh):
+        q.copy_(torch.from_numpy(qh))
+        graph.replay()
+        return y.cpu().numpy()
+
+    replay(qs[0])  # the first replay uploads the graph
+    torch.cuda.synchronize()
+    alloc0, free0 = torch.cuda.memory_allocated(dev), torch.cuda.mem_get_info(dev)[0]
+    outs = [replay(qh) for qh in qs[1:]]
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated(dev) == alloc0
+    assert torch.cuda.mem_get_info(dev)[0] == free0
+    for qh, yr, yg in zip(qs[1:], refs[1:], outs):
+        assert np.linalg.norm(yg - yr) / np.linalg.norm(yr) < 2e-5
+        yo = O.apply(og, qh)
+        assert np.abs(yg - yo).max() < 2e-5 * np.abs(yo).max()
+    del graph
+    geom.close()
+    del keep
