@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <utility>
 
 #include "ff.cuh"
 #include "fft.cuh"
@@ -253,6 +254,10 @@ __device__ __forceinline__ Ranges3 band_points3(const int* cell_start, int n, in
 // ------------------------------------------------------------------------------------------
 template <typename T, int OP, int L>
 __global__ void __launch_bounds__(kThreads3) k3_spread_rowfft(Row3Params p) {
+  // programmatic launch: wait for the previous kernel, then let the next one launch; a GMRES
+  // cycle's stop flag is read after the wait (the step just before may have written it)
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
   if (p.stop && *p.stop) return;
   constexpr int NIN = Traits3<OP>::NIN;
   constexpr int n = 1 << L;
@@ -387,6 +392,10 @@ struct YColumnIO {
 
 template <typename T, bool INV, int L>
 __global__ void __launch_bounds__(kThreads3) k3_ypass(Col3Params p) {
+  // programmatic launch: wait for the previous kernel, then let the next one launch; a GMRES
+  // cycle's stop flag is read after the wait (the step just before may have written it)
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
   if (p.stop && *p.stop) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int n = 1 << L, nh = n >> 1;
@@ -441,6 +450,10 @@ __device__ __forceinline__ void symbol3(const T* lap1, const T* der1, T lam, T s
 
 template <typename T, int OP, int L>
 __global__ void __launch_bounds__(kThreads3) k3_zpass(Col3Params p) {
+  // programmatic launch: wait for the previous kernel, then let the next one launch; a GMRES
+  // cycle's stop flag is read after the wait (the step just before may have written it)
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
   if (p.stop && *p.stop) return;
   constexpr int NIN = Traits3<OP>::NIN;
   constexpr int NOUT = Traits3<OP>::NOUT;
@@ -548,6 +561,10 @@ struct RowZLoad3 {
 
 template <typename T, int OP, int GMODE, int L>
 __global__ void __launch_bounds__(kThreads3) k3_rowifft_gather(Row3Params p) {
+  // programmatic launch: wait for the previous kernel, then let the next one launch; a GMRES
+  // cycle's stop flag is read after the wait (the step just before may have written it)
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
   if (p.stop && *p.stop) return;
   constexpr int NOUT = Traits3<OP>::NOUT;
   using PT = typename Prec3<T>::PT;
@@ -631,11 +648,11 @@ __host__ __device__ constexpr size_t smem_rows3(int n, int nf, int R) {
   return padded((size_t)nf * (R / 2) * n) * sizeof(cplx<T>);
 }
 template <typename T>
-__host__ __device__ constexpr size_t smem_y3(int n, int nf, int C) {
+constexpr size_t smem_y3(int n, int nf, int C) {  // host side (launch shapes)
   return (size_t)nf * C * seq_stride3(__builtin_ctz(n), (int)sizeof(cplx<T>)) * sizeof(cplx<T>);
 }
 template <typename T>
-__host__ __device__ constexpr size_t smem_z3(int n, int nf, int C) {
+constexpr size_t smem_z3(int n, int nf, int C) {  // host side (launch shapes)
   return (size_t)nf * 2 * C * seq_stride3(__builtin_ctz(n), (int)sizeof(cplx<T>)) * sizeof(cplx<T>) +
          2 * n * sizeof(T);
 }
@@ -656,6 +673,33 @@ inline cudaError_t opt_in_smem3(K kernel, std::atomic<unsigned long long>& done)
 
 // The five kernels of one application at n = 2^L: rows R per band, C kx columns per y pass, Cz per
 // z pass; `grid` selects the grid output of the last kernel.
+// Programmatic dependent launch of an application's kernels (IBDL_NO_PDL=1 turns it off): a kernel
+// may launch once every CTA of the previous one has passed its wait, and it waits in turn before
+// it reads anything; the launch latency is taken while the previous kernel drains.
+inline bool use_pdl3() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("IBDL_NO_PDL");
+    v = (e && atoi(e) != 0) ? 0 : 1;
+  }
+  return v == 1;
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch3(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads3);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = use_pdl3() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <typename T, int OP, int L>
 ibdl_status launch_apply_3d(Geometry* g, const Row3Params& rp, const Col3Params& cp, int R, int C, int Cz,
                             bool grid, cudaStream_t s) {
@@ -672,22 +716,22 @@ ibdl_status launch_apply_3d(Geometry* g, const Row3Params& rp, const Col3Params&
   const int rows_grid = n * (n / R), col_grid = n * ((n / 2) / C), z_grid = (n / 2 + 1) * ((n / 2) / Cz);
   const int st0 = f32 ? IBDL_STAGE_SPREAD_ROWFFT_FP32 : IBDL_STAGE_SPREAD_ROWFFT_FP64;
   if (g->timing) timing_mark(g, s, -1);
-  k3_spread_rowfft<T, OP, L><<<rows_grid, kThreads3, smem_rows3<T>(n, NIN, R), s>>>(rp);
+  IBDL_CUDA(launch3(k3_spread_rowfft<T, OP, L>, rows_grid, smem_rows3<T>(n, NIN, R), s, rp));
   if (g->timing) timing_mark(g, s, st0);
   Col3Params yp = cp;
   yp.nf = NIN;
-  k3_ypass<T, false, L><<<col_grid, kThreads3, smem_y3<T>(n, NIN, C), s>>>(yp);
+  IBDL_CUDA(launch3(k3_ypass<T, false, L>, col_grid, smem_y3<T>(n, NIN, C), s, yp));
   Col3Params zp = cp;
   zp.C = Cz;
   zp.lc = __builtin_ctz(Cz);
-  k3_zpass<T, OP, L><<<z_grid, kThreads3, smem_z3<T>(n, NMAX, Cz), s>>>(zp);
+  IBDL_CUDA(launch3(k3_zpass<T, OP, L>, z_grid, smem_z3<T>(n, NMAX, Cz), s, zp));
   yp.nf = NOUT;
-  k3_ypass<T, true, L><<<col_grid, kThreads3, smem_y3<T>(n, NOUT, C), s>>>(yp);
+  IBDL_CUDA(launch3(k3_ypass<T, true, L>, col_grid, smem_y3<T>(n, NOUT, C), s, yp));
   if (g->timing) timing_mark(g, s, st0 + 1);
   if (grid)
-    k3_rowifft_gather<T, OP, G3_GRID, L><<<rows_grid, kThreads3, smem_rows3<T>(n, NOUT, R), s>>>(rp);
+    IBDL_CUDA(launch3(k3_rowifft_gather<T, OP, G3_GRID, L>, rows_grid, smem_rows3<T>(n, NOUT, R), s, rp));
   else
-    k3_rowifft_gather<T, OP, G3_INTERP, L><<<rows_grid, kThreads3, smem_rows3<T>(n, NOUT, R), s>>>(rp);
+    IBDL_CUDA(launch3(k3_rowifft_gather<T, OP, G3_INTERP, L>, rows_grid, smem_rows3<T>(n, NOUT, R), s, rp));
   if (g->timing) timing_mark(g, s, st0 + 2);
   g->launches += 5;
   IBDL_CUDA(cudaGetLastError());
